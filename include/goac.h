@@ -1,0 +1,229 @@
+/*
+ * goac.h -- C ABI of the GB300 (sm_103a) library for the pairwise Coulomb
+ * cluster-expansion optimiser of "Optimization of Coulomb Energies in
+ * Gigantic Configurational Spaces of Multi-Element Ionic Crystals" (GOAC).
+ *
+ * Conventions (apply to every entry point):
+ *  - Pointers named *_dev are device pointers on the context's device, owned
+ *    by the caller; *_host pointers are host memory owned by the caller.
+ *    Shapes are row-major; "B x Nv" means B rows of Nv contiguous entries.
+ *  - Work is enqueued on the context's CUDA stream and is stream-ordered.
+ *    Calls that say "synchronises" block until their work is finished.
+ *  - The library allocates only its own scratch memory (owned by a context or
+ *    a problem, freed by the matching destroy call).
+ *  - Every call returns a goac_status; on failure goac_last_error() gives a
+ *    message (thread-local).  No C++ exception crosses the ABI.
+ *  - Bounded waits: no kernel of this library waits without an iteration
+ *    limit; a wait that runs out sets a device error word that the next
+ *    synchronising call reports as GOAC_ERR_TIMEOUT.
+ *  - Problems: N sites; site_class[i] = -1 marks a fixed ion of charge
+ *    fixed_q[i], otherwise the index (0..n_class-1) of the partially
+ *    occupied site class the position belongs to (the paper's "site" with
+ *    P_s positions, Eq. 1).  S species with charges z[s]; counts[k*S + s] is
+ *    the number of ions of species s in class k (the occupancies O_i of
+ *    Eq. 2c1; 0 = species not allowed in that class).  A configuration is one
+ *    int8 species index per variable site, variable sites in ascending site
+ *    order (Nv of them), which satisfies Eq. 2c2/2c3 by construction.
+ *  - Energies in eV, lengths in Angstrom, kT in eV.
+ */
+#ifndef GOAC_H
+#define GOAC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t goac_status;
+
+#define GOAC_OK 0
+#define GOAC_ERR_INVALID_ARG (-1)   /* bad sizes, pointers, counts             */
+#define GOAC_ERR_CUDA (-2)          /* a CUDA runtime/driver call failed        */
+#define GOAC_ERR_OOM (-3)           /* scratch allocation failed                */
+#define GOAC_ERR_NOT_NEUTRAL (-4)   /* total charge |sum q| > 1e-9              */
+#define GOAC_ERR_TIMEOUT (-5)       /* a bounded device wait ran out            */
+#define GOAC_ERR_INTERNAL (-6)      /* device-side consistency check failed     */
+#define GOAC_ERR_UNSUPPORTED (-7)   /* device is not sm_103 / feature missing   */
+
+/* Arithmetic forms of the batched scoring E = q^T J q. */
+#define GOAC_PREC_F64 0     /* FP64 CUDA-core GEMM: the plain path              */
+#define GOAC_PREC_TF32 1    /* tcgen05 kind::tf32, J rounded to TF32, 1 term     */
+#define GOAC_PREC_TF32X2 2  /* tcgen05 kind::tf32, J = hi + lo (TF32 each)       */
+#define GOAC_PREC_BF16X2 3  /* tcgen05 kind::f16 (BF16), J = J1 + J2             */
+#define GOAC_PREC_BF16X3 4  /* tcgen05 kind::f16 (BF16), J = J1 + J2 + J3        */
+#define GOAC_PREC_F32 5     /* FP32 CUDA cores (Monte Carlo / GA variant only)   */
+
+typedef struct goac_ctx goac_ctx;
+typedef struct goac_problem goac_problem;
+
+/* Last error message of the calling thread ("" if none).  Never NULL. */
+const char* goac_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int32_t goac_version(void);
+
+/* Create a context on `device` that enqueues on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Fails with GOAC_ERR_UNSUPPORTED unless
+ * the device is compute capability 10.3 (GB300). */
+goac_status goac_ctx_create(int32_t device, void* stream, goac_ctx** out);
+goac_status goac_ctx_destroy(goac_ctx* ctx);
+goac_status goac_ctx_set_stream(goac_ctx* ctx, void* stream);
+/* Synchronise the context stream and report any device error word. */
+goac_status goac_ctx_synchronize(goac_ctx* ctx);
+
+/* ------------------------------------------------------------------------ *
+ * Ewald pair matrix J (Section "Cluster Expansion of Coulomb Energy": the  *
+ * second-order expansion is exact for point charges; its coefficients are  *
+ * Ewald energies).  With q the charges of all N sites, E = q^T J q where    *
+ *   J_ij = ke/2 [ sum'_n erfc(alpha|d+n|)/|d+n|                             *
+ *               + (4 pi/V) sum_{0<|k|<=kcut} exp(-k^2/4alpha^2)/k^2 cos(k.d)*
+ *               - (2 alpha/sqrt(pi)) delta_ij - pi/(V alpha^2) ],           *
+ * d = minimum-image r_j - r_i (fractional components wrapped to [-1/2,1/2)),*
+ * n over lattice translations |n_a| <= nimg[a] (n = 0 dropped for i == j),  *
+ * k over reciprocal vectors with |k| <= kcut (both k and -k).  Real-space   *
+ * terms with alpha|d+n| >= 8 (erfc < 1.2e-29) are skipped.                  *
+ *   lattice_host: 3x3 row-major, rows = lattice vectors (Angstrom).         *
+ *   frac_dev: N x 3 fractional coordinates.  ke: e^2/(4 pi eps0) in eV*A.   *
+ *   J_dev: N x N FP64 output (row-major, exactly symmetric).                *
+ * Synchronises (sizes of the reciprocal set are read back).                 *
+ * ------------------------------------------------------------------------ */
+goac_status goac_build_ewald(goac_ctx* ctx, const double* lattice_host, const double* frac_dev, int32_t N,
+                             double alpha, const int32_t* nimg_host, double kcut, double ke, double* J_dev);
+
+/* ------------------------------------------------------------------------ *
+ * Problem (Eq. 2 with its constraints).  Copies what it needs from J_dev:   *
+ * J_vv (variable-variable block), its diagonal, phi_fix = J_vf q_f and      *
+ * E_const = q_f^T J_ff q_f (the paper's zero-order term and the fixed-ion   *
+ * share of the first-order term), so that                                   *
+ *   E = q_v^T J_vv q_v + 2 q_v . phi_fix + E_const.                         *
+ * All array arguments except J_dev are host arrays.  Checks that every      *
+ * class's counts add up to its size and that the total charge is neutral   *
+ * (|sum q| <= 1e-9, else GOAC_ERR_NOT_NEUTRAL unless allow_charged != 0).   *
+ * Synchronises.                                                             *
+ * ------------------------------------------------------------------------ */
+goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, int32_t N, const int32_t* site_class_host,
+                                const double* fixed_q_host, const double* z_host, int32_t S,
+                                const int32_t* counts_host, int32_t n_class, int32_t allow_charged,
+                                goac_problem** out);
+goac_status goac_problem_destroy(goac_problem* prob);
+/* Nv and E_const of a problem (host outputs; either may be NULL). */
+goac_status goac_problem_info(const goac_problem* prob, int32_t* Nv, double* E_const);
+/* Copy phi_fix (Nv doubles) to a device buffer. */
+goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
+
+/* ------------------------------------------------------------------------ *
+ * Batched scoring of a population (Eq. 2 objective, one energy per config): *
+ *   E_b = q_b^T J_vv q_b + 2 q_b . phi_fix + E_const.                       *
+ *   species_dev: B x Nv int8.  E_dev: B doubles.  precision: GOAC_PREC_*.   *
+ * F64 is the plain path; the tensor-core forms split J into TF32 / BF16     *
+ * terms, accumulate J.Q in FP32 on tcgen05 and form E in FP64.              *
+ * ------------------------------------------------------------------------ */
+goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
+
+/* Same, with host buffers: copies species H2D, scores, copies E D2H on the  *
+ * context stream and synchronises (end-to-end entry point).                 */
+goac_status goac_score_host(goac_problem* prob, const int8_t* species_host, int32_t B, int32_t precision,
+                            double* E_host);
+
+/* Top-k "n lowest structures" (Section "Implementation and Theoretical      *
+ * Background": the n lowest configurations are the output).  Selects the k  *
+ * lowest E_approx (ties: lower index), rescores them in FP64 and returns     *
+ * them sorted by the FP64 energy (ties: lower index).  idx_dev: k int32,    *
+ * E_dev: k doubles.  1 <= k <= min(B, 1024).                                 */
+goac_status goac_topk_rescore(goac_problem* prob, const int8_t* species_dev, int32_t B, const double* E_approx_dev,
+                              int32_t k, int32_t* idx_dev, double* E_dev);
+
+/* Random valid structures (SI, Random (R)): each class receives its multiset *
+ * of species in uniformly random order (Fisher-Yates; draw t of class k for  *
+ * configuration b is word t%4 of Philox4x32-10(ctr={t/4, b, k, 5}, seed)).   */
+goac_status goac_random_configs(goac_problem* prob, int32_t B, uint64_t seed, int8_t* species_dev);
+
+/* ------------------------------------------------------------------------ *
+ * Parallel-chain Metropolis swap Monte Carlo (SI, Monte Carlo): chain c,    *
+ * step t draws x = Philox4x32-10(ctr = {t_lo, t_hi, c, 0}, key = seed);     *
+ * class: the only movable class, else word 0 of Philox(ctr={t_lo,t_hi,c,1})  *
+ * with weight n_k(n_k - 1); positions a = (x0 n)>>32, b' = (x1 (n-1))>>32,   *
+ * b = b' + (b' >= a); u = ((x2>>5) 2^26 + (x3>>6)) 2^-53.  Equal species: a  *
+ * no-op.  Accept iff dE <= 1e-9 eV or u < exp(-dE/kT) (kT <= 0: the first  *
+ * test only; |dE| <= 1e-9 eV is read as dE = 0, the rounding of symmetric   *
+ * swaps),                                                                   *
+ *   dE = 2 d (phi_a - phi_b) + d^2 (J_aa + J_bb - 2 J_ab), d = q_b - q_a,    *
+ * phi = J q held per chain; on acceptance phi += d (J_:a - J_:b).           *
+ *   species_dev: C x Nv in/out.  kT_dev: C.  Steps step0 .. step0+n_steps-1 *
+ *   (resuming at step0 continues the same stream).  E_dev, bestE_dev: C     *
+ *   doubles out; best_species_dev: C x Nv out (nullable); n_accept_dev: C    *
+ *   int64 out (nullable).  precision: GOAC_PREC_F64 (trajectory-exact to    *
+ *   the FP64 definition) or GOAC_PREC_F32 (phi and J rows in FP32).         *
+ * ------------------------------------------------------------------------ */
+goac_status goac_mc_run(goac_problem* prob, int8_t* species_dev, int32_t C, const double* kT_dev, int64_t n_steps,
+                        uint64_t seed, uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
+                        int8_t* best_species_dev, int64_t* n_accept_dev);
+
+/* ------------------------------------------------------------------------ *
+ * Batched Monte Carlo over many independent problems in one persistent      *
+ * launch (the paper runs independent heuristic runs in parallel, Section    *
+ * "Internal Fortran Heuristics in GOAC").  For problem p: chains[p] chains, *
+ * species_dev[p] (chains[p] x Nv_p, in/out), kT_dev[p] (chains[p]),         *
+ * E_dev[p] / bestE_dev[p] (chains[p], out), seed + p as the Philox key.     *
+ * Host arrays of length n_probs hold the per-problem pointers.  Each chain  *
+ * is the same stream as goac_mc_run with that problem and key.  A device    *
+ * work queue hands (problem, chain) items to warps; no spin-waits.          *
+ * use_graph != 0 captures the launch sequence in a CUDA graph (replayed on  *
+ * later calls with the same arguments).                                      *
+ * ------------------------------------------------------------------------ */
+goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs,
+                              int8_t* const* species_dev, const int32_t* chains, const double* const* kT_dev,
+                              int64_t n_steps, uint64_t seed, uint64_t step0, int32_t precision,
+                              double* const* E_dev, double* const* bestE_dev, int32_t chains_per_cta,
+                              int32_t mode);
+
+/* ------------------------------------------------------------------------ *
+ * Genetic algorithm, one generation (SI, Genetic Algorithm; roulette wheel *
+ * selection).  pop_dev P x Nv with energies E_dev (P).  Children 0..e-1 are *
+ * the n_elite lowest (E, index).  Roulette on F_b = floor((Emax - E_b) /     *
+ * (Emax - Emin) 2^24) (all 1 if Emax == Emin): a 64-bit draw x picks the    *
+ * first b whose running sum of F exceeds (x F_total) >> 64; parents of child *
+ * c in generation gen: x_A = w0:w1, x_B = w2:w3 of Philox(ctr={0,gen,c,2}). *
+ * Crossover from A: for each site i ascending with child_i != B_i, j = the  *
+ * lowest site of i's class with child_j == B_i and B_j != B_i; candidate k  *
+ * is taken iff word k%4 of Philox(ctr={k/4,gen,c,3}) < 2^31.  Mutation: if  *
+ * w0 of Philox(ctr={0,gen,c,4}) < p_mut_u32, one swap (class from w1,       *
+ * positions from w2, w3 as in the Monte Carlo pick).                         *
+ *   children_dev P x Nv out; parents_dev (P x 2 int32) and nswap_dev        *
+ *   (P x 2 int32: swaps taken, candidates) are optional outputs.            *
+ * ------------------------------------------------------------------------ */
+goac_status goac_ga_generation(goac_problem* prob, const int8_t* pop_dev, const double* E_dev, int32_t P,
+                               int32_t n_elite, uint32_t p_mut_u32, uint32_t gen, uint64_t seed,
+                               int8_t* children_dev, int32_t* parents_dev, int32_t* nswap_dev);
+
+/* GA run: scores pop_dev, then n_gen x (generation + rescoring of every     *
+ * child with `precision`; with a tensor-core precision the FP64 energy is    *
+ * used only through the split form).  pop_dev (P x Nv) and E_dev (P) are    *
+ * in/out.  Generations are numbered gen0, gen0 + 1, ...                     */
+goac_status goac_ga_run(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
+                        int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0, int32_t precision);
+
+/* ------------------------------------------------------------------------ *
+ * Relaxed occupations (differentiable form; the paper's descent is discrete,*
+ * SI Gradient Descent).  logits_dev: B x Nv x S float; p = softmax over the *
+ * species allowed in each site's class; q_v = sum_s p_vs z_s;               *
+ *   E = q^T J q + lambda sum_{k,s allowed} (sum_{v in k} p_vs - n_ks)^2,    *
+ *   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks),             *
+ *   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)  (0 for masked species).       *
+ * E_dev: B doubles; dlogits_dev: B x Nv x S floats (nullable).  precision: *
+ * GOAC_PREC_F64 or GOAC_PREC_TF32X2 (J.Q on tcgen05, Q split in TF32 too).  *
+ * ------------------------------------------------------------------------ */
+goac_status goac_energy_grad(goac_problem* prob, const float* logits_dev, int32_t B, double lambda,
+                             int32_t precision, double* E_dev, float* dlogits_dev);
+
+/* Round relaxed occupations p (B x Nv x S float) to valid configurations:    *
+ * per class, (site, species) pairs by p descending (ties: lower site, then   *
+ * lower species) are assigned when the site is free and the species quota   *
+ * is left.  species_dev: B x Nv int8 out.                                    */
+goac_status goac_round_to_counts(goac_problem* prob, const float* p_dev, int32_t B, int8_t* species_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOAC_H */

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 
@@ -22,7 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "goac_oracle.c")
-_BUILD_DIR = os.path.join(_HERE, "_build")
+_BUILD_DIR = os.path.join(_HERE, "_build", platform.machine())
 _LIB_PATH = os.path.join(_BUILD_DIR, "libgoac_oracle.so")
 _lock = threading.Lock()
 _lib = None

@@ -44,6 +44,8 @@
 #include <string.h>
 
 #define ORC_PI 3.14159265358979323846
+/* Energy changes within this many eV of zero count as zero (Metropolis rule). */
+#define ORC_DE_ZERO 1e-9
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
@@ -624,8 +626,9 @@ int orc_random_configs(int64_t N, const int32_t* site_class, int32_t S, const in
 /*   class: only movable class, else from Philox(ctr={t_lo,t_hi,c,1})[0];  */
 /*   positions a = pos[x0*n >> 32], b = pos[b' + (b' >= a)], b' = x1*(n-1)>>32;*/
 /*   u = ((x2 >> 5) * 2^26 + (x3 >> 6)) * 2^-53 in [0, 1).                   */
-/* Equal species: a no-op trial.  Otherwise accept iff dE <= 0 or            */
-/* u < exp(-dE/kT) (kT <= 0: dE <= 0 only).  On acceptance the species are   */
+/* Equal species: a no-op trial.  Otherwise accept iff dE <= 1e-9 eV or      */
+/* u < exp(-dE/kT) (kT <= 0: dE <= 1e-9 eV only); |dE| <= 1e-9 eV is read as */
+/* dE = 0, since swaps related by symmetry give +-1e-14 eV under rounding.  On acceptance the species are   */
 /* swapped, phi_w += d (J[w,ia] - J[w,ib]) for every variable w (ascending),*/
 /* and E += dE.  The best E seen (strictly lower) and its configuration are */
 /* kept.  Returns the number of accepted swaps per chain in n_accept, and,   */
@@ -677,7 +680,7 @@ int orc_mc_run(const double* J, int64_t N, const int32_t* site_class, const doub
             double dE = 2.0 * d * (phi[va] - phi[vb]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
             double u = ((double)(x[2] >> 5) * 67108864.0 + (double)(x[3] >> 6)) * (1.0 / 9007199254740992.0);
             int accept;
-            if (dE <= 0.0) accept = 1;
+            if (dE <= ORC_DE_ZERO) accept = 1;
             else if (kT[ch] <= 0.0) accept = 0;
             else accept = u < exp(-dE / kT[ch]);
             if (!accept) continue;
@@ -720,7 +723,8 @@ int orc_mc_run(const double* J, int64_t N, const int32_t* site_class, const doub
 /*     and B_j != B_i (one exists because class counts agree); draw k of the */
 /*     child is word k%4 of Philox(ctr = {k/4, g, c, 3}); the swap i<->j is   */
 /*     taken iff that word < 2^31 (probability 1/2).                          */
-/*  4. Mutation: y = Philox(ctr = {0, g, c, 4}); if y0 < p_mut_u32 one swap   */
+/*  4. Mutation: y = Philox(ctr = {0, g, c, 4}); if y0 < p_mut_u32 (and some */
+/*     class has two positions) one swap                                      */
 /*     of two positions of one class (class from y1, positions from y2, y3 as */
 /*     in the Monte Carlo pair pick) is applied.                              */
 /* parents_out (P x 2) and nswap_out (P x 2: swaps taken, candidate swaps)   */
@@ -813,7 +817,7 @@ int orc_ga_generation(int64_t N, const int32_t* site_class, const int8_t* pop, c
         }
         uint32_t y[4];
         philox_draw(seed, 0u, gen, (uint32_t)c, 4u, y);
-        if (y[0] < p_mut_u32) {
+        if (y[0] < p_mut_u32 && cl.nmovable > 0) {
             int kc = pick_class(&cl, y[1]);
             int64_t va, vb;
             pick_pair(&cl, kc, y[2], y[3], &va, &vb);

@@ -1,0 +1,292 @@
+"""GB300 (sm_103a) library for the pairwise Coulomb cluster-expansion optimiser
+of "Optimization of Coulomb Energies in Gigantic Configurational Spaces of
+Multi-Element Ionic Crystals" (GOAC).
+
+This package is a thin binding over the C ABI of ``libgoac.so``
+(``include/goac.h``): it turns torch CUDA tensors into device pointers, the
+caller's current CUDA stream into the context stream, and status codes into
+exceptions.  Every step of the computation runs in the library's CUDA kernels;
+nothing here computes, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+import weakref
+
+import numpy as np
+import torch
+
+from ._lib import lib, LIB_PATH, SIGNATURES  # noqa: F401  (raises if the library is missing)
+
+#: Coulomb constant e^2 / (4 pi eps0) in eV * Angstrom (CODATA 2018).
+KE = 14.3996454784
+
+PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5}
+
+
+class GoacError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.goac_last_error().decode(errors="replace")
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GoacError(rc, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous array")
+        return C.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+class Context:
+    """A library context on one GPU, enqueuing on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib.goac_ctx_create(self.device, C.c_void_p(stream), C.byref(h)), "goac_ctx_create")
+        self._h = h
+        self._problems = weakref.WeakSet()
+        _live_contexts.add(self)
+
+    @property
+    def handle(self):
+        self.sync_stream()
+        return self._h
+
+    def sync_stream(self):
+        """Point the context at torch's current stream of its device."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib.goac_ctx_set_stream(self._h, C.c_void_p(stream)), "goac_ctx_set_stream")
+
+    def synchronize(self):
+        _check(lib.goac_ctx_synchronize(self.handle), "goac_ctx_synchronize")
+
+    def close(self):
+        """Destroy the context after every problem created on it."""
+        if getattr(self, "_h", None):
+            for p in list(getattr(self, "_problems", ())):
+                p.close()
+            lib.goac_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    for c in list(_live_contexts):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
+def build_ewald(ctx: Context, lattice, frac: torch.Tensor, alpha: float, nimg, kcut: float, ke: float = KE,
+                out: torch.Tensor | None = None) -> torch.Tensor:
+    """Ewald pair matrix J (N x N FP64 on the device); see goac_build_ewald."""
+    lat = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+    img = np.ascontiguousarray(nimg, dtype=np.int32).reshape(3)
+    frac = frac.to(device=f"cuda:{ctx.device}", dtype=torch.float64).contiguous()
+    N = frac.shape[0]
+    J = out if out is not None else torch.empty((N, N), dtype=torch.float64, device=frac.device)
+    _check(lib.goac_build_ewald(ctx.handle, _ptr(lat), _ptr(frac), N, float(alpha), _ptr(img), float(kcut),
+                                float(ke), _ptr(J)), "goac_build_ewald")
+    return J
+
+
+class Problem:
+    """Eq. 2 problem on the device (J_vv, phi_fix, E_const, classes, counts)."""
+
+    def __init__(self, ctx: Context, J: torch.Tensor, site_class, fixed_q, z, counts, allow_charged: bool = False):
+        self.ctx = ctx
+        sc = np.ascontiguousarray(site_class, dtype=np.int32)
+        fq = np.ascontiguousarray(fixed_q, dtype=np.float64)
+        zz = np.ascontiguousarray(z, dtype=np.float64)
+        cnt = np.ascontiguousarray(counts, dtype=np.int32)
+        self.S = int(zz.shape[0])
+        self.n_class = int(cnt.size // self.S)
+        self.N = int(sc.shape[0])
+        h = C.c_void_p()
+        _check(lib.goac_problem_create(ctx.handle, _ptr(J), self.N, _ptr(sc), _ptr(fq), _ptr(zz), self.S, _ptr(cnt),
+                                       self.n_class, int(bool(allow_charged)), C.byref(h)), "goac_problem_create")
+        self._h = h
+        ctx._problems.add(self)
+        nv = C.c_int32()
+        ec = C.c_double()
+        _check(lib.goac_problem_info(h, C.byref(nv), C.byref(ec)), "goac_problem_info")
+        self.Nv = int(nv.value)
+        self.E_const = float(ec.value)
+
+    @property
+    def handle(self):
+        self.ctx.sync_stream()
+        return self._h
+
+    def phi_fix(self) -> torch.Tensor:
+        out = torch.empty(self.Nv, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(lib.goac_problem_phi_fix(self.handle, _ptr(out)), "goac_problem_phi_fix")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            if getattr(self.ctx, "_h", None):
+                lib.goac_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return f"cuda:{self.ctx.device}"
+
+    # ---- scoring --------------------------------------------------------
+    def score(self, species: torch.Tensor, precision="f64", out: torch.Tensor | None = None) -> torch.Tensor:
+        B = species.shape[0]
+        E = out if out is not None else torch.empty(B, dtype=torch.float64, device=self._dev())
+        _check(lib.goac_score(self.handle, _ptr(species), B, _prec(precision), _ptr(E)), "goac_score")
+        return E
+
+    def score_host(self, species: np.ndarray | torch.Tensor, precision="f64", out=None):
+        """End-to-end scoring from host memory (pinned torch tensors are fastest)."""
+        if isinstance(species, torch.Tensor):
+            assert not species.is_cuda and species.is_contiguous()
+            sp_ptr = C.c_void_p(species.data_ptr())
+            B = species.shape[0]
+            E = out if out is not None else torch.empty(B, dtype=torch.float64, pin_memory=True)
+            e_ptr = C.c_void_p(E.data_ptr())
+        else:
+            species = np.ascontiguousarray(species, dtype=np.int8)
+            sp_ptr = _ptr(species)
+            B = species.shape[0]
+            E = out if out is not None else np.empty(B, dtype=np.float64)
+            e_ptr = _ptr(E)
+        _check(lib.goac_score_host(self.handle, sp_ptr, B, _prec(precision), e_ptr), "goac_score_host")
+        return E
+
+    def topk_rescore(self, species: torch.Tensor, E_approx: torch.Tensor, k: int):
+        idx = torch.empty(k, dtype=torch.int32, device=self._dev())
+        E = torch.empty(k, dtype=torch.float64, device=self._dev())
+        _check(lib.goac_topk_rescore(self.handle, _ptr(species), species.shape[0], _ptr(E_approx), int(k), _ptr(idx),
+                                     _ptr(E)), "goac_topk_rescore")
+        return idx, E
+
+    def random_configs(self, B: int, seed: int) -> torch.Tensor:
+        out = torch.empty((B, self.Nv), dtype=torch.int8, device=self._dev())
+        _check(lib.goac_random_configs(self.handle, int(B), int(seed), _ptr(out)), "goac_random_configs")
+        return out
+
+    # ---- Monte Carlo ----------------------------------------------------
+    def mc_run(self, species: torch.Tensor, kT, n_steps: int, seed: int, step0: int = 0, precision="f64",
+               want_best_species: bool = True):
+        """Runs in place on `species` (C x Nv int8).  Returns a dict of device tensors."""
+        Cn = species.shape[0]
+        dev = self._dev()
+        kTt = torch.as_tensor(kT, dtype=torch.float64, device=dev).expand(Cn).contiguous()
+        E = torch.empty(Cn, dtype=torch.float64, device=dev)
+        bestE = torch.empty(Cn, dtype=torch.float64, device=dev)
+        best = torch.empty_like(species) if want_best_species else None
+        nacc = torch.empty(Cn, dtype=torch.int64, device=dev)
+        _check(lib.goac_mc_run(self.handle, _ptr(species), Cn, _ptr(kTt), int(n_steps), int(seed), int(step0),
+                               _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)), "goac_mc_run")
+        return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
+
+    # ---- genetic algorithm ----------------------------------------------
+    def ga_generation(self, pop: torch.Tensor, E: torch.Tensor, n_elite: int, p_mut_u32: int, gen: int, seed: int,
+                      record: bool = False):
+        P = pop.shape[0]
+        dev = self._dev()
+        kids = torch.empty_like(pop)
+        parents = torch.empty((P, 2), dtype=torch.int32, device=dev) if record else None
+        nsw = torch.empty((P, 2), dtype=torch.int32, device=dev) if record else None
+        _check(lib.goac_ga_generation(self.handle, _ptr(pop), _ptr(E), P, int(n_elite), int(p_mut_u32), int(gen),
+                                      int(seed), _ptr(kids), _ptr(parents), _ptr(nsw)), "goac_ga_generation")
+        return kids, parents, nsw
+
+    def ga_run(self, pop: torch.Tensor, n_gen: int, n_elite: int, p_mut_u32: int, seed: int, gen0: int = 0,
+               precision="f64"):
+        """Runs in place on `pop` (P x Nv).  Returns the final energies."""
+        P = pop.shape[0]
+        E = torch.empty(P, dtype=torch.float64, device=self._dev())
+        _check(lib.goac_ga_run(self.handle, _ptr(pop), _ptr(E), P, int(n_gen), int(n_elite), int(p_mut_u32),
+                               int(seed), int(gen0), _prec(precision)), "goac_ga_run")
+        return E
+
+    # ---- relaxed occupations --------------------------------------------
+    def energy_grad(self, logits: torch.Tensor, lam: float, precision="f64", want_grad: bool = True):
+        B = logits.shape[0]
+        E = torch.empty(B, dtype=torch.float64, device=self._dev())
+        g = torch.empty_like(logits) if want_grad else None
+        _check(lib.goac_energy_grad(self.handle, _ptr(logits), B, float(lam), _prec(precision), _ptr(E), _ptr(g)),
+               "goac_energy_grad")
+        return E, g
+
+    def round_to_counts(self, p: torch.Tensor) -> torch.Tensor:
+        B = p.shape[0]
+        out = torch.empty((B, self.Nv), dtype=torch.int8, device=self._dev())
+        _check(lib.goac_round_to_counts(self.handle, _ptr(p), B, _ptr(out)), "goac_round_to_counts")
+        return out
+
+
+def batch_mc_run(ctx: Context, problems, species, kT, n_steps: int, seed: int, step0: int = 0, precision="f64",
+                 chains_per_cta: int = 4, mode: int = 2):
+    """Batched MC over independent problems (goac_batch_mc_run).  Returns (E, bestE) lists."""
+    n = len(problems)
+    dev = f"cuda:{ctx.device}"
+    E = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in species]
+    bE = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in species]
+    P = (C.c_void_p * n)(*[p._h.value for p in problems])
+    SP = (C.c_void_p * n)(*[s.data_ptr() for s in species])
+    CH = (C.c_int32 * n)(*[s.shape[0] for s in species])
+    KT = (C.c_void_p * n)(*[t.data_ptr() for t in kT])
+    EE = (C.c_void_p * n)(*[t.data_ptr() for t in E])
+    BE = (C.c_void_p * n)(*[t.data_ptr() for t in bE])
+    _check(lib.goac_batch_mc_run(ctx.handle, P, n, SP, CH, KT, int(n_steps), int(seed), int(step0), _prec(precision),
+                                 EE, BE, int(chains_per_cta), int(mode)), "goac_batch_mc_run")
+    return E, bE
+
+
+class RelaxedEnergy(torch.autograd.Function):
+    """E(logits) for relaxed occupations with the library's hand-written
+    adjoint (goac_energy_grad) as the backward pass."""
+
+    @staticmethod
+    def forward(ctx, logits, problem, lam, precision):
+        E, g = problem.energy_grad(logits.contiguous(), lam, precision, want_grad=True)
+        ctx.save_for_backward(g)
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        (g,) = ctx.saved_tensors
+        return g * gE.to(g.dtype).view(-1, 1, 1), None, None, None

@@ -1,0 +1,354 @@
+// Genetic algorithm (SI, Genetic Algorithm: roulette-wheel selection,
+// crossover by random atom swaps that take half of the differences between
+// the parents, random mutation, elitism), one generation per call and a
+// driver that rescores every child between generations.
+//
+// Device layout:
+//   k_ga_minmax   one block: E_min, E_max of the population.
+//   k_ga_fitness  F_b = floor((Emax - E_b)/(Emax - Emin) 2^24) and its running
+//                 sum as exact 64-bit integers (one block, ordered scan), so
+//                 roulette selection is an exact integer search.
+//   k_ga_rank     ranks by (E, index) to pick the elite (O(P^2) comparisons,
+//                 tiled through shared memory).
+//   k_ga_children one warp per child: parents by binary search of the running
+//                 sum, crossover in shared memory (the warp scans 32 sites at a
+//                 time with ballots; the partner site j of a candidate swap is
+//                 the lowest position of the class with child_j == B_i and
+//                 B_j != B_i, found by a ballot over the class's positions),
+//                 Philox draws per candidate, mutation, write-back.
+#include "common.cuh"
+
+namespace {
+
+__global__ void k_ga_minmax(const double* __restrict__ E, int P, double* __restrict__ mm)
+{
+    __shared__ double smin[1024], smax[1024];
+    double lo = E[0], hi = E[0];
+    for (int b = threadIdx.x; b < P; b += blockDim.x) {
+        lo = fmin(lo, E[b]);
+        hi = fmax(hi, E[b]);
+    }
+    smin[threadIdx.x] = lo;
+    smax[threadIdx.x] = hi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w; w >>= 1) {
+        if (threadIdx.x < w) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mm[0] = smin[0];
+        mm[1] = smax[0];
+    }
+}
+
+// Inclusive running sum of the integer fitness, in index order.
+__global__ void __launch_bounds__(1024) k_ga_fitness(const double* __restrict__ E, int P,
+                                                     const double* __restrict__ mm, unsigned long long* __restrict__ pre,
+                                                     unsigned long long* __restrict__ ftot)
+{
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const double emin = mm[0], emax = mm[1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < P; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        unsigned long long f = 0;
+        if (b < P) f = emax > emin ? (unsigned long long)floor((emax - E[b]) / (emax - emin) * 16777216.0) : 1ull;
+        unsigned long long incl = f;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long v = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+            unsigned long long inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            warp_tot[lane] = inc - v;   // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const unsigned long long val = carry + warp_tot[wid] + incl;
+        if (b < P) pre[b] = val;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = val;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ftot = carry;
+}
+
+__global__ void k_ga_rank(const double* __restrict__ E, int P, int k, int* __restrict__ sel)
+{
+    __shared__ double tile[256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double ei = i < P ? E[i] : 0.0;
+    int rank = 0;
+    for (int j0 = 0; j0 < P; j0 += 256) {
+        const int j = j0 + threadIdx.x;
+        tile[threadIdx.x] = j < P ? E[j] : 0.0;
+        __syncthreads();
+        const int lim = min(256, P - j0);
+        if (i < P)
+            for (int t = 0; t < lim; ++t) {
+                const double ej = tile[t];
+                rank += (ej < ei) || (ej == ei && j0 + t < i);
+            }
+        __syncthreads();
+    }
+    if (i < P && rank < k) sel[rank] = i;
+}
+
+struct GaArgs {
+    const int8_t* pop;
+    int8_t* children;
+    const unsigned long long* pre;
+    const unsigned long long* ftot;
+    const int* elite;
+    int32_t* parents;
+    int32_t* nswap;
+    const int32_t* vclass;
+    const int32_t* cls_start;
+    const int32_t* cls_pos;
+    const uint32_t* wprefix;
+    int* err;
+    uint64_t seed;
+    uint32_t wtotal, p_mut, gen;
+    int P, Nv, n_elite, ncls, nmovable, only_movable;
+};
+
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ int lower_bound_gt(const unsigned long long* pre, int P, unsigned long long t)
+{
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] > t) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void k_ga_children(GaArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (c >= a.P) return;
+    const int Nv = a.Nv;
+    const size_t slot = (((size_t)Nv + 15) & ~(size_t)15) * 2;
+    int8_t* ch = (int8_t*)(smem + slot * wib);
+    int8_t* pb = ch + (slot >> 1);
+    int8_t* out = a.children + (long)c * Nv;
+
+    if (c < a.n_elite) {
+        const int src = a.elite[c];
+        for (int w = lane; w < Nv; w += 32) out[w] = a.pop[(long)src * Nv + w];
+        if (lane == 0) {
+            if (a.parents) a.parents[2 * c] = a.parents[2 * c + 1] = src;
+            if (a.nswap) a.nswap[2 * c] = a.nswap[2 * c + 1] = 0;
+        }
+        return;
+    }
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const uint4 x = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 2u), k0, k1);
+    const unsigned long long ftot = *a.ftot;
+    const unsigned long long xa = ((unsigned long long)x.x << 32) | x.y;
+    const unsigned long long xb = ((unsigned long long)x.z << 32) | x.w;
+    const int A = lower_bound_gt(a.pre, a.P, __umul64hi(xa, ftot));
+    const int B = lower_bound_gt(a.pre, a.P, __umul64hi(xb, ftot));
+    for (int w = lane; w < Nv; w += 32) {
+        ch[w] = a.pop[(long)A * Nv + w];
+        pb[w] = a.pop[(long)B * Nv + w];
+    }
+    __syncwarp();
+
+    uint32_t kc = 0;
+    int nsw = 0;
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    for (int i0 = 0; i0 < Nv; i0 += 32) {
+        int from = 0;
+        while (true) {
+            const int i = i0 + lane;
+            const bool diff = lane >= from && i < Nv && ch[i] != pb[i];
+            const uint32_t m = __ballot_sync(0xffffffffu, diff);
+            if (m == 0u) break;
+            const int l = __ffs(m) - 1;
+            const int ii = i0 + l;
+            const int8_t want = pb[ii];
+            const int cls = a.vclass[ii];
+            const int cs = a.cls_start[cls], ce = a.cls_start[cls + 1];
+            int j = -1;
+            for (int pp = cs; pp < ce; pp += 32) {
+                const int idx = pp + lane;
+                const int w = idx < ce ? a.cls_pos[idx] : 0;
+                const bool ok = idx < ce && ch[w] == want && pb[w] != want;
+                const uint32_t mm = __ballot_sync(0xffffffffu, ok);
+                if (mm) {
+                    j = __shfl_sync(0xffffffffu, w, __ffs(mm) - 1);
+                    break;
+                }
+            }
+            if (j < 0) {
+                if (lane == 0) goacd::report(a.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
+                return;
+            }
+            if ((kc & 3u) == 0u) blk = goacd::philox(make_uint4(kc >> 2, a.gen, (uint32_t)c, 3u), k0, k1);
+            const uint32_t wv = word_of(blk, (int)(kc & 3u));
+            ++kc;
+            if (wv < 0x80000000u) {
+                __syncwarp();
+                if (lane == 0) {
+                    ch[j] = ch[ii];
+                    ch[ii] = want;
+                }
+                __syncwarp();
+                ++nsw;
+            }
+            from = l + 1;
+        }
+    }
+    const uint4 y = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 4u), k0, k1);
+    if (y.x < a.p_mut && a.nmovable > 0) {
+        int k = a.only_movable;
+        if (a.nmovable != 1) {
+            const uint32_t thr = goacd::draw_below(y.y, a.wtotal);
+            k = a.ncls - 1;
+            for (int q = 0; q < a.ncls; ++q)
+                if (a.wprefix[q] > thr) {
+                    k = q;
+                    break;
+                }
+        }
+        const int start = a.cls_start[k];
+        const uint32_t n = (uint32_t)(a.cls_start[k + 1] - start);
+        const uint32_t pa = goacd::draw_below(y.z, n);
+        const uint32_t bb = goacd::draw_below(y.w, n - 1);
+        const uint32_t pbi = bb + (bb >= pa);
+        const int va = a.cls_pos[start + pa], vb = a.cls_pos[start + pbi];
+        __syncwarp();
+        if (lane == 0) {
+            const int8_t t = ch[va];
+            ch[va] = ch[vb];
+            ch[vb] = t;
+        }
+    }
+    __syncwarp();
+    for (int w = lane; w < Nv; w += 32) out[w] = ch[w];
+    if (lane == 0) {
+        if (a.parents) {
+            a.parents[2 * c] = A;
+            a.parents[2 * c + 1] = B;
+        }
+        if (a.nswap) {
+            a.nswap[2 * c] = nsw;
+            a.nswap[2 * c + 1] = (int32_t)kc;
+        }
+    }
+}
+
+}  // namespace
+
+namespace goac {
+
+static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const double* E, int P, int n_elite,
+                                      uint32_t p_mut, uint32_t gen, uint64_t seed, int8_t* children, int32_t* parents,
+                                      int32_t* nswap)
+{
+    goac_ctx* ctx = p->ctx;
+    cudaStream_t st = ctx->stream;
+    const size_t need = sizeof(unsigned long long) * ((size_t)P + 4) + sizeof(int) * ((size_t)n_elite + 4) +
+                        2 * sizeof(double) + 256;
+    goac_status rc = ensure(p->score_tmp, need);
+    if (rc) return rc;
+    char* base = (char*)p->score_tmp.ptr;
+    unsigned long long* pre = (unsigned long long*)base;
+    unsigned long long* ftot = pre + P;
+    double* mm = (double*)(ftot + 2);
+    int* elite = (int*)(mm + 2);
+    k_ga_minmax<<<1, 1024, 0, st>>>(E, P, mm);
+    k_ga_fitness<<<1, 1024, 0, st>>>(E, P, mm, pre, ftot);
+    if (n_elite > 0) k_ga_rank<<<(P + 255) / 256, 256, 0, st>>>(E, P, n_elite, elite);
+    GOAC_LAUNCH_CHECK("ga prep");
+    GaArgs a;
+    a.pop = pop;
+    a.children = children;
+    a.pre = pre;
+    a.ftot = ftot;
+    a.elite = elite;
+    a.parents = parents;
+    a.nswap = nswap;
+    a.vclass = p->vclass_dev;
+    a.cls_start = p->cls_start_dev;
+    a.cls_pos = p->cls_pos_dev;
+    a.wprefix = p->wprefix_dev;
+    a.err = ctx->d_err;
+    a.seed = seed;
+    a.wtotal = p->wtotal;
+    a.p_mut = p_mut;
+    a.gen = gen;
+    a.P = P;
+    a.Nv = p->Nv;
+    a.n_elite = n_elite;
+    a.ncls = p->ncls;
+    a.nmovable = p->nmovable;
+    a.only_movable = p->only_movable;
+    const size_t slot = (((size_t)p->Nv + 15) & ~(size_t)15) * 2;
+    int wpb = (int)((96 * 1024) / slot);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    if (slot > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
+    const size_t smem = slot * wpb;
+    GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_ga_children<<<(P + wpb - 1) / wpb, 32 * wpb, smem, st>>>(a);
+    GOAC_LAUNCH_CHECK("k_ga_children");
+    return GOAC_OK;
+}
+
+}  // namespace goac
+
+extern "C" goac_status goac_ga_generation(goac_problem* p, const int8_t* pop_dev, const double* E_dev, int32_t P,
+                                          int32_t n_elite, uint32_t p_mut_u32, uint32_t gen, uint64_t seed,
+                                          int8_t* children_dev, int32_t* parents_dev, int32_t* nswap_dev)
+{
+    if (!p || !pop_dev || !E_dev || !children_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL");
+    if (P <= 0 || n_elite < 0 || n_elite > P) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: bad sizes");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    return goac::ga_generation_impl(p, pop_dev, E_dev, P, n_elite, p_mut_u32, gen, seed, children_dev, parents_dev,
+                                    nswap_dev);
+}
+
+extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
+                                   int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0,
+                                   int32_t precision)
+{
+    if (!p || !pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
+    if (P <= 0 || n_gen < 0 || n_elite < 0 || n_elite > P)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    goac_status rc = goac::ensure(p->phi, (size_t)P * p->Nv);
+    if (rc) return rc;
+    int8_t* kids = (int8_t*)p->phi.ptr;
+    rc = goac_score(p, pop_dev, P, precision, E_dev);
+    if (rc) return rc;
+    for (int g = 0; g < n_gen; ++g) {
+        rc = goac::ga_generation_impl(p, pop_dev, E_dev, P, n_elite, p_mut_u32, gen0 + (uint32_t)g, seed, kids,
+                                      nullptr, nullptr);
+        if (rc) return rc;
+        GOAC_CUDA(cudaMemcpyAsync(pop_dev, kids, (size_t)P * p->Nv, cudaMemcpyDeviceToDevice, p->ctx->stream));
+        rc = goac_score(p, pop_dev, P, precision, E_dev);
+        if (rc) return rc;
+    }
+    return GOAC_OK;
+}

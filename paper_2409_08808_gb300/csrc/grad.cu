@@ -1,0 +1,316 @@
+// Relaxed occupations and their hand-written adjoint, and rounding back to
+// valid integer configurations.  (The paper's gradient descent is discrete,
+// SI Gradient Descent; the relaxed form seeds MC / GA populations.)
+//
+//   p_vs = softmax over the species allowed in v's class of the logits L_vs
+//   q_v  = sum_s p_vs z_s                      (fixed sites keep their charge)
+//   E    = q^T J q + lambda sum_{k,s allowed} (sum_{v in k} p_vs - n_ks)^2
+//   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks)
+//   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)
+//
+// (2 J q)_v = 2 (J_vv q_v + phi_fix)_v.  The contraction J_vv Q runs as an
+// FP64 tiled GEMM on the CUDA cores; the elementwise chain rule is fused into
+// one kernel per configuration.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+__global__ void k_softmax(const float* __restrict__ logits, long BN, int Nv, int S, const int32_t* __restrict__ vclass,
+                          const int32_t* __restrict__ counts, const double* __restrict__ z, double* __restrict__ p,
+                          double* __restrict__ q)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    const int v = (int)(t % Nv);
+    const int k = vclass[v];
+    const float* L = logits + t * S;
+    double m = -INFINITY;
+    for (int s = 0; s < S; ++s)
+        if (counts[k * S + s] > 0 && (double)L[s] > m) m = (double)L[s];
+    double den = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double e = counts[k * S + s] > 0 ? exp((double)L[s] - m) : 0.0;
+        p[t * S + s] = e;
+        den += e;
+    }
+    double qv = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double ps = p[t * S + s] / den;
+        p[t * S + s] = ps;
+        qv += ps * z[s];
+    }
+    q[t] = qv;
+}
+
+// colsum[(b*ncls + k)*S + s] = sum_{v in class k} p[b][v][s]; one block per (b, k).
+__global__ void k_colsum(const double* __restrict__ p, int Nv, int S, int ncls, const int32_t* __restrict__ cls_start,
+                         const int32_t* __restrict__ cls_pos, double* __restrict__ colsum)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x / ncls, k = blockIdx.x % ncls;
+    const int cs = cls_start[k], ce = cls_start[k + 1];
+    for (int s = 0; s < S; ++s) {
+        double acc = 0.0;
+        for (int i = cs + threadIdx.x; i < ce; i += blockDim.x) acc += p[((long)b * Nv + cls_pos[i]) * S + s];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) colsum[((long)b * ncls + k) * S + s] = red[0];
+        __syncthreads();
+    }
+}
+
+// Phi[b][v] = sum_w J_vv[v][w] Q[b][w] (FP64, 64x64 tiles, 4x4 per thread).
+constexpr int GM = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_phi_real(const double* __restrict__ J, int ld, int Nv,
+                                                  const double* __restrict__ Q, int B, double* __restrict__ Phi)
+{
+    __shared__ double As[GK][GM + 1];
+    __shared__ double Bs[GK][GM + 1];
+    const int b0 = blockIdx.x * GM, i0 = blockIdx.y * GM;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < Nv; k0 += GK) {
+        for (int e = threadIdx.x; e < GM * GK; e += 256) {
+            const int r = e / GK, c = e % GK;
+            const int gk = k0 + c;
+            As[c][r] = J[(long)(i0 + r) * ld + gk];
+            const int gb = b0 + r;
+            Bs[c][r] = (gb < B && gk < Nv) ? Q[(long)gb * Nv + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double a[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[k][ty * 4 + u];
+                bv[u] = Bs[k][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], bv[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int gi = i0 + ty * 4 + u, gb = b0 + tx * 4 + w;
+            if (gi < Nv && gb < B) Phi[(long)gb * Nv + gi] = acc[u][w];
+        }
+}
+
+// One block per configuration: energy (with the counts penalty) and dE/dL.
+__global__ void k_grad_finish(const double* __restrict__ p, const double* __restrict__ q,
+                              const double* __restrict__ Phi, const double* __restrict__ phifix,
+                              const double* __restrict__ colsum, const int32_t* __restrict__ vclass,
+                              const int32_t* __restrict__ counts, const double* __restrict__ z, int Nv, int S,
+                              int ncls, double lambda, double E_const, double* __restrict__ E,
+                              float* __restrict__ dlogits)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const double* cb = colsum + (long)b * ncls * S;
+    double acc = 0.0;
+    for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
+        const long t = (long)b * Nv + v;
+        const double jq = Phi[t] + phifix[v];     // (J q)_v over all sites
+        acc += q[t] * (jq + phifix[v]);
+        if (dlogits) {
+            const int k = vclass[v];
+            double g[64];
+            double pg = 0.0;
+            for (int s = 0; s < S; ++s) {
+                g[s] = z[s] * 2.0 * jq + 2.0 * lambda * (cb[k * S + s] - counts[k * S + s]);
+                pg += p[t * S + s] * g[s];
+            }
+            for (int s = 0; s < S; ++s)
+                dlogits[t * S + s] = counts[k * S + s] > 0 ? (float)(p[t * S + s] * (g[s] - pg)) : 0.0f;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double pen = 0.0;
+        for (int k = 0; k < ncls; ++k)
+            for (int s = 0; s < S; ++s)
+                if (counts[k * S + s] > 0) {
+                    const double r = cb[k * S + s] - counts[k * S + s];
+                    pen += r * r;
+                }
+        E[b] = red[0] + E_const + lambda * pen;
+    }
+}
+
+// ---- rounding to counts ------------------------------------------------------
+// Sort key of a (site v, species s) pair: p descending, then v, then s ascending.
+__device__ __forceinline__ unsigned long long pair_key(float pv, int v, int s)
+{
+    return ((unsigned long long)(~__float_as_uint(pv)) << 32) | ((unsigned long long)(uint32_t)v << 8) | (uint32_t)s;
+}
+
+__global__ void k_round_keys(const float* __restrict__ p, int Nv, int S, int ncls, const int32_t* __restrict__ cls_start,
+                             const int32_t* __restrict__ cls_pos, const int32_t* __restrict__ counts,
+                             const long long* __restrict__ seg_off, const int* __restrict__ seg_M, long long per_b,
+                             unsigned long long* __restrict__ keys)
+{
+    const int b = blockIdx.x / ncls, k = blockIdx.x % ncls;
+    const int cs = cls_start[k], n = cls_start[k + 1] - cs;
+    int allowed[64];
+    int na = 0;
+    for (int s = 0; s < S; ++s)
+        if (counts[k * S + s] > 0) allowed[na++] = s;
+    unsigned long long* out = keys + (long long)b * per_b + seg_off[k];
+    const int M = seg_M[k];
+    const long m = (long)n * na;
+    for (long e = threadIdx.x; e < M; e += blockDim.x) {
+        if (e < m) {
+            const int v = cls_pos[cs + (int)(e / na)];
+            const int s = allowed[e % na];
+            out[e] = pair_key(p[((long)b * Nv + v) * S + s], v, s);
+        } else {
+            out[e] = ~0ull;
+        }
+    }
+}
+
+// Bitonic sort of each (configuration, class) segment, one block per segment.
+__global__ void __launch_bounds__(1024) k_bitonic(unsigned long long* __restrict__ keys, int ncls,
+                                                  const long long* __restrict__ seg_off, const int* __restrict__ seg_M,
+                                                  long long per_b)
+{
+    const int b = blockIdx.x / ncls, k = blockIdx.x % ncls;
+    unsigned long long* a = keys + (long long)b * per_b + seg_off[k];
+    const int M = seg_M[k];
+    for (int size = 2; size <= M; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < M; i += blockDim.x) {
+                const int l = i ^ stride;
+                if (l > i) {
+                    const unsigned long long x = a[i], y = a[l];
+                    const bool up = (i & size) == 0;
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_round_greedy(const unsigned long long* __restrict__ keys, int B, int Nv, int S, int ncls,
+                               const int32_t* __restrict__ cls_start, const int32_t* __restrict__ counts,
+                               const long long* __restrict__ seg_off, long long per_b, int8_t* __restrict__ species,
+                               int* __restrict__ err)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * ncls) return;
+    const int b = (int)(t / ncls), k = (int)(t % ncls);
+    const int n = cls_start[k + 1] - cls_start[k];
+    int na = 0;
+    int left[64];
+    for (int s = 0; s < S; ++s) {
+        left[s] = counts[k * S + s];
+        na += left[s] > 0;
+    }
+    const unsigned long long* a = keys + (long long)b * per_b + seg_off[k];
+    const long m = (long)n * na;
+    int8_t* sp = species + (long)b * Nv;
+    int placed = 0;
+    for (long r = 0; r < m && placed < n; ++r) {
+        const unsigned long long key = a[r];
+        const int v = (int)((key & 0xffffffffull) >> 8);
+        const int s = (int)(key & 0xffull);
+        if (sp[v] >= 0 || left[s] == 0) continue;
+        sp[v] = (int8_t)s;
+        left[s]--;
+        placed++;
+    }
+    if (placed != n) goacd::report(err, GOAC_ERR_INTERNAL, goac::SITE_ROUND, (int)t);
+}
+
+}  // namespace
+
+extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev, int32_t B, double lambda,
+                                        int32_t precision, double* E_dev, float* dlogits_dev)
+{
+    if (!p || !logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
+    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0");
+    if (precision != GOAC_PREC_F64) return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: only GOAC_PREC_F64");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const int Nv = p->Nv, S = p->S, ncls = p->ncls;
+    const long BN = (long)B * Nv;
+    const size_t need = sizeof(double) * ((size_t)BN * S + 2 * (size_t)BN + (size_t)B * ncls * S) + 1024;
+    goac_status rc = goac::ensure(p->grad_tmp, need);
+    if (rc) return rc;
+    double* P_ = (double*)p->grad_tmp.ptr;
+    double* Q = P_ + BN * S;
+    double* Phi = Q + BN;
+    double* colsum = Phi + BN;
+    cudaStream_t st = p->ctx->stream;
+    k_softmax<<<(int)((BN + 255) / 256), 256, 0, st>>>(logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev, p->z_dev,
+                                                       P_, Q);
+    k_colsum<<<B * ncls, 256, 0, st>>>(P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
+    dim3 grid((B + GM - 1) / GM, (Nv + GM - 1) / GM);
+    k_phi_real<<<grid, 256, 0, st>>>(p->J_vv, p->Nv_pad, Nv, Q, B, Phi);
+    k_grad_finish<<<B, 256, 0, st>>>(P_, Q, Phi, p->phifix, colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
+                                     ncls, lambda, p->E_const, E_dev, dlogits_dev);
+    GOAC_LAUNCH_CHECK("goac_energy_grad");
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_round_to_counts(goac_problem* p, const float* p_dev, int32_t B, int8_t* species_dev)
+{
+    if (!p || !p_dev || !species_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: NULL");
+    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: B < 0");
+    if (p->Nv >= (1 << 24)) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: Nv too large");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const int ncls = p->ncls, S = p->S;
+    std::vector<long long> off(ncls);
+    std::vector<int> Ms(ncls);
+    long long per_b = 0;
+    for (int k = 0; k < ncls; ++k) {
+        int na = 0;
+        for (int s = 0; s < S; ++s) na += p->counts[k * S + s] > 0;
+        const long m = (long)(p->cls_start[k + 1] - p->cls_start[k]) * na;
+        int M = 1;
+        while (M < m) M <<= 1;
+        if (M > (1 << 26)) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: class too large");
+        off[k] = per_b;
+        Ms[k] = M;
+        per_b += M;
+    }
+    const size_t keys_bytes = sizeof(unsigned long long) * (size_t)per_b * B;
+    goac_status rc = goac::ensure(p->grad_tmp, keys_bytes + sizeof(long long) * ncls + sizeof(int) * ncls + 64);
+    if (rc) return rc;
+    unsigned long long* keys = (unsigned long long*)p->grad_tmp.ptr;
+    long long* d_off = (long long*)((char*)p->grad_tmp.ptr + keys_bytes);
+    int* d_M = (int*)(d_off + ncls);
+    cudaStream_t st = p->ctx->stream;
+    GOAC_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * ncls, cudaMemcpyHostToDevice, st));
+    GOAC_CUDA(cudaMemcpyAsync(d_M, Ms.data(), sizeof(int) * ncls, cudaMemcpyHostToDevice, st));
+    GOAC_CUDA(cudaMemsetAsync(species_dev, 0xff, (size_t)B * p->Nv, st));
+    k_round_keys<<<B * ncls, 256, 0, st>>>(p_dev, p->Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, p->counts_dev, d_off,
+                                           d_M, per_b, keys);
+    k_bitonic<<<B * ncls, 1024, 0, st>>>(keys, ncls, d_off, d_M, per_b);
+    const long nt = (long)B * ncls;
+    k_round_greedy<<<(int)((nt + 127) / 128), 128, 0, st>>>(keys, B, p->Nv, S, ncls, p->cls_start_dev, p->counts_dev,
+                                                            d_off, per_b, species_dev, p->ctx->d_err);
+    GOAC_LAUNCH_CHECK("goac_round_to_counts");
+    return GOAC_OK;
+}

@@ -1,0 +1,465 @@
+// Parallel-chain Metropolis swap Monte Carlo (SI, Monte Carlo: neighbours
+// differ by one atom swap; accept with P = min[1, exp(-dE/kT)]), for one
+// problem (goac_mc_run) and for a batch of independent problems in one
+// persistent launch with a device work queue (goac_batch_mc_run).
+//
+// One chain per warp.  The chain's potential phi = J q (over all sites, so
+// including the fixed ions) and its species live in shared memory.  Proposals
+// do not depend on the state (a uniformly random ordered pair of positions in
+// a class), so each batch of 32 consecutive steps is drawn by the 32 lanes at
+// once (Philox + the J_ab / diagonal gathers in parallel).  The batch is then
+// evaluated speculatively: every pending lane computes its dE against the
+// current state, a ballot finds the earliest accepting step, that step is
+// committed (species swap, phi += d (J_a: - J_b:) with the warp reading the two
+// J rows coalesced, E += dE), and the lanes after it are re-evaluated.  The
+// result is exactly the sequential chain: steps before the first acceptance
+// were evaluated against the same state they would have seen.
+//
+// The FP64 path uses explicitly rounded operations in the order of the
+// definition (no contraction into FMA), so its trajectory follows the FP64
+// definition step for step.  The FP32 path keeps J rows and phi in FP32.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+// Energy changes within 1e-9 eV of zero are treated as zero: swaps related by
+// symmetry have dE = 0 exactly but +-1e-14 eV after rounding.
+constexpr double kDeZero = 1e-9;
+
+struct McProb {
+    const void* J;            // Nv_pad x ld, R
+    const void* diag;         // Nv, R
+    const double* z;          // S
+    const double* phifix;     // Nv
+    const int32_t* cls_start; // ncls + 1
+    const int32_t* cls_pos;   // Nv
+    const uint32_t* wprefix;  // ncls
+    int8_t* species;          // chains x Nv (in/out)
+    const double* kT;         // chains
+    double* E_out;            // chains
+    double* bestE;            // chains
+    int8_t* best_species;     // chains x Nv or null
+    int64_t* n_accept;        // chains or null
+    double E_const;
+    uint64_t seed;
+    uint32_t wtotal;
+    int ld, Nv, S, ncls, nmovable, only_movable, chains;
+};
+
+struct McScalars {
+    int64_t n_steps;
+    uint64_t step0;
+};
+
+template <typename R>
+__device__ __forceinline__ R rd_add(R a, R b);
+template <>
+__device__ __forceinline__ double rd_add<double>(double a, double b) { return __dadd_rn(a, b); }
+template <>
+__device__ __forceinline__ float rd_add<float>(float a, float b) { return __fadd_rn(a, b); }
+template <typename R>
+__device__ __forceinline__ R rd_sub(R a, R b);
+template <>
+__device__ __forceinline__ double rd_sub<double>(double a, double b) { return __dsub_rn(a, b); }
+template <>
+__device__ __forceinline__ float rd_sub<float>(float a, float b) { return __fsub_rn(a, b); }
+template <typename R>
+__device__ __forceinline__ R rd_mul(R a, R b);
+template <>
+__device__ __forceinline__ double rd_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <>
+__device__ __forceinline__ float rd_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+
+// Run one chain with one warp.  sp / phi point to this warp's shared-memory slots.
+template <typename R>
+__device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_t* sp, R* phi, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int Nv = P.Nv, ld = P.ld;
+    const R* J = (const R*)P.J;
+    const R* diag = (const R*)P.diag;
+    int8_t* gsp = P.species + (long)chain * Nv;
+
+    // load species, build phi = J_vv q + phi_fix (rows of J read coalesced: J symmetric)
+    for (int w = lane; w < Nv; w += 32) {
+        sp[w] = gsp[w];
+        phi[w] = (R)0;
+    }
+    __syncwarp();
+    for (int w = 0; w < Nv; ++w) {
+        const R qw = (R)P.z[sp[w]];
+        if (qw == (R)0) continue;
+        const R* row = J + (long)w * ld;
+        for (int v = lane; v < Nv; v += 32) phi[v] = fma(row[v], qw, phi[v]);
+    }
+    __syncwarp();
+    double e_part = 0.0;
+    for (int v = lane; v < Nv; v += 32) {
+        const double pf = P.phifix[v];
+        phi[v] = (R)((double)phi[v] + pf);
+        e_part += P.z[sp[v]] * ((double)phi[v] + pf);
+    }
+    for (int o = 16; o; o >>= 1) e_part += __shfl_xor_sync(0xffffffffu, e_part, o);
+    double E = e_part + P.E_const;
+    double best = E;
+    long nacc = 0;
+    if (P.best_species)
+        for (int w = lane; w < Nv; w += 32) P.best_species[(long)chain * Nv + w] = sp[w];
+    __syncwarp();
+
+    const double kT = P.kT[chain];
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
+        const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
+        const uint64_t t = sc.step0 + (uint64_t)s0 + (uint64_t)lane;
+        // ---- draw this lane's proposal (state independent) ----
+        int va = 0, vb = 0;
+        double u = 0.0;
+        R jsum = (R)0;
+        if (lane < nb) {
+            const uint4 x = goacd::philox(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)chain, 0u), k0, k1);
+            int k = P.only_movable;
+            if (P.nmovable != 1) {
+                const uint4 y =
+                    goacd::philox(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)chain, 1u), k0, k1);
+                const uint32_t thr = goacd::draw_below(y.x, P.wtotal);
+                k = P.ncls - 1;
+                for (int c = 0; c < P.ncls; ++c)
+                    if (P.wprefix[c] > thr) {
+                        k = c;
+                        break;
+                    }
+            }
+            const int start = P.cls_start[k];
+            const uint32_t n = (uint32_t)(P.cls_start[k + 1] - start);
+            const uint32_t a = goacd::draw_below(x.x, n);
+            const uint32_t bb = goacd::draw_below(x.y, n - 1);
+            const uint32_t b = bb + (bb >= a);
+            va = P.cls_pos[start + a];
+            vb = P.cls_pos[start + b];
+            u = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6)) * (1.0 / 9007199254740992.0);
+            jsum = rd_sub<R>(rd_add<R>(diag[va], diag[vb]), rd_mul<R>((R)2, J[(long)va * ld + vb]));
+        }
+        uint32_t pending = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        while (pending) {
+            bool acc = false;
+            R d = (R)0, dE = (R)0;
+            if ((pending >> lane) & 1u) {
+                const int sa = sp[va], sb = sp[vb];
+                if (sa != sb) {
+                    d = (R)(P.z[sb] - P.z[sa]);
+                    dE = rd_add<R>(rd_mul<R>(rd_mul<R>((R)2, d), rd_sub<R>(phi[va], phi[vb])),
+                                   rd_mul<R>(rd_mul<R>(d, d), jsum));
+                    if ((double)dE <= kDeZero) acc = true;
+                    else if (kT > 0.0) acc = u < exp(-(double)dE / kT);
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, acc);
+            if (m == 0u) break;
+            const int kl = __ffs(m) - 1;
+            const int ca = __shfl_sync(0xffffffffu, va, kl);
+            const int cb = __shfl_sync(0xffffffffu, vb, kl);
+            const R cd = __shfl_sync(0xffffffffu, d, kl);
+            const R cdE = __shfl_sync(0xffffffffu, dE, kl);
+            __syncwarp();
+            if (lane == 0) {
+                const int8_t ta = sp[ca];
+                sp[ca] = sp[cb];
+                sp[cb] = ta;
+            }
+            if (cd != (R)0) {
+                const R* ra = J + (long)ca * ld;
+                const R* rb = J + (long)cb * ld;
+                for (int w = lane; w < Nv; w += 32) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(ra[w], rb[w])));
+            }
+            __syncwarp();
+            E = E + (double)cdE;
+            ++nacc;
+            if (E < best) {
+                best = E;
+                if (P.best_species)
+                    for (int w = lane; w < Nv; w += 32) P.best_species[(long)chain * Nv + w] = sp[w];
+            }
+            pending &= ~((2u << kl) - 1u);
+        }
+    }
+    __syncwarp();
+    for (int w = lane; w < Nv; w += 32) gsp[w] = sp[w];
+    if (lane == 0) {
+        P.E_out[chain] = E;
+        P.bestE[chain] = best;
+        if (P.n_accept) P.n_accept[chain] = nacc;
+    }
+    (void)err;
+}
+
+__host__ __device__ inline size_t warp_slot_bytes(int Nv, int rbytes)
+{
+    size_t a = ((size_t)Nv * rbytes + 15) & ~(size_t)15;
+    size_t b = ((size_t)Nv + 15) & ~(size_t)15;
+    return a + b;
+}
+
+// Single problem: one warp per chain.
+template <typename R>
+__global__ void k_mc(McProb P, McScalars sc, int* err)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int wib = threadIdx.x >> 5;
+    const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (chain >= P.chains) return;
+    const size_t slot = warp_slot_bytes(P.Nv, sizeof(R));
+    uint8_t* base = smem + slot * wib;
+    R* phi = (R*)base;
+    int8_t* sp = (int8_t*)(base + (((size_t)P.Nv * sizeof(R) + 15) & ~(size_t)15));
+    run_chain<R>(P, chain, sc, sp, phi, err);
+}
+
+// Batch of problems: persistent warps take (problem, chain) items from a queue.
+template <typename R>
+__global__ void k_mc_batch(const McProb* __restrict__ probs, const int2* __restrict__ items, int n_items,
+                           int* __restrict__ counter, const McScalars* __restrict__ scp, int max_nv, int* err)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const size_t slot = warp_slot_bytes(max_nv, sizeof(R));
+    uint8_t* base = smem + slot * wib;
+    const McScalars sc = *scp;
+    while (true) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const int2 pc = items[it];
+        const McProb P = probs[pc.x];
+        R* phi = (R*)base;
+        int8_t* sp = (int8_t*)(base + (((size_t)P.Nv * sizeof(R) + 15) & ~(size_t)15));
+        run_chain<R>(P, pc.y, sc, sp, phi, err);
+        __syncwarp();
+    }
+}
+
+McProb make_desc(goac_problem* p, bool f32, int8_t* species, int C, const double* kT, double* E, double* bestE,
+                 int8_t* best_species, int64_t* nacc, uint64_t seed)
+{
+    McProb d;
+    d.J = f32 ? (const void*)p->J_f32 : (const void*)p->J_vv;
+    d.diag = f32 ? (const void*)p->diag_f32 : (const void*)p->diag;
+    d.z = p->z_dev;
+    d.phifix = p->phifix;
+    d.cls_start = p->cls_start_dev;
+    d.cls_pos = p->cls_pos_dev;
+    d.wprefix = p->wprefix_dev;
+    d.species = species;
+    d.kT = kT;
+    d.E_out = E;
+    d.bestE = bestE;
+    d.best_species = best_species;
+    d.n_accept = nacc;
+    d.E_const = p->E_const;
+    d.seed = seed;
+    d.wtotal = p->wtotal;
+    d.ld = p->Nv_pad;
+    d.Nv = p->Nv;
+    d.S = p->S;
+    d.ncls = p->ncls;
+    d.nmovable = p->nmovable;
+    d.only_movable = p->only_movable;
+    d.chains = C;
+    return d;
+}
+
+constexpr size_t kSmemBudget = 220 * 1024;
+
+}  // namespace
+
+extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
+                                   int64_t n_steps, uint64_t seed, uint64_t step0, int32_t precision, double* E_dev,
+                                   double* bestE_dev, int8_t* best_species_dev, int64_t* n_accept_dev)
+{
+    if (!p || !species_dev || !kT_dev || !E_dev || !bestE_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL argument");
+    if (C < 0 || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: negative size");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_F32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: precision must be F64 or F32");
+    if (p->nmovable == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: no class has two positions");
+    if (C == 0) return GOAC_OK;
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const bool f32 = precision == GOAC_PREC_F32;
+    if (f32) {
+        goac_status rc = goac::prepare_f32(p);
+        if (rc) return rc;
+    }
+    const size_t slot = warp_slot_bytes(p->Nv, f32 ? 4 : 8);
+    if (slot > kSmemBudget)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: Nv too large for a shared-memory chain");
+    int wpb = (int)(kSmemBudget / slot);
+    if (wpb > 8) wpb = 8;
+    if (wpb > C) wpb = C;
+    if (wpb < 1) wpb = 1;
+    const size_t smem = slot * wpb;
+    McProb d = make_desc(p, f32, species_dev, C, kT_dev, E_dev, bestE_dev, best_species_dev, n_accept_dev, seed);
+    McScalars sc{n_steps, step0};
+    const int blocks = (C + wpb - 1) / wpb;
+    if (f32) {
+        GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mc<float><<<blocks, 32 * wpb, smem, p->ctx->stream>>>(d, sc, p->ctx->d_err);
+    } else {
+        GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mc<double><<<blocks, 32 * wpb, smem, p->ctx->stream>>>(d, sc, p->ctx->d_err);
+    }
+    GOAC_LAUNCH_CHECK("k_mc");
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs,
+                                         int8_t* const* species_dev, const int32_t* chains,
+                                         const double* const* kT_dev, int64_t n_steps, uint64_t seed,
+                                         uint64_t step0, int32_t precision, double* const* E_dev,
+                                         double* const* bestE_dev, int32_t chains_per_cta, int32_t mode)
+{
+    if (!ctx || !probs || n_probs <= 0 || !species_dev || !chains || !kT_dev || !E_dev || !bestE_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: bad argument");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_F32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: precision must be F64 or F32");
+    if (mode < 0 || mode > 2) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: mode must be 0, 1 or 2");
+    if (chains_per_cta < 1 || chains_per_cta > 32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: chains_per_cta must be in [1, 32]");
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    const bool f32 = precision == GOAC_PREC_F32;
+    const int rb = f32 ? 4 : 8;
+    std::vector<McProb> descs(n_probs);
+    std::vector<int2> items;
+    int max_nv = 0;
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+    for (int i = 0; i < n_probs; ++i) {
+        goac_problem* p = probs[i];
+        if (!p || !species_dev[i] || !kT_dev[i] || !E_dev[i] || !bestE_dev[i] || chains[i] < 0)
+            return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: bad per-problem argument");
+        if (p->ctx != ctx) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: problem from another context");
+        if (p->nmovable == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: problem without moves");
+        if (f32) {
+            goac_status rc = goac::prepare_f32(p);
+            if (rc) return rc;
+        }
+        descs[i] = make_desc(p, f32, species_dev[i], chains[i], kT_dev[i], E_dev[i], bestE_dev[i], nullptr, nullptr,
+                             seed + (uint64_t)i);
+        for (int c = 0; c < chains[i]; ++c) items.push_back(make_int2(i, c));
+        if (p->Nv > max_nv) max_nv = p->Nv;
+        mix((uint64_t)(uintptr_t)p);
+        mix((uint64_t)(uintptr_t)species_dev[i]);
+        mix((uint64_t)(uintptr_t)kT_dev[i]);
+        mix((uint64_t)(uintptr_t)E_dev[i]);
+        mix((uint64_t)(uintptr_t)bestE_dev[i]);
+        mix((uint64_t)chains[i]);
+    }
+    mix(seed);
+    mix((uint64_t)precision);
+    mix((uint64_t)chains_per_cta);
+    const size_t slot = warp_slot_bytes(max_nv, rb);
+    if (slot * chains_per_cta > kSmemBudget)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: chains_per_cta x largest cell exceeds shared memory");
+    cudaStream_t st = ctx->stream;
+    const int n_items = (int)items.size();
+    if (n_items == 0) return GOAC_OK;
+
+    if (mode == 0) {
+        // baseline: one launch per problem
+        McScalars sc{n_steps, step0};
+        for (int i = 0; i < n_probs; ++i) {
+            if (descs[i].chains == 0) continue;
+            const size_t s1 = warp_slot_bytes(descs[i].Nv, rb);
+            int wpb = chains_per_cta < descs[i].chains ? chains_per_cta : descs[i].chains;
+            const size_t smem = s1 * wpb;
+            const int blocks = (descs[i].chains + wpb - 1) / wpb;
+            if (f32) {
+                GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+                k_mc<float><<<blocks, 32 * wpb, smem, st>>>(descs[i], sc, ctx->d_err);
+            } else {
+                GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+                k_mc<double><<<blocks, 32 * wpb, smem, st>>>(descs[i], sc, ctx->d_err);
+            }
+            GOAC_LAUNCH_CHECK("k_mc (per problem)");
+        }
+        return GOAC_OK;
+    }
+
+    // persistent: descriptors, items, queue counter and per-call scalars on the device
+    const size_t desc_bytes = sizeof(McProb) * n_probs;
+    const size_t item_bytes = sizeof(int2) * n_items;
+    goac_status rc = goac::ensure(ctx->batch_desc, desc_bytes);
+    if (!rc) rc = goac::ensure(ctx->batch_items, item_bytes);
+    if (!rc) rc = goac::ensure(ctx->batch_counter, 64);
+    if (rc) return rc;
+    const bool reuse = mode == 2 && ctx->batch_graph && ctx->batch_graph_key == key;
+    McScalars sc{n_steps, step0};
+    int* counter = (int*)ctx->batch_counter.ptr;
+    McScalars* d_sc = (McScalars*)((char*)ctx->batch_counter.ptr + 16);
+    if (!reuse) {
+        GOAC_CUDA(cudaMemcpyAsync(ctx->batch_desc.ptr, descs.data(), desc_bytes, cudaMemcpyHostToDevice, st));
+        GOAC_CUDA(cudaMemcpyAsync(ctx->batch_items.ptr, items.data(), item_bytes, cudaMemcpyHostToDevice, st));
+    }
+    GOAC_CUDA(cudaMemcpyAsync(d_sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, st));
+    const size_t smem = slot * chains_per_cta;
+    int per_sm = 1;
+    if (f32) {
+        GOAC_CUDA(cudaFuncSetAttribute(k_mc_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GOAC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mc_batch<float>, 32 * chains_per_cta, smem));
+    } else {
+        GOAC_CUDA(cudaFuncSetAttribute(k_mc_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GOAC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mc_batch<double>, 32 * chains_per_cta, smem));
+    }
+    if (per_sm < 1) per_sm = 1;
+    int grid = ctx->num_sms * per_sm;
+    const int need = (n_items + chains_per_cta - 1) / chains_per_cta;
+    if (grid > need) grid = need;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        if (f32)
+            k_mc_batch<float><<<grid, 32 * chains_per_cta, smem, st>>>((const McProb*)ctx->batch_desc.ptr,
+                                                                        (const int2*)ctx->batch_items.ptr, n_items,
+                                                                        counter, d_sc, max_nv, ctx->d_err);
+        else
+            k_mc_batch<double><<<grid, 32 * chains_per_cta, smem, st>>>((const McProb*)ctx->batch_desc.ptr,
+                                                                         (const int2*)ctx->batch_items.ptr, n_items,
+                                                                         counter, d_sc, max_nv, ctx->d_err);
+        return cudaGetLastError();
+    };
+    if (mode == 1) {
+        cudaError_t e = enqueue();
+        if (e != cudaSuccess) return goac::cuda_fail(e, "k_mc_batch");
+        return GOAC_OK;
+    }
+    if (!reuse) {
+        if (ctx->batch_graph) {
+            cudaGraphExecDestroy(ctx->batch_graph);
+            ctx->batch_graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        cudaStream_t cap = nullptr;
+        GOAC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        const cudaStream_t saved = st;
+        st = cap;   // enqueue() launches on `st`
+        cudaError_t e0 = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = e0 == cudaSuccess ? enqueue() : e0;
+        cudaError_t e2 = e0 == cudaSuccess ? cudaStreamEndCapture(cap, &g) : e0;
+        st = saved;
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return goac::cuda_fail(e, "k_mc_batch (capture)");
+        }
+        if (e2 != cudaSuccess) return goac::cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx->batch_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return goac::cuda_fail(e, "cudaGraphInstantiate");
+        ctx->batch_graph_key = key;
+    }
+    GOAC_CUDA(cudaGraphLaunch(ctx->batch_graph, st));
+    return GOAC_OK;
+}

@@ -1,0 +1,140 @@
+"""GPU parity of the genetic algorithm, the relaxed-occupation energy and its
+adjoint, and rounding to counts, against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import goac_synth as synth
+import oracle
+from gpu_common import build_pair, gpu_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2409_08808_gb300 as g
+    return g.Context(0)
+
+
+def _counts_ok(prob, pop):
+    vclass = prob.site_class[prob.site_class >= 0]
+    for b in range(pop.shape[0]):
+        for k in range(prob.n_class):
+            for s in range(prob.S):
+                if ((vclass == k) & (pop[b] == s)).sum() != prob.counts[k, s]:
+                    return False
+    return True
+
+
+@pytest.mark.parametrize("P,n_elite,p_mut", [(200, 4, 0.3), (64, 0, 0.0), (33, 33, 1.0)])
+def test_ga_generation_bit_exact(ctx, P, n_elite, p_mut):
+    """Same population and (oracle) energies in: identical children, parents
+    and swap counts out."""
+    prob = synth.layered_problem(reps=(3, 3, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, P, 5)
+    E = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, pop)
+    kids_o, par_o, nsw_o = oracle.ga_generation(prob.site_class, pop, E, n_elite, p_mut, gen=7, seed=99)
+    kids, par, nsw = gp.ga_generation(torch.tensor(pop, device="cuda"), torch.tensor(E, device="cuda"), n_elite,
+                                      oracle.p_mut_to_u32(p_mut), 7, 99, record=True)
+    assert np.array_equal(kids.cpu().numpy(), kids_o)
+    assert np.array_equal(par.cpu().numpy(), par_o)
+    assert np.array_equal(nsw.cpu().numpy(), nsw_o)
+
+
+def test_ga_generation_equal_energies(ctx):
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, 50, 3)
+    E = np.full(50, -123.0)
+    kids_o, par_o, _ = oracle.ga_generation(prob.site_class, pop, E, 2, 0.2, gen=0, seed=1)
+    kids, par, _ = gp.ga_generation(torch.tensor(pop, device="cuda"), torch.tensor(E, device="cuda"), 2,
+                                    oracle.p_mut_to_u32(0.2), 0, 1, record=True)
+    assert np.array_equal(kids.cpu().numpy(), kids_o)
+    assert np.array_equal(par.cpu().numpy(), par_o)
+
+
+def test_ga_run_parity(ctx):
+    prob = synth.layered_problem(reps=(2, 2, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, 48, 8)
+    fin_o, E_o = oracle.ga_run(Jo, prob.site_class, prob.fixed_q, prob.z, pop, 6, 2, 0.1, seed=4)
+    sp = torch.tensor(pop, device="cuda")
+    E = gp.ga_run(sp, 6, 2, oracle.p_mut_to_u32(0.1), 4, precision="f64").cpu().numpy()
+    assert np.array_equal(sp.cpu().numpy(), fin_o)
+    assert np.allclose(E, E_o, rtol=1e-10)
+
+
+def test_ga_layered_full_size(ctx):
+    """Layered 12x12x1 cell, N = 1296, population 1024: counts preserved,
+    elitism keeps the best energy non-increasing, FP64 and split scoring."""
+    prob = synth.layered_problem()
+    Jg, Jo = build_pair(ctx, prob) if False else (None, None)
+    import paper_2409_08808_gb300 as g
+    frac = torch.tensor(prob.frac, device="cuda")
+    Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = gp.random_configs(1024, 11)
+    best = []
+    for gen in range(3):
+        E = gp.ga_run(pop, 1, 20, oracle.p_mut_to_u32(0.1), 5, gen0=gen, precision="f64")
+        best.append(E.min().item())
+    assert best[0] >= best[1] >= best[2]
+    assert _counts_ok(prob, pop.cpu().numpy()[:64])
+    E64 = gp.score(pop, "f64")
+    E32 = gp.score(pop, "f32")
+    Ebf = gp.score(pop, "bf16x3")
+    assert torch.allclose(E, E64, rtol=0, atol=0)
+    assert (E32 - E64).abs().max().item() < 1e-3 * E64.abs().max().item()
+    assert (Ebf - E64).abs().max().item() < 1e-4 * E64.abs().max().item()
+
+
+@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5)])
+def test_energy_grad_parity(ctx, which, B):
+    prob = {"layered": lambda: synth.layered_problem(reps=(2, 1, 1)),
+            "bcc": lambda: synth.bcc_relaxed_problem(n_side=4)}[which]()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg) if which != "bcc" else None
+    if gp is None:
+        import paper_2409_08808_gb300 as g
+        gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
+    L = synth.random_logits(prob, B, 3)
+    lam = 0.05
+    E, dL = gp.energy_grad(torch.tensor(L, device="cuda"), lam, "f64")
+    E, dL = E.cpu().numpy(), dL.cpu().numpy()
+    for b in range(B):
+        Eo, go = oracle.energy_grad(Jo, prob.site_class, prob.fixed_q, prob.z, prob.counts, L[b].astype(np.float64), lam)
+        assert E[b] == pytest.approx(Eo, rel=1e-10, abs=1e-10)
+        scale = np.abs(go).max()
+        assert np.max(np.abs(dL[b] - go)) <= 1e-6 * scale + 1e-30
+
+
+def test_autograd_function(ctx):
+    import paper_2409_08808_gb300 as g
+    prob = synth.layered_problem(reps=(2, 1, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    L = torch.tensor(synth.random_logits(prob, 2, 9), device="cuda", requires_grad=True)
+    E = g.RelaxedEnergy.apply(L, gp, 0.1, "f64")
+    E.sum().backward()
+    _, dL = gp.energy_grad(L.detach(), 0.1, "f64")
+    assert torch.equal(L.grad, dL)
+
+
+@pytest.mark.parametrize("B", [1, 6])
+def test_round_to_counts_parity(ctx, B):
+    prob = synth.layered_problem(reps=(2, 2, 1))
+    Jg, _ = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    rng = np.random.default_rng(B)
+    p = rng.dirichlet(np.ones(prob.S), size=(B, prob.Nv)).astype(np.float32)
+    p[0, 3, :] = p[0, 4, :]           # exact ties between sites
+    got = gp.round_to_counts(torch.tensor(p, device="cuda")).cpu().numpy()
+    for b in range(B):
+        ref = oracle.round_to_counts(prob.site_class, prob.counts, p[b])
+        assert np.array_equal(got[b], ref)
+    assert _counts_ok(prob, got)

@@ -1,0 +1,127 @@
+"""GPU parity of parallel-chain Metropolis swap MC against the oracle, with a
+shared Philox stream: configurations bit-exact, energies within 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+import goac_synth as synth
+import oracle
+from gpu_common import build_pair, gpu_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2409_08808_gb300 as g
+    return g.Context(0)
+
+
+def _run_both(ctx, prob, C, steps, kT, seed, step0=0, init_seed=5):
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, C, init_seed)
+    ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, kT, steps, seed, step0=step0)
+    sp = torch.tensor(start, device="cuda")
+    got = gp.mc_run(sp, kT, steps, seed, step0=step0, precision="f64")
+    torch.cuda.synchronize()
+    return ref, {k: (v.cpu().numpy() if v is not None else None) for k, v in got.items()}, gp, start
+
+
+def test_mc_rocksalt_trajectory_parity(ctx):
+    """Rocksalt 2x2x2 (a = 4.2 A): 32 anions fixed at -2, 16 x +1 / 16 x +3
+    cations; 8 chains x 20,000 swaps at kT = 0.05 eV."""
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    ref, got, _, _ = _run_both(ctx, prob, 8, 20000, 0.05, seed=0x600AC)
+    assert np.array_equal(got["species"], ref["species"])
+    assert np.array_equal(got["n_accept"], ref["n_accept"])
+    assert np.array_equal(got["best_species"], ref["best_species"])
+    assert np.allclose(got["E"], ref["E"], rtol=1e-10, atol=0)
+    assert np.allclose(got["bestE"], ref["bestE"], rtol=1e-10, atol=0)
+
+
+def test_mc_multiclass_trajectory_parity(ctx):
+    prob = synth.layered_problem(reps=(2, 2, 1))
+    ref, got, _, _ = _run_both(ctx, prob, 5, 6000, 0.1, seed=77, step0=123)
+    assert np.array_equal(got["species"], ref["species"])
+    assert np.array_equal(got["n_accept"], ref["n_accept"])
+    assert np.allclose(got["E"], ref["E"], rtol=1e-10)
+
+
+def test_mc_ragged_steps_and_resume(ctx):
+    prob = synth.tiny_rocksalt_problem()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 3, 9)
+    a = torch.tensor(start, device="cuda")
+    gp.mc_run(a, 0.3, 1001, 3)
+    b = torch.tensor(start, device="cuda")
+    gp.mc_run(b, 0.3, 501, 3)
+    gp.mc_run(b, 0.3, 500, 3, step0=501)
+    assert torch.equal(a, b)
+    ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.3, 1001, 3)
+    assert np.array_equal(a.cpu().numpy(), ref["species"])
+
+
+def test_mc_zero_steps_and_zero_temperature(ctx):
+    prob = synth.tiny_rocksalt_problem()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 2, 4)
+    sp = torch.tensor(start, device="cuda")
+    out = gp.mc_run(sp, 0.0, 0, 1)
+    assert np.array_equal(sp.cpu().numpy(), start)
+    Eo = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, start)
+    assert np.allclose(out["E"].cpu().numpy(), Eo, rtol=1e-10)
+    ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.0, 700, 11)
+    gp.mc_run(sp, 0.0, 700, 11)
+    assert np.array_equal(sp.cpu().numpy(), ref["species"])
+
+
+def test_mc_f32_variant_invariants(ctx):
+    prob = synth.layered_problem(reps=(3, 3, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 16, 8)
+    sp = torch.tensor(start, device="cuda")
+    out = gp.mc_run(sp, 0.05, 4000, 21, precision="f32")
+    fin = sp.cpu().numpy()
+    vclass = prob.site_class[prob.site_class >= 0]
+    for c in range(16):
+        for k in range(prob.n_class):
+            for s in range(prob.S):
+                assert ((vclass == k) & (fin[c] == s)).sum() == prob.counts[k, s]
+    Eo = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, fin)
+    # FP32 phi drifts by ~1e-6 relative per accepted swap at most
+    assert np.allclose(out["E"].cpu().numpy(), Eo, rtol=2e-5)
+    assert np.all(out["E"].cpu().numpy() < oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, start))
+
+
+def test_batch_mc_matches_single_runs(ctx):
+    """Persistent work-queue launch (and its CUDA-graph replay) gives the same
+    chains as one launch per problem with key seed + p; problem 0 also
+    matches the oracle."""
+    import paper_2409_08808_gb300 as g
+    probs = synth.batch_problems(n_cells=5, n_min=16, n_max=160, seed=99)
+    gps, starts, kts, Jos = [], [], [], []
+    for i, pr in enumerate(probs):
+        Jg, Jo = build_pair(ctx, pr)
+        gps.append(gpu_problem(ctx, pr, Jg))
+        Jos.append(Jo)
+        starts.append(synth.random_population(pr, 3 + i, 40 + i))
+        kts.append(torch.full((3 + i,), pr.kT, dtype=torch.float64, device="cuda"))
+    results = {}
+    for mode in (0, 1, 2, 2):
+        sps = [torch.tensor(s, device="cuda") for s in starts]
+        E, bE = g.batch_mc_run(ctx, gps, sps, kts, 3000, seed=1000, mode=mode, chains_per_cta=2)
+        torch.cuda.synchronize()
+        results.setdefault(mode, []).append(([s.cpu().numpy() for s in sps], [e.cpu().numpy() for e in E]))
+    base_sp, base_E = results[0][0]
+    for mode in (1, 2):
+        for sp, E in results[mode]:
+            for i in range(len(probs)):
+                assert np.array_equal(sp[i], base_sp[i])
+                assert np.array_equal(E[i], base_E[i])
+    ref = oracle.mc_run(Jos[0], probs[0].site_class, probs[0].fixed_q, probs[0].z, starts[0], probs[0].kT, 3000, 1000)
+    assert np.array_equal(base_sp[0], ref["species"])
+    assert np.allclose(base_E[0], ref["E"], rtol=1e-10)
