@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the GOAC hot path on GB300.
+
+One step = batched scoring E = q^T J q of a population of B = 4096 count-
+preserving configurations of a random cubic cell with N = 4096 sites (16^3
+jittered grid, species +1/+2/+3/-2), in the BF16x3 split form on the tcgen05
+tensor cores.  value = energy evaluations per second over all GPUs.  The same
+run also reports: the plain FP64 GPU path on the same population and the
+speed-up, the energy error of the split form against it, the top-64 FP64
+rescoring, Monte Carlo swap trials/s at N = 4096 (FP64 and FP32 chains), the
+live roofline of the dominant kernel, the end-to-end rate through the host-
+buffer entry point, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): replicas; every rank scores its own
+population (different seed), no data-path collective; value = all ranks' work
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "config energy evals/s and MC swap trials/s at N=4096, % roofline, vs FP64 GPU path"
+N_SIDE = 16          # 16^3 = 4096 sites
+B_POP = 4096
+FORM = "bf16x3"
+TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2}
+WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +1:512 +2:1024 +3:512 -2:2048), "
+            "population B=4096 uniformly random count-preserving configurations")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", default=FORM, choices=sorted(TERMS))
+    ap.add_argument("--mc-steps", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def _dist():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[0] for r in rows]
+        mx = max(r[1] for r in rows)
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the bounded baseline and the reference arm)
+# ---------------------------------------------------------------------------
+class _OracleWork:
+    """Configurations of the benchmark cell scored by the oracle's plain
+    q^T J q.  The oracle's J for N = 4096 takes minutes to build, and the
+    scoring cost does not depend on J's values, so the timed sample uses a
+    seeded symmetric FP64 matrix of the same size in its place."""
+
+    def __init__(self, seed: int, max_cfg: int):
+        import goac_synth as synth
+        import oracle
+        self.oracle = oracle
+        oracle.build()
+        self.prob = synth.random_cubic_problem(n_side=N_SIDE)
+        rng = np.random.default_rng(seed)
+        J = rng.standard_normal((self.prob.N, self.prob.N))
+        self.J = np.ascontiguousarray(0.5 * (J + J.T))
+        self.pop = synth.random_population(self.prob, max_cfg, seed + 1)
+
+    def time(self, n_cfg: int, offset: int = 0) -> float:
+        p = self.prob
+        idx = (offset + np.arange(n_cfg)) % self.pop.shape[0]
+        sub = np.ascontiguousarray(self.pop[idx])
+        t0 = time.perf_counter()
+        self.oracle.score(self.J, p.site_class, p.fixed_q, p.z, sub)
+        return time.perf_counter() - t0
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, on this host's cores, as the reference arm.
+    Each step scores a bounded sample sized so that warm-up + steps take about
+    a minute in total."""
+    if rank != 0:
+        return
+    work = _OracleWork(11, 64)
+    t1 = work.time(2) / 2.0
+    per_step = int(max(1, min(64, 60.0 / (max(1, args.steps + args.warmup) * t1))))
+    for w in range(args.warmup):
+        work.time(per_step, w)
+    times = [work.time(per_step, k * per_step) for k in range(args.steps)]
+    ms = 1e3 * float(np.mean(times))
+    value = per_step / (ms / 1e3)
+    sample = (f"{per_step} configurations per step of the N=4096 cell, oracle q^T J q in plain C, 1 thread; "
+              f"J a seeded symmetric FP64 matrix of the same size")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 4096, "B": per_step, "form": "f64 oracle (CPU)",
+                       "parallelism": "single host thread"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("bf16_tflops"), d.get("hbm_gbs"), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+def _kernel_hash() -> str:
+    """Hash of the tensor-core scoring kernel's source (its function body and
+    the device helpers it uses); ncu counters are valid while it is unchanged."""
+    csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
+    src = open(os.path.join(csrc, "score_tc.cu")).read()
+    a = src.index("template <int T, bool TF32>\n__global__ void __launch_bounds__(192, 1)")
+    b = src.index("// Symmetric operand:")
+    h = hashlib.sha256()
+    h.update(src[a:b].encode())
+    h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(form):
+    """DRAM bytes per launch of the scoring kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"score_tc_{form}_n4096.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_sha") != _kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import goac_synth as synth
+    import paper_2409_08808_gb300 as g
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = g.Context(local)
+    prob = synth.random_cubic_problem(n_side=N_SIDE)
+    frac = torch.tensor(prob.frac, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    torch.cuda.synchronize()
+    ewald_ms = 1e3 * (time.perf_counter() - t0)
+    gp = g.Problem(ctx, J, prob.site_class, prob.fixed_q, prob.z, prob.counts)
+    del J
+    pop_np = synth.random_population(prob, B_POP, synth.SEED_BASE + 2 + 1000 * rank)
+    pop = torch.tensor(pop_np, device=dev)
+    pop_host = torch.tensor(pop_np).pin_memory()
+    form = args.form
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    # warm-up (also builds the split operand copies)
+    for _ in range(max(3, args.warmup)):
+        gp.score(pop, form)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time("score_tc")
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    E = torch.empty(B_POP, dtype=torch.float64, device=dev)
+    clocks = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = g.launch_count()
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flush between steps, outside the step events
+        starts[k].record()
+        gp.score(pop, form, out=E)
+        ends[k].record()
+    torch.cuda.synchronize()
+    launches = g.launch_count() - launches0
+    _barrier(world)
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = float(np.mean(step_ms))
+    ms = _max_over_ranks(ms_local, world)
+    kern_ms, kern_n = ctx.kernel_time("score_tc")
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+    ctx.set_timing(False)
+    value = world * B_POP / (ms / 1e3)
+
+    # roofline of the dominant kernel (executed tensor FLOPs of the split form)
+    terms = TERMS[form]
+    ld = ((prob.N + 127) // 128) * 128
+    bpad = ((B_POP + 255) // 256) * 256
+    nbm = ld // 128
+    # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld
+    flops_exec = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * bpad
+    flops_useful = 2.0 * prob.N * prob.N * B_POP
+    bf16_peak, hbm_peak, peak_kind = _peaks()
+    peak = bf16_peak if form.startswith("bf16") else bf16_peak / 2.0     # TF32 runs at half the BF16 rate
+    achieved = flops_exec / (kern_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic(form), "kernel": f"k_score_tc<{terms},{'true' if 'tf32' in form else 'false'}>",
+                "kernel_ms": kern_avg_ms, "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
+                "peak_kind": f"{peak_kind} bf16_tflops (burst)" + (" x 0.5 nominal tf32/bf16 ratio" if "tf32" in form else "")}
+
+    # end to end through the host-buffer entry point (pinned H2D + D2H inside)
+    E_host = torch.empty(B_POP, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        gp.score_host(pop_host, form, out=E_host)
+    e2e_t = []
+    for k in range(min(args.steps, 200)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gp.score_host(pop_host, form, out=E_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = _max_over_ranks(float(np.mean(e2e_t)), world)
+    e2e = {"value": world * B_POP / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(pop_np.nbytes),
+           "d2h_bytes_per_step": int(E_host.numel() * 8)}
+
+    # plain FP64 GPU path on the same population, and the split form's error
+    E_form = gp.score(pop, form).clone()
+    E64 = gp.score(pop, "f64")
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    reps64 = 2
+    for _ in range(reps64):
+        gp.score(pop, "f64", out=E64)
+    b.record()
+    torch.cuda.synchronize()
+    f64_ms = a.elapsed_time(b) / reps64
+    err = (E_form - E64).abs()
+    energy_error = {"max_abs_eV": float(err.max()), "rms_abs_eV": float(err.pow(2).mean().sqrt()),
+                    "max_rel": float((err / E64.abs()).max()), "mean_abs_E_eV": float(E64.abs().mean())}
+
+    # top-64 FP64 rescoring of the split form's best candidates
+    idx, Etop = gp.topk_rescore(pop, E_form, 64)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        gp.topk_rescore(pop, E_form, 64)
+    b.record()
+    torch.cuda.synchronize()
+    topk_ms = a.elapsed_time(b) / 3
+    top_exact = bool(torch.allclose(Etop, E64[idx.long()], rtol=1e-12, atol=0))
+    same_best = int(idx[0].item()) == int(torch.argmin(E64).item())
+
+    # Monte Carlo swap trials at N = 4096 (chains continue from a warm-up segment)
+    mc = {}
+    for prec in ("f64", "f32"):
+        Cn = 152 * (6 if prec == "f64" else 8)
+        chains = gp.random_configs(Cn, 77 + rank)
+        gp.mc_run(chains, 0.05, args.mc_steps, 5, step0=0, precision=prec)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.kernel_time("mc")
+        a.record()
+        out = gp.mc_run(chains, 0.05, args.mc_steps, 5, step0=args.mc_steps, precision=prec)
+        b.record()
+        torch.cuda.synchronize()
+        mc_kms, _ = ctx.kernel_time("mc")
+        ctx.set_timing(False)
+        mms = a.elapsed_time(b)
+        trials = Cn * args.mc_steps
+        acc = float(out["n_accept"].sum().item()) / trials
+        rb = 8 if prec == "f64" else 4
+        # bytes per trial: J_ab gather (one 32-byte sector) + per acceptance two J rows
+        bytes_alg = trials * 32 + acc * trials * 2 * prob.N * rb
+        mc[prec] = {"trials_per_s": world * trials / (_max_over_ranks(mms, world) / 1e3), "chains": Cn,
+                    "steps_per_chain": args.mc_steps, "kT_eV": 0.05, "acceptance": acc, "ms": mms,
+                    "hbm_gbs_algorithmic": bytes_alg / (mc_kms / 1e3) / 1e9,
+                    "hbm_frac": bytes_alg / (mc_kms / 1e3) / 1e9 / hbm_peak}
+
+    cpu = None
+    if rank == 0:
+        work = _OracleWork(11, args.cpu_sample)
+        n = args.cpu_sample
+        dt = work.time(n)
+        cpu = {"value": n / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} configurations of the N=4096 cell, oracle q^T J q in plain C on 1 thread "
+                         f"({dt:.1f} s), J a seeded symmetric FP64 matrix of the same size"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": prob.N, "B": B_POP, "form": form,
+                           "form_detail": f"J split in {terms} BF16 terms, Q exact, FP32 accumulate on tcgen05, "
+                                          "FP64 cross-tile sums",
+                           "l2": "256 MB buffer written between steps (outside the step events)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk,
+                "fp64_gpu_path": {"evals_per_s": world * B_POP / (f64_ms / 1e3), "ms_per_step": f64_ms,
+                                  "speedup_of_form": f64_ms / ms},
+                "energy_error_vs_fp64": energy_error,
+                "topk64_fp64_rescore": {"ms": topk_ms, "exact_vs_fp64_path": top_exact,
+                                        "lowest_matches_fp64_argmin": same_best},
+                "mc": mc, "setup": {"ewald_build_ms": ewald_ms}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -71,6 +71,22 @@ goac_status goac_ctx_destroy(goac_ctx* ctx);
 goac_status goac_ctx_set_stream(goac_ctx* ctx, void* stream);
 /* Synchronise the context stream and report any device error word. */
 goac_status goac_ctx_synchronize(goac_ctx* ctx);
+/* Per-kernel timing: when enabled, a CUDA event pair is recorded on the      *
+ * context stream around every launch of the timed kernel families:           *
+ * 0 = tensor-core scoring, 1 = CUDA-core scoring GEMM, 2 = Monte Carlo,      *
+ * 3 = GA children, 4 = Ewald real space, 5 = Ewald reciprocal SYRK.          */
+goac_status goac_ctx_set_timing(goac_ctx* ctx, int32_t enable);
+/* Total recorded milliseconds and launch count of kernel family `kernel`     *
+ * since the last query (waits for the recorded events; clears the record).  */
+goac_status goac_ctx_kernel_time(goac_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches);
+/* Failure-detection self test (no counterpart in the paper): one thread      *
+ * waits on a device barrier that nothing completes, with the clock-bounded    *
+ * wait every waiting kernel of this library uses (limit_cycles SM cycles,     *
+ * 1 .. 4e9).  Returns GOAC_ERR_TIMEOUT once the wait has run out; the context *
+ * remains usable.  Synchronises.                                              */
+goac_status goac_selftest_wait_timeout(goac_ctx* ctx, int64_t limit_cycles);
+/* Number of kernels this library has launched in the process so far. */
+int64_t goac_launch_count(void);
 
 /* ------------------------------------------------------------------------ *
  * Ewald pair matrix J (Section "Cluster Expansion of Coulomb Energy": the  *

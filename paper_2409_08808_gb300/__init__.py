@@ -82,6 +82,24 @@ class Context:
     def synchronize(self):
         _check(lib.goac_ctx_synchronize(self.handle), "goac_ctx_synchronize")
 
+    KERNELS = {"score_tc": 0, "score_cc": 1, "mc": 2, "ga": 3, "ewald_real": 4, "ewald_syrk": 5}
+
+    def set_timing(self, enable: bool):
+        _check(lib.goac_ctx_set_timing(self._h, int(bool(enable))), "goac_ctx_set_timing")
+
+    def kernel_time(self, kernel: str):
+        """(total ms, launches) of a timed kernel family since the last query."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(lib.goac_ctx_kernel_time(self._h, self.KERNELS[kernel], C.byref(ms), C.byref(n)),
+               "goac_ctx_kernel_time")
+        return float(ms.value), int(n.value)
+
+
+def launch_count() -> int:
+    """Kernels launched by libgoac in this process so far."""
+    return int(lib.goac_launch_count())
+
     def close(self):
         """Destroy the context after every problem created on it."""
         if getattr(self, "_h", None):

@@ -33,6 +33,10 @@ SIGNATURES = {
     "goac_ctx_destroy": (_st, [_p]),
     "goac_ctx_set_stream": (_st, [_p, _p]),
     "goac_ctx_synchronize": (_st, [_p]),
+    "goac_ctx_set_timing": (_st, [_p, _i32]),
+    "goac_ctx_kernel_time": (_st, [_p, _i32, _p, _p]),
+    "goac_launch_count": (_i64, []),
+    "goac_selftest_wait_timeout": (_st, [_p, _i64]),
     "goac_build_ewald": (_st, [_p, _p, _p, _i32, _d, _p, _d, _d, _p]),
     "goac_problem_create": (_st, [_p, _p, _i32, _p, _p, _p, _i32, _p, _i32, _i32, C.POINTER(_p)]),
     "goac_problem_destroy": (_st, [_p]),

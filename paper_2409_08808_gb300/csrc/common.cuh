@@ -62,6 +62,10 @@ struct goac_ctx {
     DevBuf host_io_species;        // device staging for goac_score_host
     DevBuf host_io_E;
     void* pinned = nullptr;        // not used by the stream path; reserved
+    // per-kernel event timing (goac_ctx_set_timing / goac_ctx_kernel_time)
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[8];
+    std::vector<cudaEvent_t> event_pool;
     // batched-MC graph cache
     cudaGraphExec_t batch_graph = nullptr;
     uint64_t batch_graph_key = 0;
@@ -75,6 +79,7 @@ struct goac_problem {
     goac_ctx* ctx = nullptr;
     int N = 0, Nv = 0, S = 0, ncls = 0;
     int Nv_pad = 0;            // multiple of 128 (tensor-core tiles)
+    bool has_fixed = false;    // any fixed ion (phi_fix may be non-zero)
     double E_const = 0.0;
     // host copies
     std::vector<int32_t> vclass, cls_start, cls_pos, counts;
@@ -99,6 +104,10 @@ struct goac_problem {
     float* diag_f32 = nullptr;
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
+    // persistent tensor-core schedule (device copy) for the last shape
+    DevBuf sched;
+    uint64_t sched_key = 0;
+    int sched_tiles = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -187,6 +196,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > limit_cycles) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier among `count` threads (a multiple of 32) on hardware barrier `id` (1..15).
+__device__ __forceinline__ void named_bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // ---- TMA ---------------------------------------------------------------------
@@ -307,8 +327,41 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t fmt, uint32_t M, ui
 
 }  // namespace goacd
 
-// Internal entry points shared between translation units.
+// Every kernel launch of the library goes through launch(): it counts the
+// launch (goac_launch_count) and returns the launch error.
 namespace goac {
+void count_launch();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args&&... args)
+{
+    count_launch();
+    kern<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+    return cudaGetLastError();
+}
+
+// Kernel families timed with CUDA events when timing is enabled on a context.
+enum KernelId : int {
+    KID_SCORE_TC = 0,   // tensor-core scoring main kernel
+    KID_SCORE_CC = 1,   // CUDA-core (FP64 / FP32) scoring GEMM
+    KID_MC = 2,         // Monte Carlo chains (single or batched)
+    KID_GA = 3,         // GA children
+    KID_EWALD_REAL = 4, // Ewald real-space pair kernel
+    KID_EWALD_SYRK = 5, // Ewald reciprocal SYRK
+    KID_COUNT = 8
+};
+
+// Records a CUDA event pair around the launches in its scope (no-op unless
+// timing is enabled on the context).
+struct KTimer {
+    goac_ctx* ctx;
+    int id;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(goac_ctx* c, int kid, cudaStream_t s);
+    ~KTimer();
+};
 goac_status ensure(DevBuf& b, size_t bytes);
 goac_status check_device_error(goac_ctx* ctx);
 int tc_supported(goac_ctx* ctx);

@@ -306,10 +306,10 @@ extern "C" goac_status goac_build_ewald(goac_ctx* ctx, const double* lattice_hos
     TRY(cudaMalloc(&dCart, sizeof(double) * 3 * N));
     TRY(cudaMalloc(&dImg, sizeof(double4) * nimg_total));
     TRY(cudaMemcpyAsync(dA, lattice_host, 9 * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_geometry<<<1, 32, 0, st>>>(dA, dG);
-    k_kvectors<<<1, 1024, 0, st>>>(dG, M[0], M[1], M[2], kcut, alpha, ke, dK, dCount);
-    k_frac_to_cart<<<(N + 255) / 256, 256, 0, st>>>(dG, frac_dev, N, dCart);
-    k_images<<<(nimg_total + 255) / 256, 256, 0, st>>>(dG, nimg_host[0], nimg_host[1], nimg_host[2], dImg);
+    goac::launch(k_geometry, 1, 32, 0, st, dA, dG);
+    goac::launch(k_kvectors, 1, 1024, 0, st, dG, M[0], M[1], M[2], kcut, alpha, ke, dK, dCount);
+    goac::launch(k_frac_to_cart, (N + 255) / 256, 256, 0, st, dG, frac_dev, N, dCart);
+    goac::launch(k_images, (nimg_total + 255) / 256, 256, 0, st, dG, nimg_host[0], nimg_host[1], nimg_host[2], dImg);
     TRY(cudaGetLastError());
     TRY(cudaMemcpyAsync(&K, dCount, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
@@ -320,16 +320,18 @@ extern "C" goac_status goac_build_ewald(goac_ctx* ctx, const double* lattice_hos
         long total = (long)N * ldx;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 65535 * 16) blocks = 65535 * 16;
-        k_struct_factor<<<blocks, 256, 0, st>>>(dK, K, dCart, N, dX, ldx);
+        goac::launch(k_struct_factor, blocks, 256, 0, st, dK, K, dCart, N, dX, ldx);
     }
     {
         int nb = (N + SY_BM - 1) / SY_BM;
         long ntiles = (long)nb * (nb + 1) / 2;
-        k_syrk_f64<<<(unsigned)ntiles, 256, 0, st>>>(dX, N, ldx, J_dev);
+        goac::KTimer kt(ctx, goac::KID_EWALD_SYRK, st);
+        goac::launch(k_syrk_f64, (unsigned)ntiles, 256, 0, st, dX, N, ldx, J_dev);
     }
     {
         dim3 grid((N + 15) / 16, (N + 15) / 16), block(16, 16);
-        k_real_space<<<grid, block, 0, st>>>(dG, frac_dev, N, dImg, nimg_total, alpha, ke, J_dev);
+        goac::KTimer kt(ctx, goac::KID_EWALD_REAL, st);
+        goac::launch(k_real_space, grid, block, 0, st, dG, frac_dev, N, dImg, nimg_total, alpha, ke, J_dev);
     }
     TRY(cudaGetLastError());
     TRY(cudaStreamSynchronize(st));

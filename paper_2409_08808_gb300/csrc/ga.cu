@@ -277,9 +277,9 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     unsigned long long* ftot = pre + P;
     double* mm = (double*)(ftot + 2);
     int* elite = (int*)(mm + 2);
-    k_ga_minmax<<<1, 1024, 0, st>>>(E, P, mm);
-    k_ga_fitness<<<1, 1024, 0, st>>>(E, P, mm, pre, ftot);
-    if (n_elite > 0) k_ga_rank<<<(P + 255) / 256, 256, 0, st>>>(E, P, n_elite, elite);
+    goac::launch(k_ga_minmax, 1, 1024, 0, st, E, P, mm);
+    goac::launch(k_ga_fitness, 1, 1024, 0, st, E, P, mm, pre, ftot);
+    if (n_elite > 0) goac::launch(k_ga_rank, (P + 255) / 256, 256, 0, st, E, P, n_elite, elite);
     GOAC_LAUNCH_CHECK("ga prep");
     GaArgs a;
     a.pop = pop;
@@ -311,7 +311,8 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     if (slot > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     const size_t smem = slot * wpb;
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_ga_children<<<(P + wpb - 1) / wpb, 32 * wpb, smem, st>>>(a);
+    KTimer kt(ctx, KID_GA, st);
+    goac::launch(k_ga_children, (P + wpb - 1) / wpb, 32 * wpb, smem, st, a);
     GOAC_LAUNCH_CHECK("k_ga_children");
     return GOAC_OK;
 }

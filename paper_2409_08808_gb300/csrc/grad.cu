@@ -263,12 +263,12 @@ extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev
     double* Phi = Q + BN;
     double* colsum = Phi + BN;
     cudaStream_t st = p->ctx->stream;
-    k_softmax<<<(int)((BN + 255) / 256), 256, 0, st>>>(logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev, p->z_dev,
+    goac::launch(k_softmax, (int)((BN + 255) / 256), 256, 0, st, logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev, p->z_dev,
                                                        P_, Q);
-    k_colsum<<<B * ncls, 256, 0, st>>>(P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
+    goac::launch(k_colsum, B * ncls, 256, 0, st, P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
     dim3 grid((B + GM - 1) / GM, (Nv + GM - 1) / GM);
-    k_phi_real<<<grid, 256, 0, st>>>(p->J_vv, p->Nv_pad, Nv, Q, B, Phi);
-    k_grad_finish<<<B, 256, 0, st>>>(P_, Q, Phi, p->phifix, colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
+    goac::launch(k_phi_real, grid, 256, 0, st, p->J_vv, p->Nv_pad, Nv, Q, B, Phi);
+    goac::launch(k_grad_finish, B, 256, 0, st, P_, Q, Phi, p->phifix, colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
                                      ncls, lambda, p->E_const, E_dev, dlogits_dev);
     GOAC_LAUNCH_CHECK("goac_energy_grad");
     return GOAC_OK;
@@ -305,11 +305,11 @@ extern "C" goac_status goac_round_to_counts(goac_problem* p, const float* p_dev,
     GOAC_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * ncls, cudaMemcpyHostToDevice, st));
     GOAC_CUDA(cudaMemcpyAsync(d_M, Ms.data(), sizeof(int) * ncls, cudaMemcpyHostToDevice, st));
     GOAC_CUDA(cudaMemsetAsync(species_dev, 0xff, (size_t)B * p->Nv, st));
-    k_round_keys<<<B * ncls, 256, 0, st>>>(p_dev, p->Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, p->counts_dev, d_off,
+    goac::launch(k_round_keys, B * ncls, 256, 0, st, p_dev, p->Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, p->counts_dev, d_off,
                                            d_M, per_b, keys);
-    k_bitonic<<<B * ncls, 1024, 0, st>>>(keys, ncls, d_off, d_M, per_b);
+    goac::launch(k_bitonic, B * ncls, 1024, 0, st, keys, ncls, d_off, d_M, per_b);
     const long nt = (long)B * ncls;
-    k_round_greedy<<<(int)((nt + 127) / 128), 128, 0, st>>>(keys, B, p->Nv, S, ncls, p->cls_start_dev, p->counts_dev,
+    goac::launch(k_round_greedy, (int)((nt + 127) / 128), 128, 0, st, keys, B, p->Nv, S, ncls, p->cls_start_dev, p->counts_dev,
                                                             d_off, per_b, species_dev, p->ctx->d_err);
     GOAC_LAUNCH_CHECK("goac_round_to_counts");
     return GOAC_OK;

@@ -170,9 +170,23 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                 sp[cb] = ta;
             }
             if (cd != (R)0) {
-                const R* ra = J + (long)ca * ld;
-                const R* rb = J + (long)cb * ld;
-                for (int w = lane; w < Nv; w += 32) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(ra[w], rb[w])));
+                const R* __restrict__ ra = J + (long)ca * ld;
+                const R* __restrict__ rb = J + (long)cb * ld;
+                // 8 loads of each row in flight per lane before the updates
+                for (int w0 = lane; w0 < Nv; w0 += 32 * 8) {
+                    R xa[8], xb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int w = w0 + 32 * u;
+                        xa[u] = w < Nv ? ra[w] : (R)0;
+                        xb[u] = w < Nv ? rb[w] : (R)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int w = w0 + 32 * u;
+                        if (w < Nv) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(xa[u], xb[u])));
+                    }
+                }
             }
             __syncwarp();
             E = E + (double)cdE;
@@ -304,12 +318,13 @@ extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t
     McProb d = make_desc(p, f32, species_dev, C, kT_dev, E_dev, bestE_dev, best_species_dev, n_accept_dev, seed);
     McScalars sc{n_steps, step0};
     const int blocks = (C + wpb - 1) / wpb;
+    goac::KTimer kt(p->ctx, goac::KID_MC, p->ctx->stream);
     if (f32) {
         GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mc<float><<<blocks, 32 * wpb, smem, p->ctx->stream>>>(d, sc, p->ctx->d_err);
+        goac::launch(k_mc<float>, blocks, 32 * wpb, smem, p->ctx->stream, d, sc, p->ctx->d_err);
     } else {
         GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mc<double><<<blocks, 32 * wpb, smem, p->ctx->stream>>>(d, sc, p->ctx->d_err);
+        goac::launch(k_mc<double>, blocks, 32 * wpb, smem, p->ctx->stream, d, sc, p->ctx->d_err);
     }
     GOAC_LAUNCH_CHECK("k_mc");
     return GOAC_OK;
@@ -378,10 +393,10 @@ extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* pro
             const int blocks = (descs[i].chains + wpb - 1) / wpb;
             if (f32) {
                 GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-                k_mc<float><<<blocks, 32 * wpb, smem, st>>>(descs[i], sc, ctx->d_err);
+                goac::launch(k_mc<float>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
             } else {
                 GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-                k_mc<double><<<blocks, 32 * wpb, smem, st>>>(descs[i], sc, ctx->d_err);
+                goac::launch(k_mc<double>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
             }
             GOAC_LAUNCH_CHECK("k_mc (per problem)");
         }
@@ -421,15 +436,16 @@ extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* pro
         cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
         if (f32)
-            k_mc_batch<float><<<grid, 32 * chains_per_cta, smem, st>>>((const McProb*)ctx->batch_desc.ptr,
+            goac::launch(k_mc_batch<float>, grid, 32 * chains_per_cta, smem, st, (const McProb*)ctx->batch_desc.ptr,
                                                                         (const int2*)ctx->batch_items.ptr, n_items,
                                                                         counter, d_sc, max_nv, ctx->d_err);
         else
-            k_mc_batch<double><<<grid, 32 * chains_per_cta, smem, st>>>((const McProb*)ctx->batch_desc.ptr,
+            goac::launch(k_mc_batch<double>, grid, 32 * chains_per_cta, smem, st, (const McProb*)ctx->batch_desc.ptr,
                                                                          (const int2*)ctx->batch_items.ptr, n_items,
                                                                          counter, d_sc, max_nv, ctx->d_err);
         return cudaGetLastError();
     };
+    goac::KTimer kt(ctx, goac::KID_MC, ctx->stream);
     if (mode == 1) {
         cudaError_t e = enqueue();
         if (e != cudaSuccess) return goac::cuda_fail(e, "k_mc_batch");

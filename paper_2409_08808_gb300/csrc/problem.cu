@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "common.cuh"
@@ -55,6 +56,35 @@ goac_status check_device_error(goac_ctx* ctx)
         return fail(h[0], buf);
     }
     return GOAC_OK;
+}
+
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+KTimer::KTimer(goac_ctx* c, int kid, cudaStream_t s) : ctx(c), id(kid), st(s)
+{
+    if (!ctx || !ctx->timing) return;
+    auto take = [&]() {
+        cudaEvent_t e = nullptr;
+        if (!ctx->event_pool.empty()) {
+            e = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    };
+    a = take();
+    b = take();
+    cudaEventRecord(a, st);
+}
+
+KTimer::~KTimer()
+{
+    if (!a) return;
+    cudaEventRecord(b, st);
+    ctx->timed[id].push_back({a, b});
 }
 
 int tc_supported(goac_ctx* ctx)
@@ -114,6 +144,12 @@ extern "C" goac_status goac_ctx_destroy(goac_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+    for (auto& v : ctx->timed)
+        for (auto& pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     free_buf(ctx->host_io_species);
     free_buf(ctx->host_io_E);
     free_buf(ctx->batch_desc);
@@ -123,6 +159,37 @@ extern "C" goac_status goac_ctx_destroy(goac_ctx* ctx)
     delete ctx;
     return GOAC_OK;
 }
+
+extern "C" goac_status goac_ctx_set_timing(goac_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ctx_set_timing: ctx is NULL");
+    ctx->timing = enable != 0;
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_ctx_kernel_time(goac_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches)
+{
+    if (!ctx || kernel < 0 || kernel >= goac::KID_COUNT)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ctx_kernel_time: bad argument");
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    double tot = 0.0;
+    int64_t n = 0;
+    for (auto& pr : ctx->timed[kernel]) {
+        GOAC_CUDA(cudaEventSynchronize(pr.second));
+        float ms = 0.0f;
+        GOAC_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+        ++n;
+        ctx->event_pool.push_back(pr.first);
+        ctx->event_pool.push_back(pr.second);
+    }
+    ctx->timed[kernel].clear();
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return GOAC_OK;
+}
+
+extern "C" int64_t goac_launch_count(void) { return (int64_t)goac::g_launches.load(); }
 
 extern "C" goac_status goac_ctx_set_stream(goac_ctx* ctx, void* stream)
 {
@@ -370,18 +437,19 @@ static goac_status score_cuda_core(goac_problem* p, const T* J, const int8_t* sp
         if (rc) return rc;
     }
     double* part = (double*)p->partial.ptr;
+    KTimer kt(ctx, KID_SCORE_CC, ctx->stream);
     if (E_out && phi_out)
-        k_phi<T, true, true><<<grid, 256, 0, ctx->stream>>>(J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
+        goac::launch(k_phi<T, true, true>, grid, 256, 0, ctx->stream, J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
                                                             part, phi_out);
     else if (E_out)
-        k_phi<T, true, false><<<grid, 256, 0, ctx->stream>>>(J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
+        goac::launch(k_phi<T, true, false>, grid, 256, 0, ctx->stream, J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
                                                              part, nullptr);
     else
-        k_phi<T, false, true><<<grid, 256, 0, ctx->stream>>>(J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
+        goac::launch(k_phi<T, false, true>, grid, 256, 0, ctx->stream, J, p->Nv_pad, p->Nv, species, B, p->z_dev, p->phifix,
                                                              nullptr, phi_out);
     GOAC_LAUNCH_CHECK("k_phi");
     if (E_out) {
-        k_finish_E<<<(B + 255) / 256, 256, 0, ctx->stream>>>(part, mt, B, p->E_const, E_out);
+        goac::launch(k_finish_E, (B + 255) / 256, 256, 0, ctx->stream, part, mt, B, p->E_const, E_out);
         GOAC_LAUNCH_CHECK("k_finish_E");
     }
     return GOAC_OK;
@@ -456,6 +524,7 @@ extern "C" goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, i
     p->S = S;
     p->ncls = n_class;
     p->Nv_pad = ((Nv + 127) / 128) * 128;
+    p->has_fixed = !fsite.empty();
     p->z.assign(z_host, z_host + S);
     p->counts.assign(counts_host, counts_host + n_class * S);
     p->vclass.resize(Nv);
@@ -532,9 +601,9 @@ extern "C" goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, i
         if (rc == GOAC_OK) {
             long total = (long)ld * ld;
             int blocks = (int)std::min<long>((total + 255) / 256, 65535L * 8);
-            k_gather_jvv<<<blocks, 256, 0, st>>>(J_dev, N, d_vsite, Nv, ld, p->J_vv, p->diag);
-            k_rowsum_fixed<<<(N + 7) / 8, 256, 0, st>>>(J_dev, N, d_fsite, d_fq, Nf, d_s);
-            k_fixed_finish<<<1, 256, 0, st>>>(d_s, d_vsite, Nv, ld, d_fsite, d_fq, Nf, p->phifix, d_ec);
+            goac::launch(k_gather_jvv, blocks, 256, 0, st, J_dev, N, d_vsite, Nv, ld, p->J_vv, p->diag);
+            goac::launch(k_rowsum_fixed, (N + 7) / 8, 256, 0, st, J_dev, N, d_fsite, d_fq, Nf, d_s);
+            goac::launch(k_fixed_finish, 1, 256, 0, st, d_s, d_vsite, Nv, ld, d_fsite, d_fq, Nf, p->phifix, d_ec);
             PTRY(cudaGetLastError());
             PTRY(cudaMemcpyAsync(&p->E_const, d_ec, sizeof(double), cudaMemcpyDeviceToHost, st));
             PTRY(cudaStreamSynchronize(st));
@@ -580,6 +649,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->score_tmp);
     free_buf(p->topk_tmp);
     free_buf(p->grad_tmp);
+    free_buf(p->sched);
     delete p;
     return GOAC_OK;
 }
@@ -651,12 +721,12 @@ extern "C" goac_status goac_topk_rescore(goac_problem* p, const int8_t* species_
     int* sel = (int*)p->topk_tmp.ptr;
     double* e64 = (double*)((char*)p->topk_tmp.ptr + sizeof(int) * 1024);
     int8_t* sub = (int8_t*)((char*)p->topk_tmp.ptr + sizeof(int) * 1024 + sizeof(double) * 1024);
-    k_rank_select<<<(B + 255) / 256, 256, 0, ctx->stream>>>(E_approx_dev, B, k, sel);
-    k_gather_rows<<<(int)(((long)k * p->Nv + 255) / 256), 256, 0, ctx->stream>>>(species_dev, p->Nv, sel, k, sub);
+    goac::launch(k_rank_select, (B + 255) / 256, 256, 0, ctx->stream, E_approx_dev, B, k, sel);
+    goac::launch(k_gather_rows, (int)(((long)k * p->Nv + 255) / 256), 256, 0, ctx->stream, species_dev, p->Nv, sel, k, sub);
     GOAC_LAUNCH_CHECK("topk select");
     rc = goac::score_f64(p, sub, k, e64, nullptr);
     if (rc) return rc;
-    k_sort_small<<<1, 1024, 0, ctx->stream>>>(e64, sel, k, idx_dev, E_dev);
+    goac::launch(k_sort_small, 1, 1024, 0, ctx->stream, e64, sel, k, idx_dev, E_dev);
     GOAC_LAUNCH_CHECK("k_sort_small");
     return GOAC_OK;
 }
@@ -667,9 +737,38 @@ extern "C" goac_status goac_random_configs(goac_problem* p, int32_t B, uint64_t 
     if (B == 0) return GOAC_OK;
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     long t = (long)B * p->ncls;
-    k_random_configs<<<(int)((t + 127) / 128), 128, 0, p->ctx->stream>>>(B, p->ncls, p->S, p->cls_start_dev,
+    goac::launch(k_random_configs, (int)((t + 127) / 128), 128, 0, p->ctx->stream, B, p->ncls, p->S, p->cls_start_dev,
                                                                          p->cls_pos_dev, p->counts_dev, seed, p->Nv,
                                                                          species_dev);
     GOAC_LAUNCH_CHECK("k_random_configs");
     return GOAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Failure-detection self test: one thread waits on an mbarrier that nothing
+// arrives on, with the same clock-bounded wait the tensor-core kernels use.
+// The wait runs out, the kernel records GOAC_ERR_TIMEOUT in the device error
+// word and returns; the context stays usable.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_selftest_wait(long long limit_cycles, int* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    goacd::mbar_init(&bar, 1);
+    goacd::fence_barrier_init();
+    if (!goacd::mbar_wait_bounded(&bar, 0, limit_cycles)) goacd::report(err, GOAC_ERR_TIMEOUT, 99, 0);
+}
+
+}  // namespace
+
+extern "C" goac_status goac_selftest_wait_timeout(goac_ctx* ctx, int64_t limit_cycles)
+{
+    if (!ctx || limit_cycles <= 0 || limit_cycles > 4000000000LL)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_selftest_wait_timeout: bad argument");
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    goac::launch(k_selftest_wait, 1, 32, 0, ctx->stream, (long long)limit_cycles, ctx->d_err);
+    GOAC_LAUNCH_CHECK("k_selftest_wait");
+    return goac::check_device_error(ctx);
 }

@@ -2,22 +2,30 @@
 // tcgen05 tensor cores (sm_103a): the objective of Eq. 2 evaluated for a whole
 // population as one dense contraction Phi = J_vv Q followed by a row-dot.
 //
-// J_vv is split into T low-precision terms (BF16: J = J1 + J2 [+ J3], each the
-// BF16 rounding of the remainder; TF32: hi + lo).  Charges are small integers
-// and exact in BF16 / TF32, so Q needs no split.  Per CTA one 128 (sites) x
-// 256 (configs) FP32 accumulator lives in TMEM (256 columns); every k-block
-// stage holds the T J-tiles (128 x 128 B each) and one Q-tile (256 x 128 B),
-// loaded by TMA with the 128-byte swizzle, and the single MMA thread issues
-// T x 4 tcgen05.mma (K = 16 BF16 / 8 TF32 each) into the same accumulator.
-// Warp roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
-// warp 2 = TMEM allocator; then all 4 warps run the epilogue: tcgen05.ld of
-// their 32 TMEM lanes (= 32 sites), q (Phi + 2 phi_fix) in FP32, a butterfly
-// transpose-reduce across the warp so lane l owns config column l, and the
-// 4 warp sums are added in FP64 into partial[m-tile][config].  A second tiny
-// kernel adds the m-tiles in a fixed order plus E_const (deterministic).
+// J is symmetric, so E = sum_{I <= J} q_I^T J'_IJ q_J over 128 x 128 blocks
+// with J'_II = J_II and J'_IJ = 2 J_IJ (I < J): half the products.  J' is
+// split into T low-precision terms (BF16: J' = J1 + J2 [+ J3], each the BF16
+// rounding of the remainder; TF32: hi + lo); doubling is exact in both.
+// Charges are small integers and exact in BF16 / TF32, so Q needs no split.
+// Persistent grid (one CTA per SM), tiles of 128 sites x 256 configurations
+// assigned longest-first by the host; the tile of m-block I runs over the
+// k-range from column 128 I.  Two FP32 accumulators live in TMEM (2 x 256
+// columns) so the epilogue of one tile overlaps the MMAs of the next.  Every
+// k-block stage holds the T J'-tiles (128 x 128 B) and one Q-tile (256 x
+// 128 B), loaded by TMA with the 128-byte swizzle; the single MMA thread
+// issues T x 4 tcgen05.mma (K = 16 BF16 / 8 TF32) into the tile's accumulator.
+// Warp roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer, warps
+// 2-5 = epilogue (warp 2 also owns the TMEM allocation): tcgen05.ld of their 32
+// TMEM lanes (= 32 sites), q Phi in FP32, a butterfly transpose-reduce
+// across the warp so lane l owns config column l, and the 4 warp sums are added
+// in FP64 into partial[m-tile][config].  The linear term 2 q . phi_fix is formed
+// in FP64 while Q is built (k_make_qt), and a second tiny kernel adds the
+// m-tiles in a fixed order plus the linear term and E_const (deterministic).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -35,39 +43,46 @@ struct TcCfg {
     static constexpr int STAGE = T * A_TILE + B_TILE;
     static constexpr int STAGES_RAW = (196 * 1024) / STAGE;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
-    static constexpr int BAR_BYTES = 256;
+    static constexpr int BAR_BYTES = 256;   // stage barriers, 2 + 2 accumulator barriers, TMEM slot, flag
     static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES;
 };
 
+// Persistent kernel.  CTA c processes the tiles work[work_start[c] ..
+// work_start[c+1]) (host LPT schedule, longest first); tile = (m-block I,
+// n-tile); with the symmetric operand its k-range starts at column 128 I.
 template <int T, bool TF32>
-__global__ void __launch_bounds__(128, 1)
-    k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nkb,
-               int Nv_pad, int Nv, const void* __restrict__ qt, int ldq, const double* __restrict__ phifix,
-               double* __restrict__ partial, int Bpad, int* __restrict__ err)
+__global__ void __launch_bounds__(192, 1)
+    k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int Nv_pad,
+               const void* __restrict__ qt, int ldq, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
     using Cfg = TcCfg<T>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr int STAGE = Cfg::STAGE;
     constexpr int KE = TF32 ? 32 : 64;          // elements per 128-byte row
+    constexpr int KB_PER_M = TC_M / KE;         // k-blocks per 128 columns
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint64_t* tfull = empty + STAGES;           // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;               // [2] accumulator drained
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     __shared__ float red[4][TC_N];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_M;
-    const int n0 = blockIdx.x * TC_N;
+    const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             goacd::mbar_init(&full[s], 1);
             goacd::mbar_init(&empty[s], 1);
         }
-        goacd::mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 4);
+        }
         *abort_flag = 0;
         goacd::fence_barrier_init();
     }
@@ -76,7 +91,7 @@ __global__ void __launch_bounds__(128, 1)
         goacd::prefetch_tmap(&tmB);
     }
     if (warp == 2) {
-        goacd::tmem_alloc(tmem_slot, TC_N);
+        goacd::tmem_alloc(tmem_slot, 2 * TC_N);
         goacd::tmem_relinquish();
     }
     goacd::tc_fence_before();
@@ -85,119 +100,160 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
+        // ---------------- TMA producer ----------------
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t use = (uint32_t)(kb / STAGES);
-                if (kb >= STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
-                    *abort_flag = 1;
-                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, kb);
-                    break;
-                }
-                if (*abort_flag) break;
-                uint8_t* st = smem + s * STAGE;
-                goacd::mbar_arrive_expect_tx(&full[s], STAGE);
+            int it = 0;
+            for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
+                const int2 tile = work[wi];
+                const int m0 = tile.x * TC_M, n0 = tile.y * TC_N;
+                for (int kb = tile.x * KB_PER_M; kb < nkb_total; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
+                    if (it >= STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], STAGE);
 #pragma unroll
-                for (int t = 0; t < T; ++t) goacd::tma_load_2d(st + t * A_TILE, &tmA, &full[s], kb * KE, t * Nv_pad + m0);
-                goacd::tma_load_2d(st + T * A_TILE, &tmB, &full[s], kb * KE, n0);
-                issued = kb + 1;
+                    for (int t = 0; t < T; ++t)
+                        goacd::tma_load_2d(st + t * A_TILE, &tmA, &full[s], kb * KE, t * Nv_pad + m0);
+                    goacd::tma_load_2d(st + T * A_TILE, &tmB, &full[s], kb * KE, n0);
+                }
             }
             if (*abort_flag) {
-                // drain: every copy this thread started must land before the CTA exits
-                for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                    if (!goacd::mbar_wait_bounded(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1, WAIT_LIMIT))
-                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, kb);
+                // every copy this thread started must land before the CTA exits
+                for (int k = it - STAGES < 0 ? 0 : it - STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % STAGES], (uint32_t)(k / STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = goacd::idesc_f32acc(TF32 ? 2u : 1u, TC_M, TC_N);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t use = (uint32_t)(kb / STAGES);
-                if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+            int it = 0, tl = 0;
+            for (int wi = w0; wi < w1; ++wi, ++tl) {
+                const int2 tile = work[wi];
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
                     *abort_flag = 1;
-                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, kb);
-                    break;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
                 }
-                if (*abort_flag) break;
                 goacd::tc_fence_after();
-                const uint32_t a0 = goacd::smem_u32(smem + s * STAGE);
-                const uint32_t b0 = a0 + T * A_TILE;
-#pragma unroll
-                for (int t = 0; t < T; ++t)
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = goacd::sdesc_k128(a0 + t * A_TILE + kk * 32);
-                        const uint64_t bd = goacd::sdesc_k128(b0 + kk * 32);
-                        const uint32_t acc = (kb | t | kk) != 0;
-                        if (TF32) goacd::mma_tf32(tmem, ad, bd, idesc, acc);
-                        else goacd::mma_bf16(tmem, ad, bd, idesc, acc);
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TC_N);
+                const int kb0 = tile.x * KB_PER_M;
+                for (int kb = kb0; kb < nkb_total; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
                     }
-                goacd::mma_commit(&empty[s]);
+                    goacd::tc_fence_after();
+                    const uint32_t a0 = goacd::smem_u32(smem + s * STAGE);
+                    const uint32_t b0 = a0 + T * A_TILE;
+#pragma unroll
+                    for (int t = 0; t < T; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = goacd::sdesc_k128(a0 + t * A_TILE + kk * 32);
+                            const uint64_t bd = goacd::sdesc_k128(b0 + kk * 32);
+                            const uint32_t acc = (kb != kb0 || t != 0 || kk != 0) ? 1u : 0u;
+                            if (TF32) goacd::mma_tf32(d_tmem, ad, bd, idesc, acc);
+                            else goacd::mma_bf16(d_tmem, ad, bd, idesc, acc);
+                        }
+                    goacd::mma_commit(&empty[s]);
+                }
+                goacd::mma_commit(&tfull[acc_i]);
             }
-            goacd::mma_commit(done);
         }
         __syncwarp();
-    }
-
-    // ---- epilogue: all four warps -------------------------------------------
-    const bool ok = goacd::mbar_wait_bounded(done, 0, WAIT_LIMIT) && !*abort_flag;
-    if (!ok && threadIdx.x == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, 0);
-    goacd::tc_fence_after();
-    if (ok) {
-        const int row = warp * 32 + lane;
-        const int v = m0 + row;
-        const float pf2 = v < Nv ? (float)(2.0 * phifix[v]) : 0.0f;
+    } else {
+        // ---------------- epilogue: warps 2..5 ----------------
+        const int lg = warp & 3;                   // TMEM lane group this warp may access
+        const int etid = threadIdx.x - 64;         // 0..127
+        int tl = 0;
+        for (int wi = w0; wi < w1; ++wi, ++tl) {
+            const int2 tile = work[wi];
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            const int v = tile.x * TC_M + lg * 32 + lane;
+            const long n0 = (long)tile.y * TC_N;
 #pragma unroll 1
-        for (int c = 0; c < TC_N / 32; ++c) {
-            uint32_t r[32];
-            goacd::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-            goacd::tmem_ld_wait();
-            float val[32];
+            for (int c = 0; c < TC_N / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TC_N) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                float val[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const long b = n0 + c * 32 + j;
-                float q;
-                if (TF32) q = ((const float*)qt)[b * ldq + v];
-                else q = __bfloat162float(((const __nv_bfloat16*)qt)[b * ldq + v]);
-                val[j] = q * (__uint_as_float(r[j]) + pf2);
+                for (int j = 0; j < 32; ++j) {
+                    const long b = n0 + c * 32 + j;
+                    float q;
+                    if (TF32) q = ((const float*)qt)[b * ldq + v];
+                    else q = __bfloat162float(((const __nv_bfloat16*)qt)[b * ldq + v]);
+                    val[j] = q * __uint_as_float(r[j]);
+                }
+                // butterfly transpose-reduce: afterwards lane l holds column l summed over the warp
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const bool up = (lane & sft) != 0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < sft) {
+                            const float send = up ? val[k] : val[k + sft];
+                            const float keep = up ? val[k + sft] : val[k];
+                            val[k] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+                        }
+                }
+                red[lg][c * 32 + lane] = val[0];
             }
-            // butterfly transpose-reduce: afterwards lane l holds column l summed over the warp
-#pragma unroll
-            for (int sft = 16; sft >= 1; sft >>= 1) {
-                const bool up = (lane & sft) != 0;
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (k < sft) {
-                        const float send = up ? val[k] : val[k + sft];
-                        const float keep = up ? val[k + sft] : val[k];
-                        val[k] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
-                    }
-            }
-            red[warp][c * 32 + lane] = val[0];
+            // the accumulator may be refilled once every warp's loads have completed
+            goacd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
+            goacd::named_bar_sync(1, 128);
+            if (ok)
+                for (int col = etid; col < TC_N; col += 128) {
+                    const double ssum =
+                        (double)red[0][col] + (double)red[1][col] + (double)red[2][col] + (double)red[3][col];
+                    partial[(long)tile.x * Bpad + n0 + col] = ssum;
+                }
+            goacd::named_bar_sync(1, 128);
         }
     }
     goacd::tc_fence_before();
     __syncthreads();
-    if (ok) {
-        for (int col = threadIdx.x; col < TC_N; col += 128) {
-            const double s = (double)red[0][col] + (double)red[1][col] + (double)red[2][col] + (double)red[3][col];
-            partial[(long)blockIdx.y * Bpad + n0 + col] = s;
-        }
-    }
     if (warp == 2) {
         goacd::tc_fence_after();
-        goacd::tmem_dealloc(tmem, TC_N);
+        goacd::tmem_dealloc(tmem, 2 * TC_N);
     }
 }
 
-__global__ void k_split_bf16(const double* __restrict__ J, long n, __nv_bfloat16* __restrict__ out)
+// Symmetric operand: J'_ij = J_ij on diagonal 128-blocks, 2 J_ij above them,
+// 0 below, so that q^T J q = sum over the upper block triangle of q_I^T J'_IJ q_J.
+__device__ __forceinline__ double sym_upper(const double* J, long e, int ld)
+{
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    const int bi = i / 128, bj = j / 128;
+    return bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]);
+}
+
+__global__ void k_split_bf16(const double* __restrict__ J, long n, int ld, __nv_bfloat16* __restrict__ out)
 {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double x = J[e];
+        const double x = sym_upper(J, e, ld);
         const __nv_bfloat16 t1 = __double2bfloat16(x);
         const double r1 = x - (double)__bfloat162float(t1);
         const __nv_bfloat16 t2 = __double2bfloat16(r1);
@@ -216,10 +272,10 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-__global__ void k_split_tf32(const double* __restrict__ J, long n, float* __restrict__ out)
+__global__ void k_split_tf32(const double* __restrict__ J, long n, int ld, float* __restrict__ out)
 {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-        const double x = J[e];
+        const double x = sym_upper(J, e, ld);
         const float hi = to_tf32((float)x);
         const float lo = to_tf32((float)(x - (double)hi));
         out[e] = hi;
@@ -236,31 +292,67 @@ __global__ void k_copy_f32(const double* __restrict__ J, long n, float* __restri
         diag_out[e] = (float)diag[e];
 }
 
-// Q^T[b][v] = z[species[b][v]] in BF16 or FP32, zero padded to Bpad x ld.
+// Q^T[b][v] = z[species[b][v]] in BF16 or FP32, zero padded to Bpad x ld, one
+// block per configuration row; 16 species per thread and step (one 16-byte load
+// when the row is 16-byte aligned), 16-byte stores.  With fixed ions also
+// lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
 template <typename QT>
-__global__ void k_make_qt(const int8_t* __restrict__ species, int B, int Nv, const double* __restrict__ z, int Bpad,
-                          int ld, QT* __restrict__ qt)
+__global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ species, int B, int Nv,
+                                                 const double* __restrict__ z, int ld, QT* __restrict__ qt,
+                                                 const double* __restrict__ phifix, double* __restrict__ lin)
 {
     __shared__ float zs[64];
+    __shared__ double red[256];
     if (threadIdx.x < 64) zs[threadIdx.x] = (float)z[threadIdx.x];
     __syncthreads();
-    const long total = (long)Bpad * ld;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(e / ld), v = (int)(e % ld);
-        float q = (b < B && v < Nv) ? zs[species[(long)b * Nv + v]] : 0.0f;
-        if constexpr (sizeof(QT) == 2) qt[e] = __float2bfloat16(q);
-        else qt[e] = q;
+    const int b = blockIdx.x;
+    QT* row = qt + (long)b * ld;
+    const int8_t* src = species + (long)b * Nv;
+    const bool aligned = ((Nv & 15) == 0) && (((uintptr_t)species & 15) == 0);
+    double acc = 0.0;
+    for (int v0 = threadIdx.x * 16; v0 < ld; v0 += blockDim.x * 16) {   // ld is a multiple of 128
+        int8_t s16[16];
+        if (b < B && aligned && v0 + 16 <= Nv) {
+            *(int4*)s16 = *(const int4*)(src + v0);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s16[u] = (b < B && v0 + u < Nv) ? src[v0 + u] : (int8_t)-1;
+        }
+        float q[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            q[u] = s16[u] >= 0 ? zs[s16[u]] : 0.0f;
+            if (phifix && s16[u] >= 0) acc += z[s16[u]] * (2.0 * phifix[v0 + u]);
+        }
+        if constexpr (sizeof(QT) == 2) {
+            __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16(q[u]);
+            ((int4*)(row + v0))[0] = ((const int4*)o)[0];
+            ((int4*)(row + v0))[1] = ((const int4*)o)[1];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ((float4*)(row + v0))[u] = make_float4(q[4 * u], q[4 * u + 1], q[4 * u + 2], q[4 * u + 3]);
+        }
     }
+    if (phifix == nullptr || b >= B) return;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lin[b] = red[0];
 }
 
 __global__ void k_finish_tc(const double* __restrict__ partial, int mtiles, int Bpad, int B, double E_const,
-                            double* __restrict__ E)
+                            const double* __restrict__ lin, double* __restrict__ E)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
     for (int m = 0; m < mtiles; ++m) s += partial[(long)m * Bpad + b];
-    E[b] = s + E_const;
+    E[b] = s + (lin ? lin[b] : 0.0) + E_const;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -298,6 +390,47 @@ goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int e
     return GOAC_OK;
 }
 
+// Longest-processing-time schedule of the (m-block, n-tile) tiles over the
+// CTAs of a persistent grid; cached per problem for the current shape.
+goac_status tc_schedule(goac_problem* p, int nbm, int nbn, int grid, const int2** work, const int** starts)
+{
+    const uint64_t key = ((uint64_t)nbm << 40) | ((uint64_t)nbn << 20) | (uint64_t)grid;
+    if (p->sched_key != key) {
+        std::vector<int2> tiles;
+        for (int I = 0; I < nbm; ++I)
+            for (int n = 0; n < nbn; ++n) tiles.push_back(make_int2(I, n));
+        std::stable_sort(tiles.begin(), tiles.end(), [](const int2& a, const int2& b) { return a.x < b.x; });
+        std::vector<std::vector<int2>> per(grid);
+        std::vector<long> load(grid, 0);
+        for (const int2& t : tiles) {
+            int best = 0;
+            for (int c = 1; c < grid; ++c)
+                if (load[c] < load[best]) best = c;
+            per[best].push_back(t);
+            load[best] += (nbm - t.x) + 1;   // k-blocks of 128 columns, +1 for the epilogue
+        }
+        std::vector<int2> flat;
+        std::vector<int> st(grid + 1, 0);
+        for (int c = 0; c < grid; ++c) {
+            st[c] = (int)flat.size();
+            flat.insert(flat.end(), per[c].begin(), per[c].end());
+        }
+        st[grid] = (int)flat.size();
+        const size_t bytes = sizeof(int2) * flat.size() + sizeof(int) * (grid + 1) + 64;
+        goac_status rc = goac::ensure(p->sched, bytes);
+        if (rc) return rc;
+        int2* dw = (int2*)p->sched.ptr;
+        int* ds = (int*)(dw + flat.size());
+        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice));
+        GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
+        p->sched_key = key;
+        p->sched_tiles = (int)flat.size();
+    }
+    *work = (const int2*)p->sched.ptr;
+    *starts = (const int*)((const int2*)p->sched.ptr + p->sched_tiles);
+    return GOAC_OK;
+}
+
 template <int T, bool TF32>
 goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, const void* qt,
                       double* part)
@@ -311,9 +444,15 @@ goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap&
     }
     const int ld = p->Nv_pad;
     const int nkb = TF32 ? ld / 32 : ld / 64;
-    dim3 grid(Bpad / TC_N, ld / TC_M);
-    kern<<<grid, 128, Cfg::SMEM, p->ctx->stream>>>(ma, mb, nkb, ld, p->Nv, qt, ld, p->phifix, part, Bpad,
-                                                   p->ctx->d_err);
+    const int nbm = ld / TC_M, nbn = Bpad / TC_N;
+    const int grid = std::min(nbm * nbn, p->ctx->num_sms);
+    const int2* work = nullptr;
+    const int* starts = nullptr;
+    goac_status rc = tc_schedule(p, nbm, nbn, grid, &work, &starts);
+    if (rc) return rc;
+    goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
+    goac::launch(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, nkb, ld, qt, ld, part, Bpad,
+                 p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_score_tc");
     return GOAC_OK;
 }
@@ -330,13 +469,13 @@ static goac_status prepare_split(goac_problem* p, int precision)
     if (precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3) {
         if (!p->J_bf16) {
             GOAC_CUDA(cudaMalloc(&p->J_bf16, sizeof(__nv_bfloat16) * 3 * (size_t)n));
-            k_split_bf16<<<blocks, 256, 0, st>>>(p->J_vv, n, p->J_bf16);
+            goac::launch(k_split_bf16, blocks, 256, 0, st, p->J_vv, n, p->Nv_pad, p->J_bf16);
             GOAC_LAUNCH_CHECK("k_split_bf16");
         }
     } else {
         if (!p->J_tf32) {
             GOAC_CUDA(cudaMalloc(&p->J_tf32, sizeof(float) * 2 * (size_t)n));
-            k_split_tf32<<<blocks, 256, 0, st>>>(p->J_vv, n, p->J_tf32);
+            goac::launch(k_split_tf32, blocks, 256, 0, st, p->J_vv, n, p->Nv_pad, p->J_tf32);
             GOAC_LAUNCH_CHECK("k_split_tf32");
         }
     }
@@ -350,7 +489,7 @@ goac_status prepare_f32(goac_problem* p)
     GOAC_CUDA(cudaMalloc(&p->J_f32, sizeof(float) * (size_t)n));
     GOAC_CUDA(cudaMalloc(&p->diag_f32, sizeof(float) * (size_t)p->Nv));
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
-    k_copy_f32<<<blocks, 256, 0, p->ctx->stream>>>(p->J_vv, n, p->J_f32, p->diag, p->Nv, p->diag_f32);
+    goac::launch(k_copy_f32, blocks, 256, 0, p->ctx->stream, p->J_vv, n, p->J_f32, p->diag, p->Nv, p->diag_f32);
     GOAC_LAUNCH_CHECK("k_copy_f32");
     return GOAC_OK;
 }
@@ -364,15 +503,15 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int eb = tf32 ? 4 : 2;
     rc = ensure(p->qt, (size_t)Bpad * ld * eb);
-    if (!rc) rc = ensure(p->partial, sizeof(double) * (size_t)(ld / TC_M) * Bpad);
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)(ld / TC_M) * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
+    double* lin = p->has_fixed ? (double*)p->partial.ptr + (size_t)(ld / TC_M) * Bpad : nullptr;
     {
-        const long total = (long)Bpad * ld;
-        const int blocks = (int)std::min<long>((total + 255) / 256, 65535L * 4);
-        if (tf32) k_make_qt<float><<<blocks, 256, 0, st>>>(species, B, p->Nv, p->z_dev, Bpad, ld, (float*)p->qt.ptr);
-        else k_make_qt<__nv_bfloat16><<<blocks, 256, 0, st>>>(species, B, p->Nv, p->z_dev, Bpad, ld,
-                                                             (__nv_bfloat16*)p->qt.ptr);
+        const double* pf = p->has_fixed ? p->phifix : nullptr;
+        if (tf32) goac::launch(k_make_qt<float>, Bpad, 256, 0, st, species, B, p->Nv, p->z_dev, ld, (float*)p->qt.ptr, pf, lin);
+        else goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, p->z_dev, ld,
+                                                           (__nv_bfloat16*)p->qt.ptr, pf, lin);
         GOAC_LAUNCH_CHECK("k_make_qt");
     }
     CUtensorMap ma, mb;
@@ -391,7 +530,7 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
         default: return fail(GOAC_ERR_INVALID_ARG, "score_tc: bad precision");
     }
     if (rc) return rc;
-    k_finish_tc<<<(B + 255) / 256, 256, 0, st>>>(part, ld / TC_M, Bpad, B, p->E_const, E_out);
+    goac::launch(k_finish_tc, (B + 255) / 256, 256, 0, st, part, ld / TC_M, Bpad, B, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_tc");
     return GOAC_OK;
 }

@@ -91,19 +91,55 @@ def test_score_tensor_core_forms(ctx, form, which, B):
     assert np.all(err <= tol), (err.max(), tol.min())
 
 
-def test_split_terms_reduce_error(ctx):
-    """Where FP32 accumulation error is small (N = 64 sites), every added split
-    term must cut the error: a dropped or duplicated term fails this."""
+def _round_sig(x, bits):
+    """Round to `bits` significant bits, ties to even (exact, via frexp)."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(np.ldexp(m, bits)), e - bits)
+
+
+def _tf32_rna(x32):
+    """float32 -> TF32 (10 stored mantissa bits), round to nearest, ties away."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32)
+    return ((b + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def _split_terms(J, form):
+    if form.startswith("bf16"):
+        T = 3 if form == "bf16x3" else 2
+        terms, r = [], J.copy()
+        for _ in range(T):
+            t = _round_sig(r, 8)
+            terms.append(t)
+            r = r - t
+        return terms
+    hi = _tf32_rna(J.astype(np.float32)).astype(np.float64)
+    if form == "tf32":
+        return [hi]
+    lo = _tf32_rna((J - hi).astype(np.float32)).astype(np.float64)
+    return [hi, lo]
+
+
+@pytest.mark.parametrize("form", ["bf16x2", "bf16x3", "tf32", "tf32x2"])
+def test_split_forms_match_their_definition(ctx, form):
+    """Each form equals q^T (sum of its split terms of the oracle's J) q, the
+    terms rounded exactly as the form defines them (BF16: round to nearest
+    even from FP64; TF32: FP64 -> FP32 -> TF32 round half away), within the
+    FP32 accumulation bound gamma_K R alone.  A dropped, duplicated or
+    mis-rounded term fails this."""
     prob = synth.rocksalt_problem((2, 2, 2), 4.2)
     Jg, Jo = build_pair(ctx, prob)
     gp = gpu_problem(ctx, prob, Jg)
-    pop = synth.random_population(prob, 512, 41)
-    Eo = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, pop)
-    sp = torch.tensor(pop, device="cuda")
-    err = {f: np.sqrt(np.mean((gp.score(sp, f).cpu().numpy() - Eo) ** 2)) for f in ("tf32", "tf32x2", "bf16x2", "bf16x3")}
-    assert err["tf32x2"] < err["tf32"] / 30
-    assert err["bf16x3"] < err["bf16x2"] / 8
-    assert err["bf16x2"] < err["tf32"]
+    pop = synth.random_population(prob, 300, 41)
+    vidx = np.nonzero(prob.site_class >= 0)[0]
+    Jvv = Jo[np.ix_(vidx, vidx)]
+    Jdef = sum(_split_terms(Jvv, form))
+    Jmod = Jo.copy()
+    Jmod[np.ix_(vidx, vidx)] = Jdef
+    Edef = oracle.score(Jmod, prob.site_class, prob.fixed_q, prob.z, pop)
+    Eg = gp.score(torch.tensor(pop, device="cuda"), form).cpu().numpy()
+    R = quad_scale(Jo, prob, pop)
+    K = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2}[form] * prob.Nv
+    assert np.all(np.abs(Eg - Edef) <= R * K * 2.0 ** -24)
 
 
 def test_topk_rescore(ctx):
