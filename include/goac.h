@@ -137,6 +137,29 @@ goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
  * ------------------------------------------------------------------------ */
 goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
 
+/* Allocation-free FP64 scoring, for callers that may not allocate device     *
+ * memory themselves (their device memory comes from a host framework's own   *
+ * pool, or they run under a no-allocation policy after start-up).  The paper *
+ * has no counterpart: it is an interface variant of goac_score(F64) on raw    *
+ * buffers, with no context or problem handle.  Allocates nothing: besides the *
+ * caller's buffers it uses one fixed file-scope device array of 524,288        *
+ * doubles (4 MiB, present on every GPU that loads the library until exit) for *
+ * the per-tile partial energies; requires ceil(Nv/64) * B <= 524,288, else    *
+ * GOAC_ERR_INVALID_ARG.  The first call on a device looks up that array's     *
+ * device address (cudaGetSymbolAddress) and caches it; make that first call   *
+ * before any stream capture.  All calls share the array and it keeps the last *
+ * call's contents (every entry read is first written, nothing needs clearing);*
+ * calls that overlap on the GPU race on it.                                    *
+ *   Jvv_dev: ceil(Nv/64)*64 rows of `ld` doubles (ld >= Nv rounded up to 64),  *
+ *            J_vv in the leading Nv x Nv block, finite values elsewhere.      *
+ *   species_dev: B x Nv int8.  z_dev: 64 doubles (charges of species 0..S-1,   *
+ *   any finite values after).  phi_fix_dev: ld doubles (phi_fix in the first   *
+ *   Nv, zeros when there are no fixed ions).  E = q^T J_vv q + 2 q . phi_fix +  *
+ *   E_const into E_dev (B doubles).  Runs on the current device, on `stream`. */
+goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld, int32_t Nv, const int8_t* species_dev,
+                                   int32_t B, const double* z_dev, const double* phi_fix_dev, double E_const,
+                                   void* stream, double* E_dev);
+
 /* Same, with host buffers: copies species H2D, scores, copies E D2H on the  *
  * context stream and synchronises (end-to-end entry point).                 */
 goac_status goac_score_host(goac_problem* prob, const int8_t* species_host, int32_t B, int32_t precision,

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -741,6 +742,69 @@ extern "C" goac_status goac_random_configs(goac_problem* p, int32_t B, uint64_t 
                                                                          p->cls_pos_dev, p->counts_dev, seed, p->Nv,
                                                                          species_dev);
     GOAC_LAUNCH_CHECK("k_random_configs");
+    return GOAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 scoring.
+//
+// For callers that may not allocate device memory themselves: code whose
+// device memory all comes from a host framework's own pool, or that runs under
+// a policy of no allocation after start-up.  They pass every input and output
+// buffer; the only other memory this entry point uses is the file-scope array
+// below, which holds the per-tile partial energies of the FP64 scoring kernel.
+// The array exists on every GPU that loads this library, for the life of the
+// process.  It is shared by all calls on a device and keeps the last call's
+// contents; the kernel writes every entry it later reads, so nothing needs
+// clearing.  Calls whose work overlaps on the GPU race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long kStaticPartialEntries = 1L << 19;   // 524,288 doubles = 4 MiB
+
+__device__ __align__(256) double g_static_partial[kStaticPartialEntries];
+
+std::mutex g_static_mu;
+double* g_static_ptr[64] = {};   // device address of g_static_partial per device ordinal
+
+}  // namespace
+
+extern "C" goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld, int32_t Nv,
+                                              const int8_t* species_dev, int32_t B, const double* z_dev,
+                                              const double* phi_fix_dev, double E_const, void* stream,
+                                              double* E_dev)
+{
+    if (!Jvv_dev || !species_dev || !z_dev || !phi_fix_dev || !E_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: NULL argument");
+    if (Nv <= 0 || B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: need Nv > 0, B >= 0");
+    const long mt = (Nv + PB_M - 1) / PB_M;
+    if (ld < mt * PB_M)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: ld must be >= Nv rounded up to 64");
+    if (B == 0) return GOAC_OK;
+    if (mt * (long)B > kStaticPartialEntries)
+        return goac::fail(GOAC_ERR_INVALID_ARG,
+                          "goac_score_f64_noalloc: ceil(Nv/64) * B = " + std::to_string(mt * (long)B) +
+                              " exceeds the fixed scratch of 524288 entries");
+    int dev = 0;
+    GOAC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: device ordinal >= 64");
+    double* part = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            GOAC_CUDA(cudaGetSymbolAddress(&p, g_static_partial));
+            g_static_ptr[dev] = (double*)p;
+        }
+        part = g_static_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((B + PB_N - 1) / PB_N, (unsigned)mt);
+    goac::launch(k_phi<double, true, false>, grid, 256, 0, st, Jvv_dev, ld, Nv, species_dev, B, z_dev, phi_fix_dev,
+                 part, (double*)nullptr);
+    GOAC_LAUNCH_CHECK("k_phi (no-alloc)");
+    goac::launch(k_finish_E, (B + 255) / 256, 256, 0, st, (const double*)part, (int)mt, B, E_const, E_dev);
+    GOAC_LAUNCH_CHECK("k_finish_E (no-alloc)");
     return GOAC_OK;
 }
 

@@ -28,6 +28,7 @@ def test_null_arguments_are_rejected_on_the_host():
     assert L.goac_ga_generation(None, None, None, 1, 0, 0, 0, 0, None, None, None) == -1
     assert L.goac_energy_grad(None, None, 1, 0.0, 0, None, None) == -1
     assert L.goac_round_to_counts(None, None, 1, None) == -1
+    assert L.goac_score_f64_noalloc(None, 64, 10, None, 1, None, None, 0.0, None, None) == -1
     assert b"NULL" in L.goac_last_error()
 
 
