@@ -51,6 +51,11 @@ def _args():
     ap.add_argument("--form", default=FORM, choices=sorted(TERMS))
     ap.add_argument("--mc-steps", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
+    ap.add_argument("--suite", action="store_true", help="measure the other workloads, one JSON line each")
+    ap.add_argument("--batch-cells", type=int, default=256)
+    ap.add_argument("--batch-chains", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=10000)
+    ap.add_argument("--grad-batch", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -400,8 +405,138 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_suite(args):
+    """One JSON line per workload of the build's configuration list (the
+    scoring benchmark of the default run is not repeated): rocksalt MC parity
+    run, layered-oxide GA, the uneven batch of cells (persistent / graph /
+    per-problem launches, autotuned chains per CTA), the relaxed-occupation
+    gradient at N = 8192, and Ewald build times."""
+    import torch
+
+    import goac_synth as synth
+    import oracle
+    import paper_2409_08808_gb300 as g
+
+    ctx = g.Context(0)
+    dev = torch.device("cuda", 0)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def problem(prob, allow=False):
+        frac = torch.tensor(prob.frac, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        return g.Problem(ctx, J, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=allow), J, ms
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    oracle.build()
+    # ---- rocksalt 2x2x2, N = 64: 8 chains x 20,000 swaps at kT = 0.05 eV, FP64, parity with the oracle
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    gp, J, jms = problem(prob)
+    start = synth.random_population(prob, 8, synth.SEED_BASE)
+    gp.mc_run(torch.tensor(start, device=dev), 0.05, 2000, 1)
+    chains = torch.tensor(start, device=dev)
+    ms = timed(lambda: gp.mc_run(chains, 0.05, 20000, synth.SEED_BASE))
+    Jo = oracle.ewald_J(prob.lattice, prob.frac, prob.alpha, prob.nimg, prob.kcut)
+    t0 = time.perf_counter()
+    ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.05, 20000, synth.SEED_BASE)
+    cpu_s = time.perf_counter() - t0
+    emit({"workload": "rocksalt 2x2x2 (N=64, 32 cations +1/+3), MC 8 chains x 20,000 swaps, kT=0.05 eV, FP64",
+          "gpu_ms": ms, "trials_per_s": 160000 / (ms / 1e3), "cpu_oracle_s": cpu_s,
+          "cpu_oracle_trials_per_s": 160000 / cpu_s, "cpu_cores": 1,
+          "trajectory_parity": bool(np.array_equal(chains.cpu().numpy(), ref["species"])),
+          "ewald_build_ms": jms})
+
+    # ---- layered R-3m 12x12x1, N = 1296: GA population 1024, 200 generations
+    prob = synth.layered_problem()
+    gp, J, jms = problem(prob)
+    pop0 = gp.random_configs(1024, 3)
+    res = {}
+    for prec in ("f64", "f32", "bf16x3"):
+        pop = pop0.clone()
+        gp.ga_run(pop.clone(), 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
+        box = {}
+        ms = timed(lambda: box.setdefault("E", gp.ga_run(pop, 200, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)))
+        E = box["E"]
+        res[prec] = {"ms": ms, "generations_per_s": 200 / (ms / 1e3), "child_evals_per_s": 1024 * 200 / (ms / 1e3),
+                     "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(gp.score(pop, "f64").min())}
+    work = None
+    Jr = np.random.default_rng(1).standard_normal((prob.N, prob.N))
+    Jr = 0.5 * (Jr + Jr.T)
+    popn = pop0[:256].cpu().numpy()
+    En = oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, popn)
+    t0 = time.perf_counter()
+    kids, _, _ = oracle.ga_generation(prob.site_class, popn, En, 5, 0.1, gen=0, seed=9)
+    oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, kids)
+    cpu_gen = (time.perf_counter() - t0) * 4.0   # population 256 -> 1024 (generation and scoring are linear in P)
+    emit({"workload": "layered R-3m 12x12x1 (N=1296: 432 O fixed, Li/vac 346/86, Ni2/Ni3/Mn4/Co3 108 each), "
+                      "GA population 1024 x 200 generations, elite 20, p_mut 0.1",
+          "forms": res, "cpu_oracle_s_per_generation": cpu_gen, "cpu_oracle_note":
+          "one generation of 256 children timed and scaled x4 (scoring is linear in the population), 1 thread",
+          "ewald_build_ms": jms})
+
+    # ---- uneven batch: 256 rocksalt / spinel-like cells, N in [64, 2048], 512 chains each
+    cells = synth.batch_problems(args.batch_cells)
+    gps, sps, kts = [], [], []
+    tb = 0.0
+    for i, pr in enumerate(cells):
+        gpi, _, bms = problem(pr)
+        tb += bms
+        gps.append(gpi)
+        sps.append(gpi.random_configs(args.batch_chains, 100 + i))
+        kts.append(torch.full((args.batch_chains,), pr.kT, dtype=torch.float64, device=dev))
+    best_cpc, tune_ms = g.batch_mc_autotune(ctx, gps, sps, kts, 256, "f64")
+    steps = args.batch_steps
+    trials = steps * args.batch_chains * len(cells)
+    modes = {}
+    for mode, name in ((0, "per_problem_launches"), (1, "persistent"), (2, "persistent_graph")):
+        cpc = best_cpc if mode else min(best_cpc, 4)
+        g.batch_mc_run(ctx, gps, sps, kts, 64, 7, step0=0, chains_per_cta=cpc, mode=mode)
+        ms = timed(lambda: g.batch_mc_run(ctx, gps, sps, kts, steps, 7, step0=64, chains_per_cta=cpc, mode=mode))
+        modes[name] = {"ms": ms, "trials_per_s": trials / (ms / 1e3), "chains_per_cta": cpc}
+    emit({"workload": f"{len(cells)} rocksalt/spinel-like cells, N log-uniform 64..2048, {args.batch_chains} chains "
+                      f"each, {steps} swaps per chain (kT per cell 0.01..0.2 eV), FP64",
+          "trials": trials, "modes": modes, "autotuned_chains_per_cta": best_cpc, "autotune_probe_ms": tune_ms,
+          "ewald_build_total_ms": tb,
+          "trials_per_chain_in_config": 100000,
+          "extrapolated_s_for_1e5_swaps": modes["persistent_graph"]["ms"] / 1e3 * 100000 / steps})
+    del gps, sps, kts
+
+    # ---- relaxed occupations: bcc 16^3, N = 8192, B = 2048 logits sets, 5 species
+    prob = synth.bcc_relaxed_problem()
+    gp, J, jms = problem(prob, allow=True)
+    B = args.grad_batch
+    L = torch.tensor(synth.random_logits(prob, B, 5), device=dev)
+    gp.energy_grad(L[:2].contiguous(), 0.01, "f64")
+    box = {}
+    ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, 0.01, "f64")))
+    p = torch.softmax(L, dim=-1).contiguous()
+    rms = timed(lambda: gp.round_to_counts(p))
+    emit({"workload": f"bcc 16^3 (N=8192, 5 species), relaxed occupations, B={B} logits sets",
+          "energy_grad_f64_ms": ms, "grad_steps_per_s": 1e3 / ms, "round_to_counts_ms": rms,
+          "ewald_build_ms": jms})
+
+
 def main():
     args = _args()
+    if args.suite:
+        run_suite(args)
+        return
     world, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, world, rank)

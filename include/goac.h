@@ -217,6 +217,17 @@ goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* probs, int32_t
                               double* const* E_dev, double* const* bestE_dev, int32_t chains_per_cta,
                               int32_t mode);
 
+/* Autotuner for goac_batch_mc_run (the batching form's chains-per-CTA): runs *
+ * each candidate 1, 2, 4, 8, 16, 32 that fits in shared memory for          *
+ * probe_steps steps on scratch copies of the chains (the caller's            *
+ * configurations are unchanged) in one persistent launch, times each with    *
+ * CUDA events, and returns the fastest in best_chains_per_cta (and its time   *
+ * in best_ms, nullable).  Synchronises.                                       */
+goac_status goac_batch_mc_autotune(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs,
+                                   int8_t* const* species_dev, const int32_t* chains, const double* const* kT_dev,
+                                   int64_t probe_steps, int32_t precision, int32_t* best_chains_per_cta,
+                                   double* best_ms);
+
 /* ------------------------------------------------------------------------ *
  * Genetic algorithm, one generation (SI, Genetic Algorithm; roulette wheel *
  * selection).  pop_dev P x Nv with energies E_dev (P).  Children 0..e-1 are *
@@ -251,10 +262,24 @@ goac_status goac_ga_run(goac_problem* prob, int8_t* pop_dev, double* E_dev, int3
  *   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks),             *
  *   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)  (0 for masked species).       *
  * E_dev: B doubles; dlogits_dev: B x Nv x S floats (nullable).  precision: *
- * GOAC_PREC_F64 or GOAC_PREC_TF32X2 (J.Q on tcgen05, Q split in TF32 too).  *
+ * GOAC_PREC_F64 (FP64 CUDA-core GEMM) or GOAC_PREC_TF32X2 (J.Q on tcgen05, *
+ * J and the real-valued Q each split in TF32 hi / lo, the products hi.hi,   *
+ * hi.lo and lo.hi accumulated in FP32; Phi kept in FP32).                   *
  * ------------------------------------------------------------------------ */
 goac_status goac_energy_grad(goac_problem* prob, const float* logits_dev, int32_t B, double lambda,
                              int32_t precision, double* E_dev, float* dlogits_dev);
+
+/* Projected descent on the logits (spec differentiation form, used to  *
+ * seed MC / GA populations): n_steps of L -= eta dE/dL with the gradient of  *
+ * goac_energy_grad (softmax keeps p on the simplex), in place on logits_dev. *
+ * dlogits_scratch_dev: caller buffer of B x Nv x S floats.  E_dev: energies   *
+ * after the last step.                                                        */
+goac_status goac_relaxed_descent(goac_problem* prob, float* logits_dev, int32_t B, double lambda, double eta,
+                                 int32_t n_steps, int32_t precision, float* dlogits_scratch_dev, double* E_dev);
+
+/* Relaxed occupations p = softmax of the logits over the species allowed in  *
+ * each site's class (FP64 inside, FP32 out): logits_dev, p_dev B x Nv x S.   */
+goac_status goac_occupations(goac_problem* prob, const float* logits_dev, int32_t B, float* p_dev);
 
 /* Round relaxed occupations p (B x Nv x S float) to valid configurations:    *
  * per class, (site, species) pairs by p descending (ties: lower site, then   *

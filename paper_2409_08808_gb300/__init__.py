@@ -269,6 +269,21 @@ class Problem:
                "goac_energy_grad")
         return E, g
 
+    def relaxed_descent(self, logits: torch.Tensor, lam: float, eta: float, n_steps: int, precision="tf32x2"):
+        """In-place projected descent on `logits` (B x Nv x S float); returns the final energies."""
+        B = logits.shape[0]
+        E = torch.empty(B, dtype=torch.float64, device=self._dev())
+        scratch = torch.empty_like(logits)
+        _check(lib.goac_relaxed_descent(self.handle, _ptr(logits), B, float(lam), float(eta), int(n_steps),
+                                        _prec(precision), _ptr(scratch), _ptr(E)), "goac_relaxed_descent")
+        return E
+
+    def occupations(self, logits: torch.Tensor) -> torch.Tensor:
+        """p = masked softmax of the logits (B x Nv x S float)."""
+        p = torch.empty_like(logits)
+        _check(lib.goac_occupations(self.handle, _ptr(logits), logits.shape[0], _ptr(p)), "goac_occupations")
+        return p
+
     def round_to_counts(self, p: torch.Tensor) -> torch.Tensor:
         B = p.shape[0]
         out = torch.empty((B, self.Nv), dtype=torch.int8, device=self._dev())
@@ -292,6 +307,20 @@ def batch_mc_run(ctx: Context, problems, species, kT, n_steps: int, seed: int, s
     _check(lib.goac_batch_mc_run(ctx.handle, P, n, SP, CH, KT, int(n_steps), int(seed), int(step0), _prec(precision),
                                  EE, BE, int(chains_per_cta), int(mode)), "goac_batch_mc_run")
     return E, bE
+
+
+def batch_mc_autotune(ctx: Context, problems, species, kT, probe_steps: int = 256, precision="f64"):
+    """Fastest chains-per-CTA for batch_mc_run on these problems (goac_batch_mc_autotune)."""
+    n = len(problems)
+    P = (C.c_void_p * n)(*[p._h.value for p in problems])
+    SP = (C.c_void_p * n)(*[s.data_ptr() for s in species])
+    CH = (C.c_int32 * n)(*[s.shape[0] for s in species])
+    KT = (C.c_void_p * n)(*[t.data_ptr() for t in kT])
+    best = C.c_int32()
+    ms = C.c_double()
+    _check(lib.goac_batch_mc_autotune(ctx.handle, P, n, SP, CH, KT, int(probe_steps), _prec(precision),
+                                      C.byref(best), C.byref(ms)), "goac_batch_mc_autotune")
+    return int(best.value), float(ms.value)
 
 
 class RelaxedEnergy(torch.autograd.Function):

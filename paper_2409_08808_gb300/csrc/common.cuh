@@ -99,7 +99,8 @@ struct goac_problem {
     uint32_t* wprefix_dev = nullptr;
     // lazily built operand copies for the tensor-core and FP32 paths
     __nv_bfloat16* J_bf16 = nullptr;   // [3][Nv_pad][Nv_pad]
-    float* J_tf32 = nullptr;           // [2][Nv_pad][Nv_pad] (hi, lo)
+    float* J_tf32 = nullptr;           // [2][Nv_pad][Nv_pad] (hi, lo) of the symmetric operand
+    float* J_tf32_full = nullptr;      // [2][Nv_pad][Nv_pad] (hi, lo) of J_vv itself
     float* J_f32 = nullptr;            // Nv_pad x Nv_pad (MC / GA FP32 variant)
     float* diag_f32 = nullptr;
     // scoring scratch
@@ -371,4 +372,5 @@ goac_status score_f64(goac_problem* p, const int8_t* species, int B, double* E_o
 goac_status score_f32(goac_problem* p, const int8_t* species, int B, double* E_out, float* phi_out);
 goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precision, double* E_out);
 goac_status prepare_f32(goac_problem* p);
+goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi);
 }  // namespace goac

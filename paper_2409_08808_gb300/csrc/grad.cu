@@ -8,10 +8,13 @@
 //   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks)
 //   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)
 //
-// (2 J q)_v = 2 (J_vv q_v + phi_fix)_v.  The contraction J_vv Q runs as an
-// FP64 tiled GEMM on the CUDA cores; the elementwise chain rule is fused into
-// one kernel per configuration.
+// (2 J q)_v = 2 (J_vv q_v + phi_fix)_v.  The contraction J_vv Q runs either as
+// an FP64 tiled GEMM on the CUDA cores or on the tcgen05 tensor cores with both
+// J and the real-valued Q split into TF32 hi / lo (three products); the
+// elementwise chain rule is fused into one kernel per configuration.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -110,8 +113,11 @@ __global__ void __launch_bounds__(256) k_phi_real(const double* __restrict__ J, 
 }
 
 // One block per configuration: energy (with the counts penalty) and dE/dL.
+// Phi row b starts at Phi + b * phi_ld (FP64 from the CUDA-core GEMM, FP32
+// from the tensor-core path).
+template <typename PT>
 __global__ void k_grad_finish(const double* __restrict__ p, const double* __restrict__ q,
-                              const double* __restrict__ Phi, const double* __restrict__ phifix,
+                              const PT* __restrict__ Phi, long phi_ld, const double* __restrict__ phifix,
                               const double* __restrict__ colsum, const int32_t* __restrict__ vclass,
                               const int32_t* __restrict__ counts, const double* __restrict__ z, int Nv, int S,
                               int ncls, double lambda, double E_const, double* __restrict__ E,
@@ -123,7 +129,7 @@ __global__ void k_grad_finish(const double* __restrict__ p, const double* __rest
     double acc = 0.0;
     for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
         const long t = (long)b * Nv + v;
-        const double jq = Phi[t] + phifix[v];     // (J q)_v over all sites
+        const double jq = (double)Phi[(long)b * phi_ld + v] + phifix[v];     // (J q)_v over all sites
         acc += q[t] * (jq + phifix[v]);
         if (dlogits) {
             const int k = vclass[v];
@@ -153,6 +159,50 @@ __global__ void k_grad_finish(const double* __restrict__ p, const double* __rest
                 }
         E[b] = red[0] + E_const + lambda * pen;
     }
+}
+
+// q (B x Nv, FP64) -> TF32 hi / lo planes [2][Bpad][ld] (FP32 storage), zero padded.
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_split_q(const double* __restrict__ q, int B, int Nv, int Bpad, int ld, float* __restrict__ qt2)
+{
+    const long plane = (long)Bpad * ld;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ld), v = (int)(e % ld);
+        const double x = (b < B && v < Nv) ? q[(long)b * Nv + v] : 0.0;
+        const float hi = tf32_rna((float)x);
+        qt2[e] = hi;
+        qt2[plane + e] = tf32_rna((float)(x - (double)hi));
+    }
+}
+
+// p = softmax of the logits over the species allowed in the site's class, FP32 out.
+__global__ void k_softmax_f32(const float* __restrict__ logits, long BN, int Nv, int S,
+                              const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
+                              float* __restrict__ p)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    const int k = vclass[(int)(t % Nv)];
+    const float* L = logits + t * S;
+    double m = -INFINITY;
+    for (int s = 0; s < S; ++s)
+        if (counts[k * S + s] > 0 && (double)L[s] > m) m = (double)L[s];
+    double den = 0.0;
+    for (int s = 0; s < S; ++s) den += counts[k * S + s] > 0 ? exp((double)L[s] - m) : 0.0;
+    for (int s = 0; s < S; ++s) p[t * S + s] = counts[k * S + s] > 0 ? (float)(exp((double)L[s] - m) / den) : 0.0f;
+}
+
+// L -= eta * dL (FP32, in place).
+__global__ void k_descent_step(float* __restrict__ L, const float* __restrict__ dL, long n, float eta)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        L[e] = L[e] - eta * dL[e];
 }
 
 // ---- rounding to counts ------------------------------------------------------
@@ -251,25 +301,45 @@ extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev
 {
     if (!p || !logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
     if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0");
-    if (precision != GOAC_PREC_F64) return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: only GOAC_PREC_F64");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_TF32X2)
+        return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: precision must be F64 or TF32X2");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
-    const int Nv = p->Nv, S = p->S, ncls = p->ncls;
+    const int Nv = p->Nv, S = p->S, ncls = p->ncls, ld = p->Nv_pad;
+    const bool tc = precision == GOAC_PREC_TF32X2;
+    const int Bpad = ((B + 127) / 128) * 128;
     const long BN = (long)B * Nv;
-    const size_t need = sizeof(double) * ((size_t)BN * S + 2 * (size_t)BN + (size_t)B * ncls * S) + 1024;
+    size_t need = sizeof(double) * ((size_t)BN * S + (size_t)BN + (size_t)B * ncls * S) + 2048;
+    need += tc ? sizeof(float) * (3 * (size_t)Bpad * ld) : sizeof(double) * (size_t)BN;
     goac_status rc = goac::ensure(p->grad_tmp, need);
     if (rc) return rc;
     double* P_ = (double*)p->grad_tmp.ptr;
     double* Q = P_ + BN * S;
-    double* Phi = Q + BN;
-    double* colsum = Phi + BN;
+    double* colsum = Q + BN;
+    void* phi_base = (void*)(((uintptr_t)(colsum + (long)B * ncls * S) + 255) & ~(uintptr_t)255);   // TMA: 16-byte aligned
     cudaStream_t st = p->ctx->stream;
-    goac::launch(k_softmax, (int)((BN + 255) / 256), 256, 0, st, logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev, p->z_dev,
-                                                       P_, Q);
+    goac::launch(k_softmax, (int)((BN + 255) / 256), 256, 0, st, logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev,
+                 p->z_dev, P_, Q);
     goac::launch(k_colsum, B * ncls, 256, 0, st, P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
-    dim3 grid((B + GM - 1) / GM, (Nv + GM - 1) / GM);
-    goac::launch(k_phi_real, grid, 256, 0, st, p->J_vv, p->Nv_pad, Nv, Q, B, Phi);
-    goac::launch(k_grad_finish, B, 256, 0, st, P_, Q, Phi, p->phifix, colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
-                                     ncls, lambda, p->E_const, E_dev, dlogits_dev);
+    if (tc) {
+        float* qt2 = (float*)phi_base;
+        float* Phi = qt2 + 2 * (size_t)Bpad * ld;
+        const long plane = (long)Bpad * ld;
+        goac::launch(k_split_q, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, (const double*)Q, B,
+                     Nv, Bpad, ld, qt2);
+        GOAC_LAUNCH_CHECK("k_split_q");
+        rc = goac::phi_tc(p, qt2, Bpad, Phi);
+        if (rc) return rc;
+        goac::launch(k_grad_finish<float>, B, 256, 0, st, (const double*)P_, (const double*)Q, (const float*)Phi,
+                     (long)ld, (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev,
+                     Nv, S, ncls, lambda, p->E_const, E_dev, dlogits_dev);
+    } else {
+        double* Phi = (double*)phi_base;
+        dim3 grid((B + GM - 1) / GM, (Nv + GM - 1) / GM);
+        goac::launch(k_phi_real, grid, 256, 0, st, (const double*)p->J_vv, ld, Nv, (const double*)Q, B, Phi);
+        goac::launch(k_grad_finish<double>, B, 256, 0, st, (const double*)P_, (const double*)Q, (const double*)Phi,
+                     (long)Nv, (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev,
+                     p->z_dev, Nv, S, ncls, lambda, p->E_const, E_dev, dlogits_dev);
+    }
     GOAC_LAUNCH_CHECK("goac_energy_grad");
     return GOAC_OK;
 }
@@ -312,5 +382,36 @@ extern "C" goac_status goac_round_to_counts(goac_problem* p, const float* p_dev,
     goac::launch(k_round_greedy, (int)((nt + 127) / 128), 128, 0, st, keys, B, p->Nv, S, ncls, p->cls_start_dev, p->counts_dev,
                                                             d_off, per_b, species_dev, p->ctx->d_err);
     GOAC_LAUNCH_CHECK("goac_round_to_counts");
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_relaxed_descent(goac_problem* p, float* logits_dev, int32_t B, double lambda, double eta,
+                                            int32_t n_steps, int32_t precision, float* dlogits_scratch_dev,
+                                            double* E_dev)
+{
+    if (!p || !logits_dev || !dlogits_scratch_dev || !E_dev || n_steps < 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_relaxed_descent: bad argument");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const long n = (long)B * p->Nv * p->S;
+    const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
+    for (int it = 0; it < n_steps; ++it) {
+        goac_status rc = goac_energy_grad(p, logits_dev, B, lambda, precision, E_dev, dlogits_scratch_dev);
+        if (rc) return rc;
+        goac::launch(k_descent_step, blocks, 256, 0, p->ctx->stream, logits_dev, (const float*)dlogits_scratch_dev, n,
+                     (float)eta);
+        GOAC_LAUNCH_CHECK("k_descent_step");
+    }
+    return goac_energy_grad(p, logits_dev, B, lambda, precision, E_dev, nullptr);
+}
+
+extern "C" goac_status goac_occupations(goac_problem* p, const float* logits_dev, int32_t B, float* p_dev)
+{
+    if (!p || !logits_dev || !p_dev || B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_occupations: bad argument");
+    if (B == 0) return GOAC_OK;
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const long BN = (long)B * p->Nv;
+    goac::launch(k_softmax_f32, (int)((BN + 255) / 256), 256, 0, p->ctx->stream, logits_dev, BN, p->Nv, p->S,
+                 (const int32_t*)p->vclass_dev, (const int32_t*)p->counts_dev, p_dev);
+    GOAC_LAUNCH_CHECK("k_softmax_f32");
     return GOAC_OK;
 }

@@ -20,6 +20,8 @@
 // definition step for step.  The FP32 path keeps J rows and phi in FP32.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -72,44 +74,71 @@ __device__ __forceinline__ double rd_mul<double>(double a, double b) { return __
 template <>
 __device__ __forceinline__ float rd_mul<float>(float a, float b) { return __fmul_rn(a, b); }
 
-// Run one chain with one warp.  sp / phi point to this warp's shared-memory slots.
-template <typename R>
-__device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_t* sp, R* phi, int* err)
+// Barrier over the W warps of one chain group (named barrier `id`, 1..15).
+template <int W>
+__device__ __forceinline__ void chain_sync(int id)
+{
+    if (W == 1) __syncwarp();
+    else goacd::named_bar_sync(id, 32 * W);
+}
+
+// Run one chain with a group of W warps.  sp / phi point to the group's
+// shared-memory slot.  All W warps draw and evaluate the same proposals (the
+// decisions are identical), each updates its own slice of phi on acceptance,
+// and the group synchronises after every acceptance.  phi_init / E_init: the
+// chain's potential (J_vv q + phi_fix) and energy computed beforehand; when
+// null (W == 1 only) the warp builds them itself.
+template <typename R, int W>
+__device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_t* sp, R* phi,
+                          const R* __restrict__ phi_init, const double* __restrict__ E_init, int bar_id)
 {
     const int lane = threadIdx.x & 31;
+    const int ct = threadIdx.x % (32 * W);     // thread index within the chain group
+    const int cw = ct >> 5;                    // warp index within the chain group
     const int Nv = P.Nv, ld = P.ld;
     const R* J = (const R*)P.J;
     const R* diag = (const R*)P.diag;
     int8_t* gsp = P.species + (long)chain * Nv;
 
-    // load species, build phi = J_vv q + phi_fix (rows of J read coalesced: J symmetric)
-    for (int w = lane; w < Nv; w += 32) {
-        sp[w] = gsp[w];
-        phi[w] = (R)0;
+    double E;
+    if (phi_init) {
+        for (int w = ct; w < Nv; w += 32 * W) {
+            sp[w] = gsp[w];
+            phi[w] = phi_init[(long)chain * Nv + w];
+        }
+        E = E_init[chain];
+        chain_sync<W>(bar_id);
+    } else {
+        // one warp: phi = J_vv q + phi_fix (rows of J read coalesced: J symmetric)
+        for (int w = lane; w < Nv; w += 32) {
+            sp[w] = gsp[w];
+            phi[w] = (R)0;
+        }
+        __syncwarp();
+        for (int w = 0; w < Nv; ++w) {
+            const R qw = (R)P.z[sp[w]];
+            if (qw == (R)0) continue;
+            const R* row = J + (long)w * ld;
+            for (int v = lane; v < Nv; v += 32) phi[v] = fma(row[v], qw, phi[v]);
+        }
+        __syncwarp();
+        double e_part = 0.0;
+        for (int v = lane; v < Nv; v += 32) {
+            const double pf = P.phifix[v];
+            phi[v] = (R)((double)phi[v] + pf);
+            e_part += P.z[sp[v]] * ((double)phi[v] + pf);
+        }
+        for (int o = 16; o; o >>= 1) e_part += __shfl_xor_sync(0xffffffffu, e_part, o);
+        E = e_part + P.E_const;
+        __syncwarp();
     }
-    __syncwarp();
-    for (int w = 0; w < Nv; ++w) {
-        const R qw = (R)P.z[sp[w]];
-        if (qw == (R)0) continue;
-        const R* row = J + (long)w * ld;
-        for (int v = lane; v < Nv; v += 32) phi[v] = fma(row[v], qw, phi[v]);
-    }
-    __syncwarp();
-    double e_part = 0.0;
-    for (int v = lane; v < Nv; v += 32) {
-        const double pf = P.phifix[v];
-        phi[v] = (R)((double)phi[v] + pf);
-        e_part += P.z[sp[v]] * ((double)phi[v] + pf);
-    }
-    for (int o = 16; o; o >>= 1) e_part += __shfl_xor_sync(0xffffffffu, e_part, o);
-    double E = e_part + P.E_const;
     double best = E;
     long nacc = 0;
     if (P.best_species)
-        for (int w = lane; w < Nv; w += 32) P.best_species[(long)chain * Nv + w] = sp[w];
-    __syncwarp();
+        for (int w = ct; w < Nv; w += 32 * W) P.best_species[(long)chain * Nv + w] = sp[w];
 
     const double kT = P.kT[chain];
+    const float kTf = (float)kT;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
         const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
@@ -153,7 +182,8 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                     dE = rd_add<R>(rd_mul<R>(rd_mul<R>((R)2, d), rd_sub<R>(phi[va], phi[vb])),
                                    rd_mul<R>(rd_mul<R>(d, d), jsum));
                     if ((double)dE <= kDeZero) acc = true;
-                    else if (kT > 0.0) acc = u < exp(-(double)dE / kT);
+                    else if (sizeof(R) == 8) acc = kT > 0.0 && u < exp(-(double)dE / kT);
+                    else acc = kTf > 0.0f && (float)u < expf(-(float)dE / kTf);
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, acc);
@@ -163,8 +193,8 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             const int cb = __shfl_sync(0xffffffffu, vb, kl);
             const R cd = __shfl_sync(0xffffffffu, d, kl);
             const R cdE = __shfl_sync(0xffffffffu, dE, kl);
-            __syncwarp();
-            if (lane == 0) {
+            chain_sync<W>(bar_id);                 // every warp has read the state it evaluated
+            if (ct == 0) {
                 const int8_t ta = sp[ca];
                 sp[ca] = sp[cb];
                 sp[cb] = ta;
@@ -172,41 +202,42 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             if (cd != (R)0) {
                 const R* __restrict__ ra = J + (long)ca * ld;
                 const R* __restrict__ rb = J + (long)cb * ld;
-                // 8 loads of each row in flight per lane before the updates
-                for (int w0 = lane; w0 < Nv; w0 += 32 * 8) {
+                // this warp's slice, 8 loads of each row in flight per lane
+                for (int w0 = cw * 32 + lane; w0 < Nv; w0 += 32 * W * 8) {
                     R xa[8], xb[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int w = w0 + 32 * u;
-                        xa[u] = w < Nv ? ra[w] : (R)0;
-                        xb[u] = w < Nv ? rb[w] : (R)0;
+                    for (int uu = 0; uu < 8; ++uu) {
+                        const int w = w0 + 32 * W * uu;
+                        xa[uu] = w < Nv ? ra[w] : (R)0;
+                        xb[uu] = w < Nv ? rb[w] : (R)0;
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int w = w0 + 32 * u;
-                        if (w < Nv) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(xa[u], xb[u])));
+                    for (int uu = 0; uu < 8; ++uu) {
+                        const int w = w0 + 32 * W * uu;
+                        if (w < Nv) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(xa[uu], xb[uu])));
                     }
                 }
             }
-            __syncwarp();
+            chain_sync<W>(bar_id);
             E = E + (double)cdE;
             ++nacc;
             if (E < best) {
                 best = E;
-                if (P.best_species)
-                    for (int w = lane; w < Nv; w += 32) P.best_species[(long)chain * Nv + w] = sp[w];
+                if (P.best_species) {
+                    for (int w = ct; w < Nv; w += 32 * W) P.best_species[(long)chain * Nv + w] = sp[w];
+                    chain_sync<W>(bar_id);
+                }
             }
             pending &= ~((2u << kl) - 1u);
         }
     }
-    __syncwarp();
-    for (int w = lane; w < Nv; w += 32) gsp[w] = sp[w];
-    if (lane == 0) {
+    chain_sync<W>(bar_id);
+    for (int w = ct; w < Nv; w += 32 * W) gsp[w] = sp[w];
+    if (ct == 0) {
         P.E_out[chain] = E;
         P.bestE[chain] = best;
         if (P.n_accept) P.n_accept[chain] = nacc;
     }
-    (void)err;
 }
 
 __host__ __device__ inline size_t warp_slot_bytes(int Nv, int rbytes)
@@ -216,9 +247,29 @@ __host__ __device__ inline size_t warp_slot_bytes(int Nv, int rbytes)
     return a + b;
 }
 
-// Single problem: one warp per chain.
+// Single problem: W warps per chain, chains_per_cta chains per CTA, phi / E
+// initialised beforehand by the scoring GEMM.
+template <typename R, int W>
+__global__ void k_mc(McProb P, McScalars sc, const R* __restrict__ phi_init, const double* __restrict__ E_init,
+                     int* err)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int slot_i = threadIdx.x / (32 * W);
+    const int chain = blockIdx.x * (blockDim.x / (32 * W)) + slot_i;
+    if (chain >= P.chains) return;     // whole chain groups leave together
+    const size_t slot = warp_slot_bytes(P.Nv, sizeof(R));
+    uint8_t* base = smem + slot * slot_i;
+    R* phi = (R*)base;
+    int8_t* sp = (int8_t*)(base + (((size_t)P.Nv * sizeof(R) + 15) & ~(size_t)15));
+    run_chain<R, W>(P, chain, sc, sp, phi, phi_init, E_init, 1 + slot_i);
+    (void)err;
+}
+
+// One warp per chain with the potential built in the kernel (the per-problem
+// launches of the batched baseline use the same chain code as the persistent
+// batched kernel).
 template <typename R>
-__global__ void k_mc(McProb P, McScalars sc, int* err)
+__global__ void k_mc_single(McProb P, McScalars sc, int* err)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int wib = threadIdx.x >> 5;
@@ -228,7 +279,8 @@ __global__ void k_mc(McProb P, McScalars sc, int* err)
     uint8_t* base = smem + slot * wib;
     R* phi = (R*)base;
     int8_t* sp = (int8_t*)(base + (((size_t)P.Nv * sizeof(R) + 15) & ~(size_t)15));
-    run_chain<R>(P, chain, sc, sp, phi, err);
+    run_chain<R, 1>(P, chain, sc, sp, phi, nullptr, nullptr, 0);
+    (void)err;
 }
 
 // Batch of problems: persistent warps take (problem, chain) items from a queue.
@@ -251,7 +303,7 @@ __global__ void k_mc_batch(const McProb* __restrict__ probs, const int2* __restr
         const McProb P = probs[pc.x];
         R* phi = (R*)base;
         int8_t* sp = (int8_t*)(base + (((size_t)P.Nv * sizeof(R) + 15) & ~(size_t)15));
-        run_chain<R>(P, pc.y, sc, sp, phi, err);
+        run_chain<R, 1>(P, pc.y, sc, sp, phi, nullptr, nullptr, 0);
         __syncwarp();
     }
 }
@@ -310,22 +362,42 @@ extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t
     const size_t slot = warp_slot_bytes(p->Nv, f32 ? 4 : 8);
     if (slot > kSmemBudget)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: Nv too large for a shared-memory chain");
-    int wpb = (int)(kSmemBudget / slot);
-    if (wpb > 8) wpb = 8;
-    if (wpb > C) wpb = C;
-    if (wpb < 1) wpb = 1;
-    const size_t smem = slot * wpb;
+    // potentials and energies of all chains by the tiled scoring GEMM
+    const size_t rb = f32 ? 4 : 8;
+    goac_status rc = goac::ensure(p->phi, rb * (size_t)C * p->Nv + sizeof(double) * (size_t)C + 256);
+    if (rc) return rc;
+    void* phi0 = p->phi.ptr;
+    double* E0 = (double*)((char*)p->phi.ptr + ((rb * (size_t)C * p->Nv + 255) & ~(size_t)255));
+    rc = f32 ? goac::score_f32(p, species_dev, C, E0, (float*)phi0) : goac::score_f64(p, species_dev, C, E0, (double*)phi0);
+    if (rc) return rc;
+    // warps per chain: more warps share the O(Nv) update of a long chain
+    const int W = p->Nv >= 3072 ? 4 : (p->Nv >= 1536 ? 2 : 1);
+    int cpc = (int)(kSmemBudget / slot);
+    cpc = std::min(cpc, 1024 / (32 * W));
+    cpc = std::min(cpc, 15);
+    cpc = std::min(cpc, C);
+    if (cpc < 1) cpc = 1;
+    const size_t smem = slot * cpc;
     McProb d = make_desc(p, f32, species_dev, C, kT_dev, E_dev, bestE_dev, best_species_dev, n_accept_dev, seed);
     McScalars sc{n_steps, step0};
-    const int blocks = (C + wpb - 1) / wpb;
+    const int blocks = (C + cpc - 1) / cpc;
     goac::KTimer kt(p->ctx, goac::KID_MC, p->ctx->stream);
+#define GOAC_MC_LAUNCH(RT, WW)                                                                                  \
+    do {                                                                                                        \
+        GOAC_CUDA(cudaFuncSetAttribute(k_mc<RT, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));  \
+        goac::launch(k_mc<RT, WW>, blocks, 32 * WW * cpc, smem, p->ctx->stream, d, sc, (const RT*)phi0,           \
+                     (const double*)E0, p->ctx->d_err);                                                         \
+    } while (0)
     if (f32) {
-        GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        goac::launch(k_mc<float>, blocks, 32 * wpb, smem, p->ctx->stream, d, sc, p->ctx->d_err);
+        if (W == 4) GOAC_MC_LAUNCH(float, 4);
+        else if (W == 2) GOAC_MC_LAUNCH(float, 2);
+        else GOAC_MC_LAUNCH(float, 1);
     } else {
-        GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        goac::launch(k_mc<double>, blocks, 32 * wpb, smem, p->ctx->stream, d, sc, p->ctx->d_err);
+        if (W == 4) GOAC_MC_LAUNCH(double, 4);
+        else if (W == 2) GOAC_MC_LAUNCH(double, 2);
+        else GOAC_MC_LAUNCH(double, 1);
     }
+#undef GOAC_MC_LAUNCH
     GOAC_LAUNCH_CHECK("k_mc");
     return GOAC_OK;
 }
@@ -392,11 +464,13 @@ extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* pro
             const size_t smem = s1 * wpb;
             const int blocks = (descs[i].chains + wpb - 1) / wpb;
             if (f32) {
-                GOAC_CUDA(cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-                goac::launch(k_mc<float>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
+                GOAC_CUDA(cudaFuncSetAttribute(k_mc_single<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kSmemBudget));
+                goac::launch(k_mc_single<float>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
             } else {
-                GOAC_CUDA(cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
-                goac::launch(k_mc<double>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
+                GOAC_CUDA(cudaFuncSetAttribute(k_mc_single<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kSmemBudget));
+                goac::launch(k_mc_single<double>, blocks, 32 * wpb, smem, st, descs[i], sc, ctx->d_err);
             }
             GOAC_LAUNCH_CHECK("k_mc (per problem)");
         }
@@ -477,5 +551,84 @@ extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* pro
         ctx->batch_graph_key = key;
     }
     GOAC_CUDA(cudaGraphLaunch(ctx->batch_graph, st));
+    return GOAC_OK;
+}
+
+// Autotuner for the persistent batched launch: runs every chains-per-CTA
+// candidate that fits in shared memory for `probe_steps` steps on scratch
+// copies of the chains (the caller's configurations are not touched), times
+// each with CUDA events on the context stream, and returns the fastest.
+extern "C" goac_status goac_batch_mc_autotune(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs,
+                                              int8_t* const* species_dev, const int32_t* chains,
+                                              const double* const* kT_dev, int64_t probe_steps, int32_t precision,
+                                              int32_t* best_chains_per_cta, double* best_ms)
+{
+    if (!ctx || !probs || n_probs <= 0 || !species_dev || !chains || !kT_dev || !best_chains_per_cta || probe_steps <= 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_autotune: bad argument");
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    size_t sp_bytes = 0, e_count = 0;
+    int max_nv = 0;
+    for (int i = 0; i < n_probs; ++i) {
+        if (!probs[i] || chains[i] < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_autotune: bad problem");
+        sp_bytes += (((size_t)chains[i] * probs[i]->Nv) + 255) & ~(size_t)255;
+        e_count += chains[i];
+        max_nv = std::max(max_nv, probs[i]->Nv);
+    }
+    DevBuf scratch;
+    goac_status rc = goac::ensure(scratch, sp_bytes + 2 * sizeof(double) * e_count + 1024);
+    if (rc) return rc;
+    std::vector<int8_t*> sp(n_probs);
+    std::vector<double*> E(n_probs), bE(n_probs);
+    {
+        char* cur = (char*)scratch.ptr;
+        for (int i = 0; i < n_probs; ++i) {
+            sp[i] = (int8_t*)cur;
+            cur += (((size_t)chains[i] * probs[i]->Nv) + 255) & ~(size_t)255;
+        }
+        double* d = (double*)cur;
+        for (int i = 0; i < n_probs; ++i) {
+            E[i] = d;
+            d += chains[i];
+            bE[i] = d;
+            d += chains[i];
+        }
+    }
+    const int rb = precision == GOAC_PREC_F32 ? 4 : 8;
+    const size_t slot = warp_slot_bytes(max_nv, rb);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int best = -1;
+    float best_t = 0.0f;
+    const int cands[] = {1, 2, 4, 8, 16, 32};
+    for (int cpc : cands) {
+        if (slot * cpc > kSmemBudget) break;
+        for (int i = 0; i < n_probs; ++i)
+            GOAC_CUDA(cudaMemcpyAsync(sp[i], species_dev[i], (size_t)chains[i] * probs[i]->Nv,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+        rc = goac_batch_mc_run(ctx, probs, n_probs, sp.data(), chains, kT_dev, probe_steps, 12345u, 0, precision,
+                               E.data(), bE.data(), cpc, 1);
+        if (rc) break;
+        cudaEventRecord(a, ctx->stream);
+        rc = goac_batch_mc_run(ctx, probs, n_probs, sp.data(), chains, kT_dev, probe_steps, 12345u,
+                               (uint64_t)probe_steps, precision, E.data(), bE.data(), cpc, 1);
+        cudaEventRecord(b, ctx->stream);
+        if (rc) break;
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best < 0 || ms < best_t) {
+            best = cpc;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(scratch.ptr);
+    if (rc) return rc;
+    if (best < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_autotune: no candidate fits");
+    *best_chains_per_cta = best;
+    if (best_ms) *best_ms = best_t;
     return GOAC_OK;
 }

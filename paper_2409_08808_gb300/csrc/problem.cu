@@ -642,6 +642,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->wprefix_dev);
     cudaFree(p->J_bf16);
     cudaFree(p->J_tf32);
+    cudaFree(p->J_tf32_full);
     cudaFree(p->J_f32);
     cudaFree(p->diag_f32);
     free_buf(p->qt);

@@ -241,6 +241,147 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+__device__ __forceinline__ float to_tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Phi^T = Q^T J (FP32 out) with real Q, TF32 split of both operands:
+// Phi = J_hi Q_hi + J_hi Q_lo + J_lo Q_hi (the lo*lo product is dropped).
+// One CTA per 128 (sites) x 128 (configurations) tile, 128 threads: warp 0
+// lane 0 TMA producer, warp 1 lane 0 MMA issuer (kind::tf32, M = N = 128,
+// K = 8), warp 2 TMEM owner, then 4 warps write their 32 TMEM lanes (sites)
+// to Phi[b][v] (coalesced over sites).  Used by the relaxed-occupation
+// gradient, where q = p . z is not integer.
+constexpr int PT_N = 128;
+constexpr int PT_A = TC_M * ROW_BYTES;        // 16 KB
+constexpr int PT_B = PT_N * ROW_BYTES;        // 16 KB
+constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 64 KB
+constexpr int PT_STAGES = 3;
+constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
+
+__global__ void __launch_bounds__(128, 1)
+    k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nkb, int ld,
+             int Bpad, float* __restrict__ Phi, int* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + PT_STAGES * PT_STAGE);
+    uint64_t* empty = full + PT_STAGES;
+    uint64_t* done = empty + PT_STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * PT_N;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PT_STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        goacd::mbar_init(done, 1);
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc(tmem_slot, PT_N);
+        goacd::tmem_relinquish();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % PT_STAGES;
+                const uint32_t use = (uint32_t)(kb / PT_STAGES);
+                if (kb >= PT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, kb);
+                    break;
+                }
+                if (*abort_flag) break;
+                uint8_t* st = smem + s * PT_STAGE;
+                goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
+                goacd::tma_load_2d(st, &tmA, &full[s], kb * 32, m0);
+                goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * 32, ld + m0);
+                goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * 32, n0);
+                goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * 32, Bpad + n0);
+                issued = kb + 1;
+            }
+            if (*abort_flag)
+                for (int kb = issued - PT_STAGES < 0 ? 0 : issued - PT_STAGES; kb < issued; ++kb)
+                    if (!goacd::mbar_wait_bounded(&full[kb % PT_STAGES], (uint32_t)(kb / PT_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, kb);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = goacd::idesc_f32acc(2u, TC_M, PT_N);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % PT_STAGES;
+                const uint32_t use = (uint32_t)(kb / PT_STAGES);
+                if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, kb);
+                    break;
+                }
+                if (*abort_flag) break;
+                goacd::tc_fence_after();
+                const uint32_t a_hi = goacd::smem_u32(smem + s * PT_STAGE);
+                const uint32_t a_lo = a_hi + PT_A;
+                const uint32_t b_hi = a_hi + 2 * PT_A;
+                const uint32_t b_lo = b_hi + PT_B;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t off = kk * 32;
+                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_hi + off), idesc,
+                                    (kb | kk) != 0);
+                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_lo + off), idesc, 1u);
+                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_lo + off), goacd::sdesc_k128(b_hi + off), idesc, 1u);
+                }
+                goacd::mma_commit(&empty[s]);
+            }
+            goacd::mma_commit(done);
+        }
+        __syncwarp();
+    }
+    const bool ok = __syncthreads_and(goacd::mbar_wait_bounded(done, 0, WAIT_LIMIT) && !*abort_flag);
+    if (!ok && threadIdx.x == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, 0);
+    goacd::tc_fence_after();
+    if (ok) {
+        const int v = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < PT_N / 32; ++c) {
+            uint32_t r[32];
+            goacd::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+            goacd::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]);
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc(tmem, PT_N);
+    }
+}
+
+// Full (not symmetric) J split in TF32 hi / lo for the Phi-output path.
+__global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* __restrict__ out)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const double x = J[e];
+        const float hi = to_tf32_rna((float)x);
+        out[e] = hi;
+        out[n + e] = to_tf32_rna((float)(x - (double)hi));
+    }
+}
+
 // Symmetric operand: J'_ij = J_ij on diagonal 128-blocks, 2 J_ij above them,
 // 0 below, so that q^T J q = sum over the upper block triangle of q_I^T J'_IJ q_J.
 __device__ __forceinline__ double sym_upper(const double* J, long e, int ld)
@@ -491,6 +632,35 @@ goac_status prepare_f32(goac_problem* p)
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
     goac::launch(k_copy_f32, blocks, 256, 0, p->ctx->stream, p->J_vv, n, p->J_f32, p->diag, p->Nv, p->diag_f32);
     GOAC_LAUNCH_CHECK("k_copy_f32");
+    return GOAC_OK;
+}
+
+// Phi[b][v] (FP32, Bpad x Nv_pad) = sum_w J_vv[v][w] q[b][w] for real q given as
+// TF32 hi / lo planes qt2 = [2][Bpad][Nv_pad] (FP32 storage), on tcgen05.
+goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
+{
+    const int ld = p->Nv_pad;
+    const long n = (long)ld * ld;
+    cudaStream_t st = p->ctx->stream;
+    if (!p->J_tf32_full) {
+        GOAC_CUDA(cudaMalloc(&p->J_tf32_full, sizeof(float) * 2 * (size_t)n));
+        const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
+        goac::launch(k_split_tf32_full, blocks, 256, 0, st, (const double*)p->J_vv, n, p->J_tf32_full);
+        GOAC_LAUNCH_CHECK("k_split_tf32_full");
+    }
+    CUtensorMap ma, mb;
+    goac_status rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M);
+    if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N);
+    if (rc) return rc;
+    static bool attr = false;
+    if (!attr) {
+        GOAC_CUDA(cudaFuncSetAttribute(k_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM));
+        attr = true;
+    }
+    dim3 grid(Bpad / PT_N, ld / TC_M);
+    KTimer kt(p->ctx, KID_SCORE_TC, st);
+    goac::launch(k_phi_tc, grid, 128, PT_SMEM, st, ma, mb, ld / 32, ld, Bpad, Phi, p->ctx->d_err);
+    GOAC_LAUNCH_CHECK("k_phi_tc");
     return GOAC_OK;
 }
 

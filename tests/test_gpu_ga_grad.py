@@ -113,6 +113,40 @@ def test_energy_grad_parity(ctx, which, B):
         assert np.max(np.abs(dL[b] - go)) <= 1e-6 * scale + 1e-30
 
 
+@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5)])
+def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
+    """J.Q on tcgen05 with J and the real Q split in TF32 hi/lo: within the
+    deterministic bound of the form.  Per site, |dPhi_v| <= (gamma_K + 2^-20)
+    sum_w |J_vw q_w| (K = 3 Nv products accumulated in FP32; the three kept
+    products miss at most 2^-20 relative), so |dE| <= sum_v |q_v| that bound
+    and |d(dE/dL_vs)| <= 4 max|z| p_vs that bound (+ FP32 output rounding)."""
+    import paper_2409_08808_gb300 as g
+    prob = {"layered": lambda: synth.layered_problem(reps=(2, 1, 1)),
+            "bcc": lambda: synth.bcc_relaxed_problem(n_side=4)}[which]()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
+    L = synth.random_logits(prob, B, 13)
+    lam = 0.05
+    E, dL = gp.energy_grad(torch.tensor(L, device="cuda"), lam, "tf32x2")
+    E, dL = E.cpu().numpy(), dL.cpu().numpy()
+    K = 3 * gp.Nv
+    eps = K * 2.0 ** -24 + 2.0 ** -20
+    vidx = np.nonzero(prob.site_class >= 0)[0]
+    zmax = np.abs(prob.z).max()
+    for b in range(B):
+        Eo, go = oracle.energy_grad(Jo, prob.site_class, prob.fixed_q, prob.z, prob.counts, L[b].astype(np.float64), lam)
+        Lb = L[b].astype(np.float64)
+        allowed = prob.counts[prob.site_class[vidx]] > 0
+        ex = np.where(allowed, np.exp(Lb - np.where(allowed, Lb, -np.inf).max(axis=1, keepdims=True)), 0.0)
+        pb = ex / ex.sum(axis=1, keepdims=True)
+        q = prob.fixed_q.copy()
+        q[vidx] = pb @ prob.z
+        mass = (np.abs(Jo) @ np.abs(q))[vidx]
+        assert abs(E[b] - Eo) <= eps * float(np.abs(q[vidx]) @ mass) + 1e-9
+        bound = 4 * zmax * pb * (eps * mass)[:, None] + 2.0 ** -23 * np.abs(go)
+        assert np.all(np.abs(dL[b] - go) <= bound + 1e-30)
+
+
 def test_autograd_function(ctx):
     import paper_2409_08808_gb300 as g
     prob = synth.layered_problem(reps=(2, 1, 1))

@@ -125,3 +125,28 @@ def test_batch_mc_matches_single_runs(ctx):
     ref = oracle.mc_run(Jos[0], probs[0].site_class, probs[0].fixed_q, probs[0].z, starts[0], probs[0].kT, 3000, 1000)
     assert np.array_equal(base_sp[0], ref["species"])
     assert np.allclose(base_E[0], ref["E"], rtol=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mc_multiwarp_chain_equals_single_warp_chain(ctx, prec):
+    """N = 4096 (the benchmark cell): goac_mc_run runs each chain with 4 warps
+    and GEMM-built potentials; the batched kernel runs the same chain with one
+    warp and its own potential build.  With the same Philox key both must take
+    the same swaps (the one-warp chain matches the oracle in the tests above)."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.random_cubic_problem()
+    J = g.build_ewald(ctx, prob.lattice, torch.tensor(prob.frac, device="cuda"), prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, J)
+    start = synth.random_population(prob, 6, 3)
+    a = torch.tensor(start, device="cuda")
+    out = gp.mc_run(a, 0.05, 3000, 77, step0=10, precision=prec)
+    b = torch.tensor(start, device="cuda")
+    kT = [torch.full((6,), 0.05, dtype=torch.float64, device="cuda")]
+    E, _ = g.batch_mc_run(ctx, [gp], [b], kT, 3000, 77, step0=10, precision=prec, chains_per_cta=2, mode=1)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert out["n_accept"].min().item() > 50
+    E64 = gp.score(a, "f64")
+    tol = 1e-9 if prec == "f64" else 2e-5
+    assert torch.allclose(out["E"], E64, rtol=tol, atol=0)
+    assert torch.allclose(E[0], E64, rtol=tol, atol=0)
