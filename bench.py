@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "config energy evals/s and MC swap trials/s at N=4096, % roofline, vs FP64 GPU path"
 N_SIDE = 16          # 16^3 = 4096 sites
 B_POP = 4096
-FORM = "bf16x3"
+FORM = "bf16x2"
 TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2}
 WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +1:512 +2:1024 +3:512 -2:2048), "
             "population B=4096 uniformly random count-preserving configurations")
@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--batch-chains", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=10000)
     ap.add_argument("--grad-batch", type=int, default=2048)
+    ap.add_argument("--grad-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -517,18 +518,82 @@ def run_suite(args):
           "extrapolated_s_for_1e5_swaps": modes["persistent_graph"]["ms"] / 1e3 * 100000 / steps})
     del gps, sps, kts
 
+    # ---- every scoring form at N = 4096, B = 4096 (throughput, error vs the FP64 path, roofline)
+    prob = synth.random_cubic_problem(n_side=N_SIDE)
+    gp, J, jms = problem(prob)
+    pop = torch.tensor(synth.random_population(prob, B_POP, synth.SEED_BASE + 2), device=dev)
+    E64 = gp.score(pop, "f64")
+    bf16_peak, hbm_peak, _ = _peaks()
+    ld = ((prob.N + 127) // 128) * 128
+    nbm = ld // 128
+    forms = {}
+    for form in ("f64", "f32", "tf32", "tf32x2", "bf16x2", "bf16x3"):
+        for _ in range(3):
+            gp.score(pop, form)
+        reps = 2 if form in ("f64", "f32") else 50
+        ctx.set_timing(True)
+        ctx.kernel_time("score_tc")
+        ctx.kernel_time("score_cc")
+        box = {}
+        ms = timed(lambda: [box.setdefault("E", gp.score(pop, form)) for _ in range(reps)]) / reps
+        kms, kn = ctx.kernel_time("score_tc" if form in TERMS else "score_cc")
+        ctx.set_timing(False)
+        E = gp.score(pop, form)
+        err = (E - E64).abs()
+        d = {"ms_per_population": ms, "evals_per_s": B_POP / (ms / 1e3), "speedup_vs_f64": None,
+             "max_abs_err_eV": float(err.max()), "rms_abs_err_eV": float(err.pow(2).mean().sqrt()),
+             "kernel_ms": kms / max(kn, 1)}
+        if form in TERMS:
+            flops = TERMS[form] * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
+            peak = bf16_peak if form.startswith("bf16") else bf16_peak / 2.0
+            d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
+            d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / peak
+        forms[form] = d
+    for f in forms:
+        forms[f]["speedup_vs_f64"] = forms["f64"]["ms_per_population"] / forms[f]["ms_per_population"]
+    idx, Etop = gp.topk_rescore(pop, gp.score(pop, "bf16x3"), 64)
+    emit({"workload": WORKLOAD + ", every scoring form", "forms": forms,
+          "top64_after_bf16x3_equals_fp64_top64": bool(set(idx.tolist()) == set(torch.argsort(E64)[:64].tolist())),
+          "ewald_build_ms": jms})
+    del gp, J, pop, E64
+
     # ---- relaxed occupations: bcc 16^3, N = 8192, B = 2048 logits sets, 5 species
     prob = synth.bcc_relaxed_problem()
     gp, J, jms = problem(prob, allow=True)
     B = args.grad_batch
     L = torch.tensor(synth.random_logits(prob, B, 5), device=dev)
-    gp.energy_grad(L[:2].contiguous(), 0.01, "f64")
+    lam, eta = 1.0, 0.01
+    res = {}
+    for prec in ("f64", "tf32x2"):
+        gp.energy_grad(L[:2].contiguous(), lam, prec)
+        box = {}
+        ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, lam, prec)))
+        res[prec] = {"energy_grad_ms": ms, "grad_steps_per_s": 1e3 / ms}
+    E64, g64 = gp.energy_grad(L, lam, "f64")
+    Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
+    res["tf32x2"]["max_rel_E_err"] = float(((Etc - E64).abs() / E64.abs()).max())
+    res["tf32x2"]["max_abs_grad_err_rel_to_max"] = float((gtc - g64).abs().max() / g64.abs().max())
+    Ld = L.clone()
+    E0 = gp.energy_grad(Ld, lam, "tf32x2")[0]
+    steps = args.grad_steps
     box = {}
-    ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, 0.01, "f64")))
-    p = torch.softmax(L, dim=-1).contiguous()
-    rms = timed(lambda: gp.round_to_counts(p))
-    emit({"workload": f"bcc 16^3 (N=8192, 5 species), relaxed occupations, B={B} logits sets",
-          "energy_grad_f64_ms": ms, "grad_steps_per_s": 1e3 / ms, "round_to_counts_ms": rms,
+    dms = timed(lambda: box.setdefault("E", gp.relaxed_descent(Ld, lam, eta, steps, "tf32x2")))
+    p_occ = gp.occupations(Ld)
+    rms = timed(lambda: box.setdefault("sp", gp.round_to_counts(p_occ)))
+    seeded = box["sp"]
+    E_seed = gp.score(seeded, "bf16x3")
+    rand = gp.random_configs(B, 9)
+    E_rand = gp.score(rand, "bf16x3")
+    gms = timed(lambda: box.setdefault("Eg", gp.ga_run(seeded, 5, 40, oracle.p_mut_to_u32(0.1), 3, 0, "bf16x3")))
+    emit({"workload": f"bcc 16^3 (N=8192, 5 species +1/+2/+3/+4/0), relaxed occupations, B={B} logits sets, "
+                      f"counts penalty lambda={lam}", "forms": res,
+          "descent": {"steps": steps, "eta": eta, "ms": dms, "steps_per_s": steps / (dms / 1e3),
+                      "mean_E_before_eV": float(E0.mean()), "mean_E_after_eV": float(box["E"].mean())},
+          "round_to_counts_ms": rms,
+          "seeded_population": {"mean_E_eV": float(E_seed.mean()), "min_E_eV": float(E_seed.min()),
+                                "random_population_mean_E_eV": float(E_rand.mean()),
+                                "random_population_min_E_eV": float(E_rand.min()),
+                                "ga_5_generations_ms": gms, "ga_best_E_eV": float(box["Eg"].min())},
           "ewald_build_ms": jms})
 
 

@@ -199,6 +199,29 @@ goac_status goac_mc_run(goac_problem* prob, int8_t* species_dev, int32_t C, cons
                         uint64_t seed, uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
                         int8_t* best_species_dev, int64_t* n_accept_dev);
 
+/* Simulated annealing (SI, Simulated annealing: the MC routine with the     *
+ * temperature lowered towards 0 during the run): goac_mc_run with the        *
+ * temperature of step t set to kT0 (kT1/kT0)^(t/(total_steps-1)) per chain   *
+ * (an exponential schedule, as in the paper's runs).  kT0_dev, kT1_dev: C.   */
+goac_status goac_sa_run(goac_problem* prob, int8_t* species_dev, int32_t C, const double* kT0_dev,
+                        const double* kT1_dev, int64_t total_steps, int64_t n_steps, uint64_t seed, uint64_t step0,
+                        int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
+                        int64_t* n_accept_dev);
+
+/* Replica-exchange Monte Carlo (SI, Replica Exchange Monte Carlo): G groups  *
+ * of R chains (chain c = g R + slot; species_dev is G R x Nv, in/out).  Each *
+ * round runs steps_per_round Metropolis steps per chain at its current       *
+ * temperature (steps r*steps_per_round ...), then neighbouring temperature   *
+ * ranks (k, k+1), k = r%2, r%2 + 2, ..., exchange with probability           *
+ * min[1, exp(dE (1/kT_k - 1/kT_{k+1}))], dE = E(rank k) - E(rank k+1), u from *
+ * words 0,1 of Philox(ctr = {r, g, k, 6}); an exchange swaps the two chains' *
+ * temperatures.  kT_ladder_host: R temperatures (> 0).  E_dev: G R energies;  *
+ * perm_dev: G R int32, chain holding rank k of group g at [g R + k];          *
+ * n_exchanges_host: accepted exchanges (nullable; synchronises if given).     */
+goac_status goac_remc_run(goac_problem* prob, int8_t* species_dev, int32_t G, int32_t R, const double* kT_ladder_host,
+                          int32_t n_rounds, int64_t steps_per_round, uint64_t seed, int32_t precision, double* E_dev,
+                          int32_t* perm_dev, int64_t* n_exchanges_host);
+
 /* ------------------------------------------------------------------------ *
  * Batched Monte Carlo over many independent problems in one persistent      *
  * launch (the paper runs independent heuristic runs in parallel, Section    *

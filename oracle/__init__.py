@@ -84,6 +84,8 @@ def _declare(lib):
         "orc_delta_E": (_d, [_p, _i64, _p, _i64, _i64, _d, _d]),
         "orc_random_configs": (C.c_int, [_i64, _p, _i32, _p, _i64, _u64, _p]),
         "orc_mc_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _u64, _u64, _p, _p, _p, _p, _p]),
+        "orc_sa_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _p, _i64, _i64, _u64, _u64, _p, _p, _p, _p]),
+        "orc_remc_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _i64, _i64, _u64, _p, _p, _p]),
         "orc_ga_generation": (C.c_int, [_i64, _p, _p, _p, _i64, _i64, _u32, _u32, _u64, _p, _p, _p]),
         "orc_ga_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _i64, _u32, _u64, _u32]),
         "orc_energy_grad": (_d, [_p, _i64, _p, _p, _p, _i32, _p, _p, _d, _p]),
@@ -286,6 +288,40 @@ def mc_run(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0, trace=
         raise ValueError("no movable class")
     assert best.shape == (Cn, nv)
     return {"species": sp, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc, "E_trace": tr}
+
+
+def sa_run(J, site_class, fixed_q, z, species, kT0, kT1, total, nsteps, seed, step0=0):
+    """Simulated annealing (exponential kT schedule from kT0 to kT1 over `total` steps)."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    Cn = sp.shape[0]
+    k0 = _f64(np.broadcast_to(np.asarray(kT0, dtype=np.float64), (Cn,)))
+    k1 = _f64(np.broadcast_to(np.asarray(kT1, dtype=np.float64), (Cn,)))
+    E = np.zeros(Cn)
+    bestE = np.zeros(Cn)
+    best = np.zeros_like(sp)
+    nacc = np.zeros(Cn, dtype=np.int64)
+    rc = _load().orc_sa_run(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), Cn, _ptr(k0),
+                            _ptr(k1), total, nsteps, seed, step0, _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc))
+    if rc:
+        raise ValueError("no movable class")
+    return {"species": sp, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
+
+
+def remc_run(J, site_class, fixed_q, z, species, G, R, kT_ladder, n_rounds, steps_per_round, seed):
+    """Replica exchange: G groups of R chains, exchanges after every round."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    E = np.zeros(G * R)
+    perm = np.zeros(G * R, dtype=np.int32)
+    nex = np.zeros(1, dtype=np.int64)
+    rc = _load().orc_remc_run(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), G, R,
+                              _ptr(_f64(kT_ladder)), n_rounds, steps_per_round, seed, _ptr(E), _ptr(perm), _ptr(nex))
+    if rc:
+        raise ValueError("remc failed")
+    return {"species": sp, "E": E, "perm": perm, "n_exchanges": int(nex[0])}
 
 
 def p_mut_to_u32(p_mut: float) -> int:

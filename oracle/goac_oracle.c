@@ -27,6 +27,10 @@
  *                          pinned: Eq. 2 energy equals direct Ewald energy;
  *                          sub-structure coefficients equal J-based ones.
  *   orc_delta_E            pinned: equals E(after) - E(before).
+ *   orc_sa_run             pinned: constant schedule equals orc_mc_run; kT -> 0
+ *                          end is a descent; schedule endpoints.
+ *   orc_remc_run           pinned: detailed balance of the exchange (two-level
+ *                          chi^2), perm stays a permutation, R = 1 equals MC.
  *   orc_mc_run             pinned: Boltzmann visit frequencies (chi^2) on a
  *                          brute-forced cell; count preservation; E tracking.
  *   orc_ga_generation      pinned: count preservation, elitism, inheritance
@@ -634,9 +638,41 @@ int orc_random_configs(int64_t N, const int32_t* site_class, int32_t S, const in
 /* kept.  Returns the number of accepted swaps per chain in n_accept, and,   */
 /* when E_trace (C x nsteps) is given, the energy before every step.         */
 /* ------------------------------------------------------------------------ */
+/* Temperature of step t: constant kT0, or with kT1 given the exponential    */
+/* schedule kT0 (kT1/kT0)^(t/(total-1)) of simulated annealing (SI,          */
+/* Simulated annealing: the temperature is lowered towards 0 during the run). */
+static double step_kT(double kT0, const double* kT1, int64_t ch, uint64_t t, int64_t total)
+{
+    if (!kT1 || total <= 1) return kT0;
+    return kT0 * exp(log(kT1[ch] / kT0) * ((double)t / (double)(total - 1)));
+}
+
+static int mc_core(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                   int8_t* species, int64_t C, const double* kT, const double* kT1, int64_t total,
+                   int64_t nsteps, uint64_t seed, uint64_t step0, double* E_out, double* bestE,
+                   int8_t* best_species, int64_t* n_accept, double* E_trace);
+
 int orc_mc_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
                int8_t* species, int64_t C, const double* kT, int64_t nsteps, uint64_t seed, uint64_t step0,
                double* E_out, double* bestE, int8_t* best_species, int64_t* n_accept, double* E_trace)
+{
+    return mc_core(J, N, site_class, fixed_q, z, species, C, kT, NULL, 0, nsteps, seed, step0, E_out, bestE,
+                   best_species, n_accept, E_trace);
+}
+
+/* Simulated annealing: the Monte Carlo above with kT(t) = kT0 (kT1/kT0)^(t/(total-1)) per chain. */
+int orc_sa_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+               int8_t* species, int64_t C, const double* kT0, const double* kT1, int64_t total, int64_t nsteps,
+               uint64_t seed, uint64_t step0, double* E_out, double* bestE, int8_t* best_species, int64_t* n_accept)
+{
+    return mc_core(J, N, site_class, fixed_q, z, species, C, kT0, kT1, total, nsteps, seed, step0, E_out, bestE,
+                   best_species, n_accept, NULL);
+}
+
+static int mc_core(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                   int8_t* species, int64_t C, const double* kT, const double* kT1, int64_t total,
+                   int64_t nsteps, uint64_t seed, uint64_t step0, double* E_out, double* bestE,
+                   int8_t* best_species, int64_t* n_accept, double* E_trace)
 {
     classes_t cl = make_classes(site_class, N);
     int64_t nv = cl.nv;
@@ -679,10 +715,11 @@ int orc_mc_run(const double* J, int64_t N, const int32_t* site_class, const doub
             double d = z[sb] - z[sa];
             double dE = 2.0 * d * (phi[va] - phi[vb]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
             double u = ((double)(x[2] >> 5) * 67108864.0 + (double)(x[3] >> 6)) * (1.0 / 9007199254740992.0);
+            const double kTt = step_kT(kT[ch], kT1, ch, t, total);
             int accept;
             if (dE <= ORC_DE_ZERO) accept = 1;
-            else if (kT[ch] <= 0.0) accept = 0;
-            else accept = u < exp(-dE / kT[ch]);
+            else if (kTt <= 0.0) accept = 0;
+            else accept = u < exp(-dE / kTt);
             if (!accept) continue;
             sp[va] = (int8_t)sb;
             sp[vb] = (int8_t)sa;
@@ -1069,4 +1106,53 @@ double orc_log10_configurations(int32_t nsites, const int32_t* positions, int32_
         for (int e = 0; e < nelem; ++e) l -= lgamma((double)n_se[s * nelem + e] + 1.0);
     }
     return l / log(10.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Replica-exchange Monte Carlo (SI, Replica Exchange Monte Carlo): G groups */
+/* of R chains (chain c = g R + slot) run Metropolis segments of              */
+/* steps_per_round steps at their current temperatures; after round r the    */
+/* neighbouring temperature ranks (k, k+1) with k = r%2, r%2 + 2, ... try to   */
+/* exchange: with dE = E(chain at rank k) - E(chain at rank k+1), accept with */
+/* P = min[1, exp(dE (1/kT_k - 1/kT_{k+1}))], u from words 0,1 of             */
+/* Philox(ctr = {r, g, k, 6}).  An exchange swaps the two chains'             */
+/* temperatures (equivalent to swapping configurations).  Segment r uses steps */
+/* r*steps_per_round ...; perm[g R + k] = chain holding rank k.               */
+/* ------------------------------------------------------------------------ */
+int orc_remc_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                 int8_t* species, int64_t G, int64_t R, const double* kT_ladder, int64_t n_rounds,
+                 int64_t steps_per_round, uint64_t seed, double* E_out, int32_t* perm, int64_t* n_exchanges)
+{
+    int64_t C = G * R;
+    double* kT = (double*)malloc(sizeof(double) * (size_t)(C + 1));
+    int64_t nex = 0;
+    for (int64_t g = 0; g < G; ++g)
+        for (int64_t k = 0; k < R; ++k) {
+            perm[g * R + k] = (int32_t)(g * R + k);
+            kT[g * R + k] = kT_ladder[k];
+        }
+    for (int64_t r = 0; r < n_rounds; ++r) {
+        int rc = orc_mc_run(J, N, site_class, fixed_q, z, species, C, kT, steps_per_round, seed,
+                            (uint64_t)(r * steps_per_round), E_out, NULL, NULL, NULL, NULL);
+        if (rc) { free(kT); return rc; }
+        for (int64_t g = 0; g < G; ++g)
+            for (int64_t k = r % 2; k + 1 < R; k += 2) {
+                int32_t ca = perm[g * R + k], cb = perm[g * R + k + 1];
+                double dE = E_out[ca] - E_out[cb];
+                double x = dE * (1.0 / kT_ladder[k] - 1.0 / kT_ladder[k + 1]);
+                uint32_t w[4];
+                philox_draw(seed, (uint32_t)r, (uint32_t)g, (uint32_t)k, 6u, w);
+                double u = ((double)(w[0] >> 5) * 67108864.0 + (double)(w[1] >> 6)) * (1.0 / 9007199254740992.0);
+                if (x >= 0.0 || u < exp(x)) {
+                    perm[g * R + k] = cb;
+                    perm[g * R + k + 1] = ca;
+                    kT[ca] = kT_ladder[k + 1];
+                    kT[cb] = kT_ladder[k];
+                    nex++;
+                }
+            }
+    }
+    if (n_exchanges) *n_exchanges = nex;
+    free(kT);
+    return 0;
 }

@@ -239,6 +239,35 @@ class Problem:
                                _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)), "goac_mc_run")
         return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
 
+    def sa_run(self, species: torch.Tensor, kT0, kT1, total_steps: int, n_steps: int, seed: int, step0: int = 0,
+               precision="f64"):
+        """Simulated annealing in place on `species` (exponential schedule kT0 -> kT1 over total_steps)."""
+        Cn = species.shape[0]
+        dev = self._dev()
+        k0 = torch.as_tensor(kT0, dtype=torch.float64, device=dev).expand(Cn).contiguous()
+        k1 = torch.as_tensor(kT1, dtype=torch.float64, device=dev).expand(Cn).contiguous()
+        E = torch.empty(Cn, dtype=torch.float64, device=dev)
+        bestE = torch.empty(Cn, dtype=torch.float64, device=dev)
+        best = torch.empty_like(species)
+        nacc = torch.empty(Cn, dtype=torch.int64, device=dev)
+        _check(lib.goac_sa_run(self.handle, _ptr(species), Cn, _ptr(k0), _ptr(k1), int(total_steps), int(n_steps),
+                               int(seed), int(step0), _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)),
+               "goac_sa_run")
+        return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
+
+    def remc_run(self, species: torch.Tensor, G: int, R: int, kT_ladder, n_rounds: int, steps_per_round: int,
+                 seed: int, precision="f64"):
+        """Replica exchange in place on `species` (G R x Nv).  Returns (E, perm, n_exchanges)."""
+        dev = self._dev()
+        lad = np.ascontiguousarray(kT_ladder, dtype=np.float64)
+        E = torch.empty(G * R, dtype=torch.float64, device=dev)
+        perm = torch.empty(G * R, dtype=torch.int32, device=dev)
+        nex = C.c_int64()
+        _check(lib.goac_remc_run(self.handle, _ptr(species), int(G), int(R), _ptr(lad), int(n_rounds),
+                                 int(steps_per_round), int(seed), _prec(precision), _ptr(E), _ptr(perm),
+                                 C.byref(nex)), "goac_remc_run")
+        return E, perm, int(nex.value)
+
     # ---- genetic algorithm ----------------------------------------------
     def ga_generation(self, pop: torch.Tensor, E: torch.Tensor, n_elite: int, p_mut_u32: int, gen: int, seed: int,
                       record: bool = False):

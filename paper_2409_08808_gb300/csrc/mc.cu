@@ -39,7 +39,9 @@ struct McProb {
     const int32_t* cls_pos;   // Nv
     const uint32_t* wprefix;  // ncls
     int8_t* species;          // chains x Nv (in/out)
-    const double* kT;         // chains
+    const double* kT;         // chains (start temperature of an annealing schedule)
+    const double* kT1;        // chains, end temperature of the schedule, or null (constant kT)
+    int64_t total;            // schedule length in steps
     double* E_out;            // chains
     double* bestE;            // chains
     int8_t* best_species;     // chains x Nv or null
@@ -138,16 +140,17 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
         for (int w = ct; w < Nv; w += 32 * W) P.best_species[(long)chain * Nv + w] = sp[w];
 
     const double kT = P.kT[chain];
-    const float kTf = (float)kT;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
         const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
         const uint64_t t = sc.step0 + (uint64_t)s0 + (uint64_t)lane;
         // ---- draw this lane's proposal (state independent) ----
         int va = 0, vb = 0;
-        double u = 0.0;
+        double u = 0.0, kTl = kT;
         R jsum = (R)0;
         if (lane < nb) {
+            if (P.kT1 && P.total > 1)     // simulated annealing: kT0 (kT1/kT0)^(t/(total-1))
+                kTl = kT * exp(log(P.kT1[chain] / kT) * ((double)t / (double)(P.total - 1)));
             const uint4 x = goacd::philox(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)chain, 0u), k0, k1);
             int k = P.only_movable;
             if (P.nmovable != 1) {
@@ -182,8 +185,8 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                     dE = rd_add<R>(rd_mul<R>(rd_mul<R>((R)2, d), rd_sub<R>(phi[va], phi[vb])),
                                    rd_mul<R>(rd_mul<R>(d, d), jsum));
                     if ((double)dE <= kDeZero) acc = true;
-                    else if (sizeof(R) == 8) acc = kT > 0.0 && u < exp(-(double)dE / kT);
-                    else acc = kTf > 0.0f && (float)u < expf(-(float)dE / kTf);
+                    else if (sizeof(R) == 8) acc = kTl > 0.0 && u < exp(-(double)dE / kTl);
+                    else acc = kTl > 0.0 && (float)u < expf(-(float)dE / (float)kTl);
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, acc);
@@ -321,6 +324,8 @@ McProb make_desc(goac_problem* p, bool f32, int8_t* species, int C, const double
     d.wprefix = p->wprefix_dev;
     d.species = species;
     d.kT = kT;
+    d.kT1 = nullptr;
+    d.total = 0;
     d.E_out = E;
     d.bestE = bestE;
     d.best_species = best_species;
@@ -342,9 +347,10 @@ constexpr size_t kSmemBudget = 220 * 1024;
 
 }  // namespace
 
-extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
-                                   int64_t n_steps, uint64_t seed, uint64_t step0, int32_t precision, double* E_dev,
-                                   double* bestE_dev, int8_t* best_species_dev, int64_t* n_accept_dev)
+static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
+                               const double* kT1_dev, int64_t total, int64_t n_steps, uint64_t seed, uint64_t step0,
+                               int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
+                               int64_t* n_accept_dev)
 {
     if (!p || !species_dev || !kT_dev || !E_dev || !bestE_dev)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL argument");
@@ -379,6 +385,8 @@ extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t
     if (cpc < 1) cpc = 1;
     const size_t smem = slot * cpc;
     McProb d = make_desc(p, f32, species_dev, C, kT_dev, E_dev, bestE_dev, best_species_dev, n_accept_dev, seed);
+    d.kT1 = kT1_dev;
+    d.total = total;
     McScalars sc{n_steps, step0};
     const int blocks = (C + cpc - 1) / cpc;
     goac::KTimer kt(p->ctx, goac::KID_MC, p->ctx->stream);
@@ -399,6 +407,104 @@ extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t
     }
 #undef GOAC_MC_LAUNCH
     GOAC_LAUNCH_CHECK("k_mc");
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
+                                   int64_t n_steps, uint64_t seed, uint64_t step0, int32_t precision, double* E_dev,
+                                   double* bestE_dev, int8_t* best_species_dev, int64_t* n_accept_dev)
+{
+    return mc_run_impl(p, species_dev, C, kT_dev, nullptr, 0, n_steps, seed, step0, precision, E_dev, bestE_dev,
+                       best_species_dev, n_accept_dev);
+}
+
+extern "C" goac_status goac_sa_run(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT0_dev,
+                                   const double* kT1_dev, int64_t total_steps, int64_t n_steps, uint64_t seed,
+                                   uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
+                                   int8_t* best_species_dev, int64_t* n_accept_dev)
+{
+    if (!kT1_dev || total_steps < 1) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_sa_run: kT1 and total_steps needed");
+    return mc_run_impl(p, species_dev, C, kT0_dev, kT1_dev, total_steps, n_steps, seed, step0, precision, E_dev,
+                       bestE_dev, best_species_dev, n_accept_dev);
+}
+
+namespace {
+
+__global__ void k_remc_init(int G, int R, const double* __restrict__ ladder, double* __restrict__ kT,
+                            int32_t* __restrict__ perm, unsigned long long* __restrict__ nex)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *nex = 0ull;
+    if (c >= G * R) return;
+    perm[c] = c;
+    kT[c] = ladder[c % R];
+}
+
+// Exchange attempts after round r, one thread per replica group.
+__global__ void k_remc_exchange(int G, int R, uint32_t r, const double* __restrict__ ladder, double* __restrict__ kT,
+                                const double* __restrict__ E, int32_t* __restrict__ perm, uint64_t seed,
+                                unsigned long long* __restrict__ nex)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    unsigned long long cnt = 0;
+    for (int k = (int)(r & 1u); k + 1 < R; k += 2) {
+        const int ca = perm[g * R + k], cb = perm[g * R + k + 1];
+        const double dE = E[ca] - E[cb];
+        const double x = dE * (1.0 / ladder[k] - 1.0 / ladder[k + 1]);
+        const uint4 w = goacd::philox(make_uint4(r, (uint32_t)g, (uint32_t)k, 6u), k0, k1);
+        const double u = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) * (1.0 / 9007199254740992.0);
+        if (x >= 0.0 || u < exp(x)) {
+            perm[g * R + k] = cb;
+            perm[g * R + k + 1] = ca;
+            kT[ca] = ladder[k + 1];
+            kT[cb] = ladder[k];
+            ++cnt;
+        }
+    }
+    if (cnt) atomicAdd(nex, cnt);
+}
+
+}  // namespace
+
+extern "C" goac_status goac_remc_run(goac_problem* p, int8_t* species_dev, int32_t G, int32_t R,
+                                     const double* kT_ladder_host, int32_t n_rounds, int64_t steps_per_round,
+                                     uint64_t seed, int32_t precision, double* E_dev, int32_t* perm_dev,
+                                     int64_t* n_exchanges_host)
+{
+    if (!p || !species_dev || !kT_ladder_host || !E_dev || !perm_dev || G <= 0 || R <= 0 || n_rounds < 0 ||
+        steps_per_round < 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_remc_run: bad argument");
+    for (int k = 0; k < R; ++k)
+        if (!(kT_ladder_host[k] > 0.0)) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_remc_run: temperatures must be > 0");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const int C = G * R;
+    DevBuf& buf = p->score_tmp;
+    goac_status rc = goac::ensure(buf, sizeof(double) * (2 * (size_t)C + R) + 64);
+    if (rc) return rc;
+    double* kT = (double*)buf.ptr;
+    double* bestE = kT + C;
+    double* ladder = bestE + C;
+    unsigned long long* nex = (unsigned long long*)(ladder + R);
+    cudaStream_t st = p->ctx->stream;
+    GOAC_CUDA(cudaMemcpyAsync(ladder, kT_ladder_host, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+    goac::launch(k_remc_init, (C + 255) / 256, 256, 0, st, G, R, (const double*)ladder, kT, perm_dev, nex);
+    GOAC_LAUNCH_CHECK("k_remc_init");
+    for (int r = 0; r < n_rounds; ++r) {
+        rc = mc_run_impl(p, species_dev, C, kT, nullptr, 0, steps_per_round, seed, (uint64_t)r * steps_per_round,
+                         precision, E_dev, bestE, nullptr, nullptr);
+        if (rc) return rc;
+        goac::launch(k_remc_exchange, (G + 127) / 128, 128, 0, st, G, R, (uint32_t)r, (const double*)ladder, kT,
+                     (const double*)E_dev, perm_dev, seed, nex);
+        GOAC_LAUNCH_CHECK("k_remc_exchange");
+    }
+    if (n_exchanges_host) {
+        unsigned long long h = 0;
+        GOAC_CUDA(cudaMemcpyAsync(&h, nex, sizeof(h), cudaMemcpyDeviceToHost, st));
+        GOAC_CUDA(cudaStreamSynchronize(st));
+        *n_exchanges_host = (int64_t)h;
+    }
     return GOAC_OK;
 }
 

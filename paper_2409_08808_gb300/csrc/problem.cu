@@ -372,6 +372,68 @@ __global__ void k_random_configs(int B, int ncls, int S, const int32_t* __restri
     }
 }
 
+// FP64 rescoring of a few configurations over the upper block triangle of
+// J_vv: block (I, J), I <= J, of 64 x 64 sites adds w sum_{i in I, j in J}
+// q_bi J_ij q_bj for every configuration b (w = 1 on the diagonal, 2 above),
+// configurations in chunks of 64, 4 threads per configuration.
+constexpr int RS = 64;
+
+__global__ void __launch_bounds__(256) k_rescore_pairs(const double* __restrict__ Jvv, int ld, int Nv,
+                                                       const int8_t* __restrict__ sp, int k,
+                                                       const double* __restrict__ z, double* __restrict__ partial)
+{
+    __shared__ double Jt[RS][RS + 1];
+    __shared__ double qI[RS][RS + 1];
+    __shared__ double qJ[RS][RS + 1];
+    int t = blockIdx.x;
+    int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    while (bj * (bj + 1) / 2 > t) --bj;
+    const int bi = t - bj * (bj + 1) / 2;   // bi <= bj
+    const int i0 = bi * RS, j0 = bj * RS;
+    const double w = bi == bj ? 1.0 : 2.0;
+    for (int e = threadIdx.x; e < RS * RS; e += 256) {
+        const int r = e / RS, c = e % RS;
+        Jt[r][c] = Jvv[(long)(i0 + r) * ld + j0 + c];      // padded to ld, zeros beyond Nv
+    }
+    const int cfg = threadIdx.x >> 2, part = threadIdx.x & 3;
+    for (int c0 = 0; c0 < k; c0 += RS) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < RS * RS; e += 256) {
+            const int c = e / RS, x = e % RS;
+            const int b = c0 + c;
+            qI[c][x] = (b < k && i0 + x < Nv) ? z[sp[(long)b * Nv + i0 + x]] : 0.0;
+            qJ[c][x] = (b < k && j0 + x < Nv) ? z[sp[(long)b * Nv + j0 + x]] : 0.0;
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (int jj = part * 16; jj < part * 16 + 16; ++jj) {
+            double tj = 0.0;
+#pragma unroll 8
+            for (int ii = 0; ii < RS; ++ii) tj = fma(qI[cfg][ii], Jt[ii][jj], tj);
+            acc = fma(qJ[cfg][jj], tj, acc);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0 && c0 + cfg < k) partial[(long)blockIdx.x * k + c0 + cfg] = w * acc;
+    }
+}
+
+// E_b = E_const + 2 q_b . phi_fix + sum over block pairs (fixed order); one warp per configuration.
+__global__ void k_rescore_finish(const double* __restrict__ partial, int npairs, int k, const int8_t* __restrict__ sp,
+                                 int Nv, const double* __restrict__ z, const double* __restrict__ phifix,
+                                 double E_const, double* __restrict__ E)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= k) return;
+    double s = 0.0;
+    for (int t = lane; t < npairs; t += 32) s += partial[(long)t * k + b];
+    for (int v = lane; v < Nv; v += 32) s += z[sp[(long)b * Nv + v]] * (2.0 * phifix[v]);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) E[b] = s + E_const;
+}
+
 // rank of each E by (E, index) among B; entries with rank < k are selected.
 __global__ void k_rank_select(const double* __restrict__ E, int B, int k, int* __restrict__ sel)
 {
@@ -717,17 +779,25 @@ extern "C" goac_status goac_topk_rescore(goac_problem* p, const int8_t* species_
     if (k < 1 || k > 1024 || k > B) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_topk_rescore: need 1 <= k <= min(B, 1024)");
     goac_ctx* ctx = p->ctx;
     GOAC_CUDA(cudaSetDevice(ctx->device));
-    size_t need = sizeof(int) * 1024 + sizeof(double) * 1024 + (size_t)k * p->Nv + 64;
+    const int nb = (p->Nv + RS - 1) / RS;
+    const long npairs = (long)nb * (nb + 1) / 2;
+    size_t need = sizeof(int) * 1024 + sizeof(double) * 1024 + sizeof(double) * (size_t)npairs * k +
+                  (size_t)k * p->Nv + 256;
     goac_status rc = goac::ensure(p->topk_tmp, need);
     if (rc) return rc;
     int* sel = (int*)p->topk_tmp.ptr;
     double* e64 = (double*)((char*)p->topk_tmp.ptr + sizeof(int) * 1024);
-    int8_t* sub = (int8_t*)((char*)p->topk_tmp.ptr + sizeof(int) * 1024 + sizeof(double) * 1024);
+    double* part = e64 + 1024;
+    int8_t* sub = (int8_t*)(part + (size_t)npairs * k);
     goac::launch(k_rank_select, (B + 255) / 256, 256, 0, ctx->stream, E_approx_dev, B, k, sel);
     goac::launch(k_gather_rows, (int)(((long)k * p->Nv + 255) / 256), 256, 0, ctx->stream, species_dev, p->Nv, sel, k, sub);
     GOAC_LAUNCH_CHECK("topk select");
-    rc = goac::score_f64(p, sub, k, e64, nullptr);
-    if (rc) return rc;
+    goac::launch(k_rescore_pairs, (unsigned)npairs, 256, 0, ctx->stream, (const double*)p->J_vv, p->Nv_pad, p->Nv,
+                 (const int8_t*)sub, k, (const double*)p->z_dev, part);
+    GOAC_LAUNCH_CHECK("k_rescore_pairs");
+    goac::launch(k_rescore_finish, (k + 7) / 8, 256, 0, ctx->stream, (const double*)part, (int)npairs, k,
+                 (const int8_t*)sub, p->Nv, (const double*)p->z_dev, (const double*)p->phifix, p->E_const, e64);
+    GOAC_LAUNCH_CHECK("k_rescore_finish");
     goac::launch(k_sort_small, 1, 1024, 0, ctx->stream, e64, sel, k, idx_dev, E_dev);
     GOAC_LAUNCH_CHECK("k_sort_small");
     return GOAC_OK;

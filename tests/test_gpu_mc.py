@@ -150,3 +150,36 @@ def test_mc_multiwarp_chain_equals_single_warp_chain(ctx, prec):
     tol = 1e-9 if prec == "f64" else 2e-5
     assert torch.allclose(out["E"], E64, rtol=tol, atol=0)
     assert torch.allclose(E[0], E64, rtol=tol, atol=0)
+
+
+def test_sa_trajectory_parity(ctx):
+    """Simulated annealing, kT 1.0 -> 0.01 eV over 5000 steps: same swaps as the oracle."""
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 8, 12)
+    ref = oracle.sa_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 1.0, 0.01, 5000, 5000, seed=33)
+    sp = torch.tensor(start, device="cuda")
+    out = gp.sa_run(sp, 1.0, 0.01, 5000, 5000, 33)
+    assert np.array_equal(sp.cpu().numpy(), ref["species"])
+    assert np.array_equal(out["n_accept"].cpu().numpy(), ref["n_accept"])
+    assert np.allclose(out["E"].cpu().numpy(), ref["E"], rtol=1e-10)
+
+
+def test_remc_parity(ctx):
+    """Replica exchange, 3 groups x 4 temperatures, 6 rounds of 400 steps: same
+    configurations, temperature permutation and number of exchanges."""
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    G, R = 3, 4
+    ladder = [0.05, 0.15, 0.4, 1.0]
+    start = synth.random_population(prob, G * R, 13)
+    ref = oracle.remc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, G, R, ladder, 6, 400, seed=44)
+    sp = torch.tensor(start, device="cuda")
+    E, perm, nex = gp.remc_run(sp, G, R, ladder, 6, 400, 44)
+    assert ref["n_exchanges"] > 0
+    assert nex == ref["n_exchanges"]
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    assert np.array_equal(sp.cpu().numpy(), ref["species"])
+    assert np.allclose(E.cpu().numpy(), ref["E"], rtol=1e-10)
