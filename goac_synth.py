@@ -338,3 +338,62 @@ def tiny_rocksalt_problem():
     """1x1x2 rocksalt cell: 8 anions fixed at -2 and 8 cations 4 x +1 / 4 x +3
     (70 configurations), the brute-force cell."""
     return rocksalt_problem(reps=(1, 1, 2), a=4.2)
+
+
+def o3_layered_problem(reps=(2, 2, 1), a_sqrt3=5.0, c=19.2, z_o=0.25):
+    """O3 layered oxide of the paper's scaling study (Section "High-Entropy
+    Layered Oxides", Table 1): Na2/3[Li1/6 Fe1/6 Co1/6 Ni1/6 Mn1/3]O2 in a
+    sqrt(3) cell (a = 5.0 A, c = 19.2 A) with 9 Na positions (6 Na + 3
+    vacancies), 9 TM positions (Li 1.5, Fe 1.5, Co 1.5, Ni 1.5, Mn 3) and 18 O
+    per cell; charges Na+ Li+ Fe2.5+ Co3.5+ Ni2+ Mn4+ O1.75-.  Positions: the
+    alpha-NaFeO2 (R-3m) arrangement of a hexagonal cell with a_h = a/sqrt(3)
+    (TM 3a, Na 3b, O 6c at z = +-z_o; the paper does not give z), re-expressed in
+    the sqrt(3) x sqrt(3) cell and tiled reps times."""
+    ah = a_sqrt3 / math.sqrt(3.0)
+    h1 = np.array([ah, 0.0, 0.0])
+    h2 = np.array([-0.5 * ah, math.sqrt(3) / 2 * ah, 0.0])
+    h3 = np.array([0.0, 0.0, c])
+    b1, b2 = h1 - h2, h1 + 2 * h2
+    cell = np.stack([b1, b2, h3])
+    rshift = [(0.0, 0.0, 0.0), (2 / 3, 1 / 3, 1 / 3), (1 / 3, 2 / 3, 2 / 3)]
+    basis = []
+    for s in rshift:
+        basis.append(((s[0], s[1], s[2] % 1.0), 1))              # TM 3a
+        basis.append(((s[0], s[1], (s[2] + 0.5) % 1.0), 0))      # Na 3b
+        basis.append(((s[0], s[1], (s[2] + z_o) % 1.0), -1))     # O 6c
+        basis.append(((s[0], s[1], (s[2] - z_o) % 1.0), -1))
+    inv = np.linalg.inv(cell)
+    pts, labs = [], []
+    for i in range(-3, 4):
+        for j in range(-3, 4):
+            for f, lab in basis:
+                r = (f[0] + i) * h1 + (f[1] + j) * h2 + f[2] * h3
+                g = r @ inv
+                g = np.where(np.abs(g - np.round(g)) < 1e-9, np.round(g), g)
+                if np.all(g >= -1e-9) and np.all(g < 1 - 1e-9):
+                    pts.append(g % 1.0)
+                    labs.append(lab)
+    pts = np.array(pts)
+    labs = np.array(labs)
+    order = np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2], labs))
+    pts, labs = pts[order], labs[order]
+    assert (labs == 0).sum() == 9 and (labs == 1).sum() == 9 and (labs == -1).sum() == 18
+    frac = _supercell([tuple(p) for p in pts], reps)
+    ncell = reps[0] * reps[1] * reps[2]
+    site_class = np.tile(labs.astype(np.int32), ncell)
+    z = np.array([1.0, 0.0, 1.0, 2.5, 3.5, 2.0, 4.0])
+    names = ["Na+", "Vac", "Li+", "Fe2.5+", "Co3.5+", "Ni2+", "Mn4+"]
+    counts = np.zeros((2, 7), dtype=np.int32)
+    counts[0, 0], counts[0, 1] = 6 * ncell, 3 * ncell
+    h = (3 * ncell) // 2
+    counts[1, 2:7] = [h, h, h, h, 3 * ncell]
+    assert counts[1].sum() == 9 * ncell, "the TM counts need an even number of sqrt(3) cells"
+    fixed_q = np.where(site_class == -1, -1.75, 0.0)
+    lattice = cell * np.array(reps, dtype=np.float64)[:, None]
+    alpha, nimg, kcut = default_cutoffs(lattice)
+    return Problem(name=f"O3_{reps[0]}x{reps[1]}x{reps[2]}", lattice=lattice, frac=frac, site_class=site_class,
+                   fixed_q=fixed_q, z=z, counts=counts, alpha=alpha, nimg=nimg, kcut=kcut, species_names=names)
+
+
+#: the eight sqrt(3)-supercells of Table 1
+TABLE1_CELLS = [(2, 2, 1), (2, 2, 2), (4, 4, 1), (4, 4, 2), (6, 6, 1), (8, 8, 1), (6, 6, 2), (6, 6, 3)]

@@ -208,6 +208,17 @@ goac_status goac_sa_run(goac_problem* prob, int8_t* species_dev, int32_t C, cons
                         int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
                         int64_t* n_accept_dev);
 
+/* Gradient descent over single-swap neighbours (SI, Gradient Descent), for a *
+ * batch of B configurations (species_dev B x Nv, in/out).  Each step          *
+ * evaluates dE for every pair a < b of the same class holding different      *
+ * species; if the minimum dmin < -1e-9 eV, the lowest pair (a, b)            *
+ * (lexicographic) with dE <= dmin + 1e-9 eV is swapped, else the             *
+ * configuration is a local minimum and stays.  At most max_steps steps.       *
+ * E_dev: B final energies (FP64); steps_dev: B int64 steps taken.            *
+ * Synchronises every 8 steps to stop once every configuration has converged. */
+goac_status goac_gd_run(goac_problem* prob, int8_t* species_dev, int32_t B, int32_t max_steps, double* E_dev,
+                        int64_t* steps_dev);
+
 /* Replica-exchange Monte Carlo (SI, Replica Exchange Monte Carlo): G groups  *
  * of R chains (chain c = g R + slot; species_dev is G R x Nv, in/out).  Each *
  * round runs steps_per_round Metropolis steps per chain at its current       *
@@ -221,6 +232,18 @@ goac_status goac_sa_run(goac_problem* prob, int8_t* species_dev, int32_t C, cons
 goac_status goac_remc_run(goac_problem* prob, int8_t* species_dev, int32_t G, int32_t R, const double* kT_ladder_host,
                           int32_t n_rounds, int64_t steps_per_round, uint64_t seed, int32_t precision, double* E_dev,
                           int32_t* perm_dev, int64_t* n_exchanges_host);
+
+/* Hybrid heuristic (SI, Hybrid Methods: REMC and GA called alternately, the  *
+ * best solutions passed on): n_cycles of goac_remc_run on the P = G R        *
+ * configurations (key seed + 2c), each followed by n_gen GA generations with *
+ * FP64 rescoring (goac_ga_run, key seed + 2c + 1, generations from c n_gen)  *
+ * starting from the REMC configurations; the GA population (elites first)    *
+ * starts the next cycle.  `precision` applies to the MC segments.  E_dev: P  *
+ * final energies.  Synchronises.                                              */
+goac_status goac_hybrid_run(goac_problem* prob, int8_t* species_dev, int32_t G, int32_t R,
+                            const double* kT_ladder_host, int32_t n_cycles, int32_t n_rounds, int64_t steps_per_round,
+                            int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, int32_t precision,
+                            double* E_dev);
 
 /* ------------------------------------------------------------------------ *
  * Batched Monte Carlo over many independent problems in one persistent      *

@@ -86,6 +86,9 @@ def _declare(lib):
         "orc_mc_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _u64, _u64, _p, _p, _p, _p, _p]),
         "orc_sa_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _p, _i64, _i64, _u64, _u64, _p, _p, _p, _p]),
         "orc_remc_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _i64, _i64, _u64, _p, _p, _p]),
+        "orc_gd_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _p]),
+        "orc_hybrid_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _i64, _i64, _i64, _i64, _i64, _u32,
+                                     _u64, _p]),
         "orc_ga_generation": (C.c_int, [_i64, _p, _p, _p, _i64, _i64, _u32, _u32, _u64, _p, _p, _p]),
         "orc_ga_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _i64, _u32, _u64, _u32]),
         "orc_energy_grad": (_d, [_p, _i64, _p, _p, _p, _i32, _p, _p, _d, _p]),
@@ -322,6 +325,34 @@ def remc_run(J, site_class, fixed_q, z, species, G, R, kT_ladder, n_rounds, step
     if rc:
         raise ValueError("remc failed")
     return {"species": sp, "E": E, "perm": perm, "n_exchanges": int(nex[0])}
+
+
+def gd_run(J, site_class, fixed_q, z, species, max_steps):
+    """Steepest descent over single swaps; returns final species, E and steps taken."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    Cn = sp.shape[0]
+    E = np.zeros(Cn)
+    st = np.zeros(Cn, dtype=np.int64)
+    _load().orc_gd_run(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), Cn, max_steps,
+                       _ptr(E), _ptr(st))
+    return {"species": sp, "E": E, "steps": st}
+
+
+def hybrid_run(J, site_class, fixed_q, z, species, G, R, kT_ladder, n_cycles, n_rounds, steps_per_round, n_gen,
+               n_elite, p_mut, seed):
+    """REMC <-> GA alternation; returns final population and energies."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    E = np.zeros(G * R)
+    rc = _load().orc_hybrid_run(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), G, R,
+                                _ptr(_f64(kT_ladder)), n_cycles, n_rounds, steps_per_round, n_gen, n_elite,
+                                p_mut_to_u32(p_mut), seed, _ptr(E))
+    if rc:
+        raise ValueError("hybrid failed")
+    return {"species": sp, "E": E}
 
 
 def p_mut_to_u32(p_mut: float) -> int:

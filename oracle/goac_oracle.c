@@ -27,6 +27,12 @@
  *                          pinned: Eq. 2 energy equals direct Ewald energy;
  *                          sub-structure coefficients equal J-based ones.
  *   orc_delta_E            pinned: equals E(after) - E(before).
+ *   orc_hybrid_run         pinned: composition of orc_remc_run and orc_ga_run
+ *                          (checked against calling them in turn); finds the
+ *                          brute-forced minimum.
+ *   orc_gd_run             pinned: result is a local minimum by brute force over
+ *                          all swaps; energies non-increasing; ground state is
+ *                          a fixed point.
  *   orc_sa_run             pinned: constant schedule equals orc_mc_run; kT -> 0
  *                          end is a descent; schedule endpoints.
  *   orc_remc_run           pinned: detailed balance of the exchange (two-level
@@ -1154,5 +1160,104 @@ int orc_remc_run(const double* J, int64_t N, const int32_t* site_class, const do
     }
     if (n_exchanges) *n_exchanges = nex;
     free(kT);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient descent over single-swap neighbours (SI, Gradient Descent: all  */
+/* neighbours reachable by one swap are evaluated and the lowest is taken    */
+/* until no neighbour is lower).  Each step: dE for every pair a < b of      */
+/* variable sites of the same class holding different species; dmin = min;  */
+/* if dmin < -1e-9 eV the step swaps the lowest pair (a, b) (lexicographic)  */
+/* whose dE <= dmin + 1e-9 eV (energy ties within rounding resolve by index),*/
+/* else the chain is at a local minimum.  At most max_steps steps.           */
+/* ------------------------------------------------------------------------ */
+int orc_gd_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+               int8_t* species, int64_t C, int64_t max_steps, double* E_out, int64_t* steps_out)
+{
+    classes_t cl = make_classes(site_class, N);
+    int64_t nv = cl.nv;
+    double* q = (double*)malloc(sizeof(double) * (size_t)N);
+    double* phi = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    for (int64_t ch = 0; ch < C; ++ch) {
+        int8_t* sp = species + ch * nv;
+        orc_config_charges(N, site_class, fixed_q, z, sp, q);
+        double E = orc_qJq(J, q, N);
+        for (int64_t w = 0; w < nv; ++w) {
+            int64_t i = cl.vsite[w];
+            double s = 0.0;
+            for (int64_t j = 0; j < N; ++j) s += J[i * N + j] * q[j];
+            phi[w] = s;
+        }
+        int64_t steps = 0;
+        while (steps < max_steps) {
+            double dmin = INFINITY;
+            for (int pass = 0; pass < 2; ++pass) {
+                int64_t ba = -1, bb = -1;
+                for (int64_t a = 0; a < nv && ba < 0; ++a)
+                    for (int64_t b = a + 1; b < nv; ++b) {
+                        if (cl.vclass[a] != cl.vclass[b] || sp[a] == sp[b]) continue;
+                        int64_t ia = cl.vsite[a], ib = cl.vsite[b];
+                        double d = z[sp[b]] - z[sp[a]];
+                        double dE = 2.0 * d * (phi[a] - phi[b]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
+                        if (pass == 0) {
+                            if (dE < dmin) dmin = dE;
+                        } else if (dE <= dmin + ORC_DE_ZERO) {
+                            ba = a;
+                            bb = b;
+                            break;
+                        }
+                    }
+                if (pass == 0 && !(dmin < -ORC_DE_ZERO)) goto done;
+                if (pass == 1) {
+                    int64_t ia = cl.vsite[ba], ib = cl.vsite[bb];
+                    int sa = sp[ba], sb = sp[bb];
+                    double d = z[sb] - z[sa];
+                    double dE = 2.0 * d * (phi[ba] - phi[bb]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
+                    sp[ba] = (int8_t)sb;
+                    sp[bb] = (int8_t)sa;
+                    for (int64_t w = 0; w < nv; ++w) {
+                        int64_t i = cl.vsite[w];
+                        phi[w] = phi[w] + d * (J[i * N + ia] - J[i * N + ib]);
+                    }
+                    E = E + dE;
+                }
+            }
+            steps++;
+        }
+    done:
+        if (E_out) E_out[ch] = E;
+        if (steps_out) steps_out[ch] = steps;
+    }
+    free(q);
+    free(phi);
+    free_classes(&cl);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hybrid heuristic (SI, Hybrid Methods: REMC and GA are called alternately  */
+/* and the best solutions are passed on).  P = G R configurations; cycle c:  */
+/* REMC (n_rounds rounds of steps_per_round steps, key seed + 2c) on all P,  */
+/* then n_gen GA generations (key seed + 2c + 1, generations numbered from   */
+/* c n_gen, elitism keeps the best) starting from the REMC configurations;   */
+/* the GA population (elites first) starts the next cycle's REMC.            */
+/* ------------------------------------------------------------------------ */
+int orc_hybrid_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                   int8_t* species, int64_t G, int64_t R, const double* kT_ladder, int64_t n_cycles,
+                   int64_t n_rounds, int64_t steps_per_round, int64_t n_gen, int64_t n_elite, uint32_t p_mut_u32,
+                   uint64_t seed, double* E_out)
+{
+    int64_t P = G * R;
+    int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P + 1));
+    for (int64_t c = 0; c < n_cycles; ++c) {
+        int rc = orc_remc_run(J, N, site_class, fixed_q, z, species, G, R, kT_ladder, n_rounds, steps_per_round,
+                              seed + 2 * (uint64_t)c, E_out, perm, NULL);
+        if (rc == 0)
+            rc = orc_ga_run(J, N, site_class, fixed_q, z, species, E_out, P, n_gen, n_elite, p_mut_u32,
+                            seed + 2 * (uint64_t)c + 1, (uint32_t)(c * n_gen));
+        if (rc) { free(perm); return rc; }
+    }
+    free(perm);
     return 0;
 }

@@ -239,6 +239,14 @@ class Problem:
                                _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)), "goac_mc_run")
         return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
 
+    def gd_run(self, species: torch.Tensor, max_steps: int):
+        """Steepest descent over single swaps, in place on `species`.  Returns (E, steps)."""
+        B = species.shape[0]
+        E = torch.empty(B, dtype=torch.float64, device=self._dev())
+        steps = torch.empty(B, dtype=torch.int64, device=self._dev())
+        _check(lib.goac_gd_run(self.handle, _ptr(species), B, int(max_steps), _ptr(E), _ptr(steps)), "goac_gd_run")
+        return E, steps
+
     def sa_run(self, species: torch.Tensor, kT0, kT1, total_steps: int, n_steps: int, seed: int, step0: int = 0,
                precision="f64"):
         """Simulated annealing in place on `species` (exponential schedule kT0 -> kT1 over total_steps)."""
@@ -267,6 +275,16 @@ class Problem:
                                  int(steps_per_round), int(seed), _prec(precision), _ptr(E), _ptr(perm),
                                  C.byref(nex)), "goac_remc_run")
         return E, perm, int(nex.value)
+
+    def hybrid_run(self, species: torch.Tensor, G: int, R: int, kT_ladder, n_cycles: int, n_rounds: int,
+                   steps_per_round: int, n_gen: int, n_elite: int, p_mut_u32: int, seed: int, precision="f64"):
+        """REMC <-> GA alternation in place on `species` (G R x Nv); returns final energies."""
+        lad = np.ascontiguousarray(kT_ladder, dtype=np.float64)
+        E = torch.empty(G * R, dtype=torch.float64, device=self._dev())
+        _check(lib.goac_hybrid_run(self.handle, _ptr(species), int(G), int(R), _ptr(lad), int(n_cycles),
+                                   int(n_rounds), int(steps_per_round), int(n_gen), int(n_elite), int(p_mut_u32),
+                                   int(seed), _prec(precision), _ptr(E)), "goac_hybrid_run")
+        return E
 
     # ---- genetic algorithm ----------------------------------------------
     def ga_generation(self, pop: torch.Tensor, E: torch.Tensor, n_elite: int, p_mut_u32: int, gen: int, seed: int,

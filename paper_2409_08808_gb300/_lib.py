@@ -48,6 +48,8 @@ SIGNATURES = {
     "goac_topk_rescore": (_st, [_p, _p, _i32, _p, _i32, _p, _p]),
     "goac_random_configs": (_st, [_p, _i32, _u64, _p]),
     "goac_mc_run": (_st, [_p, _p, _i32, _p, _i64, _u64, _u64, _i32, _p, _p, _p, _p]),
+    "goac_gd_run": (_st, [_p, _p, _i32, _i32, _p, _p]),
+    "goac_hybrid_run": (_st, [_p, _p, _i32, _i32, _p, _i32, _i32, _i64, _i32, _i32, _u32, _u64, _i32, _p]),
     "goac_sa_run": (_st, [_p, _p, _i32, _p, _p, _i64, _i64, _u64, _u64, _i32, _p, _p, _p, _p]),
     "goac_remc_run": (_st, [_p, _p, _i32, _i32, _p, _i32, _i64, _u64, _i32, _p, _p, _p]),
     "goac_batch_mc_run": (_st, [_p, _p, _i32, _p, _p, _p, _i64, _u64, _u64, _i32, _p, _p, _i32, _i32]),

@@ -1,0 +1,242 @@
+// Gradient descent over single-swap neighbours (SI, Gradient Descent: all
+// neighbouring solutions reachable by one swap are evaluated and the lowest
+// energy one is taken until none is lower), for a batch of configurations.
+//
+// Per step and configuration: dE(a, b) = 2 d (phi_a - phi_b) + d^2 (J_aa + J_bb
+// - 2 J_ab), d = q_b - q_a, over every pair a < b of the same class holding
+// different species.  Pass 0 finds dmin; a configuration with dmin >= -1e-9 eV
+// is at a local minimum.  Pass 1 finds the lowest pair (a, b) (lexicographic)
+// with dE <= dmin + 1e-9 eV (ties within rounding resolve by index), which is
+// then swapped: phi += d (J_:a - J_:b), E += dE.
+//
+// The pair scan is a tile computation over the upper triangle of 64 x 64
+// blocks of J_vv: each CTA stages its J tile in shared memory once and
+// evaluates it for GD_CFG configurations; per-tile candidates are reduced per
+// configuration in a fixed order.  FP64 with explicitly rounded operations in
+// the order of the definition.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int GT = 64;        // tile edge (sites)
+constexpr int GD_CFG = 4;     // configurations per CTA
+constexpr double kTie = 1e-9; // energy tie tolerance (eV)
+
+struct GdArgs {
+    const double* J;          // Nv_pad x ld
+    const double* diag;       // Nv
+    const int8_t* species;    // B x Nv
+    const double* phi;        // B x Nv
+    const int32_t* vclass;    // Nv
+    const double* z;          // 64
+    const int* active;        // B
+    const double* dmin;       // B (pass 1)
+    double* cand_val;         // ntiles x B
+    unsigned long long* cand_key;   // ntiles x B
+    int ld, Nv, B, ntiles;
+};
+
+__device__ __forceinline__ double pair_dE(double d, double pa, double pb, double jaa, double jbb, double jab)
+{
+    return __dadd_rn(__dmul_rn(__dmul_rn(2.0, d), __dsub_rn(pa, pb)),
+                     __dmul_rn(__dmul_rn(d, d), __dsub_rn(__dadd_rn(jaa, jbb), __dmul_rn(2.0, jab))));
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
+{
+    __shared__ double Jt[GT][GT + 1];
+    __shared__ double phI[GD_CFG][GT], phJ[GD_CFG][GT];
+    __shared__ int8_t spI[GD_CFG][GT], spJ[GD_CFG][GT];
+    __shared__ int clI[GT], clJ[GT];
+    __shared__ double dgI[GT], dgJ[GT];
+    __shared__ double redv[256];
+    __shared__ unsigned long long redk[256];
+    int t = blockIdx.x;
+    int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    while (bj * (bj + 1) / 2 > t) --bj;
+    const int bi = t - bj * (bj + 1) / 2;
+    const int i0 = bi * GT, j0 = bj * GT;
+    const int c0 = blockIdx.y * GD_CFG;
+    for (int e = threadIdx.x; e < GT * GT; e += 256) {
+        const int r = e / GT, c = e % GT;
+        Jt[r][c] = g.J[(long)(i0 + r) * g.ld + j0 + c];
+    }
+    for (int e = threadIdx.x; e < GT; e += 256) {
+        const bool vi = i0 + e < g.Nv, vj = j0 + e < g.Nv;
+        clI[e] = vi ? g.vclass[i0 + e] : -1;
+        clJ[e] = vj ? g.vclass[j0 + e] : -2;
+        dgI[e] = vi ? g.diag[i0 + e] : 0.0;
+        dgJ[e] = vj ? g.diag[j0 + e] : 0.0;
+    }
+    for (int e = threadIdx.x; e < GD_CFG * GT; e += 256) {
+        const int c = e / GT, x = e % GT, b = c0 + c;
+        const bool okb = b < g.B;
+        phI[c][x] = okb && i0 + x < g.Nv ? g.phi[(long)b * g.Nv + i0 + x] : 0.0;
+        phJ[c][x] = okb && j0 + x < g.Nv ? g.phi[(long)b * g.Nv + j0 + x] : 0.0;
+        spI[c][x] = okb && i0 + x < g.Nv ? g.species[(long)b * g.Nv + i0 + x] : (int8_t)-1;
+        spJ[c][x] = okb && j0 + x < g.Nv ? g.species[(long)b * g.Nv + j0 + x] : (int8_t)-1;
+    }
+    __syncthreads();
+    const int ii = threadIdx.x % GT;
+    const int jq = (threadIdx.x / GT) * 16;
+    for (int c = 0; c < GD_CFG; ++c) {
+        const int b = c0 + c;
+        const bool live = b < g.B && g.active[b];   // uniform over the block
+        if (!live) continue;
+        const double lim = PASS == 1 ? g.dmin[b] + kTie : 0.0;
+        double best = INFINITY;
+        unsigned long long key = ~0ull;
+        const int a = i0 + ii;
+        const int sa = spI[c][ii];
+        for (int jj = jq; jj < jq + 16; ++jj) {
+            const int bb = j0 + jj;
+            if (!(a < bb) || clI[ii] != clJ[jj]) continue;
+            const int sb = spJ[c][jj];
+            if (sa == sb || sa < 0 || sb < 0) continue;
+            const double d = __dsub_rn(g.z[sb], g.z[sa]);
+            const double dE = pair_dE(d, phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj], Jt[ii][jj]);
+            if (PASS == 0) {
+                if (dE < best) best = dE;
+            } else if (dE <= lim) {
+                const unsigned long long k = (unsigned long long)a * (unsigned long long)g.Nv + (unsigned long long)bb;
+                if (k < key) key = k;
+            }
+        }
+        redv[threadIdx.x] = best;
+        redk[threadIdx.x] = key;
+        __syncthreads();
+        for (int w = 128; w; w >>= 1) {
+            if (threadIdx.x < w) {
+                redv[threadIdx.x] = fmin(redv[threadIdx.x], redv[threadIdx.x + w]);
+                redk[threadIdx.x] = min(redk[threadIdx.x], redk[threadIdx.x + w]);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (PASS == 0) g.cand_val[(long)blockIdx.x * g.B + b] = redv[0];
+            else g.cand_key[(long)blockIdx.x * g.B + b] = redk[0];
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per configuration: reduce the tile candidates; pass 0 retires
+// configurations at a local minimum, pass 1 applies the chosen swap.
+template <int PASS>
+__global__ void k_gd_apply(GdArgs g, const double* __restrict__ Jfull, int8_t* __restrict__ species,
+                           double* __restrict__ phi, int* __restrict__ active, double* __restrict__ dmin,
+                           double* __restrict__ E, long long* __restrict__ steps, int* __restrict__ n_active)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= g.B || !active[b]) return;
+    if (PASS == 0) {
+        double m = INFINITY;
+        for (int t = lane; t < g.ntiles; t += 32) m = fmin(m, g.cand_val[(long)t * g.B + b]);
+        for (int o = 16; o; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            dmin[b] = m;
+            if (!(m < -kTie)) active[b] = 0;
+            else atomicAdd(n_active, 1);
+        }
+        return;
+    }
+    unsigned long long k = ~0ull;
+    for (int t = lane; t < g.ntiles; t += 32) k = min(k, g.cand_key[(long)t * g.B + b]);
+    for (int o = 16; o; o >>= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+    const int a = (int)(k / (unsigned long long)g.Nv), c = (int)(k % (unsigned long long)g.Nv);
+    int8_t* sp = species + (long)b * g.Nv;
+    double* ph = phi + (long)b * g.Nv;
+    const int sa = sp[a], sc = sp[c];
+    const double d = __dsub_rn(g.z[sc], g.z[sa]);
+    const double dE = pair_dE(d, ph[a], ph[c], g.diag[a], g.diag[c], Jfull[(long)a * g.ld + c]);
+    __syncwarp();
+    const double* ra = Jfull + (long)a * g.ld;
+    const double* rc = Jfull + (long)c * g.ld;
+    for (int w = lane; w < g.Nv; w += 32) ph[w] = __dadd_rn(ph[w], __dmul_rn(d, __dsub_rn(ra[w], rc[w])));
+    __syncwarp();
+    if (lane == 0) {
+        sp[a] = (int8_t)sc;
+        sp[c] = (int8_t)sa;
+        E[b] = E[b] + dE;
+        steps[b] += 1;
+    }
+}
+
+__global__ void k_gd_init(int B, int* active, long long* steps)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) {
+        active[b] = 1;
+        steps[b] = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t B, int32_t max_steps,
+                                   double* E_dev, int64_t* steps_dev)
+{
+    if (!p || !species_dev || !E_dev || !steps_dev || B < 0 || max_steps < 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_gd_run: bad argument");
+    if (B == 0) return GOAC_OK;
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    goac_ctx* ctx = p->ctx;
+    cudaStream_t st = ctx->stream;
+    const int nb = (p->Nv + GT - 1) / GT;
+    const int ntiles = nb * (nb + 1) / 2;
+    const size_t need = sizeof(double) * (size_t)B * p->Nv + sizeof(double) * (size_t)ntiles * B +
+                        sizeof(unsigned long long) * (size_t)ntiles * B + sizeof(double) * B + sizeof(int) * (B + 4) +
+                        1024;
+    goac_status rc = goac::ensure(p->grad_tmp, need);
+    if (rc) return rc;
+    double* phi = (double*)p->grad_tmp.ptr;
+    double* cval = phi + (size_t)B * p->Nv;
+    unsigned long long* ckey = (unsigned long long*)(cval + (size_t)ntiles * B);
+    double* dmin = (double*)(ckey + (size_t)ntiles * B);
+    int* active = (int*)(dmin + B);
+    int* n_active = active + B;
+    rc = goac::score_f64(p, species_dev, B, E_dev, phi);
+    if (rc) return rc;
+    goac::launch(k_gd_init, (B + 255) / 256, 256, 0, st, B, active, (long long*)steps_dev);
+    GdArgs g;
+    g.J = p->J_vv;
+    g.diag = p->diag;
+    g.species = species_dev;
+    g.phi = phi;
+    g.vclass = p->vclass_dev;
+    g.z = p->z_dev;
+    g.active = active;
+    g.dmin = dmin;
+    g.cand_val = cval;
+    g.cand_key = ckey;
+    g.ld = p->Nv_pad;
+    g.Nv = p->Nv;
+    g.B = B;
+    g.ntiles = ntiles;
+    dim3 grid(ntiles, (B + GD_CFG - 1) / GD_CFG);
+    const int ablocks = (B + 7) / 8;
+    for (int s = 0; s < max_steps; ++s) {
+        GOAC_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+        goac::launch(k_gd_pairs<0>, grid, 256, 0, st, g);
+        goac::launch(k_gd_apply<0>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
+                     E_dev, (long long*)steps_dev, n_active);
+        goac::launch(k_gd_pairs<1>, grid, 256, 0, st, g);
+        goac::launch(k_gd_apply<1>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
+                     E_dev, (long long*)steps_dev, n_active);
+        GOAC_LAUNCH_CHECK("gd step");
+        if ((s & 7) == 7 || s + 1 == max_steps) {
+            int h = 0;
+            GOAC_CUDA(cudaMemcpyAsync(&h, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GOAC_CUDA(cudaStreamSynchronize(st));
+            if (h == 0) break;
+        }
+    }
+    return GOAC_OK;
+}

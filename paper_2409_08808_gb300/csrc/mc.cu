@@ -738,3 +738,32 @@ extern "C" goac_status goac_batch_mc_autotune(goac_ctx* ctx, goac_problem* const
     if (best_ms) *best_ms = best_t;
     return GOAC_OK;
 }
+
+// Hybrid heuristic (SI, Hybrid Methods): n_cycles of replica exchange on all
+// P = G R configurations followed by n_gen GA generations on them; the GA
+// population (elites first) starts the next cycle's replica exchange.  Keys:
+// seed + 2c for the exchange cycle c, seed + 2c + 1 for its GA (generations
+// numbered from c n_gen).
+extern "C" goac_status goac_hybrid_run(goac_problem* p, int8_t* species_dev, int32_t G, int32_t R,
+                                       const double* kT_ladder_host, int32_t n_cycles, int32_t n_rounds,
+                                       int64_t steps_per_round, int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32,
+                                       uint64_t seed, int32_t precision, double* E_dev)
+{
+    if (!p || !species_dev || !kT_ladder_host || !E_dev || G <= 0 || R <= 0 || n_cycles < 0 || n_gen < 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_hybrid_run: bad argument");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const int P = G * R;
+    DevBuf perm;
+    goac_status rc = goac::ensure(perm, sizeof(int32_t) * (size_t)P);
+    if (rc) return rc;
+    for (int c = 0; c < n_cycles && rc == GOAC_OK; ++c) {
+        rc = goac_remc_run(p, species_dev, G, R, kT_ladder_host, n_rounds, steps_per_round, seed + 2 * (uint64_t)c,
+                           precision, E_dev, (int32_t*)perm.ptr, nullptr);
+        if (rc == GOAC_OK)
+            rc = goac_ga_run(p, species_dev, E_dev, P, n_gen, n_elite, p_mut_u32, seed + 2 * (uint64_t)c + 1,
+                             (uint32_t)(c * n_gen), GOAC_PREC_F64);
+    }
+    cudaStreamSynchronize(p->ctx->stream);
+    cudaFree(perm.ptr);
+    return rc;
+}

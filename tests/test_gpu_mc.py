@@ -183,3 +183,34 @@ def test_remc_parity(ctx):
     assert np.array_equal(perm.cpu().numpy(), ref["perm"])
     assert np.array_equal(sp.cpu().numpy(), ref["species"])
     assert np.allclose(E.cpu().numpy(), ref["E"], rtol=1e-10)
+
+
+@pytest.mark.parametrize("which,B", [("rocksalt", 8), ("layered", 5)])
+def test_gd_parity(ctx, which, B):
+    """All-pairs steepest descent: same end configurations, steps and energies
+    as the oracle (ties within 1e-9 eV resolve to the lowest pair on both sides)."""
+    prob = {"rocksalt": lambda: synth.rocksalt_problem((2, 2, 2), 4.2),
+            "layered": lambda: synth.layered_problem(reps=(2, 2, 1))}[which]()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, B, 19)
+    ref = oracle.gd_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 500)
+    sp = torch.tensor(start, device="cuda")
+    E, steps = gp.gd_run(sp, 500)
+    assert np.array_equal(steps.cpu().numpy(), ref["steps"])
+    assert np.array_equal(sp.cpu().numpy(), ref["species"])
+    assert np.allclose(E.cpu().numpy(), ref["E"], rtol=1e-10)
+    assert ref["steps"].max() > 3
+
+
+def test_hybrid_parity(ctx):
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 8, 23)
+    lad = [0.05, 0.15, 0.4, 1.0]
+    ref = oracle.hybrid_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 2, 4, lad, 2, 3, 300, 3, 1, 0.2, seed=7)
+    sp = torch.tensor(start, device="cuda")
+    E = gp.hybrid_run(sp, 2, 4, lad, 2, 3, 300, 3, 1, oracle.p_mut_to_u32(0.2), 7)
+    assert np.array_equal(sp.cpu().numpy(), ref["species"])
+    assert np.allclose(E.cpu().numpy(), ref["E"], rtol=1e-10)

@@ -71,3 +71,43 @@ def test_remc_exchange_acceptance(tiny):
     assert abs(frac - p) < 4 * math.sqrt(p * (1 - p) / G)
     perm = r["perm"].reshape(G, 2)
     assert np.all(np.sort(perm, axis=1) == np.arange(G * 2).reshape(G, 2))
+
+
+def test_gd_reaches_local_minimum(tiny):
+    """Every swap from the descent's end point raises the energy (checked by
+    fresh q^T J q evaluations); energies never increase; the brute-forced
+    ground state is a fixed point."""
+    prob, J = tiny
+    start = synth.random_population(prob, 6, 14)
+    E0 = oracle.score(J, prob.site_class, prob.fixed_q, prob.z, start)
+    r = oracle.gd_run(J, prob.site_class, prob.fixed_q, prob.z, start, 100)
+    assert np.all(r["E"] <= E0 + 1e-9) and np.all(r["steps"] < 100)
+    assert np.allclose(r["E"], oracle.score(J, prob.site_class, prob.fixed_q, prob.z, r["species"]), rtol=1e-12)
+    for c in range(6):
+        base = r["species"][c]
+        Eb = oracle.score(J, prob.site_class, prob.fixed_q, prob.z, base[None])[0]
+        for a in range(8):
+            for b in range(a + 1, 8):
+                if base[a] == base[b]:
+                    continue
+                t = base.copy()
+                t[a], t[b] = base[b], base[a]
+                assert oracle.score(J, prob.site_class, prob.fixed_q, prob.z, t[None])[0] >= Eb - 1e-9
+    gs = oracle.enumerate_all(J, prob.site_class, prob.fixed_q, prob.z, prob.counts, max_argmin=1)["argmin"][0]
+    r2 = oracle.gd_run(J, prob.site_class, prob.fixed_q, prob.z, gs[None], 10)
+    assert r2["steps"][0] == 0 and np.array_equal(r2["species"][0], gs)
+
+
+def test_hybrid_is_remc_then_ga(tiny):
+    prob, J = tiny
+    start = synth.random_population(prob, 8, 31)
+    lad = [0.1, 0.3, 0.6, 1.2]
+    h = oracle.hybrid_run(J, prob.site_class, prob.fixed_q, prob.z, start, 2, 4, lad, 2, 3, 50, 4, 1, 0.2, seed=5)
+    sp = start.copy()
+    for c in range(2):
+        r = oracle.remc_run(J, prob.site_class, prob.fixed_q, prob.z, sp, 2, 4, lad, 3, 50, seed=5 + 2 * c)
+        sp, E = oracle.ga_run(J, prob.site_class, prob.fixed_q, prob.z, r["species"], 4, 1, 0.2, seed=5 + 2 * c + 1,
+                              gen0=c * 4)
+    assert np.array_equal(h["species"], sp) and np.allclose(h["E"], E, rtol=1e-13)
+    emin = oracle.enumerate_all(J, prob.site_class, prob.fixed_q, prob.z, prob.counts)["Emin"]
+    assert h["E"].min() == pytest.approx(emin, rel=1e-12)
