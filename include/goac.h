@@ -53,6 +53,7 @@ typedef int32_t goac_status;
 #define GOAC_PREC_BF16X2 3  /* tcgen05 kind::f16 (BF16), J = J1 + J2             */
 #define GOAC_PREC_BF16X3 4  /* tcgen05 kind::f16 (BF16), J = J1 + J2 + J3        */
 #define GOAC_PREC_F32 5     /* FP32 CUDA cores (Monte Carlo / GA variant only)   */
+#define GOAC_PREC_EXACT 6   /* tcgen05 integer-digit split (FP64-grade, see below) */
 
 typedef struct goac_ctx goac_ctx;
 typedef struct goac_problem goac_problem;
@@ -133,7 +134,12 @@ goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
  *   E_b = q_b^T J_vv q_b + 2 q_b . phi_fix + E_const.                       *
  *   species_dev: B x Nv int8.  E_dev: B doubles.  precision: GOAC_PREC_*.   *
  * F64 is the plain path; the tensor-core forms split J into TF32 / BF16     *
- * terms, accumulate J.Q in FP32 on tcgen05 and form E in FP64.              *
+ * terms, accumulate J.Q in FP32 on tcgen05 and form E in FP64.  EXACT      *
+ * (integer charges after a power-of-two scaling, 128 max|q| Nv < 2^24, else  *
+ * GOAC_ERR_UNSUPPORTED): each 64-row panel of J is scaled by a power of two   *
+ * and cut into six signed 8-bit digits, so every tensor-core product and     *
+ * partial sum is an integer below 2^24 and exact; digits are combined with   *
+ * 64-bit integers and FP64 (truncation 2^-48 of the panel's largest entry).  *
  * ------------------------------------------------------------------------ */
 goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
 

@@ -105,10 +105,15 @@ struct goac_problem {
     float* diag_f32 = nullptr;
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
-    // persistent tensor-core schedule (device copy) for the last shape
-    DevBuf sched;
-    uint64_t sched_key = 0;
-    int sched_tiles = 0;
+    // persistent tensor-core schedules (device copies) for the last shapes
+    DevBuf sched, sched_ex;
+    uint64_t sched_key = 0, sched_ex_key = 0;
+    int sched_tiles = 0, sched_ex_tiles = 0;
+    // exact form: digits of the symmetric operand, panel exponents, scaled charges
+    __nv_bfloat16* J_dig = nullptr;    // [6][Nv_pad][Nv_pad]
+    int* dig_exp = nullptr;            // Nv_pad / 64
+    double* zq_dev = nullptr;          // 64, charges times 2^dig_kq
+    int dig_kq = -1;
 };
 
 // ---------------------------------------------------------------------------

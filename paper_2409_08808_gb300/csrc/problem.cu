@@ -714,6 +714,10 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->topk_tmp);
     free_buf(p->grad_tmp);
     free_buf(p->sched);
+    free_buf(p->sched_ex);
+    cudaFree(p->J_dig);
+    cudaFree(p->dig_exp);
+    cudaFree(p->zq_dev);
     delete p;
     return GOAC_OK;
 }
@@ -747,7 +751,8 @@ extern "C" goac_status goac_score(goac_problem* p, const int8_t* species_dev, in
         case GOAC_PREC_TF32:
         case GOAC_PREC_TF32X2:
         case GOAC_PREC_BF16X2:
-        case GOAC_PREC_BF16X3: return goac::score_tc(p, species_dev, B, precision, E_dev);
+        case GOAC_PREC_BF16X3:
+        case GOAC_PREC_EXACT: return goac::score_tc(p, species_dev, B, precision, E_dev);
         default: return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: unknown precision");
     }
 }

@@ -23,6 +23,8 @@
 // m-tiles in a fixed order plus the linear term and E_const (deterministic).
 #include <cudaTypedefs.h>
 
+#include <math.h>
+
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -382,6 +384,223 @@ __global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact form: integer-digit split of the symmetric operand on tcgen05.
+// J' at 64-block granularity (J'_II = J_II, J'_IJ = 2 J_IJ for I < J, 0
+// below) is scaled per 64-row panel I by 2^-e_I (|J'| <= 2^e_I) and written as
+// six signed digits, J'/2^e_I = 2^-7 sum_t a_t 2^-8t + r, a_t in [-128, 128]
+// (exact in BF16), |r| <= 2^-48.  Charges are integers after a power-of-two
+// scaling, so every product a_t q and every partial sum over <= Nv_pad sites
+// is an integer below 2^24: the FP32 accumulators hold the digit sums exactly.
+// Tile = (panel I of 64 sites, 128 configurations): M = configurations (TMEM
+// lanes), N = 64 sites per digit, six accumulators at columns 64 t.  The
+// epilogue forms P_t = sum_i q_bi Phi_t,bi in 64-bit integers and the panel's
+// contribution 2^(e_I - 7) sum_t 2^-8t P_t in FP64.
+constexpr int EX_T = 6;                        // digits
+constexpr int EX_N = 64;                       // sites per tile
+constexpr int EX_M = 128;                      // configurations per tile
+constexpr int EX_A = EX_M * ROW_BYTES;         // 16 KB (Q^T tile)
+constexpr int EX_B = EX_N * ROW_BYTES;         // 8 KB per digit tile
+constexpr int EX_STAGE = EX_A + EX_T * EX_B;   // 64 KB
+constexpr int EX_STAGES = 3;
+constexpr int EX_SMEM = EX_STAGES * EX_STAGE + 1024 + 256;
+
+__global__ void __launch_bounds__(192, 1)
+    k_score_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int ld,
+                  const __nv_bfloat16* __restrict__ qt, const int* __restrict__ panel_exp, double* __restrict__ partial,
+                  int Bpad, int* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + EX_STAGES * EX_STAGE);
+    uint64_t* empty = full + EX_STAGES;
+    uint64_t* tfull = empty + EX_STAGES;
+    uint64_t* tempty = tfull + 1;
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < EX_STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        goacd::mbar_init(tfull, 1);
+        goacd::mbar_init(tempty, 4);
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc(tmem_slot, 512);
+        goacd::tmem_relinquish();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
+                const int2 tile = work[wi];                 // x = panel, y = configuration block
+                for (int kb = tile.x; kb < nkb_total; ++kb, ++it) {
+                    const int s = it % EX_STAGES;
+                    const uint32_t use = (uint32_t)(it / EX_STAGES);
+                    if (it >= EX_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * EX_STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], EX_STAGE);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 64, tile.y * EX_M);
+#pragma unroll
+                    for (int t = 0; t < EX_T; ++t)
+                        goacd::tma_load_2d(st + EX_A + t * EX_B, &tmB, &full[s], kb * 64, t * ld + tile.x * EX_N);
+                }
+            }
+            if (*abort_flag)
+                for (int k = it - EX_STAGES < 0 ? 0 : it - EX_STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % EX_STAGES], (uint32_t)(k / EX_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, EX_M, EX_N);
+            int it = 0, tl = 0;
+            for (int wi = w0; wi < w1; ++wi, ++tl) {
+                const int2 tile = work[wi];
+                if (tl >= 1 && !goacd::mbar_wait_bounded(tempty, (uint32_t)(tl - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
+                }
+                goacd::tc_fence_after();
+                for (int kb = tile.x; kb < nkb_total; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % EX_STAGES;
+                    const uint32_t use = (uint32_t)(it / EX_STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t a0 = goacd::smem_u32(smem + s * EX_STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = goacd::sdesc_k128(a0 + kk * 32);
+#pragma unroll
+                        for (int t = 0; t < EX_T; ++t) {
+                            const uint64_t bd = goacd::sdesc_k128(a0 + EX_A + t * EX_B + kk * 32);
+                            goacd::mma_bf16(tmem + (uint32_t)(t * EX_N), ad, bd, idesc,
+                                            (kb != tile.x || kk != 0) ? 1u : 0u);
+                        }
+                    }
+                    goacd::mma_commit(&empty[s]);
+                }
+                goacd::mma_commit(tfull);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int lg = warp & 3;
+        const int etid = threadIdx.x - 64;
+        (void)etid;
+        int tl = 0;
+        for (int wi = w0; wi < w1; ++wi, ++tl) {
+            const int2 tile = work[wi];
+            const bool ok = goacd::mbar_wait_bounded(tfull, (uint32_t)tl & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            const int b = tile.y * EX_M + lg * 32 + lane;
+            // this configuration's 64 charges of the panel (integers)
+            int q[EX_N];
+            {
+                const int4* src = (const int4*)(qt + (long)b * ld + tile.x * EX_N);
+#pragma unroll
+                for (int u = 0; u < EX_N / 8; ++u) {
+                    const int4 v = src[u];
+                    const __nv_bfloat16* h = (const __nv_bfloat16*)&v;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) q[8 * u + e] = __float2int_rn(__bfloat162float(h[e]));
+                }
+            }
+            double acc = 0.0;
+#pragma unroll 1
+            for (int t = EX_T - 1; t >= 0; --t) {
+                long long P = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t r[32];
+                    goacd::tmem_ld_32x32b_x32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(t * EX_N + h * 32), r);
+                    goacd::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        P += (long long)q[h * 32 + j] * (long long)__float2int_rn(__uint_as_float(r[j]));
+                }
+                acc += ldexp((double)P, -8 * t);       // exact scaling; smallest digit first
+            }
+            goacd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) goacd::mbar_arrive(tempty);
+            if (ok) partial[(long)tile.x * Bpad + b] = ldexp(acc, panel_exp[tile.x] - 7);
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc(tmem, 512);
+    }
+}
+
+// Per 64-row panel I of the symmetric operand: e_I with max |J'| <= 2^e_I.
+__global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restrict__ pexp)
+{
+    __shared__ double red[256];
+    const int I = blockIdx.x;
+    double m = 0.0;
+    for (long e = threadIdx.x; e < (long)EX_N * ld; e += blockDim.x) {
+        const int r = (int)(e / ld), j = (int)(e % ld);
+        const int i = I * EX_N + r;
+        if (j / EX_N < I) continue;
+        const double v = fabs(J[(long)i * ld + j]) * (j / EX_N > I ? 2.0 : 1.0);
+        m = fmax(m, v);
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int e = 0;
+        if (red[0] > 0.0) frexp(red[0], &e);     // red < 2^e
+        pexp[I] = e;
+    }
+}
+
+__global__ void k_split_digits(const double* __restrict__ J, int ld, const int* __restrict__ pexp,
+                               __nv_bfloat16* __restrict__ out)
+{
+    const long n = (long)ld * ld;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        const int bi = i / EX_N, bj = j / EX_N;
+        double x = bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]);
+        x = ldexp(x, 7 - pexp[bi]);               // |x| <= 128
+#pragma unroll
+        for (int t = 0; t < EX_T; ++t) {
+            const double a = rint(x);
+            out[t * n + e] = __double2bfloat16(a);
+            x = (x - a) * 256.0;
+        }
+    }
+}
+
 // Symmetric operand: J'_ij = J_ij on diagonal 128-blocks, 2 J_ij above them,
 // 0 below, so that q^T J q = sum over the upper block triangle of q_I^T J'_IJ q_J.
 __device__ __forceinline__ double sym_upper(const double* J, long e, int ld)
@@ -439,12 +658,13 @@ __global__ void k_copy_f32(const double* __restrict__ J, long n, float* __restri
 // lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
 template <typename QT>
 __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ species, int B, int Nv,
-                                                 const double* __restrict__ z, int ld, QT* __restrict__ qt,
-                                                 const double* __restrict__ phifix, double* __restrict__ lin)
+                                                 const double* __restrict__ zq, const double* __restrict__ z, int ld,
+                                                 QT* __restrict__ qt, const double* __restrict__ phifix,
+                                                 double* __restrict__ lin)
 {
     __shared__ float zs[64];
     __shared__ double red[256];
-    if (threadIdx.x < 64) zs[threadIdx.x] = (float)z[threadIdx.x];
+    if (threadIdx.x < 64) zs[threadIdx.x] = (float)zq[threadIdx.x];
     __syncthreads();
     const int b = blockIdx.x;
     QT* row = qt + (long)b * ld;
@@ -484,6 +704,16 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
         __syncthreads();
     }
     if (threadIdx.x == 0) lin[b] = red[0];
+}
+
+__global__ void k_finish_exact(const double* __restrict__ partial, int npanels, int Bpad, int B, int kq2,
+                               double E_const, const double* __restrict__ lin, double* __restrict__ E)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int m = 0; m < npanels; ++m) s += partial[(long)m * Bpad + b];
+    E[b] = ldexp(s, -kq2) + (lin ? lin[b] : 0.0) + E_const;
 }
 
 __global__ void k_finish_tc(const double* __restrict__ partial, int mtiles, int Bpad, int B, double E_const,
@@ -533,10 +763,11 @@ goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int e
 
 // Longest-processing-time schedule of the (m-block, n-tile) tiles over the
 // CTAs of a persistent grid; cached per problem for the current shape.
-goac_status tc_schedule(goac_problem* p, int nbm, int nbn, int grid, const int2** work, const int** starts)
+goac_status tc_schedule_into(DevBuf& sched, uint64_t& sched_key, int& sched_tiles, int nbm, int nbn, int grid,
+                             const int2** work, const int** starts)
 {
     const uint64_t key = ((uint64_t)nbm << 40) | ((uint64_t)nbn << 20) | (uint64_t)grid;
-    if (p->sched_key != key) {
+    if (sched_key != key) {
         std::vector<int2> tiles;
         for (int I = 0; I < nbm; ++I)
             for (int n = 0; n < nbn; ++n) tiles.push_back(make_int2(I, n));
@@ -558,18 +789,23 @@ goac_status tc_schedule(goac_problem* p, int nbm, int nbn, int grid, const int2*
         }
         st[grid] = (int)flat.size();
         const size_t bytes = sizeof(int2) * flat.size() + sizeof(int) * (grid + 1) + 64;
-        goac_status rc = goac::ensure(p->sched, bytes);
+        goac_status rc = goac::ensure(sched, bytes);
         if (rc) return rc;
-        int2* dw = (int2*)p->sched.ptr;
+        int2* dw = (int2*)sched.ptr;
         int* ds = (int*)(dw + flat.size());
         GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice));
         GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
-        p->sched_key = key;
-        p->sched_tiles = (int)flat.size();
+        sched_key = key;
+        sched_tiles = (int)flat.size();
     }
-    *work = (const int2*)p->sched.ptr;
-    *starts = (const int*)((const int2*)p->sched.ptr + p->sched_tiles);
+    *work = (const int2*)sched.ptr;
+    *starts = (const int*)((const int2*)sched.ptr + sched_tiles);
     return GOAC_OK;
+}
+
+goac_status tc_schedule(goac_problem* p, int nbm, int nbn, int grid, const int2** work, const int** starts)
+{
+    return tc_schedule_into(p->sched, p->sched_key, p->sched_tiles, nbm, nbn, grid, work, starts);
 }
 
 template <int T, bool TF32>
@@ -664,8 +900,87 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     return GOAC_OK;
 }
 
+// Digits of the symmetric operand and the charge scaling of the exact form.
+static goac_status prepare_exact(goac_problem* p)
+{
+    if (p->J_dig) return GOAC_OK;
+    int kq = -1;
+    double qmax = 0.0;
+    for (int k = 0; k <= 4 && kq < 0; ++k) {
+        bool ok = true;
+        for (double zz : p->z) {
+            const double v = ldexp(zz, k);
+            if (v != rint(v)) ok = false;
+        }
+        if (ok) kq = k;
+    }
+    if (kq < 0) return fail(GOAC_ERR_UNSUPPORTED, "exact form: species charges are not multiples of 1/16");
+    for (double zz : p->z) qmax = std::max(qmax, fabs(ldexp(zz, kq)));
+    if (128.0 * qmax * (double)p->Nv_pad >= 16777216.0)
+        return fail(GOAC_ERR_UNSUPPORTED, "exact form: 128 max|q| Nv exceeds 2^24 (digit sums would not be exact in FP32)");
+    const int ld = p->Nv_pad;
+    const long n = (long)ld * ld;
+    std::vector<double> zq(64, 0.0);
+    for (int s2 = 0; s2 < p->S; ++s2) zq[s2] = ldexp(p->z[s2], kq);
+    GOAC_CUDA(cudaMalloc(&p->zq_dev, sizeof(double) * 64));
+    GOAC_CUDA(cudaMemcpy(p->zq_dev, zq.data(), sizeof(double) * 64, cudaMemcpyHostToDevice));
+    GOAC_CUDA(cudaMalloc(&p->dig_exp, sizeof(int) * (ld / EX_N)));
+    GOAC_CUDA(cudaMalloc(&p->J_dig, sizeof(__nv_bfloat16) * EX_T * (size_t)n));
+    cudaStream_t st = p->ctx->stream;
+    goac::launch(k_panel_exp, ld / EX_N, 256, 0, st, (const double*)p->J_vv, ld, p->dig_exp);
+    const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
+    goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, (const int*)p->dig_exp, p->J_dig);
+    GOAC_LAUNCH_CHECK("exact digits");
+    p->dig_kq = kq;
+    return GOAC_OK;
+}
+
+static goac_status score_exact(goac_problem* p, const int8_t* species, int B, double* E_out)
+{
+    goac_status rc = prepare_exact(p);
+    if (rc) return rc;
+    const int ld = p->Nv_pad;
+    const int Bpad = ((B + EX_M - 1) / EX_M) * EX_M;
+    const int nbm = ld / EX_N, nbn = Bpad / EX_M;
+    rc = ensure(p->qt, (size_t)Bpad * ld * 2);
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * Bpad + Bpad));
+    if (rc) return rc;
+    cudaStream_t st = p->ctx->stream;
+    double* part = (double*)p->partial.ptr;
+    double* lin = p->has_fixed ? part + (size_t)nbm * Bpad : nullptr;
+    goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+                 (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr,
+                 (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
+    GOAC_LAUNCH_CHECK("k_make_qt (exact)");
+    CUtensorMap ma, mb;
+    rc = make_map(&ma, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, EX_M);
+    if (!rc) rc = make_map(&mb, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, EX_N);
+    if (rc) return rc;
+    static bool attr = false;
+    if (!attr) {
+        GOAC_CUDA(cudaFuncSetAttribute(k_score_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, EX_SMEM));
+        attr = true;
+    }
+    const int grid = std::min(nbm * nbn, p->ctx->num_sms);
+    const int2* work = nullptr;
+    const int* starts = nullptr;
+    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn, grid, &work, &starts);
+    if (rc) return rc;
+    {
+        KTimer kt(p->ctx, KID_SCORE_TC, st);
+        goac::launch(k_score_exact, grid, 192, EX_SMEM, st, ma, mb, work, starts, ld / 64, ld,
+                     (const __nv_bfloat16*)p->qt.ptr, (const int*)p->dig_exp, part, Bpad, p->ctx->d_err);
+        GOAC_LAUNCH_CHECK("k_score_exact");
+    }
+    goac::launch(k_finish_exact, (B + 255) / 256, 256, 0, st, (const double*)part, nbm, Bpad, B, 2 * p->dig_kq,
+                 p->E_const, (const double*)lin, E_out);
+    GOAC_LAUNCH_CHECK("k_finish_exact");
+    return GOAC_OK;
+}
+
 goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precision, double* E_out)
 {
+    if (precision == GOAC_PREC_EXACT) return score_exact(p, species, B, E_out);
     goac_status rc = prepare_split(p, precision);
     if (rc) return rc;
     const bool tf32 = precision == GOAC_PREC_TF32 || precision == GOAC_PREC_TF32X2;
@@ -679,9 +994,12 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     double* lin = p->has_fixed ? (double*)p->partial.ptr + (size_t)(ld / TC_M) * Bpad : nullptr;
     {
         const double* pf = p->has_fixed ? p->phifix : nullptr;
-        if (tf32) goac::launch(k_make_qt<float>, Bpad, 256, 0, st, species, B, p->Nv, p->z_dev, ld, (float*)p->qt.ptr, pf, lin);
-        else goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, p->z_dev, ld,
-                                                           (__nv_bfloat16*)p->qt.ptr, pf, lin);
+        if (tf32)
+            goac::launch(k_make_qt<float>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->z_dev,
+                         (const double*)p->z_dev, ld, (float*)p->qt.ptr, pf, lin);
+        else
+            goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->z_dev,
+                         (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, pf, lin);
         GOAC_LAUNCH_CHECK("k_make_qt");
     }
     CUtensorMap ma, mb;

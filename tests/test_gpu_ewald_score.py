@@ -213,3 +213,34 @@ def test_score_full_size_swap_property(ctx):
     R = quad_scale(Jh, prob, pop[:8])
     tol = form_tolerance("bf16x3", R, prob.Nv)
     assert np.all(np.abs(Et1[:8] - E1[:8]) <= tol)
+
+
+@pytest.mark.parametrize("which,B", [("rocksalt", 37), ("layered", 300), ("o3", 129), ("random300", 700)])
+def test_score_exact_form(ctx, which, B):
+    """Integer-digit split: |E_exact - E_oracle| <= sum_ij |q_i||q_j| 2^-47 max|J|
+    (six 8-bit digits per 64-row panel, largest doubled entry scaled to 2^7)."""
+    prob = {"rocksalt": lambda: synth.rocksalt_problem((2, 2, 2), 4.2),
+            "layered": lambda: synth.layered_problem(reps=(3, 3, 1)),
+            "o3": lambda: synth.o3_layered_problem((2, 2, 1)),
+            "random300": lambda: _random_cell_problem(300, 9)}[which]()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, B, 61)
+    Eo = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, pop)
+    Eg = gp.score(torch.tensor(pop, device="cuda"), "exact").cpu().numpy()
+    vidx = np.nonzero(prob.site_class >= 0)[0]
+    qabs = np.abs(prob.z[pop]).sum(axis=1)
+    bound = qabs ** 2 * 2.0 ** -47 * 2 * np.abs(Jo[np.ix_(vidx, vidx)]).max() + 1e-10 * np.abs(Eo)
+    assert np.all(np.abs(Eg - Eo) <= bound), np.max(np.abs(Eg - Eo) / bound)
+    assert np.max(np.abs(Eg - Eo) / np.abs(Eo)) <= 1e-10
+
+
+def test_score_exact_full_size_matches_fp64_path(ctx):
+    import paper_2409_08808_gb300 as g
+    prob = synth.random_cubic_problem()
+    J = g.build_ewald(ctx, prob.lattice, torch.tensor(prob.frac, device="cuda"), prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, J)
+    pop = torch.tensor(synth.random_population(prob, 1000, 71), device="cuda")
+    E64 = gp.score(pop, "f64")
+    Eex = gp.score(pop, "exact")
+    assert ((Eex - E64).abs() / E64.abs()).max().item() <= 1e-11
