@@ -38,7 +38,7 @@ METRIC = "config energy evals/s and MC swap trials/s at N=4096, % roofline, vs F
 N_SIDE = 16          # 16^3 = 4096 sites
 B_POP = 4096
 FORM = "bf16x2"
-TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2}
+TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2, "exact": 6}   # exact: six BF16 digits
 WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +1:512 +2:1024 +3:512 -2:2048), "
             "population B=4096 uniformly random count-preserving configurations")
 
@@ -216,13 +216,18 @@ def _peaks():
     return 1900.0, 6800.0, "fallback"
 
 
-def _kernel_hash() -> str:
-    """Hash of the tensor-core scoring kernel's source (its function body and
-    the device helpers it uses); ncu counters are valid while it is unchanged."""
+def _kernel_hash(form="bf16x2") -> str:
+    """Hash of the tensor-core scoring kernel's source for `form` (its function
+    body and the device helpers it uses); ncu counters are valid while it is
+    unchanged."""
     csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
     src = open(os.path.join(csrc, "score_tc.cu")).read()
-    a = src.index("template <int T, bool TF32>\n__global__ void __launch_bounds__(192, 1)")
-    b = src.index("// Symmetric operand:")
+    if form == "exact":
+        a = src.index("__global__ void __launch_bounds__(192, 1)\n    k_score_exact(")
+        b = src.index("// Per 128-row panel I of the symmetric operand")
+    else:
+        a = src.index("template <int T, bool TF32>\n__global__ void __launch_bounds__(192, 1)")
+        b = src.index("__device__ __forceinline__ float to_tf32_rna(")
     h = hashlib.sha256()
     h.update(src[a:b].encode())
     h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
@@ -236,7 +241,7 @@ def _traffic(form):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("kernel_sha") != _kernel_hash():
+    if d.get("kernel_sha") != _kernel_hash(form):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -306,10 +311,11 @@ def run_ours(args, world, rank, local):
     flops_exec = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * bpad
     flops_useful = 2.0 * prob.N * prob.N * B_POP
     bf16_peak, hbm_peak, peak_kind = _peaks()
-    peak = bf16_peak if form.startswith("bf16") else bf16_peak / 2.0     # TF32 runs at half the BF16 rate
+    peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak     # TF32 runs at half the BF16 rate
     achieved = flops_exec / (kern_avg_ms / 1e3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(form), "kernel": f"k_score_tc<{terms},{'true' if 'tf32' in form else 'false'}>",
+                "traffic": _traffic(form),
+                "kernel": "k_score_exact" if form == "exact" else f"k_score_tc<{terms},{'true' if 'tf32' in form else 'false'}>",
                 "kernel_ms": kern_avg_ms, "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
                 "peak_kind": f"{peak_kind} bf16_tflops (burst)" + (" x 0.5 nominal tf32/bf16 ratio" if "tf32" in form else "")}
 
@@ -541,21 +547,16 @@ def run_suite(args):
         ctx.kernel_time("score_cc")
         box = {}
         ms = timed(lambda: [box.setdefault("E", gp.score(pop, form)) for _ in range(reps)]) / reps
-        kms, kn = ctx.kernel_time("score_tc" if form in TERMS or form == "exact" else "score_cc")
+        kms, kn = ctx.kernel_time("score_tc" if form in TERMS else "score_cc")
         ctx.set_timing(False)
         E = gp.score(pop, form)
         err = (E - E64).abs()
         d = {"ms_per_population": ms, "evals_per_s": B_POP / (ms / 1e3), "speedup_vs_f64": None,
              "max_abs_err_eV": float(err.max()), "rms_abs_err_eV": float(err.pow(2).mean().sqrt()),
              "kernel_ms": kms / max(kn, 1)}
-        if form == "exact":
-            nb64 = ld // 64
-            flops = 6 * 2.0 * 64 * 64 * (nb64 * (nb64 + 1) // 2) * ((B_POP + 127) // 128 * 128)
-            d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
-            d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / bf16_peak
         if form in TERMS:
             flops = TERMS[form] * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
-            peak = bf16_peak if form.startswith("bf16") else bf16_peak / 2.0
+            peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak
             d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
             d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / peak
         forms[form] = d

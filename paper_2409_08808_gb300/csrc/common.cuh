@@ -111,7 +111,7 @@ struct goac_problem {
     int sched_tiles = 0, sched_ex_tiles = 0;
     // exact form: digits of the symmetric operand, panel exponents, scaled charges
     __nv_bfloat16* J_dig = nullptr;    // [6][Nv_pad][Nv_pad]
-    int* dig_exp = nullptr;            // Nv_pad / 64
+    int* dig_exp = nullptr;            // Nv_pad / 128
     double* zq_dev = nullptr;          // 64, charges times 2^dig_kq
     int dig_kq = -1;
 };

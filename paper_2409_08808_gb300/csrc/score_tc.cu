@@ -386,39 +386,40 @@ __global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* _
 
 // ---------------------------------------------------------------------------
 // Exact form: integer-digit split of the symmetric operand on tcgen05.
-// J' at 64-block granularity (J'_II = J_II, J'_IJ = 2 J_IJ for I < J, 0
-// below) is scaled per 64-row panel I by 2^-e_I (|J'| <= 2^e_I) and written as
-// six signed digits, J'/2^e_I = 2^-7 sum_t a_t 2^-8t + r, a_t in [-128, 128]
-// (exact in BF16), |r| <= 2^-48.  Charges are integers after a power-of-two
-// scaling, so every product a_t q and every partial sum over <= Nv_pad sites
-// is an integer below 2^24: the FP32 accumulators hold the digit sums exactly.
-// Tile = (panel I of 64 sites, 128 configurations): M = configurations (TMEM
-// lanes), N = 64 sites per digit, six accumulators at columns 64 t.  The
-// epilogue forms P_t = sum_i q_bi Phi_t,bi in 64-bit integers and the panel's
-// contribution 2^(e_I - 7) sum_t 2^-8t P_t in FP64.
+// J' (128-block upper triangle as above) is scaled per 128-row panel I by
+// 2^-e_I (|J'| <= 2^e_I) and written as six signed digits,
+// J'/2^e_I = 2^-7 sum_t a_t 2^-8t + r, a_t in [-128, 128] (exact in BF16),
+// |r| <= 2^-48.  Charges are integers after a power-of-two scaling, so every
+// product a_t q and every partial sum over <= Nv_pad sites is an integer below
+// 2^24: the FP32 accumulators hold the digit sums Phi_t = A_t Q exactly.
+// A tile is (panel I, 256 configurations, digit t): the same M = 128 sites x
+// N = 256 configurations MMA shape, stage layout and double-buffered TMEM
+// accumulators as k_score_tc with one term.  The epilogue forms
+// P_t,b = sum_i q_bi Phi_t,ib exactly in 32-bit integers (each accumulator
+// split into 12-bit halves so that no sum over the 128 sites can overflow) and
+// stores it as an FP64 integer; k_finish_exact scales by 2^(e_I - 7 - 8t).
 constexpr int EX_T = 6;                        // digits
-constexpr int EX_N = 64;                       // sites per tile
-constexpr int EX_M = 128;                      // configurations per tile
-constexpr int EX_A = EX_M * ROW_BYTES;         // 16 KB (Q^T tile)
-constexpr int EX_B = EX_N * ROW_BYTES;         // 8 KB per digit tile
-constexpr int EX_STAGE = EX_A + EX_T * EX_B;   // 64 KB
-constexpr int EX_STAGES = 3;
+constexpr int EX_STAGE = A_TILE + B_TILE;      // 48 KB
+constexpr int EX_STAGES = 4;
 constexpr int EX_SMEM = EX_STAGES * EX_STAGE + 1024 + 256;
 
 __global__ void __launch_bounds__(192, 1)
     k_score_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int ld,
-                  const __nv_bfloat16* __restrict__ qt, const int* __restrict__ panel_exp, double* __restrict__ partial,
-                  int Bpad, int* __restrict__ err)
+                  const __nv_bfloat16* __restrict__ qt, double* __restrict__ partial, int Bpad,
+                  int* __restrict__ err)
 {
+    constexpr int KB_PER_M = TC_M / 64;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + EX_STAGES * EX_STAGE);
     uint64_t* empty = full + EX_STAGES;
-    uint64_t* tfull = empty + EX_STAGES;
-    uint64_t* tempty = tfull + 1;
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    uint64_t* tfull = empty + EX_STAGES;        // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;               // [2] accumulator drained
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    __shared__ int red_hi[4][TC_N], red_lo[4][TC_N];
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
     if (threadIdx.x == 0) {
@@ -426,25 +427,34 @@ __global__ void __launch_bounds__(192, 1)
             goacd::mbar_init(&full[s], 1);
             goacd::mbar_init(&empty[s], 1);
         }
-        goacd::mbar_init(tfull, 1);
-        goacd::mbar_init(tempty, 4);
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 4);
+        }
         *abort_flag = 0;
         goacd::fence_barrier_init();
     }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmA);
+        goacd::prefetch_tmap(&tmB);
+    }
     if (warp == 2) {
-        goacd::tmem_alloc(tmem_slot, 512);
+        goacd::tmem_alloc(tmem_slot, 2 * TC_N);
         goacd::tmem_relinquish();
     }
     goacd::tc_fence_before();
     __syncthreads();
     goacd::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+
     if (warp == 0) {
+        // ---------------- TMA producer ----------------
         if (lane == 0) {
             int it = 0;
             for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
-                const int2 tile = work[wi];                 // x = panel, y = configuration block
-                for (int kb = tile.x; kb < nkb_total; ++kb, ++it) {
+                const int2 tile = work[wi];             // x = panel, y = configuration block * EX_T + digit
+                const int m0 = tile.x * TC_M, n0 = (tile.y / EX_T) * TC_N, t = tile.y % EX_T;
+                for (int kb = tile.x * KB_PER_M; kb < nkb_total; ++kb, ++it) {
                     const int s = it % EX_STAGES;
                     const uint32_t use = (uint32_t)(it / EX_STAGES);
                     if (it >= EX_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
@@ -455,10 +465,8 @@ __global__ void __launch_bounds__(192, 1)
                     if (*abort_flag) break;
                     uint8_t* st = smem + s * EX_STAGE;
                     goacd::mbar_arrive_expect_tx(&full[s], EX_STAGE);
-                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 64, tile.y * EX_M);
-#pragma unroll
-                    for (int t = 0; t < EX_T; ++t)
-                        goacd::tma_load_2d(st + EX_A + t * EX_B, &tmB, &full[s], kb * 64, t * ld + tile.x * EX_N);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 64, t * ld + m0);
+                    goacd::tma_load_2d(st + A_TILE, &tmB, &full[s], kb * 64, n0);
                 }
             }
             if (*abort_flag)
@@ -468,17 +476,22 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, EX_M, EX_N);
+            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, TC_M, TC_N);
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
                 const int2 tile = work[wi];
-                if (tl >= 1 && !goacd::mbar_wait_bounded(tempty, (uint32_t)(tl - 1) & 1, WAIT_LIMIT)) {
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
                     *abort_flag = 1;
                     goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
                 }
                 goacd::tc_fence_after();
-                for (int kb = tile.x; kb < nkb_total; ++kb, ++it) {
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TC_N);
+                const int kb0 = tile.x * KB_PER_M;
+                for (int kb = kb0; kb < nkb_total; ++kb, ++it) {
                     if (*abort_flag) break;
                     const int s = it % EX_STAGES;
                     const uint32_t use = (uint32_t)(it / EX_STAGES);
@@ -490,84 +503,94 @@ __global__ void __launch_bounds__(192, 1)
                     goacd::tc_fence_after();
                     const uint32_t a0 = goacd::smem_u32(smem + s * EX_STAGE);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = goacd::sdesc_k128(a0 + kk * 32);
-#pragma unroll
-                        for (int t = 0; t < EX_T; ++t) {
-                            const uint64_t bd = goacd::sdesc_k128(a0 + EX_A + t * EX_B + kk * 32);
-                            goacd::mma_bf16(tmem + (uint32_t)(t * EX_N), ad, bd, idesc,
-                                            (kb != tile.x || kk != 0) ? 1u : 0u);
-                        }
-                    }
+                    for (int kk = 0; kk < 4; ++kk)
+                        goacd::mma_bf16(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
+                                        goacd::sdesc_k128(a0 + A_TILE + kk * 32), idesc,
+                                        (kb != kb0 || kk != 0) ? 1u : 0u);
                     goacd::mma_commit(&empty[s]);
                 }
-                goacd::mma_commit(tfull);
+                goacd::mma_commit(&tfull[acc_i]);
             }
         }
         __syncwarp();
     } else {
+        // ---------------- epilogue: warps 2..5 ----------------
         const int lg = warp & 3;
         const int etid = threadIdx.x - 64;
-        (void)etid;
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
             const int2 tile = work[wi];
-            const bool ok = goacd::mbar_wait_bounded(tfull, (uint32_t)tl & 1, WAIT_LIMIT) && !*abort_flag;
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
-            const int b = tile.y * EX_M + lg * 32 + lane;
-            // this configuration's 64 charges of the panel (integers)
-            int q[EX_N];
-            {
-                const int4* src = (const int4*)(qt + (long)b * ld + tile.x * EX_N);
-#pragma unroll
-                for (int u = 0; u < EX_N / 8; ++u) {
-                    const int4 v = src[u];
-                    const __nv_bfloat16* h = (const __nv_bfloat16*)&v;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) q[8 * u + e] = __float2int_rn(__bfloat162float(h[e]));
-                }
-            }
-            double acc = 0.0;
+            const int v = tile.x * TC_M + lg * 32 + lane;
+            const long n0 = (long)(tile.y / EX_T) * TC_N;
 #pragma unroll 1
-            for (int t = EX_T - 1; t >= 0; --t) {
-                long long P = 0;
+            for (int c = 0; c < TC_N / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TC_N) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                int hi[32], lo[32];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t r[32];
-                    goacd::tmem_ld_32x32b_x32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(t * EX_N + h * 32), r);
-                    goacd::tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        P += (long long)q[h * 32 + j] * (long long)__float2int_rn(__uint_as_float(r[j]));
+                for (int j = 0; j < 32; ++j) {
+                    const long b = n0 + c * 32 + j;
+                    const int q = __float2int_rn(__bfloat162float(qt[b * ld + v]));
+                    const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
+                    hi[j] = (a >> 12) * q;
+                    lo[j] = (a & 4095) * q;
                 }
-                acc += ldexp((double)P, -8 * t);       // exact scaling; smallest digit first
+                // butterfly transpose-reduce: afterwards lane l holds column l summed over the warp
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const bool up = (lane & sft) != 0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < sft) {
+                            const int sh = up ? hi[k] : hi[k + sft], kh = up ? hi[k + sft] : hi[k];
+                            const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
+                            hi[k] = kh + __shfl_xor_sync(0xffffffffu, sh, sft);
+                            lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                        }
+                }
+                red_hi[lg][c * 32 + lane] = hi[0];
+                red_lo[lg][c * 32 + lane] = lo[0];
             }
             goacd::tc_fence_before();
             __syncwarp();
-            if (lane == 0) goacd::mbar_arrive(tempty);
-            if (ok) partial[(long)tile.x * Bpad + b] = ldexp(acc, panel_exp[tile.x] - 7);
+            if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
+            goacd::named_bar_sync(1, 128);
+            if (ok)
+                for (int col = etid; col < TC_N; col += 128) {
+                    const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
+                    const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
+                    partial[((long)tile.x * EX_T + tile.y % EX_T) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                }
+            goacd::named_bar_sync(1, 128);
         }
     }
     goacd::tc_fence_before();
     __syncthreads();
     if (warp == 2) {
         goacd::tc_fence_after();
-        goacd::tmem_dealloc(tmem, 512);
+        goacd::tmem_dealloc(tmem, 2 * TC_N);
     }
 }
 
-// Per 64-row panel I of the symmetric operand: e_I with max |J'| <= 2^e_I.
+// Per 128-row panel I of the symmetric operand: e_I with max |J'| < 2^e_I.
 __global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restrict__ pexp)
 {
     __shared__ double red[256];
     const int I = blockIdx.x;
     double m = 0.0;
-    for (long e = threadIdx.x; e < (long)EX_N * ld; e += blockDim.x) {
+    for (long e = threadIdx.x; e < (long)TC_M * ld; e += blockDim.x) {
         const int r = (int)(e / ld), j = (int)(e % ld);
-        const int i = I * EX_N + r;
-        if (j / EX_N < I) continue;
-        const double v = fabs(J[(long)i * ld + j]) * (j / EX_N > I ? 2.0 : 1.0);
+        const int i = I * TC_M + r;
+        if (j / TC_M < I) continue;
+        const double v = fabs(J[(long)i * ld + j]) * (j / TC_M > I ? 2.0 : 1.0);
         m = fmax(m, v);
     }
     red[threadIdx.x] = m;
@@ -583,13 +606,14 @@ __global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restric
     }
 }
 
+// Digit t of J'/2^e_I at [t][i][j]: a_t = rint of the remainder scaled by 2^(7 + 8t).
 __global__ void k_split_digits(const double* __restrict__ J, int ld, const int* __restrict__ pexp,
                                __nv_bfloat16* __restrict__ out)
 {
     const long n = (long)ld * ld;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / ld), j = (int)(e % ld);
-        const int bi = i / EX_N, bj = j / EX_N;
+        const int bi = i / TC_M, bj = j / TC_M;
         double x = bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]);
         x = ldexp(x, 7 - pexp[bi]);               // |x| <= 128
 #pragma unroll
@@ -706,13 +730,18 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
     if (threadIdx.x == 0) lin[b] = red[0];
 }
 
-__global__ void k_finish_exact(const double* __restrict__ partial, int npanels, int Bpad, int B, int kq2,
-                               double E_const, const double* __restrict__ lin, double* __restrict__ E)
+__global__ void k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pexp,
+                               int Bpad, int B, int kq2, double E_const, const double* __restrict__ lin,
+                               double* __restrict__ E)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
-    for (int m = 0; m < npanels; ++m) s += partial[(long)m * Bpad + b];
+    for (int m = 0; m < npanels; ++m) {
+        double d = 0.0;
+        for (int t = EX_T - 1; t >= 0; --t) d += ldexp(partial[((long)m * EX_T + t) * Bpad + b], -8 * t);
+        s += ldexp(d, pexp[m] - 7);
+    }
     E[b] = ldexp(s, -kq2) + (lin ? lin[b] : 0.0) + E_const;
 }
 
@@ -924,10 +953,10 @@ static goac_status prepare_exact(goac_problem* p)
     for (int s2 = 0; s2 < p->S; ++s2) zq[s2] = ldexp(p->z[s2], kq);
     GOAC_CUDA(cudaMalloc(&p->zq_dev, sizeof(double) * 64));
     GOAC_CUDA(cudaMemcpy(p->zq_dev, zq.data(), sizeof(double) * 64, cudaMemcpyHostToDevice));
-    GOAC_CUDA(cudaMalloc(&p->dig_exp, sizeof(int) * (ld / EX_N)));
+    GOAC_CUDA(cudaMalloc(&p->dig_exp, sizeof(int) * (ld / TC_M)));
     GOAC_CUDA(cudaMalloc(&p->J_dig, sizeof(__nv_bfloat16) * EX_T * (size_t)n));
     cudaStream_t st = p->ctx->stream;
-    goac::launch(k_panel_exp, ld / EX_N, 256, 0, st, (const double*)p->J_vv, ld, p->dig_exp);
+    goac::launch(k_panel_exp, ld / TC_M, 256, 0, st, (const double*)p->J_vv, ld, p->dig_exp);
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
     goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, (const int*)p->dig_exp, p->J_dig);
     GOAC_LAUNCH_CHECK("exact digits");
@@ -940,40 +969,41 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     goac_status rc = prepare_exact(p);
     if (rc) return rc;
     const int ld = p->Nv_pad;
-    const int Bpad = ((B + EX_M - 1) / EX_M) * EX_M;
-    const int nbm = ld / EX_N, nbn = Bpad / EX_M;
+    const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
+    const int nbm = ld / TC_M, nbn = Bpad / TC_N;
     rc = ensure(p->qt, (size_t)Bpad * ld * 2);
-    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * Bpad + Bpad));
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * EX_T * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
     double* part = (double*)p->partial.ptr;
-    double* lin = p->has_fixed ? part + (size_t)nbm * Bpad : nullptr;
+    double* lin = p->has_fixed ? part + (size_t)nbm * EX_T * Bpad : nullptr;
     goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
                  (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr,
                  (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
     CUtensorMap ma, mb;
-    rc = make_map(&ma, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, EX_M);
-    if (!rc) rc = make_map(&mb, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, EX_N);
+    rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
     if (rc) return rc;
     static bool attr = false;
     if (!attr) {
         GOAC_CUDA(cudaFuncSetAttribute(k_score_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, EX_SMEM));
         attr = true;
     }
-    const int grid = std::min(nbm * nbn, p->ctx->num_sms);
+    const int grid = std::min(nbm * nbn * EX_T, p->ctx->num_sms);
     const int2* work = nullptr;
     const int* starts = nullptr;
-    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn, grid, &work, &starts);
+    // tiles (I, n * EX_T + t): the LPT schedule sees EX_T times as many configuration blocks
+    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn * EX_T, grid, &work, &starts);
     if (rc) return rc;
     {
         KTimer kt(p->ctx, KID_SCORE_TC, st);
         goac::launch(k_score_exact, grid, 192, EX_SMEM, st, ma, mb, work, starts, ld / 64, ld,
-                     (const __nv_bfloat16*)p->qt.ptr, (const int*)p->dig_exp, part, Bpad, p->ctx->d_err);
+                     (const __nv_bfloat16*)p->qt.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact");
     }
-    goac::launch(k_finish_exact, (B + 255) / 256, 256, 0, st, (const double*)part, nbm, Bpad, B, 2 * p->dig_kq,
-                 p->E_const, (const double*)lin, E_out);
+    goac::launch(k_finish_exact, (B + 255) / 256, 256, 0, st, (const double*)part, nbm, (const int*)p->dig_exp,
+                 Bpad, B, 2 * p->dig_kq, p->E_const, (const double*)lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_exact");
     return GOAC_OK;
 }

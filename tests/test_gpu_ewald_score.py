@@ -218,7 +218,8 @@ def test_score_full_size_swap_property(ctx):
 @pytest.mark.parametrize("which,B", [("rocksalt", 37), ("layered", 300), ("o3", 129), ("random300", 700)])
 def test_score_exact_form(ctx, which, B):
     """Integer-digit split: |E_exact - E_oracle| <= sum_ij |q_i||q_j| 2^-47 max|J|
-    (six 8-bit digits per 64-row panel, largest doubled entry scaled to 2^7)."""
+    (six 8-bit digits per 128-row panel I: each J' entry keeps a residual below
+    2^(e_I - 48) <= 2^-46 max|J|)."""
     prob = {"rocksalt": lambda: synth.rocksalt_problem((2, 2, 2), 4.2),
             "layered": lambda: synth.layered_problem(reps=(3, 3, 1)),
             "o3": lambda: synth.o3_layered_problem((2, 2, 1)),
