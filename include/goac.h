@@ -136,10 +136,11 @@ goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
  * F64 is the plain path; the tensor-core forms split J into TF32 / BF16     *
  * terms, accumulate J.Q in FP32 on tcgen05 and form E in FP64.  EXACT      *
  * (integer charges after a power-of-two scaling, 128 max|q| Nv < 2^24, else  *
- * GOAC_ERR_UNSUPPORTED): each 64-row panel of J is scaled by a power of two   *
- * and cut into six signed 8-bit digits, so every tensor-core product and     *
- * partial sum is an integer below 2^24 and exact; digits are combined with   *
- * 64-bit integers and FP64 (truncation 2^-48 of the panel's largest entry).  *
+ * GOAC_ERR_UNSUPPORTED): each 128-row panel of J is scaled by a power of    *
+ * two and cut into six signed 8-bit digits, so every tensor-core product and *
+ * partial sum is an integer below 2^24 and exact; digit sums are weighted by *
+ * the charges in 32-bit integers and combined in FP64 (truncation 2^-48 of   *
+ * the panel's largest entry).                                                *
  * ------------------------------------------------------------------------ */
 goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
 
@@ -170,6 +171,22 @@ goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld, int32_t Nv
  * context stream and synchronises (end-to-end entry point).                 */
 goac_status goac_score_host(goac_problem* prob, const int8_t* species_host, int32_t B, int32_t precision,
                             double* E_host);
+
+/* Pipelined host-buffer scoring for a stream of populations (the paper's    *
+ * objective, Eq. 2, as in goac_score; the paper has no counterpart: its     *
+ * populations live in host memory next to its CPU code).  Enqueues, without *
+ * waiting: the H2D copy of species_host (B x Nv int8) into one of two        *
+ * device staging slots on the context's own copy stream, the scoring on the *
+ * context stream once that copy has landed, and the D2H copy of the B       *
+ * energies into E_host.  Consecutive calls alternate slots, so the copy of  *
+ * call k+1 overlaps the scoring of call k; a slot is refilled only after    *
+ * the scoring that read it has finished.  The caller keeps species_host     *
+ * unchanged and does not read E_host until goac_ctx_synchronize(ctx)        *
+ * returns.  Both host buffers should be page-locked: with pageable memory   *
+ * the copies are correct but block the host, and nothing overlaps.  Errors  *
+ * of the enqueued work are reported by goac_ctx_synchronize.                */
+goac_status goac_score_host_async(goac_problem* prob, const int8_t* species_host, int32_t B, int32_t precision,
+                                  double* E_host);
 
 /* Top-k "n lowest structures" (Section "Implementation and Theoretical      *
  * Background": the n lowest configurations are the output).  Selects the k  *

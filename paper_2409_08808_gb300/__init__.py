@@ -67,6 +67,7 @@ class Context:
         _check(lib.goac_ctx_create(self.device, C.c_void_p(stream), C.byref(h)), "goac_ctx_create")
         self._h = h
         self._problems = weakref.WeakSet()
+        self._inflight = []      # host tensors of enqueued asynchronous copies
         _live_contexts.add(self)
 
     @property
@@ -81,6 +82,7 @@ class Context:
 
     def synchronize(self):
         _check(lib.goac_ctx_synchronize(self.handle), "goac_ctx_synchronize")
+        self._inflight.clear()
 
     KERNELS = {"score_tc": 0, "score_cc": 1, "mc": 2, "ga": 3, "ewald_real": 4, "ewald_syrk": 5}
 
@@ -210,6 +212,23 @@ class Problem:
             E = out if out is not None else np.empty(B, dtype=np.float64)
             e_ptr = _ptr(E)
         _check(lib.goac_score_host(self.handle, sp_ptr, B, _prec(precision), e_ptr), "goac_score_host")
+        return E
+
+    def score_host_async(self, species: torch.Tensor, precision="f64", out: torch.Tensor | None = None):
+        """Pipelined end-to-end scoring: enqueue the copy of `species` (pinned
+        host int8 tensor, B x Nv) to the device, the scoring and the copy of
+        the energies into `out` (pinned host float64 tensor), and return at
+        once.  Calls alternate two device staging slots, so the copy of the
+        next population overlaps the scoring of this one.  `species` must stay
+        unchanged and `out` unread until ctx.synchronize()."""
+        assert isinstance(species, torch.Tensor) and not species.is_cuda and species.is_contiguous()
+        assert species.dtype == torch.int8 and species.dim() == 2 and species.shape[1] == self.Nv
+        B = species.shape[0]
+        E = out if out is not None else torch.empty(B, dtype=torch.float64, pin_memory=True)
+        assert not E.is_cuda and E.dtype == torch.float64 and E.numel() >= B and E.is_contiguous()
+        _check(lib.goac_score_host_async(self.handle, C.c_void_p(species.data_ptr()), B, _prec(precision),
+                                         C.c_void_p(E.data_ptr())), "goac_score_host_async")
+        self.ctx._inflight.append((species, E))
         return E
 
     def topk_rescore(self, species: torch.Tensor, E_approx: torch.Tensor, k: int):

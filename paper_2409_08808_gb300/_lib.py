@@ -44,6 +44,7 @@ SIGNATURES = {
     "goac_problem_phi_fix": (_st, [_p, _p]),
     "goac_score": (_st, [_p, _p, _i32, _i32, _p]),
     "goac_score_host": (_st, [_p, _p, _i32, _i32, _p]),
+    "goac_score_host_async": (_st, [_p, _p, _i32, _i32, _p]),
     "goac_score_f64_noalloc": (_st, [_p, _i32, _i32, _p, _i32, _p, _p, _d, _p, _p]),
     "goac_topk_rescore": (_st, [_p, _p, _i32, _p, _i32, _p, _p]),
     "goac_random_configs": (_st, [_p, _i32, _u64, _p]),

@@ -62,6 +62,14 @@ struct goac_ctx {
     DevBuf host_io_species;        // device staging for goac_score_host
     DevBuf host_io_E;
     void* pinned = nullptr;        // not used by the stream path; reserved
+    // pipelined host-buffer scoring (goac_score_host_async): two staging slots
+    cudaStream_t copy_stream = nullptr;
+    DevBuf async_species[2];
+    DevBuf async_E[2];
+    cudaEvent_t async_h2d[2] = {nullptr, nullptr};    // slot's species copy landed
+    cudaEvent_t async_done[2] = {nullptr, nullptr};   // slot's scoring and E copy finished
+    bool async_used[2] = {false, false};
+    int async_next = 0;
     // per-kernel event timing (goac_ctx_set_timing / goac_ctx_kernel_time)
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[8];

@@ -153,6 +153,16 @@ extern "C" goac_status goac_ctx_destroy(goac_ctx* ctx)
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     free_buf(ctx->host_io_species);
     free_buf(ctx->host_io_E);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (int s = 0; s < 2; ++s) {
+        if (ctx->async_h2d[s]) cudaEventDestroy(ctx->async_h2d[s]);
+        if (ctx->async_done[s]) cudaEventDestroy(ctx->async_done[s]);
+        free_buf(ctx->async_species[s]);
+        free_buf(ctx->async_E[s]);
+    }
     free_buf(ctx->batch_desc);
     free_buf(ctx->batch_items);
     free_buf(ctx->batch_counter);
@@ -203,6 +213,7 @@ extern "C" goac_status goac_ctx_synchronize(goac_ctx* ctx)
 {
     if (!ctx) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ctx_synchronize: ctx is NULL");
     GOAC_CUDA(cudaSetDevice(ctx->device));
+    if (ctx->copy_stream) GOAC_CUDA(cudaStreamSynchronize(ctx->copy_stream));
     return goac::check_device_error(ctx);
 }
 
@@ -773,6 +784,42 @@ extern "C" goac_status goac_score_host(goac_problem* p, const int8_t* species_ho
     if (rc) return rc;
     GOAC_CUDA(cudaMemcpyAsync(E_host, ctx->host_io_E.ptr, eb, cudaMemcpyDeviceToHost, ctx->stream));
     GOAC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_score_host_async(goac_problem* p, const int8_t* species_host, int32_t B,
+                                             int32_t precision, double* E_host)
+{
+    if (!p || !species_host || !E_host) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: NULL argument");
+    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: B < 0");
+    goac_ctx* ctx = p->ctx;
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    if (!ctx->copy_stream) {
+        GOAC_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (int s = 0; s < 2; ++s) {
+            GOAC_CUDA(cudaEventCreateWithFlags(&ctx->async_h2d[s], cudaEventDisableTiming));
+            GOAC_CUDA(cudaEventCreateWithFlags(&ctx->async_done[s], cudaEventDisableTiming));
+        }
+    }
+    const int s = ctx->async_next;
+    const size_t sb = (size_t)B * p->Nv, eb = sizeof(double) * (size_t)B;
+    if (ctx->async_species[s].bytes < sb || ctx->async_E[s].bytes < eb) {
+        // growing a slot frees its old buffer: let the work that uses it finish first
+        if (ctx->async_used[s]) GOAC_CUDA(cudaEventSynchronize(ctx->async_done[s]));
+        goac_status rc = goac::ensure(ctx->async_species[s], sb);
+        if (!rc) rc = goac::ensure(ctx->async_E[s], eb);
+        if (rc) return rc;
+    }
+    if (ctx->async_used[s]) GOAC_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->async_done[s], 0));
+    GOAC_CUDA(cudaMemcpyAsync(ctx->async_species[s].ptr, species_host, sb, cudaMemcpyHostToDevice, ctx->copy_stream));
+    GOAC_CUDA(cudaEventRecord(ctx->async_h2d[s], ctx->copy_stream));
+    GOAC_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->async_h2d[s], 0));
+    goac_status rc = goac_score(p, (const int8_t*)ctx->async_species[s].ptr, B, precision, (double*)ctx->async_E[s].ptr);
+    if (rc) return rc;
+    GOAC_CUDA(cudaMemcpyAsync(E_host, ctx->async_E[s].ptr, eb, cudaMemcpyDeviceToHost, ctx->stream));
+    GOAC_CUDA(cudaEventRecord(ctx->async_done[s], ctx->stream));
+    ctx->async_used[s] = true;
+    ctx->async_next = s ^ 1;
     return GOAC_OK;
 }
 
