@@ -218,8 +218,8 @@ def _peaks():
 
 def _kernel_hash(form="bf16x2") -> str:
     """Hash of the tensor-core scoring kernel's source for `form` (its function
-    body and the device helpers it uses); ncu counters are valid while it is
-    unchanged."""
+    body and the device helpers of common.cuh it uses); ncu counters are valid
+    while it is unchanged."""
     csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
     src = open(os.path.join(csrc, "score_tc.cu")).read()
     if form == "exact":
@@ -228,9 +228,10 @@ def _kernel_hash(form="bf16x2") -> str:
     else:
         a = src.index("template <int T, bool TF32>\n__global__ void __launch_bounds__(192, 1)")
         b = src.index("__device__ __forceinline__ float to_tf32_rna(")
+    common = open(os.path.join(csrc, "common.cuh")).read()
     h = hashlib.sha256()
     h.update(src[a:b].encode())
-    h.update(open(os.path.join(csrc, "common.cuh"), "rb").read())
+    h.update(common[common.index("namespace goacd {"):common.index("}  // namespace goacd")].encode())
     return h.hexdigest()[:16]
 
 

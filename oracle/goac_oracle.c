@@ -637,9 +637,10 @@ int orc_random_configs(int64_t N, const int32_t* site_class, int32_t S, const in
 /*   positions a = pos[x0*n >> 32], b = pos[b' + (b' >= a)], b' = x1*(n-1)>>32;*/
 /*   u = ((x2 >> 5) * 2^26 + (x3 >> 6)) * 2^-53 in [0, 1).                   */
 /* Equal species: a no-op trial.  Otherwise accept iff dE <= 1e-9 eV or      */
-/* u < exp(-dE/kT) (kT <= 0: dE <= 1e-9 eV only); |dE| <= 1e-9 eV is read as */
-/* dE = 0, since swaps related by symmetry give +-1e-14 eV under rounding.  On acceptance the species are   */
-/* swapped, phi_w += d (J[w,ia] - J[w,ib]) for every variable w (ascending),*/
+/* dE < -kT ln u, the event u < exp(-dE/kT) (u = 0 accepts; kT <= 0: dE <=  */
+/* 1e-9 eV only); |dE| <= 1e-9 eV is read as dE = 0, since swaps related by */
+/* symmetry give +-1e-14 eV under rounding.  On acceptance the species are  */
+/* swapped, phi_w = fma(d, J[w,ia] - J[w,ib], phi_w) for every variable w,  */
 /* and E += dE.  The best E seen (strictly lower) and its configuration are */
 /* kept.  Returns the number of accepted swaps per chain in n_accept, and,   */
 /* when E_trace (C x nsteps) is given, the energy before every step.         */
@@ -723,16 +724,19 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
             double u = ((double)(x[2] >> 5) * 67108864.0 + (double)(x[3] >> 6)) * (1.0 / 9007199254740992.0);
             const double kTt = step_kT(kT[ch], kT1, ch, t, total);
             int accept;
+            /* Metropolis (SI, Monte Carlo): accept with probability min[1, exp(-dE/kT)],
+               i.e. u < exp(-dE/kT), taken as the same event dE < -kT ln u */
             if (dE <= ORC_DE_ZERO) accept = 1;
             else if (kTt <= 0.0) accept = 0;
-            else accept = u < exp(-dE / kTt);
+            else accept = u == 0.0 || dE < -kTt * log(u);
             if (!accept) continue;
             sp[va] = (int8_t)sb;
             sp[vb] = (int8_t)sa;
+            /* phi_w += d (J_wa - J_wb), one rounding for the product and the sum */
             if (d != 0.0)
                 for (int64_t w = 0; w < nv; ++w) {
                     int64_t i = cl.vsite[w];
-                    phi[w] = phi[w] + d * (J[i * N + ia] - J[i * N + ib]);
+                    phi[w] = fma(d, J[i * N + ia] - J[i * N + ib], phi[w]);
                 }
             E = E + dE;
             nacc++;

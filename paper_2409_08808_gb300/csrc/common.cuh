@@ -122,6 +122,10 @@ struct goac_problem {
     int* dig_exp = nullptr;            // Nv_pad / 128
     double* zq_dev = nullptr;          // 64, charges times 2^dig_kq
     int dig_kq = -1;
+    // exact-form potentials: digits of J_vv itself, its panel exponents, digit sums
+    __nv_bfloat16* J_dig_full = nullptr;   // [6][Nv_pad][Nv_pad]
+    int* dig_exp_full = nullptr;           // Nv_pad / 128
+    DevBuf phi_dig;                        // [6][Bpad][Nv_pad] int32
 };
 
 // ---------------------------------------------------------------------------
@@ -386,4 +390,9 @@ goac_status score_f32(goac_problem* p, const int8_t* species, int B, double* E_o
 goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precision, double* E_out);
 goac_status prepare_f32(goac_problem* p);
 goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi);
+// Exact-form potentials and energies (phi = J_vv q + phi_fix, B x Nv FP64, and
+// E as score_f64) on the tensor cores; false from exact_supported() means the
+// charges do not admit the exact form and score_f64 must be used.
+bool exact_supported(goac_problem* p);
+goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, double* phi_out);
 }  // namespace goac

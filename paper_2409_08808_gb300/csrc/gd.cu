@@ -202,7 +202,10 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     double* dmin = (double*)(ckey + (size_t)ntiles * B);
     int* active = (int*)(dmin + B);
     int* n_active = active + B;
-    rc = goac::score_f64(p, species_dev, B, E_dev, phi);
+    // starting potentials: exact integer-digit contraction on the tensor cores
+    // when the charges admit it, else the FP64 GEMM
+    rc = goac::exact_supported(p) ? goac::phi_exact(p, species_dev, B, E_dev, phi)
+                                  : goac::score_f64(p, species_dev, B, E_dev, phi);
     if (rc) return rc;
     goac::launch(k_gd_init, (B + 255) / 256, 256, 0, st, B, active, (long long*)steps_dev);
     GdArgs g;

@@ -16,8 +16,9 @@
 // were evaluated against the same state they would have seen.
 //
 // The FP64 path uses explicitly rounded operations in the order of the
-// definition (no contraction into FMA), so its trajectory follows the FP64
-// definition step for step.  The FP32 path keeps J rows and phi in FP32.
+// definition (dE without contraction, the phi update as one fused multiply-add,
+// acceptance as dE < -kT ln u), so its trajectory follows the FP64 definition
+// step for step.  The FP32 path keeps J rows and phi in FP32.
 #include <math.h>
 
 #include <algorithm>
@@ -75,6 +76,13 @@ template <>
 __device__ __forceinline__ double rd_mul<double>(double a, double b) { return __dmul_rn(a, b); }
 template <>
 __device__ __forceinline__ float rd_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+
+template <typename R>
+__device__ __forceinline__ R rd_fma(R a, R b, R c);
+template <>
+__device__ __forceinline__ double rd_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <>
+__device__ __forceinline__ float rd_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // Barrier over the W warps of one chain group (named barrier `id`, 1..15).
 template <int W>
@@ -148,6 +156,7 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
         int va = 0, vb = 0;
         double u = 0.0, kTl = kT;
         R jsum = (R)0;
+        R thr = (R)-INFINITY;      // accept iff dE <= 1e-9 eV or dE < thr = -kT ln u
         if (lane < nb) {
             if (P.kT1 && P.total > 1)     // simulated annealing: kT0 (kT1/kT0)^(t/(total-1))
                 kTl = kT * exp(log(P.kT1[chain] / kT) * ((double)t / (double)(P.total - 1)));
@@ -173,6 +182,13 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             vb = P.cls_pos[start + b];
             u = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6)) * (1.0 / 9007199254740992.0);
             jsum = rd_sub<R>(rd_add<R>(diag[va], diag[vb]), rd_mul<R>((R)2, J[(long)va * ld + vb]));
+            // Metropolis: u < exp(-dE/kT) is the event dE < -kT ln u, so the
+            // threshold is formed once per proposal, not per evaluation
+            if (kTl > 0.0) {
+                if (u == 0.0) thr = (R)INFINITY;
+                else if (sizeof(R) == 8) thr = (R)(-kTl * log(u));
+                else thr = (R)(-(float)kTl * logf((float)u));
+            }
         }
         uint32_t pending = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
         while (pending) {
@@ -184,9 +200,7 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                     d = (R)(P.z[sb] - P.z[sa]);
                     dE = rd_add<R>(rd_mul<R>(rd_mul<R>((R)2, d), rd_sub<R>(phi[va], phi[vb])),
                                    rd_mul<R>(rd_mul<R>(d, d), jsum));
-                    if ((double)dE <= kDeZero) acc = true;
-                    else if (sizeof(R) == 8) acc = kTl > 0.0 && u < exp(-(double)dE / kTl);
-                    else acc = kTl > 0.0 && (float)u < expf(-(float)dE / (float)kTl);
+                    acc = (double)dE <= kDeZero || dE < thr;
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, acc);
@@ -217,7 +231,7 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
 #pragma unroll
                     for (int uu = 0; uu < 8; ++uu) {
                         const int w = w0 + 32 * W * uu;
-                        if (w < Nv) phi[w] = rd_add<R>(phi[w], rd_mul<R>(cd, rd_sub<R>(xa[uu], xb[uu])));
+                        if (w < Nv) phi[w] = rd_fma<R>(cd, rd_sub<R>(xa[uu], xb[uu]), phi[w]);
                     }
                 }
             }
@@ -374,7 +388,11 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
     if (rc) return rc;
     void* phi0 = p->phi.ptr;
     double* E0 = (double*)((char*)p->phi.ptr + ((rb * (size_t)C * p->Nv + 255) & ~(size_t)255));
-    rc = f32 ? goac::score_f32(p, species_dev, C, E0, (float*)phi0) : goac::score_f64(p, species_dev, C, E0, (double*)phi0);
+    // (FP64: the exact integer-digit contraction on the tensor cores when the
+    // charges admit it, else the FP64 GEMM)
+    if (f32) rc = goac::score_f32(p, species_dev, C, E0, (float*)phi0);
+    else if (goac::exact_supported(p)) rc = goac::phi_exact(p, species_dev, C, E0, (double*)phi0);
+    else rc = goac::score_f64(p, species_dev, C, E0, (double*)phi0);
     if (rc) return rc;
     // warps per chain: more warps share the O(Nv) update of a long chain
     const int W = p->Nv >= 3072 ? 4 : (p->Nv >= 1536 ? 2 : 1);

@@ -729,6 +729,9 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->J_dig);
     cudaFree(p->dig_exp);
     cudaFree(p->zq_dev);
+    cudaFree(p->J_dig_full);
+    cudaFree(p->dig_exp_full);
+    free_buf(p->phi_dig);
     delete p;
     return GOAC_OK;
 }

@@ -580,8 +580,9 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-// Per 128-row panel I of the symmetric operand: e_I with max |J'| < 2^e_I.
-__global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restrict__ pexp)
+// Per 128-row panel I of the symmetric operand (sym != 0) or of J itself:
+// e_I with max |J'| (max |J|) < 2^e_I.
+__global__ void k_panel_exp(const double* __restrict__ J, int ld, int sym, int* __restrict__ pexp)
 {
     __shared__ double red[256];
     const int I = blockIdx.x;
@@ -589,8 +590,8 @@ __global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restric
     for (long e = threadIdx.x; e < (long)TC_M * ld; e += blockDim.x) {
         const int r = (int)(e / ld), j = (int)(e % ld);
         const int i = I * TC_M + r;
-        if (j / TC_M < I) continue;
-        const double v = fabs(J[(long)i * ld + j]) * (j / TC_M > I ? 2.0 : 1.0);
+        if (sym && j / TC_M < I) continue;
+        const double v = fabs(J[(long)i * ld + j]) * (sym && j / TC_M > I ? 2.0 : 1.0);
         m = fmax(m, v);
     }
     red[threadIdx.x] = m;
@@ -606,15 +607,16 @@ __global__ void k_panel_exp(const double* __restrict__ J, int ld, int* __restric
     }
 }
 
-// Digit t of J'/2^e_I at [t][i][j]: a_t = rint of the remainder scaled by 2^(7 + 8t).
-__global__ void k_split_digits(const double* __restrict__ J, int ld, const int* __restrict__ pexp,
+// Digit t of J'/2^e_I (sym != 0) or J/2^e_I at [t][i][j]: a_t = rint of the
+// remainder scaled by 2^(7 + 8t).
+__global__ void k_split_digits(const double* __restrict__ J, int ld, int sym, const int* __restrict__ pexp,
                                __nv_bfloat16* __restrict__ out)
 {
     const long n = (long)ld * ld;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / ld), j = (int)(e % ld);
         const int bi = i / TC_M, bj = j / TC_M;
-        double x = bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]);
+        double x = !sym ? J[e] : (bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]));
         x = ldexp(x, 7 - pexp[bi]);               // |x| <= 128
 #pragma unroll
         for (int t = 0; t < EX_T; ++t) {
@@ -623,6 +625,178 @@ __global__ void k_split_digits(const double* __restrict__ J, int ld, const int* 
             x = (x - a) * 256.0;
         }
     }
+}
+
+// Potentials Phi = J_vv Q through the integer-digit split of J_vv itself (the
+// exact-form counterpart of the FP64 GEMM, used to start FP64 chains).  Tile =
+// (panel I, 256 configurations, digit t) over the whole k-range; all tiles
+// have the same length and are dealt round-robin to the persistent grid, digit
+// fastest so that concurrent CTAs share Q tiles in L2.  Same stages, MMA shape
+// and double-buffered TMEM accumulators as k_score_exact; the epilogue stores
+// each exact digit sum as a 32-bit integer, Phi_t[b][v].
+__global__ void __launch_bounds__(192, 1)
+    k_phi_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ntiles,
+                int nbm, int nkb, int ld, int Bpad, int* __restrict__ Phi, int* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + EX_STAGES * EX_STAGE);
+    uint64_t* empty = full + EX_STAGES;
+    uint64_t* tfull = empty + EX_STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < EX_STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 4);
+        }
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmA);
+        goacd::prefetch_tmap(&tmB);
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc(tmem_slot, 2 * TC_N);
+        goacd::tmem_relinquish();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x) {
+                const int t = id % EX_T, I = (id / EX_T) % nbm, n = id / (EX_T * nbm);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % EX_STAGES;
+                    const uint32_t use = (uint32_t)(it / EX_STAGES);
+                    if (it >= EX_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * EX_STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], EX_STAGE);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 64, t * ld + I * TC_M);
+                    goacd::tma_load_2d(st + A_TILE, &tmB, &full[s], kb * 64, n * TC_N);
+                }
+            }
+            if (*abort_flag)
+                for (int k = it - EX_STAGES < 0 ? 0 : it - EX_STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % EX_STAGES], (uint32_t)(k / EX_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, TC_M, TC_N);
+            int it = 0, tl = 0;
+            for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
+                }
+                goacd::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TC_N);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % EX_STAGES;
+                    const uint32_t use = (uint32_t)(it / EX_STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t a0 = goacd::smem_u32(smem + s * EX_STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        goacd::mma_bf16(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
+                                        goacd::sdesc_k128(a0 + A_TILE + kk * 32), idesc,
+                                        (kb != 0 || kk != 0) ? 1u : 0u);
+                    goacd::mma_commit(&empty[s]);
+                }
+                goacd::mma_commit(&tfull[acc_i]);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int lg = warp & 3;
+        int tl = 0;
+        for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
+            const int t = id % EX_T, I = (id / EX_T) % nbm, n = id / (EX_T * nbm);
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            const int v = I * TC_M + lg * 32 + lane;
+            int* dst = Phi + ((long)t * Bpad + (long)n * TC_N) * ld + v;
+#pragma unroll 1
+            for (int c = 0; c < TC_N / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TC_N) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                if (ok)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) dst[(long)(c * 32 + j) * ld] = __float2int_rn(__uint_as_float(r[j]));
+            }
+            goacd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc(tmem, 2 * TC_N);
+    }
+}
+
+// phi_bv = 2^(e_I - 7 - kq) sum_t 2^-8t Phi_t[b][v] + phi_fix_v (digits smallest
+// first) and E_b = sum_v q_bv (phi_bv + phi_fix_v) + E_const, one block per
+// configuration, fixed reduction order.
+__global__ void __launch_bounds__(256)
+    k_phi_exact_finish(const int* __restrict__ Phi, int Bpad, int ld, int Nv, const int* __restrict__ pexp, int kq,
+                       const double* __restrict__ phifix, const int8_t* __restrict__ species,
+                       const double* __restrict__ z, double E_const, double* __restrict__ phi_out,
+                       double* __restrict__ E_out)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    double e = 0.0;
+    for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
+        double d = 0.0;
+        for (int t = EX_T - 1; t >= 0; --t) d += ldexp((double)Phi[((long)t * Bpad + b) * ld + v], -8 * t);
+        const double pf = phifix[v];
+        const double ph = ldexp(d, pexp[v / TC_M] - 7 - kq) + pf;
+        if (phi_out) phi_out[(long)b * Nv + v] = ph;
+        e += z[species[(long)b * Nv + v]] * (ph + pf);
+    }
+    if (!E_out) return;
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) E_out[b] = red[0] + E_const;
 }
 
 // Symmetric operand: J'_ij = J_ij on diagonal 128-blocks, 2 J_ij above them,
@@ -929,38 +1103,100 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     return GOAC_OK;
 }
 
-// Digits of the symmetric operand and the charge scaling of the exact form.
-static goac_status prepare_exact(goac_problem* p)
+// Charge scaling of the exact form: the smallest kq <= 4 with every species
+// charge times 2^kq an integer, and 128 max|q 2^kq| Nv_pad < 2^24.
+static int exact_kq(const goac_problem* p)
 {
-    if (p->J_dig) return GOAC_OK;
-    int kq = -1;
-    double qmax = 0.0;
-    for (int k = 0; k <= 4 && kq < 0; ++k) {
+    for (int k = 0; k <= 4; ++k) {
         bool ok = true;
+        double qmax = 0.0;
         for (double zz : p->z) {
             const double v = ldexp(zz, k);
             if (v != rint(v)) ok = false;
+            qmax = std::max(qmax, fabs(v));
         }
-        if (ok) kq = k;
+        if (ok) return 128.0 * qmax * (double)p->Nv_pad < 16777216.0 ? k : -2;
     }
-    if (kq < 0) return fail(GOAC_ERR_UNSUPPORTED, "exact form: species charges are not multiples of 1/16");
-    for (double zz : p->z) qmax = std::max(qmax, fabs(ldexp(zz, kq)));
-    if (128.0 * qmax * (double)p->Nv_pad >= 16777216.0)
+    return -1;
+}
+
+bool exact_supported(goac_problem* p) { return exact_kq(p) >= 0; }
+
+static goac_status exact_charges(goac_problem* p)
+{
+    if (p->zq_dev) return GOAC_OK;
+    const int kq = exact_kq(p);
+    if (kq == -1) return fail(GOAC_ERR_UNSUPPORTED, "exact form: species charges are not multiples of 1/16");
+    if (kq == -2)
         return fail(GOAC_ERR_UNSUPPORTED, "exact form: 128 max|q| Nv exceeds 2^24 (digit sums would not be exact in FP32)");
-    const int ld = p->Nv_pad;
-    const long n = (long)ld * ld;
     std::vector<double> zq(64, 0.0);
     for (int s2 = 0; s2 < p->S; ++s2) zq[s2] = ldexp(p->z[s2], kq);
     GOAC_CUDA(cudaMalloc(&p->zq_dev, sizeof(double) * 64));
     GOAC_CUDA(cudaMemcpy(p->zq_dev, zq.data(), sizeof(double) * 64, cudaMemcpyHostToDevice));
-    GOAC_CUDA(cudaMalloc(&p->dig_exp, sizeof(int) * (ld / TC_M)));
-    GOAC_CUDA(cudaMalloc(&p->J_dig, sizeof(__nv_bfloat16) * EX_T * (size_t)n));
-    cudaStream_t st = p->ctx->stream;
-    goac::launch(k_panel_exp, ld / TC_M, 256, 0, st, (const double*)p->J_vv, ld, p->dig_exp);
-    const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
-    goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, (const int*)p->dig_exp, p->J_dig);
-    GOAC_LAUNCH_CHECK("exact digits");
     p->dig_kq = kq;
+    return GOAC_OK;
+}
+
+// Digits and panel exponents of the symmetric operand (sym) or of J_vv itself.
+static goac_status build_digits(goac_problem* p, bool sym, __nv_bfloat16** dig, int** pexp)
+{
+    goac_status rc = exact_charges(p);
+    if (rc) return rc;
+    const int ld = p->Nv_pad;
+    const long n = (long)ld * ld;
+    GOAC_CUDA(cudaMalloc(pexp, sizeof(int) * (ld / TC_M)));
+    GOAC_CUDA(cudaMalloc(dig, sizeof(__nv_bfloat16) * EX_T * (size_t)n));
+    cudaStream_t st = p->ctx->stream;
+    goac::launch(k_panel_exp, ld / TC_M, 256, 0, st, (const double*)p->J_vv, ld, sym ? 1 : 0, *pexp);
+    const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
+    goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, sym ? 1 : 0, (const int*)*pexp, *dig);
+    GOAC_LAUNCH_CHECK("exact digits");
+    return GOAC_OK;
+}
+
+static goac_status prepare_exact(goac_problem* p)
+{
+    if (p->J_dig) return GOAC_OK;
+    return build_digits(p, true, &p->J_dig, &p->dig_exp);
+}
+
+goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, double* phi_out)
+{
+    if (!p->J_dig_full) {
+        goac_status rc = build_digits(p, false, &p->J_dig_full, &p->dig_exp_full);
+        if (rc) return rc;
+    }
+    const int ld = p->Nv_pad;
+    const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
+    const int nbm = ld / TC_M, nbn = Bpad / TC_N;
+    goac_status rc = ensure(p->qt, (size_t)Bpad * ld * 2);
+    if (!rc) rc = ensure(p->phi_dig, sizeof(int) * (size_t)EX_T * Bpad * ld);
+    if (rc) return rc;
+    cudaStream_t st = p->ctx->stream;
+    goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+                 (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, (const double*)nullptr, (double*)nullptr);
+    GOAC_LAUNCH_CHECK("k_make_qt (exact potentials)");
+    CUtensorMap ma, mb;
+    rc = make_map(&ma, p->J_dig_full, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
+    if (rc) return rc;
+    static bool attr = false;
+    if (!attr) {
+        GOAC_CUDA(cudaFuncSetAttribute(k_phi_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, EX_SMEM));
+        attr = true;
+    }
+    const int ntiles = nbm * nbn * EX_T;
+    const int grid = std::min(ntiles, p->ctx->num_sms);
+    {
+        KTimer kt(p->ctx, KID_SCORE_TC, st);
+        goac::launch(k_phi_exact, grid, 192, EX_SMEM, st, ma, mb, ntiles, nbm, ld / 64, ld, Bpad,
+                     (int*)p->phi_dig.ptr, p->ctx->d_err);
+        GOAC_LAUNCH_CHECK("k_phi_exact");
+    }
+    goac::launch(k_phi_exact_finish, B, 256, 0, st, (const int*)p->phi_dig.ptr, Bpad, ld, p->Nv,
+                 (const int*)p->dig_exp_full, p->dig_kq, (const double*)p->phifix, species, (const double*)p->z_dev,
+                 p->E_const, phi_out, E_out);
+    GOAC_LAUNCH_CHECK("k_phi_exact_finish");
     return GOAC_OK;
 }
 

@@ -214,3 +214,31 @@ def test_hybrid_parity(ctx):
     E = gp.hybrid_run(sp, 2, 4, lad, 2, 3, 300, 3, 1, oracle.p_mut_to_u32(0.2), 7)
     assert np.array_equal(sp.cpu().numpy(), ref["species"])
     assert np.allclose(E.cpu().numpy(), ref["E"], rtol=1e-10)
+
+
+def test_mc_exact_potentials_quarter_charges(ctx):
+    """O3 layered oxide 2x2x1 (charges in quarters: O 1.75-, Fe 2.5+, Co 3.5+),
+    whose FP64 chains start from the integer-digit tensor-core potentials:
+    trajectories identical to the oracle's."""
+    prob = synth.o3_layered_problem((2, 2, 1))
+    ref, got, _, _ = _run_both(ctx, prob, 6, 5000, 0.1, seed=31)
+    assert np.array_equal(got["species"], ref["species"])
+    assert np.array_equal(got["n_accept"], ref["n_accept"])
+    assert np.allclose(got["E"], ref["E"], rtol=1e-10, atol=0)
+
+
+def test_mc_exact_potentials_full_size(ctx):
+    """N = 4096, 300 chains: the starting energies from the integer-digit
+    potentials equal the FP64 scoring path, and after 64 swaps per chain the
+    running energies equal FP64 rescoring of the final configurations."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.random_cubic_problem()
+    J = g.build_ewald(ctx, prob.lattice, torch.tensor(prob.frac, device="cuda"), prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, J)
+    sp = gp.random_configs(300, 5)
+    E64 = gp.score(sp, "f64")
+    out = gp.mc_run(sp.clone(), 0.05, 0, 1)
+    assert ((out["E"] - E64).abs() / E64.abs()).max().item() <= 1e-11
+    out = gp.mc_run(sp, 0.05, 64, 1)
+    E64 = gp.score(sp, "f64")
+    assert ((out["E"] - E64).abs() / E64.abs()).max().item() <= 1e-10
