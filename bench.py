@@ -38,6 +38,7 @@ METRIC = "config energy evals/s and MC swap trials/s at N=4096, % roofline, vs F
 N_SIDE = 16          # 16^3 = 4096 sites
 B_POP = 4096
 FORM = "bf16x2"
+E2E_CELLS = 4          # cells scored round robin in the end-to-end leg
 TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2, "exact": 6}   # exact: six BF16 digits
 WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +1:512 +2:1024 +3:512 -2:2048), "
             "population B=4096 uniformly random count-preserving configurations")
@@ -53,6 +54,8 @@ def _args():
     ap.add_argument("--mc-steps", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
     ap.add_argument("--suite", action="store_true", help="measure the other workloads, one JSON line each")
+    ap.add_argument("--only", default="mc,ga,batch,forms,relaxed",
+                    help="suite sections to run (comma separated: mc, ga, batch, forms, relaxed)")
     ap.add_argument("--batch-cells", type=int, default=256)
     ap.add_argument("--batch-chains", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=10000)
@@ -321,27 +324,36 @@ def run_ours(args, world, rank, local):
                 "peak_kind": f"{peak_kind} bf16_tflops (burst)" + (" x 0.5 nominal tf32/bf16 ratio" if "tf32" in form else "")}
 
     # End to end through the public host-buffer API: every step copies its
-    # population from pinned host memory and its energies back.  Pipelined
-    # entry point (copy of step k+1 overlaps the scoring of step k); the L2
-    # flush between steps is enqueued on the scoring stream, inside the timed
-    # region.  Two different host populations alternate.
-    pop2_np = synth.random_population(prob, B_POP, synth.SEED_BASE + 3 + 1000 * rank)
-    pops_host = [pop_host, torch.tensor(pop2_np).pin_memory()]
-    E_hosts = [torch.empty(B_POP, dtype=torch.float64).pin_memory() for _ in range(2)]
-    for k in range(4):
-        gp.score_host_async(pops_host[k % 2], form, out=E_hosts[k % 2])
+    # population from pinned host memory and its energies back, through the
+    # pipelined entry point (the copy of step k+1 overlaps the scoring of step
+    # k).  Inputs larger than L2 instead of a flush: E2E_CELLS different
+    # N = 4096 cells (jitter seeds) are scored round robin, each step a fresh
+    # population, so a cell's operands were last touched E2E_CELLS - 1 steps
+    # (> 129 MB of traffic) earlier.
+    cells = [gp]
+    for c in range(1, E2E_CELLS):
+        pc = synth.random_cubic_problem(n_side=N_SIDE, seed=synth.SEED_BASE + 2 + 97 * c)
+        Jc = g.build_ewald(ctx, pc.lattice, torch.tensor(pc.frac, device=dev), pc.alpha, pc.nimg, pc.kcut)
+        cells.append(g.Problem(ctx, Jc, pc.site_class, pc.fixed_q, pc.z, pc.counts))
+        del Jc
+    pops_host = [pop_host] + [torch.tensor(synth.random_population(prob, B_POP, synth.SEED_BASE + 3 + c + 1000 * rank))
+                              .pin_memory() for c in range(1, 2 * E2E_CELLS)]
+    E_hosts = [torch.empty(B_POP, dtype=torch.float64).pin_memory() for _ in range(2 * E2E_CELLS)]
+    n_e2e = max(2 * E2E_CELLS, min(args.steps, 400) // (2 * E2E_CELLS) * (2 * E2E_CELLS))
+    for k in range(2 * E2E_CELLS):
+        cells[k % E2E_CELLS].score_host_async(pops_host[k], form, out=E_hosts[k])
     ctx.synchronize()
-    n_e2e = min(args.steps, 400)
     _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(n_e2e):
-        flush.zero_()
-        gp.score_host_async(pops_host[k % 2], form, out=E_hosts[k % 2])
+        j = k % (2 * E2E_CELLS)
+        cells[j % E2E_CELLS].score_host_async(pops_host[j], form, out=E_hosts[j])
     ctx.synchronize()
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / n_e2e, world)
-    E_dev = [gp.score(torch.tensor(p.numpy(), device=dev), form).cpu() for p in pops_host]
-    e2e_ok = all(bool(torch.equal(E_hosts[(n_e2e - 1 - j) % 2], E_dev[(n_e2e - 1 - j) % 2])) for j in range(2))
+    e2e_ok = all(bool(torch.equal(E_hosts[j], cells[j % E2E_CELLS].score(pops_host[j].to(dev), form).cpu()))
+                 for j in range(2 * E2E_CELLS))
+    del cells
     # the blocking entry point (copy, score, copy back, synchronise) for comparison
     E_host = E_hosts[0]
     e2e_t = []
@@ -355,7 +367,10 @@ def run_ours(args, world, rank, local):
     e2e = {"value": world * B_POP / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(pop_np.nbytes),
            "d2h_bytes_per_step": int(E_host.numel() * 8), "api": "Problem.score_host_async (goac_score_host_async)",
            "steps": n_e2e, "energies_equal_device_path": e2e_ok,
-           "blocking_api_value": world * B_POP / e2e_block_s}
+           "l2": f"no flush: {E2E_CELLS} different N=4096 cells round robin, 8 host populations "
+                 f"(one cell's operands + inputs ~85 MB; a {E2E_CELLS}-step cycle > 2x the 129 MB L2)",
+           "blocking_api_value": world * B_POP / e2e_block_s,
+           "blocking_api_l2": "256 MB flush between steps, outside the host timer"}
 
     # plain FP64 GPU path on the same population, and the split form's error
     E_form = gp.score(pop, form).clone()
@@ -480,156 +495,174 @@ def run_suite(args):
         print(json.dumps(d), flush=True)
 
     oracle.build()
-    # ---- rocksalt 2x2x2, N = 64: 8 chains x 20,000 swaps at kT = 0.05 eV, FP64, parity with the oracle
-    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
-    gp, J, jms = problem(prob)
-    start = synth.random_population(prob, 8, synth.SEED_BASE)
-    gp.mc_run(torch.tensor(start, device=dev), 0.05, 2000, 1)
-    chains = torch.tensor(start, device=dev)
-    ms = timed(lambda: gp.mc_run(chains, 0.05, 20000, synth.SEED_BASE))
-    Jo = oracle.ewald_J(prob.lattice, prob.frac, prob.alpha, prob.nimg, prob.kcut)
-    t0 = time.perf_counter()
-    ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.05, 20000, synth.SEED_BASE)
-    cpu_s = time.perf_counter() - t0
-    emit({"workload": "rocksalt 2x2x2 (N=64, 32 cations +1/+3), MC 8 chains x 20,000 swaps, kT=0.05 eV, FP64",
-          "gpu_ms": ms, "trials_per_s": 160000 / (ms / 1e3), "cpu_oracle_s": cpu_s,
-          "cpu_oracle_trials_per_s": 160000 / cpu_s, "cpu_cores": 1,
-          "trajectory_parity": bool(np.array_equal(chains.cpu().numpy(), ref["species"])),
-          "ewald_build_ms": jms})
+    only = set(x.strip() for x in args.only.split(","))
 
-    # ---- layered R-3m 12x12x1, N = 1296: GA population 1024, 200 generations
-    prob = synth.layered_problem()
-    gp, J, jms = problem(prob)
-    pop0 = gp.random_configs(1024, 3)
-    res = {}
-    for prec in ("f64", "f32", "bf16x3"):
-        pop = pop0.clone()
-        gp.ga_run(pop.clone(), 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
+    def want(section):
+        return section in only
+
+    if want("mc"):
+        # ---- rocksalt 2x2x2, N = 64: 8 chains x 20,000 swaps at kT = 0.05 eV, FP64, parity with the oracle
+        prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+        gp, J, jms = problem(prob)
+        start = synth.random_population(prob, 8, synth.SEED_BASE)
+        gp.mc_run(torch.tensor(start, device=dev), 0.05, 2000, 1)
+        chains = torch.tensor(start, device=dev)
+        ms = timed(lambda: gp.mc_run(chains, 0.05, 20000, synth.SEED_BASE))
+        Jo = oracle.ewald_J(prob.lattice, prob.frac, prob.alpha, prob.nimg, prob.kcut)
+        t0 = time.perf_counter()
+        ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.05, 20000, synth.SEED_BASE)
+        cpu_s = time.perf_counter() - t0
+        emit({"workload": "rocksalt 2x2x2 (N=64, 32 cations +1/+3), MC 8 chains x 20,000 swaps, kT=0.05 eV, FP64",
+              "gpu_ms": ms, "trials_per_s": 160000 / (ms / 1e3), "cpu_oracle_s": cpu_s,
+              "cpu_oracle_trials_per_s": 160000 / cpu_s, "cpu_cores": 1,
+              "trajectory_parity": bool(np.array_equal(chains.cpu().numpy(), ref["species"])),
+              "ewald_build_ms": jms})
+
+    if want("ga"):
+        # ---- layered R-3m 12x12x1, N = 1296: GA population 1024, 200 generations
+        prob = synth.layered_problem()
+        gp, J, jms = problem(prob)
+        pop0 = gp.random_configs(1024, 3)
+        res = {}
+        for prec in ("f64", "f32", "bf16x3"):
+            pop = pop0.clone()
+            gp.ga_run(pop.clone(), 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
+            box = {}
+            ctx.set_timing(True)
+            ctx.kernel_time("ga")
+            ms = timed(lambda: box.setdefault("E", gp.ga_run(pop, 200, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)))
+            gk_ms, gk_n = ctx.kernel_time("ga")
+            ctx.set_timing(False)
+            E = box["E"]
+            # children kernel: reads both parents, writes the child (int8 species)
+            ga_bytes = 3.0 * 1024 * prob.Nv
+            gk_avg = gk_ms / max(gk_n, 1)
+            res[prec] = {"ms": ms, "generations_per_s": 200 / (ms / 1e3), "child_evals_per_s": 1024 * 200 / (ms / 1e3),
+                         "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(gp.score(pop, "f64").min()),
+                         "children_kernel_ms": gk_avg,
+                         "children_kernel_hbm_gbs_algorithmic": ga_bytes / (gk_avg / 1e3) / 1e9}
+        work = None
+        Jr = np.random.default_rng(1).standard_normal((prob.N, prob.N))
+        Jr = 0.5 * (Jr + Jr.T)
+        popn = pop0[:256].cpu().numpy()
+        En = oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, popn)
+        t0 = time.perf_counter()
+        kids, _, _ = oracle.ga_generation(prob.site_class, popn, En, 5, 0.1, gen=0, seed=9)
+        oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, kids)
+        cpu_gen = (time.perf_counter() - t0) * 4.0   # population 256 -> 1024 (generation and scoring are linear in P)
+        emit({"workload": "layered R-3m 12x12x1 (N=1296: 432 O fixed, Li/vac 346/86, Ni2/Ni3/Mn4/Co3 108 each), "
+                          "GA population 1024 x 200 generations, elite 20, p_mut 0.1",
+              "forms": res, "cpu_oracle_s_per_generation": cpu_gen, "cpu_oracle_note":
+              "one generation of 256 children timed and scaled x4 (scoring is linear in the population), 1 thread",
+              "ewald_build_ms": jms})
+
+    if want("batch"):
+        # ---- uneven batch: 256 rocksalt / spinel-like cells, N in [64, 2048], 512 chains each
+        cells = synth.batch_problems(args.batch_cells)
+        gps, sps, kts = [], [], []
+        tb = 0.0
+        for i, pr in enumerate(cells):
+            gpi, _, bms = problem(pr)
+            tb += bms
+            gps.append(gpi)
+            sps.append(gpi.random_configs(args.batch_chains, 100 + i))
+            kts.append(torch.full((args.batch_chains,), pr.kT, dtype=torch.float64, device=dev))
+        best_cpc, tune_ms = g.batch_mc_autotune(ctx, gps, sps, kts, 256, "f64")
+        steps = args.batch_steps
+        trials = steps * args.batch_chains * len(cells)
+        modes = {}
+        for mode, name in ((0, "per_problem_launches"), (1, "persistent"), (2, "persistent_graph")):
+            cpc = best_cpc if mode else min(best_cpc, 4)
+            g.batch_mc_run(ctx, gps, sps, kts, 64, 7, step0=0, chains_per_cta=cpc, mode=mode)
+            ms = timed(lambda: g.batch_mc_run(ctx, gps, sps, kts, steps, 7, step0=64, chains_per_cta=cpc, mode=mode))
+            modes[name] = {"ms": ms, "trials_per_s": trials / (ms / 1e3), "chains_per_cta": cpc}
+        emit({"workload": f"{len(cells)} rocksalt/spinel-like cells, N log-uniform 64..2048, {args.batch_chains} chains "
+                          f"each, {steps} swaps per chain (kT per cell 0.01..0.2 eV), FP64",
+              "trials": trials, "modes": modes, "autotuned_chains_per_cta": best_cpc, "autotune_probe_ms": tune_ms,
+              "ewald_build_total_ms": tb,
+              "trials_per_chain_in_config": 100000,
+              "extrapolated_s_for_1e5_swaps": modes["persistent_graph"]["ms"] / 1e3 * 100000 / steps})
+        del gps, sps, kts
+
+    if want("forms"):
+        # ---- every scoring form at N = 4096, B = 4096 (throughput, error vs the FP64 path, roofline)
+        prob = synth.random_cubic_problem(n_side=N_SIDE)
+        gp, J, jms = problem(prob)
+        pop = torch.tensor(synth.random_population(prob, B_POP, synth.SEED_BASE + 2), device=dev)
+        E64 = gp.score(pop, "f64")
+        bf16_peak, hbm_peak, _ = _peaks()
+        ld = ((prob.N + 127) // 128) * 128
+        nbm = ld // 128
+        forms = {}
+        for form in ("f64", "f32", "tf32", "tf32x2", "bf16x2", "bf16x3", "exact"):
+            for _ in range(3):
+                gp.score(pop, form)
+            reps = 2 if form in ("f64", "f32") else 50
+            ctx.set_timing(True)
+            ctx.kernel_time("score_tc")
+            ctx.kernel_time("score_cc")
+            box = {}
+            ms = timed(lambda: [box.setdefault("E", gp.score(pop, form)) for _ in range(reps)]) / reps
+            kms, kn = ctx.kernel_time("score_tc" if form in TERMS else "score_cc")
+            ctx.set_timing(False)
+            E = gp.score(pop, form)
+            err = (E - E64).abs()
+            d = {"ms_per_population": ms, "evals_per_s": B_POP / (ms / 1e3), "speedup_vs_f64": None,
+                 "max_abs_err_eV": float(err.max()), "rms_abs_err_eV": float(err.pow(2).mean().sqrt()),
+                 "kernel_ms": kms / max(kn, 1)}
+            if form in TERMS:
+                flops = TERMS[form] * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
+                peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak
+                d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
+                d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / peak
+            forms[form] = d
+        for f in forms:
+            forms[f]["speedup_vs_f64"] = forms["f64"]["ms_per_population"] / forms[f]["ms_per_population"]
+        idx, Etop = gp.topk_rescore(pop, gp.score(pop, "bf16x3"), 64)
+        emit({"workload": WORKLOAD + ", every scoring form", "forms": forms,
+              "top64_after_bf16x3_equals_fp64_top64": bool(set(idx.tolist()) == set(torch.argsort(E64)[:64].tolist())),
+              "ewald_build_ms": jms})
+        del gp, J, pop, E64
+
+    if want("relaxed"):
+        # ---- relaxed occupations: bcc 16^3, N = 8192, B = 2048 logits sets, 5 species
+        prob = synth.bcc_relaxed_problem()
+        gp, J, jms = problem(prob, allow=True)
+        B = args.grad_batch
+        L = torch.tensor(synth.random_logits(prob, B, 5), device=dev)
+        lam, eta = 1.0, 0.01
+        res = {}
+        for prec in ("f64", "tf32x2"):
+            gp.energy_grad(L[:2].contiguous(), lam, prec)
+            box = {}
+            ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, lam, prec)))
+            res[prec] = {"energy_grad_ms": ms, "grad_steps_per_s": 1e3 / ms}
+        E64, g64 = gp.energy_grad(L, lam, "f64")
+        Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
+        res["tf32x2"]["max_rel_E_err"] = float(((Etc - E64).abs() / E64.abs()).max())
+        res["tf32x2"]["max_abs_grad_err_rel_to_max"] = float((gtc - g64).abs().max() / g64.abs().max())
+        Ld = L.clone()
+        E0 = gp.energy_grad(Ld, lam, "tf32x2")[0]
+        steps = args.grad_steps
         box = {}
-        ms = timed(lambda: box.setdefault("E", gp.ga_run(pop, 200, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)))
-        E = box["E"]
-        res[prec] = {"ms": ms, "generations_per_s": 200 / (ms / 1e3), "child_evals_per_s": 1024 * 200 / (ms / 1e3),
-                     "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(gp.score(pop, "f64").min())}
-    work = None
-    Jr = np.random.default_rng(1).standard_normal((prob.N, prob.N))
-    Jr = 0.5 * (Jr + Jr.T)
-    popn = pop0[:256].cpu().numpy()
-    En = oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, popn)
-    t0 = time.perf_counter()
-    kids, _, _ = oracle.ga_generation(prob.site_class, popn, En, 5, 0.1, gen=0, seed=9)
-    oracle.score(Jr, prob.site_class, prob.fixed_q, prob.z, kids)
-    cpu_gen = (time.perf_counter() - t0) * 4.0   # population 256 -> 1024 (generation and scoring are linear in P)
-    emit({"workload": "layered R-3m 12x12x1 (N=1296: 432 O fixed, Li/vac 346/86, Ni2/Ni3/Mn4/Co3 108 each), "
-                      "GA population 1024 x 200 generations, elite 20, p_mut 0.1",
-          "forms": res, "cpu_oracle_s_per_generation": cpu_gen, "cpu_oracle_note":
-          "one generation of 256 children timed and scaled x4 (scoring is linear in the population), 1 thread",
-          "ewald_build_ms": jms})
-
-    # ---- uneven batch: 256 rocksalt / spinel-like cells, N in [64, 2048], 512 chains each
-    cells = synth.batch_problems(args.batch_cells)
-    gps, sps, kts = [], [], []
-    tb = 0.0
-    for i, pr in enumerate(cells):
-        gpi, _, bms = problem(pr)
-        tb += bms
-        gps.append(gpi)
-        sps.append(gpi.random_configs(args.batch_chains, 100 + i))
-        kts.append(torch.full((args.batch_chains,), pr.kT, dtype=torch.float64, device=dev))
-    best_cpc, tune_ms = g.batch_mc_autotune(ctx, gps, sps, kts, 256, "f64")
-    steps = args.batch_steps
-    trials = steps * args.batch_chains * len(cells)
-    modes = {}
-    for mode, name in ((0, "per_problem_launches"), (1, "persistent"), (2, "persistent_graph")):
-        cpc = best_cpc if mode else min(best_cpc, 4)
-        g.batch_mc_run(ctx, gps, sps, kts, 64, 7, step0=0, chains_per_cta=cpc, mode=mode)
-        ms = timed(lambda: g.batch_mc_run(ctx, gps, sps, kts, steps, 7, step0=64, chains_per_cta=cpc, mode=mode))
-        modes[name] = {"ms": ms, "trials_per_s": trials / (ms / 1e3), "chains_per_cta": cpc}
-    emit({"workload": f"{len(cells)} rocksalt/spinel-like cells, N log-uniform 64..2048, {args.batch_chains} chains "
-                      f"each, {steps} swaps per chain (kT per cell 0.01..0.2 eV), FP64",
-          "trials": trials, "modes": modes, "autotuned_chains_per_cta": best_cpc, "autotune_probe_ms": tune_ms,
-          "ewald_build_total_ms": tb,
-          "trials_per_chain_in_config": 100000,
-          "extrapolated_s_for_1e5_swaps": modes["persistent_graph"]["ms"] / 1e3 * 100000 / steps})
-    del gps, sps, kts
-
-    # ---- every scoring form at N = 4096, B = 4096 (throughput, error vs the FP64 path, roofline)
-    prob = synth.random_cubic_problem(n_side=N_SIDE)
-    gp, J, jms = problem(prob)
-    pop = torch.tensor(synth.random_population(prob, B_POP, synth.SEED_BASE + 2), device=dev)
-    E64 = gp.score(pop, "f64")
-    bf16_peak, hbm_peak, _ = _peaks()
-    ld = ((prob.N + 127) // 128) * 128
-    nbm = ld // 128
-    forms = {}
-    for form in ("f64", "f32", "tf32", "tf32x2", "bf16x2", "bf16x3", "exact"):
-        for _ in range(3):
-            gp.score(pop, form)
-        reps = 2 if form in ("f64", "f32") else 50
-        ctx.set_timing(True)
-        ctx.kernel_time("score_tc")
-        ctx.kernel_time("score_cc")
-        box = {}
-        ms = timed(lambda: [box.setdefault("E", gp.score(pop, form)) for _ in range(reps)]) / reps
-        kms, kn = ctx.kernel_time("score_tc" if form in TERMS else "score_cc")
-        ctx.set_timing(False)
-        E = gp.score(pop, form)
-        err = (E - E64).abs()
-        d = {"ms_per_population": ms, "evals_per_s": B_POP / (ms / 1e3), "speedup_vs_f64": None,
-             "max_abs_err_eV": float(err.max()), "rms_abs_err_eV": float(err.pow(2).mean().sqrt()),
-             "kernel_ms": kms / max(kn, 1)}
-        if form in TERMS:
-            flops = TERMS[form] * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
-            peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak
-            d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
-            d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / peak
-        forms[form] = d
-    for f in forms:
-        forms[f]["speedup_vs_f64"] = forms["f64"]["ms_per_population"] / forms[f]["ms_per_population"]
-    idx, Etop = gp.topk_rescore(pop, gp.score(pop, "bf16x3"), 64)
-    emit({"workload": WORKLOAD + ", every scoring form", "forms": forms,
-          "top64_after_bf16x3_equals_fp64_top64": bool(set(idx.tolist()) == set(torch.argsort(E64)[:64].tolist())),
-          "ewald_build_ms": jms})
-    del gp, J, pop, E64
-
-    # ---- relaxed occupations: bcc 16^3, N = 8192, B = 2048 logits sets, 5 species
-    prob = synth.bcc_relaxed_problem()
-    gp, J, jms = problem(prob, allow=True)
-    B = args.grad_batch
-    L = torch.tensor(synth.random_logits(prob, B, 5), device=dev)
-    lam, eta = 1.0, 0.01
-    res = {}
-    for prec in ("f64", "tf32x2"):
-        gp.energy_grad(L[:2].contiguous(), lam, prec)
-        box = {}
-        ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, lam, prec)))
-        res[prec] = {"energy_grad_ms": ms, "grad_steps_per_s": 1e3 / ms}
-    E64, g64 = gp.energy_grad(L, lam, "f64")
-    Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
-    res["tf32x2"]["max_rel_E_err"] = float(((Etc - E64).abs() / E64.abs()).max())
-    res["tf32x2"]["max_abs_grad_err_rel_to_max"] = float((gtc - g64).abs().max() / g64.abs().max())
-    Ld = L.clone()
-    E0 = gp.energy_grad(Ld, lam, "tf32x2")[0]
-    steps = args.grad_steps
-    box = {}
-    dms = timed(lambda: box.setdefault("E", gp.relaxed_descent(Ld, lam, eta, steps, "tf32x2")))
-    p_occ = gp.occupations(Ld)
-    rms = timed(lambda: box.setdefault("sp", gp.round_to_counts(p_occ)))
-    seeded = box["sp"]
-    E_seed = gp.score(seeded, "bf16x3")
-    rand = gp.random_configs(B, 9)
-    E_rand = gp.score(rand, "bf16x3")
-    gms = timed(lambda: box.setdefault("Eg", gp.ga_run(seeded, 5, 40, oracle.p_mut_to_u32(0.1), 3, 0, "bf16x3")))
-    emit({"workload": f"bcc 16^3 (N=8192, 5 species +1/+2/+3/+4/0), relaxed occupations, B={B} logits sets, "
-                      f"counts penalty lambda={lam}", "forms": res,
-          "descent": {"steps": steps, "eta": eta, "ms": dms, "steps_per_s": steps / (dms / 1e3),
-                      "mean_E_before_eV": float(E0.mean()), "mean_E_after_eV": float(box["E"].mean())},
-          "round_to_counts_ms": rms,
-          "seeded_population": {"mean_E_eV": float(E_seed.mean()), "min_E_eV": float(E_seed.min()),
-                                "random_population_mean_E_eV": float(E_rand.mean()),
-                                "random_population_min_E_eV": float(E_rand.min()),
-                                "ga_5_generations_ms": gms, "ga_best_E_eV": float(box["Eg"].min())},
-          "ewald_build_ms": jms})
-
+        dms = timed(lambda: box.setdefault("E", gp.relaxed_descent(Ld, lam, eta, steps, "tf32x2")))
+        p_occ = gp.occupations(Ld)
+        rms = timed(lambda: box.setdefault("sp", gp.round_to_counts(p_occ)))
+        seeded = box["sp"]
+        E_seed = gp.score(seeded, "bf16x3")
+        rand = gp.random_configs(B, 9)
+        E_rand = gp.score(rand, "bf16x3")
+        gms = timed(lambda: box.setdefault("Eg", gp.ga_run(seeded, 5, 40, oracle.p_mut_to_u32(0.1), 3, 0, "bf16x3")))
+        emit({"workload": f"bcc 16^3 (N=8192, 5 species +1/+2/+3/+4/0), relaxed occupations, B={B} logits sets, "
+                          f"counts penalty lambda={lam}", "forms": res,
+              "descent": {"steps": steps, "eta": eta, "ms": dms, "steps_per_s": steps / (dms / 1e3),
+                          "mean_E_before_eV": float(E0.mean()), "mean_E_after_eV": float(box["E"].mean())},
+              "round_to_counts_ms": rms,
+              "seeded_population": {"mean_E_eV": float(E_seed.mean()), "min_E_eV": float(E_seed.min()),
+                                    "random_population_mean_E_eV": float(E_rand.mean()),
+                                    "random_population_min_E_eV": float(E_rand.min()),
+                                    "ga_5_generations_ms": gms, "ga_best_E_eV": float(box["Eg"].min())},
+              "ewald_build_ms": jms})
 
 def run_paper(args):
     """The paper's heuristics on its own workloads, one JSON line per cell: the
