@@ -103,6 +103,7 @@ struct goac_problem {
     int32_t* vclass_dev = nullptr;
     int32_t* cls_start_dev = nullptr;
     int32_t* cls_pos_dev = nullptr;
+    int32_t* cls_rank_dev = nullptr;   // Nv: index p of each variable site in cls_pos
     int32_t* counts_dev = nullptr;
     uint32_t* wprefix_dev = nullptr;
     // lazily built operand copies for the tensor-core and FP32 paths

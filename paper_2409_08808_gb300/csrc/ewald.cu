@@ -24,6 +24,11 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Four doubles, 32-byte aligned (k-vector with its weight, or image translation with a flag).
+struct __align__(32) Vec4d {
+    double x, y, z, w;
+};
+
 struct Geom {
     double A[9];
     double B[9];
@@ -53,7 +58,7 @@ __global__ void k_geometry(const double* __restrict__ A_in, Geom* __restrict__ g
 // in linear order, keep the half space (m1 > 0, or m1 == 0 and m2 > 0, or
 // m1 == m2 == 0 and m3 > 0) with |k| <= kcut, compact with a block scan.
 __global__ void __launch_bounds__(1024) k_kvectors(const Geom* __restrict__ g, int M1, int M2, int M3, double kcut,
-                                                   double alpha, double ke, double4* __restrict__ kv,
+                                                   double alpha, double ke, Vec4d* __restrict__ kv,
                                                    int* __restrict__ count)
 {
     __shared__ int warp_sums[32];
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(1024) k_kvectors(const Geom* __restrict__ g, i
         if (keep) {
             int pos = base + warp_sums[wid] + wpre;
             double w = ke * (4.0 * kPi / V) * exp(-k2 / (4.0 * alpha * alpha)) / k2;
-            kv[pos] = make_double4(kx, ky, kz, sqrt(w));
+            kv[pos] = Vec4d{kx, ky, kz, sqrt(w)};
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) base += warp_sums[wid] + wpre + keep;
@@ -121,7 +126,7 @@ __global__ void k_frac_to_cart(const Geom* __restrict__ g, const double* __restr
 
 // X[i][t] = sqrt(w_t) cos(k_t . r_i), X[i][K + t] = sqrt(w_t) sin(k_t . r_i); zero
 // padding for columns 2K .. ldx-1.
-__global__ void k_struct_factor(const double4* __restrict__ kv, int K, const double* __restrict__ cart, int N,
+__global__ void k_struct_factor(const Vec4d* __restrict__ kv, int K, const double* __restrict__ cart, int N,
                                 double* __restrict__ X, int ldx)
 {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -132,7 +137,7 @@ __global__ void k_struct_factor(const double4* __restrict__ kv, int K, const dou
         double v = 0.0;
         if (t < 2 * K) {
             int kk = t < K ? t : t - K;
-            double4 k = kv[kk];
+            Vec4d k = kv[kk];
             double ph = k.x * cart[3 * i] + k.y * cart[3 * i + 1] + k.z * cart[3 * i + 2];
             double s, c;
             sincos(ph, &s, &c);
@@ -195,11 +200,26 @@ __global__ void __launch_bounds__(256) k_syrk_f64(const double* __restrict__ X, 
 
 // Real-space image sum for pairs i <= j, plus self and background; the
 // reciprocal part is read from the lower triangle written by k_syrk_f64.
+// Terms with alpha r >= 6 are skipped (erfc(6) = 2.2e-17).  The image list is
+// first screened with an FP32 distance test whose cutoff carries a 1e-4
+// relative margin (FP32 r^2 is within 1e-6 of FP64), so no image that the FP64
+// test keeps is ever screened out; every kept term is evaluated in FP64.
+constexpr double kRealCut = 6.0;
+constexpr int kMaxImgF = 1024;
+
 __global__ void __launch_bounds__(256) k_real_space(const Geom* __restrict__ g, const double* __restrict__ frac,
-                                                    int N, const double4* __restrict__ img, int nimg_total,
+                                                    int N, const Vec4d* __restrict__ img, int nimg_total,
                                                     double alpha, double ke, double* __restrict__ J)
 {
-    if (blockIdx.x < blockIdx.y) return;   // tile strictly below the diagonal
+    __shared__ float4 imgf[kMaxImgF];
+    if (blockIdx.x < blockIdx.y) return;   // tile strictly below the diagonal (uniform per block)
+    const bool screen = nimg_total <= kMaxImgF;
+    if (screen)
+        for (int t = threadIdx.y * 16 + threadIdx.x; t < nimg_total; t += 256) {
+            const Vec4d n = img[t];
+            imgf[t] = make_float4((float)n.x, (float)n.y, (float)n.z, (float)n.w);
+        }
+    __syncthreads();
     const int i = blockIdx.y * 16 + threadIdx.y;
     const int j = blockIdx.x * 16 + threadIdx.x;
     if (i >= N || j >= N || i > j) return;
@@ -211,10 +231,17 @@ __global__ void __launch_bounds__(256) k_real_space(const Geom* __restrict__ g, 
     }
     double d[3];
     for (int c = 0; c < 3; ++c) d[c] = df[0] * A[c] + df[1] * A[3 + c] + df[2] * A[6 + c];
-    const double rc2 = 64.0 / (alpha * alpha);   // alpha r < 8
+    const double rc2 = kRealCut * kRealCut / (alpha * alpha);
+    const float rc2f = (float)(rc2 * (1.0 + 1e-4));
+    const float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
     double real = 0.0;
     for (int t = 0; t < nimg_total; ++t) {
-        const double4 n = img[t];
+        if (screen) {
+            const float4 nf = imgf[t];
+            const float fx = dx + nf.x, fy = dy + nf.y, fz = dz + nf.z;
+            if (fx * fx + fy * fy + fz * fz >= rc2f) continue;
+        }
+        const Vec4d n = img[t];
         if (i == j && n.w != 0.0) continue;      // n = 0 term of the self pair
         double rx = d[0] + n.x, ry = d[1] + n.y, rz = d[2] + n.z;
         double r2 = rx * rx + ry * ry + rz * rz;
@@ -231,7 +258,7 @@ __global__ void __launch_bounds__(256) k_real_space(const Geom* __restrict__ g, 
 }
 
 // Image translations n1 a1 + n2 a2 + n3 a3 for |n_a| <= nimg[a]; w = 1 marks n = 0.
-__global__ void k_images(const Geom* __restrict__ g, int n1, int n2, int n3, double4* __restrict__ img)
+__global__ void k_images(const Geom* __restrict__ g, int n1, int n2, int n3, Vec4d* __restrict__ img)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int tot = (2 * n1 + 1) * (2 * n2 + 1) * (2 * n3 + 1);
@@ -243,7 +270,7 @@ __global__ void k_images(const Geom* __restrict__ g, int n1, int n2, int n3, dou
     double x = a * A[0] + b * A[3] + c * A[6];
     double y = a * A[1] + b * A[4] + c * A[7];
     double z = a * A[2] + b * A[5] + c * A[8];
-    img[t] = make_double4(x, y, z, (a == 0 && b == 0 && c == 0) ? 1.0 : 0.0);
+    img[t] = Vec4d{x, y, z, (a == 0 && b == 0 && c == 0) ? 1.0 : 0.0};
 }
 
 }  // namespace
@@ -274,10 +301,10 @@ extern "C" goac_status goac_build_ewald(goac_ctx* ctx, const double* lattice_hos
 
     double* dA = nullptr;
     Geom* dG = nullptr;
-    double4* dK = nullptr;
+    Vec4d* dK = nullptr;
     int* dCount = nullptr;
     double* dCart = nullptr;
-    double4* dImg = nullptr;
+    Vec4d* dImg = nullptr;
     double* dX = nullptr;
     goac_status rc = GOAC_OK;
     int K = 0;
@@ -301,10 +328,10 @@ extern "C" goac_status goac_build_ewald(goac_ctx* ctx, const double* lattice_hos
     } while (0)
     TRY(cudaMalloc(&dA, 9 * sizeof(double)));
     TRY(cudaMalloc(&dG, sizeof(Geom)));
-    TRY(cudaMalloc(&dK, sizeof(double4) * (box + 1)));
+    TRY(cudaMalloc(&dK, sizeof(Vec4d) * (box + 1)));
     TRY(cudaMalloc(&dCount, sizeof(int)));
     TRY(cudaMalloc(&dCart, sizeof(double) * 3 * N));
-    TRY(cudaMalloc(&dImg, sizeof(double4) * nimg_total));
+    TRY(cudaMalloc(&dImg, sizeof(Vec4d) * nimg_total));
     TRY(cudaMemcpyAsync(dA, lattice_host, 9 * sizeof(double), cudaMemcpyHostToDevice, st));
     goac::launch(k_geometry, 1, 32, 0, st, dA, dG);
     goac::launch(k_kvectors, 1, 1024, 0, st, dG, M[0], M[1], M[2], kcut, alpha, ke, dK, dCount);

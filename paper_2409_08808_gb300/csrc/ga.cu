@@ -14,8 +14,9 @@
 //                 sum, crossover in shared memory (the warp scans 32 sites at a
 //                 time with ballots; the partner site j of a candidate swap is
 //                 the lowest position of the class with child_j == B_i and
-//                 B_j != B_i, found by a ballot over the class's positions),
-//                 Philox draws per candidate, mutation, write-back.
+//                 B_j != B_i, kept per species as a bitmask over class
+//                 positions and found by one ballot over 32 words), Philox
+//                 draws per candidate, mutation, write-back.
 #include "common.cuh"
 
 namespace {
@@ -117,11 +118,12 @@ struct GaArgs {
     const int32_t* vclass;
     const int32_t* cls_start;
     const int32_t* cls_pos;
+    const int32_t* cls_rank;
     const uint32_t* wprefix;
     int* err;
     uint64_t seed;
     uint32_t wtotal, p_mut, gen;
-    int P, Nv, n_elite, ncls, nmovable, only_movable;
+    int P, Nv, S, n_elite, ncls, nmovable, only_movable;
 };
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int i)
@@ -140,6 +142,16 @@ __device__ __forceinline__ int lower_bound_gt(const unsigned long long* pre, int
     return lo;
 }
 
+// Shared-memory slot of one child warp: child and parent B (Nv bytes each,
+// 16-byte rounded) and, per species s, a bitmask over class positions p of the
+// sites with child = s != B (mis[s][p / 32]).
+__host__ __device__ inline size_t ga_slot_bytes(int Nv, int S)
+{
+    const size_t sp = ((size_t)Nv + 15) & ~(size_t)15;
+    const size_t words = ((size_t)Nv + 31) / 32;
+    return 2 * sp + (((size_t)S * words * 4 + 15) & ~(size_t)15);
+}
+
 __global__ void k_ga_children(GaArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -147,9 +159,11 @@ __global__ void k_ga_children(GaArgs a)
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.P) return;
     const int Nv = a.Nv;
-    const size_t slot = (((size_t)Nv + 15) & ~(size_t)15) * 2;
-    int8_t* ch = (int8_t*)(smem + slot * wib);
-    int8_t* pb = ch + (slot >> 1);
+    const int W = (Nv + 31) / 32;
+    uint8_t* base = smem + ga_slot_bytes(Nv, a.S) * wib;
+    int8_t* ch = (int8_t*)base;
+    int8_t* pb = ch + (((size_t)Nv + 15) & ~(size_t)15);
+    uint32_t* mis = (uint32_t*)(pb + (((size_t)Nv + 15) & ~(size_t)15));
     int8_t* out = a.children + (long)c * Nv;
 
     if (c < a.n_elite) {
@@ -172,46 +186,86 @@ __global__ void k_ga_children(GaArgs a)
         ch[w] = a.pop[(long)A * Nv + w];
         pb[w] = a.pop[(long)B * Nv + w];
     }
+    for (int e = lane; e < a.S * W; e += 32) mis[e] = 0u;
+    __syncwarp();
+    for (int q = lane; q < Nv; q += 32) {
+        const int w = a.cls_pos[q];
+        const int8_t s = ch[w];
+        if ((unsigned)s < (unsigned)a.S && s != pb[w]) atomicOr(&mis[s * W + (q >> 5)], 1u << (q & 31));
+    }
     __syncwarp();
 
+    // Crossover: for each site i (ascending) where the child differs from B,
+    // the candidate swap pairs i with the lowest class position holding B_i
+    // where B differs (the lowest set bit of mis[B_i] in i's class), taken with
+    // probability 1/2.
     uint32_t kc = 0;
     int nsw = 0;
-    uint4 blk = make_uint4(0, 0, 0, 0);
+    uint4 blk = make_uint4(0, 0, 0, 0);    // this lane's Philox block of the current batch of 128 candidates
     for (int i0 = 0; i0 < Nv; i0 += 32) {
+        // per-lane facts of this chunk's sites (B does not change)
+        const int il = i0 + lane;
+        int8_t my_b = 0;
+        int my_cs = 0, my_ce = 0, my_rank = 0;
+        if (il < Nv) {
+            my_b = pb[il];
+            const int k = a.vclass[il];
+            my_cs = a.cls_start[k];
+            my_ce = a.cls_start[k + 1];
+            my_rank = a.cls_rank[il];
+        }
         int from = 0;
         while (true) {
-            const int i = i0 + lane;
-            const bool diff = lane >= from && i < Nv && ch[i] != pb[i];
+            const bool diff = lane >= from && il < Nv && ch[il] != my_b;
             const uint32_t m = __ballot_sync(0xffffffffu, diff);
             if (m == 0u) break;
             const int l = __ffs(m) - 1;
             const int ii = i0 + l;
-            const int8_t want = pb[ii];
-            const int cls = a.vclass[ii];
-            const int cs = a.cls_start[cls], ce = a.cls_start[cls + 1];
-            int j = -1;
-            for (int pp = cs; pp < ce; pp += 32) {
-                const int idx = pp + lane;
-                const int w = idx < ce ? a.cls_pos[idx] : 0;
-                const bool ok = idx < ce && ch[w] == want && pb[w] != want;
-                const uint32_t mm = __ballot_sync(0xffffffffu, ok);
+            const int8_t want = (int8_t)__shfl_sync(0xffffffffu, (int)my_b, l);
+            if ((unsigned)want >= (unsigned)a.S) {      // not a species of the problem
+                if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
+                return;
+            }
+            const int cs = __shfl_sync(0xffffffffu, my_cs, l), ce = __shfl_sync(0xffffffffu, my_ce, l);
+            const int pi = __shfl_sync(0xffffffffu, my_rank, l);
+            const int wlo = cs >> 5, whi = (ce - 1) >> 5;
+            const uint32_t* mw = mis + want * W;
+            int pp = -1;
+            for (int w0 = wlo; w0 <= whi; w0 += 32) {
+                const int wi = w0 + lane;
+                uint32_t bits = 0u;
+                if (wi <= whi) {
+                    bits = mw[wi];
+                    if (wi == wlo) bits &= ~0u << (cs & 31);
+                    if (wi == whi && (ce & 31)) bits &= (1u << (ce & 31)) - 1u;
+                }
+                const uint32_t mm = __ballot_sync(0xffffffffu, bits != 0u);
                 if (mm) {
-                    j = __shfl_sync(0xffffffffu, w, __ffs(mm) - 1);
+                    const int ll = __ffs(mm) - 1;
+                    const uint32_t bw = __shfl_sync(0xffffffffu, bits, ll);
+                    pp = (w0 + ll) * 32 + __ffs(bw) - 1;
                     break;
                 }
             }
-            if (j < 0) {
+            if (pp < 0) {
                 if (lane == 0) goacd::report(a.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
                 return;
             }
-            if ((kc & 3u) == 0u) blk = goacd::philox(make_uint4(kc >> 2, a.gen, (uint32_t)c, 3u), k0, k1);
-            const uint32_t wv = word_of(blk, (int)(kc & 3u));
+            // candidate kc uses word kc & 3 of Philox block kc >> 2 (ctr {kc >> 2, gen, c, 3});
+            // the warp draws 32 consecutive blocks at a time, lane t holding block 32 q + t
+            if ((kc & 127u) == 0u) blk = goacd::philox(make_uint4((kc >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
+            const uint32_t wv = __shfl_sync(0xffffffffu, word_of(blk, (int)(kc & 3u)), (int)((kc >> 2) & 31u));
             ++kc;
             if (wv < 0x80000000u) {
                 __syncwarp();
                 if (lane == 0) {
-                    ch[j] = ch[ii];
+                    const int j = a.cls_pos[pp];
+                    const int8_t old = ch[ii];               // old != want
+                    ch[j] = old;
                     ch[ii] = want;
+                    mis[old * W + (pi >> 5)] &= ~(1u << (pi & 31));     // i now equals B_i
+                    mis[want * W + (pp >> 5)] &= ~(1u << (pp & 31));    // j no longer holds B_i
+                    if (pb[j] != old) mis[old * W + (pp >> 5)] |= 1u << (pp & 31);
                 }
                 __syncwarp();
                 ++nsw;
@@ -292,6 +346,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     a.vclass = p->vclass_dev;
     a.cls_start = p->cls_start_dev;
     a.cls_pos = p->cls_pos_dev;
+    a.cls_rank = p->cls_rank_dev;
     a.wprefix = p->wprefix_dev;
     a.err = ctx->d_err;
     a.seed = seed;
@@ -300,15 +355,17 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     a.gen = gen;
     a.P = P;
     a.Nv = p->Nv;
+    a.S = p->S;
     a.n_elite = n_elite;
     a.ncls = p->ncls;
     a.nmovable = p->nmovable;
     a.only_movable = p->only_movable;
-    const size_t slot = (((size_t)p->Nv + 15) & ~(size_t)15) * 2;
-    int wpb = (int)((96 * 1024) / slot);
-    if (wpb > 8) wpb = 8;
-    if (wpb < 1) wpb = 1;
+    // warps (children) per block: a power of two up to 8, small enough that
+    // the grid spreads over at least two blocks per SM, within 96 KB
+    const size_t slot = ga_slot_bytes(p->Nv, p->S);
     if (slot > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
+    int wpb = 8;
+    while (wpb > 1 && ((size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
     const size_t smem = slot * wpb;
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     KTimer kt(ctx, KID_GA, st);

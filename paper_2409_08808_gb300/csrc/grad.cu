@@ -8,10 +8,12 @@
 //   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks)
 //   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)
 //
-// (2 J q)_v = 2 (J_vv q_v + phi_fix)_v.  The contraction J_vv Q runs either as
-// an FP64 tiled GEMM on the CUDA cores or on the tcgen05 tensor cores with both
-// J and the real-valued Q split into TF32 hi / lo (three products); the
-// elementwise chain rule is fused into one kernel per configuration.
+// (2 J q)_v = 2 (J_vv q_v + phi_fix)_v.  Two paths: the FP64 check path (FP64
+// softmax, tiled FP64 GEMM on the CUDA cores, FP64 chain rule), and the fast
+// path, where one FP32 pass forms p, q and q's TF32 hi / lo planes, the
+// contraction runs on the tcgen05 tensor cores with both J and Q split into
+// TF32 hi / lo (three products), and the chain rule runs in FP32 with the
+// energy accumulated in FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -161,24 +163,11 @@ __global__ void k_grad_finish(const double* __restrict__ p, const double* __rest
     }
 }
 
-// q (B x Nv, FP64) -> TF32 hi / lo planes [2][Bpad][ld] (FP32 storage), zero padded.
 __device__ __forceinline__ float tf32_rna(float x)
 {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
-}
-
-__global__ void k_split_q(const double* __restrict__ q, int B, int Nv, int Bpad, int ld, float* __restrict__ qt2)
-{
-    const long plane = (long)Bpad * ld;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(e / ld), v = (int)(e % ld);
-        const double x = (b < B && v < Nv) ? q[(long)b * Nv + v] : 0.0;
-        const float hi = tf32_rna((float)x);
-        qt2[e] = hi;
-        qt2[plane + e] = tf32_rna((float)(x - (double)hi));
-    }
 }
 
 // p = softmax of the logits over the species allowed in the site's class, FP32 out.
@@ -196,6 +185,116 @@ __global__ void k_softmax_f32(const float* __restrict__ logits, long BN, int Nv,
     double den = 0.0;
     for (int s = 0; s < S; ++s) den += counts[k * S + s] > 0 ? exp((double)L[s] - m) : 0.0;
     for (int s = 0; s < S; ++s) p[t * S + s] = counts[k * S + s] > 0 ? (float)(exp((double)L[s] - m) / den) : 0.0f;
+}
+
+// ---- tensor-core (TF32x2) path: FP32 elementwise chain ----------------------
+// One pass over the padded operand: p = softmax of the logits over the
+// species allowed in the site's class (FP32, B x Nv x S), q = sum_s p_s z_s,
+// and q's TF32 hi / lo planes [2][Bpad][ld] for the contraction (zero padded).
+__global__ void k_relax_prep(const float* __restrict__ logits, int B, int Nv, int S, int Bpad, int ld,
+                             const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
+                             const double* __restrict__ z, float* __restrict__ p, float* __restrict__ qt2)
+{
+    const long plane = (long)Bpad * ld;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ld), v = (int)(e % ld);
+        float q = 0.0f;
+        if (b < B && v < Nv) {
+            const int k = vclass[v];
+            const long t = (long)b * Nv + v;
+            const float* L = logits + t * S;
+            float m = -INFINITY;
+            for (int s = 0; s < S; ++s)
+                if (counts[k * S + s] > 0) m = fmaxf(m, L[s]);
+            float den = 0.0f;
+            for (int s = 0; s < S; ++s) den += counts[k * S + s] > 0 ? expf(L[s] - m) : 0.0f;
+            const float inv = 1.0f / den;
+            for (int s = 0; s < S; ++s) {
+                const float ps = counts[k * S + s] > 0 ? expf(L[s] - m) * inv : 0.0f;
+                p[t * S + s] = ps;
+                q = fmaf(ps, (float)z[s], q);
+            }
+        }
+        const float hi = tf32_rna(q);
+        qt2[e] = hi;
+        qt2[plane + e] = tf32_rna(q - hi);
+    }
+}
+
+// colsum[(b*ncls + k)*S + s] = sum_{v in class k} p[b][v][s] from FP32 p:
+// per-thread FP32 partial sums over strided positions, FP64 block reduction.
+__global__ void k_colsum_f32(const float* __restrict__ p, int Nv, int S, int ncls, const int32_t* __restrict__ cls_start,
+                             const int32_t* __restrict__ cls_pos, double* __restrict__ colsum)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x / ncls, k = blockIdx.x % ncls;
+    const int cs = cls_start[k], ce = cls_start[k + 1];
+    for (int s = 0; s < S; ++s) {
+        float acc = 0.0f;
+        for (int i = cs + threadIdx.x; i < ce; i += blockDim.x) acc += p[((long)b * Nv + cls_pos[i]) * S + s];
+        red[threadIdx.x] = (double)acc;
+        __syncthreads();
+        for (int w = 128; w; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) colsum[((long)b * ncls + k) * S + s] = red[0];
+        __syncthreads();
+    }
+}
+
+// One block per configuration, FP32 chain rule (q recomputed from p), energy
+// accumulated in FP64: E_b = sum_v q_v (Phi_v + 2 phi_fix_v) + E_const + penalty.
+__global__ void k_grad_finish_f32(const float* __restrict__ p, const float* __restrict__ Phi, long phi_ld,
+                                  const double* __restrict__ phifix, const double* __restrict__ colsum,
+                                  const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
+                                  const double* __restrict__ z, int Nv, int S, int ncls, double lambda,
+                                  double E_const, double* __restrict__ E, float* __restrict__ dlogits)
+{
+    __shared__ double red[256];
+    __shared__ float zs[64];
+    const int b = blockIdx.x;
+    const double* cb = colsum + (long)b * ncls * S;
+    if (threadIdx.x < 64) zs[threadIdx.x] = threadIdx.x < S ? (float)z[threadIdx.x] : 0.0f;
+    __syncthreads();
+    double acc = 0.0;
+    for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
+        const long t = (long)b * Nv + v;
+        const float* pv = p + t * S;
+        const double pf = phifix[v];
+        const float jq = Phi[(long)b * phi_ld + v] + (float)pf;     // (J q)_v over all sites
+        float q = 0.0f;
+        for (int s = 0; s < S; ++s) q = fmaf(pv[s], zs[s], q);
+        acc += (double)q * ((double)Phi[(long)b * phi_ld + v] + 2.0 * pf);
+        if (dlogits) {
+            const int k = vclass[v];
+            float pg = 0.0f;
+            for (int s = 0; s < S; ++s) {
+                const float gs = zs[s] * 2.0f * jq + (float)(2.0 * lambda * (cb[k * S + s] - counts[k * S + s]));
+                pg = fmaf(pv[s], gs, pg);
+            }
+            for (int s = 0; s < S; ++s) {
+                const float gs = zs[s] * 2.0f * jq + (float)(2.0 * lambda * (cb[k * S + s] - counts[k * S + s]));
+                dlogits[t * S + s] = counts[k * S + s] > 0 ? pv[s] * (gs - pg) : 0.0f;
+            }
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double pen = 0.0;
+        for (int k = 0; k < ncls; ++k)
+            for (int s = 0; s < S; ++s)
+                if (counts[k * S + s] > 0) {
+                    const double r = cb[k * S + s] - counts[k * S + s];
+                    pen += r * r;
+                }
+        E[b] = red[0] + E_const + lambda * pen;
+    }
 }
 
 // L -= eta * dL (FP32, in place).
@@ -308,32 +407,39 @@ extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev
     const bool tc = precision == GOAC_PREC_TF32X2;
     const int Bpad = ((B + 127) / 128) * 128;
     const long BN = (long)B * Nv;
-    size_t need = sizeof(double) * ((size_t)BN * S + (size_t)BN + (size_t)B * ncls * S) + 2048;
-    need += tc ? sizeof(float) * (3 * (size_t)Bpad * ld) : sizeof(double) * (size_t)BN;
-    goac_status rc = goac::ensure(p->grad_tmp, need);
-    if (rc) return rc;
-    double* P_ = (double*)p->grad_tmp.ptr;
-    double* Q = P_ + BN * S;
-    double* colsum = Q + BN;
-    void* phi_base = (void*)(((uintptr_t)(colsum + (long)B * ncls * S) + 255) & ~(uintptr_t)255);   // TMA: 16-byte aligned
     cudaStream_t st = p->ctx->stream;
-    goac::launch(k_softmax, (int)((BN + 255) / 256), 256, 0, st, logits_dev, BN, Nv, S, p->vclass_dev, p->counts_dev,
-                 p->z_dev, P_, Q);
-    goac::launch(k_colsum, B * ncls, 256, 0, st, P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
     if (tc) {
-        float* qt2 = (float*)phi_base;
+        // FP32 elementwise chain around the TF32x2 contraction
+        size_t need = sizeof(float) * (size_t)BN * S + sizeof(double) * (size_t)B * ncls * S +
+                      sizeof(float) * 3 * (size_t)Bpad * ld + 1024;
+        goac_status rc = goac::ensure(p->grad_tmp, need);
+        if (rc) return rc;
+        float* P32 = (float*)p->grad_tmp.ptr;
+        double* colsum = (double*)(((uintptr_t)(P32 + BN * S) + 255) & ~(uintptr_t)255);
+        float* qt2 = (float*)(((uintptr_t)(colsum + (long)B * ncls * S) + 255) & ~(uintptr_t)255);   // TMA: aligned
         float* Phi = qt2 + 2 * (size_t)Bpad * ld;
         const long plane = (long)Bpad * ld;
-        goac::launch(k_split_q, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, (const double*)Q, B,
-                     Nv, Bpad, ld, qt2);
-        GOAC_LAUNCH_CHECK("k_split_q");
+        goac::launch(k_relax_prep, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, logits_dev, B,
+                     Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2);
+        goac::launch(k_colsum_f32, B * ncls, 256, 0, st, (const float*)P32, Nv, S, ncls, p->cls_start_dev,
+                     p->cls_pos_dev, colsum);
+        GOAC_LAUNCH_CHECK("k_relax_prep");
         rc = goac::phi_tc(p, qt2, Bpad, Phi);
         if (rc) return rc;
-        goac::launch(k_grad_finish<float>, B, 256, 0, st, (const double*)P_, (const double*)Q, (const float*)Phi,
-                     (long)ld, (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev,
-                     Nv, S, ncls, lambda, p->E_const, E_dev, dlogits_dev);
+        goac::launch(k_grad_finish_f32, B, 256, 0, st, (const float*)P32, (const float*)Phi, (long)ld,
+                     (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
+                     ncls, lambda, p->E_const, E_dev, dlogits_dev);
     } else {
-        double* Phi = (double*)phi_base;
+        size_t need = sizeof(double) * ((size_t)BN * S + (size_t)BN + (size_t)B * ncls * S + (size_t)BN) + 2048;
+        goac_status rc = goac::ensure(p->grad_tmp, need);
+        if (rc) return rc;
+        double* P_ = (double*)p->grad_tmp.ptr;
+        double* Q = P_ + BN * S;
+        double* colsum = Q + BN;
+        double* Phi = colsum + (long)B * ncls * S;
+        goac::launch(k_softmax, (int)((BN + 255) / 256), 256, 0, st, logits_dev, BN, Nv, S, p->vclass_dev,
+                     p->counts_dev, p->z_dev, P_, Q);
+        goac::launch(k_colsum, B * ncls, 256, 0, st, P_, Nv, S, ncls, p->cls_start_dev, p->cls_pos_dev, colsum);
         dim3 grid((B + GM - 1) / GM, (Nv + GM - 1) / GM);
         goac::launch(k_phi_real, grid, 256, 0, st, (const double*)p->J_vv, ld, Nv, (const double*)Q, B, Phi);
         goac::launch(k_grad_finish<double>, B, 256, 0, st, (const double*)P_, (const double*)Q, (const double*)Phi,

@@ -614,6 +614,8 @@ extern "C" goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, i
             p->cls_pos[p->cls_start[k] + fill[k]++] = v;
         }
     }
+    std::vector<int32_t> cls_rank(Nv);
+    for (int q = 0; q < Nv; ++q) cls_rank[p->cls_pos[q]] = q;
     p->wprefix.resize(n_class);
     uint64_t acc = 0;
     for (int k = 0; k < n_class; ++k) {
@@ -648,6 +650,7 @@ extern "C" goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, i
     PTRY(cudaMalloc(&p->vclass_dev, sizeof(int32_t) * Nv));
     PTRY(cudaMalloc(&p->cls_start_dev, sizeof(int32_t) * (n_class + 1)));
     PTRY(cudaMalloc(&p->cls_pos_dev, sizeof(int32_t) * Nv));
+    PTRY(cudaMalloc(&p->cls_rank_dev, sizeof(int32_t) * Nv));
     PTRY(cudaMalloc(&p->counts_dev, sizeof(int32_t) * n_class * S));
     PTRY(cudaMalloc(&p->wprefix_dev, sizeof(uint32_t) * n_class));
     PTRY(cudaMalloc(&d_vsite, sizeof(int32_t) * Nv));
@@ -664,6 +667,7 @@ extern "C" goac_status goac_problem_create(goac_ctx* ctx, const double* J_dev, i
         PTRY(cudaMemcpyAsync(p->cls_start_dev, p->cls_start.data(), sizeof(int32_t) * (n_class + 1),
                              cudaMemcpyHostToDevice, st));
         PTRY(cudaMemcpyAsync(p->cls_pos_dev, p->cls_pos.data(), sizeof(int32_t) * Nv, cudaMemcpyHostToDevice, st));
+        PTRY(cudaMemcpyAsync(p->cls_rank_dev, cls_rank.data(), sizeof(int32_t) * Nv, cudaMemcpyHostToDevice, st));
         PTRY(cudaMemcpyAsync(p->counts_dev, counts_host, sizeof(int32_t) * n_class * S, cudaMemcpyHostToDevice, st));
         PTRY(cudaMemcpyAsync(p->wprefix_dev, p->wprefix.data(), sizeof(uint32_t) * n_class, cudaMemcpyHostToDevice,
                              st));
@@ -711,6 +715,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->vclass_dev);
     cudaFree(p->cls_start_dev);
     cudaFree(p->cls_pos_dev);
+    cudaFree(p->cls_rank_dev);
     cudaFree(p->counts_dev);
     cudaFree(p->wprefix_dev);
     cudaFree(p->J_bf16);
