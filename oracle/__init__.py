@@ -94,6 +94,7 @@ def _declare(lib):
         "orc_energy_grad": (_d, [_p, _i64, _p, _p, _p, _i32, _p, _p, _d, _p]),
         "orc_round_to_counts": (C.c_int, [_i64, _p, _i32, _p, _p, _p]),
         "orc_enumerate": (_i64, [_p, _i64, _p, _p, _p, _i32, _p, _d, _p, _p, _i64, _p, _p, _i64]),
+        "orc_enumerate_two_species": (_i64, [_p, _i64, _p, _p, _p, _p, _d, _p, _p, _i64, _p]),
         "orc_log10_configurations": (_d, [_i32, _p, _i32, _p]),
     }
     for name, (res, args) in sig.items():
@@ -424,6 +425,24 @@ def enumerate_all(J, site_class, fixed_q, z, counts, tol=1e-9, max_argmin=4096, 
     k = int(min(nmin[0], max_argmin))
     return {"n_configs": int(total), "Emin": float(emin[0]), "argmin": amin[:k].copy(),
             "n_argmin": int(nmin[0]), "all_E": allE[:min(total, max_all)].copy() if max_all else None}
+
+
+def enumerate_two_species(J, site_class, fixed_q, z, counts, tol=1e-9, max_argmin=4096):
+    """Exhaustive minimum of a problem whose one movable class holds two
+    species (orc_enumerate_two_species): every C(n, k) placement."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    nv = int((sc >= 0).sum())
+    emin = np.zeros(1)
+    amin = np.zeros((max(max_argmin, 1), nv), dtype=np.int8)
+    nmin = np.zeros(1, dtype=np.int64)
+    total = _load().orc_enumerate_two_species(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)),
+                                              _ptr(_i32a(np.asarray(counts).ravel())), tol, _ptr(emin), _ptr(amin),
+                                              max_argmin, _ptr(nmin))
+    if total < 0:
+        raise ValueError("enumerate_two_species: needs one movable class holding two species")
+    k = int(min(nmin[0], max_argmin))
+    return {"n_configs": int(total), "Emin": float(emin[0]), "argmin": amin[:k].copy(), "n_argmin": int(nmin[0])}
 
 
 def log10_configurations(positions, n_se):

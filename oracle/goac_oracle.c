@@ -46,6 +46,8 @@
  *   orc_round_to_counts    pinned: counts; brute-force optimality of the
  *                          greedy on a one-hot input.
  *   orc_enumerate          pinned: exact count of Eq. 1; closed-form NaCl.
+ *   orc_enumerate_two_species  pinned: equals orc_enumerate (minimum, its
+ *                          minimisers, the count) on cells small enough for both.
  *   orc_log10_configurations  pinned: Table 1 and the NaCl / FeSbO4 counts.
  */
 #include <math.h>
@@ -1103,6 +1105,117 @@ int64_t orc_enumerate(const double* J, int64_t N, const int32_t* site_class, con
     free(cur);
     free(sp);
     free(q);
+    free_classes(&cl);
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exhaustive enumeration for a problem whose only movable class holds two  */
+/* species (every other site fixed): all C(n, k) placements of the k sites  */
+/* of the second species among the class's n positions.  With q0 the        */
+/* charges with species 0 everywhere in the class and delta = z1 - z0, the  */
+/* energy of the set S of second-species positions is                       */
+/*   E(S) = E0 + sum_{i in S} h_i + sum_{i<j in S} W_ij,                    */
+/*   E0 = q0^T J q0,  h_i = 2 delta (J q0)_i + delta^2 J_ii,                */
+/*   W_ij = 2 delta^2 J_ij,                                                 */
+/* the quadratic form expanded in the occupation variables (Eq. 2 with two  */
+/* species).  Positions are visited in order, depth first, include before  */
+/* exclude; adding position i adds h_i + g_i with g = sum_{j in S} W_.j, and */
+/* g is kept per depth (no undo, no drift).  Returns the number of          */
+/* configurations, the minimum energy and the minimisers within tol (as     */
+/* species vectors over the variable sites, up to max_argmin of them).      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, k;
+    const double* h;     /* n */
+    const double* W;     /* n x n */
+    double* g;           /* (k + 1) x n: field of the chosen set at each depth */
+    int32_t* chosen;     /* k */
+    double tol, best;
+    int64_t total, nmin, max_argmin;
+    int32_t* argsets;    /* max_argmin x k */
+} enum2_t;
+
+static void enum2_rec(enum2_t* st, int64_t pos, int64_t depth, double E)
+{
+    if (depth == st->k) {
+        st->total++;
+        if (E < st->best - st->tol) {
+            st->best = E;
+            st->nmin = 0;
+        }
+        if (fabs(E - st->best) <= st->tol) {
+            if (st->nmin < st->max_argmin)
+                memcpy(st->argsets + st->nmin * st->k, st->chosen, sizeof(int32_t) * (size_t)st->k);
+            st->nmin++;
+        }
+        return;
+    }
+    if (st->n - pos < st->k - depth) return;
+    /* include position pos */
+    const double* g = st->g + depth * st->n;
+    double* g2 = st->g + (depth + 1) * st->n;
+    const double* Wp = st->W + pos * st->n;
+    for (int64_t j = 0; j < st->n; ++j) g2[j] = g[j] + Wp[j];
+    st->chosen[depth] = (int32_t)pos;
+    enum2_rec(st, pos + 1, depth + 1, E + st->h[pos] + g[pos]);
+    /* exclude it */
+    enum2_rec(st, pos + 1, depth, E);
+}
+
+int64_t orc_enumerate_two_species(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q,
+                                  const double* z, const int32_t* counts, double tol, double* Emin,
+                                  int8_t* argmin, int64_t max_argmin, int64_t* n_argmin)
+{
+    classes_t cl = make_classes(site_class, N);
+    if (cl.nmovable != 1 || cl.ncls != 1 || counts[0] + counts[1] != cl.nv) {
+        free_classes(&cl);
+        return -1;
+    }
+    const int64_t n = cl.nv, k = counts[1];
+    int8_t* sp0 = (int8_t*)calloc((size_t)n + 1, 1);       /* species 0 everywhere */
+    double* q0 = (double*)malloc(sizeof(double) * (size_t)N);
+    orc_config_charges(N, site_class, fixed_q, z, sp0, q0);
+    const double delta = z[1] - z[0];
+    double* h = (double*)malloc(sizeof(double) * (size_t)n);
+    double* W = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    for (int64_t a = 0; a < n; ++a) {
+        const int64_t ia = cl.vsite[a];
+        double jq = 0.0;
+        for (int64_t j = 0; j < N; ++j) jq += J[ia * N + j] * q0[j];
+        h[a] = 2.0 * delta * jq + delta * delta * J[ia * N + ia];
+        for (int64_t b = 0; b < n; ++b) W[a * n + b] = a == b ? 0.0 : 2.0 * delta * delta * J[ia * N + cl.vsite[b]];
+    }
+    enum2_t st;
+    st.n = n;
+    st.k = k;
+    st.h = h;
+    st.W = W;
+    st.g = (double*)calloc((size_t)((k + 1) * n), sizeof(double));
+    st.chosen = (int32_t*)malloc(sizeof(int32_t) * (size_t)(k + 1));
+    st.tol = tol;
+    st.best = INFINITY;
+    st.total = 0;
+    st.nmin = 0;
+    st.max_argmin = max_argmin;
+    st.argsets = (int32_t*)malloc(sizeof(int32_t) * (size_t)((max_argmin > 0 ? max_argmin : 1) * (k + 1)));
+    enum2_rec(&st, 0, 0, orc_qJq(J, q0, N));
+    *Emin = st.best;
+    if (n_argmin) *n_argmin = st.nmin;
+    const int64_t kept = st.nmin < max_argmin ? st.nmin : max_argmin;
+    for (int64_t m = 0; m < kept && argmin; ++m) {
+        int8_t* out = argmin + m * n;
+        memset(out, 0, (size_t)n);
+        for (int64_t t = 0; t < k; ++t) out[st.argsets[m * k + t]] = 1;
+    }
+    const int64_t total = st.total;
+    free(st.g);
+    free(st.chosen);
+    free(st.argsets);
+    free(h);
+    free(W);
+    free(q0);
+    free(sp0);
     free_classes(&cl);
     return total;
 }
