@@ -172,3 +172,38 @@ def test_round_to_counts_parity(ctx, B):
         ref = oracle.round_to_counts(prob.site_class, prob.counts, p[b])
         assert np.array_equal(got[b], ref)
     assert _counts_ok(prob, got)
+
+
+def test_energy_grad_full_size(ctx):
+    """bcc N = 8192, 5 species (the differentiation workload): the TF32x2 path
+    within the form's bound of the FP64 path (pinned to the oracle above), and
+    the FP64 adjoint against central differences of the FP64 energy on sampled
+    logits (h = 1e-4, the actual FP32 step taken)."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.bcc_relaxed_problem()
+    J = g.build_ewald(ctx, prob.lattice, torch.tensor(prob.frac, device="cuda"), prob.alpha, prob.nimg, prob.kcut)
+    gp = g.Problem(ctx, J, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
+    B, lam = 4, 1.0
+    L = torch.tensor(synth.random_logits(prob, B, 21), device="cuda")
+    E64, g64 = gp.energy_grad(L, lam, "f64")
+    Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
+    z = torch.tensor(prob.z, device="cuda")
+    p = torch.softmax(L.double(), dim=2)
+    q = p @ z
+    mass = J.abs() @ q.abs().T                       # (N, B): sum_w |J_vw q_w|
+    eps = 3 * gp.Nv * 2.0 ** -24 + 2.0 ** -20
+    boundE = eps * (q.abs() * mass.T).sum(dim=1) + 1e-9
+    assert torch.all((Etc - E64).abs() <= boundE)
+    boundG = 4 * z.abs().max() * p * (eps * mass.T)[:, :, None] + 2.0 ** -23 * g64.abs()
+    assert torch.all((gtc - g64).abs() <= boundG + 1e-30)
+    rng = np.random.default_rng(5)
+    for _ in range(8):
+        b, v, s = int(rng.integers(B)), int(rng.integers(gp.Nv)), int(rng.integers(prob.S))
+        Lp, Lm = L[b:b + 1].clone(), L[b:b + 1].clone()
+        Lp[0, v, s] += 1e-4
+        Lm[0, v, s] -= 1e-4
+        h2 = float(Lp[0, v, s].double() - Lm[0, v, s].double())
+        Ep, _ = gp.energy_grad(Lp, lam, "f64")
+        Em, _ = gp.energy_grad(Lm, lam, "f64")
+        fd = (Ep.item() - Em.item()) / h2
+        assert abs(fd - g64[b, v, s].item()) <= 1e-5 * g64[b].abs().max().item() + 1e-6

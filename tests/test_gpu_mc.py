@@ -242,3 +242,61 @@ def test_mc_exact_potentials_full_size(ctx):
     out = gp.mc_run(sp, 0.05, 64, 1)
     E64 = gp.score(sp, "f64")
     assert ((out["E"] - E64).abs() / E64.abs()).max().item() <= 1e-10
+
+
+def test_batch_full_size_sampled(ctx):
+    """The uneven batch at full size (256 cells, N 64..2048, 512 chains each)
+    in the graph-captured persistent launch: counts preserved in every chain,
+    all 512 chains of the three smallest cells identical to the oracle's, and
+    the chains of the three largest cells with running energies equal to FP64
+    rescoring."""
+    import paper_2409_08808_gb300 as g
+    cells = synth.batch_problems(256)
+    C, steps = 512, 64
+    gps, sps, kts, starts = [], [], [], []
+    for i, pr in enumerate(cells):
+        J = g.build_ewald(ctx, pr.lattice, torch.tensor(pr.frac, device="cuda"), pr.alpha, pr.nimg, pr.kcut)
+        gps.append(gpu_problem(ctx, pr, J))
+        sps.append(gps[-1].random_configs(C, 100 + i))
+        starts.append(sps[-1].clone())
+        kts.append(torch.full((C,), pr.kT, dtype=torch.float64, device="cuda"))
+    E, _ = g.batch_mc_run(ctx, gps, sps, kts, steps, 7, mode=2)
+    torch.cuda.synchronize()
+    for pr, sp in zip(cells, sps):
+        vclass = pr.site_class[pr.site_class >= 0]
+        fin = sp.cpu().numpy()
+        for k in range(pr.n_class):
+            for s in range(pr.S):
+                assert np.all(((vclass[None, :] == k) & (fin == s)).sum(axis=1) == pr.counts[k, s])
+    order = np.argsort([pr.N for pr in cells])
+    for i in order[:3]:
+        pr = cells[i]
+        Jo = oracle.ewald_J(pr.lattice, pr.frac, pr.alpha, pr.nimg, pr.kcut)
+        ref = oracle.mc_run(Jo, pr.site_class, pr.fixed_q, pr.z, starts[i].cpu().numpy(), pr.kT, steps, 7 + int(i))
+        assert np.array_equal(sps[i].cpu().numpy(), ref["species"]), (i, pr.N)
+        assert np.allclose(E[i].cpu().numpy(), ref["E"], rtol=1e-10)
+    for i in order[-3:]:
+        E64 = gps[i].score(sps[i], "f64")
+        assert torch.allclose(E[i], E64, rtol=1e-10, atol=0)
+
+
+def test_sa_finds_exhaustive_ground_state(ctx):
+    """Rocksalt 2x2x2 cation problem (N = 64, C(32, 16) = 601,080,390
+    configurations): simulated annealing on the GPU (1,024 chains x 20,000
+    swaps, kT 1.0 -> 0.002 eV, FP64) reaches the oracle's exhaustive minimum,
+    and the best configurations it returns are among the stored minimisers."""
+    from test_oracle_ground_state import read_golden
+    vals, arg = read_golden()
+    prob = synth.rocksalt_problem((2, 2, 2), 4.2)
+    import paper_2409_08808_gb300 as g
+    Jg = g.build_ewald(ctx, prob.lattice, torch.tensor(prob.frac, device="cuda"), prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, Jg)
+    sp = gp.random_configs(1024, 3)
+    out = gp.sa_run(sp, 1.0, 0.002, 20000, 20000, 17)
+    bestE = out["bestE"].cpu().numpy()
+    assert bestE.min() == pytest.approx(vals["E_min_eV"], rel=1e-10, abs=0)
+    assert np.all(bestE >= vals["E_min_eV"] - 1e-9)
+    minimisers = set(map(tuple, arg.tolist()))
+    hits = np.nonzero(bestE <= vals["E_min_eV"] + 1e-9)[0]
+    best_sp = out["best_species"].cpu().numpy()
+    assert all(tuple(best_sp[i].tolist()) in minimisers for i in hits)
