@@ -9,7 +9,7 @@
 //                 sum as exact 64-bit integers (one block, ordered scan), so
 //                 roulette selection is an exact integer search.
 //   k_ga_rank     ranks by (E, index) to pick the elite (O(P^2) comparisons,
-//                 tiled through shared memory).
+//                 one warp per individual).
 //   k_ga_children one warp per child: parents by binary search of the running
 //                 sum, crossover in shared memory (the warp scans 32 sites at a
 //                 time with ballots; the partner site j of a candidate swap is
@@ -86,25 +86,22 @@ __global__ void __launch_bounds__(1024) k_ga_fitness(const double* __restrict__ 
     if (threadIdx.x == 0) *ftot = carry;
 }
 
+// Elite selection: the rank of individual i by (E, index) is the number of j
+// with E_j < E_i, or E_j == E_i and j < i; one warp per i (lanes stride over
+// j, warp sum), so the O(P^2) comparisons spread over P warps.
 __global__ void k_ga_rank(const double* __restrict__ E, int P, int k, int* __restrict__ sel)
 {
-    __shared__ double tile[256];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const double ei = i < P ? E[i] : 0.0;
+    const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= P) return;                       // whole warps leave together
+    const double ei = E[i];
     int rank = 0;
-    for (int j0 = 0; j0 < P; j0 += 256) {
-        const int j = j0 + threadIdx.x;
-        tile[threadIdx.x] = j < P ? E[j] : 0.0;
-        __syncthreads();
-        const int lim = min(256, P - j0);
-        if (i < P)
-            for (int t = 0; t < lim; ++t) {
-                const double ej = tile[t];
-                rank += (ej < ei) || (ej == ei && j0 + t < i);
-            }
-        __syncthreads();
+    for (int j = lane; j < P; j += 32) {
+        const double ej = E[j];
+        rank += (ej < ei) || (ej == ei && j < i);
     }
-    if (i < P && rank < k) sel[rank] = i;
+    rank = __reduce_add_sync(0xffffffffu, rank);
+    if (lane == 0 && rank < k) sel[rank] = i;
 }
 
 struct GaArgs {
@@ -333,7 +330,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     int* elite = (int*)(mm + 2);
     goac::launch(k_ga_minmax, 1, 1024, 0, st, E, P, mm);
     goac::launch(k_ga_fitness, 1, 1024, 0, st, E, P, mm, pre, ftot);
-    if (n_elite > 0) goac::launch(k_ga_rank, (P + 255) / 256, 256, 0, st, E, P, n_elite, elite);
+    if (n_elite > 0) goac::launch(k_ga_rank, (P + 7) / 8, 256, 0, st, E, P, n_elite, elite);
     GOAC_LAUNCH_CHECK("ga prep");
     GaArgs a;
     a.pop = pop;
