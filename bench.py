@@ -425,6 +425,13 @@ def run_ours(args, world, rank, local):
                     "steps_per_chain": args.mc_steps, "kT_eV": 0.05, "acceptance": acc, "ms": mms,
                     "hbm_gbs_algorithmic": bytes_alg / (mc_kms / 1e3) / 1e9,
                     "hbm_frac": bytes_alg / (mc_kms / 1e3) / 1e9 / hbm_peak}
+        if prec == "f64":
+            # the FP64 chain is bound by the FP64 pipe: per accepted swap one subtract and one FMA
+            # per site (the potential update); peak = 152 SMs x 2 FP64 FMA/clk x 2.07 GHz
+            # (6.29e11 instr/s, the rate the FP64 SYRK reaches at 99 % FP64-pipe activity)
+            fp64_instr = acc * trials * 2.0 * prob.N
+            mc[prec]["fp64_instr_per_s_update"] = fp64_instr / (mc_kms / 1e3)
+            mc[prec]["fp64_pipe_frac_update"] = fp64_instr / (mc_kms / 1e3) / (152 * 2 * 2.07e9)
 
     cpu = None
     if rank == 0:
