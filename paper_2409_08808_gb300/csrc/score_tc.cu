@@ -21,6 +21,9 @@
 // in FP64 into partial[m-tile][config].  The linear term 2 q . phi_fix is formed
 // in FP64 while Q is built (k_make_qt), and a second tiny kernel adds the
 // m-tiles in a fixed order plus the linear term and E_const (deterministic).
+// The three kernels of a step are chained as programmatic dependent launches:
+// each successor sets itself up while its predecessor drains and waits
+// (griddepcontrol.wait) before reading the predecessor's output.
 #include <cudaTypedefs.h>
 
 #include <math.h>
@@ -100,6 +103,10 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     goacd::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // launched as a dependent of k_make_qt: the set-up above overlaps its tail;
+    // Q^T (and the linear term) are read only after it has completed
+    goacd::pdl_wait();
+    goacd::pdl_trigger();
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -862,6 +869,7 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
 {
     __shared__ float zs[64];
     __shared__ double red[256];
+    goacd::pdl_trigger();       // the scoring kernel may set itself up meanwhile
     if (threadIdx.x < 64) zs[threadIdx.x] = (float)zq[threadIdx.x];
     __syncthreads();
     const int b = blockIdx.x;
@@ -922,6 +930,7 @@ __global__ void k_finish_exact(const double* __restrict__ partial, int npanels, 
 __global__ void k_finish_tc(const double* __restrict__ partial, int mtiles, int Bpad, int B, double E_const,
                             const double* __restrict__ lin, double* __restrict__ E)
 {
+    goacd::pdl_wait();          // the partial sums of the scoring kernel
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
@@ -1031,7 +1040,7 @@ goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap&
     goac_status rc = tc_schedule(p, nbm, nbn, grid, &work, &starts);
     if (rc) return rc;
     goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
-    goac::launch(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, nkb, ld, qt, ld, part, Bpad,
+    goac::launch_pdl(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, nkb, ld, qt, ld, part, Bpad,
                  p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_score_tc");
     return GOAC_OK;
@@ -1284,7 +1293,7 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
         default: return fail(GOAC_ERR_INVALID_ARG, "score_tc: bad precision");
     }
     if (rc) return rc;
-    goac::launch(k_finish_tc, (B + 255) / 256, 256, 0, st, part, ld / TC_M, Bpad, B, p->E_const, lin, E_out);
+    goac::launch_pdl(k_finish_tc, (B + 255) / 256, 256, 0, st, part, ld / TC_M, Bpad, B, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_tc");
     return GOAC_OK;
 }
