@@ -221,61 +221,102 @@ __global__ void k_relax_prep(const float* __restrict__ logits, int B, int Nv, in
     }
 }
 
-// colsum[(b*ncls + k)*S + s] = sum_{v in class k} p[b][v][s] from FP32 p:
-// per-thread FP32 partial sums over strided positions, FP64 block reduction.
-__global__ void k_colsum_f32(const float* __restrict__ p, int Nv, int S, int ncls, const int32_t* __restrict__ cls_start,
-                             const int32_t* __restrict__ cls_pos, double* __restrict__ colsum)
+// colsum[(b*ncls + k)*S + s] = sum_{v in class k} p[b][v][s] from FP32 p, one
+// block per (b, k) and one pass over the class's sites: each thread keeps FP32
+// partial sums of all species (S <= 8) of its strided positions, then the block
+// adds them in FP64 in a fixed order.  More species: one pass per species.
+__global__ void __launch_bounds__(256) k_colsum_f32(const float* __restrict__ p, int Nv, int S, int ncls,
+                                                    const int32_t* __restrict__ cls_start,
+                                                    const int32_t* __restrict__ cls_pos, double* __restrict__ colsum)
 {
-    __shared__ double red[256];
+    __shared__ double red[8][256];
     const int b = blockIdx.x / ncls, k = blockIdx.x % ncls;
     const int cs = cls_start[k], ce = cls_start[k + 1];
+    if (S <= 8) {
+        float a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = cs + threadIdx.x; i < ce; i += blockDim.x) {
+            const float* pv = p + ((long)b * Nv + cls_pos[i]) * S;
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (s < S) a[s] += pv[s];
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) red[s][threadIdx.x] = (double)a[s];
+        __syncthreads();
+        for (int w = 128; w; w >>= 1) {
+            if (threadIdx.x < w)
+#pragma unroll
+                for (int s = 0; s < 8; ++s) red[s][threadIdx.x] += red[s][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x < S) colsum[((long)b * ncls + k) * S + threadIdx.x] = red[threadIdx.x][0];
+        return;
+    }
     for (int s = 0; s < S; ++s) {
         float acc = 0.0f;
         for (int i = cs + threadIdx.x; i < ce; i += blockDim.x) acc += p[((long)b * Nv + cls_pos[i]) * S + s];
-        red[threadIdx.x] = (double)acc;
+        red[0][threadIdx.x] = (double)acc;
         __syncthreads();
         for (int w = 128; w; w >>= 1) {
-            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            if (threadIdx.x < w) red[0][threadIdx.x] += red[0][threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) colsum[((long)b * ncls + k) * S + s] = red[0];
+        if (threadIdx.x == 0) colsum[((long)b * ncls + k) * S + s] = red[0][0];
         __syncthreads();
     }
 }
 
 // One block per configuration, FP32 chain rule (q recomputed from p), energy
 // accumulated in FP64: E_b = sum_v q_v (Phi_v + 2 phi_fix_v) + E_const + penalty.
-__global__ void k_grad_finish_f32(const float* __restrict__ p, const float* __restrict__ Phi, long phi_ld,
-                                  const double* __restrict__ phifix, const double* __restrict__ colsum,
-                                  const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
-                                  const double* __restrict__ z, int Nv, int S, int ncls, double lambda,
-                                  double E_const, double* __restrict__ E, float* __restrict__ dlogits)
+// The per-(class, species) penalty terms 2 lambda (colsum - n) and the allowed
+// mask are formed once per block (FP64, then FP32) in shared memory.
+__global__ void __launch_bounds__(256) k_grad_finish_f32(const float* __restrict__ p, const float* __restrict__ Phi,
+                                                         long phi_ld, const double* __restrict__ phifix,
+                                                         const double* __restrict__ colsum,
+                                                         const int32_t* __restrict__ vclass,
+                                                         const int32_t* __restrict__ counts,
+                                                         const double* __restrict__ z, int Nv, int S, int ncls,
+                                                         double lambda, double E_const, double* __restrict__ E,
+                                                         float* __restrict__ dlogits)
 {
+    constexpr int PEN_MAX = 512;                  // ncls * S entries held in shared memory
     __shared__ double red[256];
     __shared__ float zs[64];
+    __shared__ float pen[PEN_MAX];
+    __shared__ unsigned char allowed[PEN_MAX];
     const int b = blockIdx.x;
     const double* cb = colsum + (long)b * ncls * S;
+    const int npen = ncls * S;
     if (threadIdx.x < 64) zs[threadIdx.x] = threadIdx.x < S ? (float)z[threadIdx.x] : 0.0f;
+    for (int e = threadIdx.x; e < npen && e < PEN_MAX; e += blockDim.x) {
+        pen[e] = (float)(2.0 * lambda * (cb[e] - counts[e]));
+        allowed[e] = counts[e] > 0;
+    }
     __syncthreads();
+    const bool in_smem = npen <= PEN_MAX;
     double acc = 0.0;
     for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
         const long t = (long)b * Nv + v;
         const float* pv = p + t * S;
-        const double pf = phifix[v];
-        const float jq = Phi[(long)b * phi_ld + v] + (float)pf;     // (J q)_v over all sites
+        const float pf = (float)phifix[v];
+        const float phi = Phi[(long)b * phi_ld + v];
+        const float jq = phi + pf;                 // (J q)_v over all sites
         float q = 0.0f;
         for (int s = 0; s < S; ++s) q = fmaf(pv[s], zs[s], q);
-        acc += (double)q * ((double)Phi[(long)b * phi_ld + v] + 2.0 * pf);
+        acc += (double)(q * (phi + 2.0f * pf));
         if (dlogits) {
             const int k = vclass[v];
             float pg = 0.0f;
             for (int s = 0; s < S; ++s) {
-                const float gs = zs[s] * 2.0f * jq + (float)(2.0 * lambda * (cb[k * S + s] - counts[k * S + s]));
-                pg = fmaf(pv[s], gs, pg);
+                const int e = k * S + s;
+                const float pe = in_smem ? pen[e] : (float)(2.0 * lambda * (cb[e] - counts[e]));
+                pg = fmaf(pv[s], fmaf(2.0f * zs[s], jq, pe), pg);
             }
             for (int s = 0; s < S; ++s) {
-                const float gs = zs[s] * 2.0f * jq + (float)(2.0 * lambda * (cb[k * S + s] - counts[k * S + s]));
-                dlogits[t * S + s] = counts[k * S + s] > 0 ? pv[s] * (gs - pg) : 0.0f;
+                const int e = k * S + s;
+                const bool al = in_smem ? allowed[e] != 0 : counts[e] > 0;
+                const float pe = in_smem ? pen[e] : (float)(2.0 * lambda * (cb[e] - counts[e]));
+                dlogits[t * S + s] = al ? pv[s] * (fmaf(2.0f * zs[s], jq, pe) - pg) : 0.0f;
             }
         }
     }
@@ -286,14 +327,14 @@ __global__ void k_grad_finish_f32(const float* __restrict__ p, const float* __re
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double pen = 0.0;
+        double pn = 0.0;
         for (int k = 0; k < ncls; ++k)
             for (int s = 0; s < S; ++s)
                 if (counts[k * S + s] > 0) {
                     const double r = cb[k * S + s] - counts[k * S + s];
-                    pen += r * r;
+                    pn += r * r;
                 }
-        E[b] = red[0] + E_const + lambda * pen;
+        E[b] = red[0] + E_const + lambda * pn;
     }
 }
 
