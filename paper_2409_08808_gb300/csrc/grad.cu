@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_grad_finish_f32(const float* __restrict
                                                          const int32_t* __restrict__ counts,
                                                          const double* __restrict__ z, int Nv, int S, int ncls,
                                                          double lambda, double E_const, double* __restrict__ E,
-                                                         float* __restrict__ dlogits)
+                                                         float* __restrict__ dlogits, float* logits_upd, float eta)
 {
     constexpr int PEN_MAX = 512;                  // ncls * S entries held in shared memory
     __shared__ double red[256];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_grad_finish_f32(const float* __restrict
         float q = 0.0f;
         for (int s = 0; s < S; ++s) q = fmaf(pv[s], zs[s], q);
         acc += (double)(q * (phi + 2.0f * pf));
-        if (dlogits) {
+        if (dlogits || logits_upd) {
             const int k = vclass[v];
             float pg = 0.0f;
             for (int s = 0; s < S; ++s) {
@@ -316,7 +316,10 @@ __global__ void __launch_bounds__(256) k_grad_finish_f32(const float* __restrict
                 const int e = k * S + s;
                 const bool al = in_smem ? allowed[e] != 0 : counts[e] > 0;
                 const float pe = in_smem ? pen[e] : (float)(2.0 * lambda * (cb[e] - counts[e]));
-                dlogits[t * S + s] = al ? pv[s] * (fmaf(2.0f * zs[s], jq, pe) - pg) : 0.0f;
+                const float g = al ? pv[s] * (fmaf(2.0f * zs[s], jq, pe) - pg) : 0.0f;
+                if (dlogits) dlogits[t * S + s] = g;
+                // descent step in place (this step's p was formed from the old logits)
+                if (logits_upd) logits_upd[t * S + s] = logits_upd[t * S + s] - eta * g;
             }
         }
     }
@@ -436,8 +439,22 @@ __global__ void k_round_greedy(const unsigned long long* __restrict__ keys, int 
 
 }  // namespace
 
+// Energies and dE/dL (dlogits_dev, nullable); with logits_upd (TF32x2 only) the
+// chain-rule kernel also applies L -= eta dE/dL in place, so that a descent step
+// needs no separate pass over the gradient.
+static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, int32_t B, double lambda,
+                                    int32_t precision, double* E_dev, float* dlogits_dev, float* logits_upd,
+                                    float eta);
+
 extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev, int32_t B, double lambda,
                                         int32_t precision, double* E_dev, float* dlogits_dev)
+{
+    return energy_grad_impl(p, logits_dev, B, lambda, precision, E_dev, dlogits_dev, nullptr, 0.0f);
+}
+
+static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, int32_t B, double lambda,
+                                    int32_t precision, double* E_dev, float* dlogits_dev, float* logits_upd,
+                                    float eta)
 {
     if (!p || !logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
     if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0");
@@ -469,7 +486,7 @@ extern "C" goac_status goac_energy_grad(goac_problem* p, const float* logits_dev
         if (rc) return rc;
         goac::launch(k_grad_finish_f32, B, 256, 0, st, (const float*)P32, (const float*)Phi, (long)ld,
                      (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
-                     ncls, lambda, p->E_const, E_dev, dlogits_dev);
+                     ncls, lambda, p->E_const, E_dev, dlogits_dev, logits_upd, eta);
     } else {
         size_t need = sizeof(double) * ((size_t)BN * S + (size_t)BN + (size_t)B * ncls * S + (size_t)BN) + 2048;
         goac_status rc = goac::ensure(p->grad_tmp, need);
@@ -542,6 +559,12 @@ extern "C" goac_status goac_relaxed_descent(goac_problem* p, float* logits_dev, 
     const long n = (long)B * p->Nv * p->S;
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
     for (int it = 0; it < n_steps; ++it) {
+        if (precision == GOAC_PREC_TF32X2) {
+            // gradient and step fused: the chain-rule kernel updates the logits in place
+            goac_status rc = energy_grad_impl(p, logits_dev, B, lambda, precision, E_dev, nullptr, logits_dev, (float)eta);
+            if (rc) return rc;
+            continue;
+        }
         goac_status rc = goac_energy_grad(p, logits_dev, B, lambda, precision, E_dev, dlogits_scratch_dev);
         if (rc) return rc;
         goac::launch(k_descent_step, blocks, 256, 0, p->ctx->stream, logits_dev, (const float*)dlogits_scratch_dev, n,

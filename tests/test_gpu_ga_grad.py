@@ -207,3 +207,28 @@ def test_energy_grad_full_size(ctx):
         Em, _ = gp.energy_grad(Lm, lam, "f64")
         fd = (Ep.item() - Em.item()) / h2
         assert abs(fd - g64[b, v, s].item()) <= 1e-5 * g64[b].abs().max().item() + 1e-6
+
+
+@pytest.mark.parametrize("prec", ["f64", "tf32x2"])
+def test_relaxed_descent_equals_gradient_steps(ctx, prec):
+    """goac_relaxed_descent (for TF32x2 the step is fused into the chain-rule
+    kernel) gives the logits of the same number of explicit steps
+    L <- L - eta dE/dL taken with goac_energy_grad, up to the FP32 rounding of
+    the update, and the energy decreases."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.bcc_relaxed_problem(n_side=4)
+    Jg, _ = build_pair(ctx, prob)
+    gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
+    lam, eta, n = 0.5, 0.002, 5
+    L0 = torch.tensor(synth.random_logits(prob, 3, 17), device="cuda")
+    E_start, _ = gp.energy_grad(L0, lam, prec)
+    L1 = L0.clone()
+    E1 = gp.relaxed_descent(L1, lam, eta, n, prec)
+    L2 = L0.clone()
+    for _ in range(n):
+        _, dL = gp.energy_grad(L2, lam, prec)
+        L2 = L2 - eta * dL
+    E2, _ = gp.energy_grad(L2, lam, prec)
+    assert torch.allclose(L1, L2, rtol=1e-5, atol=1e-5)
+    assert torch.allclose(E1, E2, rtol=1e-7, atol=0)
+    assert torch.all(E1 < E_start)
