@@ -259,11 +259,16 @@ __device__ __forceinline__ float to_tf32_rna(float x)
 
 // Phi^T = Q^T J (FP32 out) with real Q, TF32 split of both operands:
 // Phi = J_hi Q_hi + J_hi Q_lo + J_lo Q_hi (the lo*lo product is dropped).
-// One CTA per 128 (sites) x 128 (configurations) tile, 128 threads: warp 0
-// lane 0 TMA producer, warp 1 lane 0 MMA issuer (kind::tf32, M = N = 128,
-// K = 8), warp 2 TMEM owner, then 4 warps write their 32 TMEM lanes (sites)
-// to Phi[b][v] (coalesced over sites).  Used by the relaxed-occupation
-// gradient, where q = p . z is not integer.
+// Used by the relaxed-occupation gradient, where q = p . z is not integer.
+// Persistent grid (one CTA per SM, 192 threads): warp 0 lane 0 TMA producer,
+// warp 1 lane 0 MMA issuer (kind::tf32, M = 128 sites, N = 128
+// configurations, K = 8), warps 2-5 epilogue (warp 2 owns TMEM).  Tiles of
+// 128 sites x 128 configurations over the whole k-range, dealt round robin
+// with the configuration block fastest (CTAs running together share J's rows
+// in L2); each stage holds J hi / lo and Q hi / lo (128 x 32 FP32 each).  Two
+// FP32 accumulators in TMEM (2 x 128 columns) let the epilogue of one tile,
+// which writes its 32 TMEM lanes (sites) to Phi[b][v] coalesced over sites,
+// overlap the MMAs of the next.
 constexpr int PT_N = 128;
 constexpr int PT_A = TC_M * ROW_BYTES;        // 16 KB
 constexpr int PT_B = PT_N * ROW_BYTES;        // 16 KB
@@ -271,30 +276,37 @@ constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 64 KB
 constexpr int PT_STAGES = 3;
 constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
 
-__global__ void __launch_bounds__(128, 1)
-    k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nkb, int ld,
-             int Bpad, float* __restrict__ Phi, int* __restrict__ err)
+__global__ void __launch_bounds__(192, 1)
+    k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ntiles, int nbn,
+             int nkb, int ld, int Bpad, float* __restrict__ Phi, int* __restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + PT_STAGES * PT_STAGE);
     uint64_t* empty = full + PT_STAGES;
-    uint64_t* done = empty + PT_STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint64_t* tfull = empty + PT_STAGES;         // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;                // [2] accumulator drained
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * PT_N;
     if (threadIdx.x == 0) {
         for (int s = 0; s < PT_STAGES; ++s) {
             goacd::mbar_init(&full[s], 1);
             goacd::mbar_init(&empty[s], 1);
         }
-        goacd::mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 4);
+        }
         *abort_flag = 0;
         goacd::fence_barrier_init();
     }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmA);
+        goacd::prefetch_tmap(&tmB);
+    }
     if (warp == 2) {
-        goacd::tmem_alloc(tmem_slot, PT_N);
+        goacd::tmem_alloc(tmem_slot, 2 * PT_N);
         goacd::tmem_relinquish();
     }
     goacd::tc_fence_before();
@@ -302,81 +314,111 @@ __global__ void __launch_bounds__(128, 1)
     goacd::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     if (warp == 0) {
+        // ---------------- TMA producer ----------------
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % PT_STAGES;
-                const uint32_t use = (uint32_t)(kb / PT_STAGES);
-                if (kb >= PT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
-                    *abort_flag = 1;
-                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, kb);
-                    break;
+            int it = 0;
+            for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x) {
+                const int m0 = (id / nbn) * TC_M, n0 = (id % nbn) * PT_N;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % PT_STAGES;
+                    const uint32_t use = (uint32_t)(it / PT_STAGES);
+                    if (it >= PT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * PT_STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 32, m0);
+                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * 32, ld + m0);
+                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * 32, n0);
+                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * 32, Bpad + n0);
                 }
-                if (*abort_flag) break;
-                uint8_t* st = smem + s * PT_STAGE;
-                goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
-                goacd::tma_load_2d(st, &tmA, &full[s], kb * 32, m0);
-                goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * 32, ld + m0);
-                goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * 32, n0);
-                goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * 32, Bpad + n0);
-                issued = kb + 1;
             }
             if (*abort_flag)
-                for (int kb = issued - PT_STAGES < 0 ? 0 : issued - PT_STAGES; kb < issued; ++kb)
-                    if (!goacd::mbar_wait_bounded(&full[kb % PT_STAGES], (uint32_t)(kb / PT_STAGES) & 1, WAIT_LIMIT))
-                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, kb);
+                for (int k = it - PT_STAGES < 0 ? 0 : it - PT_STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % PT_STAGES], (uint32_t)(k / PT_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
         }
         __syncwarp();
     } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = goacd::idesc_f32acc(2u, TC_M, PT_N);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % PT_STAGES;
-                const uint32_t use = (uint32_t)(kb / PT_STAGES);
-                if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+            int it = 0, tl = 0;
+            for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
                     *abort_flag = 1;
-                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, kb);
-                    break;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
                 }
-                if (*abort_flag) break;
                 goacd::tc_fence_after();
-                const uint32_t a_hi = goacd::smem_u32(smem + s * PT_STAGE);
-                const uint32_t a_lo = a_hi + PT_A;
-                const uint32_t b_hi = a_hi + 2 * PT_A;
-                const uint32_t b_lo = b_hi + PT_B;
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * PT_N);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % PT_STAGES;
+                    const uint32_t use = (uint32_t)(it / PT_STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t a_hi = goacd::smem_u32(smem + s * PT_STAGE);
+                    const uint32_t a_lo = a_hi + PT_A;
+                    const uint32_t b_hi = a_hi + 2 * PT_A;
+                    const uint32_t b_lo = b_hi + PT_B;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t off = kk * 32;
-                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_hi + off), idesc,
-                                    (kb | kk) != 0);
-                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_lo + off), idesc, 1u);
-                    goacd::mma_tf32(tmem, goacd::sdesc_k128(a_lo + off), goacd::sdesc_k128(b_hi + off), idesc, 1u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t off = kk * 32;
+                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_hi + off), idesc,
+                                        (kb | kk) != 0);
+                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_lo + off), idesc,
+                                        1u);
+                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_lo + off), goacd::sdesc_k128(b_hi + off), idesc,
+                                        1u);
+                    }
+                    goacd::mma_commit(&empty[s]);
                 }
-                goacd::mma_commit(&empty[s]);
+                goacd::mma_commit(&tfull[acc_i]);
             }
-            goacd::mma_commit(done);
         }
         __syncwarp();
-    }
-    const bool ok = __syncthreads_and(goacd::mbar_wait_bounded(done, 0, WAIT_LIMIT) && !*abort_flag);
-    if (!ok && threadIdx.x == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, 0);
-    goacd::tc_fence_after();
-    if (ok) {
-        const int v = m0 + warp * 32 + lane;
+    } else {
+        // ---------------- epilogue: warps 2..5 ----------------
+        const int lg = warp & 3;                   // TMEM lane group this warp may access
+        int tl = 0;
+        for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
+            const int m0 = (id / nbn) * TC_M, n0 = (id % nbn) * PT_N;
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            const int v = m0 + lg * 32 + lane;
 #pragma unroll 1
-        for (int c = 0; c < PT_N / 32; ++c) {
-            uint32_t r[32];
-            goacd::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-            goacd::tmem_ld_wait();
+            for (int c = 0; c < PT_N / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * PT_N) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                if (ok)
 #pragma unroll
-            for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]);
+            }
+            goacd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
         }
     }
     goacd::tc_fence_before();
     __syncthreads();
     if (warp == 2) {
         goacd::tc_fence_after();
-        goacd::tmem_dealloc(tmem, PT_N);
+        goacd::tmem_dealloc(tmem, 2 * PT_N);
     }
 }
 
@@ -1105,9 +1147,12 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
         GOAC_CUDA(cudaFuncSetAttribute(k_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM));
         attr = true;
     }
-    dim3 grid(Bpad / PT_N, ld / TC_M);
+    if (Bpad % PT_N != 0) return fail(GOAC_ERR_INTERNAL, "phi_tc: padded batch must be a multiple of 128");
+    const int nbn = Bpad / PT_N;
+    const int ntiles = (ld / TC_M) * nbn;
+    const int grid = std::min(ntiles, p->ctx->num_sms);
     KTimer kt(p->ctx, KID_SCORE_TC, st);
-    goac::launch(k_phi_tc, grid, 128, PT_SMEM, st, ma, mb, ld / 32, ld, Bpad, Phi, p->ctx->d_err);
+    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, ntiles, nbn, ld / 32, ld, Bpad, Phi, p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_phi_tc");
     return GOAC_OK;
 }
