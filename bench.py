@@ -47,7 +47,7 @@ WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", default=FORM, choices=sorted(TERMS))
