@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -995,6 +996,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
+// Opt a kernel into its large dynamic shared memory on the given (current)
+// device, once per device: the attribute belongs to the device, so a process
+// with contexts on several GPUs must set it on each.
+goac_status smem_attr_once(const void* kern, int smem, std::atomic<uint64_t>& done, int device)
+{
+    const uint64_t bit = 1ull << (device & 63);
+    if (done.load() & bit) return GOAC_OK;
+    GOAC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    done.fetch_or(bit);
+    return GOAC_OK;
+}
+
 // 2D K-major tensor map: inner dim = `inner` elements (row pitch `pitch_elems`),
 // outer dim = `rows`; box = 128 bytes x box_rows, 128-byte swizzle.
 goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int elem_bytes, long inner, long rows,
@@ -1068,10 +1081,10 @@ goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap&
 {
     using Cfg = TcCfg<T>;
     auto kern = k_score_tc<T, TF32>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        GOAC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
-        attr_set = true;
+    static std::atomic<uint64_t> attr_done{0};
+    {
+        goac_status rc0 = smem_attr_once((const void*)kern, Cfg::SMEM, attr_done, p->ctx->device);
+        if (rc0) return rc0;
     }
     const int ld = p->Nv_pad;
     const int nkb = TF32 ? ld / 32 : ld / 64;
@@ -1142,11 +1155,9 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     goac_status rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M);
     if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N);
     if (rc) return rc;
-    static bool attr = false;
-    if (!attr) {
-        GOAC_CUDA(cudaFuncSetAttribute(k_phi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr_done{0};
+    rc = smem_attr_once((const void*)k_phi_tc, PT_SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
     if (Bpad % PT_N != 0) return fail(GOAC_ERR_INTERNAL, "phi_tc: padded batch must be a multiple of 128");
     const int nbn = Bpad / PT_N;
     const int ntiles = (ld / TC_M) * nbn;
@@ -1234,11 +1245,9 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
     rc = make_map(&ma, p->J_dig_full, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
     if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
     if (rc) return rc;
-    static bool attr = false;
-    if (!attr) {
-        GOAC_CUDA(cudaFuncSetAttribute(k_phi_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, EX_SMEM));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr_done{0};
+    rc = smem_attr_once((const void*)k_phi_exact, EX_SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
     const int ntiles = nbm * nbn * EX_T;
     const int grid = std::min(ntiles, p->ctx->num_sms);
     {
@@ -1275,11 +1284,9 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
     if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
     if (rc) return rc;
-    static bool attr = false;
-    if (!attr) {
-        GOAC_CUDA(cudaFuncSetAttribute(k_score_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, EX_SMEM));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr_done{0};
+    rc = smem_attr_once((const void*)k_score_exact, EX_SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
     const int grid = std::min(nbm * nbn * EX_T, p->ctx->num_sms);
     const int2* work = nullptr;
     const int* starts = nullptr;
