@@ -13,6 +13,11 @@
  *    a problem, freed by the matching destroy call).
  *  - Every call returns a goac_status; on failure goac_last_error() gives a
  *    message (thread-local).  No C++ exception crosses the ABI.
+ *  - Empty batches: a call whose number of configurations, chains or
+ *    individuals (B, C, P, G) is 0 does nothing and returns GOAC_OK; its
+ *    per-configuration buffers may then be NULL (the problem or context
+ *    handle is still required, and the other arguments are still checked).
+ *    A negative count, or one above GOAC_MAX_BATCH, is GOAC_ERR_INVALID_ARG.
  *  - Bounded waits: no kernel of this library waits without an iteration
  *    limit; a wait that runs out sets a device error word that the next
  *    synchronising call reports as GOAC_ERR_TIMEOUT.
@@ -45,6 +50,11 @@ typedef int32_t goac_status;
 #define GOAC_ERR_TIMEOUT (-5)       /* a bounded device wait ran out            */
 #define GOAC_ERR_INTERNAL (-6)      /* device-side consistency check failed     */
 #define GOAC_ERR_UNSUPPORTED (-7)   /* device is not sm_103 / feature missing   */
+
+/* Largest number of configurations, chains or individuals in one call:     *
+ * 2^31 - 256, so that a batch padded to whole 256-configuration tiles still *
+ * has an int32 count.                                                       */
+#define GOAC_MAX_BATCH 2147483392
 
 /* Arithmetic forms of the batched scoring E = q^T J q. */
 #define GOAC_PREC_F64 0     /* FP64 CUDA-core GEMM: the plain path              */
@@ -217,6 +227,7 @@ goac_status goac_random_configs(goac_problem* prob, int32_t B, uint64_t seed, in
  *   doubles out; best_species_dev: C x Nv out (nullable); n_accept_dev: C    *
  *   int64 out (nullable).  precision: GOAC_PREC_F64 (trajectory-exact to    *
  *   the FP64 definition) or GOAC_PREC_F32 (phi and J rows in FP32).         *
+ *   GOAC_ERR_INVALID_ARG when no class has two positions (no swap exists).   *
  * ------------------------------------------------------------------------ */
 goac_status goac_mc_run(goac_problem* prob, int8_t* species_dev, int32_t C, const double* kT_dev, int64_t n_steps,
                         uint64_t seed, uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,

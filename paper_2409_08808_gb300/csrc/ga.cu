@@ -377,8 +377,10 @@ extern "C" goac_status goac_ga_generation(goac_problem* p, const int8_t* pop_dev
                                           int32_t n_elite, uint32_t p_mut_u32, uint32_t gen, uint64_t seed,
                                           int8_t* children_dev, int32_t* parents_dev, int32_t* nswap_dev)
 {
-    if (!p || !pop_dev || !E_dev || !children_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL");
-    if (P <= 0 || n_elite < 0 || n_elite > P) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: bad sizes");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL problem");
+    if (P < 0 || P > GOAC_MAX_BATCH || n_elite < 0 || n_elite > P) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: bad sizes");
+    if (P == 0) return GOAC_OK;
+    if (!pop_dev || !E_dev || !children_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     return goac::ga_generation_impl(p, pop_dev, E_dev, P, n_elite, p_mut_u32, gen, seed, children_dev, parents_dev,
                                     nswap_dev);
@@ -388,9 +390,11 @@ extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_d
                                    int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0,
                                    int32_t precision)
 {
-    if (!p || !pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
-    if (P <= 0 || n_gen < 0 || n_elite < 0 || n_elite > P)
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL problem");
+    if (P < 0 || P > GOAC_MAX_BATCH || n_gen < 0 || n_elite < 0 || n_elite > P)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes");
+    if (P == 0) return GOAC_OK;
+    if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     goac_status rc = goac::ensure(p->phi, (size_t)P * p->Nv);
     if (rc) return rc;

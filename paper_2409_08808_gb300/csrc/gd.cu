@@ -183,9 +183,9 @@ __global__ void k_gd_init(int B, int* active, long long* steps)
 extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t B, int32_t max_steps,
                                    double* E_dev, int64_t* steps_dev)
 {
-    if (!p || !species_dev || !E_dev || !steps_dev || B < 0 || max_steps < 0)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_gd_run: bad argument");
+    if (!p || B < 0 || B > GOAC_MAX_BATCH || max_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_gd_run: bad argument");
     if (B == 0) return GOAC_OK;
+    if (!species_dev || !E_dev || !steps_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_gd_run: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;

@@ -456,8 +456,10 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
                                     int32_t precision, double* E_dev, float* dlogits_dev, float* logits_upd,
                                     float eta)
 {
-    if (!p || !logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
-    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL problem");
+    if (B <= 0 || B > GOAC_MAX_BATCH)
+        return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0 or B > GOAC_MAX_BATCH");
+    if (!logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
     if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_TF32X2)
         return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: precision must be F64 or TF32X2");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
@@ -510,8 +512,10 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
 
 extern "C" goac_status goac_round_to_counts(goac_problem* p, const float* p_dev, int32_t B, int8_t* species_dev)
 {
-    if (!p || !p_dev || !species_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: NULL");
-    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: B < 0");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: NULL problem");
+    if (B <= 0 || B > GOAC_MAX_BATCH)
+        return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: B < 0 or B > GOAC_MAX_BATCH");
+    if (!p_dev || !species_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: NULL");
     if (p->Nv >= (1 << 24)) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_round_to_counts: Nv too large");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const int ncls = p->ncls, S = p->S;
@@ -553,8 +557,10 @@ extern "C" goac_status goac_relaxed_descent(goac_problem* p, float* logits_dev, 
                                             int32_t n_steps, int32_t precision, float* dlogits_scratch_dev,
                                             double* E_dev)
 {
-    if (!p || !logits_dev || !dlogits_scratch_dev || !E_dev || n_steps < 0)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_relaxed_descent: bad argument");
+    if (!p || B < 0 || B > GOAC_MAX_BATCH || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_relaxed_descent: bad argument");
+    if (B == 0) return GOAC_OK;
+    if (!logits_dev || !dlogits_scratch_dev || !E_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_relaxed_descent: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const long n = (long)B * p->Nv * p->S;
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
@@ -576,8 +582,9 @@ extern "C" goac_status goac_relaxed_descent(goac_problem* p, float* logits_dev, 
 
 extern "C" goac_status goac_occupations(goac_problem* p, const float* logits_dev, int32_t B, float* p_dev)
 {
-    if (!p || !logits_dev || !p_dev || B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_occupations: bad argument");
+    if (!p || B < 0 || B > GOAC_MAX_BATCH) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_occupations: bad argument");
     if (B == 0) return GOAC_OK;
+    if (!logits_dev || !p_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_occupations: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const long BN = (long)B * p->Nv;
     goac::launch(k_softmax_f32, (int)((BN + 255) / 256), 256, 0, p->ctx->stream, logits_dev, BN, p->Nv, p->S,

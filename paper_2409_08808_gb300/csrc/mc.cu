@@ -366,13 +366,14 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
                                int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
                                int64_t* n_accept_dev)
 {
-    if (!p || !species_dev || !kT_dev || !E_dev || !bestE_dev)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL argument");
-    if (C < 0 || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: negative size");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL problem");
+    if (C < 0 || C > GOAC_MAX_BATCH || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: bad size");
     if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_F32)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: precision must be F64 or F32");
     if (p->nmovable == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: no class has two positions");
     if (C == 0) return GOAC_OK;
+    if (!species_dev || !kT_dev || !E_dev || !bestE_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const bool f32 = precision == GOAC_PREC_F32;
     if (f32) {
@@ -441,7 +442,8 @@ extern "C" goac_status goac_sa_run(goac_problem* p, int8_t* species_dev, int32_t
                                    uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
                                    int8_t* best_species_dev, int64_t* n_accept_dev)
 {
-    if (!kT1_dev || total_steps < 1) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_sa_run: kT1 and total_steps needed");
+    if (total_steps < 1) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_sa_run: total_steps must be >= 1");
+    if (C != 0 && !kT1_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_sa_run: kT1 needed");
     return mc_run_impl(p, species_dev, C, kT0_dev, kT1_dev, total_steps, n_steps, seed, step0, precision, E_dev,
                        bestE_dev, best_species_dev, n_accept_dev);
 }
@@ -491,9 +493,14 @@ extern "C" goac_status goac_remc_run(goac_problem* p, int8_t* species_dev, int32
                                      uint64_t seed, int32_t precision, double* E_dev, int32_t* perm_dev,
                                      int64_t* n_exchanges_host)
 {
-    if (!p || !species_dev || !kT_ladder_host || !E_dev || !perm_dev || G <= 0 || R <= 0 || n_rounds < 0 ||
-        steps_per_round < 0)
+    if (!p || G < 0 || R <= 0 || n_rounds < 0 || steps_per_round < 0 || (int64_t)G * R > GOAC_MAX_BATCH)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_remc_run: bad argument");
+    if (G == 0) {
+        if (n_exchanges_host) *n_exchanges_host = 0;
+        return GOAC_OK;
+    }
+    if (!species_dev || !kT_ladder_host || !E_dev || !perm_dev)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_remc_run: NULL argument");
     for (int k = 0; k < R; ++k)
         if (!(kT_ladder_host[k] > 0.0)) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_remc_run: temperatures must be > 0");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
@@ -549,8 +556,10 @@ extern "C" goac_status goac_batch_mc_run(goac_ctx* ctx, goac_problem* const* pro
     auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
     for (int i = 0; i < n_probs; ++i) {
         goac_problem* p = probs[i];
-        if (!p || !species_dev[i] || !kT_dev[i] || !E_dev[i] || !bestE_dev[i] || chains[i] < 0)
+        if (!p || chains[i] < 0 || (chains[i] > 0 && (!species_dev[i] || !kT_dev[i] || !E_dev[i] || !bestE_dev[i])))
             return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: bad per-problem argument");
+        if ((int64_t)items.size() + chains[i] > GOAC_MAX_BATCH)
+            return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: more than GOAC_MAX_BATCH chains in all");
         if (p->ctx != ctx) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: problem from another context");
         if (p->nmovable == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_mc_run: problem without moves");
         if (f32) {
@@ -728,8 +737,9 @@ extern "C" goac_status goac_batch_mc_autotune(goac_ctx* ctx, goac_problem* const
     for (int cpc : cands) {
         if (slot * cpc > kSmemBudget) break;
         for (int i = 0; i < n_probs; ++i)
-            GOAC_CUDA(cudaMemcpyAsync(sp[i], species_dev[i], (size_t)chains[i] * probs[i]->Nv,
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
+            if (chains[i] > 0)
+                GOAC_CUDA(cudaMemcpyAsync(sp[i], species_dev[i], (size_t)chains[i] * probs[i]->Nv,
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
         rc = goac_batch_mc_run(ctx, probs, n_probs, sp.data(), chains, kT_dev, probe_steps, 12345u, 0, precision,
                                E.data(), bE.data(), cpc, 1);
         if (rc) break;
@@ -767,8 +777,10 @@ extern "C" goac_status goac_hybrid_run(goac_problem* p, int8_t* species_dev, int
                                        int64_t steps_per_round, int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32,
                                        uint64_t seed, int32_t precision, double* E_dev)
 {
-    if (!p || !species_dev || !kT_ladder_host || !E_dev || G <= 0 || R <= 0 || n_cycles < 0 || n_gen < 0)
+    if (!p || G < 0 || R <= 0 || n_cycles < 0 || n_gen < 0 || (int64_t)G * R > GOAC_MAX_BATCH)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_hybrid_run: bad argument");
+    if (G == 0) return GOAC_OK;
+    if (!species_dev || !kT_ladder_host || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_hybrid_run: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const int P = G * R;
     DevBuf perm;

@@ -760,9 +760,10 @@ extern "C" goac_status goac_problem_phi_fix(const goac_problem* p, double* phi_f
 extern "C" goac_status goac_score(goac_problem* p, const int8_t* species_dev, int32_t B, int32_t precision,
                                   double* E_dev)
 {
-    if (!p || !species_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: NULL argument");
-    if (B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: B < 0");
-    if (B == 0) return GOAC_OK;
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: NULL problem");
+    if (B <= 0 || B > GOAC_MAX_BATCH)
+        return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: B < 0 or B > GOAC_MAX_BATCH");
+    if (!species_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score: NULL argument");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     switch (precision) {
         case GOAC_PREC_F64: return goac::score_f64(p, species_dev, B, E_dev, nullptr);
@@ -779,8 +780,10 @@ extern "C" goac_status goac_score(goac_problem* p, const int8_t* species_dev, in
 extern "C" goac_status goac_score_host(goac_problem* p, const int8_t* species_host, int32_t B, int32_t precision,
                                        double* E_host)
 {
-    if (!p || !species_host || !E_host) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host: NULL argument");
-    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host: B < 0");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host: NULL problem");
+    if (B <= 0 || B > GOAC_MAX_BATCH)
+        return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host: B < 0 or B > GOAC_MAX_BATCH");
+    if (!species_host || !E_host) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host: NULL argument");
     goac_ctx* ctx = p->ctx;
     GOAC_CUDA(cudaSetDevice(ctx->device));
     size_t sb = (size_t)B * p->Nv, eb = sizeof(double) * (size_t)B;
@@ -798,8 +801,10 @@ extern "C" goac_status goac_score_host(goac_problem* p, const int8_t* species_ho
 extern "C" goac_status goac_score_host_async(goac_problem* p, const int8_t* species_host, int32_t B,
                                              int32_t precision, double* E_host)
 {
-    if (!p || !species_host || !E_host) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: NULL argument");
-    if (B <= 0) return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: B < 0");
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: NULL problem");
+    if (B <= 0 || B > GOAC_MAX_BATCH)
+        return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: B < 0 or B > GOAC_MAX_BATCH");
+    if (!species_host || !E_host) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_host_async: NULL argument");
     goac_ctx* ctx = p->ctx;
     GOAC_CUDA(cudaSetDevice(ctx->device));
     if (!ctx->copy_stream) {
@@ -836,7 +841,7 @@ extern "C" goac_status goac_topk_rescore(goac_problem* p, const int8_t* species_
 {
     if (!p || !species_dev || !E_approx_dev || !idx_dev || !E_dev)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_topk_rescore: NULL argument");
-    if (k < 1 || k > 1024 || k > B) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_topk_rescore: need 1 <= k <= min(B, 1024)");
+    if (k < 1 || k > 1024 || k > B || B > GOAC_MAX_BATCH) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_topk_rescore: need 1 <= k <= min(B, 1024)");
     goac_ctx* ctx = p->ctx;
     GOAC_CUDA(cudaSetDevice(ctx->device));
     const int nb = (p->Nv + RS - 1) / RS;
@@ -865,8 +870,9 @@ extern "C" goac_status goac_topk_rescore(goac_problem* p, const int8_t* species_
 
 extern "C" goac_status goac_random_configs(goac_problem* p, int32_t B, uint64_t seed, int8_t* species_dev)
 {
-    if (!p || !species_dev || B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_random_configs: bad argument");
+    if (!p || B < 0 || B > GOAC_MAX_BATCH) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_random_configs: bad argument");
     if (B == 0) return GOAC_OK;
+    if (!species_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_random_configs: NULL output");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     long t = (long)B * p->ncls;
     goac::launch(k_random_configs, (int)((t + 127) / 128), 128, 0, p->ctx->stream, B, p->ncls, p->S, p->cls_start_dev,
@@ -905,13 +911,15 @@ extern "C" goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld,
                                               const double* phi_fix_dev, double E_const, void* stream,
                                               double* E_dev)
 {
-    if (!Jvv_dev || !species_dev || !z_dev || !phi_fix_dev || !E_dev)
+    if (!Jvv_dev || !z_dev || !phi_fix_dev)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: NULL argument");
-    if (Nv <= 0 || B < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: need Nv > 0, B >= 0");
+    if (Nv <= 0 || B < 0 || B > GOAC_MAX_BATCH)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: need Nv > 0, 0 <= B <= GOAC_MAX_BATCH");
     const long mt = (Nv + PB_M - 1) / PB_M;
     if (ld < mt * PB_M)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: ld must be >= Nv rounded up to 64");
     if (B == 0) return GOAC_OK;
+    if (!species_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: NULL argument");
     if (mt * (long)B > kStaticPartialEntries)
         return goac::fail(GOAC_ERR_INVALID_ARG,
                           "goac_score_f64_noalloc: ceil(Nv/64) * B = " + std::to_string(mt * (long)B) +

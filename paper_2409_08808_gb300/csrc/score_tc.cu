@@ -30,7 +30,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <mutex>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -1033,20 +1036,26 @@ goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int e
 goac_status tc_schedule_into(DevBuf& sched, uint64_t& sched_key, int& sched_tiles, int nbm, int nbn, int grid,
                              const int2** work, const int** starts)
 {
-    const uint64_t key = ((uint64_t)nbm << 40) | ((uint64_t)nbn << 20) | (uint64_t)grid;
+    // key fields: nbm < 2^18 (Nv < 2^25), nbn < 2^26 (B < 2^31 times the 6 digits of the exact form), grid < 2^20
+    if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || grid <= 0 || grid >= (1 << 20))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "tile schedule: shape out of range");
+    const uint64_t key = ((uint64_t)nbm << 46) | ((uint64_t)nbn << 20) | (uint64_t)grid;
     if (sched_key != key) {
         std::vector<int2> tiles;
         for (int I = 0; I < nbm; ++I)
             for (int n = 0; n < nbn; ++n) tiles.push_back(make_int2(I, n));
         std::stable_sort(tiles.begin(), tiles.end(), [](const int2& a, const int2& b) { return a.x < b.x; });
+        // each tile goes to the least-loaded CTA (ties: the lowest index), a min-heap on (load, CTA)
         std::vector<std::vector<int2>> per(grid);
-        std::vector<long> load(grid, 0);
+        std::priority_queue<std::pair<long, int>, std::vector<std::pair<long, int>>,
+                            std::greater<std::pair<long, int>>>
+            heap;
+        for (int c = 0; c < grid; ++c) heap.push({0L, c});
         for (const int2& t : tiles) {
-            int best = 0;
-            for (int c = 1; c < grid; ++c)
-                if (load[c] < load[best]) best = c;
+            const auto [ld0, best] = heap.top();
+            heap.pop();
             per[best].push_back(t);
-            load[best] += (nbm - t.x) + 1;   // k-blocks of 128 columns, +1 for the epilogue
+            heap.push({ld0 + (nbm - t.x) + 1, best});   // k-blocks of 128 columns, +1 for the epilogue
         }
         std::vector<int2> flat;
         std::vector<int> st(grid + 1, 0);

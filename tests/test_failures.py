@@ -32,6 +32,24 @@ def test_null_arguments_are_rejected_on_the_host():
     assert b"NULL" in L.goac_last_error()
 
 
+def test_empty_and_oversized_batches_on_the_host():
+    """B = 0 returns GOAC_OK before any buffer is touched (its per-configuration
+    pointers may be NULL); B < 0 or B > GOAC_MAX_BATCH = 2^31 - 256 is rejected.
+    The allocation-free entry point needs no context, so this runs without a
+    GPU: the non-NULL addresses below are never dereferenced."""
+    import pathlib
+    import re
+    from paper_2409_08808_gb300 import _lib
+    L = _lib.lib
+    hdr = (pathlib.Path(__file__).resolve().parents[1] / "include" / "goac.h").read_text()
+    assert int(re.search(r"#define GOAC_MAX_BATCH (\d+)", hdr).group(1)) == 2 ** 31 - 256
+    fake = C.c_void_p(256)
+    assert L.goac_score_f64_noalloc(fake, 64, 10, None, 0, fake, fake, 0.0, None, None) == 0
+    for B in (-1, 2 ** 31 - 255):
+        assert L.goac_score_f64_noalloc(fake, 64, 10, fake, B, fake, fake, 0.0, None, fake) == -1
+    assert L.goac_score(None, None, 0, 0, None) == -1          # the problem handle is still required
+
+
 @pytest.mark.gpu
 def test_device_wait_runs_out_and_context_survives():
     import paper_2409_08808_gb300 as g
