@@ -563,23 +563,48 @@ def run_suite(args):
         gp, J, jms = problem(prob)
         pop0 = gp.random_configs(1024, 3)
         res = {}
-        for prec in ("f64", "f32", "bf16x3"):
+        for prec in ("f64", "f64_incr", "exact", "f32", "bf16x3"):
             pop = pop0.clone()
             gp.ga_run(pop.clone(), 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
             box = {}
             ctx.set_timing(True)
             ctx.kernel_time("ga")
+            ctx.kernel_time("ga_incr")
             ms = timed(lambda: box.setdefault("E", gp.ga_run(pop, 200, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)))
             gk_ms, gk_n = ctx.kernel_time("ga")
+            ik_ms, ik_n = ctx.kernel_time("ga_incr")
             ctx.set_timing(False)
             E = box["E"]
             # children kernel: reads both parents, writes the child (int8 species)
             ga_bytes = 3.0 * 1024 * prob.Nv
             gk_avg = gk_ms / max(gk_n, 1)
+            E64 = gp.score(pop, "f64")
             res[prec] = {"ms": ms, "generations_per_s": 200 / (ms / 1e3), "child_evals_per_s": 1024 * 200 / (ms / 1e3),
-                         "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(gp.score(pop, "f64").min()),
+                         "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(E64.min()),
+                         "max_rel_dev_from_fp64_rescoring": float(((E - E64).abs() / E64.abs()).max()),
                          "children_kernel_ms": gk_avg,
                          "children_kernel_hbm_gbs_algorithmic": ga_bytes / (gk_avg / 1e3) / 1e9}
+            if ik_n:
+                res[prec]["incremental_kernel_ms"] = ik_ms / ik_n
+        # the incremental rescoring kernel on one generation bred from the random population:
+        # M_c changed sites per child -> M_c Nv FP64 FMAs and M_c J rows (Nv doubles each)
+        kids, par, _ = gp.ga_generation(pop0, gp.score(pop0, "f64"), 20, oracle.p_mut_to_u32(0.1), 0, 9, record=True)
+        pa, pb = par[:, 0].long(), par[:, 1].long()
+        M = torch.minimum((kids != pop0[pa]).sum(1), (kids != pop0[pb]).sum(1)).double().sum().item()
+        ctx.set_timing(True)
+        ctx.kernel_time("ga_incr")
+        for _ in range(20):
+            gp.ga_run(pop0.clone(), 1, 20, oracle.p_mut_to_u32(0.1), 9, 0, "f64_incr")
+        ik_ms, ik_n = ctx.kernel_time("ga_incr")
+        ctx.set_timing(False)
+        ik = ik_ms / max(ik_n, 1) / 1e3
+        incr_bytes = 8.0 * M * prob.Nv + 2 * 8.0 * 1024 * prob.Nv + 3.0 * 1024 * prob.Nv
+        res["f64_incr_one_generation"] = {
+            "changed_sites_per_child": M / 1024, "kernel_ms": ik * 1e3,
+            "fp64_tflops": 2.0 * M * prob.Nv / ik / 1e12,
+            "algorithmic_gbs": incr_bytes / ik / 1e9,
+            "note": "J rows of the changed sites + parent and child potentials + species; the rows mostly come "
+                    "from L2 (J_vv is 6 MB)"}
         work = None
         Jr = np.random.default_rng(1).standard_normal((prob.N, prob.N))
         Jr = 0.5 * (Jr + Jr.T)

@@ -64,6 +64,7 @@ typedef int32_t goac_status;
 #define GOAC_PREC_BF16X3 4  /* tcgen05 kind::f16 (BF16), J = J1 + J2 + J3        */
 #define GOAC_PREC_F32 5     /* FP32 CUDA cores (Monte Carlo / GA variant only)   */
 #define GOAC_PREC_EXACT 6   /* tcgen05 integer-digit split (FP64-grade, see below) */
+#define GOAC_PREC_F64_INCR 7 /* GA runs only: incremental FP64 rescoring (goac_ga_run) */
 
 typedef struct goac_ctx goac_ctx;
 typedef struct goac_problem goac_problem;
@@ -85,7 +86,8 @@ goac_status goac_ctx_synchronize(goac_ctx* ctx);
 /* Per-kernel timing: when enabled, a CUDA event pair is recorded on the      *
  * context stream around every launch of the timed kernel families:           *
  * 0 = tensor-core scoring, 1 = CUDA-core scoring GEMM, 2 = Monte Carlo,      *
- * 3 = GA children, 4 = Ewald real space, 5 = Ewald reciprocal SYRK.          */
+ * 3 = GA children, 4 = Ewald real space, 5 = Ewald reciprocal SYRK,          *
+ * 6 = incremental GA rescoring.                                               */
 goac_status goac_ctx_set_timing(goac_ctx* ctx, int32_t enable);
 /* Total recorded milliseconds and launch count of kernel family `kernel`     *
  * since the last query (waits for the recorded events; clears the record).  */
@@ -330,7 +332,17 @@ goac_status goac_ga_generation(goac_problem* prob, const int8_t* pop_dev, const 
 /* GA run: scores pop_dev, then n_gen x (generation + rescoring of every     *
  * child with `precision`; with a tensor-core precision the FP64 energy is    *
  * used only through the split form).  pop_dev (P x Nv) and E_dev (P) are    *
- * in/out.  Generations are numbered gen0, gen0 + 1, ...                     */
+ * in/out.  Generations are numbered gen0, gen0 + 1, ...                     *
+ * GOAC_PREC_F64_INCR rescores incrementally in FP64 (the paper's GA keeps   *
+ * the energies of its structures; the rescoring of a child from its parent *
+ * is this library's reading): the potentials phi = J_vv q + phi_fix of the  *
+ * population are formed once, and each child c takes the parent P (of its   *
+ * two; ties: the first) from which it differs in fewer sites, then          *
+ *   phi_c = phi_P + sum_{s: c_s != P_s} (z[c_s] - z[P_s]) J_vv[s][:]        *
+ * over the changed sites in ascending order and                             *
+ *   E_c = sum_v q_c,v (phi_c,v + phi_fix,v) + E_const,                      *
+ * equal to the full q^T J q to FP64 rounding.  Needs Nv <= 17066, else      *
+ * GOAC_ERR_UNSUPPORTED.                                                     */
 goac_status goac_ga_run(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
                         int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0, int32_t precision);
 

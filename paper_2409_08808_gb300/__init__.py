@@ -22,7 +22,7 @@ from ._lib import lib, LIB_PATH, SIGNATURES  # noqa: F401  (raises if the librar
 #: Coulomb constant e^2 / (4 pi eps0) in eV * Angstrom (CODATA 2018).
 KE = 14.3996454784
 
-PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5, "exact": 6}
+PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5, "exact": 6, "f64_incr": 7}
 
 
 class GoacError(RuntimeError):
@@ -84,7 +84,7 @@ class Context:
         _check(lib.goac_ctx_synchronize(self.handle), "goac_ctx_synchronize")
         self._inflight.clear()
 
-    KERNELS = {"score_tc": 0, "score_cc": 1, "mc": 2, "ga": 3, "ewald_real": 4, "ewald_syrk": 5}
+    KERNELS = {"score_tc": 0, "score_cc": 1, "mc": 2, "ga": 3, "ewald_real": 4, "ewald_syrk": 5, "ga_incr": 6}
 
     def set_timing(self, enable: bool):
         _check(lib.goac_ctx_set_timing(self._h, int(bool(enable))), "goac_ctx_set_timing")

@@ -114,6 +114,7 @@ struct goac_problem {
     float* diag_f32 = nullptr;
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
+    DevBuf ga_incr;            // incremental GA rescoring: 2 x P x Nv potentials, P x 2 parents
     // persistent tensor-core schedules (device copies) for the last shapes
     DevBuf sched, sched_ex;
     uint64_t sched_key = 0, sched_ex_key = 0;
@@ -403,6 +404,7 @@ enum KernelId : int {
     KID_GA = 3,         // GA children
     KID_EWALD_REAL = 4, // Ewald real-space pair kernel
     KID_EWALD_SYRK = 5, // Ewald reciprocal SYRK
+    KID_GA_INCR = 6,    // incremental GA rescoring
     KID_COUNT = 8
 };
 

@@ -17,6 +17,8 @@
 //                 B_j != B_i, kept per species as a bitmask over class
 //                 positions and found by one ballot over 32 words), Philox
 //                 draws per candidate, mutation, write-back.
+#include <utility>
+
 #include "common.cuh"
 
 namespace {
@@ -309,6 +311,153 @@ __global__ void k_ga_children(GaArgs a)
     }
 }
 
+// Incremental FP64 rescoring of the children (SI, Genetic Algorithm; the
+// incremental form of the Eq. 2 objective): with phi = J_vv q + phi_fix kept
+// for every individual, a child c and the parent P (of its two) from which it
+// differs in fewer sites give
+//   phi_c = phi_P + sum_{s: c_s != P_s} (z[c_s] - z[P_s]) J_vv[s][:],
+//   E_c   = sum_v q_c,v (phi_c,v + phi_fix,v) + E_const,
+// the changed sites taken in ascending order.  One block per child; the list
+// of changed sites and charge differences sits in shared memory, each thread
+// accumulates GI_R sites per pass over the list (coalesced reads of the J rows).
+constexpr int GI_THREADS = 256;
+constexpr int GI_R = 4;
+
+struct GaIncrArgs {
+    const int8_t* pop;        // P x Nv parents
+    const double* phi_pop;    // P x Nv
+    const int8_t* kids;       // P x Nv
+    const int32_t* parents;   // P x 2
+    const double* J;          // J_vv, rows of ld doubles
+    const double* z;          // 64
+    const double* phifix;     // Nv
+    double* phi_kids;         // P x Nv out
+    double* E_kids;           // P out
+    int* err;
+    double E_const;
+    int ld, Nv, P, S;
+};
+
+__global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    double* dq = (double*)smem;               // Nv
+    int* idx = (int*)(dq + g.Nv);             // Nv
+    __shared__ int wcnt[GI_THREADS / 32][2];
+    __shared__ double wsum[GI_THREADS / 32];
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = GI_THREADS / 32;
+    const int Nv = g.Nv;
+    const int A = g.parents[2 * c], B = g.parents[2 * c + 1];
+    if ((unsigned)A >= (unsigned)g.P || (unsigned)B >= (unsigned)g.P) {
+        if (tid == 0) goacd::report(g.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
+        return;
+    }
+    const int8_t* kid = g.kids + (long)c * Nv;
+    const int8_t* pa = g.pop + (long)A * Nv;
+    const int8_t* pb = g.pop + (long)B * Nv;
+    // the nearer parent (ties: A)
+    int da = 0, db = 0;
+    for (int v = tid; v < Nv; v += GI_THREADS) {
+        const int8_t k = kid[v];
+        da += k != pa[v];
+        db += k != pb[v];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        da += __shfl_xor_sync(0xffffffffu, da, o);
+        db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    if (lane == 0) {
+        wcnt[wid][0] = da;
+        wcnt[wid][1] = db;
+    }
+    __syncthreads();
+    int DA = 0, DB = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        DA += wcnt[w][0];
+        DB += wcnt[w][1];
+    }
+    const bool useB = DB < DA;
+    const int par = useB ? B : A;
+    const int8_t* pp = useB ? pb : pa;
+    __syncthreads();
+    // changed sites in ascending order and their charge differences
+    int M = 0;
+    bool bad = false;
+    for (int v0 = 0; v0 < Nv; v0 += GI_THREADS) {
+        const int v = v0 + tid;
+        bool f = false;
+        int sk = 0, sp = 0;
+        if (v < Nv) {
+            sk = kid[v];
+            sp = pp[v];
+            f = sk != sp;
+            if ((unsigned)sk >= (unsigned)g.S || (unsigned)sp >= (unsigned)g.S) {
+                bad = true;
+                f = false;
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid][0] = __popc(m);
+        __syncthreads();
+        int off = M, tot = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            off += w < wid ? wcnt[w][0] : 0;
+            tot += wcnt[w][0];
+        }
+        if (f) {
+            const int pos = off + __popc(m & ((1u << lane) - 1u));
+            idx[pos] = v;
+            dq[pos] = g.z[sk] - g.z[sp];
+        }
+        M += tot;
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) goacd::report(g.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
+        return;
+    }
+    double e = 0.0;
+    for (int v0 = 0; v0 < Nv; v0 += GI_THREADS * GI_R) {
+        double acc[GI_R];
+#pragma unroll
+        for (int r = 0; r < GI_R; ++r) {
+            const int v = v0 + r * GI_THREADS + tid;
+            acc[r] = v < Nv ? g.phi_pop[(long)par * Nv + v] : 0.0;
+        }
+        for (int t = 0; t < M; ++t) {
+            const double d = dq[t];
+            const double* row = g.J + (long)idx[t] * g.ld;
+#pragma unroll
+            for (int r = 0; r < GI_R; ++r) {
+                const int v = v0 + r * GI_THREADS + tid;
+                if (v < Nv) acc[r] = fma(d, row[v], acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < GI_R; ++r) {
+            const int v = v0 + r * GI_THREADS + tid;
+            if (v < Nv) {
+                g.phi_kids[(long)c * Nv + v] = acc[r];
+                e = fma(g.z[kid[v]], acc[r] + g.phifix[v], e);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) wsum[wid] = e;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += wsum[w];
+        g.E_kids[c] = s + g.E_const;
+    }
+}
+
 }  // namespace
 
 namespace goac {
@@ -371,6 +520,59 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     return GOAC_OK;
 }
 
+// GA run with incremental FP64 rescoring: the potentials of the population
+// are formed once by the FP64 scoring GEMM, then every generation forms each
+// child's potential and energy from its nearer parent's (k_ga_incr).
+static goac_status ga_run_incremental(goac_problem* p, int8_t* pop, double* E, int P, int n_gen, int n_elite,
+                                      uint32_t p_mut, uint64_t seed, uint32_t gen0)
+{
+    goac_ctx* ctx = p->ctx;
+    cudaStream_t st = ctx->stream;
+    const int Nv = p->Nv;
+    const size_t smem = (sizeof(double) + sizeof(int)) * (size_t)Nv;
+    if (smem > 200 * 1024) return fail(GOAC_ERR_UNSUPPORTED, "goac_ga_run: incremental rescoring needs Nv <= 17066");
+    goac_status rc = ensure(p->phi, (size_t)P * Nv);
+    if (rc) return rc;
+    const size_t phi_bytes = sizeof(double) * (size_t)P * Nv;
+    rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)P + 256);
+    if (rc) return rc;
+    int8_t* kids = (int8_t*)p->phi.ptr;
+    double* phi_a = (double*)p->ga_incr.ptr;
+    double* phi_b = (double*)((char*)p->ga_incr.ptr + phi_bytes);
+    int32_t* parents = (int32_t*)((char*)p->ga_incr.ptr + 2 * phi_bytes);
+    rc = score_f64(p, pop, P, E, phi_a);
+    if (rc) return rc;
+    GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    for (int g = 0; g < n_gen; ++g) {
+        rc = ga_generation_impl(p, pop, E, P, n_elite, p_mut, gen0 + (uint32_t)g, seed, kids, parents, nullptr);
+        if (rc) return rc;
+        GaIncrArgs a;
+        a.pop = pop;
+        a.phi_pop = phi_a;
+        a.kids = kids;
+        a.parents = parents;
+        a.J = p->J_vv;
+        a.z = p->z_dev;
+        a.phifix = p->phifix;
+        a.phi_kids = phi_b;
+        a.E_kids = E;
+        a.err = ctx->d_err;
+        a.E_const = p->E_const;
+        a.ld = p->Nv_pad;
+        a.Nv = Nv;
+        a.P = P;
+        a.S = p->S;
+        {
+            KTimer kt(ctx, KID_GA_INCR, st);
+            goac::launch(k_ga_incr, P, GI_THREADS, smem, st, a);
+        }
+        GOAC_LAUNCH_CHECK("k_ga_incr");
+        GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)P * Nv, cudaMemcpyDeviceToDevice, st));
+        std::swap(phi_a, phi_b);
+    }
+    return GOAC_OK;
+}
+
 }  // namespace goac
 
 extern "C" goac_status goac_ga_generation(goac_problem* p, const int8_t* pop_dev, const double* E_dev, int32_t P,
@@ -396,6 +598,8 @@ extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_d
     if (P == 0) return GOAC_OK;
     if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    if (precision == GOAC_PREC_F64_INCR)
+        return goac::ga_run_incremental(p, pop_dev, E_dev, P, n_gen, n_elite, p_mut_u32, seed, gen0);
     goac_status rc = goac::ensure(p->phi, (size_t)P * p->Nv);
     if (rc) return rc;
     int8_t* kids = (int8_t*)p->phi.ptr;

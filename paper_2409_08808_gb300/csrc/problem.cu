@@ -729,6 +729,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->score_tmp);
     free_buf(p->topk_tmp);
     free_buf(p->grad_tmp);
+    free_buf(p->ga_incr);
     free_buf(p->sched);
     free_buf(p->sched_ex);
     cudaFree(p->J_dig);
