@@ -144,6 +144,12 @@ __device__ __forceinline__ int lower_bound_gt(const unsigned long long* pre, int
 // Shared-memory slot of one child warp: child and parent B (Nv bytes each,
 // 16-byte rounded) and, per species s, a bitmask over class positions p of the
 // sites with child = s != B (mis[s][p / 32]).
+// Block-wide copy of the class positions at the front of shared memory.
+__host__ __device__ inline size_t ga_cpos_bytes(int Nv)
+{
+    return ((size_t)Nv * 4 + 15) & ~(size_t)15;
+}
+
 __host__ __device__ inline size_t ga_slot_bytes(int Nv, int S)
 {
     const size_t sp = ((size_t)Nv + 15) & ~(size_t)15;
@@ -154,12 +160,16 @@ __host__ __device__ inline size_t ga_slot_bytes(int Nv, int S)
 __global__ void k_ga_children(GaArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    const int Nv = a.Nv;
+    // block-wide copy of the class positions (site of class position p), then one slot per warp
+    int32_t* cpos = (int32_t*)smem;
+    for (int q = threadIdx.x; q < Nv; q += blockDim.x) cpos[q] = a.cls_pos[q];
+    __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.P) return;
-    const int Nv = a.Nv;
     const int W = (Nv + 31) / 32;
-    uint8_t* base = smem + ga_slot_bytes(Nv, a.S) * wib;
+    uint8_t* base = smem + ga_cpos_bytes(Nv) + ga_slot_bytes(Nv, a.S) * wib;
     int8_t* ch = (int8_t*)base;
     int8_t* pb = ch + (((size_t)Nv + 15) & ~(size_t)15);
     uint32_t* mis = (uint32_t*)(pb + (((size_t)Nv + 15) & ~(size_t)15));
@@ -188,7 +198,7 @@ __global__ void k_ga_children(GaArgs a)
     for (int e = lane; e < a.S * W; e += 32) mis[e] = 0u;
     __syncwarp();
     for (int q = lane; q < Nv; q += 32) {
-        const int w = a.cls_pos[q];
+        const int w = cpos[q];
         const int8_t s = ch[w];
         if ((unsigned)s < (unsigned)a.S && s != pb[w]) atomicOr(&mis[s * W + (q >> 5)], 1u << (q & 31));
     }
@@ -197,36 +207,42 @@ __global__ void k_ga_children(GaArgs a)
     // Crossover: for each site i (ascending) where the child differs from B,
     // the candidate swap pairs i with the lowest class position holding B_i
     // where B differs (the lowest set bit of mis[B_i] in i's class), taken with
-    // probability 1/2.
+    // probability 1/2.  Within a chunk of 32 sites the child values and the
+    // candidate mask live in registers: a taken swap changes the child at i and
+    // at its partner j, and only j (if it lies later in the chunk) can change
+    // its candidate bit.
     uint32_t kc = 0;
     int nsw = 0;
     uint4 blk = make_uint4(0, 0, 0, 0);    // this lane's Philox block of the current batch of 128 candidates
     for (int i0 = 0; i0 < Nv; i0 += 32) {
-        // per-lane facts of this chunk's sites (B does not change)
         const int il = i0 + lane;
-        int8_t my_b = 0;
-        int my_cs = 0, my_ce = 0, my_rank = 0;
+        int my_b = 0, my_c = 0, my_cs = 0, my_ce = 0, my_rank = 0;
         if (il < Nv) {
             my_b = pb[il];
+            my_c = ch[il];
             const int k = a.vclass[il];
             my_cs = a.cls_start[k];
             my_ce = a.cls_start[k + 1];
             my_rank = a.cls_rank[il];
         }
-        int from = 0;
-        while (true) {
-            const bool diff = lane >= from && il < Nv && ch[il] != my_b;
-            const uint32_t m = __ballot_sync(0xffffffffu, diff);
-            if (m == 0u) break;
+        uint32_t m = __ballot_sync(0xffffffffu, il < Nv && my_c != my_b);
+        while (m) {
             const int l = __ffs(m) - 1;
+            m &= m - 1u;
             const int ii = i0 + l;
-            const int8_t want = (int8_t)__shfl_sync(0xffffffffu, (int)my_b, l);
+            // candidate kc uses word kc & 3 of Philox block kc >> 2 (ctr {kc >> 2, gen, c, 3});
+            // the warp draws 32 consecutive blocks at a time, lane t holding block 32 q + t
+            if ((kc & 127u) == 0u) blk = goacd::philox(make_uint4((kc >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
+            const uint32_t wv = __shfl_sync(0xffffffffu, word_of(blk, (int)(kc & 3u)), (int)((kc >> 2) & 31u));
+            ++kc;
+            const int want = __shfl_sync(0xffffffffu, my_b, l);
+            const int old = __shfl_sync(0xffffffffu, my_c, l);
+            const int cs = __shfl_sync(0xffffffffu, my_cs, l), ce = __shfl_sync(0xffffffffu, my_ce, l);
+            const int pi = __shfl_sync(0xffffffffu, my_rank, l);
             if ((unsigned)want >= (unsigned)a.S) {      // not a species of the problem
                 if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
                 return;
             }
-            const int cs = __shfl_sync(0xffffffffu, my_cs, l), ce = __shfl_sync(0xffffffffu, my_ce, l);
-            const int pi = __shfl_sync(0xffffffffu, my_rank, l);
             const int wlo = cs >> 5, whi = (ce - 1) >> 5;
             const uint32_t* mw = mis + want * W;
             int pp = -1;
@@ -250,18 +266,17 @@ __global__ void k_ga_children(GaArgs a)
                 if (lane == 0) goacd::report(a.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
                 return;
             }
-            // candidate kc uses word kc & 3 of Philox block kc >> 2 (ctr {kc >> 2, gen, c, 3});
-            // the warp draws 32 consecutive blocks at a time, lane t holding block 32 q + t
-            if ((kc & 127u) == 0u) blk = goacd::philox(make_uint4((kc >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
-            const uint32_t wv = __shfl_sync(0xffffffffu, word_of(blk, (int)(kc & 3u)), (int)((kc >> 2) & 31u));
-            ++kc;
             if (wv < 0x80000000u) {
-                __syncwarp();
+                const int j = cpos[pp];
+                const int jl = j - i0;                      // j != ii; in this chunk iff 0 <= jl < 32
+                const int pbj = __shfl_sync(0xffffffffu, my_b, jl & 31);
+                if (lane == l) my_c = want;
+                if (lane == jl) my_c = old;
+                if (jl > l && jl < 32) m = old != pbj ? (m | (1u << jl)) : (m & ~(1u << jl));
+                __syncwarp();                               // every lane has read mis for this candidate
                 if (lane == 0) {
-                    const int j = a.cls_pos[pp];
-                    const int8_t old = ch[ii];               // old != want
-                    ch[j] = old;
-                    ch[ii] = want;
+                    ch[j] = (int8_t)old;
+                    ch[ii] = (int8_t)want;
                     mis[old * W + (pi >> 5)] &= ~(1u << (pi & 31));     // i now equals B_i
                     mis[want * W + (pp >> 5)] &= ~(1u << (pp & 31));    // j no longer holds B_i
                     if (pb[j] != old) mis[old * W + (pp >> 5)] |= 1u << (pp & 31);
@@ -269,7 +284,6 @@ __global__ void k_ga_children(GaArgs a)
                 __syncwarp();
                 ++nsw;
             }
-            from = l + 1;
         }
     }
     const uint4 y = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 4u), k0, k1);
@@ -289,7 +303,7 @@ __global__ void k_ga_children(GaArgs a)
         const uint32_t pa = goacd::draw_below(y.z, n);
         const uint32_t bb = goacd::draw_below(y.w, n - 1);
         const uint32_t pbi = bb + (bb >= pa);
-        const int va = a.cls_pos[start + pa], vb = a.cls_pos[start + pbi];
+        const int va = cpos[start + pa], vb = cpos[start + pbi];
         __syncwarp();
         if (lane == 0) {
             const int8_t t = ch[va];
@@ -508,11 +522,11 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     a.only_movable = p->only_movable;
     // warps (children) per block: a power of two up to 8, small enough that
     // the grid spreads over at least two blocks per SM, within 96 KB
-    const size_t slot = ga_slot_bytes(p->Nv, p->S);
-    if (slot > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
+    const size_t slot = ga_slot_bytes(p->Nv, p->S), cpos = ga_cpos_bytes(p->Nv);
+    if (slot + cpos > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     int wpb = 8;
-    while (wpb > 1 && ((size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
-    const size_t smem = slot * wpb;
+    while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
+    const size_t smem = cpos + slot * wpb;
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     KTimer kt(ctx, KID_GA, st);
     goac::launch(k_ga_children, (P + wpb - 1) / wpb, 32 * wpb, smem, st, a);
