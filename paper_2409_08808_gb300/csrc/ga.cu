@@ -216,16 +216,15 @@ __global__ void k_ga_children(GaArgs a)
     uint4 blk = make_uint4(0, 0, 0, 0);    // this lane's Philox block of the current batch of 128 candidates
     for (int i0 = 0; i0 < Nv; i0 += 32) {
         const int il = i0 + lane;
-        int my_b = 0, my_c = 0, my_cs = 0, my_ce = 0, my_rank = 0;
+        // per lane: B's species, the child's species and the class position (8 + 8 + 16 bits),
+        // and the class's position range (16 + 16 bits), so a candidate takes two shuffles
+        uint32_t my_bcr = 0u, my_rng = 0u;
         if (il < Nv) {
-            my_b = pb[il];
-            my_c = ch[il];
             const int k = a.vclass[il];
-            my_cs = a.cls_start[k];
-            my_ce = a.cls_start[k + 1];
-            my_rank = a.cls_rank[il];
+            my_bcr = (uint32_t)(uint8_t)pb[il] | ((uint32_t)(uint8_t)ch[il] << 8) | ((uint32_t)a.cls_rank[il] << 16);
+            my_rng = (uint32_t)a.cls_start[k] | ((uint32_t)a.cls_start[k + 1] << 16);
         }
-        uint32_t m = __ballot_sync(0xffffffffu, il < Nv && my_c != my_b);
+        uint32_t m = __ballot_sync(0xffffffffu, il < Nv && ((my_bcr ^ (my_bcr >> 8)) & 0xffu) != 0u);
         while (m) {
             const int l = __ffs(m) - 1;
             m &= m - 1u;
@@ -235,10 +234,9 @@ __global__ void k_ga_children(GaArgs a)
             if ((kc & 127u) == 0u) blk = goacd::philox(make_uint4((kc >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
             const uint32_t wv = __shfl_sync(0xffffffffu, word_of(blk, (int)(kc & 3u)), (int)((kc >> 2) & 31u));
             ++kc;
-            const int want = __shfl_sync(0xffffffffu, my_b, l);
-            const int old = __shfl_sync(0xffffffffu, my_c, l);
-            const int cs = __shfl_sync(0xffffffffu, my_cs, l), ce = __shfl_sync(0xffffffffu, my_ce, l);
-            const int pi = __shfl_sync(0xffffffffu, my_rank, l);
+            const uint32_t bcr = __shfl_sync(0xffffffffu, my_bcr, l), rng = __shfl_sync(0xffffffffu, my_rng, l);
+            const int want = (int8_t)(bcr & 0xffu), old = (int8_t)((bcr >> 8) & 0xffu), pi = (int)(bcr >> 16);
+            const int cs = (int)(rng & 0xffffu), ce = (int)(rng >> 16);
             if ((unsigned)want >= (unsigned)a.S) {      // not a species of the problem
                 if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
                 return;
@@ -269,17 +267,17 @@ __global__ void k_ga_children(GaArgs a)
             if (wv < 0x80000000u) {
                 const int j = cpos[pp];
                 const int jl = j - i0;                      // j != ii; in this chunk iff 0 <= jl < 32
-                const int pbj = __shfl_sync(0xffffffffu, my_b, jl & 31);
-                if (lane == l) my_c = want;
-                if (lane == jl) my_c = old;
+                const int pbj = pb[j];
+                if (lane == l) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)want << 8);
+                if (lane == jl) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)old << 8);
                 if (jl > l && jl < 32) m = old != pbj ? (m | (1u << jl)) : (m & ~(1u << jl));
                 __syncwarp();                               // every lane has read mis for this candidate
-                if (lane == 0) {
+                if (lane == 0) {                            // three updates of different bits
                     ch[j] = (int8_t)old;
                     ch[ii] = (int8_t)want;
-                    mis[old * W + (pi >> 5)] &= ~(1u << (pi & 31));     // i now equals B_i
-                    mis[want * W + (pp >> 5)] &= ~(1u << (pp & 31));    // j no longer holds B_i
-                    if (pb[j] != old) mis[old * W + (pp >> 5)] |= 1u << (pp & 31);
+                    atomicAnd(&mis[old * W + (pi >> 5)], ~(1u << (pi & 31)));     // i now equals B_i
+                    atomicAnd(&mis[want * W + (pp >> 5)], ~(1u << (pp & 31)));    // j no longer holds B_i
+                    if (pbj != old) atomicOr(&mis[old * W + (pp >> 5)], 1u << (pp & 31));
                 }
                 __syncwarp();
                 ++nsw;
@@ -523,7 +521,8 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     // warps (children) per block: a power of two up to 8, small enough that
     // the grid spreads over at least two blocks per SM, within 96 KB
     const size_t slot = ga_slot_bytes(p->Nv, p->S), cpos = ga_cpos_bytes(p->Nv);
-    if (slot + cpos > 200 * 1024) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
+    // (this bounds Nv below 33,437, so class positions fit the 16-bit fields the kernel packs)
+    if (slot + cpos > 200 * 1024 || p->Nv > 65535) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     int wpb = 8;
     while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
     const size_t smem = cpos + slot * wpb;
