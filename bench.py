@@ -683,9 +683,21 @@ def run_suite(args):
         for f in forms:
             forms[f]["speedup_vs_f64"] = forms["f64"]["ms_per_population"] / forms[f]["ms_per_population"]
         idx, Etop = gp.topk_rescore(pop, gp.score(pop, "bf16x3"), 64)
+        # top-k selection alone against the batch size: the 16-site rocksalt cell makes the FP64
+        # rescoring of the k = 64 candidates negligible; up to 512 configurations the pairwise
+        # rank kernel, above it the radix select
+        tiny = synth.tiny_rocksalt_problem()
+        gpt, _, _ = problem(tiny)
+        sel_ms = {}
+        for Bs in (512, 513, 4096, 262144, 1048576):
+            spt = gpt.random_configs(Bs, 5)
+            Et = torch.randn(Bs, dtype=torch.float64, device=dev)
+            gpt.topk_rescore(spt, Et, 64)
+            sel_ms[str(Bs)] = timed(lambda: [gpt.topk_rescore(spt, Et, 64) for _ in range(10)]) / 10
+            del spt, Et
         emit({"workload": WORKLOAD + ", every scoring form", "forms": forms,
               "top64_after_bf16x3_equals_fp64_top64": bool(set(idx.tolist()) == set(torch.argsort(E64)[:64].tolist())),
-              "ewald_build_ms": jms})
+              "topk64_select_ms_vs_batch": sel_ms, "ewald_build_ms": jms})
         del gp, J, pop, E64
 
     if want("relaxed"):

@@ -204,7 +204,10 @@ goac_status goac_score_host_async(goac_problem* prob, const int8_t* species_host
  * Background": the n lowest configurations are the output).  Selects the k  *
  * lowest E_approx (ties: lower index), rescores them in FP64 and returns     *
  * them sorted by the FP64 energy (ties: lower index).  idx_dev: k int32,    *
- * E_dev: k doubles.  1 <= k <= min(B, 1024).                                 */
+ * E_dev: k doubles.  1 <= k <= min(B, 1024).  E_approx_dev must hold no NaN *
+ * (-0 and +0 are equal).  Up to 512 configurations the selection ranks      *
+ * every pair; above, a radix select over an order-preserving 64-bit key of *
+ * E (six 11-bit digit passes, then an ordered compaction) does it in O(B).  */
 goac_status goac_topk_rescore(goac_problem* prob, const int8_t* species_dev, int32_t B, const double* E_approx_dev,
                               int32_t k, int32_t* idx_dev, double* E_dev);
 

@@ -467,6 +467,242 @@ __global__ void k_rank_select(const double* __restrict__ E, int B, int k, int* _
     if (i < B && rank < k) sel[rank] = i;
 }
 
+// Top-k selection in O(B) for large batches, with the result of k_rank_select
+// (the k smallest (E, index)): E is mapped to an order-preserving 64-bit key
+// (-0 read as +0), six passes of an 11-bit digit histogram over the keys that
+// share the digits fixed so far find the key T of the k-th smallest, and an
+// ordered compaction takes every key below T and the lowest-index keys equal
+// to T.  The selected indices come out in index order (keys below T first).
+constexpr int TK_BINS = 2048;
+constexpr int TK_BLOCK = 1024;           // elements per compaction block: 256 threads x 4
+constexpr int kTopkRankMax = 512;        // up to this batch the quadratic rank kernel is used
+
+struct TopkState {
+    unsigned long long prefix, mask;     // digits fixed so far and their bit mask
+    int need, cnt_lt;                    // rank still wanted among keys matching prefix; keys below
+};
+
+__device__ __forceinline__ unsigned long long topk_key(double e)
+{
+    if (e == 0.0) e = 0.0;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(e);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__global__ void __launch_bounds__(256) k_topk_init(TopkState* st, unsigned int* hist, int k)
+{
+    for (int i = threadIdx.x; i < TK_BINS; i += 256) hist[i] = 0u;
+    if (threadIdx.x == 0) {
+        st->prefix = 0ull;
+        st->mask = 0ull;
+        st->need = k;
+        st->cnt_lt = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_topk_hist(const double* __restrict__ E, int B, const TopkState* __restrict__ st,
+                                                   int shift, unsigned int* __restrict__ hist)
+{
+    __shared__ unsigned int h[TK_BINS];
+    for (int i = threadIdx.x; i < TK_BINS; i += 256) h[i] = 0u;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix, mask = st->mask;
+    for (long i = (long)blockIdx.x * 256 + threadIdx.x; i < B; i += (long)gridDim.x * 256) {
+        const unsigned long long key = topk_key(E[i]);
+        if (((key ^ prefix) & mask) == 0ull) atomicAdd(&h[(key >> shift) & (TK_BINS - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TK_BINS; i += 256)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One block: the bin holding rank `need` among the counted keys fixes the next digit.
+__global__ void __launch_bounds__(256) k_topk_pick(TopkState* st, unsigned int* hist, int shift)
+{
+    __shared__ unsigned int part[256];
+    __shared__ int found_v;
+    __shared__ unsigned int found_below;
+    const int t = threadIdx.x;
+    const unsigned int need = (unsigned int)st->need;
+    unsigned int loc[TK_BINS / 256], sum = 0u;
+#pragma unroll
+    for (int u = 0; u < TK_BINS / 256; ++u) {
+        loc[u] = hist[t * (TK_BINS / 256) + u];
+        sum += loc[u];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {             // inclusive scan over the 256 partial sums
+        const unsigned int v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    const unsigned int excl = part[t] - sum;
+    if (excl < need && need <= part[t]) {           // exactly one thread
+        unsigned int c = excl;
+#pragma unroll
+        for (int u = 0; u < TK_BINS / 256; ++u) {
+            if (c + loc[u] >= need) {
+                found_v = t * (TK_BINS / 256) + u;
+                found_below = c;
+                break;
+            }
+            c += loc[u];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < TK_BINS / 256; ++u) hist[t * (TK_BINS / 256) + u] = 0u;
+    __syncthreads();
+    if (t == 0) {
+        st->prefix |= (unsigned long long)found_v << shift;
+        st->mask |= (unsigned long long)(TK_BINS - 1) << shift;
+        st->need -= (int)found_below;
+        st->cnt_lt += (int)found_below;
+    }
+}
+
+// Per 1024-element block: keys below T and keys equal to T.
+__global__ void __launch_bounds__(256) k_topk_count(const double* __restrict__ E, int B, const TopkState* __restrict__ st,
+                                                    int2* __restrict__ cnt)
+{
+    __shared__ int red[2][8];
+    const unsigned long long T = st->prefix;
+    const long base = (long)blockIdx.x * TK_BLOCK;
+    int lt = 0, eq = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long i = base + threadIdx.x * 4 + u;
+        if (i < B) {
+            const unsigned long long key = topk_key(E[i]);
+            lt += key < T;
+            eq += key == T;
+        }
+    }
+    lt = __reduce_add_sync(0xffffffffu, lt);
+    eq = __reduce_add_sync(0xffffffffu, eq);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = lt;
+        red[1][threadIdx.x >> 5] = eq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0, b = 0;
+        for (int w = 0; w < 8; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        cnt[blockIdx.x] = make_int2(a, b);
+    }
+}
+
+// One block: exclusive scan of the per-block counts, in block order.
+__global__ void __launch_bounds__(1024) k_topk_scan(const int2* __restrict__ cnt, int nb, int2* __restrict__ off)
+{
+    __shared__ int wl[32], we[32];
+    __shared__ int carry_l, carry_e;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_l = carry_e = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const int2 v = b < nb ? cnt[b] : make_int2(0, 0);
+        int l = v.x, e = v.y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int tl = __shfl_up_sync(0xffffffffu, l, o), te = __shfl_up_sync(0xffffffffu, e, o);
+            if (lane >= o) {
+                l += tl;
+                e += te;
+            }
+        }
+        if (lane == 31) {
+            wl[wid] = l;
+            we[wid] = e;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            int xl = wl[lane], xe = we[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tl = __shfl_up_sync(0xffffffffu, xl, o), te = __shfl_up_sync(0xffffffffu, xe, o);
+                if (lane >= o) {
+                    xl += tl;
+                    xe += te;
+                }
+            }
+            wl[lane] = xl;
+            we[lane] = xe;
+        }
+        __syncthreads();
+        const int pl = carry_l + (wid ? wl[wid - 1] : 0), pe = carry_e + (wid ? we[wid - 1] : 0);
+        if (b < nb) off[b] = make_int2(pl + l - v.x, pe + e - v.y);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_l += wl[31];
+            carry_e += we[31];
+        }
+        __syncthreads();
+    }
+}
+
+// Per 1024-element block: keys below T to sel[off.x ...], keys equal to T to
+// sel[cnt_lt + off.y ...] while fewer than `need` have been placed; index order.
+__global__ void __launch_bounds__(256) k_topk_write(const double* __restrict__ E, int B, const TopkState* __restrict__ st,
+                                                    const int2* __restrict__ off, int* __restrict__ sel)
+{
+    __shared__ int wl[8], we[8];
+    const unsigned long long T = st->prefix;
+    const int need = st->need, cnt_lt = st->cnt_lt;
+    const int2 o = off[blockIdx.x];
+    if (o.x >= cnt_lt && o.y >= need) return;       // nothing of this block is selected (uniform)
+    const long base = (long)blockIdx.x * TK_BLOCK;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    bool fl[4], fe[4];
+    int nl = 0, ne = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long i = base + threadIdx.x * 4 + u;
+        fl[u] = fe[u] = false;
+        if (i < B) {
+            const unsigned long long key = topk_key(E[i]);
+            fl[u] = key < T;
+            fe[u] = key == T;
+        }
+        nl += fl[u];
+        ne += fe[u];
+    }
+    int il = nl, ie = ne;                            // inclusive scans in thread order
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int tl = __shfl_up_sync(0xffffffffu, il, d), te = __shfl_up_sync(0xffffffffu, ie, d);
+        if (lane >= d) {
+            il += tl;
+            ie += te;
+        }
+    }
+    if (lane == 31) {
+        wl[wid] = il;
+        we[wid] = ie;
+    }
+    __syncthreads();
+    int pl = 0, pe = 0;
+    for (int w = 0; w < wid; ++w) {
+        pl += wl[w];
+        pe += we[w];
+    }
+    int rl = o.x + pl + il - nl, re = o.y + pe + ie - ne;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = (int)(base + threadIdx.x * 4 + u);
+        if (fl[u]) sel[rl++] = i;
+        if (fe[u]) {
+            if (re < need) sel[cnt_lt + re] = i;
+            ++re;
+        }
+    }
+}
+
 __global__ void k_gather_rows(const int8_t* __restrict__ src, int Nv, const int* __restrict__ sel, int k,
                               int8_t* __restrict__ dst)
 {
@@ -847,15 +1083,37 @@ extern "C" goac_status goac_topk_rescore(goac_problem* p, const int8_t* species_
     GOAC_CUDA(cudaSetDevice(ctx->device));
     const int nb = (p->Nv + RS - 1) / RS;
     const long npairs = (long)nb * (nb + 1) / 2;
-    size_t need = sizeof(int) * 1024 + sizeof(double) * 1024 + sizeof(double) * (size_t)npairs * k +
-                  (size_t)k * p->Nv + 256;
+    const int nblk = (int)(((long)B + TK_BLOCK - 1) / TK_BLOCK);
+    const size_t sub_bytes = ((size_t)k * p->Nv + 255) & ~(size_t)255;
+    size_t need = sizeof(int) * 1024 + sizeof(double) * 1024 + sizeof(double) * (size_t)npairs * k + sub_bytes;
+    const size_t radix_at = need;
+    if (B > kTopkRankMax) need += 256 + sizeof(unsigned int) * TK_BINS + 2 * sizeof(int2) * (size_t)nblk;
     goac_status rc = goac::ensure(p->topk_tmp, need);
     if (rc) return rc;
     int* sel = (int*)p->topk_tmp.ptr;
     double* e64 = (double*)((char*)p->topk_tmp.ptr + sizeof(int) * 1024);
     double* part = e64 + 1024;
     int8_t* sub = (int8_t*)(part + (size_t)npairs * k);
-    goac::launch(k_rank_select, (B + 255) / 256, 256, 0, ctx->stream, E_approx_dev, B, k, sel);
+    if (B <= kTopkRankMax) {
+        goac::launch(k_rank_select, (B + 255) / 256, 256, 0, ctx->stream, E_approx_dev, B, k, sel);
+    } else {
+        TopkState* st = (TopkState*)((char*)p->topk_tmp.ptr + radix_at);
+        unsigned int* hist = (unsigned int*)((char*)st + 256);
+        int2* cnt = (int2*)(hist + TK_BINS);
+        int2* off = cnt + nblk;
+        goac::launch(k_topk_init, 1, 256, 0, ctx->stream, st, hist, k);
+        const int hgrid = (int)std::min<long>(((long)B + 255) / 256, (long)ctx->num_sms * 8);
+        const int shifts[6] = {53, 42, 31, 20, 9, 0};
+        for (int ps = 0; ps < 6; ++ps) {
+            goac::launch(k_topk_hist, hgrid, 256, 0, ctx->stream, E_approx_dev, B, (const TopkState*)st, shifts[ps],
+                         hist);
+            goac::launch(k_topk_pick, 1, 256, 0, ctx->stream, st, hist, shifts[ps]);
+        }
+        goac::launch(k_topk_count, nblk, 256, 0, ctx->stream, E_approx_dev, B, (const TopkState*)st, cnt);
+        goac::launch(k_topk_scan, 1, 1024, 0, ctx->stream, (const int2*)cnt, nblk, off);
+        goac::launch(k_topk_write, nblk, 256, 0, ctx->stream, E_approx_dev, B, (const TopkState*)st,
+                     (const int2*)off, sel);
+    }
     goac::launch(k_gather_rows, (int)(((long)k * p->Nv + 255) / 256), 256, 0, ctx->stream, species_dev, p->Nv, sel, k, sub);
     GOAC_LAUNCH_CHECK("topk select");
     goac::launch(k_rescore_pairs, (unsigned)npairs, 256, 0, ctx->stream, (const double*)p->J_vv, p->Nv_pad, p->Nv,

@@ -276,3 +276,28 @@ def test_population_over_2gib(ctx):
     rc = gp.random_configs(B, 6)
     rows = torch.cat([torch.arange(0, 200, device="cuda"), last]).long()
     assert _counts_ok(prob, rc[rows].cpu().numpy())
+
+
+@pytest.mark.parametrize("B,k", [(513, 64), (1025, 1024), (16385, 64), (250_000, 1024), (40_000, 1)])
+def test_topk_radix_select(ctx, B, k):
+    """Above 512 configurations the top-k selection is a radix select: the
+    same set as the k smallest (E, index) of the given approximate energies,
+    here integers and halves with many ties at and across the k-th place, and
+    -0 / +0 together; the rescored energies are the oracle's."""
+    prob = synth.tiny_rocksalt_problem()
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, B, 3)
+    rng = np.random.default_rng(B + k)
+    Ea = rng.integers(0, 400, B).astype(np.float64) * 0.5 - 100.0
+    Ea[rng.integers(0, B, 50)] = -0.0
+    Ea[rng.integers(0, B, 50)] = 0.0
+    Ea[rng.integers(0, B, 3 * k)] = -250.0          # a block of ties at the smallest value
+    want = np.lexsort((np.arange(B), Ea))[:k]
+    idx, E = gp.topk_rescore(torch.tensor(pop, device="cuda"), torch.tensor(Ea, device="cuda"), k)
+    idx, E = idx.cpu().numpy(), E.cpu().numpy()
+    assert sorted(idx.tolist()) == sorted(want.tolist())
+    Eo = oracle.score(Jo, prob.site_class, prob.fixed_q, prob.z, pop[np.sort(want)])
+    Eo_by = dict(zip(np.sort(want).tolist(), Eo.tolist()))
+    assert np.allclose(E, [Eo_by[i] for i in idx.tolist()], rtol=1e-10)
+    assert np.all(np.diff(E) >= 0)
