@@ -173,7 +173,20 @@ def test_energy_grad_parity(ctx, which, B):
         assert np.max(np.abs(dL[b] - go)) <= 1e-6 * scale + 1e-30
 
 
-@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5)])
+def _many_species_problem():
+    """120 random sites in one class holding 10 species (more than the
+    register path of the column sums takes), charged."""
+    rng = np.random.default_rng(21)
+    A = np.diag([9.0, 9.5, 10.0]) + rng.uniform(-0.5, 0.5, (3, 3))
+    n = 120
+    prob = synth.Problem(name="s10", lattice=A, frac=rng.uniform(0, 1, (n, 3)), site_class=np.zeros(n, np.int32),
+                         fixed_q=np.zeros(n), z=np.array([1.0, 2.0, 3.0, -1.0, -2.0, 0.0, 1.5, -0.5, 4.0, -3.0]),
+                         counts=np.full((1, 10), 12, np.int32), alpha=0.0, nimg=(0, 0, 0), kcut=0.0)
+    prob.alpha, prob.nimg, prob.kcut = synth.default_cutoffs(A)
+    return prob
+
+
+@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5), ("s10", 4)])
 def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
     """J.Q on tcgen05 with J and the real Q split in TF32 hi/lo: within the
     deterministic bound of the form.  Per site, |dPhi_v| <= (gamma_K + 2^-20)
@@ -182,7 +195,8 @@ def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
     and |d(dE/dL_vs)| <= 4 max|z| p_vs that bound (+ FP32 output rounding)."""
     import paper_2409_08808_gb300 as g
     prob = {"layered": lambda: synth.layered_problem(reps=(2, 1, 1)),
-            "bcc": lambda: synth.bcc_relaxed_problem(n_side=4)}[which]()
+            "bcc": lambda: synth.bcc_relaxed_problem(n_side=4),
+            "s10": _many_species_problem}[which]()
     Jg, Jo = build_pair(ctx, prob)
     gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
     L = synth.random_logits(prob, B, 13)
