@@ -54,7 +54,7 @@ def _args():
     ap.add_argument("--mc-steps", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
     ap.add_argument("--suite", action="store_true", help="measure the other workloads, one JSON line each")
-    ap.add_argument("--only", default="mc,ga,batch,forms,relaxed",
+    ap.add_argument("--only", default="mc,ga,batch,forms,relaxed,gd",
                     help="suite sections to run (comma separated: mc, ga, batch, forms, relaxed)")
     ap.add_argument("--batch-cells", type=int, default=256)
     ap.add_argument("--batch-chains", type=int, default=512)
@@ -619,6 +619,34 @@ def run_suite(args):
               "forms": res, "cpu_oracle_s_per_generation": cpu_gen, "cpu_oracle_note":
               "one generation of 256 children timed and scaled x4 (scoring is linear in the population), 1 thread",
               "ewald_build_ms": jms})
+
+    if want("gd"):
+        # ---- all-pairs steepest descent: layered R-3m 12x12x1 (N = 1296), 256 random configurations
+        prob = synth.layered_problem()
+        gp, J, jms = problem(prob)
+        B_gd = 256
+        start = gp.random_configs(B_gd, 41)
+        gp.gd_run(start.clone(), 2)
+        sp = start.clone()
+        box = {}
+        ms = timed(lambda: box.setdefault("r", gp.gd_run(sp, 1000)))
+        E_gd, steps = box["r"]
+        st = steps.double()
+        vclass = prob.site_class[prob.site_class >= 0]
+        pairs = float(sum(int((vclass == k).sum()) * (int((vclass == k).sum()) - 1) // 2 for k in range(prob.n_class)))
+        # per step of a live configuration: pass 0 (minimum) and pass 1 (lowest pair within the tie);
+        # the step that finds the local minimum runs pass 0 only
+        checks = pairs * float((2 * st + 1).sum())
+        E0 = gp.score(start, "f64")
+        emit({"workload": f"layered R-3m 12x12x1 (N=1296, Nv=864), {B_gd} random configurations, all-pairs steepest "
+                          "descent over single swaps to a local minimum, FP64",
+              "ms": ms, "steps_max": int(st.max()), "steps_mean": float(st.mean()),
+              "same_class_pairs_per_configuration": pairs,
+              "pair_checks_per_s": checks / (ms / 1e3),
+              "mean_E_start_eV": float(E0.mean()), "mean_E_end_eV": float(E_gd.mean()),
+              "end_is_fp64_consistent": bool(((E_gd - gp.score(sp, "f64")).abs() / E_gd.abs()).max() < 1e-10),
+              "ewald_build_ms": jms})
+        del gp, J
 
     if want("batch"):
         # ---- uneven batch: 256 rocksalt / spinel-like cells, N in [64, 2048], 512 chains each
