@@ -327,7 +327,7 @@ goac_status goac_batch_mc_autotune(goac_ctx* ctx, goac_problem* const* probs, in
  * positions from w2, w3 as in the Monte Carlo pick).                         *
  *   children_dev P x Nv out; parents_dev (P x 2 int32) and nswap_dev        *
  *   (P x 2 int32: swaps taken, candidates) are optional outputs.  A child's  *
- *   working set lives in shared memory: Nv <= 33,437 (fewer with many        *
+ *   working set lives in shared memory: Nv <= 33,432 (fewer with many        *
  *   species), else GOAC_ERR_INVALID_ARG.                                     *
  * ------------------------------------------------------------------------ */
 goac_status goac_ga_generation(goac_problem* prob, const int8_t* pop_dev, const double* E_dev, int32_t P,

@@ -521,7 +521,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     // warps (children) per block: a power of two up to 8, small enough that
     // the grid spreads over at least two blocks per SM, within 96 KB
     const size_t slot = ga_slot_bytes(p->Nv, p->S), cpos = ga_cpos_bytes(p->Nv);
-    // (this bounds Nv below 33,437, so class positions fit the 16-bit fields the kernel packs)
+    // (this bounds Nv to at most 33,432, so class positions fit the 16-bit fields the kernel packs)
     if (slot + cpos > 200 * 1024 || p->Nv > 65535) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     int wpb = 8;
     while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
