@@ -586,6 +586,18 @@ def run_suite(args):
                          "children_kernel_hbm_gbs_algorithmic": ga_bytes / (gk_avg / 1e3) / 1e9}
             if ik_n:
                 res[prec]["incremental_kernel_ms"] = ik_ms / ik_n
+        # R independent populations in one run: the children of all come from one launch and
+        # are rescored by one call over R P configurations
+        for prec in ("f64_incr", "bf16x3"):
+            R_pop = 8
+            popR = gp.random_configs(R_pop * 1024, 17)
+            gp.ga_run_populations(popR.clone(), R_pop, 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
+            ms = timed(lambda: gp.ga_run_populations(popR, R_pop, 50, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec))
+            res[f"{prec}_{R_pop}_populations"] = {
+                "ms": ms, "generations_per_s": 50 / (ms / 1e3),
+                "population_generations_per_s": R_pop * 50 / (ms / 1e3),
+                "child_evals_per_s": R_pop * 1024 * 50 / (ms / 1e3)}
+            del popR
         # the incremental rescoring kernel on one generation bred from the random population:
         # M_c changed sites per child -> M_c Nv FP64 FMAs and M_c J rows (Nv doubles each)
         kids, par, _ = gp.ga_generation(pop0, gp.score(pop0, "f64"), 20, oracle.p_mut_to_u32(0.1), 0, 9, record=True)

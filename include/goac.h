@@ -351,6 +351,18 @@ goac_status goac_ga_generation(goac_problem* prob, const int8_t* pop_dev, const 
 goac_status goac_ga_run(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
                         int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0, int32_t precision);
 
+/* R independent GA populations of P configurations each (the paper compares  *
+ * independent runs of its heuristics; this runs them together): population  *
+ * r occupies rows r P .. r P + P - 1 of pop_dev (R P x Nv) and E_dev (R P)   *
+ * and evolves exactly as goac_ga_run with key seed + r would on it alone     *
+ * (selection, elitism, crossover and mutation within the population; parent *
+ * indices population-local).  Every generation's children of all            *
+ * populations come from one launch and are rescored by one call over R P     *
+ * configurations.  R P <= GOAC_MAX_BATCH.                                    */
+goac_status goac_ga_run_populations(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t R, int32_t P,
+                                    int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0,
+                                    int32_t precision);
+
 /* ------------------------------------------------------------------------ *
  * Relaxed occupations (differentiable form; the paper's descent is discrete,*
  * SI Gradient Descent).  logits_dev: B x Nv x S float; p = softmax over the *

@@ -326,6 +326,18 @@ class Problem:
                                int(seed), int(gen0), _prec(precision)), "goac_ga_run")
         return E
 
+    def ga_run_populations(self, pop: torch.Tensor, R: int, n_gen: int, n_elite: int, p_mut_u32: int, seed: int,
+                           gen0: int = 0, precision="f64"):
+        """R independent populations in place on `pop` (R P x Nv, population r in rows r P ...);
+        population r evolves as ga_run with seed + r.  Returns the final energies (R P)."""
+        RP = pop.shape[0]
+        assert R > 0 and RP % R == 0
+        E = torch.empty(RP, dtype=torch.float64, device=self._dev())
+        _check(lib.goac_ga_run_populations(self.handle, _ptr(pop), _ptr(E), int(R), RP // R, int(n_gen), int(n_elite),
+                                           int(p_mut_u32), int(seed), int(gen0), _prec(precision)),
+               "goac_ga_run_populations")
+        return E
+
     # ---- relaxed occupations --------------------------------------------
     def energy_grad(self, logits: torch.Tensor, lam: float, precision="f64", want_grad: bool = True):
         B = logits.shape[0]

@@ -26,6 +26,8 @@ namespace {
 __global__ void k_ga_minmax(const double* __restrict__ E, int P, double* __restrict__ mm)
 {
     __shared__ double smin[1024], smax[1024];
+    E += (long)blockIdx.x * P;                // one block per population
+    mm += 2 * blockIdx.x;
     double lo = E[0], hi = E[0];
     for (int b = threadIdx.x; b < P; b += blockDim.x) {
         lo = fmin(lo, E[b]);
@@ -54,6 +56,10 @@ __global__ void __launch_bounds__(1024) k_ga_fitness(const double* __restrict__ 
 {
     __shared__ unsigned long long warp_tot[32];
     __shared__ unsigned long long carry;
+    E += (long)blockIdx.x * P;                // one block per population
+    mm += 2 * blockIdx.x;
+    pre += (long)blockIdx.x * P;
+    ftot += blockIdx.x;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const double emin = mm[0], emax = mm[1];
@@ -91,11 +97,14 @@ __global__ void __launch_bounds__(1024) k_ga_fitness(const double* __restrict__ 
 // Elite selection: the rank of individual i by (E, index) is the number of j
 // with E_j < E_i, or E_j == E_i and j < i; one warp per i (lanes stride over
 // j, warp sum), so the O(P^2) comparisons spread over P warps.
-__global__ void k_ga_rank(const double* __restrict__ E, int P, int k, int* __restrict__ sel)
+__global__ void k_ga_rank(const double* __restrict__ E, int R, int P, int k, int* __restrict__ sel)
 {
-    const int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const long gi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= P) return;                       // whole warps leave together
+    if (gi >= (long)R * P) return;            // whole warps leave together
+    const int r = (int)(gi / P), i = (int)(gi % P);
+    E += (long)r * P;                         // individual i of population r
+    sel += (long)r * k;
     const double ei = E[i];
     int rank = 0;
     for (int j = lane; j < P; j += 32) {
@@ -122,7 +131,7 @@ struct GaArgs {
     int* err;
     uint64_t seed;
     uint32_t wtotal, p_mut, gen;
-    int P, Nv, S, n_elite, ncls, nmovable, only_movable;
+    int R, P, Nv, S, n_elite, ncls, nmovable, only_movable;   // R populations of P
 };
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int i)
@@ -166,34 +175,40 @@ __global__ void k_ga_children(GaArgs a)
     for (int q = threadIdx.x; q < Nv; q += blockDim.x) cpos[q] = a.cls_pos[q];
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (c >= a.P) return;
+    const long cg = (long)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (cg >= (long)a.R * a.P) return;
+    // child c of population r: the population's own parents, fitness sums and
+    // elite, Philox key seed + r
+    const int r = (int)(cg / a.P), c = (int)(cg % a.P);
+    const int8_t* popr = a.pop + (long)r * a.P * Nv;
     const int W = (Nv + 31) / 32;
     uint8_t* base = smem + ga_cpos_bytes(Nv) + ga_slot_bytes(Nv, a.S) * wib;
     int8_t* ch = (int8_t*)base;
     int8_t* pb = ch + (((size_t)Nv + 15) & ~(size_t)15);
     uint32_t* mis = (uint32_t*)(pb + (((size_t)Nv + 15) & ~(size_t)15));
-    int8_t* out = a.children + (long)c * Nv;
+    int8_t* out = a.children + cg * Nv;
 
     if (c < a.n_elite) {
-        const int src = a.elite[c];
-        for (int w = lane; w < Nv; w += 32) out[w] = a.pop[(long)src * Nv + w];
+        const int src = a.elite[(long)r * a.n_elite + c];
+        for (int w = lane; w < Nv; w += 32) out[w] = popr[(long)src * Nv + w];
         if (lane == 0) {
-            if (a.parents) a.parents[2 * c] = a.parents[2 * c + 1] = src;
-            if (a.nswap) a.nswap[2 * c] = a.nswap[2 * c + 1] = 0;
+            if (a.parents) a.parents[2 * cg] = a.parents[2 * cg + 1] = src;
+            if (a.nswap) a.nswap[2 * cg] = a.nswap[2 * cg + 1] = 0;
         }
         return;
     }
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const uint64_t key = a.seed + (uint64_t)r;
+    const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
     const uint4 x = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 2u), k0, k1);
-    const unsigned long long ftot = *a.ftot;
+    const unsigned long long* prer = a.pre + (long)r * a.P;
+    const unsigned long long ftot = a.ftot[r];
     const unsigned long long xa = ((unsigned long long)x.x << 32) | x.y;
     const unsigned long long xb = ((unsigned long long)x.z << 32) | x.w;
-    const int A = lower_bound_gt(a.pre, a.P, __umul64hi(xa, ftot));
-    const int B = lower_bound_gt(a.pre, a.P, __umul64hi(xb, ftot));
+    const int A = lower_bound_gt(prer, a.P, __umul64hi(xa, ftot));
+    const int B = lower_bound_gt(prer, a.P, __umul64hi(xb, ftot));
     for (int w = lane; w < Nv; w += 32) {
-        ch[w] = a.pop[(long)A * Nv + w];
-        pb[w] = a.pop[(long)B * Nv + w];
+        ch[w] = popr[(long)A * Nv + w];
+        pb[w] = popr[(long)B * Nv + w];
     }
     for (int e = lane; e < a.S * W; e += 32) mis[e] = 0u;
     __syncwarp();
@@ -313,12 +328,12 @@ __global__ void k_ga_children(GaArgs a)
     for (int w = lane; w < Nv; w += 32) out[w] = ch[w];
     if (lane == 0) {
         if (a.parents) {
-            a.parents[2 * c] = A;
-            a.parents[2 * c + 1] = B;
+            a.parents[2 * cg] = A;
+            a.parents[2 * cg + 1] = B;
         }
         if (a.nswap) {
-            a.nswap[2 * c] = nsw;
-            a.nswap[2 * c + 1] = (int32_t)kc;
+            a.nswap[2 * cg] = nsw;
+            a.nswap[2 * cg + 1] = (int32_t)kc;
         }
     }
 }
@@ -336,10 +351,10 @@ constexpr int GI_THREADS = 256;
 constexpr int GI_R = 4;
 
 struct GaIncrArgs {
-    const int8_t* pop;        // P x Nv parents
-    const double* phi_pop;    // P x Nv
-    const int8_t* kids;       // P x Nv
-    const int32_t* parents;   // P x 2
+    const int8_t* pop;        // R P x Nv parents (R populations of P)
+    const double* phi_pop;    // R P x Nv
+    const int8_t* kids;       // R P x Nv
+    const int32_t* parents;   // R P x 2, indices within the child's population
     const double* J;          // J_vv, rows of ld doubles
     const double* z;          // 64
     const double* phifix;     // Nv
@@ -357,17 +372,20 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
     int* idx = (int*)(dq + g.Nv);             // Nv
     __shared__ int wcnt[GI_THREADS / 32][2];
     __shared__ double wsum[GI_THREADS / 32];
-    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long c = blockIdx.x;                // child c of population c / P
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int NW = GI_THREADS / 32;
     const int Nv = g.Nv;
-    const int A = g.parents[2 * c], B = g.parents[2 * c + 1];
-    if ((unsigned)A >= (unsigned)g.P || (unsigned)B >= (unsigned)g.P) {
-        if (tid == 0) goacd::report(g.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
+    const int A0 = g.parents[2 * c], B0 = g.parents[2 * c + 1];
+    if ((unsigned)A0 >= (unsigned)g.P || (unsigned)B0 >= (unsigned)g.P) {
+        if (tid == 0) goacd::report(g.err, GOAC_ERR_INTERNAL, goac::SITE_GA, (int)c);
         return;
     }
-    const int8_t* kid = g.kids + (long)c * Nv;
-    const int8_t* pa = g.pop + (long)A * Nv;
-    const int8_t* pb = g.pop + (long)B * Nv;
+    const long base = c / g.P * g.P;
+    const long A = base + A0, B = base + B0;
+    const int8_t* kid = g.kids + c * Nv;
+    const int8_t* pa = g.pop + A * Nv;
+    const int8_t* pb = g.pop + B * Nv;
     // the nearer parent (ties: A)
     int da = 0, db = 0;
     for (int v = tid; v < Nv; v += GI_THREADS) {
@@ -392,7 +410,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         DB += wcnt[w][1];
     }
     const bool useB = DB < DA;
-    const int par = useB ? B : A;
+    const long par = useB ? B : A;
     const int8_t* pp = useB ? pb : pa;
     __syncthreads();
     // changed sites in ascending order and their charge differences
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         __syncthreads();
     }
     if (__syncthreads_or(bad)) {
-        if (tid == 0) goacd::report(g.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
+        if (tid == 0) goacd::report(g.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, (int)c);
         return;
     }
     double e = 0.0;
@@ -438,7 +456,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
 #pragma unroll
         for (int r = 0; r < GI_R; ++r) {
             const int v = v0 + r * GI_THREADS + tid;
-            acc[r] = v < Nv ? g.phi_pop[(long)par * Nv + v] : 0.0;
+            acc[r] = v < Nv ? g.phi_pop[par * Nv + v] : 0.0;
         }
         for (int t = 0; t < M; ++t) {
             const double d = dq[t];
@@ -453,7 +471,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         for (int r = 0; r < GI_R; ++r) {
             const int v = v0 + r * GI_THREADS + tid;
             if (v < Nv) {
-                g.phi_kids[(long)c * Nv + v] = acc[r];
+                g.phi_kids[c * Nv + v] = acc[r];
                 e = fma(g.z[kid[v]], acc[r] + g.phifix[v], e);
             }
         }
@@ -474,24 +492,27 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
 
 namespace goac {
 
-static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const double* E, int P, int n_elite,
-                                      uint32_t p_mut, uint32_t gen, uint64_t seed, int8_t* children, int32_t* parents,
-                                      int32_t* nswap)
+// One generation of R independent populations of P (population r: rows r P ..
+// r P + P - 1, Philox key seed + r).
+static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const double* E, int R, int P,
+                                      int n_elite, uint32_t p_mut, uint32_t gen, uint64_t seed, int8_t* children,
+                                      int32_t* parents, int32_t* nswap)
 {
     goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;
-    const size_t need = sizeof(unsigned long long) * ((size_t)P + 4) + sizeof(int) * ((size_t)n_elite + 4) +
-                        2 * sizeof(double) + 256;
+    const long RP = (long)R * P;
+    const size_t need = sizeof(unsigned long long) * ((size_t)RP + (size_t)R + 2) + 2 * sizeof(double) * (size_t)R +
+                        sizeof(int) * ((size_t)R * n_elite + 4) + 256;
     goac_status rc = ensure(p->score_tmp, need);
     if (rc) return rc;
     char* base = (char*)p->score_tmp.ptr;
     unsigned long long* pre = (unsigned long long*)base;
-    unsigned long long* ftot = pre + P;
-    double* mm = (double*)(ftot + 2);
-    int* elite = (int*)(mm + 2);
-    goac::launch(k_ga_minmax, 1, 1024, 0, st, E, P, mm);
-    goac::launch(k_ga_fitness, 1, 1024, 0, st, E, P, mm, pre, ftot);
-    if (n_elite > 0) goac::launch(k_ga_rank, (P + 7) / 8, 256, 0, st, E, P, n_elite, elite);
+    unsigned long long* ftot = pre + RP;
+    double* mm = (double*)(ftot + R + 1);
+    int* elite = (int*)(mm + 2 * (size_t)R);
+    goac::launch(k_ga_minmax, R, 1024, 0, st, E, P, mm);
+    goac::launch(k_ga_fitness, R, 1024, 0, st, E, P, mm, pre, ftot);
+    if (n_elite > 0) goac::launch(k_ga_rank, (int)((RP + 7) / 8), 256, 0, st, E, R, P, n_elite, elite);
     GOAC_LAUNCH_CHECK("ga prep");
     GaArgs a;
     a.pop = pop;
@@ -511,6 +532,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     a.wtotal = p->wtotal;
     a.p_mut = p_mut;
     a.gen = gen;
+    a.R = R;
     a.P = P;
     a.Nv = p->Nv;
     a.S = p->S;
@@ -524,11 +546,11 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     // (this bounds Nv to at most 33,432, so class positions fit the 16-bit fields the kernel packs)
     if (slot + cpos > 200 * 1024 || p->Nv > 65535) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     int wpb = 8;
-    while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (P + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
+    while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (RP + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
     const size_t smem = cpos + slot * wpb;
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     KTimer kt(ctx, KID_GA, st);
-    goac::launch(k_ga_children, (P + wpb - 1) / wpb, 32 * wpb, smem, st, a);
+    goac::launch(k_ga_children, (int)((RP + wpb - 1) / wpb), 32 * wpb, smem, st, a);
     GOAC_LAUNCH_CHECK("k_ga_children");
     return GOAC_OK;
 }
@@ -536,28 +558,29 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
 // GA run with incremental FP64 rescoring: the potentials of the population
 // are formed once by the FP64 scoring GEMM, then every generation forms each
 // child's potential and energy from its nearer parent's (k_ga_incr).
-static goac_status ga_run_incremental(goac_problem* p, int8_t* pop, double* E, int P, int n_gen, int n_elite,
-                                      uint32_t p_mut, uint64_t seed, uint32_t gen0)
+static goac_status ga_run_incremental(goac_problem* p, int8_t* pop, double* E, int R, int P, int n_gen,
+                                      int n_elite, uint32_t p_mut, uint64_t seed, uint32_t gen0)
 {
     goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;
     const int Nv = p->Nv;
+    const long RP = (long)R * P;
     const size_t smem = (sizeof(double) + sizeof(int)) * (size_t)Nv;
     if (smem > 200 * 1024) return fail(GOAC_ERR_UNSUPPORTED, "goac_ga_run: incremental rescoring needs Nv <= 17066");
-    goac_status rc = ensure(p->phi, (size_t)P * Nv);
+    goac_status rc = ensure(p->phi, (size_t)RP * Nv);
     if (rc) return rc;
-    const size_t phi_bytes = sizeof(double) * (size_t)P * Nv;
-    rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)P + 256);
+    const size_t phi_bytes = sizeof(double) * (size_t)RP * Nv;
+    rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)RP + 256);
     if (rc) return rc;
     int8_t* kids = (int8_t*)p->phi.ptr;
     double* phi_a = (double*)p->ga_incr.ptr;
     double* phi_b = (double*)((char*)p->ga_incr.ptr + phi_bytes);
     int32_t* parents = (int32_t*)((char*)p->ga_incr.ptr + 2 * phi_bytes);
-    rc = score_f64(p, pop, P, E, phi_a);
+    rc = score_f64(p, pop, (int)RP, E, phi_a);
     if (rc) return rc;
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     for (int g = 0; g < n_gen; ++g) {
-        rc = ga_generation_impl(p, pop, E, P, n_elite, p_mut, gen0 + (uint32_t)g, seed, kids, parents, nullptr);
+        rc = ga_generation_impl(p, pop, E, R, P, n_elite, p_mut, gen0 + (uint32_t)g, seed, kids, parents, nullptr);
         if (rc) return rc;
         GaIncrArgs a;
         a.pop = pop;
@@ -577,10 +600,10 @@ static goac_status ga_run_incremental(goac_problem* p, int8_t* pop, double* E, i
         a.S = p->S;
         {
             KTimer kt(ctx, KID_GA_INCR, st);
-            goac::launch(k_ga_incr, P, GI_THREADS, smem, st, a);
+            goac::launch(k_ga_incr, (int)RP, GI_THREADS, smem, st, a);
         }
         GOAC_LAUNCH_CHECK("k_ga_incr");
-        GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)P * Nv, cudaMemcpyDeviceToDevice, st));
+        GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
         std::swap(phi_a, phi_b);
     }
     return GOAC_OK;
@@ -597,34 +620,42 @@ extern "C" goac_status goac_ga_generation(goac_problem* p, const int8_t* pop_dev
     if (P == 0) return GOAC_OK;
     if (!pop_dev || !E_dev || !children_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
-    return goac::ga_generation_impl(p, pop_dev, E_dev, P, n_elite, p_mut_u32, gen, seed, children_dev, parents_dev,
+    return goac::ga_generation_impl(p, pop_dev, E_dev, 1, P, n_elite, p_mut_u32, gen, seed, children_dev, parents_dev,
                                     nswap_dev);
+}
+
+extern "C" goac_status goac_ga_run_populations(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t R,
+                                               int32_t P, int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32,
+                                               uint64_t seed, uint32_t gen0, int32_t precision)
+{
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL problem");
+    if (R < 0 || P < 0 || (int64_t)R * P > GOAC_MAX_BATCH || n_gen < 0 || n_elite < 0 || n_elite > P)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes");
+    if (R == 0 || P == 0) return GOAC_OK;
+    if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    if (precision == GOAC_PREC_F64_INCR)
+        return goac::ga_run_incremental(p, pop_dev, E_dev, R, P, n_gen, n_elite, p_mut_u32, seed, gen0);
+    const int RP = R * P;
+    goac_status rc = goac::ensure(p->phi, (size_t)RP * p->Nv);
+    if (rc) return rc;
+    int8_t* kids = (int8_t*)p->phi.ptr;
+    rc = goac_score(p, pop_dev, RP, precision, E_dev);
+    if (rc) return rc;
+    for (int g = 0; g < n_gen; ++g) {
+        rc = goac::ga_generation_impl(p, pop_dev, E_dev, R, P, n_elite, p_mut_u32, gen0 + (uint32_t)g, seed, kids,
+                                      nullptr, nullptr);
+        if (rc) return rc;
+        GOAC_CUDA(cudaMemcpyAsync(pop_dev, kids, (size_t)RP * p->Nv, cudaMemcpyDeviceToDevice, p->ctx->stream));
+        rc = goac_score(p, pop_dev, RP, precision, E_dev);
+        if (rc) return rc;
+    }
+    return GOAC_OK;
 }
 
 extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
                                    int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0,
                                    int32_t precision)
 {
-    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL problem");
-    if (P < 0 || P > GOAC_MAX_BATCH || n_gen < 0 || n_elite < 0 || n_elite > P)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes");
-    if (P == 0) return GOAC_OK;
-    if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
-    GOAC_CUDA(cudaSetDevice(p->ctx->device));
-    if (precision == GOAC_PREC_F64_INCR)
-        return goac::ga_run_incremental(p, pop_dev, E_dev, P, n_gen, n_elite, p_mut_u32, seed, gen0);
-    goac_status rc = goac::ensure(p->phi, (size_t)P * p->Nv);
-    if (rc) return rc;
-    int8_t* kids = (int8_t*)p->phi.ptr;
-    rc = goac_score(p, pop_dev, P, precision, E_dev);
-    if (rc) return rc;
-    for (int g = 0; g < n_gen; ++g) {
-        rc = goac::ga_generation_impl(p, pop_dev, E_dev, P, n_elite, p_mut_u32, gen0 + (uint32_t)g, seed, kids,
-                                      nullptr, nullptr);
-        if (rc) return rc;
-        GOAC_CUDA(cudaMemcpyAsync(pop_dev, kids, (size_t)P * p->Nv, cudaMemcpyDeviceToDevice, p->ctx->stream));
-        rc = goac_score(p, pop_dev, P, precision, E_dev);
-        if (rc) return rc;
-    }
-    return GOAC_OK;
+    return goac_ga_run_populations(p, pop_dev, E_dev, 1, P, n_gen, n_elite, p_mut_u32, seed, gen0, precision);
 }

@@ -84,6 +84,28 @@ def test_ga_run_incremental_parity(ctx):
     assert np.max(np.abs(E - E_o) / np.abs(E_o)) <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["f64", "f64_incr"])
+def test_ga_populations_equal_separate_runs(ctx, prec):
+    """Three populations of 40 in one run (children of all from one launch,
+    one rescoring call): each equals goac_ga_run on it alone with key seed + r,
+    bit for bit, and population 1 equals the oracle's GA with that key."""
+    prob = synth.layered_problem(reps=(2, 2, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    R, P, n_gen, n_elite, seed = 3, 40, 5, 3, 11
+    pops = [synth.random_population(prob, P, 100 + r) for r in range(R)]
+    sp = torch.tensor(np.concatenate(pops), device="cuda")
+    E = gp.ga_run_populations(sp, R, n_gen, n_elite, oracle.p_mut_to_u32(0.2), seed, precision=prec)
+    for r in range(R):
+        spr = torch.tensor(pops[r], device="cuda")
+        Er = gp.ga_run(spr, n_gen, n_elite, oracle.p_mut_to_u32(0.2), seed + r, precision=prec)
+        assert torch.equal(sp[r * P:(r + 1) * P], spr)
+        assert torch.equal(E[r * P:(r + 1) * P], Er)
+    fin_o, E_o = oracle.ga_run(Jo, prob.site_class, prob.fixed_q, prob.z, pops[1], n_gen, n_elite, 0.2, seed=seed + 1)
+    assert np.array_equal(sp[P:2 * P].cpu().numpy(), fin_o)
+    assert np.max(np.abs(E[P:2 * P].cpu().numpy() - E_o) / np.abs(E_o)) <= 1e-10
+
+
 def test_ga_incremental_degenerate_cell(ctx):
     """Rocksalt 2x2x2: symmetry and duplicated individuals make many energies
     equal, so the GA's rank and fitness decisions sit on ties that FP64 rounding
