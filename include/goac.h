@@ -378,7 +378,8 @@ goac_status goac_ga_run_populations(goac_problem* prob, int8_t* pop_dev, double*
 goac_status goac_energy_grad(goac_problem* prob, const float* logits_dev, int32_t B, double lambda,
                              int32_t precision, double* E_dev, float* dlogits_dev);
 
-/* Projected descent on the logits (spec differentiation form, used to  *
+/* Projected descent on the logits (the relaxed, differentiable form; the    *
+ * paper's own gradient descent is discrete, SI Gradient Descent; used to     *
  * seed MC / GA populations): n_steps of L -= eta dE/dL with the gradient of  *
  * goac_energy_grad (softmax keeps p on the simplex), in place on logits_dev. *
  * dlogits_scratch_dev: caller buffer of B x Nv x S floats.  E_dev: energies   *
