@@ -433,6 +433,7 @@ def run_ours(args, world, rank, local):
     for prec in ("f64", "f32"):
         Cn = 152 * (6 if prec == "f64" else 8)
         chains = gp.random_configs(Cn, 77 + rank)
+        W_t, cpc_t, _ = gp.mc_autotune(chains, 0.05, 128, prec)      # launch shape for this cell
         gp.mc_run(chains, 0.05, args.mc_steps, 5, step0=0, precision=prec)
         torch.cuda.synchronize()
         ctx.set_timing(True)
@@ -451,6 +452,7 @@ def run_ours(args, world, rank, local):
         bytes_alg = trials * 32 + acc * trials * 2 * prob.N * rb
         mc[prec] = {"trials_per_s": world * trials / (_max_over_ranks(mms, world) / 1e3), "chains": Cn,
                     "steps_per_chain": args.mc_steps, "kT_eV": 0.05, "acceptance": acc, "ms": mms,
+                    "autotuned_warps_per_chain": W_t, "autotuned_chains_per_cta": cpc_t,
                     "hbm_gbs_algorithmic": bytes_alg / (mc_kms / 1e3) / 1e9,
                     "hbm_frac": bytes_alg / (mc_kms / 1e3) / 1e9 / hbm_peak}
         if prec == "f64":

@@ -238,6 +238,18 @@ goac_status goac_mc_run(goac_problem* prob, int8_t* species_dev, int32_t C, cons
                         uint64_t seed, uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
                         int8_t* best_species_dev, int64_t* n_accept_dev);
 
+/* Launch-shape autotuner for goac_mc_run / goac_sa_run / goac_remc_run (no *
+ * counterpart in the paper): each (warps per chain W, chains per CTA) in     *
+ * {1, 2, 4} x {1, 2, 4, 8, 15} that fits in shared memory runs probe_steps  *
+ * steps on a scratch copy of species_dev (C x Nv, not modified) with the    *
+ * temperatures kT_dev (C); the fastest (CUDA events on the context stream)  *
+ * is kept in the problem for `precision` and used by later calls.  The      *
+ * trajectories do not depend on the launch shape.  W_out, cpc_out, ms_out   *
+ * (host, nullable): the choice and its probe time.  Synchronises.           */
+goac_status goac_mc_autotune(goac_problem* prob, const int8_t* species_dev, int32_t C, const double* kT_dev,
+                             int64_t probe_steps, int32_t precision, int32_t* W_out, int32_t* cpc_out,
+                             double* ms_out);
+
 /* Simulated annealing (SI, Simulated annealing: the MC routine with the     *
  * temperature lowered towards 0 during the run): goac_mc_run with the        *
  * temperature of step t set to kT0 (kT1/kT0)^(t/(total_steps-1)) per chain   *

@@ -258,6 +258,16 @@ class Problem:
                                _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)), "goac_mc_run")
         return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
 
+    def mc_autotune(self, species: torch.Tensor, kT, probe_steps: int = 256, precision="f64"):
+        """Time the Monte Carlo launch shapes on a copy of `species` and keep the fastest for
+        later runs of this problem.  Returns (warps per chain, chains per CTA, probe ms)."""
+        Cn = species.shape[0]
+        kTt = torch.as_tensor(kT, dtype=torch.float64, device=self._dev()).expand(Cn).contiguous()
+        W, c, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib.goac_mc_autotune(self.handle, _ptr(species), Cn, _ptr(kTt), int(probe_steps), _prec(precision),
+                                    C.byref(W), C.byref(c), C.byref(ms)), "goac_mc_autotune")
+        return int(W.value), int(c.value), float(ms.value)
+
     def gd_run(self, species: torch.Tensor, max_steps: int):
         """Steepest descent over single swaps, in place on `species`.  Returns (E, steps)."""
         B = species.shape[0]

@@ -115,6 +115,7 @@ struct goac_problem {
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
     DevBuf ga_incr;            // incremental GA rescoring: 2 x P x Nv potentials, P x 2 parents
+    int mc_tuned[2][2] = {{0, 0}, {0, 0}};   // [FP64, FP32]: autotuned {warps per chain, chains per CTA}, 0 = none
     // persistent tensor-core schedules (device copies) for the last shapes
     DevBuf sched, sched_ex;
     uint64_t sched_key = 0, sched_ex_key = 0;

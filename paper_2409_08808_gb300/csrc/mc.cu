@@ -361,10 +361,11 @@ constexpr size_t kSmemBudget = 220 * 1024;
 
 }  // namespace
 
+// W_force / cpc_force (> 0) override the launch shape (the autotuner's probes).
 static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
                                const double* kT1_dev, int64_t total, int64_t n_steps, uint64_t seed, uint64_t step0,
                                int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
-                               int64_t* n_accept_dev)
+                               int64_t* n_accept_dev, int W_force = 0, int cpc_force = 0)
 {
     if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL problem");
     if (C < 0 || C > GOAC_MAX_BATCH || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: bad size");
@@ -395,11 +396,14 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
     else if (goac::exact_supported(p)) rc = goac::phi_exact(p, species_dev, C, E0, (double*)phi0);
     else rc = goac::score_f64(p, species_dev, C, E0, (double*)phi0);
     if (rc) return rc;
-    // warps per chain: more warps share the O(Nv) update of a long chain
-    const int W = p->Nv >= 3072 ? 4 : (p->Nv >= 1536 ? 2 : 1);
+    // launch shape: warps per chain (more warps share the O(Nv) update of a long
+    // chain) and chains per CTA, from the autotuner when it has run for this
+    // problem and precision, else by size; the trajectories do not depend on it
+    const int* tuned = p->mc_tuned[f32 ? 1 : 0];
+    int W = W_force ? W_force : (tuned[0] ? tuned[0] : (p->Nv >= 3072 ? 4 : (p->Nv >= 1536 ? 2 : 1)));
     int cpc = (int)(kSmemBudget / slot);
     cpc = std::min(cpc, 1024 / (32 * W));
-    cpc = std::min(cpc, 15);
+    cpc = std::min(cpc, cpc_force ? cpc_force : (tuned[1] ? tuned[1] : 15));
     cpc = std::min(cpc, C);
     if (cpc < 1) cpc = 1;
     const size_t smem = slot * cpc;
@@ -446,6 +450,77 @@ extern "C" goac_status goac_sa_run(goac_problem* p, int8_t* species_dev, int32_t
     if (C != 0 && !kT1_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_sa_run: kT1 needed");
     return mc_run_impl(p, species_dev, C, kT0_dev, kT1_dev, total_steps, n_steps, seed, step0, precision, E_dev,
                        bestE_dev, best_species_dev, n_accept_dev);
+}
+
+// Autotuner of the single-problem Monte Carlo launch: every (warps per chain,
+// chains per CTA) in {1, 2, 4} x {1, 2, 4, 8, 15} that fits runs `probe_steps`
+// steps on a scratch copy of the chains (twice, the second timed with CUDA
+// events on the context stream); the fastest is kept for this problem and
+// precision and used by later goac_mc_run / goac_sa_run / goac_remc_run calls.
+extern "C" goac_status goac_mc_autotune(goac_problem* p, const int8_t* species_dev, int32_t C, const double* kT_dev,
+                                        int64_t probe_steps, int32_t precision, int32_t* W_out, int32_t* cpc_out,
+                                        double* ms_out)
+{
+    if (!p || !species_dev || !kT_dev || C <= 0 || C > GOAC_MAX_BATCH || probe_steps <= 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_autotune: bad argument");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_F32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_autotune: precision must be F64 or F32");
+    if (p->nmovable == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_autotune: no class has two positions");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    cudaStream_t st = p->ctx->stream;
+    const size_t sp_bytes = ((size_t)C * p->Nv + 255) & ~(size_t)255;
+    DevBuf scratch;
+    goac_status rc = goac::ensure(scratch, sp_bytes + 2 * sizeof(double) * (size_t)C + 256);
+    if (rc) return rc;
+    int8_t* sp = (int8_t*)scratch.ptr;
+    double* E = (double*)((char*)scratch.ptr + sp_bytes);
+    double* bE = E + C;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int bestW = 0, bestc = 0;
+    float best_t = 0.0f;
+    const int Ws[3] = {1, 2, 4}, cpcs[5] = {1, 2, 4, 8, 15};
+    const size_t slot = warp_slot_bytes(p->Nv, precision == GOAC_PREC_F32 ? 4 : 8);
+    for (int wi = 0; wi < 3 && !rc; ++wi) {
+        for (int ci = 0; ci < 5 && !rc; ++ci) {
+            const int W = Ws[wi], cpc = cpcs[ci];
+            if (slot * cpc > kSmemBudget || 32 * W * cpc > 1024 || (cpc > C && cpc != 1)) continue;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {
+                const cudaError_t e = cudaMemcpyAsync(sp, species_dev, (size_t)C * p->Nv, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) {
+                    rc = goac::cuda_fail(e, "goac_mc_autotune: copy");
+                    break;
+                }
+                if (rep == 1) cudaEventRecord(a, st);
+                rc = mc_run_impl(p, sp, C, kT_dev, nullptr, 0, probe_steps, 12345u, 0, precision, E, bE, nullptr,
+                                 nullptr, W, cpc);
+                if (!rc && rep == 1) cudaEventRecord(b, st);
+            }
+            if (rc) break;
+            cudaEventSynchronize(b);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (bestW == 0 || ms < best_t) {
+                bestW = W;
+                bestc = cpc;
+                best_t = ms;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(st);
+    cudaFree(scratch.ptr);
+    if (rc) return rc;
+    if (bestW == 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_autotune: no launch shape fits");
+    int* tuned = p->mc_tuned[precision == GOAC_PREC_F32 ? 1 : 0];
+    tuned[0] = bestW;
+    tuned[1] = bestc;
+    if (W_out) *W_out = bestW;
+    if (cpc_out) *cpc_out = bestc;
+    if (ms_out) *ms_out = best_t;
+    return GOAC_OK;
 }
 
 namespace {

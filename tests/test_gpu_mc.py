@@ -63,6 +63,29 @@ def test_mc_ragged_steps_and_resume(ctx):
     assert np.array_equal(a.cpu().numpy(), ref["species"])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mc_autotune_keeps_trajectories(ctx, prec):
+    """The autotuned launch shape (warps per chain, chains per CTA) changes no
+    trajectory: the same chains as with the size-based shape, and in FP64 the
+    oracle's."""
+    prob = synth.layered_problem(reps=(3, 3, 1))
+    Jg, Jo = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    start = synth.random_population(prob, 40, 12)
+    before = torch.tensor(start, device="cuda")
+    out0 = gp.mc_run(before, 0.1, 3000, 5, precision=prec)
+    W, cpc, ms = gp.mc_autotune(torch.tensor(start, device="cuda"), 0.1, 200, prec)
+    assert W in (1, 2, 4) and cpc in (1, 2, 4, 8, 15) and ms > 0
+    after = torch.tensor(start, device="cuda")
+    out1 = gp.mc_run(after, 0.1, 3000, 5, precision=prec)
+    assert torch.equal(before, after)
+    assert torch.equal(out0["n_accept"], out1["n_accept"])
+    assert torch.equal(out0["E"], out1["E"])
+    if prec == "f64":
+        ref = oracle.mc_run(Jo, prob.site_class, prob.fixed_q, prob.z, start, 0.1, 3000, 5)
+        assert np.array_equal(after.cpu().numpy(), ref["species"])
+
+
 def test_mc_zero_steps_and_zero_temperature(ctx):
     prob = synth.tiny_rocksalt_problem()
     Jg, Jo = build_pair(ctx, prob)
