@@ -247,6 +247,21 @@ def test_score_exact_full_size_matches_fp64_path(ctx):
     assert ((Eex - E64).abs() / E64.abs()).max().item() <= 1e-11
 
 
+@pytest.mark.parametrize("form", ["bf16x2", "f64"])
+def test_score_host_matches_device_path(ctx, form):
+    """The blocking host entry point with 3,000 configurations: the same
+    energies as the device entry point, bit for bit, from pinned and from
+    pageable host memory."""
+    prob = synth.layered_problem(reps=(3, 3, 1))
+    Jg, _ = build_pair(ctx, prob)
+    gp = gpu_problem(ctx, prob, Jg)
+    pop = synth.random_population(prob, 3000, 55)
+    Ed = gp.score(torch.tensor(pop, device="cuda"), form).cpu().numpy()
+    assert np.array_equal(gp.score_host(pop, form), Ed)
+    pinned = torch.tensor(pop).pin_memory()
+    assert np.array_equal(gp.score_host(pinned, form).numpy(), Ed)
+
+
 def test_score_host_async_pipeline(ctx):
     """Pipelined host-buffer scoring: a stream of populations of different sizes
     (the staging slots grow mid-stream) gives, after one synchronisation, the
