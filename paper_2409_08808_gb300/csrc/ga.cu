@@ -134,11 +134,6 @@ struct GaArgs {
     int R, P, Nv, S, n_elite, ncls, nmovable, only_movable;   // R populations of P
 };
 
-__device__ __forceinline__ uint32_t word_of(const uint4& v, int i)
-{
-    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
-
 __device__ __forceinline__ int lower_bound_gt(const unsigned long long* pre, int P, unsigned long long t)
 {
     int lo = 0, hi = P - 1;
@@ -228,34 +223,54 @@ __global__ void k_ga_children(GaArgs a)
     // its candidate bit.
     uint32_t kc = 0;
     int nsw = 0;
-    uint4 blk = make_uint4(0, 0, 0, 0);    // this lane's Philox block of the current batch of 128 candidates
+    // Philox cache: lane t holds block (cache_lo >> 2) + t, so the warp holds draws [cache_lo, cache_hi)
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    uint32_t cache_lo = 0u, cache_hi = 0u;
     for (int i0 = 0; i0 < Nv; i0 += 32) {
         const int il = i0 + lane;
         // per lane: B's species, the child's species and the class position (8 + 8 + 16 bits),
         // and the class's position range (16 + 16 bits), so a candidate takes two shuffles
         uint32_t my_bcr = 0u, my_rng = 0u;
+        bool bad = false;
         if (il < Nv) {
             const int k = a.vclass[il];
-            my_bcr = (uint32_t)(uint8_t)pb[il] | ((uint32_t)(uint8_t)ch[il] << 8) | ((uint32_t)a.cls_rank[il] << 16);
+            const int sb = pb[il], sc = ch[il];
+            bad = (unsigned)sb >= (unsigned)a.S || (unsigned)sc >= (unsigned)a.S;
+            my_bcr = (uint32_t)(uint8_t)sb | ((uint32_t)(uint8_t)sc << 8) | ((uint32_t)a.cls_rank[il] << 16);
             my_rng = (uint32_t)a.cls_start[k] | ((uint32_t)a.cls_start[k + 1] << 16);
+        }
+        if (__any_sync(0xffffffffu, bad)) {         // not a species of the problem
+            if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
+            return;
         }
         uint32_t m = __ballot_sync(0xffffffffu, il < Nv && ((my_bcr ^ (my_bcr >> 8)) & 0xffu) != 0u);
         while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1u;
+            // A candidate that is not taken changes nothing, and its draw is known in advance:
+            // the remaining candidate of rank t (set bits of m in site order) uses draw kc + t,
+            // so the warp finds the first taken one at once and only that one needs its partner.
+            if (kc + 32u > cache_hi) {
+                cache_lo = kc & ~3u;
+                cache_hi = cache_lo + 128u;
+                blk = goacd::philox(make_uint4((cache_lo >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
+            }
+            const uint32_t d = kc + (uint32_t)__popc(m & ((1u << lane) - 1u));
+            const int src = (int)((d >> 2) - (cache_lo >> 2)) & 31;
+            const uint32_t x0 = __shfl_sync(0xffffffffu, blk.x, src), x1 = __shfl_sync(0xffffffffu, blk.y, src);
+            const uint32_t x2 = __shfl_sync(0xffffffffu, blk.z, src), x3 = __shfl_sync(0xffffffffu, blk.w, src);
+            const uint32_t dq = d & 3u;
+            const uint32_t wv = dq == 0u ? x0 : dq == 1u ? x1 : dq == 2u ? x2 : x3;
+            const uint32_t tm = __ballot_sync(0xffffffffu, ((m >> lane) & 1u) != 0u && wv < 0x80000000u);
+            if (tm == 0u) {                                // no further swap in this chunk
+                kc += (uint32_t)__popc(m);
+                break;
+            }
+            const int l = __ffs(tm) - 1;
+            kc += (uint32_t)__popc(m & ((1u << l) - 1u)) + 1u;
+            m &= l == 31 ? 0u : (~0u << (l + 1));
             const int ii = i0 + l;
-            // candidate kc uses word kc & 3 of Philox block kc >> 2 (ctr {kc >> 2, gen, c, 3});
-            // the warp draws 32 consecutive blocks at a time, lane t holding block 32 q + t
-            if ((kc & 127u) == 0u) blk = goacd::philox(make_uint4((kc >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
-            const uint32_t wv = __shfl_sync(0xffffffffu, word_of(blk, (int)(kc & 3u)), (int)((kc >> 2) & 31u));
-            ++kc;
             const uint32_t bcr = __shfl_sync(0xffffffffu, my_bcr, l), rng = __shfl_sync(0xffffffffu, my_rng, l);
             const int want = (int8_t)(bcr & 0xffu), old = (int8_t)((bcr >> 8) & 0xffu), pi = (int)(bcr >> 16);
             const int cs = (int)(rng & 0xffffu), ce = (int)(rng >> 16);
-            if ((unsigned)want >= (unsigned)a.S) {      // not a species of the problem
-                if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
-                return;
-            }
             const int wlo = cs >> 5, whi = (ce - 1) >> 5;
             const uint32_t* mw = mis + want * W;
             int pp = -1;
@@ -279,24 +294,22 @@ __global__ void k_ga_children(GaArgs a)
                 if (lane == 0) goacd::report(a.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
                 return;
             }
-            if (wv < 0x80000000u) {
-                const int j = cpos[pp];
-                const int jl = j - i0;                      // j != ii; in this chunk iff 0 <= jl < 32
-                const int pbj = pb[j];
-                if (lane == l) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)want << 8);
-                if (lane == jl) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)old << 8);
-                if (jl > l && jl < 32) m = old != pbj ? (m | (1u << jl)) : (m & ~(1u << jl));
-                __syncwarp();                               // every lane has read mis for this candidate
-                if (lane == 0) {                            // three updates of different bits
-                    ch[j] = (int8_t)old;
-                    ch[ii] = (int8_t)want;
-                    atomicAnd(&mis[old * W + (pi >> 5)], ~(1u << (pi & 31)));     // i now equals B_i
-                    atomicAnd(&mis[want * W + (pp >> 5)], ~(1u << (pp & 31)));    // j no longer holds B_i
-                    if (pbj != old) atomicOr(&mis[old * W + (pp >> 5)], 1u << (pp & 31));
-                }
-                __syncwarp();
-                ++nsw;
+            const int j = cpos[pp];
+            const int jl = j - i0;                      // j != ii; in this chunk iff 0 <= jl < 32
+            const int pbj = pb[j];
+            if (lane == l) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)want << 8);
+            if (lane == jl) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)old << 8);
+            if (jl > l && jl < 32) m = old != pbj ? (m | (1u << jl)) : (m & ~(1u << jl));
+            __syncwarp();                               // every lane has read mis for this candidate
+            if (lane == 0) {                            // three updates of different bits
+                ch[j] = (int8_t)old;
+                ch[ii] = (int8_t)want;
+                atomicAnd(&mis[old * W + (pi >> 5)], ~(1u << (pi & 31)));     // i now equals B_i
+                atomicAnd(&mis[want * W + (pp >> 5)], ~(1u << (pp & 31)));    // j no longer holds B_i
+                if (pbj != old) atomicOr(&mis[old * W + (pp >> 5)], 1u << (pp & 31));
             }
+            __syncwarp();
+            ++nsw;
         }
     }
     const uint4 y = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 4u), k0, k1);
