@@ -1,22 +1,29 @@
 // Genetic algorithm (SI, Genetic Algorithm: roulette-wheel selection,
 // crossover by random atom swaps that take half of the differences between
 // the parents, random mutation, elitism), one generation per call and a
-// driver that rescores every child between generations.
+// driver that rescores every child between generations, for R independent
+// populations of P at once (population r: rows r P .., Philox key seed + r).
 //
-// Device layout:
-//   k_ga_minmax   one block: E_min, E_max of the population.
-//   k_ga_fitness  F_b = floor((Emax - E_b)/(Emax - Emin) 2^24) and its running
-//                 sum as exact 64-bit integers (one block, ordered scan), so
-//                 roulette selection is an exact integer search.
-//   k_ga_rank     ranks by (E, index) to pick the elite (O(P^2) comparisons,
-//                 one warp per individual).
+// Device layout (one block or warp range per population where it says so):
+//   k_ga_minmax   one block per population: E_min, E_max.
+//   k_ga_fitness  one block per population: F_b = floor((Emax - E_b)/(Emax -
+//                 Emin) 2^24) and its running sum as exact 64-bit integers
+//                 (ordered scan), so roulette selection is an exact integer
+//                 search.
+//   k_ga_rank     ranks by (E, index) within the population to pick the elite
+//                 (O(P^2) comparisons, one warp per individual).
 //   k_ga_children one warp per child: parents by binary search of the running
-//                 sum, crossover in shared memory (the warp scans 32 sites at a
-//                 time with ballots; the partner site j of a candidate swap is
-//                 the lowest position of the class with child_j == B_i and
-//                 B_j != B_i, kept per species as a bitmask over class
-//                 positions and found by one ballot over 32 words), Philox
-//                 draws per candidate, mutation, write-back.
+//                 sum, crossover in shared memory (32 sites at a time, the
+//                 chunk's child values and candidate mask in registers; the
+//                 draws of all remaining candidates of a chunk evaluated at
+//                 once, so only taken swaps are processed one by one; the
+//                 partner site j of a taken swap is the lowest position of the
+//                 class with child_j == B_i and B_j != B_i, kept per species as
+//                 a bitmask over class positions and found by one ballot over
+//                 32 words), mutation, write-back.
+//   k_ga_incr     incremental FP64 rescoring, one block per child: the
+//                 potential and energy from the nearer parent's potential and
+//                 the J rows of the sites where the child differs from it.
 #include <utility>
 
 #include "common.cuh"
