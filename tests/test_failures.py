@@ -30,6 +30,9 @@ def test_null_arguments_are_rejected_on_the_host():
     assert L.goac_round_to_counts(None, None, 1, None) == -1
     assert L.goac_score_f64_noalloc(None, 64, 10, None, 1, None, None, 0.0, None, None) == -1
     assert b"NULL" in L.goac_last_error()
+    assert L.goac_ga_run_populations(None, None, None, 2, 8, 1, 0, 0, 0, 0, 0) == -1
+    assert L.goac_mc_autotune(None, None, 4, None, 16, 0, None, None, None) == -1
+    assert L.goac_topk_rescore(None, None, 8, None, 4, None, None) == -1
 
 
 def test_empty_and_oversized_batches_on_the_host():
