@@ -26,10 +26,15 @@ PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5, "e
 
 
 class GoacError(RuntimeError):
-    def __init__(self, status: int, where: str):
-        msg = lib.goac_last_error().decode(errors="replace")
+    def __init__(self, status: int, where: str, msg: str | None = None):
+        if msg is None:
+            msg = lib.goac_last_error().decode(errors="replace")
         super().__init__(f"{where}: status {status}: {msg}")
         self.status = status
+
+
+#: status of a call on a closed context or problem (GOAC_ERR_INVALID_ARG)
+_ERR_INVALID_ARG = -1
 
 
 def _check(rc: int, where: str):
@@ -75,10 +80,20 @@ class Context:
         self.sync_stream()
         return self._h
 
+    @property
+    def closed(self) -> bool:
+        return not getattr(self, "_h", None)
+
+    def _live(self, where: str):
+        if self.closed:
+            raise GoacError(_ERR_INVALID_ARG, where, "the context is closed")
+        return self._h
+
     def sync_stream(self):
         """Point the context at torch's current stream of its device."""
+        h = self._live("goac_ctx_set_stream")
         stream = torch.cuda.current_stream(self.device).cuda_stream
-        _check(lib.goac_ctx_set_stream(self._h, C.c_void_p(stream)), "goac_ctx_set_stream")
+        _check(lib.goac_ctx_set_stream(h, C.c_void_p(stream)), "goac_ctx_set_stream")
 
     def synchronize(self):
         _check(lib.goac_ctx_synchronize(self.handle), "goac_ctx_synchronize")
@@ -87,34 +102,44 @@ class Context:
     KERNELS = {"score_tc": 0, "score_cc": 1, "mc": 2, "ga": 3, "ewald_real": 4, "ewald_syrk": 5, "ga_incr": 6}
 
     def set_timing(self, enable: bool):
-        _check(lib.goac_ctx_set_timing(self._h, int(bool(enable))), "goac_ctx_set_timing")
+        _check(lib.goac_ctx_set_timing(self._live("goac_ctx_set_timing"), int(bool(enable))), "goac_ctx_set_timing")
 
     def kernel_time(self, kernel: str):
         """(total ms, launches) of a timed kernel family since the last query."""
         ms = C.c_double()
         n = C.c_int64()
-        _check(lib.goac_ctx_kernel_time(self._h, self.KERNELS[kernel], C.byref(ms), C.byref(n)),
-               "goac_ctx_kernel_time")
+        _check(lib.goac_ctx_kernel_time(self._live("goac_ctx_kernel_time"), self.KERNELS[kernel], C.byref(ms),
+                                        C.byref(n)), "goac_ctx_kernel_time")
         return float(ms.value), int(n.value)
 
-
-def launch_count() -> int:
-    """Kernels launched by libgoac in this process so far."""
-    return int(lib.goac_launch_count())
-
     def close(self):
-        """Destroy the context after every problem created on it."""
-        if getattr(self, "_h", None):
-            for p in list(getattr(self, "_problems", ())):
-                p.close()
-            lib.goac_ctx_destroy(self._h)
-            self._h = None
+        """Destroy every problem created on this context, then the context
+        (goac_problem_destroy, goac_ctx_destroy); their device memory is
+        freed.  Closing twice is a no-op; any later use raises GoacError."""
+        if self.closed:
+            return
+        for p in list(getattr(self, "_problems", ())):
+            p.close()
+        h, self._h = self._h, None
+        _live_contexts.discard(self)
+        _check(lib.goac_ctx_destroy(h), "goac_ctx_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels launched by libgoac in this process so far."""
+    return int(lib.goac_launch_count())
 
 
 _live_contexts = weakref.WeakSet()
@@ -167,6 +192,8 @@ class Problem:
 
     @property
     def handle(self):
+        if not getattr(self, "_h", None):
+            raise GoacError(_ERR_INVALID_ARG, "goac_problem", "the problem is closed")
         self.ctx.sync_stream()
         return self._h
 
@@ -176,10 +203,16 @@ class Problem:
         return out
 
     def close(self):
-        if getattr(self, "_h", None):
-            if getattr(self.ctx, "_h", None):
-                lib.goac_problem_destroy(self._h)
-            self._h = None
+        """Free the problem's device memory (goac_problem_destroy).  A problem
+        whose context was closed first was already destroyed with it."""
+        h = getattr(self, "_h", None)
+        if not h:
+            return
+        self._h = None
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and not ctx.closed:
+            ctx._problems.discard(self)
+            _check(lib.goac_problem_destroy(h), "goac_problem_destroy")
 
     def __del__(self):
         try:
@@ -386,7 +419,7 @@ def batch_mc_run(ctx: Context, problems, species, kT, n_steps: int, seed: int, s
     dev = f"cuda:{ctx.device}"
     E = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in species]
     bE = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in species]
-    P = (C.c_void_p * n)(*[p._h.value for p in problems])
+    P = (C.c_void_p * n)(*[p.handle.value for p in problems])
     SP = (C.c_void_p * n)(*[s.data_ptr() for s in species])
     CH = (C.c_int32 * n)(*[s.shape[0] for s in species])
     KT = (C.c_void_p * n)(*[t.data_ptr() for t in kT])
@@ -400,7 +433,7 @@ def batch_mc_run(ctx: Context, problems, species, kT, n_steps: int, seed: int, s
 def batch_mc_autotune(ctx: Context, problems, species, kT, probe_steps: int = 256, precision="f64"):
     """Fastest chains-per-CTA for batch_mc_run on these problems (goac_batch_mc_autotune)."""
     n = len(problems)
-    P = (C.c_void_p * n)(*[p._h.value for p in problems])
+    P = (C.c_void_p * n)(*[p.handle.value for p in problems])
     SP = (C.c_void_p * n)(*[s.data_ptr() for s in species])
     CH = (C.c_int32 * n)(*[s.shape[0] for s in species])
     KT = (C.c_void_p * n)(*[t.data_ptr() for t in kT])

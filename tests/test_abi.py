@@ -44,3 +44,39 @@ def test_oracle_shares_no_code_with_the_library():
     assert "import paper_2409_08808_gb300" not in src and "from paper_2409_08808_gb300" not in src
     assert "#include" not in src.replace("#include <math.h>", "").replace("#include <stdint.h>", "").replace(
         "#include <stdlib.h>", "").replace("#include <string.h>", "")
+
+
+def test_binding_context_and_problem_lifetime_methods():
+    """Context and Problem expose close() as methods of the class (a context's
+    close destroys its problems first, then the context), and using a closed
+    context or problem raises GoacError instead of passing a stale handle."""
+    import __graft_entry__
+    __graft_entry__.build_library_only()
+    import paper_2409_08808_gb300 as g
+    for cls in (g.Context, g.Problem):
+        assert callable(getattr(cls, "close", None)), cls
+        assert callable(getattr(cls, "__del__", None)), cls
+    assert isinstance(g.Context.__dict__["closed"], property)
+    assert not hasattr(g.launch_count, "close")
+    # a context object whose handle is gone behaves as closed (no device needed)
+    c = g.Context.__new__(g.Context)
+    c._h = None
+    c._problems = set()
+    assert c.closed
+    c.close()                       # closing a closed context is a no-op
+    try:
+        c.sync_stream()
+    except g.GoacError as e:
+        assert e.status == -1 and "closed" in str(e)
+    else:
+        raise AssertionError("a closed context was used")
+    p = g.Problem.__new__(g.Problem)
+    p._h = None
+    p.ctx = c
+    p.close()
+    try:
+        p.handle
+    except g.GoacError as e:
+        assert "closed" in str(e)
+    else:
+        raise AssertionError("a closed problem was used")

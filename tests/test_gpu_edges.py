@@ -301,3 +301,48 @@ def test_topk_radix_select(ctx, B, k):
     Eo_by = dict(zip(np.sort(want).tolist(), Eo.tolist()))
     assert np.allclose(E, [Eo_by[i] for i in idx.tolist()], rtol=1e-10)
     assert np.all(np.diff(E) >= 0)
+
+
+def test_context_close_returns_device_memory():
+    """50 contexts, each with a problem that has built its lazily allocated
+    operands (FP64 and BF16x2 scoring, an MC run), are created and closed: the
+    device's free memory returns to its starting level (no handle or buffer
+    leaks), and a closed context or problem raises GoacError when used."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.layered_problem(reps=(2, 2, 1))
+    frac = torch.tensor(prob.frac, device="cuda")
+    pop = torch.tensor(synth.random_population(prob, 64, 3), device="cuda")
+
+    def one_round():
+        c = g.Context(0)
+        J = g.build_ewald(c, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+        p = g.Problem(c, J, prob.site_class, prob.fixed_q, prob.z, prob.counts)
+        E64 = p.score(pop, "f64")
+        Ebf = p.score(pop, "bf16x2")
+        p.mc_run(pop[:8].clone(), 0.1, 64, 1)
+        c.synchronize()
+        out = (E64.cpu(), Ebf.cpu())
+        c.close()
+        del J, E64, Ebf
+        return c, p, out
+
+    one_round()                     # module loading and torch's own caches first
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    first = None
+    for _ in range(50):
+        c, p, out = one_round()
+        if first is None:
+            first = out
+        assert torch.equal(out[0], first[0]) and torch.equal(out[1], first[1])
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 <= 4 << 20, (free0, free1)
+    assert c.closed
+    with pytest.raises(g.GoacError):
+        c.synchronize()
+    with pytest.raises(g.GoacError):
+        p.score(pop, "f64")
+    c.close()                       # a second close is a no-op

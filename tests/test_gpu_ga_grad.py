@@ -155,7 +155,6 @@ def test_ga_layered_full_size(ctx):
     """Layered 12x12x1 cell, N = 1296, population 1024: counts preserved,
     elitism keeps the best energy non-increasing, FP64 and split scoring."""
     prob = synth.layered_problem()
-    Jg, Jo = build_pair(ctx, prob) if False else (None, None)
     import paper_2409_08808_gb300 as g
     frac = torch.tensor(prob.frac, device="cuda")
     Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
@@ -173,6 +172,11 @@ def test_ga_layered_full_size(ctx):
     assert torch.allclose(E, E64, rtol=0, atol=0)
     assert (E32 - E64).abs().max().item() < 1e-3 * E64.abs().max().item()
     assert (Ebf - E64).abs().max().item() < 1e-4 * E64.abs().max().item()
+    # the oracle's q^T J q on the GPU-built J for elites, the middle and the last children
+    fin = pop.cpu().numpy()
+    rows = np.array([0, 1, 19, 20, 511, 1022, 1023])
+    Eo = oracle.score(Jg.cpu().numpy(), prob.site_class, prob.fixed_q, prob.z, fin[rows])
+    assert np.max(np.abs(E.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
 
 
 @pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5)])
