@@ -171,7 +171,7 @@ def layered_problem(reps=(12, 12, 1), a_h=2.88, c=14.2, z_o=0.25):
     a3 = np.array([0.0, 0.0, c * reps[2]])
     lattice = np.stack([a1, a2, a3])
     alpha, nimg, kcut = default_cutoffs(lattice)
-    return Problem(name="layered12x12x1", lattice=lattice, frac=frac, site_class=site_class, fixed_q=fixed_q,
+    return Problem(name=f"layered{reps[0]}x{reps[1]}x{reps[2]}", lattice=lattice, frac=frac, site_class=site_class, fixed_q=fixed_q,
                    z=z, counts=counts, alpha=alpha, nimg=nimg, kcut=kcut, species_names=names)
 
 

@@ -87,6 +87,9 @@ def _declare(lib):
         "orc_sa_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _p, _i64, _i64, _u64, _u64, _p, _p, _p, _p]),
         "orc_remc_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _i64, _i64, _u64, _p, _p, _p]),
         "orc_gd_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _p]),
+        "orc_gd_run_literal": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _p]),
+        "orc_mc_run_literal": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _u64, _u64, _p, _p, _p, _p,
+                                         _p]),
         "orc_hybrid_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _i64, _p, _i64, _i64, _i64, _i64, _i64, _u32,
                                      _u64, _p]),
         "orc_ga_generation": (C.c_int, [_i64, _p, _p, _p, _i64, _i64, _u32, _u32, _u64, _p, _p, _p]),
@@ -294,6 +297,30 @@ def mc_run(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0, trace=
     return {"species": sp, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc, "E_trace": tr}
 
 
+def mc_run_literal(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0):
+    """Metropolis swap MC with the paper's rule taken literally (accept iff
+    dE <= 0 or u < exp(-dE/kT), plain phi update): the twin that mc_run is
+    checked against.  Also returns, per chain, the proposals with
+    0 < dE <= 1e-9 eV (n_band) and those within 1e-9 of the exp/log boundary
+    (n_close)."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    Cn = sp.shape[0]
+    kTa = _f64(np.broadcast_to(np.asarray(kT, dtype=np.float64), (Cn,)))
+    E = np.zeros(Cn)
+    bestE = np.zeros(Cn)
+    nacc = np.zeros(Cn, dtype=np.int64)
+    nband = np.zeros(Cn, dtype=np.int64)
+    nclose = np.zeros(Cn, dtype=np.int64)
+    rc = _load().orc_mc_run_literal(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp),
+                                    Cn, _ptr(kTa), nsteps, seed, step0, _ptr(E), _ptr(bestE), _ptr(nacc),
+                                    _ptr(nband), _ptr(nclose))
+    if rc:
+        raise ValueError("no movable class")
+    return {"species": sp, "E": E, "bestE": bestE, "n_accept": nacc, "n_band": nband, "n_close": nclose}
+
+
 def sa_run(J, site_class, fixed_q, z, species, kT0, kT1, total, nsteps, seed, step0=0):
     """Simulated annealing (exponential kT schedule from kT0 to kT1 over `total` steps)."""
     J = _f64(J)
@@ -338,6 +365,20 @@ def gd_run(J, site_class, fixed_q, z, species, max_steps):
     st = np.zeros(Cn, dtype=np.int64)
     _load().orc_gd_run(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), Cn, max_steps,
                        _ptr(E), _ptr(st))
+    return {"species": sp, "E": E, "steps": st}
+
+
+def gd_run_literal(J, site_class, fixed_q, z, species, max_steps):
+    """Steepest descent with the literal rule (strict dE < 0, exact argmin,
+    no tie band): the twin that gd_run is checked against."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    Cn = sp.shape[0]
+    E = np.zeros(Cn)
+    st = np.zeros(Cn, dtype=np.int64)
+    _load().orc_gd_run_literal(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), Cn,
+                               max_steps, _ptr(E), _ptr(st))
     return {"species": sp, "E": E, "steps": st}
 
 

@@ -38,7 +38,13 @@
  *   orc_remc_run           pinned: detailed balance of the exchange (two-level
  *                          chi^2), perm stays a permutation, R = 1 equals MC.
  *   orc_mc_run             pinned: Boltzmann visit frequencies (chi^2) on a
- *                          brute-forced cell; count preservation; E tracking.
+ *                          brute-forced cell; count preservation; E tracking;
+ *                          the same trajectories as orc_mc_run_literal (the
+ *                          paper's rule without the tie band and log form).
+ *   orc_mc_run_literal,
+ *   orc_gd_run_literal     the literal-rule twins: checked against their own
+ *                          definitions by the same properties (Boltzmann
+ *                          visits, local minima by fresh rescoring).
  *   orc_ga_generation      pinned: count preservation, elitism, inheritance
  *                          of common sites, 50 % swap acceptance (statistical).
  *   orc_random_configs     pinned: counts; uniformity (chi^2) on small cells.
@@ -758,6 +764,88 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
 }
 
 /* ------------------------------------------------------------------------ */
+/* The Metropolis rule of SI, Monte Carlo, taken literally: a twin of        */
+/* mc_core that accepts iff dE <= 0, else iff u < exp(-dE/kT) (kT <= 0:      */
+/* dE <= 0 only), and updates phi_w = phi_w + d (J_wa - J_wb) with the       */
+/* product and the sum rounded separately.  Same draws, pair map and no-op   */
+/* rule as mc_core.  It exists to show that mc_core's two readings (|dE| <=  */
+/* 1e-9 eV counted as zero; the event u < exp(-dE/kT) tested as dE < -kT ln u */
+/* with an fma update) take the paper's decisions on the tested workloads.   */
+/* Per-chain diagnostics (each nullable): n_band = proposals with            */
+/* 0 < dE <= 1e-9 eV (accepted outright by mc_core, drawn for here);         */
+/* n_close = proposals with kT > 0 and |dE/kT + ln u| < 1e-9, where the two  */
+/* forms of the Metropolis test could round to different decisions.         */
+/* ------------------------------------------------------------------------ */
+int orc_mc_run_literal(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q,
+                       const double* z, int8_t* species, int64_t C, const double* kT, int64_t nsteps,
+                       uint64_t seed, uint64_t step0, double* E_out, double* bestE, int64_t* n_accept,
+                       int64_t* n_band, int64_t* n_close)
+{
+    classes_t cl = make_classes(site_class, N);
+    int64_t nv = cl.nv;
+    if (cl.nmovable == 0) {
+        free_classes(&cl);
+        return -1;
+    }
+    double* q = (double*)malloc(sizeof(double) * (size_t)N);
+    double* phi = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    for (int64_t ch = 0; ch < C; ++ch) {
+        int8_t* sp = species + ch * nv;
+        orc_config_charges(N, site_class, fixed_q, z, sp, q);
+        double E = orc_qJq(J, q, N);
+        for (int64_t w = 0; w < nv; ++w) {
+            double acc = 0.0;
+            for (int64_t j = 0; j < N; ++j) acc += J[cl.vsite[w] * N + j] * q[j];
+            phi[w] = acc;
+        }
+        double best = E;
+        int64_t nacc = 0, nband = 0, nclose = 0;
+        for (int64_t s = 0; s < nsteps; ++s) {
+            uint64_t t = step0 + (uint64_t)s;
+            uint32_t x[4];
+            philox_draw(seed, (uint32_t)t, (uint32_t)(t >> 32), (uint32_t)ch, 0u, x);
+            int k = cl.only_movable;
+            if (cl.nmovable != 1) {
+                uint32_t y[4];
+                philox_draw(seed, (uint32_t)t, (uint32_t)(t >> 32), (uint32_t)ch, 1u, y);
+                k = pick_class(&cl, y[0]);
+            }
+            int64_t va, vb;
+            pick_pair(&cl, k, x[0], x[1], &va, &vb);
+            int sa = sp[va], sb = sp[vb];
+            if (sa == sb) continue;
+            int64_t ia = cl.vsite[va], ib = cl.vsite[vb];
+            double d = z[sb] - z[sa];
+            double dE = 2.0 * d * (phi[va] - phi[vb]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
+            double u = ((double)(x[2] >> 5) * 67108864.0 + (double)(x[3] >> 6)) * (1.0 / 9007199254740992.0);
+            if (dE > 0.0 && dE <= 1e-9) nband++;
+            if (kT[ch] > 0.0 && u > 0.0 && fabs(dE / kT[ch] + log(u)) < 1e-9) nclose++;
+            int accept = dE <= 0.0 || (kT[ch] > 0.0 && u < exp(-dE / kT[ch]));
+            if (!accept) continue;
+            sp[va] = (int8_t)sb;
+            sp[vb] = (int8_t)sa;
+            for (int64_t w = 0; w < nv; ++w) {
+                double dj = J[cl.vsite[w] * N + ia] - J[cl.vsite[w] * N + ib];
+                double step = d * dj;
+                phi[w] = phi[w] + step;
+            }
+            E = E + dE;
+            nacc++;
+            if (E < best) best = E;
+        }
+        if (E_out) E_out[ch] = E;
+        if (bestE) bestE[ch] = best;
+        if (n_accept) n_accept[ch] = nacc;
+        if (n_band) n_band[ch] = nband;
+        if (n_close) n_close[ch] = nclose;
+    }
+    free(q);
+    free(phi);
+    free_classes(&cl);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Genetic algorithm, one generation (SI, Genetic Algorithm; roulette wheel */
 /* selection).  Population P x Nv with energies E.                          */
 /*  1. Elitism: children 0..n_elite-1 are the n_elite lowest-E individuals, */
@@ -1343,6 +1431,70 @@ int orc_gd_run(const double* J, int64_t N, const int32_t* site_class, const doub
             steps++;
         }
     done:
+        if (E_out) E_out[ch] = E;
+        if (steps_out) steps_out[ch] = steps;
+    }
+    free(q);
+    free(phi);
+    free_classes(&cl);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient descent with the SI, Gradient Descent rule taken literally: a     */
+/* twin of orc_gd_run without the 1e-9 eV band.  Each step takes the lowest   */
+/* dE over all same-class pairs a < b of different species; if it is < 0 the */
+/* first pair (lexicographic) whose dE equals it exactly is swapped, else the */
+/* configuration is a local minimum.  Used to show that the band of           */
+/* orc_gd_run (ties within rounding resolved by index) changes no end state   */
+/* of consequence on brute-forced cells.                                      */
+/* ------------------------------------------------------------------------ */
+int orc_gd_run_literal(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q,
+                       const double* z, int8_t* species, int64_t C, int64_t max_steps, double* E_out,
+                       int64_t* steps_out)
+{
+    classes_t cl = make_classes(site_class, N);
+    int64_t nv = cl.nv;
+    double* q = (double*)malloc(sizeof(double) * (size_t)N);
+    double* phi = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    for (int64_t ch = 0; ch < C; ++ch) {
+        int8_t* sp = species + ch * nv;
+        orc_config_charges(N, site_class, fixed_q, z, sp, q);
+        double E = orc_qJq(J, q, N);
+        for (int64_t w = 0; w < nv; ++w) {
+            double acc = 0.0;
+            for (int64_t j = 0; j < N; ++j) acc += J[cl.vsite[w] * N + j] * q[j];
+            phi[w] = acc;
+        }
+        int64_t steps = 0;
+        for (; steps < max_steps; ++steps) {
+            double dmin = 0.0;
+            int64_t ba = -1, bb = -1;
+            for (int64_t a = 0; a < nv; ++a)
+                for (int64_t b = a + 1; b < nv; ++b) {
+                    if (cl.vclass[a] != cl.vclass[b] || sp[a] == sp[b]) continue;
+                    int64_t ia = cl.vsite[a], ib = cl.vsite[b];
+                    double d = z[sp[b]] - z[sp[a]];
+                    double dE = 2.0 * d * (phi[a] - phi[b]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
+                    if (dE < dmin) {
+                        dmin = dE;
+                        ba = a;
+                        bb = b;
+                    }
+                }
+            if (ba < 0) break;
+            int64_t ia = cl.vsite[ba], ib = cl.vsite[bb];
+            int sa = sp[ba], sb = sp[bb];
+            double d = z[sb] - z[sa];
+            sp[ba] = (int8_t)sb;
+            sp[bb] = (int8_t)sa;
+            for (int64_t w = 0; w < nv; ++w) {
+                double dj = J[cl.vsite[w] * N + ia] - J[cl.vsite[w] * N + ib];
+                double step = d * dj;
+                phi[w] = phi[w] + step;
+            }
+            E = E + dmin;
+        }
         if (E_out) E_out[ch] = E;
         if (steps_out) steps_out[ch] = steps;
     }
