@@ -857,11 +857,7 @@ def run_paper(args):
                 "methods": res, "best_E_per_ion_eV": best[0] / prob.N}
         print(json.dumps(line), flush=True)
     # NaCl 3x3x3: 216 positions, 108 Na+ / 108 Cl- on one class; optimum = rocksalt order
-    lattice, frac, _ = synth.rocksalt_cell((3, 3, 3), 5.62)
-    L = 3 * 5.62
-    prob = synth.Problem(name="NaCl3x3x3", lattice=lattice, frac=frac, site_class=np.zeros(216, np.int32),
-                         fixed_q=np.zeros(216), z=np.array([1.0, -1.0]), counts=np.array([[108, 108]], np.int32),
-                         alpha=5.0 / L, nimg=(2, 2, 2), kcut=8 * 2 * math.pi / L)
+    prob, _ = synth.nacl_problem((3, 3, 3), 5.62)
     res, best = methods(prob, args.paper_chains, args.paper_steps * 25, 1024, 1000)
     M_ref = 1.747564594633182
     E_opt = -108 * M_ref * 14.3996454784 / 2.81

@@ -397,3 +397,19 @@ def o3_layered_problem(reps=(2, 2, 1), a_sqrt3=5.0, c=19.2, z_o=0.25):
 
 #: the eight sqrt(3)-supercells of Table 1
 TABLE1_CELLS = [(2, 2, 1), (2, 2, 2), (4, 4, 1), (4, 4, 2), (6, 6, 1), (8, 8, 1), (6, 6, 2), (6, 6, 3)]
+
+
+def nacl_problem(reps=(3, 3, 3), a=5.62):
+    """NaCl supercell of the paper's rocksalt study (Section "Atomistic
+    Configurations in NaCl"): every position of the rocksalt lattice in one
+    class, half Na+ and half Cl- (216 positions, 108 / 108 for 3x3x3, about
+    10^64 configurations); the known optimum is rocksalt order, which is
+    returned as `is_anion` (species 1 = Cl- on the anion sublattice)."""
+    lattice, frac, is_anion = rocksalt_cell(reps, a)
+    n = frac.shape[0]
+    L = float(np.cbrt(abs(np.linalg.det(lattice))))
+    prob = Problem(name=f"NaCl{reps[0]}x{reps[1]}x{reps[2]}", lattice=lattice, frac=frac,
+                   site_class=np.zeros(n, np.int32), fixed_q=np.zeros(n), z=np.array([1.0, -1.0]),
+                   counts=np.array([[n // 2, n // 2]], np.int32), alpha=5.0 / L, nimg=(2, 2, 2),
+                   kcut=8 * 2 * math.pi / L, species_names=["Na+", "Cl-"])
+    return prob, np.asarray(is_anion, dtype=np.int8)

@@ -250,6 +250,14 @@ goac_status goac_mc_autotune(goac_problem* prob, const int8_t* species_dev, int3
                              int64_t probe_steps, int32_t precision, int32_t* W_out, int32_t* cpc_out,
                              double* ms_out);
 
+/* Set the launch shape that goac_mc_autotune would choose (no counterpart  *
+ * in the paper): W warps per chain (1, 2 or 4) and chains_per_cta (1..32,   *
+ * capped by shared memory and 1,024 threads) for `precision` (F64 or F32);  *
+ * 0 restores the size-based choice for that field.  Host only; later         *
+ * goac_mc_run / goac_sa_run / goac_remc_run calls of the problem use it.    *
+ * The trajectories do not depend on the launch shape.                        */
+goac_status goac_mc_set_shape(goac_problem* prob, int32_t precision, int32_t W, int32_t chains_per_cta);
+
 /* Simulated annealing (SI, Simulated annealing: the MC routine with the     *
  * temperature lowered towards 0 during the run): goac_mc_run with the        *
  * temperature of step t set to kT0 (kT1/kT0)^(t/(total_steps-1)) per chain   *

@@ -301,6 +301,11 @@ class Problem:
                                     C.byref(W), C.byref(c), C.byref(ms)), "goac_mc_autotune")
         return int(W.value), int(c.value), float(ms.value)
 
+    def mc_set_shape(self, W: int = 0, chains_per_cta: int = 0, precision="f64"):
+        """Fix the Monte Carlo launch shape (warps per chain, chains per CTA); 0 = by size."""
+        _check(lib.goac_mc_set_shape(self.handle, _prec(precision), int(W), int(chains_per_cta)),
+               "goac_mc_set_shape")
+
     def gd_run(self, species: torch.Tensor, max_steps: int):
         """Steepest descent over single swaps, in place on `species`.  Returns (E, steps)."""
         B = species.shape[0]

@@ -523,6 +523,22 @@ extern "C" goac_status goac_mc_autotune(goac_problem* p, const int8_t* species_d
     return GOAC_OK;
 }
 
+// Fix the Monte Carlo launch shape of a problem (no counterpart in the paper):
+// what goac_mc_autotune would store, set by the caller; 0 restores the
+// size-based choice.  The trajectories do not depend on it.
+extern "C" goac_status goac_mc_set_shape(goac_problem* p, int32_t precision, int32_t W, int32_t chains_per_cta)
+{
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_set_shape: NULL problem");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_F32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_set_shape: precision must be F64 or F32");
+    if (!(W == 0 || W == 1 || W == 2 || W == 4) || chains_per_cta < 0 || chains_per_cta > 32)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_set_shape: W must be 0, 1, 2 or 4 and chains per CTA 0..32");
+    int* tuned = p->mc_tuned[precision == GOAC_PREC_F32 ? 1 : 0];
+    tuned[0] = W;
+    tuned[1] = chains_per_cta;
+    return GOAC_OK;
+}
+
 namespace {
 
 __global__ void k_remc_init(int G, int R, const double* __restrict__ ladder, double* __restrict__ kT,
