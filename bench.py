@@ -3,13 +3,15 @@
 
 One step = batched scoring E = q^T J q of a population of B = 4096 count-
 preserving configurations of a random cubic cell with N = 4096 sites (16^3
-jittered grid, species +1/+2/+3/-2), in the BF16x3 split form on the tcgen05
-tensor cores.  value = energy evaluations per second over all GPUs.  The same
-run also reports: the plain FP64 GPU path on the same population and the
-speed-up, the energy error of the split form against it, the top-64 FP64
-rescoring, Monte Carlo swap trials/s at N = 4096 (FP64 and FP32 chains), the
-live roofline of the dominant kernel, the end-to-end rate through the host-
-buffer entry point, and the CPU oracle on a bounded sample.
+jittered grid, species +1/+2/+3/-2), in the FP64-grade exact integer-digit form
+on the tcgen05 tensor cores (energies within 1e-10 relative of the FP64
+oracle).  value = energy evaluations per second over all GPUs.  The same run
+also reports: the BF16x2 split form (throughput, roofline, energy error), the
+plain FP64 GPU path on the same population and the speed-ups, the top-64 FP64
+rescoring of the BF16x2 candidates, Monte Carlo swap trials/s at N = 4096 (FP64
+and FP32 chains), the live roofline of the dominant kernel, the end-to-end
+rate through the host-buffer entry point, and the CPU oracle on a bounded
+sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,9 +39,10 @@ sys.path.insert(0, ROOT)
 METRIC = "config energy evals/s and MC swap trials/s at N=4096, % roofline, vs FP64 GPU path"
 N_SIDE = 16          # 16^3 = 4096 sites
 B_POP = 4096
-FORM = "bf16x2"
+FORM = "exact"          # FP64-grade headline form
+SECOND_FORM = "bf16x2"  # reported beside it with its own error and roofline
 E2E_CELLS = 4          # cells scored round robin in the end-to-end leg
-TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2, "exact": 6}   # exact: six BF16 digits
+TERMS = {"bf16x2": 2, "bf16x3": 3, "tf32": 1, "tf32x2": 2}   # exact: digits per problem (exact_info)
 WORKLOAD = ("random cubic cell N=4096 (16^3 grid, spacing 2.5 A, jitter 0.3 A; +1:512 +2:1024 +3:512 -2:2048), "
             "population B=4096 uniformly random count-preserving configurations")
 
@@ -204,20 +207,23 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     cores = _host_cores()
-    work = _OracleWork(11, 64 * cores)
+    work = _OracleWork(11, B_POP)
     t1 = work.time(2 * cores, threads=cores) / (2.0 * cores)
-    per_step = int(max(1, min(64 * cores, 60.0 / (max(1, args.steps + args.warmup) * t1))))
+    # each step scores the GPU arm's whole population (B = 4096) when warm-up + steps fit in
+    # about two and a half minutes, else a contiguous sample of it
+    per_step = int(max(1, min(B_POP, 150.0 / (max(1, args.steps + args.warmup) * t1))))
     for w in range(args.warmup):
         work.time(per_step, w, threads=cores)
     times = [work.time(per_step, k * per_step, threads=cores) for k in range(args.steps)]
     ms = 1e3 * float(np.mean(times))
     value = per_step / (ms / 1e3)
-    sample = (f"{per_step} configurations per step of the N=4096 cell, oracle q^T J q in plain C, {cores} threads; "
-              f"J a seeded symmetric FP64 matrix of the same size")
+    sample = (f"{per_step} of the {B_POP} configurations per step of the N=4096 cell, oracle q^T J q in plain C, "
+              f"{cores} threads; J a seeded symmetric FP64 matrix of the same size")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": 4096, "B": per_step, "form": "f64 oracle (CPU)",
+            "config": {"workload": WORKLOAD, "N": 4096, "B": B_POP, "configs_scored_per_step": per_step,
+                       "same_population_as_gpu_arm": per_step == B_POP, "form": "f64 oracle (CPU)",
                        "parallelism": f"{cores} host threads"},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -267,6 +273,72 @@ def _traffic(form):
     return d.get("dram_bytes_per_launch")
 
 
+def _time_form(gp, pop, form, steps, flush, E):
+    """Per-step CUDA-event times (ms) of `steps` scoring calls, the L2 flushed
+    between steps outside the step events; also the kernels launched."""
+    import torch
+
+    import paper_2409_08808_gb300 as g
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    launches0 = g.launch_count()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record()
+        gp.score(pop, form, out=E)
+        ends[k].record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], g.launch_count() - launches0
+
+
+def _kernel_ms(ctx, gp, pop, form, steps, flush, E):
+    """Average duration of the scoring kernel: the library's CUDA events around
+    each launch, on the stream it is launched on, L2 flushed between steps."""
+    import torch
+    ctx.set_timing(True)
+    ctx.kernel_time("score_tc")
+    for _ in range(steps):
+        flush.zero_()
+        gp.score(pop, form, out=E)
+    torch.cuda.synchronize()
+    kern_ms, kern_n = ctx.kernel_time("score_tc")
+    ctx.set_timing(False)
+    return kern_ms / max(kern_n, 1), kern_n
+
+
+def _roofline(form, terms, kern_ms, kern_n, N, B):
+    ld = ((N + 127) // 128) * 128
+    bpad = ((B + 255) // 256) * 256
+    nbm = ld // 128
+    # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld
+    flops_exec = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * bpad
+    flops_useful = 2.0 * N * N * B
+    bf16_peak, _, peak_kind = _peaks()
+    tf32 = "tf32" in form
+    peak = bf16_peak / 2.0 if tf32 else bf16_peak     # TF32 runs at half the BF16 rate; FP16 = BF16
+    achieved = flops_exec / (kern_ms / 1e3) / 1e12
+    kernel = "k_score_exact" if form == "exact" else f"k_score_tc<{terms},{'true' if tf32 else 'false'}>"
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": _traffic(form), "kernel": kernel, "kernel_ms": kern_ms,
+            "kernel_timing": f"CUDA events around each launch, a second loop of {kern_n} steps (L2 flushed "
+                             f"between steps)",
+            "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
+            "useful_frac": flops_useful / (kern_ms / 1e3) / 1e12 / peak,
+            "peak_kind": f"{peak_kind} bf16_tflops (burst)" + (" x 0.5 nominal tf32/bf16 ratio" if tf32 else
+                                                              (", FP16 runs at the BF16 rate" if form == "exact"
+                                                               else ""))}
+
+
+def _mc_profile(prec):
+    """DRAM bytes and duration of the Monte Carlo kernel from the committed ncu
+    summary (profiles/mc_<prec>_n4096.json) if present, else None."""
+    path = os.path.join(ROOT, "profiles", f"mc_{prec}_n4096.json")
+    if not os.path.exists(path):
+        return None
+    return json.load(open(path))
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -289,67 +361,39 @@ def run_ours(args, world, rank, local):
     pop = torch.tensor(pop_np, device=dev)
     pop_host = torch.tensor(pop_np).pin_memory()
     form = args.form
+    other = SECOND_FORM if form != SECOND_FORM else "exact"
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    info = gp.exact_info()
+    terms = {f: (info[1] if f == "exact" else TERMS[f]) for f in (form, other)}
 
-    # warm-up (also builds the split operand copies)
+    # warm-up (also builds the split operand copies of both forms)
     for _ in range(max(3, args.warmup)):
         gp.score(pop, form)
+        gp.score(pop, other)
     torch.cuda.synchronize()
 
     # timed steps: only the two step events per step (no per-kernel events, which would
     # sit between the chained kernels of a step)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     E = torch.empty(B_POP, dtype=torch.float64, device=dev)
     clocks = ClockSampler(local)
     _barrier(world)
     torch.cuda.synchronize()
     clocks.start()
-    launches0 = g.launch_count()
-    for k in range(args.steps):
-        flush.zero_()                      # L2 flush between steps, outside the step events
-        starts[k].record()
-        gp.score(pop, form, out=E)
-        ends[k].record()
-    torch.cuda.synchronize()
-    launches = g.launch_count() - launches0
+    step_ms, launches = _time_form(gp, pop, form, args.steps, flush, E)
     _barrier(world)
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_local = float(np.mean(step_ms))
-    ms = _max_over_ranks(ms_local, world)
+    ms = _max_over_ranks(float(np.mean(step_ms)), world)
     value = world * B_POP / (ms / 1e3)
 
-    # the dominant kernel's own duration: the same steps again with the library's per-kernel
-    # CUDA events around the scoring kernel (on the stream it is launched on)
-    ctx.set_timing(True)
-    ctx.kernel_time("score_tc")
-    for k in range(min(args.steps, 400)):
-        flush.zero_()
-        gp.score(pop, form, out=E)
-    torch.cuda.synchronize()
-    kern_ms, kern_n = ctx.kernel_time("score_tc")
-    kern_avg_ms = kern_ms / max(kern_n, 1)
-    ctx.set_timing(False)
+    # the dominant kernel's own duration: the same steps again with the library's
+    # per-kernel CUDA events around the scoring kernel
+    kern_ms, kern_n = _kernel_ms(ctx, gp, pop, form, min(args.steps, 400), flush, E)
+    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP)
 
-    # roofline of the dominant kernel (executed tensor FLOPs of the split form)
-    terms = TERMS[form]
-    ld = ((prob.N + 127) // 128) * 128
-    bpad = ((B_POP + 255) // 256) * 256
-    nbm = ld // 128
-    # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld
-    flops_exec = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * bpad
-    flops_useful = 2.0 * prob.N * prob.N * B_POP
-    bf16_peak, hbm_peak, peak_kind = _peaks()
-    peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak     # TF32 runs at half the BF16 rate
-    achieved = flops_exec / (kern_avg_ms / 1e3) / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(form),
-                "kernel": "k_score_exact" if form == "exact" else f"k_score_tc<{terms},{'true' if 'tf32' in form else 'false'}>",
-                "kernel_ms": kern_avg_ms, "kernel_timing": f"CUDA events around each launch, second loop of "
-                                                         f"{kern_n} steps (L2 flushed between steps)",
-                "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
-                "peak_kind": f"{peak_kind} bf16_tflops (burst)" + (" x 0.5 nominal tf32/bf16 ratio" if "tf32" in form else "")}
+    # the other form (BF16x2 beside the FP64-grade headline): same timing, own roofline
+    o_ms, _ = _time_form(gp, pop, other, min(args.steps, 400), flush, E)
+    o_ms = _max_over_ranks(float(np.mean(o_ms)), world)
+    o_kms, o_kn = _kernel_ms(ctx, gp, pop, other, min(args.steps, 400), flush, E)
 
     # End to end through the public host-buffer API: every step copies its
     # population from pinned host memory and its energies back, through the
@@ -381,6 +425,8 @@ def run_ours(args, world, rank, local):
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / n_e2e, world)
     e2e_ok = all(bool(torch.equal(E_hosts[j], cells[j % E2E_CELLS].score(pops_host[j].to(dev), form).cpu()))
                  for j in range(2 * E2E_CELLS))
+    for c in cells[1:]:
+        c.close()
     del cells
     # the blocking entry point (copy, score, copy back, synchronise) for comparison
     E_host = E_hosts[0]
@@ -400,8 +446,9 @@ def run_ours(args, world, rank, local):
            "blocking_api_value": world * B_POP / e2e_block_s,
            "blocking_api_l2": "256 MB flush between steps, outside the host timer"}
 
-    # plain FP64 GPU path on the same population, and the split form's error
+    # plain FP64 GPU path on the same population, and the error of each form against it
     E_form = gp.score(pop, form).clone()
+    E_other = gp.score(pop, other).clone()
     E64 = gp.score(pop, "f64")
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -412,16 +459,19 @@ def run_ours(args, world, rank, local):
     b.record()
     torch.cuda.synchronize()
     f64_ms = a.elapsed_time(b) / reps64
-    err = (E_form - E64).abs()
-    energy_error = {"max_abs_eV": float(err.max()), "rms_abs_eV": float(err.pow(2).mean().sqrt()),
-                    "max_rel": float((err / E64.abs()).max()), "mean_abs_E_eV": float(E64.abs().mean())}
 
-    # top-64 FP64 rescoring of the split form's best candidates
-    idx, Etop = gp.topk_rescore(pop, E_form, 64)
+    def err_vs_fp64(Ef):
+        err = (Ef - E64).abs()
+        return {"max_abs_eV": float(err.max()), "rms_abs_eV": float(err.pow(2).mean().sqrt()),
+                "max_rel": float((err / E64.abs()).max()), "mean_abs_E_eV": float(E64.abs().mean())}
+
+    # top-64 FP64 rescoring of the BF16x2 form's best candidates
+    E_bf = E_form if form == SECOND_FORM else E_other
+    idx, Etop = gp.topk_rescore(pop, E_bf, 64)
     torch.cuda.synchronize()
     a.record()
     for _ in range(3):
-        gp.topk_rescore(pop, E_form, 64)
+        gp.topk_rescore(pop, E_bf, 64)
     b.record()
     torch.cuda.synchronize()
     topk_ms = a.elapsed_time(b) / 3
@@ -452,16 +502,27 @@ def run_ours(args, world, rank, local):
         bytes_alg = trials * 32 + acc * trials * 2 * prob.N * rb
         mc[prec] = {"trials_per_s": world * trials / (_max_over_ranks(mms, world) / 1e3), "chains": Cn,
                     "steps_per_chain": args.mc_steps, "kT_eV": 0.05, "acceptance": acc, "ms": mms,
-                    "autotuned_warps_per_chain": W_t, "autotuned_chains_per_cta": cpc_t,
-                    "hbm_gbs_algorithmic": bytes_alg / (mc_kms / 1e3) / 1e9,
-                    "hbm_frac": bytes_alg / (mc_kms / 1e3) / 1e9 / hbm_peak}
+                    "kernel_ms": mc_kms, "autotuned_warps_per_chain": W_t, "autotuned_chains_per_cta": cpc_t,
+                    "algorithmic_gbs": bytes_alg / (mc_kms / 1e3) / 1e9,
+                    "algorithmic_bytes_served_by": (f"mostly L2: the J rows of accepted swaps "
+                                                    f"({prob.N * prob.N * rb / 1e6:.0f} MB of J in "
+                                                    f"{'FP64' if rb == 8 else 'FP32'}) hit in the 129 MB L2, "
+                                                    f"so this rate is not an HBM rate")}
+        prof = _mc_profile(prec)
+        if prof:
+            mc[prec]["ncu_dram"] = {"bytes_per_launch": prof["dram_bytes_per_launch"],
+                                    "gbs": prof["dram_bytes_per_launch"] / (prof["gpu_time_us_ncu"] * 1e-6) / 1e9,
+                                    "workload": prof["workload"], "source": prof["source"]}
         if prec == "f64":
             # the FP64 chain is bound by the FP64 pipe: per accepted swap one subtract and one FMA
             # per site (the potential update); peak = 152 SMs x 2 FP64 FMA/clk x 2.07 GHz
             # (6.29e11 instr/s, the rate the FP64 SYRK reaches at 99 % FP64-pipe activity)
             fp64_instr = acc * trials * 2.0 * prob.N
+            mc[prec]["bound"] = "fp64 pipe"
             mc[prec]["fp64_instr_per_s_update"] = fp64_instr / (mc_kms / 1e3)
             mc[prec]["fp64_pipe_frac_update"] = fp64_instr / (mc_kms / 1e3) / (152 * 2 * 2.07e9)
+        else:
+            mc[prec]["bound"] = "L2 / load latency (J rows of accepted swaps)"
 
     cpu = None
     if rank == 0:
@@ -477,20 +538,30 @@ def run_ours(args, world, rank, local):
                "single_thread": {"value": n1 / dt1, "cores": 1, "sample": f"{n1} configurations ({dt1:.1f} s)"}}
 
     if rank == 0:
+        if form == "exact":
+            dtype = "exact-int/f64"
+            detail = (f"exact integer digits: J' (symmetric operand) per 128-row panel in {info[1]} FP16 digits of "
+                      f"{info[0]} bits ({info[0] * info[1]} bits), charges exact in FP16, digit sums exact integers "
+                      f"in the FP32 tcgen05 accumulators, combined in FP64: FP64-grade (truncation <= 2^-{info[0] * info[1]}"
+                      f" of each panel's largest |J'|; within 1e-10 relative of the FP64 oracle)")
+        else:
+            dtype = "bf16" if "bf16" in form else "tf32"
+            detail = f"J split in {terms[form]} terms, Q exact, FP32 accumulate on tcgen05, FP64 cross-tile sums"
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": prob.N, "B": B_POP, "form": form,
-                           "form_detail": f"J split in {terms} BF16 terms, Q exact, FP32 accumulate on tcgen05, "
-                                          "FP64 cross-tile sums",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": prob.N, "B": B_POP, "form": form, "form_detail": detail,
                            "l2": "256 MB buffer written between steps (outside the step events)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk,
+                "energy_error_vs_fp64": err_vs_fp64(E_form),
+                other: {"value": world * B_POP / (o_ms / 1e3), "unit": "evals/s", "ms_per_step": o_ms,
+                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP),
+                        "energy_error_vs_fp64": err_vs_fp64(E_other), "speedup_over_fp64_path": f64_ms / o_ms},
                 "fp64_gpu_path": {"evals_per_s": world * B_POP / (f64_ms / 1e3), "ms_per_step": f64_ms,
                                   "speedup_of_form": f64_ms / ms},
-                "energy_error_vs_fp64": energy_error,
-                "topk64_fp64_rescore": {"ms": topk_ms, "exact_vs_fp64_path": top_exact,
+                "topk64_fp64_rescore": {"form": SECOND_FORM, "ms": topk_ms, "exact_vs_fp64_path": top_exact,
                                         "lowest_matches_fp64_argmin": same_best},
                 "mc": mc, "setup": {"ewald_build_ms": ewald_ms}}
         print(json.dumps(line), flush=True)
@@ -709,15 +780,17 @@ def run_suite(args):
             ctx.kernel_time("score_cc")
             box = {}
             ms = timed(lambda: [box.setdefault("E", gp.score(pop, form)) for _ in range(reps)]) / reps
-            kms, kn = ctx.kernel_time("score_tc" if form in TERMS else "score_cc")
+            tc_form = form in TERMS or form == "exact"
+            kms, kn = ctx.kernel_time("score_tc" if tc_form else "score_cc")
             ctx.set_timing(False)
             E = gp.score(pop, form)
             err = (E - E64).abs()
             d = {"ms_per_population": ms, "evals_per_s": B_POP / (ms / 1e3), "speedup_vs_f64": None,
                  "max_abs_err_eV": float(err.max()), "rms_abs_err_eV": float(err.pow(2).mean().sqrt()),
                  "kernel_ms": kms / max(kn, 1)}
-            if form in TERMS:
-                flops = TERMS[form] * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
+            if tc_form:
+                terms = gp.exact_info()[1] if form == "exact" else TERMS[form]
+                flops = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * ((B_POP + 255) // 256 * 256)
                 peak = bf16_peak / 2.0 if "tf32" in form else bf16_peak
                 d["tensor_tflops"] = flops / (d["kernel_ms"] / 1e3) / 1e12
                 d["tensor_frac_of_measured_peak"] = d["tensor_tflops"] / peak

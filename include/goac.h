@@ -147,14 +147,23 @@ goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
  *   species_dev: B x Nv int8.  E_dev: B doubles.  precision: GOAC_PREC_*.   *
  * F64 is the plain path; the tensor-core forms split J into TF32 / BF16     *
  * terms, accumulate J.Q in FP32 on tcgen05 and form E in FP64.  EXACT      *
- * (integer charges after a power-of-two scaling, 128 max|q| Nv < 2^24, else  *
+ * (charges integers after a power-of-two scaling 2^kq, kq <= 4, and          *
+ * 128 max|q 2^kq| Nv_pad < 2^24, Nv_pad = Nv rounded up to 128; else        *
  * GOAC_ERR_UNSUPPORTED): each 128-row panel of J is scaled by a power of    *
- * two and cut into six signed 8-bit digits, so every tensor-core product and *
- * partial sum is an integer below 2^24 and exact; digit sums are weighted by *
- * the charges in 32-bit integers and combined in FP64 (truncation 2^-48 of   *
- * the panel's largest entry).                                                *
+ * two and cut into T signed r-bit digits held in FP16 (r = 10, T = 5 when   *
+ * 512 max|q 2^kq| Nv_pad < 2^24, else r = 8, T = 6), so every tensor-core    *
+ * product and partial sum is an integer below 2^24 and exact; digit sums are *
+ * weighted by the charges in 32-bit integers and combined in FP64          *
+ * (truncation 2^-rT <= 2^-48 of the panel's largest entry).                 *
  * ------------------------------------------------------------------------ */
 goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
+
+/* Digit layout the EXACT form uses on this problem (host outputs, nullable):  *
+ * digit_bits r, digits T and the charge scaling kq of the rule above; the     *
+ * truncation of J is then at most 2^-rT of each panel's largest entry.       *
+ * GOAC_ERR_UNSUPPORTED when the charges do not admit the exact form.          */
+goac_status goac_problem_exact_info(const goac_problem* prob, int32_t* digit_bits, int32_t* digits,
+                                    int32_t* charge_shift);
 
 /* Allocation-free FP64 scoring, for callers that may not allocate device     *
  * memory themselves (their device memory comes from a host framework's own   *
@@ -237,6 +246,29 @@ goac_status goac_random_configs(goac_problem* prob, int32_t B, uint64_t seed, in
 goac_status goac_mc_run(goac_problem* prob, int8_t* species_dev, int32_t C, const double* kT_dev, int64_t n_steps,
                         uint64_t seed, uint64_t step0, int32_t precision, double* E_dev, double* bestE_dev,
                         int8_t* best_species_dev, int64_t* n_accept_dev);
+
+/* Run-level stop and statistics of the Monte Carlo chains (Section         *
+ * "Internal Fortran Heuristics in GOAC": a run ends after a given number of *
+ * steps, or of steps without improvement).  goac_mc_run with:               *
+ *   patience: with patience > 0 a chain stops after step t once             *
+ *     t - t_imp >= patience, t_imp being the last step whose acceptance      *
+ *     lowered E by more than 1e-9 eV below E at the previous such step (the  *
+ *     start, step0 - 1, counts as one); 0 = run all n_steps.                 *
+ *   stats (nullable; each pointer nullable, device arrays of C int64):       *
+ *     n_accept_dev accepted swaps; n_noop_dev proposals of two positions     *
+ *     holding the same species; best_step_dev the step at which the chain    *
+ *     first reached its best energy (step0 - 1: the starting configuration); *
+ *     steps_dev the steps run (< n_steps when patience stopped the chain).   *
+ * The other arguments are those of goac_mc_run.                              */
+typedef struct goac_mc_stats {
+    int64_t* n_accept_dev;
+    int64_t* n_noop_dev;
+    int64_t* best_step_dev;
+    int64_t* steps_dev;
+} goac_mc_stats;
+goac_status goac_mc_run_ex(goac_problem* prob, int8_t* species_dev, int32_t C, const double* kT_dev, int64_t n_steps,
+                           uint64_t seed, uint64_t step0, int32_t precision, int64_t patience, double* E_dev,
+                           double* bestE_dev, int8_t* best_species_dev, const goac_mc_stats* stats);
 
 /* Launch-shape autotuner for goac_mc_run / goac_sa_run / goac_remc_run (no *
  * counterpart in the paper): each (warps per chain W, chains per CTA) in     *
@@ -370,6 +402,44 @@ goac_status goac_ga_generation(goac_problem* prob, const int8_t* pop_dev, const 
  * GOAC_ERR_UNSUPPORTED.                                                     */
 goac_status goac_ga_run(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
                         int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0, int32_t precision);
+
+/* GA run with the run-level stops of Section "Internal Fortran Heuristics in *
+ * GOAC" (a run ends after a number of generations, or of generations        *
+ * without improvement, or a time budget) and the n lowest structures as      *
+ * output (Section "Implementation and Theoretical Background").  R           *
+ * populations of params->P in pop_dev (R P x Nv) and E_dev (R P), each       *
+ * evolving as goac_ga_run with key seed + r (goac_ga_run_populations).       *
+ * Patience: after generation g the population's lowest energy b_g improves  *
+ * when b_g < b_ref - 1e-9 eV, b_ref the lowest energy at the previous       *
+ * improvement (at first the initial population's); with patience > 0 a      *
+ * population stops once `patience` generations in a row brought none (later *
+ * generations leave it unchanged).  time_budget_s > 0: the host checks the   *
+ * wall clock every 8 generations and stops there once it is spent.          *
+ * topk > 0 (<= min(P, 1024)): the topk lowest of each final population,      *
+ * rescored in FP64 and sorted (goac_topk_rescore), into top_idx_dev (R topk  *
+ * int32, indices within the population) and topE_dev (R topk doubles).       *
+ * stats_host (nullable): R entries.  Synchronises when patience, a time      *
+ * budget or stats are given.                                                 */
+typedef struct goac_ga_params {
+    int32_t P;               /* individuals per population                      */
+    int32_t n_gen;           /* most generations                                */
+    int32_t n_elite;         /* the n_elite lowest (E, index) survive            */
+    uint32_t p_mut_u32;      /* mutation probability x 2^32                      */
+    int32_t precision;       /* rescoring form, GOAC_PREC_* (F64_INCR included) */
+    int32_t patience;        /* generations without improvement (0: no limit)   */
+    uint32_t gen0;           /* number of the first generation (draw counter)   */
+    double time_budget_s;    /* host wall-clock budget in seconds (0: none)     */
+} goac_ga_params;
+typedef struct goac_ga_stats {
+    int32_t generations;     /* generations run                                 */
+    int32_t best_generation; /* generation of the last improvement (0: none)    */
+    int32_t stop_reason;     /* 0: n_gen reached, 1: patience, 2: time budget    */
+    int32_t reserved;
+    double best_E;           /* lowest energy of the final population            */
+} goac_ga_stats;
+goac_status goac_ga_run_ex(goac_problem* prob, int8_t* pop_dev, double* E_dev, int32_t R,
+                           const goac_ga_params* params, uint64_t seed, int32_t topk, int32_t* top_idx_dev,
+                           double* topE_dev, goac_ga_stats* stats_host);
 
 /* R independent GA populations of P configurations each (the paper compares  *
  * independent runs of its heuristics; this runs them together): population  *

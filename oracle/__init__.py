@@ -94,6 +94,10 @@ def _declare(lib):
                                      _u64, _p]),
         "orc_ga_generation": (C.c_int, [_i64, _p, _p, _p, _i64, _i64, _u32, _u32, _u64, _p, _p, _p]),
         "orc_ga_run": (C.c_int, [_p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _i64, _u32, _u64, _u32]),
+        "orc_ga_run_ex": (C.c_int, [_p, _i64, _p, _p, _p, _p, _p, _i64, _i64, _i64, _u32, _u64, _u32, _i64, _p, _p,
+                                    _p]),
+        "orc_mc_run_ex": (C.c_int, [_p, _i64, _p, _p, _p, _p, _i64, _p, _i64, _u64, _u64, _i64, _p, _p, _p, _p, _p,
+                                    _p, _p]),
         "orc_energy_grad": (_d, [_p, _i64, _p, _p, _p, _i32, _p, _p, _d, _p]),
         "orc_round_to_counts": (C.c_int, [_i64, _p, _i32, _p, _p, _p]),
         "orc_enumerate": (_i64, [_p, _i64, _p, _p, _p, _i32, _p, _d, _p, _p, _i64, _p, _p, _i64]),
@@ -297,6 +301,28 @@ def mc_run(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0, trace=
     return {"species": sp, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc, "E_trace": tr}
 
 
+def mc_run_ex(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0, patience=0):
+    """mc_run with a patience (0: none) and per-chain statistics (n_noop,
+    best_step, steps_done)."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    sp = np.array(species, dtype=np.int8, copy=True, order="C")
+    Cn = sp.shape[0]
+    kTa = _f64(np.broadcast_to(np.asarray(kT, dtype=np.float64), (Cn,)))
+    E = np.zeros(Cn)
+    bestE = np.zeros(Cn)
+    best = np.zeros_like(sp)
+    out = {k: np.zeros(Cn, dtype=np.int64) for k in ("n_accept", "n_noop", "best_step", "steps_done")}
+    rc = _load().orc_mc_run_ex(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(sp), Cn,
+                               _ptr(kTa), nsteps, seed, step0, patience, _ptr(E), _ptr(bestE), _ptr(best),
+                               _ptr(out["n_accept"]), _ptr(out["n_noop"]), _ptr(out["best_step"]),
+                               _ptr(out["steps_done"]))
+    if rc:
+        raise ValueError("no movable class")
+    out.update({"species": sp, "E": E, "bestE": bestE, "best_species": best})
+    return out
+
+
 def mc_run_literal(J, site_class, fixed_q, z, species, kT, nsteps, seed, step0=0):
     """Metropolis swap MC with the paper's rule taken literally (accept iff
     dE <= 0 or u < exp(-dE/kT), plain phi update): the twin that mc_run is
@@ -427,6 +453,24 @@ def ga_run(J, site_class, fixed_q, z, pop, n_gen, n_elite, p_mut, seed, gen0=0):
     if rc:
         raise ValueError(f"ga_run failed rc={rc}")
     return pp, E
+
+
+def ga_run_ex(J, site_class, fixed_q, z, pop, n_gen, n_elite, p_mut, seed, gen0=0, patience=0):
+    """ga_run with the no-improvement patience: returns (pop, E, generations
+    run, generation of the last improvement, stopped by patience)."""
+    J = _f64(J)
+    sc = _i32a(site_class)
+    pop = np.array(pop, dtype=np.int8, copy=True, order="C")
+    E = np.zeros(pop.shape[0])
+    g = np.zeros(1, np.int64)
+    bg = np.zeros(1, np.int64)
+    st = np.zeros(1, np.int32)
+    rc = _load().orc_ga_run_ex(_ptr(J), sc.shape[0], _ptr(sc), _ptr(_f64(fixed_q)), _ptr(_f64(z)), _ptr(pop), _ptr(E),
+                               pop.shape[0], n_gen, n_elite, p_mut_to_u32(p_mut), seed, gen0, patience, _ptr(g),
+                               _ptr(bg), _ptr(st))
+    if rc:
+        raise ValueError("ga failed")
+    return pop, E, int(g[0]), int(bg[0]), bool(st[0])
 
 
 def energy_grad(J, site_class, fixed_q, z, counts, logits, lam):

@@ -45,6 +45,11 @@
  *   orc_gd_run_literal     the literal-rule twins: checked against their own
  *                          definitions by the same properties (Boltzmann
  *                          visits, local minima by fresh rescoring).
+ *   orc_mc_run_ex,
+ *   orc_ga_run_ex          patience and statistics: equal orc_mc_run /
+ *                          orc_ga_run when patience is 0 or never reached;
+ *                          the stop step / generation is checked against the
+ *                          rule recomputed from the recorded energy traces.
  *   orc_ga_generation      pinned: count preservation, elitism, inheritance
  *                          of common sites, 50 % swap acceptance (statistical).
  *   orc_random_configs     pinned: counts; uniformity (chi^2) on small cells.
@@ -662,17 +667,44 @@ static double step_kT(double kT0, const double* kT1, int64_t ch, uint64_t t, int
     return kT0 * exp(log(kT1[ch] / kT0) * ((double)t / (double)(total - 1)));
 }
 
+/* Stopping on a run without improvement (Section "Internal Fortran          */
+/* Heuristics in GOAC": a run may end after a number of steps without         */
+/* improvement).  With patience > 0 a chain stops after step t once           */
+/* t - t_imp >= patience, t_imp being the last step whose acceptance lowered   */
+/* E by more than 1e-9 eV below the energy at the previous such step (the     */
+/* start, step0 - 1, counts as one).  Per-chain statistics (each nullable):    */
+/* n_noop = proposals of two positions holding the same species; best_step =  */
+/* the step at which the best E (strictly lower than every earlier one) was   */
+/* first reached (step0 - 1: the start); steps_done = steps run.              */
+typedef struct {
+    int64_t patience;
+    int64_t* n_noop;
+    int64_t* best_step;
+    int64_t* steps_done;
+} mc_extra;
+
 static int mc_core(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
                    int8_t* species, int64_t C, const double* kT, const double* kT1, int64_t total,
                    int64_t nsteps, uint64_t seed, uint64_t step0, double* E_out, double* bestE,
-                   int8_t* best_species, int64_t* n_accept, double* E_trace);
+                   int8_t* best_species, int64_t* n_accept, double* E_trace, const mc_extra* ex);
 
 int orc_mc_run(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
                int8_t* species, int64_t C, const double* kT, int64_t nsteps, uint64_t seed, uint64_t step0,
                double* E_out, double* bestE, int8_t* best_species, int64_t* n_accept, double* E_trace)
 {
     return mc_core(J, N, site_class, fixed_q, z, species, C, kT, NULL, 0, nsteps, seed, step0, E_out, bestE,
-                   best_species, n_accept, E_trace);
+                   best_species, n_accept, E_trace, NULL);
+}
+
+/* orc_mc_run with a patience (0: none) and the statistics described above. */
+int orc_mc_run_ex(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                  int8_t* species, int64_t C, const double* kT, int64_t nsteps, uint64_t seed, uint64_t step0,
+                  int64_t patience, double* E_out, double* bestE, int8_t* best_species, int64_t* n_accept,
+                  int64_t* n_noop, int64_t* best_step, int64_t* steps_done)
+{
+    mc_extra ex = {patience, n_noop, best_step, steps_done};
+    return mc_core(J, N, site_class, fixed_q, z, species, C, kT, NULL, 0, nsteps, seed, step0, E_out, bestE,
+                   best_species, n_accept, NULL, &ex);
 }
 
 /* Simulated annealing: the Monte Carlo above with kT(t) = kT0 (kT1/kT0)^(t/(total-1)) per chain. */
@@ -681,13 +713,13 @@ int orc_sa_run(const double* J, int64_t N, const int32_t* site_class, const doub
                uint64_t seed, uint64_t step0, double* E_out, double* bestE, int8_t* best_species, int64_t* n_accept)
 {
     return mc_core(J, N, site_class, fixed_q, z, species, C, kT0, kT1, total, nsteps, seed, step0, E_out, bestE,
-                   best_species, n_accept, NULL);
+                   best_species, n_accept, NULL, NULL);
 }
 
 static int mc_core(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
                    int8_t* species, int64_t C, const double* kT, const double* kT1, int64_t total,
                    int64_t nsteps, uint64_t seed, uint64_t step0, double* E_out, double* bestE,
-                   int8_t* best_species, int64_t* n_accept, double* E_trace)
+                   int8_t* best_species, int64_t* n_accept, double* E_trace, const mc_extra* ex)
 {
     classes_t cl = make_classes(site_class, N);
     int64_t nv = cl.nv;
@@ -709,9 +741,16 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
         }
         double best = E;
         if (best_species) memcpy(best_species + ch * nv, sp, (size_t)nv);
-        int64_t nacc = 0;
+        int64_t nacc = 0, nnoop = 0, done = nsteps;
+        int64_t t_best = (int64_t)step0 - 1, t_imp = (int64_t)step0 - 1;
+        double E_imp = E;
+        const int64_t patience = ex ? ex->patience : 0;
         for (int64_t s = 0; s < nsteps; ++s) {
             uint64_t t = step0 + (uint64_t)s;
+            if (patience > 0 && (int64_t)t - 1 - t_imp >= patience) {   /* stopped after step t - 1 */
+                done = s;
+                break;
+            }
             uint32_t x[4];
             philox_draw(seed, (uint32_t)t, (uint32_t)(t >> 32), (uint32_t)ch, 0u, x);
             int k;
@@ -725,7 +764,10 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
             pick_pair(&cl, k, x[0], x[1], &va, &vb);
             int sa = sp[va], sb = sp[vb];
             if (E_trace) E_trace[ch * nsteps + s] = E;   /* energy before step s */
-            if (sa == sb) continue;
+            if (sa == sb) {
+                nnoop++;
+                continue;
+            }
             int64_t ia = cl.vsite[va], ib = cl.vsite[vb];
             double d = z[sb] - z[sa];
             double dE = 2.0 * d * (phi[va] - phi[vb]) + d * d * (J[ia * N + ia] + J[ib * N + ib] - 2.0 * J[ia * N + ib]);
@@ -750,12 +792,20 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
             nacc++;
             if (E < best) {
                 best = E;
+                t_best = (int64_t)t;
                 if (best_species) memcpy(best_species + ch * nv, sp, (size_t)nv);
+            }
+            if (E < E_imp - ORC_DE_ZERO) {
+                E_imp = E;
+                t_imp = (int64_t)t;
             }
         }
         if (E_out) E_out[ch] = E;
         if (bestE) bestE[ch] = best;
         if (n_accept) n_accept[ch] = nacc;
+        if (ex && ex->n_noop) ex->n_noop[ch] = nnoop;
+        if (ex && ex->best_step) ex->best_step[ch] = t_best;
+        if (ex && ex->steps_done) ex->steps_done[ch] = done;
     }
     free(q);
     free(phi);
@@ -986,6 +1036,56 @@ int orc_ga_run(const double* J, int64_t N, const int32_t* site_class, const doub
         orc_score(J, N, site_class, fixed_q, z, pop, P, E);
     }
     free(next);
+    return 0;
+}
+
+/* GA run with the run-level stop of Section "Internal Fortran Heuristics in */
+/* GOAC" (a run may end after a number of generations without improvement):  */
+/* after generation g (1 ..) the population's lowest energy b_g is an        */
+/* improvement when b_g < b_ref - 1e-9 eV, b_ref being the lowest energy at   */
+/* the previous improvement (the initial population's at first); with        */
+/* patience > 0 the run stops once `patience` generations in a row brought no */
+/* improvement.  Outputs (nullable): generations run, the generation of the   */
+/* last improvement (0: none) and whether patience stopped the run.           */
+int orc_ga_run_ex(const double* J, int64_t N, const int32_t* site_class, const double* fixed_q, const double* z,
+                  int8_t* pop, double* E, int64_t P, int64_t n_gen, int64_t n_elite, uint32_t p_mut_u32,
+                  uint64_t seed, uint32_t gen0, int64_t patience, int64_t* gens_out, int64_t* best_gen_out,
+                  int32_t* stopped_out)
+{
+    int64_t nv = count_variable(site_class, N);
+    int8_t* next = (int8_t*)malloc((size_t)(P * nv + 1));
+    orc_score(J, N, site_class, fixed_q, z, pop, P, E);
+    double b_ref = E[0];
+    for (int64_t b = 1; b < P; ++b)
+        if (E[b] < b_ref) b_ref = E[b];
+    int64_t g = 0, stall = 0, best_gen = 0;
+    int32_t stopped = 0;
+    while (g < n_gen) {
+        int rc = orc_ga_generation(N, site_class, pop, E, P, n_elite, p_mut_u32, gen0 + (uint32_t)g, seed, next,
+                                   NULL, NULL);
+        if (rc) { free(next); return rc; }
+        memcpy(pop, next, (size_t)(P * nv));
+        orc_score(J, N, site_class, fixed_q, z, pop, P, E);
+        g++;
+        double b_g = E[0];
+        for (int64_t b = 1; b < P; ++b)
+            if (E[b] < b_g) b_g = E[b];
+        if (b_g < b_ref - ORC_DE_ZERO) {
+            b_ref = b_g;
+            stall = 0;
+            best_gen = g;
+        } else {
+            stall++;
+        }
+        if (patience > 0 && stall >= patience) {
+            stopped = 1;
+            break;
+        }
+    }
+    free(next);
+    if (gens_out) *gens_out = g;
+    if (best_gen_out) *best_gen_out = best_gen;
+    if (stopped_out) *stopped_out = stopped;
     return 0;
 }
 

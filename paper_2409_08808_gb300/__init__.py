@@ -17,7 +17,7 @@ import weakref
 import numpy as np
 import torch
 
-from ._lib import lib, LIB_PATH, SIGNATURES  # noqa: F401  (raises if the library is missing)
+from ._lib import lib, LIB_PATH, SIGNATURES, GaParams, GaStats, McStats  # noqa: F401  (raises if missing)
 
 #: Coulomb constant e^2 / (4 pi eps0) in eV * Angstrom (CODATA 2018).
 KE = 14.3996454784
@@ -197,6 +197,16 @@ class Problem:
         self.ctx.sync_stream()
         return self._h
 
+    def exact_info(self):
+        """(digit bits r, digits T, charge scaling kq) of the exact form on this
+        problem, or None when its charges do not admit it."""
+        r, T, kq = C.c_int32(), C.c_int32(), C.c_int32()
+        rc = lib.goac_problem_exact_info(self.handle, C.byref(r), C.byref(T), C.byref(kq))
+        if rc == -7:
+            return None
+        _check(rc, "goac_problem_exact_info")
+        return int(r.value), int(T.value), int(kq.value)
+
     def phi_fix(self) -> torch.Tensor:
         out = torch.empty(self.Nv, dtype=torch.float64, device=f"cuda:{self.ctx.device}")
         _check(lib.goac_problem_phi_fix(self.handle, _ptr(out)), "goac_problem_phi_fix")
@@ -291,6 +301,26 @@ class Problem:
                                _prec(precision), _ptr(E), _ptr(bestE), _ptr(best), _ptr(nacc)), "goac_mc_run")
         return {"species": species, "E": E, "bestE": bestE, "best_species": best, "n_accept": nacc}
 
+    def mc_run_ex(self, species: torch.Tensor, kT, n_steps: int, seed: int, step0: int = 0, precision="f64",
+                  patience: int = 0, want_best_species: bool = True):
+        """mc_run with a no-improvement patience (0: none) and per-chain statistics:
+        n_accept, n_noop, best_step (step0 - 1: the start), steps (steps run)."""
+        Cn = species.shape[0]
+        dev = self._dev()
+        kTt = torch.as_tensor(kT, dtype=torch.float64, device=dev).expand(Cn).contiguous()
+        E = torch.empty(Cn, dtype=torch.float64, device=dev)
+        bestE = torch.empty(Cn, dtype=torch.float64, device=dev)
+        best = torch.empty_like(species) if want_best_species else None
+        st = {k: torch.empty(Cn, dtype=torch.int64, device=dev) for k in ("n_accept", "n_noop", "best_step", "steps")}
+        ms = McStats(st["n_accept"].data_ptr() if Cn else None, st["n_noop"].data_ptr() if Cn else None,
+                     st["best_step"].data_ptr() if Cn else None, st["steps"].data_ptr() if Cn else None)
+        _check(lib.goac_mc_run_ex(self.handle, _ptr(species), Cn, _ptr(kTt), int(n_steps), int(seed), int(step0),
+                                  _prec(precision), int(patience), _ptr(E), _ptr(bestE), _ptr(best), C.byref(ms)),
+               "goac_mc_run_ex")
+        out = {"species": species, "E": E, "bestE": bestE, "best_species": best}
+        out.update(st)
+        return out
+
     def mc_autotune(self, species: torch.Tensor, kT, probe_steps: int = 256, precision="f64"):
         """Time the Monte Carlo launch shapes on a copy of `species` and keep the fastest for
         later runs of this problem.  Returns (warps per chain, chains per CTA, probe ms)."""
@@ -373,6 +403,27 @@ class Problem:
         _check(lib.goac_ga_run(self.handle, _ptr(pop), _ptr(E), P, int(n_gen), int(n_elite), int(p_mut_u32),
                                int(seed), int(gen0), _prec(precision)), "goac_ga_run")
         return E
+
+    def ga_run_ex(self, pop: torch.Tensor, n_gen: int, n_elite: int, p_mut_u32: int, seed: int, gen0: int = 0,
+                  precision="f64", patience: int = 0, R: int = 1, time_budget_s: float = 0.0, topk: int = 0):
+        """GA run(s) in place on `pop` (R P x Nv) with the run-level stops (patience,
+        wall-clock budget) and the topk lowest of each final population rescored in
+        FP64.  Returns a dict: E (R P), stats (list of R dicts), top_idx / top_E (R x topk)."""
+        RP = pop.shape[0]
+        assert R > 0 and RP % R == 0
+        P = RP // R
+        dev = self._dev()
+        E = torch.empty(RP, dtype=torch.float64, device=dev)
+        prm = GaParams(P, int(n_gen), int(n_elite), int(p_mut_u32), _prec(precision), int(patience), int(gen0),
+                       float(time_budget_s))
+        stats = (GaStats * R)()
+        ti = torch.empty((R, topk), dtype=torch.int32, device=dev) if topk else None
+        tE = torch.empty((R, topk), dtype=torch.float64, device=dev) if topk else None
+        _check(lib.goac_ga_run_ex(self.handle, _ptr(pop), _ptr(E), int(R), C.byref(prm), int(seed), int(topk),
+                                  _ptr(ti), _ptr(tE), stats), "goac_ga_run_ex")
+        st = [{"generations": x.generations, "best_generation": x.best_generation, "stop_reason": x.stop_reason,
+               "best_E": x.best_E} for x in stats]
+        return {"E": E, "stats": st, "top_idx": ti, "top_E": tE}
 
     def ga_run_populations(self, pop: torch.Tensor, R: int, n_gen: int, n_elite: int, p_mut_u32: int, seed: int,
                            gen0: int = 0, precision="f64"):

@@ -5,6 +5,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,20 +116,22 @@ struct goac_problem {
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
     DevBuf ga_incr;            // incremental GA rescoring: 2 x P x Nv potentials, P x 2 parents
+    DevBuf ga_track;           // per-population run-level stop state and final min / max
     int mc_tuned[2][2] = {{0, 0}, {0, 0}};   // [FP64, FP32]: autotuned {warps per chain, chains per CTA}, 0 = none
     // persistent tensor-core schedules (device copies) for the last shapes
     DevBuf sched, sched_ex;
     uint64_t sched_key = 0, sched_ex_key = 0;
     int sched_tiles = 0, sched_ex_tiles = 0;
-    // exact form: digits of the symmetric operand, panel exponents, scaled charges
-    __nv_bfloat16* J_dig = nullptr;    // [6][Nv_pad][Nv_pad]
+    // exact form: FP16 digits of the symmetric operand, panel exponents, scaled charges
+    __half* J_dig = nullptr;           // [dig_T][Nv_pad][Nv_pad]
     int* dig_exp = nullptr;            // Nv_pad / 128
     double* zq_dev = nullptr;          // 64, charges times 2^dig_kq
     int dig_kq = -1;
+    int dig_r = 0, dig_T = 0;          // digit width (bits) and number of digits
     // exact-form potentials: digits of J_vv itself, its panel exponents, digit sums
-    __nv_bfloat16* J_dig_full = nullptr;   // [6][Nv_pad][Nv_pad]
-    int* dig_exp_full = nullptr;           // Nv_pad / 128
-    DevBuf phi_dig;                        // [6][Bpad][Nv_pad] int32
+    __half* J_dig_full = nullptr;      // [dig_T][Nv_pad][Nv_pad]
+    int* dig_exp_full = nullptr;       // Nv_pad / 128
+    DevBuf phi_dig;                    // [dig_T][Bpad][Nv_pad] int32
 };
 
 // ---------------------------------------------------------------------------
@@ -287,7 +290,8 @@ __device__ __forceinline__ void tc_fence_after()
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 inputs, FP32 accumulate).
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 or FP16 inputs, as the
+// instruction descriptor says; FP32 accumulate).
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate)
 {
@@ -353,8 +357,8 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, A/B format fmt (1 = BF16, 2 = TF32),
-// both K-major, M x N tile.
+// Instruction descriptor: FP32 accumulator, A/B format fmt (kind::f16: 0 = FP16,
+// 1 = BF16; kind::tf32: 2 = TF32), both K-major, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t fmt, uint32_t M, uint32_t N)
 {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
@@ -433,5 +437,6 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi);
 // E as score_f64) on the tensor cores; false from exact_supported() means the
 // charges do not admit the exact form and score_f64 must be used.
 bool exact_supported(goac_problem* p);
+goac_status exact_info(const goac_problem* p, int32_t* digit_bits, int32_t* digits, int32_t* charge_shift);
 goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, double* phi_out);
 }  // namespace goac

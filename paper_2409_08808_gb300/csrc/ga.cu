@@ -5,11 +5,11 @@
 // populations of P at once (population r: rows r P .., Philox key seed + r).
 //
 // Device layout (one block or warp range per population where it says so):
-//   k_ga_minmax   one block per population: E_min, E_max.
-//   k_ga_fitness  one block per population: F_b = floor((Emax - E_b)/(Emax -
-//                 Emin) 2^24) and its running sum as exact 64-bit integers
-//                 (ordered scan), so roulette selection is an exact integer
-//                 search.
+//   k_ga_select   one block per population: E_min, E_max, the patience state of
+//                 the population (run-level stop), F_b = floor((Emax - E_b) /
+//                 (Emax - Emin) 2^24) and its running sum as exact 64-bit
+//                 integers (ordered scan), so roulette selection is an exact
+//                 integer search.
 //   k_ga_rank     ranks by (E, index) within the population to pick the elite
 //                 (O(P^2) comparisons, one warp per individual).
 //   k_ga_children one warp per child: parents by binary search of the running
@@ -24,15 +24,38 @@
 //   k_ga_incr     incremental FP64 rescoring, one block per child: the
 //                 potential and energy from the nearer parent's potential and
 //                 the J rows of the sites where the child differs from it.
+#include <algorithm>
+#include <chrono>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
 namespace {
 
-__global__ void k_ga_minmax(const double* __restrict__ E, int P, double* __restrict__ mm)
+// Run-level stop of one population (no improvement for `patience`
+// generations), kept on the device so that the generation loop needs no host
+// round trip: ref = the lowest energy at the last improvement, stall = the
+// generations since, stop = the population is finished (its later generations
+// copy it unchanged), gens = generations run, best_gen = generation of the last
+// improvement (0: the initial population), best = the current lowest energy.
+struct GaTrack {
+    double ref, best;
+    int stall, best_gen, stop, gens;
+};
+
+// One block per population: E_min / E_max, then (tracking) the patience
+// update for the population as it stands after g generations, then (fitness)
+// F_b = floor((Emax - E_b) / (Emax - Emin) 2^24) and its inclusive running
+// sum in index order as exact 64-bit integers.
+__global__ void __launch_bounds__(1024) k_ga_select(const double* __restrict__ E, int P, double* __restrict__ mm,
+                                                    unsigned long long* __restrict__ pre,
+                                                    unsigned long long* __restrict__ ftot, int fitness,
+                                                    GaTrack* __restrict__ track, int g, int patience)
 {
     __shared__ double smin[1024], smax[1024];
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry;
     E += (long)blockIdx.x * P;                // one block per population
     mm += 2 * blockIdx.x;
     double lo = E[0], hi = E[0];
@@ -50,26 +73,35 @@ __global__ void k_ga_minmax(const double* __restrict__ E, int P, double* __restr
         }
         __syncthreads();
     }
+    const double emin = smin[0], emax = smax[0];
     if (threadIdx.x == 0) {
-        mm[0] = smin[0];
-        mm[1] = smax[0];
+        mm[0] = emin;
+        mm[1] = emax;
+        if (track) {
+            GaTrack& tr = track[blockIdx.x];
+            if (g == 0) {
+                tr.ref = emin;
+                tr.best = emin;
+                tr.stall = tr.best_gen = tr.stop = tr.gens = 0;
+            } else if (!tr.stop) {
+                tr.gens = g;
+                tr.best = emin;
+                if (emin < tr.ref - 1e-9) {
+                    tr.ref = emin;
+                    tr.stall = 0;
+                    tr.best_gen = g;
+                } else {
+                    tr.stall++;
+                }
+                if (patience > 0 && tr.stall >= patience) tr.stop = 1;
+            }
+        }
+        carry = 0;
     }
-}
-
-// Inclusive running sum of the integer fitness, in index order.
-__global__ void __launch_bounds__(1024) k_ga_fitness(const double* __restrict__ E, int P,
-                                                     const double* __restrict__ mm, unsigned long long* __restrict__ pre,
-                                                     unsigned long long* __restrict__ ftot)
-{
-    __shared__ unsigned long long warp_tot[32];
-    __shared__ unsigned long long carry;
-    E += (long)blockIdx.x * P;                // one block per population
-    mm += 2 * blockIdx.x;
+    if (!fitness) return;
+    __syncthreads();
     pre += (long)blockIdx.x * P;
     ftot += blockIdx.x;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const double emin = mm[0], emax = mm[1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int base = 0; base < P; base += blockDim.x) {
         const int b = base + threadIdx.x;
@@ -128,6 +160,7 @@ struct GaArgs {
     const unsigned long long* pre;
     const unsigned long long* ftot;
     const int* elite;
+    const GaTrack* track;     // per population, or null: a finished population is copied unchanged
     int32_t* parents;
     int32_t* nswap;
     const int32_t* vclass;
@@ -190,6 +223,14 @@ __global__ void k_ga_children(GaArgs a)
     uint32_t* mis = (uint32_t*)(pb + (((size_t)Nv + 15) & ~(size_t)15));
     int8_t* out = a.children + cg * Nv;
 
+    if (a.track && a.track[r].stop) {         // finished (patience): the child is the individual itself
+        for (int w = lane; w < Nv; w += 32) out[w] = popr[(long)c * Nv + w];
+        if (lane == 0) {
+            if (a.parents) a.parents[2 * cg] = a.parents[2 * cg + 1] = c;
+            if (a.nswap) a.nswap[2 * cg] = a.nswap[2 * cg + 1] = 0;
+        }
+        return;
+    }
     if (c < a.n_elite) {
         const int src = a.elite[(long)r * a.n_elite + c];
         for (int w = lane; w < Nv; w += 32) out[w] = popr[(long)src * Nv + w];
@@ -516,7 +557,8 @@ namespace goac {
 // r P + P - 1, Philox key seed + r).
 static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const double* E, int R, int P,
                                       int n_elite, uint32_t p_mut, uint32_t gen, uint64_t seed, int8_t* children,
-                                      int32_t* parents, int32_t* nswap)
+                                      int32_t* parents, int32_t* nswap, GaTrack* track = nullptr, int g = 0,
+                                      int patience = 0)
 {
     goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;
@@ -530,8 +572,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     unsigned long long* ftot = pre + RP;
     double* mm = (double*)(ftot + R + 1);
     int* elite = (int*)(mm + 2 * (size_t)R);
-    goac::launch(k_ga_minmax, R, 1024, 0, st, E, P, mm);
-    goac::launch(k_ga_fitness, R, 1024, 0, st, E, P, mm, pre, ftot);
+    goac::launch(k_ga_select, R, 1024, 0, st, E, P, mm, pre, ftot, 1, track, g, patience);
     if (n_elite > 0) goac::launch(k_ga_rank, (int)((RP + 7) / 8), 256, 0, st, E, R, P, n_elite, elite);
     GOAC_LAUNCH_CHECK("ga prep");
     GaArgs a;
@@ -540,6 +581,7 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     a.pre = pre;
     a.ftot = ftot;
     a.elite = elite;
+    a.track = track;
     a.parents = parents;
     a.nswap = nswap;
     a.vclass = p->vclass_dev;
@@ -575,56 +617,127 @@ static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const 
     return GOAC_OK;
 }
 
-// GA run with incremental FP64 rescoring: the potentials of the population
-// are formed once by the FP64 scoring GEMM, then every generation forms each
-// child's potential and energy from its nearer parent's (k_ga_incr).
-static goac_status ga_run_incremental(goac_problem* p, int8_t* pop, double* E, int R, int P, int n_gen,
-                                      int n_elite, uint32_t p_mut, uint64_t seed, uint32_t gen0)
+struct GaRunOpts {
+    int n_gen, n_elite, precision, patience;
+    uint32_t p_mut, gen0;
+    double time_budget_s;
+};
+
+// GA run over R populations of P: initial scoring, then per generation the
+// children (ga_generation_impl) and their rescoring, dense (goac_score in the
+// requested form) or incremental in FP64 (k_ga_incr from the nearer parent's
+// potential; the potentials of the population are formed once by the FP64
+// scoring GEMM).  With tracking, the select kernel of each generation keeps the
+// per-population patience state on the device and finished populations are
+// copied unchanged; the host looks at the states every 8 generations (one
+// small copy) to stop launching once every population has finished or the
+// wall-clock budget is spent.
+static goac_status ga_run_core(goac_problem* p, int8_t* pop, double* E, int R, int P, const GaRunOpts& o,
+                               uint64_t seed, goac_ga_stats* stats)
 {
     goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;
     const int Nv = p->Nv;
     const long RP = (long)R * P;
-    const size_t smem = (sizeof(double) + sizeof(int)) * (size_t)Nv;
-    if (smem > 200 * 1024) return fail(GOAC_ERR_UNSUPPORTED, "goac_ga_run: incremental rescoring needs Nv <= 17066");
+    const bool incr = o.precision == GOAC_PREC_F64_INCR;
+    const bool tracking = o.patience > 0 || o.time_budget_s > 0.0 || stats != nullptr;
+    const size_t smem_incr = (sizeof(double) + sizeof(int)) * (size_t)Nv;
+    if (incr && smem_incr > 200 * 1024)
+        return fail(GOAC_ERR_UNSUPPORTED, "goac_ga_run: incremental rescoring needs Nv <= 17066");
     goac_status rc = ensure(p->phi, (size_t)RP * Nv);
     if (rc) return rc;
-    const size_t phi_bytes = sizeof(double) * (size_t)RP * Nv;
-    rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)RP + 256);
-    if (rc) return rc;
     int8_t* kids = (int8_t*)p->phi.ptr;
-    double* phi_a = (double*)p->ga_incr.ptr;
-    double* phi_b = (double*)((char*)p->ga_incr.ptr + phi_bytes);
-    int32_t* parents = (int32_t*)((char*)p->ga_incr.ptr + 2 * phi_bytes);
-    rc = score_f64(p, pop, (int)RP, E, phi_a);
-    if (rc) return rc;
-    GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    for (int g = 0; g < n_gen; ++g) {
-        rc = ga_generation_impl(p, pop, E, R, P, n_elite, p_mut, gen0 + (uint32_t)g, seed, kids, parents, nullptr);
+    GaTrack* track = nullptr;
+    double* mm_fin = nullptr;
+    if (tracking) {
+        rc = ensure(p->ga_track, sizeof(GaTrack) * (size_t)R + 2 * sizeof(double) * (size_t)R + 64);
         if (rc) return rc;
-        GaIncrArgs a;
-        a.pop = pop;
-        a.phi_pop = phi_a;
-        a.kids = kids;
-        a.parents = parents;
-        a.J = p->J_vv;
-        a.z = p->z_dev;
-        a.phifix = p->phifix;
-        a.phi_kids = phi_b;
-        a.E_kids = E;
-        a.err = ctx->d_err;
-        a.E_const = p->E_const;
-        a.ld = p->Nv_pad;
-        a.Nv = Nv;
-        a.P = P;
-        a.S = p->S;
-        {
-            KTimer kt(ctx, KID_GA_INCR, st);
-            goac::launch(k_ga_incr, (int)RP, GI_THREADS, smem, st, a);
+        track = (GaTrack*)p->ga_track.ptr;
+        mm_fin = (double*)(track + R);
+    }
+    double* phi_a = nullptr;
+    double* phi_b = nullptr;
+    int32_t* parents = nullptr;
+    if (incr) {
+        const size_t phi_bytes = sizeof(double) * (size_t)RP * Nv;
+        rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)RP + 256);
+        if (rc) return rc;
+        phi_a = (double*)p->ga_incr.ptr;
+        phi_b = (double*)((char*)p->ga_incr.ptr + phi_bytes);
+        parents = (int32_t*)((char*)p->ga_incr.ptr + 2 * phi_bytes);
+        rc = score_f64(p, pop, (int)RP, E, phi_a);
+        GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    } else {
+        rc = goac_score(p, pop, (int)RP, o.precision, E);
+    }
+    if (rc) return rc;
+    const auto t_start = std::chrono::steady_clock::now();
+    std::vector<GaTrack> host(tracking ? R : 0);
+    int stop_reason = 0, g = 0;
+    for (; g < o.n_gen; ++g) {
+        rc = ga_generation_impl(p, pop, E, R, P, o.n_elite, o.p_mut, o.gen0 + (uint32_t)g, seed, kids, parents,
+                                nullptr, track, g, o.patience);
+        if (rc) return rc;
+        if (incr) {
+            GaIncrArgs a;
+            a.pop = pop;
+            a.phi_pop = phi_a;
+            a.kids = kids;
+            a.parents = parents;
+            a.J = p->J_vv;
+            a.z = p->z_dev;
+            a.phifix = p->phifix;
+            a.phi_kids = phi_b;
+            a.E_kids = E;
+            a.err = ctx->d_err;
+            a.E_const = p->E_const;
+            a.ld = p->Nv_pad;
+            a.Nv = Nv;
+            a.P = P;
+            a.S = p->S;
+            {
+                KTimer kt(ctx, KID_GA_INCR, st);
+                goac::launch(k_ga_incr, (int)RP, GI_THREADS, smem_incr, st, a);
+            }
+            GOAC_LAUNCH_CHECK("k_ga_incr");
+            GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
+            std::swap(phi_a, phi_b);
+        } else {
+            GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
+            rc = goac_score(p, pop, (int)RP, o.precision, E);
+            if (rc) return rc;
         }
-        GOAC_LAUNCH_CHECK("k_ga_incr");
-        GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
-        std::swap(phi_a, phi_b);
+        if (tracking && (o.patience > 0 || o.time_budget_s > 0.0) && (g + 1) % 8 == 0 && g + 1 < o.n_gen) {
+            GOAC_CUDA(cudaMemcpyAsync(host.data(), track, sizeof(GaTrack) * (size_t)R, cudaMemcpyDeviceToHost, st));
+            GOAC_CUDA(cudaStreamSynchronize(st));
+            bool all = o.patience > 0;
+            for (int r = 0; r < R && all; ++r) all = host[r].stop != 0;
+            if (all) {
+                ++g;
+                break;
+            }
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (o.time_budget_s > 0.0 && el >= o.time_budget_s) {
+                stop_reason = 2;
+                ++g;
+                break;
+            }
+        }
+    }
+    if (!tracking) return GOAC_OK;
+    // the state after the last generation run
+    goac::launch(k_ga_select, R, 1024, 0, st, (const double*)E, P, mm_fin, (unsigned long long*)nullptr,
+                 (unsigned long long*)nullptr, 0, track, g, o.patience);
+    GOAC_LAUNCH_CHECK("k_ga_select (final)");
+    if (stats) {
+        GOAC_CUDA(cudaMemcpyAsync(host.data(), track, sizeof(GaTrack) * (size_t)R, cudaMemcpyDeviceToHost, st));
+        GOAC_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) {
+            stats[r].generations = host[r].stop ? host[r].gens : g;
+            stats[r].best_generation = host[r].best_gen;
+            stats[r].stop_reason = host[r].stop ? 1 : stop_reason;
+            stats[r].best_E = host[r].best;
+        }
     }
     return GOAC_OK;
 }
@@ -654,23 +767,8 @@ extern "C" goac_status goac_ga_run_populations(goac_problem* p, int8_t* pop_dev,
     if (R == 0 || P == 0) return GOAC_OK;
     if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
-    if (precision == GOAC_PREC_F64_INCR)
-        return goac::ga_run_incremental(p, pop_dev, E_dev, R, P, n_gen, n_elite, p_mut_u32, seed, gen0);
-    const int RP = R * P;
-    goac_status rc = goac::ensure(p->phi, (size_t)RP * p->Nv);
-    if (rc) return rc;
-    int8_t* kids = (int8_t*)p->phi.ptr;
-    rc = goac_score(p, pop_dev, RP, precision, E_dev);
-    if (rc) return rc;
-    for (int g = 0; g < n_gen; ++g) {
-        rc = goac::ga_generation_impl(p, pop_dev, E_dev, R, P, n_elite, p_mut_u32, gen0 + (uint32_t)g, seed, kids,
-                                      nullptr, nullptr);
-        if (rc) return rc;
-        GOAC_CUDA(cudaMemcpyAsync(pop_dev, kids, (size_t)RP * p->Nv, cudaMemcpyDeviceToDevice, p->ctx->stream));
-        rc = goac_score(p, pop_dev, RP, precision, E_dev);
-        if (rc) return rc;
-    }
-    return GOAC_OK;
+    goac::GaRunOpts o{n_gen, n_elite, precision, 0, p_mut_u32, gen0, 0.0};
+    return goac::ga_run_core(p, pop_dev, E_dev, R, P, o, seed, nullptr);
 }
 
 extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
@@ -678,4 +776,29 @@ extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_d
                                    int32_t precision)
 {
     return goac_ga_run_populations(p, pop_dev, E_dev, 1, P, n_gen, n_elite, p_mut_u32, seed, gen0, precision);
+}
+
+extern "C" goac_status goac_ga_run_ex(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t R,
+                                      const goac_ga_params* prm, uint64_t seed, int32_t topk, int32_t* top_idx_dev,
+                                      double* topE_dev, goac_ga_stats* stats_host)
+{
+    if (!p || !prm) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: NULL problem or parameters");
+    const int32_t P = prm->P;
+    if (R < 0 || P < 0 || (int64_t)R * P > GOAC_MAX_BATCH || prm->n_gen < 0 || prm->n_elite < 0 ||
+        prm->n_elite > P || prm->patience < 0 || !(prm->time_budget_s >= 0.0))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: bad sizes or parameters");
+    if (topk < 0 || (R > 0 && P > 0 && topk > std::min(P, 1024)))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: topk must be in 0 .. min(P, 1024)");
+    if (R == 0 || P == 0) return GOAC_OK;
+    if (!pop_dev || !E_dev || (topk > 0 && (!top_idx_dev || !topE_dev)))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: NULL");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    goac::GaRunOpts o{prm->n_gen, prm->n_elite, prm->precision, prm->patience, prm->p_mut_u32, prm->gen0,
+                      prm->time_budget_s};
+    goac_status rc = goac::ga_run_core(p, pop_dev, E_dev, R, P, o, seed, stats_host);
+    if (rc || topk == 0) return rc;
+    for (int r = 0; r < R && !rc; ++r)
+        rc = goac_topk_rescore(p, pop_dev + (size_t)r * P * p->Nv, P, E_dev + (size_t)r * P, topk,
+                               top_idx_dev + (size_t)r * topk, topE_dev + (size_t)r * topk);
+    return rc;
 }

@@ -47,6 +47,10 @@ struct McProb {
     double* bestE;            // chains
     int8_t* best_species;     // chains x Nv or null
     int64_t* n_accept;        // chains or null
+    int64_t* n_noop;          // chains or null: proposals of two positions with the same species
+    int64_t* best_step;       // chains or null: step of the first visit of the best E (step0 - 1: start)
+    int64_t* steps_done;      // chains or null: steps run
+    int64_t patience;         // stop a chain after this many steps without improvement (0: never)
     double E_const;
     uint64_t seed;
     uint32_t wtotal;
@@ -143,13 +147,21 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
         __syncwarp();
     }
     double best = E;
-    long nacc = 0;
+    long nacc = 0, nnoop = 0;
     if (P.best_species)
         for (int w = ct; w < Nv; w += 32 * W) P.best_species[(long)chain * Nv + w] = sp[w];
+    // run-level stop (no improvement for `patience` steps): steps t < t_stop run;
+    // an acceptance that lowers E by more than 1e-9 eV below E_imp moves t_stop on
+    const int64_t t_end = (int64_t)sc.step0 + sc.n_steps;
+    int64_t t_best = (int64_t)sc.step0 - 1, t_imp = (int64_t)sc.step0 - 1;
+    double E_imp = E;
+    int64_t t_stop = P.patience > 0 ? min(t_end, t_imp + P.patience + 1) : t_end;
 
     const double kT = P.kT[chain];
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
+        const int64_t tb = (int64_t)sc.step0 + s0;      // first step of this batch
+        if (tb >= t_stop) break;
         const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
         const uint64_t t = sc.step0 + (uint64_t)s0 + (uint64_t)lane;
         // ---- draw this lane's proposal (state independent) ----
@@ -190,12 +202,19 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                 else thr = (R)(-(float)kTl * logf((float)u));
             }
         }
-        uint32_t pending = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        const uint32_t valid = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        // lanes whose step lies before t_stop
+        auto live = [&](int64_t ts) -> uint32_t {
+            const int64_t k = ts - tb;
+            return k >= 32 ? 0xffffffffu : (k <= 0 ? 0u : ((1u << k) - 1u));
+        };
+        uint32_t pending = valid & live(t_stop);
         while (pending) {
-            bool acc = false;
+            bool acc = false, noop = false;
             R d = (R)0, dE = (R)0;
             if ((pending >> lane) & 1u) {
                 const int sa = sp[va], sb = sp[vb];
+                noop = sa == sb;
                 if (sa != sb) {
                     d = (R)(P.z[sb] - P.z[sa]);
                     dE = rd_add<R>(rd_mul<R>(rd_mul<R>((R)2, d), rd_sub<R>(phi[va], phi[vb])),
@@ -204,8 +223,13 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, acc);
-            if (m == 0u) break;
+            const uint32_t nm = __ballot_sync(0xffffffffu, noop);
+            if (m == 0u) {                         // every pending step is rejected or a no-op
+                nnoop += __popc(nm);
+                break;
+            }
             const int kl = __ffs(m) - 1;
+            nnoop += __popc(nm & ((1u << kl) - 1u));   // steps before the acceptance are final
             const int ca = __shfl_sync(0xffffffffu, va, kl);
             const int cb = __shfl_sync(0xffffffffu, vb, kl);
             const R cd = __shfl_sync(0xffffffffu, d, kl);
@@ -240,12 +264,19 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             ++nacc;
             if (E < best) {
                 best = E;
+                t_best = tb + kl;
                 if (P.best_species) {
                     for (int w = ct; w < Nv; w += 32 * W) P.best_species[(long)chain * Nv + w] = sp[w];
                     chain_sync<W>(bar_id);
                 }
             }
-            pending &= ~((2u << kl) - 1u);
+            if (P.patience > 0 && E < E_imp - kDeZero) {
+                E_imp = E;
+                t_imp = tb + kl;
+                t_stop = min(t_end, t_imp + P.patience + 1);
+            }
+            // the steps after the committed one, up to t_stop (which an improvement moves on)
+            pending = valid & ~((2u << kl) - 1u) & live(t_stop);
         }
     }
     chain_sync<W>(bar_id);
@@ -254,6 +285,9 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
         P.E_out[chain] = E;
         P.bestE[chain] = best;
         if (P.n_accept) P.n_accept[chain] = nacc;
+        if (P.n_noop) P.n_noop[chain] = nnoop;
+        if (P.best_step) P.best_step[chain] = t_best;
+        if (P.steps_done) P.steps_done[chain] = t_stop - (int64_t)sc.step0;
     }
 }
 
@@ -344,6 +378,10 @@ McProb make_desc(goac_problem* p, bool f32, int8_t* species, int C, const double
     d.bestE = bestE;
     d.best_species = best_species;
     d.n_accept = nacc;
+    d.n_noop = nullptr;
+    d.best_step = nullptr;
+    d.steps_done = nullptr;
+    d.patience = 0;
     d.E_const = p->E_const;
     d.seed = seed;
     d.wtotal = p->wtotal;
@@ -365,7 +403,8 @@ constexpr size_t kSmemBudget = 220 * 1024;
 static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
                                const double* kT1_dev, int64_t total, int64_t n_steps, uint64_t seed, uint64_t step0,
                                int32_t precision, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
-                               int64_t* n_accept_dev, int W_force = 0, int cpc_force = 0)
+                               int64_t* n_accept_dev, int W_force = 0, int cpc_force = 0, int64_t patience = 0,
+                               const goac_mc_stats* stats = nullptr)
 {
     if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: NULL problem");
     if (C < 0 || C > GOAC_MAX_BATCH || n_steps < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: bad size");
@@ -410,6 +449,13 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
     McProb d = make_desc(p, f32, species_dev, C, kT_dev, E_dev, bestE_dev, best_species_dev, n_accept_dev, seed);
     d.kT1 = kT1_dev;
     d.total = total;
+    d.patience = patience;
+    if (stats) {
+        if (stats->n_accept_dev) d.n_accept = stats->n_accept_dev;
+        d.n_noop = stats->n_noop_dev;
+        d.best_step = stats->best_step_dev;
+        d.steps_done = stats->steps_dev;
+    }
     McScalars sc{n_steps, step0};
     const int blocks = (C + cpc - 1) / cpc;
     goac::KTimer kt(p->ctx, goac::KID_MC, p->ctx->stream);
@@ -439,6 +485,16 @@ extern "C" goac_status goac_mc_run(goac_problem* p, int8_t* species_dev, int32_t
 {
     return mc_run_impl(p, species_dev, C, kT_dev, nullptr, 0, n_steps, seed, step0, precision, E_dev, bestE_dev,
                        best_species_dev, n_accept_dev);
+}
+
+extern "C" goac_status goac_mc_run_ex(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT_dev,
+                                      int64_t n_steps, uint64_t seed, uint64_t step0, int32_t precision,
+                                      int64_t patience, double* E_dev, double* bestE_dev, int8_t* best_species_dev,
+                                      const goac_mc_stats* stats)
+{
+    if (patience < 0) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run_ex: patience must be >= 0");
+    return mc_run_impl(p, species_dev, C, kT_dev, nullptr, 0, n_steps, seed, step0, precision, E_dev, bestE_dev,
+                       best_species_dev, nullptr, 0, 0, patience, stats);
 }
 
 extern "C" goac_status goac_sa_run(goac_problem* p, int8_t* species_dev, int32_t C, const double* kT0_dev,

@@ -966,6 +966,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->topk_tmp);
     free_buf(p->grad_tmp);
     free_buf(p->ga_incr);
+    free_buf(p->ga_track);
     free_buf(p->sched);
     free_buf(p->sched_ex);
     cudaFree(p->J_dig);
@@ -992,6 +993,13 @@ extern "C" goac_status goac_problem_phi_fix(const goac_problem* p, double* phi_f
     GOAC_CUDA(cudaMemcpyAsync(phi_fix_dev, p->phifix, sizeof(double) * p->Nv, cudaMemcpyDeviceToDevice,
                               p->ctx->stream));
     return GOAC_OK;
+}
+
+extern "C" goac_status goac_problem_exact_info(const goac_problem* p, int32_t* digit_bits, int32_t* digits,
+                                               int32_t* charge_shift)
+{
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_problem_exact_info: NULL problem");
+    return goac::exact_info(p, digit_bits, digits, charge_shift);
 }
 
 extern "C" goac_status goac_score(goac_problem* p, const int8_t* species_dev, int32_t B, int32_t precision,

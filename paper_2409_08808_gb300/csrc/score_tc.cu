@@ -33,6 +33,7 @@
 #include <functional>
 #include <mutex>
 #include <queue>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -440,27 +441,28 @@ __global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* _
 // ---------------------------------------------------------------------------
 // Exact form: integer-digit split of the symmetric operand on tcgen05.
 // J' (128-block upper triangle as above) is scaled per 128-row panel I by
-// 2^-e_I (|J'| <= 2^e_I) and written as six signed digits,
-// J'/2^e_I = 2^-7 sum_t a_t 2^-8t + r, a_t in [-128, 128] (exact in BF16),
-// |r| <= 2^-48.  Charges are integers after a power-of-two scaling, so every
-// product a_t q and every partial sum over <= Nv_pad sites is an integer below
-// 2^24: the FP32 accumulators hold the digit sums Phi_t = A_t Q exactly.
-// A tile is (panel I, 256 configurations, digit t): the same M = 128 sites x
-// N = 256 configurations MMA shape, stage layout and double-buffered TMEM
-// accumulators as k_score_tc with one term.  The epilogue forms
-// P_t,b = sum_i q_bi Phi_t,ib exactly in 32-bit integers (each accumulator
-// split into 12-bit halves so that no sum over the 128 sites can overflow) and
-// stores it as an FP64 integer; k_finish_exact scales by 2^(e_I - 7 - 8t).
-constexpr int EX_T = 6;                        // digits
+// 2^-e_I (|J'| < 2^e_I) and written as T signed digits of r bits,
+// J'/2^e_I = sum_t a_t 2^-(r-1+rt) + res, a_t in [-2^(r-1), 2^(r-1)] (exact in
+// FP16 for r <= 11), |res| <= 2^-rT.  The host picks r = 10, T = 5 (50 bits)
+// when 2^9 max|q| Nv_pad < 2^24, else r = 8, T = 6 (48 bits) when
+// 2^7 max|q| Nv_pad < 2^24.  Charges are integers after a power-of-two
+// scaling and exact in FP16, so every product a_t q and every partial sum over
+// <= Nv_pad sites is an integer below 2^24: the FP32 accumulators hold the
+// digit sums Phi_t = A_t Q exactly.  A tile is (panel I, 256 configurations,
+// digit t): the same M = 128 sites x N = 256 configurations MMA shape, stage
+// layout and double-buffered TMEM accumulators as k_score_tc with one term,
+// with kind::f16 on FP16 operands.  The epilogue forms P_t,b = sum_i q_bi
+// Phi_t,ib exactly in 32-bit integers (each accumulator split into 12-bit
+// halves so that no sum over the 128 sites can overflow) and stores it as an
+// FP64 integer; k_finish_exact scales by 2^(e_I - (r-1) - rt).
 constexpr int EX_STAGE = A_TILE + B_TILE;      // 48 KB
 constexpr int EX_STAGES = 4;
 constexpr int EX_SMEM = EX_STAGES * EX_STAGE + 1024 + 256;
 
 __global__ void __launch_bounds__(192, 1)
     k_score_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int ld,
-                  const __nv_bfloat16* __restrict__ qt, double* __restrict__ partial, int Bpad,
-                  int* __restrict__ err)
+                  const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int ld, int T,
+                  const __half* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
     constexpr int KB_PER_M = TC_M / 64;
     extern __shared__ uint8_t smem_raw[];
@@ -499,14 +501,17 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     goacd::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // launched as a dependent of k_make_qt: the set-up above overlaps its tail
+    goacd::pdl_wait();
+    goacd::pdl_trigger();
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
             int it = 0;
             for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
-                const int2 tile = work[wi];             // x = panel, y = configuration block * EX_T + digit
-                const int m0 = tile.x * TC_M, n0 = (tile.y / EX_T) * TC_N, t = tile.y % EX_T;
+                const int2 tile = work[wi];             // x = panel, y = configuration block * T + digit
+                const int m0 = tile.x * TC_M, n0 = (tile.y / T) * TC_N, t = tile.y % T;
                 for (int kb = tile.x * KB_PER_M; kb < nkb_total; ++kb, ++it) {
                     const int s = it % EX_STAGES;
                     const uint32_t use = (uint32_t)(it / EX_STAGES);
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, TC_M, TC_N);
+            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, TC_M, TC_N);   // FP16 digits and charges
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
                 const int2 tile = work[wi];
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(192, 1)
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
             const int v = tile.x * TC_M + lg * 32 + lane;
-            const long n0 = (long)(tile.y / EX_T) * TC_N;
+            const long n0 = (long)(tile.y / T) * TC_N;
 #pragma unroll 1
             for (int c = 0; c < TC_N / 32; ++c) {
                 uint32_t r[32];
@@ -591,7 +596,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const long b = n0 + c * 32 + j;
-                    const int q = __float2int_rn(__bfloat162float(qt[b * ld + v]));
+                    const int q = __float2int_rn(__half2float(qt[b * ld + v]));
                     const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
                     hi[j] = (a >> 12) * q;
                     lo[j] = (a & 4095) * q;
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(192, 1)
                 for (int col = etid; col < TC_N; col += 128) {
                     const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
                     const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
-                    partial[((long)tile.x * EX_T + tile.y % EX_T) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                    partial[((long)tile.x * T + tile.y % T) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
                 }
             goacd::named_bar_sync(1, 128);
         }
@@ -661,21 +666,21 @@ __global__ void k_panel_exp(const double* __restrict__ J, int ld, int sym, int* 
 }
 
 // Digit t of J'/2^e_I (sym != 0) or J/2^e_I at [t][i][j]: a_t = rint of the
-// remainder scaled by 2^(7 + 8t).
-__global__ void k_split_digits(const double* __restrict__ J, int ld, int sym, const int* __restrict__ pexp,
-                               __nv_bfloat16* __restrict__ out)
+// remainder scaled by 2^(r-1+rt), stored in FP16 (|a_t| <= 2^(r-1) <= 1024).
+__global__ void k_split_digits(const double* __restrict__ J, int ld, int sym, const int* __restrict__ pexp, int r,
+                               int T, __half* __restrict__ out)
 {
     const long n = (long)ld * ld;
+    const double radix = ldexp(1.0, r);
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / ld), j = (int)(e % ld);
         const int bi = i / TC_M, bj = j / TC_M;
         double x = !sym ? J[e] : (bj < bi ? 0.0 : (bj > bi ? 2.0 * J[e] : J[e]));
-        x = ldexp(x, 7 - pexp[bi]);               // |x| <= 128
-#pragma unroll
-        for (int t = 0; t < EX_T; ++t) {
+        x = ldexp(x, r - 1 - pexp[bi]);           // |x| < 2^(r-1)
+        for (int t = 0; t < T; ++t) {
             const double a = rint(x);
-            out[t * n + e] = __double2bfloat16(a);
-            x = (x - a) * 256.0;
+            out[t * n + e] = __double2half((double)a);
+            x = (x - a) * radix;
         }
     }
 }
@@ -689,7 +694,7 @@ __global__ void k_split_digits(const double* __restrict__ J, int ld, int sym, co
 // each exact digit sum as a 32-bit integer, Phi_t[b][v].
 __global__ void __launch_bounds__(192, 1)
     k_phi_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ntiles,
-                int nbm, int nkb, int ld, int Bpad, int* __restrict__ Phi, int* __restrict__ err)
+                int nbm, int nkb, int ld, int Bpad, int T, int* __restrict__ Phi, int* __restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -729,7 +734,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int it = 0;
             for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x) {
-                const int t = id % EX_T, I = (id / EX_T) % nbm, n = id / (EX_T * nbm);
+                const int t = id % T, I = (id / T) % nbm, n = id / (T * nbm);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % EX_STAGES;
                     const uint32_t use = (uint32_t)(it / EX_STAGES);
@@ -753,7 +758,7 @@ __global__ void __launch_bounds__(192, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, TC_M, TC_N);
+            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, TC_M, TC_N);   // FP16 digits and charges
             int it = 0, tl = 0;
             for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
                 const int acc_i = tl & 1;
@@ -790,7 +795,7 @@ __global__ void __launch_bounds__(192, 1)
         const int lg = warp & 3;
         int tl = 0;
         for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
-            const int t = id % EX_T, I = (id / EX_T) % nbm, n = id / (EX_T * nbm);
+            const int t = id % T, I = (id / T) % nbm, n = id / (T * nbm);
             const int acc_i = tl & 1;
             const uint32_t ause = (uint32_t)(tl >> 1);
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
@@ -822,12 +827,12 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-// phi_bv = 2^(e_I - 7 - kq) sum_t 2^-8t Phi_t[b][v] + phi_fix_v (digits smallest
-// first) and E_b = sum_v q_bv (phi_bv + phi_fix_v) + E_const, one block per
-// configuration, fixed reduction order.
+// phi_bv = 2^(e_I - (r-1) - kq) sum_t 2^-rt Phi_t[b][v] + phi_fix_v (digits
+// smallest first) and E_b = sum_v q_bv (phi_bv + phi_fix_v) + E_const, one block
+// per configuration, fixed reduction order.
 __global__ void __launch_bounds__(256)
     k_phi_exact_finish(const int* __restrict__ Phi, int Bpad, int ld, int Nv, const int* __restrict__ pexp, int kq,
-                       const double* __restrict__ phifix, const int8_t* __restrict__ species,
+                       int r, int T, const double* __restrict__ phifix, const int8_t* __restrict__ species,
                        const double* __restrict__ z, double E_const, double* __restrict__ phi_out,
                        double* __restrict__ E_out)
 {
@@ -836,9 +841,9 @@ __global__ void __launch_bounds__(256)
     double e = 0.0;
     for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
         double d = 0.0;
-        for (int t = EX_T - 1; t >= 0; --t) d += ldexp((double)Phi[((long)t * Bpad + b) * ld + v], -8 * t);
+        for (int t = T - 1; t >= 0; --t) d += ldexp((double)Phi[((long)t * Bpad + b) * ld + v], -r * t);
         const double pf = phifix[v];
-        const double ph = ldexp(d, pexp[v / TC_M] - 7 - kq) + pf;
+        const double ph = ldexp(d, pexp[v / TC_M] - (r - 1) - kq) + pf;
         if (phi_out) phi_out[(long)b * Nv + v] = ph;
         e += z[species[(long)b * Nv + v]] * (ph + pf);
     }
@@ -903,7 +908,7 @@ __global__ void k_copy_f32(const double* __restrict__ J, long n, float* __restri
         diag_out[e] = (float)diag[e];
 }
 
-// Q^T[b][v] = z[species[b][v]] in BF16 or FP32, zero padded to Bpad x ld, one
+// Q^T[b][v] = z[species[b][v]] in BF16, FP16 or FP32, zero padded to Bpad x ld, one
 // block per configuration row; 16 species per thread and step (one 16-byte load
 // when the row is 16-byte aligned), 16-byte stores.  With fixed ions also
 // lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
@@ -937,7 +942,13 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
             q[u] = s16[u] >= 0 ? zs[s16[u]] : 0.0f;
             if (phifix && s16[u] >= 0) acc += z[s16[u]] * (2.0 * phifix[v0 + u]);
         }
-        if constexpr (sizeof(QT) == 2) {
+        if constexpr (std::is_same<QT, __half>::value) {
+            __align__(16) __half o[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) o[u] = __float2half_rn(q[u]);
+            ((int4*)(row + v0))[0] = ((const int4*)o)[0];
+            ((int4*)(row + v0))[1] = ((const int4*)o)[1];
+        } else if constexpr (sizeof(QT) == 2) {
             __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
             for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16(q[u]);
@@ -958,19 +969,34 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
     if (threadIdx.x == 0) lin[b] = red[0];
 }
 
-__global__ void k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pexp,
-                               int Bpad, int B, int kq2, double E_const, const double* __restrict__ lin,
-                               double* __restrict__ E)
+// E_b = 2^-2kq sum_I 2^(e_I - (r-1)) sum_t 2^-rt P_t,I,b + lin_b + E_const.  One
+// block of 8 warps per 32 configurations: lane = configuration (coalesced
+// loads of the partials), warp w takes panels w, w + 8, ...; digits are added
+// smallest first and the 8 warp sums in a fixed order (deterministic).
+__global__ void __launch_bounds__(256)
+    k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pexp, int Bpad, int B,
+                   int r, int T, int kq2, double E_const, const double* __restrict__ lin, double* __restrict__ E)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+    __shared__ double red[8][33];
+    goacd::pdl_wait();          // the digit sums of the scoring kernel
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 32 + lane;
     double s = 0.0;
-    for (int m = 0; m < npanels; ++m) {
-        double d = 0.0;
-        for (int t = EX_T - 1; t >= 0; --t) d += ldexp(partial[((long)m * EX_T + t) * Bpad + b], -8 * t);
-        s += ldexp(d, pexp[m] - 7);
+    if (b < B)
+        for (int m = warp; m < npanels; m += 8) {
+            const double* pm = partial + (long)m * T * Bpad + b;
+            double d = 0.0;
+            for (int t = T - 1; t >= 0; --t) d += ldexp(pm[(long)t * Bpad], -r * t);
+            s += ldexp(d, pexp[m] - (r - 1));
+        }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        double tot = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) tot += red[w][lane];
+        E[b] = ldexp(tot, -kq2) + (lin ? lin[b] : 0.0) + E_const;
     }
-    E[b] = ldexp(s, -kq2) + (lin ? lin[b] : 0.0) + E_const;
 }
 
 __global__ void k_finish_tc(const double* __restrict__ partial, int mtiles, int Bpad, int B, double E_const,
@@ -1178,8 +1204,11 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
 }
 
 // Charge scaling of the exact form: the smallest kq <= 4 with every species
-// charge times 2^kq an integer, and 128 max|q 2^kq| Nv_pad < 2^24.
-static int exact_kq(const goac_problem* p)
+// charge times 2^kq an integer (-1: none), and the digit layout: r = 10 bits,
+// T = 5 digits when 2^9 max|q 2^kq| Nv_pad < 2^24, else r = 8, T = 6 when
+// 2^7 max|q 2^kq| Nv_pad < 2^24 (-2: neither), so that every digit sum of the
+// tensor-core contraction is an integer below 2^24.
+static int exact_layout(const goac_problem* p, int* r_out, int* T_out)
 {
     for (int k = 0; k <= 4; ++k) {
         bool ok = true;
@@ -1189,17 +1218,41 @@ static int exact_kq(const goac_problem* p)
             if (v != rint(v)) ok = false;
             qmax = std::max(qmax, fabs(v));
         }
-        if (ok) return 128.0 * qmax * (double)p->Nv_pad < 16777216.0 ? k : -2;
+        if (!ok) continue;
+        const double bound = qmax * (double)p->Nv_pad;
+        if (512.0 * bound < 16777216.0) {
+            if (r_out) *r_out = 10;
+            if (T_out) *T_out = 5;
+        } else if (128.0 * bound < 16777216.0) {
+            if (r_out) *r_out = 8;
+            if (T_out) *T_out = 6;
+        } else {
+            return -2;
+        }
+        return k;
     }
     return -1;
 }
 
-bool exact_supported(goac_problem* p) { return exact_kq(p) >= 0; }
+bool exact_supported(goac_problem* p) { return exact_layout(p, nullptr, nullptr) >= 0; }
+
+goac_status exact_info(const goac_problem* p, int32_t* digit_bits, int32_t* digits, int32_t* charge_shift)
+{
+    int r = 0, T = 0;
+    const int kq = exact_layout(p, &r, &T);
+    if (kq == -1) return fail(GOAC_ERR_UNSUPPORTED, "exact form: species charges are not multiples of 1/16");
+    if (kq == -2) return fail(GOAC_ERR_UNSUPPORTED, "exact form: 128 max|q| Nv exceeds 2^24");
+    if (digit_bits) *digit_bits = r;
+    if (digits) *digits = T;
+    if (charge_shift) *charge_shift = kq;
+    return GOAC_OK;
+}
 
 static goac_status exact_charges(goac_problem* p)
 {
     if (p->zq_dev) return GOAC_OK;
-    const int kq = exact_kq(p);
+    int r = 0, T = 0;
+    const int kq = exact_layout(p, &r, &T);
     if (kq == -1) return fail(GOAC_ERR_UNSUPPORTED, "exact form: species charges are not multiples of 1/16");
     if (kq == -2)
         return fail(GOAC_ERR_UNSUPPORTED, "exact form: 128 max|q| Nv exceeds 2^24 (digit sums would not be exact in FP32)");
@@ -1208,22 +1261,25 @@ static goac_status exact_charges(goac_problem* p)
     GOAC_CUDA(cudaMalloc(&p->zq_dev, sizeof(double) * 64));
     GOAC_CUDA(cudaMemcpy(p->zq_dev, zq.data(), sizeof(double) * 64, cudaMemcpyHostToDevice));
     p->dig_kq = kq;
+    p->dig_r = r;
+    p->dig_T = T;
     return GOAC_OK;
 }
 
 // Digits and panel exponents of the symmetric operand (sym) or of J_vv itself.
-static goac_status build_digits(goac_problem* p, bool sym, __nv_bfloat16** dig, int** pexp)
+static goac_status build_digits(goac_problem* p, bool sym, __half** dig, int** pexp)
 {
     goac_status rc = exact_charges(p);
     if (rc) return rc;
     const int ld = p->Nv_pad;
     const long n = (long)ld * ld;
     GOAC_CUDA(cudaMalloc(pexp, sizeof(int) * (ld / TC_M)));
-    GOAC_CUDA(cudaMalloc(dig, sizeof(__nv_bfloat16) * EX_T * (size_t)n));
+    GOAC_CUDA(cudaMalloc(dig, sizeof(__half) * p->dig_T * (size_t)n));
     cudaStream_t st = p->ctx->stream;
     goac::launch(k_panel_exp, ld / TC_M, 256, 0, st, (const double*)p->J_vv, ld, sym ? 1 : 0, *pexp);
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
-    goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, sym ? 1 : 0, (const int*)*pexp, *dig);
+    goac::launch(k_split_digits, blocks, 256, 0, st, (const double*)p->J_vv, ld, sym ? 1 : 0, (const int*)*pexp,
+                 p->dig_r, p->dig_T, *dig);
     GOAC_LAUNCH_CHECK("exact digits");
     return GOAC_OK;
 }
@@ -1241,33 +1297,34 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
         if (rc) return rc;
     }
     const int ld = p->Nv_pad;
+    const int T = p->dig_T;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int nbm = ld / TC_M, nbn = Bpad / TC_N;
     goac_status rc = ensure(p->qt, (size_t)Bpad * ld * 2);
-    if (!rc) rc = ensure(p->phi_dig, sizeof(int) * (size_t)EX_T * Bpad * ld);
+    if (!rc) rc = ensure(p->phi_dig, sizeof(int) * (size_t)T * Bpad * ld);
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
-    goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
-                 (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, (const double*)nullptr, (double*)nullptr);
+    goac::launch(k_make_qt<__half>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+                 (const double*)p->z_dev, ld, (__half*)p->qt.ptr, (const double*)nullptr, (double*)nullptr);
     GOAC_LAUNCH_CHECK("k_make_qt (exact potentials)");
     CUtensorMap ma, mb;
-    rc = make_map(&ma, p->J_dig_full, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
+    rc = make_map(&ma, p->J_dig_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TC_N);
     if (rc) return rc;
     static std::atomic<uint64_t> attr_done{0};
     rc = smem_attr_once((const void*)k_phi_exact, EX_SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
-    const int ntiles = nbm * nbn * EX_T;
+    const int ntiles = nbm * nbn * T;
     const int grid = std::min(ntiles, p->ctx->num_sms);
     {
         KTimer kt(p->ctx, KID_SCORE_TC, st);
-        goac::launch(k_phi_exact, grid, 192, EX_SMEM, st, ma, mb, ntiles, nbm, ld / 64, ld, Bpad,
+        goac::launch(k_phi_exact, grid, 192, EX_SMEM, st, ma, mb, ntiles, nbm, ld / 64, ld, Bpad, T,
                      (int*)p->phi_dig.ptr, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_phi_exact");
     }
     goac::launch(k_phi_exact_finish, B, 256, 0, st, (const int*)p->phi_dig.ptr, Bpad, ld, p->Nv,
-                 (const int*)p->dig_exp_full, p->dig_kq, (const double*)p->phifix, species, (const double*)p->z_dev,
-                 p->E_const, phi_out, E_out);
+                 (const int*)p->dig_exp_full, p->dig_kq, p->dig_r, T, (const double*)p->phifix, species,
+                 (const double*)p->z_dev, p->E_const, phi_out, E_out);
     GOAC_LAUNCH_CHECK("k_phi_exact_finish");
     return GOAC_OK;
 }
@@ -1277,39 +1334,40 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     goac_status rc = prepare_exact(p);
     if (rc) return rc;
     const int ld = p->Nv_pad;
+    const int T = p->dig_T;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int nbm = ld / TC_M, nbn = Bpad / TC_N;
     rc = ensure(p->qt, (size_t)Bpad * ld * 2);
-    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * EX_T * Bpad + Bpad));
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * T * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
     double* part = (double*)p->partial.ptr;
-    double* lin = p->has_fixed ? part + (size_t)nbm * EX_T * Bpad : nullptr;
-    goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
-                 (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr,
+    double* lin = p->has_fixed ? part + (size_t)nbm * T * Bpad : nullptr;
+    goac::launch(k_make_qt<__half>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+                 (const double*)p->z_dev, ld, (__half*)p->qt.ptr,
                  (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
     CUtensorMap ma, mb;
-    rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, (long)EX_T * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ld, Bpad, ld, TC_N);
+    rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TC_N);
     if (rc) return rc;
     static std::atomic<uint64_t> attr_done{0};
     rc = smem_attr_once((const void*)k_score_exact, EX_SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
-    const int grid = std::min(nbm * nbn * EX_T, p->ctx->num_sms);
+    const int grid = std::min(nbm * nbn * T, p->ctx->num_sms);
     const int2* work = nullptr;
     const int* starts = nullptr;
-    // tiles (I, n * EX_T + t): the LPT schedule sees EX_T times as many configuration blocks
-    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn * EX_T, grid, &work, &starts);
+    // tiles (I, n * T + t): the LPT schedule sees T times as many configuration blocks
+    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn * T, grid, &work, &starts);
     if (rc) return rc;
     {
         KTimer kt(p->ctx, KID_SCORE_TC, st);
-        goac::launch(k_score_exact, grid, 192, EX_SMEM, st, ma, mb, work, starts, ld / 64, ld,
-                     (const __nv_bfloat16*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+        goac::launch_pdl(k_score_exact, grid, 192, EX_SMEM, st, ma, mb, work, starts, ld / 64, ld, T,
+                         (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact");
     }
-    goac::launch(k_finish_exact, (B + 255) / 256, 256, 0, st, (const double*)part, nbm, (const int*)p->dig_exp,
-                 Bpad, B, 2 * p->dig_kq, p->E_const, (const double*)lin, E_out);
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, st, (const double*)part, nbm, (const int*)p->dig_exp,
+                     Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, (const double*)lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_exact");
     return GOAC_OK;
 }
