@@ -68,6 +68,10 @@ def _args():
     ap.add_argument("--paper-cells", default="2x2x1,2x2x2,4x4x1,4x4x2,6x6x1,8x8x1,6x6x2,6x6x3")
     ap.add_argument("--paper-chains", type=int, default=1024)
     ap.add_argument("--paper-steps", type=int, default=20000)
+    ap.add_argument("--nacl-steps", type=int, default=12_500_000, help="swaps per chain on NaCl 3x3x3")
+    ap.add_argument("--nacl-methods", default="MC,SA,REMC,GA,HY")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="default run: leave out the light runs of the other workloads")
     return ap.parse_args()
 
 
@@ -564,10 +568,22 @@ def run_ours(args, world, rank, local):
                 "topk64_fp64_rescore": {"form": SECOND_FORM, "ms": topk_ms, "exact_vs_fp64_path": top_exact,
                                         "lowest_matches_fp64_argmin": same_best},
                 "mc": mc, "setup": {"ewald_build_ms": ewald_ms}}
+        if not args.no_workloads:
+            # light runs of the other workloads (GA, gradient descent, the uneven batch of cells, the relaxed-
+            # occupation gradient, the paper's O3 cells and NaCl), one dict each, timed with CUDA events
+            t_w = time.perf_counter()
+            light = argparse.Namespace(**vars(args))
+            light.only, light.batch_steps, light.grad_steps = "mc,ga,gd,batch,relaxed", 2000, 100
+            light.paper_cells, light.paper_steps, light.nacl_methods = "2x2x1,4x4x1,6x6x1", 20000, "SA"
+            workloads = []
+            run_suite(light, ctx, workloads)
+            run_paper(light, ctx, workloads)
+            line["workloads"] = workloads
+            line["workloads_s"] = time.perf_counter() - t_w
         print(json.dumps(line), flush=True)
 
 
-def run_suite(args):
+def run_suite(args, ctx=None, out=None):
     """One JSON line per workload of the build's configuration list (the
     scoring benchmark of the default run is not repeated): rocksalt MC parity
     run, layered-oxide GA, the uneven batch of cells (persistent / graph /
@@ -579,7 +595,7 @@ def run_suite(args):
     import oracle
     import paper_2409_08808_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = ctx or g.Context(0)
     dev = torch.device("cuda", 0)
 
     def ev():
@@ -604,7 +620,10 @@ def run_suite(args):
         return g.Problem(ctx, J, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=allow), J, ms
 
     def emit(d):
-        print(json.dumps(d), flush=True)
+        if out is None:
+            print(json.dumps(d), flush=True)
+        else:
+            out.append(d)
 
     oracle.build()
     only = set(x.strip() for x in args.only.split(","))
@@ -652,7 +671,9 @@ def run_suite(args):
             ga_bytes = 3.0 * 1024 * prob.Nv
             gk_avg = gk_ms / max(gk_n, 1)
             E64 = gp.score(pop, "f64")
+            gen_bytes = 3.0 * 1024 * prob.Nv + (8.0 * 1024 * prob.Nv * 3 if prec == "f64_incr" else 0.0)
             res[prec] = {"ms": ms, "generations_per_s": 200 / (ms / 1e3), "child_evals_per_s": 1024 * 200 / (ms / 1e3),
+                         "generation_algorithmic_gbs_min": gen_bytes / (ms / 200 / 1e3) / 1e9,
                          "best_E_eV": float(E.min()), "best_E_fp64_rescored_eV": float(E64.min()),
                          "max_rel_dev_from_fp64_rescoring": float(((E - E64).abs() / E64.abs()).max()),
                          "children_kernel_ms": gk_avg,
@@ -684,10 +705,14 @@ def run_suite(args):
         ctx.set_timing(False)
         ik = ik_ms / max(ik_n, 1) / 1e3
         incr_bytes = 8.0 * M * prob.Nv + 2 * 8.0 * 1024 * prob.Nv + 3.0 * 1024 * prob.Nv
+        _, hbm_peak_ga, _ = _peaks()
         res["f64_incr_one_generation"] = {
             "changed_sites_per_child": M / 1024, "kernel_ms": ik * 1e3,
             "fp64_tflops": 2.0 * M * prob.Nv / ik / 1e12,
+            # FP64 pipe peak: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+            "fp64_pipe_frac": 2.0 * M * prob.Nv / ik / 1.2585e12,
             "algorithmic_gbs": incr_bytes / ik / 1e9,
+            "algorithmic_frac_of_hbm_copy_peak": incr_bytes / ik / 1e9 / hbm_peak_ga,
             "note": "J rows of the changed sites + parent and child potentials + species; the rows mostly come "
                     "from L2 (J_vv is 6 MB)"}
         work = None
@@ -855,7 +880,7 @@ def run_suite(args):
                                     "ga_5_generations_ms": gms, "ga_best_E_eV": float(box["Eg"].min())},
               "ewald_build_ms": jms})
 
-def run_paper(args):
+def run_paper(args, ctx=None, out=None):
     """The paper's heuristics on its own workloads, one JSON line per cell: the
     O3 layered-oxide sqrt(3) supercells of Table 1 and NaCl 3x3x3 (known
     optimum, Eq. 3).  Per method: best energy per ion (FP64 rescored), GPU time.
@@ -866,7 +891,13 @@ def run_paper(args):
     import oracle
     import paper_2409_08808_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = ctx or g.Context(0)
+
+    def emit(d):
+        if out is None:
+            print(json.dumps(d), flush=True)
+        else:
+            out.append(d)
     dev = torch.device("cuda", 0)
 
     def timed(fn):
@@ -878,7 +909,7 @@ def run_paper(args):
         torch.cuda.synchronize()
         return out, a.elapsed_time(b)
 
-    def methods(prob, C, steps, ga_pop, ga_gen):
+    def methods(prob, C, steps, ga_pop, ga_gen, which=("MC", "SA", "REMC", "GA", "HY")):
         frac = torch.tensor(prob.frac, device=dev)
         (J, gp), build_ms = timed(lambda: (lambda J_: (J_, g.Problem(ctx, J_, prob.site_class, prob.fixed_q, prob.z,
                                                                      prob.counts)))(
@@ -897,41 +928,47 @@ def run_paper(args):
             if best_any is None or e < best_any[0]:
                 best_any = (e, sp[i].clone())
 
-        sp = gp.random_configs(C, 1)
-        out, ms = timed(lambda: gp.mc_run(sp, 0.75, steps, 11, precision="f64"))
-        record("MC", out["best_species"], ms, {"kT_eV": 0.75, "chains": C, "steps": steps})
-        sp = gp.random_configs(C, 2)
-        out, ms = timed(lambda: gp.sa_run(sp, 1.0, 0.002, steps, steps, 12))
-        record("SA", out["best_species"], ms, {"kT_eV": "1.0 -> 0.002 (exponential)", "chains": C, "steps": steps})
+        if "MC" in which:
+            sp = gp.random_configs(C, 1)
+            o, ms = timed(lambda: gp.mc_run(sp, 0.75, steps, 11, precision="f64"))
+            record("MC", o["best_species"], ms, {"kT_eV": 0.75, "chains": C, "steps": steps})
+        if "SA" in which:
+            sp = gp.random_configs(C, 2)
+            o, ms = timed(lambda: gp.sa_run(sp, 1.0, 0.002, steps, steps, 12))
+            record("SA", o["best_species"], ms, {"kT_eV": "1.0 -> 0.002 (exponential)", "chains": C, "steps": steps})
         R = 8
         lad = list(np.geomspace(0.02, 1.0, R))
         G = max(1, C // R)
-        sp = gp.random_configs(G * R, 3)
         rounds = 20
-        (Er, perm, nex), ms = timed(lambda: gp.remc_run(sp, G, R, lad, rounds, steps // rounds, 13))
-        record("REMC", sp, ms, {"groups": G, "ladder_eV": [round(x, 4) for x in lad], "rounds": rounds,
-                                "steps_per_round": steps // rounds, "exchanges": nex})
-        pop = gp.random_configs(ga_pop, 4)
-        E, ms = timed(lambda: gp.ga_run(pop, ga_gen, max(1, ga_pop // 50), oracle.p_mut_to_u32(0.1), 14, 0, "bf16x2"))
-        record("GA", pop, ms, {"population": ga_pop, "generations": ga_gen, "scoring": "bf16x2, FP64 rescored"})
-        sp = gp.random_configs(G * R, 5)
-        E, ms = timed(lambda: gp.hybrid_run(sp, G, R, lad, 4, rounds // 4, steps // rounds, ga_gen // 4,
-                                            max(1, (G * R) // 50), oracle.p_mut_to_u32(0.1), 15))
-        record("HY", sp, ms, {"cycles": 4})
+        if "REMC" in which:
+            sp = gp.random_configs(G * R, 3)
+            (Er, perm, nex), ms = timed(lambda: gp.remc_run(sp, G, R, lad, rounds, steps // rounds, 13))
+            record("REMC", sp, ms, {"groups": G, "ladder_eV": [round(x, 4) for x in lad], "rounds": rounds,
+                                    "steps_per_round": steps // rounds, "exchanges": nex})
+        if "GA" in which:
+            pop = gp.random_configs(ga_pop, 4)
+            E, ms = timed(lambda: gp.ga_run(pop, ga_gen, max(1, ga_pop // 50), oracle.p_mut_to_u32(0.1), 14, 0,
+                                            "bf16x2"))
+            record("GA", pop, ms, {"population": ga_pop, "generations": ga_gen, "scoring": "bf16x2, FP64 rescored"})
+        if "HY" in which:
+            sp = gp.random_configs(G * R, 5)
+            E, ms = timed(lambda: gp.hybrid_run(sp, G, R, lad, 4, rounds // 4, steps // rounds, ga_gen // 4,
+                                                max(1, (G * R) // 50), oracle.p_mut_to_u32(0.1), 15))
+            record("HY", sp, ms, {"cycles": 4})
         return res, best_any
 
-    out_lines = []
-    for reps in [tuple(int(x) for x in c.split("x")) for c in args.paper_cells.split(",")]:
+    for reps in [tuple(int(x) for x in c.split("x")) for c in args.paper_cells.split(",") if c]:
         prob = synth.o3_layered_problem(reps)
         res, best = methods(prob, args.paper_chains, args.paper_steps, 1024, 200)
         pos = [int((prob.site_class == k).sum()) for k in range(2)]
         line = {"workload": f"O3-Na2/3[Li1/6Fe1/6Co1/6Ni1/6Mn1/3]O2 sqrt3 {reps[0]}x{reps[1]}x{reps[2]} "
                             f"(N={prob.N}, 10^{oracle.log10_configurations(pos, prob.counts):.0f} configurations)",
-                "methods": res, "best_E_per_ion_eV": best[0] / prob.N}
-        print(json.dumps(line), flush=True)
+                "methods": res, "best_E_per_ion_eV": best[0] / prob.N,
+                "budget": f"{args.paper_chains} chains x {args.paper_steps} swaps; GA 1024 x 200 generations"}
+        emit(line)
     # NaCl 3x3x3: 216 positions, 108 Na+ / 108 Cl- on one class; optimum = rocksalt order
     prob, _ = synth.nacl_problem((3, 3, 3), 5.62)
-    res, best = methods(prob, args.paper_chains, args.paper_steps * 25, 1024, 1000)
+    res, best = methods(prob, args.paper_chains, args.nacl_steps, 1024, 1000, tuple(args.nacl_methods.split(",")))
     M_ref = 1.747564594633182
     E_opt = -108 * M_ref * 14.3996454784 / 2.81
     for k, v in res.items():
@@ -939,8 +976,9 @@ def run_paper(args):
             continue
         v["madelung"] = abs(v["best_E_eV"]) * 2.81 / (108 * 14.3996454784)
         v["found_optimum"] = bool(abs(v["best_E_eV"] - E_opt) < 1e-6 * abs(E_opt))
-    print(json.dumps({"workload": "NaCl 3x3x3, 216 positions 50/50 Na/Cl (10^64 configurations), r = 2.81 A",
-                      "optimum_E_eV": E_opt, "madelung_ref": M_ref, "methods": res}), flush=True)
+    emit({"workload": "NaCl 3x3x3, 216 positions 50/50 Na/Cl (10^64 configurations), r = 2.81 A",
+          "optimum_E_eV": E_opt, "madelung_ref": M_ref, "methods": res,
+          "budget": f"{args.paper_chains} chains x {args.nacl_steps} swaps"})
 
 
 def main():
