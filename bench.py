@@ -256,7 +256,7 @@ def _kernel_hash(form="bf16x2") -> str:
         a = src.index("__global__ void __launch_bounds__(192, 1)\n    k_score_exact(")
         b = src.index("// Per 128-row panel I of the symmetric operand")
     else:
-        a = src.index("template <int T, bool TF32>\n__global__ void __launch_bounds__(192, 1)")
+        a = src.index("template <int T, bool TF32, int TN>\n__global__ void __launch_bounds__(192, 1)")
         b = src.index("__device__ __forceinline__ float to_tf32_rna(")
     common = open(os.path.join(csrc, "common.cuh")).read()
     h = hashlib.sha256()

@@ -158,6 +158,23 @@ goac_status goac_problem_phi_fix(const goac_problem* prob, double* phi_fix_dev);
  * ------------------------------------------------------------------------ */
 goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision, double* E_dev);
 
+/* Tile shape of the tensor-core scoring kernels (no counterpart in the       *
+ * paper; the results of EXACT do not depend on it, those of the split forms  *
+ * change only by FP32 rounding).  A tile covers 128 sites x tile_n (128 or   *
+ * 256) configurations; ksplit > 0 cuts each 128-row panel's column range     *
+ * into chunks of ksplit 128-column blocks scored as separate tiles (the       *
+ * row-dot is linear, so each chunk adds a partial sum; this spreads small    *
+ * populations over all SMs).  goac_score_set_shape stores a shape for         *
+ * (precision, B rounded up to 256) (tile_n = ksplit = 0: the default, 256     *
+ * and whole ranges); goac_score_autotune times every shape in {256, 128} x   *
+ * {0, 16, 8, 4, 2} on species_dev (B x Nv), CUDA events on the context       *
+ * stream, stores the fastest for later goac_score calls with that precision  *
+ * and padded B, and returns it (tile_n_out, ksplit_out, ms_out: nullable;    *
+ * ms per scoring call).  Host-side store; autotune synchronises.              */
+goac_status goac_score_set_shape(goac_problem* prob, int32_t precision, int32_t B, int32_t tile_n, int32_t ksplit);
+goac_status goac_score_autotune(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision,
+                                int32_t* tile_n_out, int32_t* ksplit_out, double* ms_out);
+
 /* Digit layout the EXACT form uses on this problem (host outputs, nullable):  *
  * digit_bits r, digits T and the charge scaling kq of the rule above; the     *
  * truncation of J is then at most 2^-rT of each panel's largest entry.       *
@@ -238,7 +255,10 @@ goac_status goac_random_configs(goac_problem* prob, int32_t B, uint64_t seed, in
  * phi = J q held per chain; on acceptance phi += d (J_:a - J_:b).           *
  *   species_dev: C x Nv in/out.  kT_dev: C.  Steps step0 .. step0+n_steps-1 *
  *   (resuming at step0 continues the same stream).  E_dev, bestE_dev: C     *
- *   doubles out; best_species_dev: C x Nv out (nullable); n_accept_dev: C    *
+ *   doubles out (best: the last energy that undercut every earlier one by   *
+ *   more than the 1e-9 eV tie, so that which of several symmetry-equivalent *
+ *   configurations is kept does not follow rounding); best_species_dev:     *
+ *   C x Nv out (nullable), the configuration of that energy; n_accept_dev: C *
  *   int64 out (nullable).  precision: GOAC_PREC_F64 (trajectory-exact to    *
  *   the FP64 definition) or GOAC_PREC_F32 (phi and J rows in FP32).         *
  *   GOAC_ERR_INVALID_ARG when no class has two positions (no swap exists).   *

@@ -654,8 +654,8 @@ int orc_random_configs(int64_t N, const int32_t* site_class, int32_t S, const in
 /* 1e-9 eV only); |dE| <= 1e-9 eV is read as dE = 0, since swaps related by */
 /* symmetry give +-1e-14 eV under rounding.  On acceptance the species are  */
 /* swapped, phi_w = fma(d, J[w,ia] - J[w,ib], phi_w) for every variable w,  */
-/* and E += dE.  The best E seen (strictly lower) and its configuration are */
-/* kept.  Returns the number of accepted swaps per chain in n_accept, and,   */
+/* and E += dE.  The best E seen (lower than every earlier one by more than  */
+/* the 1e-9 eV tie) and its configuration are kept.  Returns the number of accepted swaps per chain in n_accept, and,   */
 /* when E_trace (C x nsteps) is given, the energy before every step.         */
 /* ------------------------------------------------------------------------ */
 /* Temperature of step t: constant kT0, or with kT1 given the exponential    */
@@ -674,8 +674,8 @@ static double step_kT(double kT0, const double* kT1, int64_t ch, uint64_t t, int
 /* E by more than 1e-9 eV below the energy at the previous such step (the     */
 /* start, step0 - 1, counts as one).  Per-chain statistics (each nullable):    */
 /* n_noop = proposals of two positions holding the same species; best_step =  */
-/* the step at which the best E (strictly lower than every earlier one) was   */
-/* first reached (step0 - 1: the start); steps_done = steps run.              */
+/* the step at which the best E (lower than every earlier one by more than    */
+/* 1e-9 eV) was reached (step0 - 1: the start); steps_done = steps run.       */
 typedef struct {
     int64_t patience;
     int64_t* n_noop;
@@ -790,7 +790,9 @@ static int mc_core(const double* J, int64_t N, const int32_t* site_class, const 
                 }
             E = E + dE;
             nacc++;
-            if (E < best) {
+            /* a new best must be lower by more than the 1e-9 eV tie: otherwise which of
+               several symmetry-equivalent configurations is recorded follows rounding */
+            if (E < best - ORC_DE_ZERO) {
                 best = E;
                 t_best = (int64_t)t;
                 if (best_species) memcpy(best_species + ch * nv, sp, (size_t)nv);
@@ -881,7 +883,7 @@ int orc_mc_run_literal(const double* J, int64_t N, const int32_t* site_class, co
             }
             E = E + dE;
             nacc++;
-            if (E < best) best = E;
+            if (E < best - 1e-9) best = E;
         }
         if (E_out) E_out[ch] = E;
         if (bestE) bestE[ch] = best;

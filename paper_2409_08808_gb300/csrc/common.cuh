@@ -9,7 +9,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/goac.h"
@@ -83,6 +85,14 @@ struct goac_ctx {
     DevBuf batch_counter;
 };
 
+// A persistent scoring kernel's tile schedule on the device (tiles, per-CTA
+// starts, per-panel partial-slot starts) and the shape it was built for.
+struct TcSched {
+    DevBuf buf;
+    uint64_t key[2] = {0, 0};
+    int ntiles = 0, nslots = 0, grid = 0;
+};
+
 // Per-problem data on the device.  Kernels receive the plain pointers.
 struct goac_problem {
     goac_ctx* ctx = nullptr;
@@ -119,9 +129,9 @@ struct goac_problem {
     DevBuf ga_track;           // per-population run-level stop state and final min / max
     int mc_tuned[2][2] = {{0, 0}, {0, 0}};   // [FP64, FP32]: autotuned {warps per chain, chains per CTA}, 0 = none
     // persistent tensor-core schedules (device copies) for the last shapes
-    DevBuf sched, sched_ex;
-    uint64_t sched_key = 0, sched_ex_key = 0;
-    int sched_tiles = 0, sched_ex_tiles = 0;
+    TcSched sched, sched_ex;
+    // scoring tile shape per (precision, padded batch): {configurations per tile, k-chunk in 128-column blocks}
+    std::map<std::pair<int, int>, std::pair<int, int>> tile_shape;
     // exact form: FP16 digits of the symmetric operand, panel exponents, scaled charges
     __half* J_dig = nullptr;           // [dig_T][Nv_pad][Nv_pad]
     int* dig_exp = nullptr;            // Nv_pad / 128
@@ -438,5 +448,7 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi);
 // charges do not admit the exact form and score_f64 must be used.
 bool exact_supported(goac_problem* p);
 goac_status exact_info(const goac_problem* p, int32_t* digit_bits, int32_t* digits, int32_t* charge_shift);
-goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, double* phi_out);
+// phi_out: B x Nv FP64, or FP32 (rounded once from the FP64-grade value) when phi_f32.
+goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, void* phi_out,
+                      bool phi_f32 = false);
 }  // namespace goac

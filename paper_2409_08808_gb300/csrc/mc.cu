@@ -262,7 +262,7 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             chain_sync<W>(bar_id);
             E = E + (double)cdE;
             ++nacc;
-            if (E < best) {
+            if (E < best - kDeZero) {          // a new best: lower by more than the tie
                 best = E;
                 t_best = tb + kl;
                 if (P.best_species) {
@@ -423,16 +423,17 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
     const size_t slot = warp_slot_bytes(p->Nv, f32 ? 4 : 8);
     if (slot > kSmemBudget)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_mc_run: Nv too large for a shared-memory chain");
-    // potentials and energies of all chains by the tiled scoring GEMM
+    // potentials and energies of all chains
     const size_t rb = f32 ? 4 : 8;
     goac_status rc = goac::ensure(p->phi, rb * (size_t)C * p->Nv + sizeof(double) * (size_t)C + 256);
     if (rc) return rc;
     void* phi0 = p->phi.ptr;
     double* E0 = (double*)((char*)p->phi.ptr + ((rb * (size_t)C * p->Nv + 255) & ~(size_t)255));
-    // (FP64: the exact integer-digit contraction on the tensor cores when the
-    // charges admit it, else the FP64 GEMM)
-    if (f32) rc = goac::score_f32(p, species_dev, C, E0, (float*)phi0);
-    else if (goac::exact_supported(p)) rc = goac::phi_exact(p, species_dev, C, E0, (double*)phi0);
+    // (the exact integer-digit contraction on the tensor cores when the charges
+    // admit it, phi rounded to FP32 once for FP32 chains; else the FP64 or FP32
+    // CUDA-core GEMM)
+    if (goac::exact_supported(p)) rc = goac::phi_exact(p, species_dev, C, E0, phi0, f32);
+    else if (f32) rc = goac::score_f32(p, species_dev, C, E0, (float*)phi0);
     else rc = goac::score_f64(p, species_dev, C, E0, (double*)phi0);
     if (rc) return rc;
     // launch shape: warps per chain (more warps share the O(Nv) update of a long

@@ -967,8 +967,8 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->grad_tmp);
     free_buf(p->ga_incr);
     free_buf(p->ga_track);
-    free_buf(p->sched);
-    free_buf(p->sched_ex);
+    free_buf(p->sched.buf);
+    free_buf(p->sched_ex.buf);
     cudaFree(p->J_dig);
     cudaFree(p->dig_exp);
     cudaFree(p->zq_dev);

@@ -42,35 +42,46 @@
 namespace {
 
 constexpr int TC_M = 128;              // sites per tile (TMEM lanes)
-constexpr int TC_N = 256;              // configurations per tile (TMEM columns)
+constexpr int TC_N = 256;              // configurations per tile (TMEM columns), wide shape
+constexpr int TC_NS = 128;             // the narrow shape
 constexpr int ROW_BYTES = 128;         // one k-block row: 64 BF16 or 32 FP32
 constexpr int A_TILE = TC_M * ROW_BYTES;
 constexpr int B_TILE = TC_N * ROW_BYTES;
 constexpr long long WAIT_LIMIT = 4000000000LL;   // ~2 s of SM clock
 
-template <int T>
+template <int T, int TN = TC_N>
 struct TcCfg {
-    static constexpr int STAGE = T * A_TILE + B_TILE;
+    static constexpr int STAGE = T * A_TILE + TN * ROW_BYTES;
     static constexpr int STAGES_RAW = (196 * 1024) / STAGE;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
     static constexpr int BAR_BYTES = 256;   // stage barriers, 2 + 2 accumulator barriers, TMEM slot, flag
     static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES;
 };
 
+// One unit of work of the persistent scoring kernels: m-block I (128 sites),
+// configuration tile n (TN configurations), k-blocks [kb0, kb1) of the
+// symmetric operand's row panel I (its columns run from 128 I; the host may
+// split that range into chunks), the partial-sum slot it writes and, in the
+// exact form, the digit t.
+struct TcTile {
+    int I, n, kb0, kb1, slot, t;
+};
+
 // Persistent kernel.  CTA c processes the tiles work[work_start[c] ..
-// work_start[c+1]) (host LPT schedule, longest first); tile = (m-block I,
-// n-tile); with the symmetric operand its k-range starts at column 128 I.
-template <int T, bool TF32>
+// work_start[c+1]) (host LPT schedule, longest first).  Each tile's FP64 row-
+// dots go to partial[slot][configuration]; the finishing kernel adds the slots
+// in a fixed order (the row-dot is linear in Phi, so a split k-range only adds
+// slots).
+template <int T, bool TF32, int TN>
 __global__ void __launch_bounds__(192, 1)
     k_score_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int Nv_pad,
+               const TcTile* __restrict__ work, const int* __restrict__ work_start, int Nv_pad,
                const void* __restrict__ qt, int ldq, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
-    using Cfg = TcCfg<T>;
+    using Cfg = TcCfg<T, TN>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr int STAGE = Cfg::STAGE;
     constexpr int KE = TF32 ? 32 : 64;          // elements per 128-byte row
-    constexpr int KB_PER_M = TC_M / KE;         // k-blocks per 128 columns
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t* tempty = tfull + 2;               // [2] accumulator drained
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    __shared__ float red[4][TC_N];
+    __shared__ float red[4][TN];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(192, 1)
         goacd::prefetch_tmap(&tmB);
     }
     if (warp == 2) {
-        goacd::tmem_alloc(tmem_slot, 2 * TC_N);
+        goacd::tmem_alloc(tmem_slot, 2 * TN);
         goacd::tmem_relinquish();
     }
     goacd::tc_fence_before();
@@ -118,9 +129,9 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int it = 0;
             for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
-                const int2 tile = work[wi];
-                const int m0 = tile.x * TC_M, n0 = tile.y * TC_N;
-                for (int kb = tile.x * KB_PER_M; kb < nkb_total; ++kb, ++it) {
+                const TcTile tile = work[wi];
+                const int m0 = tile.I * TC_M, n0 = tile.n * TN;
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t use = (uint32_t)(it / STAGES);
                     if (it >= STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
@@ -148,10 +159,10 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(TF32 ? 2u : 1u, TC_M, TC_N);
+            constexpr uint32_t idesc = goacd::idesc_f32acc(TF32 ? 2u : 1u, TC_M, TN);
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
-                const int2 tile = work[wi];
+                const TcTile tile = work[wi];
                 const int acc_i = tl & 1;
                 const uint32_t ause = (uint32_t)(tl >> 1);
                 if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
@@ -159,9 +170,9 @@ __global__ void __launch_bounds__(192, 1)
                     goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
                 }
                 goacd::tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TC_N);
-                const int kb0 = tile.x * KB_PER_M;
-                for (int kb = kb0; kb < nkb_total; ++kb, ++it) {
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TN);
+                const int kb0 = tile.kb0;
+                for (int kb = kb0; kb < tile.kb1; ++kb, ++it) {
                     if (*abort_flag) break;
                     const int s = it % STAGES;
                     const uint32_t use = (uint32_t)(it / STAGES);
@@ -195,18 +206,18 @@ __global__ void __launch_bounds__(192, 1)
         const int etid = threadIdx.x - 64;         // 0..127
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
-            const int2 tile = work[wi];
+            const TcTile tile = work[wi];
             const int acc_i = tl & 1;
             const uint32_t ause = (uint32_t)(tl >> 1);
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
-            const int v = tile.x * TC_M + lg * 32 + lane;
-            const long n0 = (long)tile.y * TC_N;
+            const int v = tile.I * TC_M + lg * 32 + lane;
+            const long n0 = (long)tile.n * TN;
 #pragma unroll 1
-            for (int c = 0; c < TC_N / 32; ++c) {
+            for (int c = 0; c < TN / 32; ++c) {
                 uint32_t r[32];
-                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TC_N) + ((uint32_t)(lg * 32) << 16) +
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
                                               (uint32_t)(c * 32),
                                           r);
                 goacd::tmem_ld_wait();
@@ -239,10 +250,10 @@ __global__ void __launch_bounds__(192, 1)
             if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
             goacd::named_bar_sync(1, 128);
             if (ok)
-                for (int col = etid; col < TC_N; col += 128) {
+                for (int col = etid; col < TN; col += 128) {
                     const double ssum =
                         (double)red[0][col] + (double)red[1][col] + (double)red[2][col] + (double)red[3][col];
-                    partial[(long)tile.x * Bpad + n0 + col] = ssum;
+                    partial[(long)tile.slot * Bpad + n0 + col] = ssum;
                 }
             goacd::named_bar_sync(1, 128);
         }
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     if (warp == 2) {
         goacd::tc_fence_after();
-        goacd::tmem_dealloc(tmem, 2 * TC_N);
+        goacd::tmem_dealloc(tmem, 2 * TN);
     }
 }
 
@@ -455,30 +466,40 @@ __global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* _
 // Phi_t,ib exactly in 32-bit integers (each accumulator split into 12-bit
 // halves so that no sum over the 128 sites can overflow) and stores it as an
 // FP64 integer; k_finish_exact scales by 2^(e_I - (r-1) - rt).
-constexpr int EX_STAGE = A_TILE + B_TILE;      // 48 KB
+constexpr int EX_STAGE = A_TILE + B_TILE;      // 48 KB (k_phi_exact)
 constexpr int EX_STAGES = 4;
 constexpr int EX_SMEM = EX_STAGES * EX_STAGE + 1024 + 256;
 
+// Stages of k_score_exact for a tile width: as many as fit in 196 KB, at most 6.
+template <int TN>
+struct ExCfg {
+    static constexpr int STAGE = A_TILE + TN * ROW_BYTES;
+    static constexpr int STAGES = (196 * 1024) / STAGE > 6 ? 6 : (196 * 1024) / STAGE;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int TN>
 __global__ void __launch_bounds__(192, 1)
     k_score_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const int2* __restrict__ work, const int* __restrict__ work_start, int nkb_total, int ld, int T,
+                  const TcTile* __restrict__ work, const int* __restrict__ work_start, int ld, int T,
                   const __half* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
-    constexpr int KB_PER_M = TC_M / 64;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + EX_STAGES * EX_STAGE);
-    uint64_t* empty = full + EX_STAGES;
-    uint64_t* tfull = empty + EX_STAGES;        // [2] accumulator ready
+    constexpr int STAGE = A_TILE + TN * ROW_BYTES;
+    constexpr int STAGES = ExCfg<TN>::STAGES;
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;           // [2] accumulator ready
     uint64_t* tempty = tfull + 2;               // [2] accumulator drained
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    __shared__ int red_hi[4][TC_N], red_lo[4][TC_N];
+    __shared__ int red_hi[4][TN], red_lo[4][TN];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
     if (threadIdx.x == 0) {
-        for (int s = 0; s < EX_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             goacd::mbar_init(&full[s], 1);
             goacd::mbar_init(&empty[s], 1);
         }
@@ -494,7 +515,7 @@ __global__ void __launch_bounds__(192, 1)
         goacd::prefetch_tmap(&tmB);
     }
     if (warp == 2) {
-        goacd::tmem_alloc(tmem_slot, 2 * TC_N);
+        goacd::tmem_alloc(tmem_slot, 2 * TN);
         goacd::tmem_relinquish();
     }
     goacd::tc_fence_before();
@@ -510,36 +531,36 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int it = 0;
             for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
-                const int2 tile = work[wi];             // x = panel, y = configuration block * T + digit
-                const int m0 = tile.x * TC_M, n0 = (tile.y / T) * TC_N, t = tile.y % T;
-                for (int kb = tile.x * KB_PER_M; kb < nkb_total; ++kb, ++it) {
-                    const int s = it % EX_STAGES;
-                    const uint32_t use = (uint32_t)(it / EX_STAGES);
-                    if (it >= EX_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                const TcTile tile = work[wi];
+                const int m0 = tile.I * TC_M, n0 = tile.n * TN, t = tile.t;
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
+                    if (it >= STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
                         *abort_flag = 1;
                         goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
                         break;
                     }
                     if (*abort_flag) break;
-                    uint8_t* st = smem + s * EX_STAGE;
-                    goacd::mbar_arrive_expect_tx(&full[s], EX_STAGE);
+                    uint8_t* st = smem + s * STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], STAGE);
                     goacd::tma_load_2d(st, &tmA, &full[s], kb * 64, t * ld + m0);
                     goacd::tma_load_2d(st + A_TILE, &tmB, &full[s], kb * 64, n0);
                 }
             }
             if (*abort_flag)
-                for (int k = it - EX_STAGES < 0 ? 0 : it - EX_STAGES; k < it; ++k)
-                    if (!goacd::mbar_wait_bounded(&full[k % EX_STAGES], (uint32_t)(k / EX_STAGES) & 1, WAIT_LIMIT))
+                for (int k = it - STAGES < 0 ? 0 : it - STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % STAGES], (uint32_t)(k / STAGES) & 1, WAIT_LIMIT))
                         goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, TC_M, TC_N);   // FP16 digits and charges
+            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, TC_M, TN);   // FP16 digits and charges
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
-                const int2 tile = work[wi];
+                const TcTile tile = work[wi];
                 const int acc_i = tl & 1;
                 const uint32_t ause = (uint32_t)(tl >> 1);
                 if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
@@ -547,19 +568,19 @@ __global__ void __launch_bounds__(192, 1)
                     goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
                 }
                 goacd::tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TC_N);
-                const int kb0 = tile.x * KB_PER_M;
-                for (int kb = kb0; kb < nkb_total; ++kb, ++it) {
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TN);
+                const int kb0 = tile.kb0;
+                for (int kb = kb0; kb < tile.kb1; ++kb, ++it) {
                     if (*abort_flag) break;
-                    const int s = it % EX_STAGES;
-                    const uint32_t use = (uint32_t)(it / EX_STAGES);
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
                     if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
                         *abort_flag = 1;
                         goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
                         break;
                     }
                     goacd::tc_fence_after();
-                    const uint32_t a0 = goacd::smem_u32(smem + s * EX_STAGE);
+                    const uint32_t a0 = goacd::smem_u32(smem + s * STAGE);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         goacd::mma_bf16(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
@@ -577,18 +598,18 @@ __global__ void __launch_bounds__(192, 1)
         const int etid = threadIdx.x - 64;
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
-            const int2 tile = work[wi];
+            const TcTile tile = work[wi];
             const int acc_i = tl & 1;
             const uint32_t ause = (uint32_t)(tl >> 1);
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
-            const int v = tile.x * TC_M + lg * 32 + lane;
-            const long n0 = (long)(tile.y / T) * TC_N;
+            const int v = tile.I * TC_M + lg * 32 + lane;
+            const long n0 = (long)tile.n * TN;
 #pragma unroll 1
-            for (int c = 0; c < TC_N / 32; ++c) {
+            for (int c = 0; c < TN / 32; ++c) {
                 uint32_t r[32];
-                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TC_N) + ((uint32_t)(lg * 32) << 16) +
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
                                               (uint32_t)(c * 32),
                                           r);
                 goacd::tmem_ld_wait();
@@ -622,10 +643,10 @@ __global__ void __launch_bounds__(192, 1)
             if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
             goacd::named_bar_sync(1, 128);
             if (ok)
-                for (int col = etid; col < TC_N; col += 128) {
+                for (int col = etid; col < TN; col += 128) {
                     const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
                     const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
-                    partial[((long)tile.x * T + tile.y % T) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                    partial[((long)tile.slot * T + tile.t) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
                 }
             goacd::named_bar_sync(1, 128);
         }
@@ -634,7 +655,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     if (warp == 2) {
         goacd::tc_fence_after();
-        goacd::tmem_dealloc(tmem, 2 * TC_N);
+        goacd::tmem_dealloc(tmem, 2 * TN);
     }
 }
 
@@ -830,10 +851,11 @@ __global__ void __launch_bounds__(192, 1)
 // phi_bv = 2^(e_I - (r-1) - kq) sum_t 2^-rt Phi_t[b][v] + phi_fix_v (digits
 // smallest first) and E_b = sum_v q_bv (phi_bv + phi_fix_v) + E_const, one block
 // per configuration, fixed reduction order.
+template <typename PT>
 __global__ void __launch_bounds__(256)
     k_phi_exact_finish(const int* __restrict__ Phi, int Bpad, int ld, int Nv, const int* __restrict__ pexp, int kq,
                        int r, int T, const double* __restrict__ phifix, const int8_t* __restrict__ species,
-                       const double* __restrict__ z, double E_const, double* __restrict__ phi_out,
+                       const double* __restrict__ z, double E_const, PT* __restrict__ phi_out,
                        double* __restrict__ E_out)
 {
     __shared__ double red[256];
@@ -844,7 +866,7 @@ __global__ void __launch_bounds__(256)
         for (int t = T - 1; t >= 0; --t) d += ldexp((double)Phi[((long)t * Bpad + b) * ld + v], -r * t);
         const double pf = phifix[v];
         const double ph = ldexp(d, pexp[v / TC_M] - (r - 1) - kq) + pf;
-        if (phi_out) phi_out[(long)b * Nv + v] = ph;
+        if (phi_out) phi_out[(long)b * Nv + v] = (PT)ph;      // FP32 chains: phi rounded once
         e += z[species[(long)b * Nv + v]] * (ph + pf);
     }
     if (!E_out) return;
@@ -969,13 +991,17 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
     if (threadIdx.x == 0) lin[b] = red[0];
 }
 
-// E_b = 2^-2kq sum_I 2^(e_I - (r-1)) sum_t 2^-rt P_t,I,b + lin_b + E_const.  One
-// block of 8 warps per 32 configurations: lane = configuration (coalesced
-// loads of the partials), warp w takes panels w, w + 8, ...; digits are added
-// smallest first and the 8 warp sums in a fixed order (deterministic).
+// E_b = 2^-2kq sum_I 2^(e_I - (r-1)) sum_t 2^-rt P_t,I,b + lin_b + E_const,
+// P_t,I,b the sum of panel I's k-chunk partials (slots pslot[I] ..
+// pslot[I+1]) of digit t: exact integers below 2^53, so the result does not
+// depend on how the panel's k-range was split.  One block of 8 warps per 32
+// configurations: lane = configuration (coalesced loads of the partials), warp
+// w takes panels w, w + 8, ...; digits are added smallest first and the 8
+// warp sums in a fixed order (deterministic).
 __global__ void __launch_bounds__(256)
-    k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pexp, int Bpad, int B,
-                   int r, int T, int kq2, double E_const, const double* __restrict__ lin, double* __restrict__ E)
+    k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pslot,
+                   const int* __restrict__ pexp, int Bpad, int B, int r, int T, int kq2, double E_const,
+                   const double* __restrict__ lin, double* __restrict__ E)
 {
     __shared__ double red[8][33];
     goacd::pdl_wait();          // the digit sums of the scoring kernel
@@ -984,9 +1010,13 @@ __global__ void __launch_bounds__(256)
     double s = 0.0;
     if (b < B)
         for (int m = warp; m < npanels; m += 8) {
-            const double* pm = partial + (long)m * T * Bpad + b;
+            const int s0 = pslot[m], s1 = pslot[m + 1];
             double d = 0.0;
-            for (int t = T - 1; t >= 0; --t) d += ldexp(pm[(long)t * Bpad], -r * t);
+            for (int t = T - 1; t >= 0; --t) {
+                double P = 0.0;
+                for (int sl = s0; sl < s1; ++sl) P += partial[((long)sl * T + t) * Bpad + b];
+                d += ldexp(P, -r * t);
+            }
             s += ldexp(d, pexp[m] - (r - 1));
         }
     red[warp][lane] = s;
@@ -999,14 +1029,15 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__global__ void k_finish_tc(const double* __restrict__ partial, int mtiles, int Bpad, int B, double E_const,
+// E_b = sum over the partial-sum slots in order + lin_b + E_const.
+__global__ void k_finish_tc(const double* __restrict__ partial, int nslots, int Bpad, int B, double E_const,
                             const double* __restrict__ lin, double* __restrict__ E)
 {
     goacd::pdl_wait();          // the partial sums of the scoring kernel
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
-    for (int m = 0; m < mtiles; ++m) s += partial[(long)m * Bpad + b];
+    for (int m = 0; m < nslots; ++m) s += partial[(long)m * Bpad + b];
     E[b] = s + (lin ? lin[b] : 0.0) + E_const;
 }
 
@@ -1057,82 +1088,144 @@ goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int e
     return GOAC_OK;
 }
 
-// Longest-processing-time schedule of the (m-block, n-tile) tiles over the
-// CTAs of a persistent grid; cached per problem for the current shape.
-goac_status tc_schedule_into(DevBuf& sched, uint64_t& sched_key, int& sched_tiles, int nbm, int nbn, int grid,
-                             const int2** work, const int** starts)
+// Number of tiles (x) and partial-sum slots (y) of a shape: panel I has
+// nbm - I blocks of 128 columns, cut into chunks of kc blocks (kc = 0: one).
+int2 tc_tile_count(int nbm, int nbn, int T, int kc)
 {
-    // key fields: nbm < 2^18 (Nv < 2^25), nbn < 2^26 (B < 2^31 times the 6 digits of the exact form), grid < 2^20
-    if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || grid <= 0 || grid >= (1 << 20))
+    long tiles = 0;
+    int slots = 0;
+    for (int I = 0; I < nbm; ++I) {
+        const int nch = kc > 0 ? (nbm - I + kc - 1) / kc : 1;
+        slots += nch;
+        tiles += (long)nch * nbn * T;
+    }
+    return make_int2((int)std::min<long>(tiles, 1L << 30), slots);
+}
+
+// Longest-processing-time schedule of the tiles (panel I, configuration tile
+// n, k-chunk, digit t) over the CTAs of a persistent grid, cached per problem
+// for the last shape.  Panel I's k-range (k-blocks from I kbm to nkb, kbm
+// k-blocks per 128 columns) is cut into chunks of kc 128-column blocks (kc = 0:
+// one chunk); each (I, chunk) is one partial-sum slot, slots numbered panel by
+// panel, so the slots of panel I are pslot[I] .. pslot[I+1].  Tiles go
+// longest first to the least-loaded CTA (ties: the lowest index).
+goac_status tc_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int kbm, int grid, const TcTile** work,
+                        const int** starts, const int** pslot)
+{
+    if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || grid <= 0 || grid >= (1 << 20) || T < 1 ||
+        T > 15 || kc < 0 || kc >= (1 << 16) || kbm < 1 || kbm > 15)
         return goac::fail(GOAC_ERR_INVALID_ARG, "tile schedule: shape out of range");
-    const uint64_t key = ((uint64_t)nbm << 46) | ((uint64_t)nbn << 20) | (uint64_t)grid;
-    if (sched_key != key) {
-        std::vector<int2> tiles;
-        for (int I = 0; I < nbm; ++I)
-            for (int n = 0; n < nbn; ++n) tiles.push_back(make_int2(I, n));
-        std::stable_sort(tiles.begin(), tiles.end(), [](const int2& a, const int2& b) { return a.x < b.x; });
+    const uint64_t k0 = ((uint64_t)nbm << 46) | ((uint64_t)nbn << 20) | (uint64_t)grid;
+    const uint64_t k1 = ((uint64_t)T << 24) | ((uint64_t)kc << 8) | (uint64_t)kbm;
+    if (sc.key[0] != k0 || sc.key[1] != k1) {
+        const int nkb = nbm * kbm;
+        std::vector<TcTile> tiles;
+        std::vector<int> ps(nbm + 1, 0);
+        int slot = 0;
+        for (int I = 0; I < nbm; ++I) {
+            ps[I] = slot;
+            const int step = kc > 0 ? kc * kbm : nkb - I * kbm;
+            for (int kb0 = I * kbm; kb0 < nkb; kb0 += step, ++slot) {
+                const int kb1 = std::min(nkb, kb0 + step);
+                for (int n = 0; n < nbn; ++n)
+                    for (int t = 0; t < T; ++t) tiles.push_back(TcTile{I, n, kb0, kb1, slot, t});
+            }
+        }
+        ps[nbm] = slot;
+        std::stable_sort(tiles.begin(), tiles.end(),
+                         [](const TcTile& a, const TcTile& b) { return a.kb1 - a.kb0 > b.kb1 - b.kb0; });
         // each tile goes to the least-loaded CTA (ties: the lowest index), a min-heap on (load, CTA)
-        std::vector<std::vector<int2>> per(grid);
+        std::vector<std::vector<TcTile>> per(grid);
         std::priority_queue<std::pair<long, int>, std::vector<std::pair<long, int>>,
                             std::greater<std::pair<long, int>>>
             heap;
         for (int c = 0; c < grid; ++c) heap.push({0L, c});
-        for (const int2& t : tiles) {
+        for (const TcTile& t : tiles) {
             const auto [ld0, best] = heap.top();
             heap.pop();
             per[best].push_back(t);
-            heap.push({ld0 + (nbm - t.x) + 1, best});   // k-blocks of 128 columns, +1 for the epilogue
+            heap.push({ld0 + (t.kb1 - t.kb0) / kbm + 1, best});   // 128-column blocks, +1 for the epilogue
         }
-        std::vector<int2> flat;
+        std::vector<TcTile> flat;
         std::vector<int> st(grid + 1, 0);
         for (int c = 0; c < grid; ++c) {
             st[c] = (int)flat.size();
             flat.insert(flat.end(), per[c].begin(), per[c].end());
         }
         st[grid] = (int)flat.size();
-        const size_t bytes = sizeof(int2) * flat.size() + sizeof(int) * (grid + 1) + 64;
-        goac_status rc = goac::ensure(sched, bytes);
+        const size_t bytes = sizeof(TcTile) * flat.size() + sizeof(int) * (grid + 1 + nbm + 1) + 64;
+        goac_status rc = goac::ensure(sc.buf, bytes);
         if (rc) return rc;
-        int2* dw = (int2*)sched.ptr;
+        TcTile* dw = (TcTile*)sc.buf.ptr;
         int* ds = (int*)(dw + flat.size());
-        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice));
+        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(TcTile) * flat.size(), cudaMemcpyHostToDevice));
         GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
-        sched_key = key;
-        sched_tiles = (int)flat.size();
+        GOAC_CUDA(cudaMemcpy(ds + grid + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice));
+        sc.key[0] = k0;
+        sc.key[1] = k1;
+        sc.ntiles = (int)flat.size();
+        sc.nslots = slot;
+        sc.grid = grid;
     }
-    *work = (const int2*)sched.ptr;
-    *starts = (const int*)((const int2*)sched.ptr + sched_tiles);
+    *work = (const TcTile*)sc.buf.ptr;
+    *starts = (const int*)((const TcTile*)sc.buf.ptr + sc.ntiles);
+    if (pslot) *pslot = *starts + sc.grid + 1;
     return GOAC_OK;
 }
 
-goac_status tc_schedule(goac_problem* p, int nbm, int nbn, int grid, const int2** work, const int** starts)
+template <int T, bool TF32, int TN>
+goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, int B, int kc,
+                      const void* qt, double* part)
 {
-    return tc_schedule_into(p->sched, p->sched_key, p->sched_tiles, nbm, nbn, grid, work, starts);
-}
-
-template <int T, bool TF32>
-goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, const void* qt,
-                      double* part)
-{
-    using Cfg = TcCfg<T>;
-    auto kern = k_score_tc<T, TF32>;
+    using Cfg = TcCfg<T, TN>;
+    auto kern = k_score_tc<T, TF32, TN>;
     static std::atomic<uint64_t> attr_done{0};
     {
         goac_status rc0 = smem_attr_once((const void*)kern, Cfg::SMEM, attr_done, p->ctx->device);
         if (rc0) return rc0;
     }
     const int ld = p->Nv_pad;
-    const int nkb = TF32 ? ld / 32 : ld / 64;
-    const int nbm = ld / TC_M, nbn = Bpad / TC_N;
-    const int grid = std::min(nbm * nbn, p->ctx->num_sms);
-    const int2* work = nullptr;
+    const int nbm = ld / TC_M, nbn = (B + TN - 1) / TN;
+    const int2 cnt = tc_tile_count(nbm, nbn, 1, kc);
+    const int grid = std::min(cnt.x, p->ctx->num_sms);
+    const TcTile* work = nullptr;
     const int* starts = nullptr;
-    goac_status rc = tc_schedule(p, nbm, nbn, grid, &work, &starts);
+    goac_status rc = tc_schedule(p->sched, nbm, nbn, 1, kc, TF32 ? 4 : 2, grid, &work, &starts, nullptr);
     if (rc) return rc;
     goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
-    goac::launch_pdl(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, nkb, ld, qt, ld, part, Bpad,
-                 p->ctx->d_err);
+    goac::launch_pdl(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, ld, qt, ld, part, Bpad,
+                     p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_score_tc");
+    return GOAC_OK;
+}
+
+template <int TN>
+goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, int B, int kc,
+                         double* part, const double* lin, double* E_out)
+{
+    using Cfg = ExCfg<TN>;
+    auto kern = k_score_exact<TN>;
+    static std::atomic<uint64_t> attr_done{0};
+    goac_status rc = smem_attr_once((const void*)kern, Cfg::SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
+    const int ld = p->Nv_pad, T = p->dig_T;
+    const int nbm = ld / TC_M, nbn = (B + TN - 1) / TN;
+    const int2 cnt = tc_tile_count(nbm, nbn, T, kc);
+    const int grid = std::min(cnt.x, p->ctx->num_sms);
+    const TcTile* work = nullptr;
+    const int* starts = nullptr;
+    const int* pslot = nullptr;
+    rc = tc_schedule(p->sched_ex, nbm, nbn, T, kc, 2, grid, &work, &starts, &pslot);
+    if (rc) return rc;
+    {
+        goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
+        goac::launch_pdl(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, ld, T,
+                         (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+        GOAC_LAUNCH_CHECK("k_score_exact");
+    }
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, p->ctx->stream, (const double*)part, nbm, pslot,
+                     (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
+    GOAC_LAUNCH_CHECK("k_finish_exact");
     return GOAC_OK;
 }
 
@@ -1290,7 +1383,7 @@ static goac_status prepare_exact(goac_problem* p)
     return build_digits(p, true, &p->J_dig, &p->dig_exp);
 }
 
-goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, double* phi_out)
+goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_out, void* phi_out, bool phi_f32)
 {
     if (!p->J_dig_full) {
         goac_status rc = build_digits(p, false, &p->J_dig_full, &p->dig_exp_full);
@@ -1322,11 +1415,26 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
                      (int*)p->phi_dig.ptr, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_phi_exact");
     }
-    goac::launch(k_phi_exact_finish, B, 256, 0, st, (const int*)p->phi_dig.ptr, Bpad, ld, p->Nv,
-                 (const int*)p->dig_exp_full, p->dig_kq, p->dig_r, T, (const double*)p->phifix, species,
-                 (const double*)p->z_dev, p->E_const, phi_out, E_out);
+    if (phi_f32)
+        goac::launch(k_phi_exact_finish<float>, B, 256, 0, st, (const int*)p->phi_dig.ptr, Bpad, ld, p->Nv,
+                     (const int*)p->dig_exp_full, p->dig_kq, p->dig_r, T, (const double*)p->phifix, species,
+                     (const double*)p->z_dev, p->E_const, (float*)phi_out, E_out);
+    else
+        goac::launch(k_phi_exact_finish<double>, B, 256, 0, st, (const int*)p->phi_dig.ptr, Bpad, ld, p->Nv,
+                     (const int*)p->dig_exp_full, p->dig_kq, p->dig_r, T, (const double*)p->phifix, species,
+                     (const double*)p->z_dev, p->E_const, (double*)phi_out, E_out);
     GOAC_LAUNCH_CHECK("k_phi_exact_finish");
     return GOAC_OK;
+}
+
+// Tile shape of the scoring kernels for (precision, padded batch): the one
+// goac_score_autotune or goac_score_set_shape stored, else 256 configurations
+// per tile and whole panel ranges.
+static void pick_shape(const goac_problem* p, int precision, int Bpad, int* TN, int* kc)
+{
+    const auto it = p->tile_shape.find(std::make_pair(precision, Bpad));
+    *TN = it != p->tile_shape.end() ? it->second.first : TC_N;
+    *kc = it != p->tile_shape.end() ? it->second.second : 0;
 }
 
 static goac_status score_exact(goac_problem* p, const int8_t* species, int B, double* E_out)
@@ -1336,40 +1444,39 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     const int ld = p->Nv_pad;
     const int T = p->dig_T;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
-    const int nbm = ld / TC_M, nbn = Bpad / TC_N;
+    const int nbm = ld / TC_M;
+    int TN = 0, kc = 0;
+    pick_shape(p, GOAC_PREC_EXACT, Bpad, &TN, &kc);
+    const int nslots = tc_tile_count(nbm, (B + TN - 1) / TN, T, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * 2);
-    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nbm * T * Bpad + Bpad));
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * T * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
     double* part = (double*)p->partial.ptr;
-    double* lin = p->has_fixed ? part + (size_t)nbm * T * Bpad : nullptr;
+    double* lin = p->has_fixed ? part + (size_t)nslots * T * Bpad : nullptr;
     goac::launch(k_make_qt<__half>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
                  (const double*)p->z_dev, ld, (__half*)p->qt.ptr,
                  (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
     CUtensorMap ma, mb;
     rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TC_N);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TN);
     if (rc) return rc;
-    static std::atomic<uint64_t> attr_done{0};
-    rc = smem_attr_once((const void*)k_score_exact, EX_SMEM, attr_done, p->ctx->device);
-    if (rc) return rc;
-    const int grid = std::min(nbm * nbn * T, p->ctx->num_sms);
-    const int2* work = nullptr;
-    const int* starts = nullptr;
-    // tiles (I, n * T + t): the LPT schedule sees T times as many configuration blocks
-    rc = tc_schedule_into(p->sched_ex, p->sched_ex_key, p->sched_ex_tiles, nbm, nbn * T, grid, &work, &starts);
-    if (rc) return rc;
-    {
-        KTimer kt(p->ctx, KID_SCORE_TC, st);
-        goac::launch_pdl(k_score_exact, grid, 192, EX_SMEM, st, ma, mb, work, starts, ld / 64, ld, T,
-                         (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
-        GOAC_LAUNCH_CHECK("k_score_exact");
+    if (TN == TC_NS) return launch_exact<TC_NS>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
+    return launch_exact<TC_N>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
+}
+
+template <int TN>
+static goac_status launch_split(goac_problem* p, int precision, const CUtensorMap& ma, const CUtensorMap& mb,
+                                int Bpad, int B, int kc, double* part)
+{
+    switch (precision) {
+        case GOAC_PREC_TF32: return launch_tc<1, true, TN>(p, ma, mb, Bpad, B, kc, p->qt.ptr, part);
+        case GOAC_PREC_TF32X2: return launch_tc<2, true, TN>(p, ma, mb, Bpad, B, kc, p->qt.ptr, part);
+        case GOAC_PREC_BF16X2: return launch_tc<2, false, TN>(p, ma, mb, Bpad, B, kc, p->qt.ptr, part);
+        case GOAC_PREC_BF16X3: return launch_tc<3, false, TN>(p, ma, mb, Bpad, B, kc, p->qt.ptr, part);
+        default: return fail(GOAC_ERR_INVALID_ARG, "score_tc: bad precision");
     }
-    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, st, (const double*)part, nbm, (const int*)p->dig_exp,
-                     Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, (const double*)lin, E_out);
-    GOAC_LAUNCH_CHECK("k_finish_exact");
-    return GOAC_OK;
 }
 
 goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precision, double* E_out)
@@ -1381,11 +1488,14 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     const int ld = p->Nv_pad;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int eb = tf32 ? 4 : 2;
+    int TN = 0, kc = 0;
+    pick_shape(p, precision, Bpad, &TN, &kc);
+    const int nslots = tc_tile_count(ld / TC_M, (B + TN - 1) / TN, 1, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * eb);
-    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)(ld / TC_M) * Bpad + Bpad));
+    if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
-    double* lin = p->has_fixed ? (double*)p->partial.ptr + (size_t)(ld / TC_M) * Bpad : nullptr;
+    double* lin = p->has_fixed ? (double*)p->partial.ptr + (size_t)nslots * Bpad : nullptr;
     {
         const double* pf = p->has_fixed ? p->phifix : nullptr;
         if (tf32)
@@ -1401,20 +1511,94 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     void* abase = tf32 ? (void*)p->J_tf32 : (void*)p->J_bf16;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     rc = make_map(&ma, abase, dt, eb, ld, (long)terms_alloc * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, dt, eb, ld, Bpad, ld, TC_N);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, dt, eb, ld, Bpad, ld, TN);
     if (rc) return rc;
     double* part = (double*)p->partial.ptr;
-    switch (precision) {
-        case GOAC_PREC_TF32: rc = launch_tc<1, true>(p, ma, mb, Bpad, p->qt.ptr, part); break;
-        case GOAC_PREC_TF32X2: rc = launch_tc<2, true>(p, ma, mb, Bpad, p->qt.ptr, part); break;
-        case GOAC_PREC_BF16X2: rc = launch_tc<2, false>(p, ma, mb, Bpad, p->qt.ptr, part); break;
-        case GOAC_PREC_BF16X3: rc = launch_tc<3, false>(p, ma, mb, Bpad, p->qt.ptr, part); break;
-        default: return fail(GOAC_ERR_INVALID_ARG, "score_tc: bad precision");
-    }
+    rc = TN == TC_NS ? launch_split<TC_NS>(p, precision, ma, mb, Bpad, B, kc, part)
+                     : launch_split<TC_N>(p, precision, ma, mb, Bpad, B, kc, part);
     if (rc) return rc;
-    goac::launch_pdl(k_finish_tc, (B + 255) / 256, 256, 0, st, part, ld / TC_M, Bpad, B, p->E_const, lin, E_out);
+    goac::launch_pdl(k_finish_tc, (B + 255) / 256, 256, 0, st, part, nslots, Bpad, B, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_tc");
     return GOAC_OK;
 }
 
+// Tensor-core forms whose tile shape can be chosen.
+static bool shaped_form(int precision)
+{
+    return precision == GOAC_PREC_TF32 || precision == GOAC_PREC_TF32X2 || precision == GOAC_PREC_BF16X2 ||
+           precision == GOAC_PREC_BF16X3 || precision == GOAC_PREC_EXACT;
+}
+
 }  // namespace goac
+
+extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, int32_t B, int32_t tile_n,
+                                            int32_t ksplit)
+{
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: NULL problem");
+    if (!goac::shaped_form(precision))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: not a tensor-core form");
+    if (B < 1 || B > GOAC_MAX_BATCH || !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 ||
+        ksplit > 65535)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: B >= 1, tile_n 0, 128 or 256, ksplit 0..65535");
+    const int Bpad = ((B + 255) / 256) * 256;
+    const auto key = std::make_pair((int)precision, Bpad);
+    if (tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
+    else p->tile_shape[key] = std::make_pair(tile_n == 0 ? 256 : (int)tile_n, (int)ksplit);
+    return GOAC_OK;
+}
+
+extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* species_dev, int32_t B, int32_t precision,
+                                           int32_t* tile_n_out, int32_t* ksplit_out, double* ms_out)
+{
+    if (!p || !species_dev || B < 1 || B > GOAC_MAX_BATCH)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_autotune: bad argument");
+    if (!goac::shaped_form(precision))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_autotune: not a tensor-core form");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    cudaStream_t st = p->ctx->stream;
+    double* E = nullptr;
+    GOAC_CUDA(cudaMalloc(&E, sizeof(double) * (size_t)B));
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int nbm = p->Nv_pad / 128;
+    const int Bpad = ((B + 255) / 256) * 256;
+    const auto key = std::make_pair((int)precision, Bpad);
+    const int tns[2] = {256, 128}, kcs[5] = {0, 16, 8, 4, 2};
+    int best_tn = 0, best_kc = 0;
+    float best = 0.0f;
+    goac_status rc = GOAC_OK;
+    for (int i = 0; i < 2 && !rc; ++i)
+        for (int j = 0; j < 5 && !rc; ++j) {
+            if (kcs[j] >= nbm) continue;                 // the same as whole panel ranges
+            p->tile_shape[key] = std::make_pair(tns[i], kcs[j]);
+            rc = goac_score(p, species_dev, B, precision, E);     // schedule, operands, warm-up
+            if (rc) break;
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3 && !rc; ++r) rc = goac_score(p, species_dev, B, precision, E);
+            cudaEventRecord(b, st);
+            if (rc) break;
+            cudaEventSynchronize(b);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (best_tn == 0 || ms < best) {
+                best_tn = tns[i];
+                best_kc = kcs[j];
+                best = ms;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(st);
+    cudaFree(E);
+    if (rc) {
+        p->tile_shape.erase(key);
+        return rc;
+    }
+    p->tile_shape[key] = std::make_pair(best_tn, best_kc);
+    if (tile_n_out) *tile_n_out = best_tn;
+    if (ksplit_out) *ksplit_out = best_kc;
+    if (ms_out) *ms_out = best / 3.0;
+    rc = goac::check_device_error(p->ctx);
+    return rc;
+}

@@ -1,0 +1,105 @@
+"""Tile shapes of the tensor-core scoring kernels and their autotuner.
+
+A tile covers 128 sites x 128 or 256 configurations, over the whole column
+range of its row panel or over chunks of it (each chunk adds a partial row-dot
+sum).  The exact integer-digit form must give the same energies bit for bit in
+every shape (its chunk partials are exact integers added exactly); the split
+forms must stay within their derived bound of the oracle in every shape; the
+autotuner's choice must be one of the shapes and be used afterwards."""
+import numpy as np
+import pytest
+import torch
+
+import goac_synth as synth
+import oracle
+from gpu_common import build_pair, form_tolerance, gpu_problem
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(256, 0), (128, 0), (256, 16), (128, 8), (256, 4), (128, 2), (256, 1)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2409_08808_gb300 as g
+    return g.Context(0)
+
+
+@pytest.fixture(scope="module")
+def cubic(ctx):
+    import paper_2409_08808_gb300 as g
+    prob = synth.random_cubic_problem(n_side=16)
+    frac = torch.tensor(prob.frac, device="cuda")
+    Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    return prob, gpu_problem(ctx, prob, Jg), Jg.cpu().numpy()
+
+
+@pytest.mark.parametrize("B", [1000, 1024])
+def test_exact_form_identical_in_every_shape(cubic, B):
+    prob, gp, Jc = cubic
+    pop = torch.tensor(synth.random_population(prob, B, 21), device="cuda")
+    gp.score_set_shape(B, "exact", 0, 0)
+    ref = gp.score(pop, "exact").clone()
+    for tn, kc in SHAPES:
+        gp.score_set_shape(B, "exact", tn, kc)
+        E = gp.score(pop, "exact")
+        assert torch.equal(E, ref), (tn, kc)
+    gp.score_set_shape(B, "exact", 0, 0)
+    rows = np.array([0, 1, B // 2, B - 1])
+    Eo = oracle.score(Jc, prob.site_class, prob.fixed_q, prob.z, pop.cpu().numpy()[rows])
+    assert np.max(np.abs(ref.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
+
+
+@pytest.mark.parametrize("form", ["bf16x2", "bf16x3", "tf32x2"])
+def test_split_forms_within_bound_in_every_shape(ctx, form):
+    """Layered 12x12x1 cell (Nv = 864, seven 128-row panels), a ragged population."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.layered_problem()
+    frac = torch.tensor(prob.frac, device="cuda")
+    Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, Jg)
+    Jc = Jg.cpu().numpy()
+    B = 1061
+    pop_np = synth.random_population(prob, B, 5)
+    pop = torch.tensor(pop_np, device="cuda")
+    rows = np.array([0, 127, 128, 255, 256, 700, 1023, 1024, B - 1])
+    Eo = oracle.score(Jc, prob.site_class, prob.fixed_q, prob.z, pop_np[rows])
+    q = [oracle.config_charges(prob.site_class, prob.fixed_q, prob.z, pop_np[r]) for r in rows]
+    R = np.array([np.sqrt(((qq[:, None] * Jc * qq[None, :]) ** 2).sum()) for qq in q])
+    tol = form_tolerance(form, R, prob.Nv)
+    base = None
+    for tn, kc in SHAPES:
+        gp.score_set_shape(B, form, tn, kc)
+        E = gp.score(pop, form).cpu().numpy()
+        assert np.all(np.abs(E[rows] - Eo) <= tol), (tn, kc)
+        if base is None:
+            base = E
+        elif kc == 0:
+            # the same k-order per tile: only the configuration tiling differs
+            assert np.array_equal(E, base), (tn, kc)
+    gp.score_set_shape(B, form, 0, 0)
+
+
+@pytest.mark.parametrize("form,B", [("exact", 512), ("bf16x3", 1024), ("bf16x2", 4096)])
+def test_autotuner_choice(cubic, form, B):
+    prob, gp, _ = cubic
+    pop = torch.tensor(synth.random_population(prob, B, 3), device="cuda")
+    gp.score_set_shape(B, form, 0, 0)
+    ref = gp.score(pop, form).clone()
+    tn, kc, ms = gp.score_autotune(pop, form)
+    assert tn in (128, 256) and kc in (0, 16, 8, 4, 2) and ms > 0
+    E = gp.score(pop, form)
+    if form == "exact" or kc == 0:
+        assert torch.equal(E, ref)
+    else:
+        assert (E - ref).abs().max().item() <= 1e-6 * ref.abs().max().item()
+    gp.score_set_shape(B, form, 0, 0)
+
+
+def test_set_shape_rejects_bad_shapes(cubic):
+    import paper_2409_08808_gb300 as g
+    _, gp, _ = cubic
+    for args in [(0, "exact", 128, 0), (16, "exact", 64, 0), (16, "exact", 128, -1), (16, "f64", 128, 0),
+                 (16, "f32", 0, 4)]:
+        with pytest.raises(g.GoacError):
+            gp.score_set_shape(*args)

@@ -64,10 +64,11 @@ def test_mc_statistics_and_patience_from_replay():
     rep = _replay(J, prob, start, kT, nsteps, seed)
     for c, (noop, E_after) in enumerate(rep):
         assert full["n_noop"][c] == noop.sum()
-        # best step: first step whose energy is below every earlier one (and the start)
+        # best step: the last step whose energy undercut every earlier one (and the start) by more than
+        # the 1e-9 eV tie
         run_min, t_best = E0[c], -1
         for t, e in enumerate(E_after):
-            if e < run_min:
+            if e < run_min - 1e-9:
                 run_min, t_best = e, t
         assert full["best_step"][c] == t_best and full["bestE"][c] == run_min
         # patience: improvements by more than 1e-9 eV; stop after the first t with t - t_imp >= patience
