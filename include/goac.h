@@ -473,6 +473,19 @@ goac_status goac_ga_run_populations(goac_problem* prob, int8_t* pop_dev, double*
                                     int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32, uint64_t seed, uint32_t gen0,
                                     int32_t precision);
 
+/* GA populations of several problems of different sizes in one launch per   *
+ * step (the batching form; the paper compares independent runs of its        *
+ * heuristics): problem i evolves the population pop_dev[i] (P[i] x Nv_i,     *
+ * in/out) with energies E_dev[i] (P[i], out) exactly as goac_ga_run with key *
+ * seed + i and the common n_gen, n_elite (<= every P[i]), p_mut_u32, gen0.   *
+ * Each generation's select, elite, children and rescoring kernels serve all  *
+ * populations at once.  precision: GOAC_PREC_F64_INCR (incremental FP64      *
+ * rescoring) only.  Every problem belongs to ctx and appears once; host      *
+ * arrays of length n_probs.                                                  */
+goac_status goac_batch_ga_run(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs, int8_t* const* pop_dev,
+                              double* const* E_dev, const int32_t* P, int32_t n_gen, int32_t n_elite,
+                              uint32_t p_mut_u32, uint64_t seed, uint32_t gen0, int32_t precision);
+
 /* ------------------------------------------------------------------------ *
  * Relaxed occupations (differentiable form; the paper's descent is discrete,*
  * SI Gradient Descent).  logits_dev: B x Nv x S float; p = softmax over the *

@@ -499,6 +499,23 @@ def batch_mc_run(ctx: Context, problems, species, kT, n_steps: int, seed: int, s
     return E, bE
 
 
+def batch_ga_run(ctx: Context, problems, pops, n_gen: int, n_elite: int, p_mut_u32: int, seed: int, gen0: int = 0,
+                 precision="f64_incr"):
+    """GA populations of several problems (pops[i]: P_i x Nv_i int8, in place) in one
+    launch per step (goac_batch_ga_run); population i evolves as ga_run with seed + i.
+    Returns the final energies (list of tensors)."""
+    n = len(problems)
+    dev = f"cuda:{ctx.device}"
+    E = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in pops]
+    PR = (C.c_void_p * n)(*[p.handle.value for p in problems])
+    SP = (C.c_void_p * n)(*[s.data_ptr() for s in pops])
+    EE = (C.c_void_p * n)(*[t.data_ptr() for t in E])
+    PP = (C.c_int32 * n)(*[s.shape[0] for s in pops])
+    _check(lib.goac_batch_ga_run(ctx.handle, PR, n, SP, EE, PP, int(n_gen), int(n_elite), int(p_mut_u32), int(seed),
+                                 int(gen0), _prec(precision)), "goac_batch_ga_run")
+    return E
+
+
 def batch_mc_autotune(ctx: Context, problems, species, kT, probe_steps: int = 256, precision="f64"):
     """Fastest chains-per-CTA for batch_mc_run on these problems (goac_batch_mc_autotune)."""
     n = len(problems)

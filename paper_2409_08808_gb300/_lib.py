@@ -81,6 +81,7 @@ SIGNATURES = {
     "goac_ga_run": (_st, [_p, _p, _p, _i32, _i32, _i32, _u32, _u64, _u32, _i32]),
     "goac_ga_run_ex": (_st, [_p, _p, _p, _i32, C.POINTER(GaParams), _u64, _i32, _p, _p, C.POINTER(GaStats)]),
     "goac_ga_run_populations": (_st, [_p, _p, _p, _i32, _i32, _i32, _i32, _u32, _u64, _u32, _i32]),
+    "goac_batch_ga_run": (_st, [_p, _p, _i32, _p, _p, _p, _i32, _i32, _u32, _u64, _u32, _i32]),
     "goac_mc_autotune": (_st, [_p, _p, _i32, _p, _i64, _i32, _p, _p, _p]),
     "goac_mc_set_shape": (_st, [_p, _i32, _i32, _i32]),
     "goac_energy_grad": (_st, [_p, _p, _i32, _d, _i32, _p, _p]),

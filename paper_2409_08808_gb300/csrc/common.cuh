@@ -83,6 +83,7 @@ struct goac_ctx {
     DevBuf batch_desc;
     DevBuf batch_items;
     DevBuf batch_counter;
+    DevBuf ga_dev;                 // batched GA: device copy of the population entries
 };
 
 // A persistent scoring kernel's tile schedule on the device (tiles, per-CTA
@@ -126,7 +127,8 @@ struct goac_problem {
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
     DevBuf ga_incr;            // incremental GA rescoring: 2 x P x Nv potentials, P x 2 parents
-    DevBuf ga_track;           // per-population run-level stop state and final min / max
+    DevBuf ga_buf;             // GA: second population buffer, fitness sums, elite, stop states, parents
+    DevBuf ga_dev;             // GA: device copy of the population entries
     int mc_tuned[2][2] = {{0, 0}, {0, 0}};   // [FP64, FP32]: autotuned {warps per chain, chains per CTA}, 0 = none
     // persistent tensor-core schedules (device copies) for the last shapes
     TcSched sched, sched_ex;

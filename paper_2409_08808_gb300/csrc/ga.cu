@@ -1,8 +1,10 @@
 // Genetic algorithm (SI, Genetic Algorithm: roulette-wheel selection,
 // crossover by random atom swaps that take half of the differences between
 // the parents, random mutation, elitism), one generation per call and a
-// driver that rescores every child between generations, for R independent
-// populations of P at once (population r: rows r P .., Philox key seed + r).
+// driver that rescores every child between generations.  Every launch serves
+// a list of populations (GaEntry): R independent populations of one problem
+// (population r: Philox key seed + r), or one population for each of several
+// problems of different sizes (the batching form).
 //
 // Device layout (one block or warp range per population where it says so):
 //   k_ga_select   one block per population: E_min, E_max, the patience state of
@@ -12,7 +14,8 @@
 //                 integer search.
 //   k_ga_rank     ranks by (E, index) within the population to pick the elite
 //                 (O(P^2) comparisons, one warp per individual).
-//   k_ga_children one warp per child: parents by binary search of the running
+//   k_ga_children one warp per child (a block's warps all belong to one
+//                 population): parents by binary search of the running
 //                 sum, crossover in shared memory (32 sites at a time, the
 //                 chunk's child values and candidate mask in registers; the
 //                 draws of all remaining candidates of a chunk evaluated at
@@ -24,6 +27,8 @@
 //   k_ga_incr     incremental FP64 rescoring, one block per child: the
 //                 potential and energy from the nearer parent's potential and
 //                 the J rows of the sites where the child differs from it.
+// Populations and potentials are double-buffered: generation g reads buffer
+// g & 1 and writes the other, so no copy is needed between generations.
 #include <algorithm>
 #include <chrono>
 #include <utility>
@@ -44,20 +49,74 @@ struct GaTrack {
     int stall, best_gen, stop, gens;
 };
 
+// One population: its problem's data, its buffers and its place in the
+// launches (child0: its first individual in the concatenation of all the
+// launch's populations; block0: its first block of the children kernel).
+struct GaEntry {
+    const int32_t* vclass;
+    const int32_t* cls_start;
+    const int32_t* cls_pos;
+    const int32_t* cls_rank;
+    const uint32_t* wprefix;
+    const double* J;          // J_vv, rows of ld doubles (incremental rescoring)
+    const double* z;          // 64
+    const double* phifix;     // Nv
+    int8_t* pop[2];           // P x Nv each, double-buffered
+    double* phi[2];           // P x Nv each (incremental rescoring), double-buffered
+    double* E;                // P: energies of the current population
+    unsigned long long* pre;  // P: running sum of the integer fitness
+    unsigned long long* ftot; // 1
+    double* mm;               // 2: E_min, E_max
+    int* elite;               // n_elite
+    GaTrack* track;           // 1, or null
+    int32_t* parents;         // P x 2, or null
+    int32_t* nswap;           // P x 2, or null
+    uint64_t key;
+    double E_const;
+    uint32_t wtotal;
+    int Nv, S, ncls, nmovable, only_movable, ld, P, n_elite, block0;
+    long child0;
+};
+
+// The entry holding global index x of a prefix field (child0 or block0): the
+// last entry whose start is <= x.
+__device__ __forceinline__ int entry_of_child(const GaEntry* __restrict__ e, int n, long x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e[mid].child0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int entry_of_block(const GaEntry* __restrict__ e, int n, int x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e[mid].block0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // One block per population: E_min / E_max, then (tracking) the patience
 // update for the population as it stands after g generations, then (fitness)
 // F_b = floor((Emax - E_b) / (Emax - Emin) 2^24) and its inclusive running
 // sum in index order as exact 64-bit integers.
-__global__ void __launch_bounds__(1024) k_ga_select(const double* __restrict__ E, int P, double* __restrict__ mm,
-                                                    unsigned long long* __restrict__ pre,
-                                                    unsigned long long* __restrict__ ftot, int fitness,
-                                                    GaTrack* __restrict__ track, int g, int patience)
+__global__ void __launch_bounds__(1024) k_ga_select(const GaEntry* __restrict__ ents, int fitness, int g,
+                                                    int patience)
 {
     __shared__ double smin[1024], smax[1024];
     __shared__ unsigned long long warp_tot[32];
     __shared__ unsigned long long carry;
-    E += (long)blockIdx.x * P;                // one block per population
-    mm += 2 * blockIdx.x;
+    const GaEntry& en = ents[blockIdx.x];     // one block per population
+    const double* __restrict__ E = en.E;
+    const int P = en.P;
+    double* mm = en.mm;
+    GaTrack* track = en.track;
     double lo = E[0], hi = E[0];
     for (int b = threadIdx.x; b < P; b += blockDim.x) {
         lo = fmin(lo, E[b]);
@@ -78,7 +137,7 @@ __global__ void __launch_bounds__(1024) k_ga_select(const double* __restrict__ E
         mm[0] = emin;
         mm[1] = emax;
         if (track) {
-            GaTrack& tr = track[blockIdx.x];
+            GaTrack& tr = *track;
             if (g == 0) {
                 tr.ref = emin;
                 tr.best = emin;
@@ -100,8 +159,8 @@ __global__ void __launch_bounds__(1024) k_ga_select(const double* __restrict__ E
     }
     if (!fitness) return;
     __syncthreads();
-    pre += (long)blockIdx.x * P;
-    ftot += blockIdx.x;
+    unsigned long long* pre = en.pre;
+    unsigned long long* ftot = en.ftot;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int base = 0; base < P; base += blockDim.x) {
         const int b = base + threadIdx.x;
@@ -136,43 +195,24 @@ __global__ void __launch_bounds__(1024) k_ga_select(const double* __restrict__ E
 // Elite selection: the rank of individual i by (E, index) is the number of j
 // with E_j < E_i, or E_j == E_i and j < i; one warp per i (lanes stride over
 // j, warp sum), so the O(P^2) comparisons spread over P warps.
-__global__ void k_ga_rank(const double* __restrict__ E, int R, int P, int k, int* __restrict__ sel)
+__global__ void k_ga_rank(const GaEntry* __restrict__ ents, int n_ents, long total)
 {
     const long gi = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (gi >= (long)R * P) return;            // whole warps leave together
-    const int r = (int)(gi / P), i = (int)(gi % P);
-    E += (long)r * P;                         // individual i of population r
-    sel += (long)r * k;
+    if (gi >= total) return;                  // whole warps leave together
+    const GaEntry& en = ents[entry_of_child(ents, n_ents, gi)];
+    const int i = (int)(gi - en.child0);      // individual i of this population
+    if (en.n_elite == 0) return;
+    const double* E = en.E;
     const double ei = E[i];
     int rank = 0;
-    for (int j = lane; j < P; j += 32) {
+    for (int j = lane; j < en.P; j += 32) {
         const double ej = E[j];
         rank += (ej < ei) || (ej == ei && j < i);
     }
     rank = __reduce_add_sync(0xffffffffu, rank);
-    if (lane == 0 && rank < k) sel[rank] = i;
+    if (lane == 0 && rank < en.n_elite) en.elite[rank] = i;
 }
-
-struct GaArgs {
-    const int8_t* pop;
-    int8_t* children;
-    const unsigned long long* pre;
-    const unsigned long long* ftot;
-    const int* elite;
-    const GaTrack* track;     // per population, or null: a finished population is copied unchanged
-    int32_t* parents;
-    int32_t* nswap;
-    const int32_t* vclass;
-    const int32_t* cls_start;
-    const int32_t* cls_pos;
-    const int32_t* cls_rank;
-    const uint32_t* wprefix;
-    int* err;
-    uint64_t seed;
-    uint32_t wtotal, p_mut, gen;
-    int R, P, Nv, S, n_elite, ncls, nmovable, only_movable;   // R populations of P
-};
 
 __device__ __forceinline__ int lower_bound_gt(const unsigned long long* pre, int P, unsigned long long t)
 {
@@ -201,50 +241,53 @@ __host__ __device__ inline size_t ga_slot_bytes(int Nv, int S)
     return 2 * sp + (((size_t)S * words * 4 + 15) & ~(size_t)15);
 }
 
-__global__ void k_ga_children(GaArgs a)
+// Children of generation `gen` (which reads pop[parity] of every population
+// and writes pop[parity ^ 1]); the warps of a block all serve the population
+// whose block range holds the block.
+__global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int wpb, uint32_t gen, int parity,
+                              uint32_t p_mut, int* err)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    const GaEntry& a = ents[entry_of_block(ents, n_ents, blockIdx.x)];
     const int Nv = a.Nv;
     // block-wide copy of the class positions (site of class position p), then one slot per warp
     int32_t* cpos = (int32_t*)smem;
     for (int q = threadIdx.x; q < Nv; q += blockDim.x) cpos[q] = a.cls_pos[q];
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long cg = (long)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (cg >= (long)a.R * a.P) return;
-    // child c of population r: the population's own parents, fitness sums and
-    // elite, Philox key seed + r
-    const int r = (int)(cg / a.P), c = (int)(cg % a.P);
-    const int8_t* popr = a.pop + (long)r * a.P * Nv;
+    const int c = (blockIdx.x - a.block0) * wpb + wib;
+    if (c >= a.P) return;
+    // child c: the population's own parents, fitness sums and elite, its own Philox key
+    const int8_t* popr = a.pop[parity];
     const int W = (Nv + 31) / 32;
     uint8_t* base = smem + ga_cpos_bytes(Nv) + ga_slot_bytes(Nv, a.S) * wib;
     int8_t* ch = (int8_t*)base;
     int8_t* pb = ch + (((size_t)Nv + 15) & ~(size_t)15);
     uint32_t* mis = (uint32_t*)(pb + (((size_t)Nv + 15) & ~(size_t)15));
-    int8_t* out = a.children + cg * Nv;
+    int8_t* out = a.pop[parity ^ 1] + (long)c * Nv;
 
-    if (a.track && a.track[r].stop) {         // finished (patience): the child is the individual itself
+    if (a.track && a.track->stop) {           // finished (patience): the child is the individual itself
         for (int w = lane; w < Nv; w += 32) out[w] = popr[(long)c * Nv + w];
         if (lane == 0) {
-            if (a.parents) a.parents[2 * cg] = a.parents[2 * cg + 1] = c;
-            if (a.nswap) a.nswap[2 * cg] = a.nswap[2 * cg + 1] = 0;
+            if (a.parents) a.parents[2 * c] = a.parents[2 * c + 1] = c;
+            if (a.nswap) a.nswap[2 * c] = a.nswap[2 * c + 1] = 0;
         }
         return;
     }
     if (c < a.n_elite) {
-        const int src = a.elite[(long)r * a.n_elite + c];
+        const int src = a.elite[c];
         for (int w = lane; w < Nv; w += 32) out[w] = popr[(long)src * Nv + w];
         if (lane == 0) {
-            if (a.parents) a.parents[2 * cg] = a.parents[2 * cg + 1] = src;
-            if (a.nswap) a.nswap[2 * cg] = a.nswap[2 * cg + 1] = 0;
+            if (a.parents) a.parents[2 * c] = a.parents[2 * c + 1] = src;
+            if (a.nswap) a.nswap[2 * c] = a.nswap[2 * c + 1] = 0;
         }
         return;
     }
-    const uint64_t key = a.seed + (uint64_t)r;
+    const uint64_t key = a.key;
     const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
-    const uint4 x = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 2u), k0, k1);
-    const unsigned long long* prer = a.pre + (long)r * a.P;
-    const unsigned long long ftot = a.ftot[r];
+    const uint4 x = goacd::philox(make_uint4(0u, gen, (uint32_t)c, 2u), k0, k1);
+    const unsigned long long* prer = a.pre;
+    const unsigned long long ftot = *a.ftot;
     const unsigned long long xa = ((unsigned long long)x.x << 32) | x.y;
     const unsigned long long xb = ((unsigned long long)x.z << 32) | x.w;
     const int A = lower_bound_gt(prer, a.P, __umul64hi(xa, ftot));
@@ -288,7 +331,7 @@ __global__ void k_ga_children(GaArgs a)
             my_rng = (uint32_t)a.cls_start[k] | ((uint32_t)a.cls_start[k + 1] << 16);
         }
         if (__any_sync(0xffffffffu, bad)) {         // not a species of the problem
-            if (lane == 0) goacd::report(a.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
+            if (lane == 0) goacd::report(err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, c);
             return;
         }
         uint32_t m = __ballot_sync(0xffffffffu, il < Nv && ((my_bcr ^ (my_bcr >> 8)) & 0xffu) != 0u);
@@ -299,7 +342,7 @@ __global__ void k_ga_children(GaArgs a)
             if (kc + 32u > cache_hi) {
                 cache_lo = kc & ~3u;
                 cache_hi = cache_lo + 128u;
-                blk = goacd::philox(make_uint4((cache_lo >> 2) + (uint32_t)lane, a.gen, (uint32_t)c, 3u), k0, k1);
+                blk = goacd::philox(make_uint4((cache_lo >> 2) + (uint32_t)lane, gen, (uint32_t)c, 3u), k0, k1);
             }
             const uint32_t d = kc + (uint32_t)__popc(m & ((1u << lane) - 1u));
             const int src = (int)((d >> 2) - (cache_lo >> 2)) & 31;
@@ -339,7 +382,7 @@ __global__ void k_ga_children(GaArgs a)
                 }
             }
             if (pp < 0) {
-                if (lane == 0) goacd::report(a.err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
+                if (lane == 0) goacd::report(err, GOAC_ERR_INTERNAL, goac::SITE_GA, c);
                 return;
             }
             const int j = cpos[pp];
@@ -360,8 +403,8 @@ __global__ void k_ga_children(GaArgs a)
             ++nsw;
         }
     }
-    const uint4 y = goacd::philox(make_uint4(0u, a.gen, (uint32_t)c, 4u), k0, k1);
-    if (y.x < a.p_mut && a.nmovable > 0) {
+    const uint4 y = goacd::philox(make_uint4(0u, gen, (uint32_t)c, 4u), k0, k1);
+    if (y.x < p_mut && a.nmovable > 0) {
         int k = a.only_movable;
         if (a.nmovable != 1) {
             const uint32_t thr = goacd::draw_below(y.y, a.wtotal);
@@ -389,12 +432,12 @@ __global__ void k_ga_children(GaArgs a)
     for (int w = lane; w < Nv; w += 32) out[w] = ch[w];
     if (lane == 0) {
         if (a.parents) {
-            a.parents[2 * cg] = A;
-            a.parents[2 * cg + 1] = B;
+            a.parents[2 * c] = A;
+            a.parents[2 * c + 1] = B;
         }
         if (a.nswap) {
-            a.nswap[2 * cg] = nsw;
-            a.nswap[2 * cg + 1] = (int32_t)kc;
+            a.nswap[2 * c] = nsw;
+            a.nswap[2 * c + 1] = (int32_t)kc;
         }
     }
 }
@@ -411,42 +454,31 @@ __global__ void k_ga_children(GaArgs a)
 constexpr int GI_THREADS = 256;
 constexpr int GI_R = 4;
 
-struct GaIncrArgs {
-    const int8_t* pop;        // R P x Nv parents (R populations of P)
-    const double* phi_pop;    // R P x Nv
-    const int8_t* kids;       // R P x Nv
-    const int32_t* parents;   // R P x 2, indices within the child's population
-    const double* J;          // J_vv, rows of ld doubles
-    const double* z;          // 64
-    const double* phifix;     // Nv
-    double* phi_kids;         // P x Nv out
-    double* E_kids;           // P out
-    int* err;
-    double E_const;
-    int ld, Nv, P, S;
-};
-
-__global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
+// Children of every population: block = child (population by its child0);
+// reads pop[parity] / phi[parity] (the parents) and pop[parity ^ 1] (the
+// children), writes phi[parity ^ 1] and the energies.
+__global__ void __launch_bounds__(GI_THREADS) k_ga_incr(const GaEntry* __restrict__ ents, int n_ents, int parity,
+                                                        int* err)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    const GaEntry& g = ents[entry_of_child(ents, n_ents, (long)blockIdx.x)];
+    const long c = (long)blockIdx.x - g.child0;   // child c of this population
     double* dq = (double*)smem;               // Nv
     int* idx = (int*)(dq + g.Nv);             // Nv
     __shared__ int wcnt[GI_THREADS / 32][2];
     __shared__ double wsum[GI_THREADS / 32];
-    const long c = blockIdx.x;                // child c of population c / P
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int NW = GI_THREADS / 32;
     const int Nv = g.Nv;
     const int A0 = g.parents[2 * c], B0 = g.parents[2 * c + 1];
     if ((unsigned)A0 >= (unsigned)g.P || (unsigned)B0 >= (unsigned)g.P) {
-        if (tid == 0) goacd::report(g.err, GOAC_ERR_INTERNAL, goac::SITE_GA, (int)c);
+        if (tid == 0) goacd::report(err, GOAC_ERR_INTERNAL, goac::SITE_GA, (int)c);
         return;
     }
-    const long base = c / g.P * g.P;
-    const long A = base + A0, B = base + B0;
-    const int8_t* kid = g.kids + c * Nv;
-    const int8_t* pa = g.pop + A * Nv;
-    const int8_t* pb = g.pop + B * Nv;
+    const long A = A0, B = B0;
+    const int8_t* kid = g.pop[parity ^ 1] + c * Nv;
+    const int8_t* pa = g.pop[parity] + A * Nv;
+    const int8_t* pb = g.pop[parity] + B * Nv;
     // the nearer parent (ties: A)
     int da = 0, db = 0;
     for (int v = tid; v < Nv; v += GI_THREADS) {
@@ -508,7 +540,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         __syncthreads();
     }
     if (__syncthreads_or(bad)) {
-        if (tid == 0) goacd::report(g.err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, (int)c);
+        if (tid == 0) goacd::report(err, GOAC_ERR_INVALID_ARG, goac::SITE_GA, (int)c);
         return;
     }
     double e = 0.0;
@@ -517,7 +549,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
 #pragma unroll
         for (int r = 0; r < GI_R; ++r) {
             const int v = v0 + r * GI_THREADS + tid;
-            acc[r] = v < Nv ? g.phi_pop[par * Nv + v] : 0.0;
+            acc[r] = v < Nv ? g.phi[parity][par * Nv + v] : 0.0;
         }
         for (int t = 0; t < M; ++t) {
             const double d = dq[t];
@@ -532,7 +564,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         for (int r = 0; r < GI_R; ++r) {
             const int v = v0 + r * GI_THREADS + tid;
             if (v < Nv) {
-                g.phi_kids[c * Nv + v] = acc[r];
+                g.phi[parity ^ 1][c * Nv + v] = acc[r];
                 e = fma(g.z[kid[v]], acc[r] + g.phifix[v], e);
             }
         }
@@ -545,7 +577,7 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) s += wsum[w];
-        g.E_kids[c] = s + g.E_const;
+        g.E[c] = s + g.E_const;
     }
 }
 
@@ -553,66 +585,148 @@ __global__ void __launch_bounds__(GI_THREADS) k_ga_incr(GaIncrArgs g)
 
 namespace goac {
 
-// One generation of R independent populations of P (population r: rows r P ..
-// r P + P - 1, Philox key seed + r).
-static goac_status ga_generation_impl(goac_problem* p, const int8_t* pop, const double* E, int R, int P,
-                                      int n_elite, uint32_t p_mut, uint32_t gen, uint64_t seed, int8_t* children,
-                                      int32_t* parents, int32_t* nswap, GaTrack* track = nullptr, int g = 0,
-                                      int patience = 0)
+// The populations of one GA launch sequence: host and device copies of the
+// entries, and the launch geometry of the children and rescoring kernels.
+struct GaLaunch {
+    std::vector<GaEntry> e;
+    std::vector<goac_problem*> prob;   // problem of each entry
+    GaEntry* dev = nullptr;
+    long total = 0;                     // individuals over all entries
+    int wpb = 1, blocks = 0, max_nv = 0;
+    size_t smem_children = 0, smem_incr = 0;
+    bool any_elite = false;
+};
+
+// Entries for R populations of P of problem p in its scratch buffer ga_buf:
+// population r is rows r P .. of pop0 and E (its second buffer pop1, or rows
+// of the scratch when null), Philox key seed + r.  The entries' device copy
+// goes to `devbuf` (the problem's own, or a batch's).
+static goac_status ga_entries(goac_problem* p, int8_t* pop0, int8_t* pop1, double* E, int R, int P, int n_elite,
+                              uint64_t seed, bool incr, bool tracking, int32_t* parents, int32_t* nswap,
+                              GaLaunch& L)
 {
-    goac_ctx* ctx = p->ctx;
-    cudaStream_t st = ctx->stream;
-    const long RP = (long)R * P;
-    const size_t need = sizeof(unsigned long long) * ((size_t)RP + (size_t)R + 2) + 2 * sizeof(double) * (size_t)R +
-                        sizeof(int) * ((size_t)R * n_elite + 4) + 256;
-    goac_status rc = ensure(p->score_tmp, need);
+    const int Nv = p->Nv;
+    const size_t RP = (size_t)R * P;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_pop = pop1 ? 0 : al(RP * Nv), b_pre = al(8 * RP), b_ftot = al(8 * (size_t)R),
+                 b_mm = al(16 * (size_t)R), b_el = al(4 * (size_t)R * (n_elite > 0 ? n_elite : 1)),
+                 b_tr = al(sizeof(GaTrack) * (size_t)R), b_par = (incr && !parents) ? al(8 * RP) : 0;
+    goac_status rc = ensure(p->ga_buf, b_pop + b_pre + b_ftot + b_mm + b_el + b_tr + b_par + 256);
     if (rc) return rc;
-    char* base = (char*)p->score_tmp.ptr;
-    unsigned long long* pre = (unsigned long long*)base;
-    unsigned long long* ftot = pre + RP;
-    double* mm = (double*)(ftot + R + 1);
-    int* elite = (int*)(mm + 2 * (size_t)R);
-    goac::launch(k_ga_select, R, 1024, 0, st, E, P, mm, pre, ftot, 1, track, g, patience);
-    if (n_elite > 0) goac::launch(k_ga_rank, (int)((RP + 7) / 8), 256, 0, st, E, R, P, n_elite, elite);
-    GOAC_LAUNCH_CHECK("ga prep");
-    GaArgs a;
-    a.pop = pop;
-    a.children = children;
-    a.pre = pre;
-    a.ftot = ftot;
-    a.elite = elite;
-    a.track = track;
-    a.parents = parents;
-    a.nswap = nswap;
-    a.vclass = p->vclass_dev;
-    a.cls_start = p->cls_start_dev;
-    a.cls_pos = p->cls_pos_dev;
-    a.cls_rank = p->cls_rank_dev;
-    a.wprefix = p->wprefix_dev;
-    a.err = ctx->d_err;
-    a.seed = seed;
-    a.wtotal = p->wtotal;
-    a.p_mut = p_mut;
-    a.gen = gen;
-    a.R = R;
-    a.P = P;
-    a.Nv = p->Nv;
-    a.S = p->S;
-    a.n_elite = n_elite;
-    a.ncls = p->ncls;
-    a.nmovable = p->nmovable;
-    a.only_movable = p->only_movable;
-    // warps (children) per block: a power of two up to 8, small enough that
-    // the grid spreads over at least two blocks per SM, within 96 KB
-    const size_t slot = ga_slot_bytes(p->Nv, p->S), cpos = ga_cpos_bytes(p->Nv);
+    char* q = (char*)p->ga_buf.ptr;
+    int8_t* pop1s = pop1 ? pop1 : (int8_t*)q;
+    q += b_pop;
+    unsigned long long* pre = (unsigned long long*)q;
+    q += b_pre;
+    unsigned long long* ftot = (unsigned long long*)q;
+    q += b_ftot;
+    double* mm = (double*)q;
+    q += b_mm;
+    int* elite = (int*)q;
+    q += b_el;
+    GaTrack* track = (GaTrack*)q;
+    q += b_tr;
+    int32_t* par = parents ? parents : (incr ? (int32_t*)q : nullptr);
+    double* phi0 = nullptr;
+    if (incr) {
+        rc = ensure(p->ga_incr, 2 * sizeof(double) * RP * Nv + 256);
+        if (rc) return rc;
+        phi0 = (double*)p->ga_incr.ptr;
+    }
+    for (int r = 0; r < R; ++r) {
+        GaEntry e{};
+        e.vclass = p->vclass_dev;
+        e.cls_start = p->cls_start_dev;
+        e.cls_pos = p->cls_pos_dev;
+        e.cls_rank = p->cls_rank_dev;
+        e.wprefix = p->wprefix_dev;
+        e.J = p->J_vv;
+        e.z = p->z_dev;
+        e.phifix = p->phifix;
+        e.pop[0] = pop0 + (size_t)r * P * Nv;
+        e.pop[1] = pop1s + (size_t)r * P * Nv;
+        e.phi[0] = incr ? phi0 + (size_t)r * P * Nv : nullptr;
+        e.phi[1] = incr ? phi0 + RP * Nv + (size_t)r * P * Nv : nullptr;
+        e.E = E + (size_t)r * P;
+        e.pre = pre + (size_t)r * P;
+        e.ftot = ftot + r;
+        e.mm = mm + 2 * r;
+        e.elite = elite + (size_t)r * (n_elite > 0 ? n_elite : 1);
+        e.track = tracking ? track + r : nullptr;
+        e.parents = par ? par + 2 * (size_t)r * P : nullptr;
+        e.nswap = nswap ? nswap + 2 * (size_t)r * P : nullptr;
+        e.key = seed + (uint64_t)r;
+        e.E_const = p->E_const;
+        e.wtotal = p->wtotal;
+        e.Nv = Nv;
+        e.S = p->S;
+        e.ncls = p->ncls;
+        e.nmovable = p->nmovable;
+        e.only_movable = p->only_movable;
+        e.ld = p->Nv_pad;
+        e.P = P;
+        e.n_elite = n_elite;
+        L.e.push_back(e);
+        L.prob.push_back(p);
+    }
+    return GOAC_OK;
+}
+
+// Launch geometry of the entries and their device copy in `devbuf`: warps
+// (children) per block a power of two up to 8, small enough that the grid
+// spreads over at least two blocks per SM, within 96 KB of shared memory for
+// the largest population's working set.
+static goac_status ga_finalize(goac_ctx* ctx, GaLaunch& L, DevBuf& devbuf)
+{
+    size_t slot = 0, cpos = 0;
+    L.total = 0;
+    L.max_nv = 0;
+    L.any_elite = false;
+    for (const GaEntry& e : L.e) {
+        slot = std::max(slot, ga_slot_bytes(e.Nv, e.S));
+        cpos = std::max(cpos, ga_cpos_bytes(e.Nv));
+        L.total += e.P;
+        L.max_nv = std::max(L.max_nv, e.Nv);
+        L.any_elite = L.any_elite || e.n_elite > 0;
+    }
     // (this bounds Nv to at most 33,432, so class positions fit the 16-bit fields the kernel packs)
-    if (slot + cpos > 200 * 1024 || p->Nv > 65535) return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
+    if (slot + cpos > 200 * 1024 || L.max_nv > 65535)
+        return fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: Nv too large");
     int wpb = 8;
-    while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (RP + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
-    const size_t smem = cpos + slot * wpb;
+    while (wpb > 1 && (cpos + (size_t)wpb * slot > 96 * 1024 || (L.total + wpb - 1) / wpb < 2 * ctx->num_sms)) wpb >>= 1;
+    L.wpb = wpb;
+    L.smem_children = cpos + slot * wpb;
+    L.smem_incr = (sizeof(double) + sizeof(int)) * (size_t)L.max_nv;
+    long child0 = 0;
+    int block0 = 0;
+    for (GaEntry& e : L.e) {
+        e.child0 = child0;
+        e.block0 = block0;
+        child0 += e.P;
+        block0 += (e.P + wpb - 1) / wpb;
+    }
+    L.blocks = block0;
+    goac_status rc = ensure(devbuf, sizeof(GaEntry) * L.e.size() + 64);
+    if (rc) return rc;
+    L.dev = (GaEntry*)devbuf.ptr;
+    GOAC_CUDA(cudaMemcpyAsync(L.dev, L.e.data(), sizeof(GaEntry) * L.e.size(), cudaMemcpyHostToDevice, ctx->stream));
+    return GOAC_OK;
+}
+
+// One generation of every entry: generation number gen reads buffers
+// `parity` and writes the other; g / patience drive the run-level stop.
+static goac_status ga_gen_launch(goac_ctx* ctx, const GaLaunch& L, uint32_t gen, int parity, uint32_t p_mut, int g,
+                                 int patience)
+{
+    cudaStream_t st = ctx->stream;
+    const int n = (int)L.e.size();
+    goac::launch(k_ga_select, n, 1024, 0, st, (const GaEntry*)L.dev, 1, g, patience);
+    if (L.any_elite) goac::launch(k_ga_rank, (int)((L.total + 7) / 8), 256, 0, st, (const GaEntry*)L.dev, n, L.total);
+    GOAC_LAUNCH_CHECK("ga prep");
     GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     KTimer kt(ctx, KID_GA, st);
-    goac::launch(k_ga_children, (int)((RP + wpb - 1) / wpb), 32 * wpb, smem, st, a);
+    goac::launch(k_ga_children, L.blocks, 32 * L.wpb, L.smem_children, st, (const GaEntry*)L.dev, n, L.wpb, gen,
+                 parity, p_mut, ctx->d_err);
     GOAC_LAUNCH_CHECK("k_ga_children");
     return GOAC_OK;
 }
@@ -623,95 +737,63 @@ struct GaRunOpts {
     double time_budget_s;
 };
 
-// GA run over R populations of P: initial scoring, then per generation the
-// children (ga_generation_impl) and their rescoring, dense (goac_score in the
-// requested form) or incremental in FP64 (k_ga_incr from the nearer parent's
-// potential; the potentials of the population are formed once by the FP64
-// scoring GEMM).  With tracking, the select kernel of each generation keeps the
-// per-population patience state on the device and finished populations are
-// copied unchanged; the host looks at the states every 8 generations (one
-// small copy) to stop launching once every population has finished or the
-// wall-clock budget is spent.
-static goac_status ga_run_core(goac_problem* p, int8_t* pop, double* E, int R, int P, const GaRunOpts& o,
-                               uint64_t seed, goac_ga_stats* stats)
+// GA run over the entries of L (populations of one problem, or of several
+// problems when every entry's rescoring is incremental): initial scoring,
+// then per generation the children and their rescoring, dense (goac_score in
+// the requested form over the single problem's populations) or incremental in
+// FP64 (k_ga_incr from the nearer parent's potential; the potentials of the
+// starting populations by the FP64 scoring GEMM).  With tracking, the select
+// kernel keeps each population's patience state on the device and finished
+// populations are copied unchanged; the host looks at the states every 8
+// generations (one small copy) to stop launching once every population has
+// finished or the wall-clock budget is spent.  The final population ends up in
+// each entry's pop[0].
+static goac_status ga_run_core(goac_ctx* ctx, GaLaunch& L, const GaRunOpts& o, goac_ga_stats* stats)
 {
-    goac_ctx* ctx = p->ctx;
     cudaStream_t st = ctx->stream;
-    const int Nv = p->Nv;
-    const long RP = (long)R * P;
     const bool incr = o.precision == GOAC_PREC_F64_INCR;
-    const bool tracking = o.patience > 0 || o.time_budget_s > 0.0 || stats != nullptr;
-    const size_t smem_incr = (sizeof(double) + sizeof(int)) * (size_t)Nv;
-    if (incr && smem_incr > 200 * 1024)
+    const bool tracking = L.e[0].track != nullptr;
+    const int n = (int)L.e.size();
+    if (incr && L.smem_incr > 200 * 1024)
         return fail(GOAC_ERR_UNSUPPORTED, "goac_ga_run: incremental rescoring needs Nv <= 17066");
-    goac_status rc = ensure(p->phi, (size_t)RP * Nv);
-    if (rc) return rc;
-    int8_t* kids = (int8_t*)p->phi.ptr;
-    GaTrack* track = nullptr;
-    double* mm_fin = nullptr;
-    if (tracking) {
-        rc = ensure(p->ga_track, sizeof(GaTrack) * (size_t)R + 2 * sizeof(double) * (size_t)R + 64);
-        if (rc) return rc;
-        track = (GaTrack*)p->ga_track.ptr;
-        mm_fin = (double*)(track + R);
-    }
-    double* phi_a = nullptr;
-    double* phi_b = nullptr;
-    int32_t* parents = nullptr;
-    if (incr) {
-        const size_t phi_bytes = sizeof(double) * (size_t)RP * Nv;
-        rc = ensure(p->ga_incr, 2 * phi_bytes + sizeof(int32_t) * 2 * (size_t)RP + 256);
-        if (rc) return rc;
-        phi_a = (double*)p->ga_incr.ptr;
-        phi_b = (double*)((char*)p->ga_incr.ptr + phi_bytes);
-        parents = (int32_t*)((char*)p->ga_incr.ptr + 2 * phi_bytes);
-        rc = score_f64(p, pop, (int)RP, E, phi_a);
-        GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    } else {
-        rc = goac_score(p, pop, (int)RP, o.precision, E);
+    goac_status rc = GOAC_OK;
+    // starting energies (and potentials), per run of entries that share a problem
+    for (int i = 0; i < n && !rc;) {
+        int j = i;
+        while (j < n && L.prob[j] == L.prob[i] && L.e[j].pop[0] == L.e[i].pop[0] + (size_t)(j - i) * L.e[i].P * L.e[i].Nv)
+            ++j;
+        const int RP = L.e[i].P * (j - i);
+        rc = incr ? score_f64(L.prob[i], L.e[i].pop[0], RP, L.e[i].E, L.e[i].phi[0])
+                  : goac_score(L.prob[i], L.e[i].pop[0], RP, o.precision, L.e[i].E);
+        i = j;
     }
     if (rc) return rc;
+    if (incr) GOAC_CUDA(cudaFuncSetAttribute(k_ga_incr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     const auto t_start = std::chrono::steady_clock::now();
-    std::vector<GaTrack> host(tracking ? R : 0);
+    std::vector<GaTrack> host(tracking ? n : 0);
     int stop_reason = 0, g = 0;
     for (; g < o.n_gen; ++g) {
-        rc = ga_generation_impl(p, pop, E, R, P, o.n_elite, o.p_mut, o.gen0 + (uint32_t)g, seed, kids, parents,
-                                nullptr, track, g, o.patience);
+        const int parity = g & 1;
+        rc = ga_gen_launch(ctx, L, o.gen0 + (uint32_t)g, parity, o.p_mut, g, o.patience);
         if (rc) return rc;
         if (incr) {
-            GaIncrArgs a;
-            a.pop = pop;
-            a.phi_pop = phi_a;
-            a.kids = kids;
-            a.parents = parents;
-            a.J = p->J_vv;
-            a.z = p->z_dev;
-            a.phifix = p->phifix;
-            a.phi_kids = phi_b;
-            a.E_kids = E;
-            a.err = ctx->d_err;
-            a.E_const = p->E_const;
-            a.ld = p->Nv_pad;
-            a.Nv = Nv;
-            a.P = P;
-            a.S = p->S;
             {
                 KTimer kt(ctx, KID_GA_INCR, st);
-                goac::launch(k_ga_incr, (int)RP, GI_THREADS, smem_incr, st, a);
+                goac::launch(k_ga_incr, (int)L.total, GI_THREADS, L.smem_incr, st, (const GaEntry*)L.dev, n, parity,
+                             ctx->d_err);
             }
             GOAC_LAUNCH_CHECK("k_ga_incr");
-            GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
-            std::swap(phi_a, phi_b);
         } else {
-            GOAC_CUDA(cudaMemcpyAsync(pop, kids, (size_t)RP * Nv, cudaMemcpyDeviceToDevice, st));
-            rc = goac_score(p, pop, (int)RP, o.precision, E);
+            // a single problem: its populations' second buffers are contiguous
+            rc = goac_score(L.prob[0], L.e[0].pop[parity ^ 1], (int)L.total, o.precision, L.e[0].E);
             if (rc) return rc;
         }
         if (tracking && (o.patience > 0 || o.time_budget_s > 0.0) && (g + 1) % 8 == 0 && g + 1 < o.n_gen) {
-            GOAC_CUDA(cudaMemcpyAsync(host.data(), track, sizeof(GaTrack) * (size_t)R, cudaMemcpyDeviceToHost, st));
+            for (int r = 0; r < n; ++r)
+                GOAC_CUDA(cudaMemcpyAsync(&host[r], L.e[r].track, sizeof(GaTrack), cudaMemcpyDeviceToHost, st));
             GOAC_CUDA(cudaStreamSynchronize(st));
             bool all = o.patience > 0;
-            for (int r = 0; r < R && all; ++r) all = host[r].stop != 0;
+            for (int r = 0; r < n && all; ++r) all = host[r].stop != 0;
             if (all) {
                 ++g;
                 break;
@@ -724,18 +806,31 @@ static goac_status ga_run_core(goac_problem* p, int8_t* pop, double* E, int R, i
             }
         }
     }
+    // the final populations into pop[0]
+    if (g & 1)
+        for (int i = 0; i < n;) {
+            int j = i;
+            while (j < n && L.prob[j] == L.prob[i] &&
+                   L.e[j].pop[1] == L.e[i].pop[1] + (size_t)(j - i) * L.e[i].P * L.e[i].Nv &&
+                   L.e[j].pop[0] == L.e[i].pop[0] + (size_t)(j - i) * L.e[i].P * L.e[i].Nv)
+                ++j;
+            GOAC_CUDA(cudaMemcpyAsync(L.e[i].pop[0], L.e[i].pop[1], (size_t)(j - i) * L.e[i].P * L.e[i].Nv,
+                                      cudaMemcpyDeviceToDevice, st));
+            i = j;
+        }
     if (!tracking) return GOAC_OK;
     // the state after the last generation run
-    goac::launch(k_ga_select, R, 1024, 0, st, (const double*)E, P, mm_fin, (unsigned long long*)nullptr,
-                 (unsigned long long*)nullptr, 0, track, g, o.patience);
+    goac::launch(k_ga_select, n, 1024, 0, st, (const GaEntry*)L.dev, 0, g, o.patience);
     GOAC_LAUNCH_CHECK("k_ga_select (final)");
     if (stats) {
-        GOAC_CUDA(cudaMemcpyAsync(host.data(), track, sizeof(GaTrack) * (size_t)R, cudaMemcpyDeviceToHost, st));
+        for (int r = 0; r < n; ++r)
+            GOAC_CUDA(cudaMemcpyAsync(&host[r], L.e[r].track, sizeof(GaTrack), cudaMemcpyDeviceToHost, st));
         GOAC_CUDA(cudaStreamSynchronize(st));
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < n; ++r) {
             stats[r].generations = host[r].stop ? host[r].gens : g;
             stats[r].best_generation = host[r].best_gen;
             stats[r].stop_reason = host[r].stop ? 1 : stop_reason;
+            stats[r].reserved = 0;
             stats[r].best_E = host[r].best;
         }
     }
@@ -753,22 +848,40 @@ extern "C" goac_status goac_ga_generation(goac_problem* p, const int8_t* pop_dev
     if (P == 0) return GOAC_OK;
     if (!pop_dev || !E_dev || !children_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_generation: NULL");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
-    return goac::ga_generation_impl(p, pop_dev, E_dev, 1, P, n_elite, p_mut_u32, gen, seed, children_dev, parents_dev,
-                                    nswap_dev);
+    goac::GaLaunch L;
+    goac_status rc = goac::ga_entries(p, const_cast<int8_t*>(pop_dev), children_dev, const_cast<double*>(E_dev), 1, P,
+                                      n_elite, seed, false, false, parents_dev, nswap_dev, L);
+    if (!rc) rc = goac::ga_finalize(p->ctx, L, p->ga_dev);
+    if (!rc) rc = goac::ga_gen_launch(p->ctx, L, gen, 0, p_mut_u32, 0, 0);
+    return rc;
+}
+
+static goac_status ga_run_problem(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t R, int32_t P,
+                                  const goac::GaRunOpts& o, uint64_t seed, goac_ga_stats* stats)
+{
+    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL problem");
+    if (R < 0 || P < 0 || (int64_t)R * P > GOAC_MAX_BATCH || o.n_gen < 0 || o.n_elite < 0 || o.n_elite > P ||
+        o.patience < 0 || !(o.time_budget_s >= 0.0))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes or parameters");
+    if (R == 0 || P == 0) return GOAC_OK;
+    if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
+    GOAC_CUDA(cudaSetDevice(p->ctx->device));
+    const bool incr = o.precision == GOAC_PREC_F64_INCR;
+    const bool tracking = o.patience > 0 || o.time_budget_s > 0.0 || stats != nullptr;
+    goac::GaLaunch L;
+    goac_status rc = goac::ga_entries(p, pop_dev, nullptr, E_dev, R, P, o.n_elite, seed, incr, tracking, nullptr,
+                                      nullptr, L);
+    if (!rc) rc = goac::ga_finalize(p->ctx, L, p->ga_dev);
+    if (!rc) rc = goac::ga_run_core(p->ctx, L, o, stats);
+    return rc;
 }
 
 extern "C" goac_status goac_ga_run_populations(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t R,
                                                int32_t P, int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32,
                                                uint64_t seed, uint32_t gen0, int32_t precision)
 {
-    if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL problem");
-    if (R < 0 || P < 0 || (int64_t)R * P > GOAC_MAX_BATCH || n_gen < 0 || n_elite < 0 || n_elite > P)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: bad sizes");
-    if (R == 0 || P == 0) return GOAC_OK;
-    if (!pop_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run: NULL");
-    GOAC_CUDA(cudaSetDevice(p->ctx->device));
     goac::GaRunOpts o{n_gen, n_elite, precision, 0, p_mut_u32, gen0, 0.0};
-    return goac::ga_run_core(p, pop_dev, E_dev, R, P, o, seed, nullptr);
+    return ga_run_problem(p, pop_dev, E_dev, R, P, o, seed, nullptr);
 }
 
 extern "C" goac_status goac_ga_run(goac_problem* p, int8_t* pop_dev, double* E_dev, int32_t P, int32_t n_gen,
@@ -784,21 +897,51 @@ extern "C" goac_status goac_ga_run_ex(goac_problem* p, int8_t* pop_dev, double* 
 {
     if (!p || !prm) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: NULL problem or parameters");
     const int32_t P = prm->P;
-    if (R < 0 || P < 0 || (int64_t)R * P > GOAC_MAX_BATCH || prm->n_gen < 0 || prm->n_elite < 0 ||
-        prm->n_elite > P || prm->patience < 0 || !(prm->time_budget_s >= 0.0))
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: bad sizes or parameters");
     if (topk < 0 || (R > 0 && P > 0 && topk > std::min(P, 1024)))
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: topk must be in 0 .. min(P, 1024)");
-    if (R == 0 || P == 0) return GOAC_OK;
-    if (!pop_dev || !E_dev || (topk > 0 && (!top_idx_dev || !topE_dev)))
+    if (R > 0 && P > 0 && topk > 0 && (!top_idx_dev || !topE_dev))
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_ga_run_ex: NULL");
-    GOAC_CUDA(cudaSetDevice(p->ctx->device));
     goac::GaRunOpts o{prm->n_gen, prm->n_elite, prm->precision, prm->patience, prm->p_mut_u32, prm->gen0,
                       prm->time_budget_s};
-    goac_status rc = goac::ga_run_core(p, pop_dev, E_dev, R, P, o, seed, stats_host);
-    if (rc || topk == 0) return rc;
+    goac_status rc = ga_run_problem(p, pop_dev, E_dev, R, P, o, seed, stats_host);
+    if (rc || topk == 0 || R == 0 || P == 0) return rc;
     for (int r = 0; r < R && !rc; ++r)
         rc = goac_topk_rescore(p, pop_dev + (size_t)r * P * p->Nv, P, E_dev + (size_t)r * P, topk,
                                top_idx_dev + (size_t)r * topk, topE_dev + (size_t)r * topk);
+    return rc;
+}
+
+extern "C" goac_status goac_batch_ga_run(goac_ctx* ctx, goac_problem* const* probs, int32_t n_probs,
+                                         int8_t* const* pop_dev, double* const* E_dev, const int32_t* P,
+                                         int32_t n_gen, int32_t n_elite, uint32_t p_mut_u32, uint64_t seed,
+                                         uint32_t gen0, int32_t precision)
+{
+    if (!ctx || n_probs < 0 || (n_probs > 0 && (!probs || !pop_dev || !E_dev || !P)) || n_gen < 0 || n_elite < 0)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_ga_run: bad argument");
+    if (precision != GOAC_PREC_F64_INCR)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_ga_run: precision must be GOAC_PREC_F64_INCR");
+    int64_t total = 0;
+    for (int i = 0; i < n_probs; ++i) {
+        if (!probs[i] || probs[i]->ctx != ctx || P[i] < 0 || n_elite > P[i])
+            return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_ga_run: bad problem or population size");
+        if (P[i] > 0 && (!pop_dev[i] || !E_dev[i])) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_ga_run: NULL");
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i] && P[i] > 0 && P[j] > 0)
+                return goac::fail(GOAC_ERR_INVALID_ARG,
+                                  "goac_batch_ga_run: a problem appears twice (use goac_ga_run_populations)");
+        total += P[i];
+    }
+    if (total > GOAC_MAX_BATCH) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_batch_ga_run: too many individuals");
+    if (total == 0) return GOAC_OK;
+    GOAC_CUDA(cudaSetDevice(ctx->device));
+    goac::GaLaunch L;
+    goac_status rc = GOAC_OK;
+    for (int i = 0; i < n_probs && !rc; ++i)
+        if (P[i] > 0)
+            rc = goac::ga_entries(probs[i], pop_dev[i], nullptr, E_dev[i], 1, P[i], n_elite, seed + (uint64_t)i, true,
+                                  false, nullptr, nullptr, L);
+    if (!rc) rc = goac::ga_finalize(ctx, L, ctx->ga_dev);
+    goac::GaRunOpts o{n_gen, n_elite, precision, 0, p_mut_u32, gen0, 0.0};
+    if (!rc) rc = goac::ga_run_core(ctx, L, o, nullptr);
     return rc;
 }

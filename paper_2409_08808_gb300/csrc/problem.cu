@@ -166,6 +166,7 @@ extern "C" goac_status goac_ctx_destroy(goac_ctx* ctx)
     free_buf(ctx->batch_desc);
     free_buf(ctx->batch_items);
     free_buf(ctx->batch_counter);
+    free_buf(ctx->ga_dev);
     cudaFree(ctx->d_err);
     delete ctx;
     return GOAC_OK;
@@ -966,7 +967,8 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     free_buf(p->topk_tmp);
     free_buf(p->grad_tmp);
     free_buf(p->ga_incr);
-    free_buf(p->ga_track);
+    free_buf(p->ga_buf);
+    free_buf(p->ga_dev);
     free_buf(p->sched.buf);
     free_buf(p->sched_ex.buf);
     cudaFree(p->J_dig);
