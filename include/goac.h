@@ -190,17 +190,21 @@ goac_status goac_problem_exact_info(const goac_problem* prob, int32_t* digit_bit
  * caller's buffers it uses one fixed file-scope device array of 524,288        *
  * doubles (4 MiB, present on every GPU that loads the library until exit) for *
  * the per-tile partial energies; requires ceil(Nv/64) * B <= 524,288, else    *
- * GOAC_ERR_INVALID_ARG.  The first call on a device looks up that array's     *
- * device address (cudaGetSymbolAddress) and caches it; make that first call   *
- * before any stream capture.  All calls share the array and it keeps the last *
- * call's contents (every entry read is first written, nothing needs clearing);*
- * calls that overlap on the GPU race on it.                                    *
+ * GOAC_ERR_INVALID_ARG.  Each call outside a stream capture looks up that     *
+ * array's device address (cudaGetSymbolAddress) and caches it per device, so  *
+ * a device whose context was reset gets the new address; a call inside a      *
+ * capture uses the cached one, so make a first call on each device before any *
+ * stream capture (else GOAC_ERR_INVALID_ARG).  All calls share the array and  *
+ * it keeps the last call's contents (every entry read is first written,      *
+ * nothing needs clearing); calls that overlap on the GPU race on it.         *
  *   Jvv_dev: ceil(Nv/64)*64 rows of `ld` doubles (ld >= Nv rounded up to 64),  *
  *            J_vv in the leading Nv x Nv block, finite values elsewhere.      *
- *   species_dev: B x Nv int8.  z_dev: 64 doubles (charges of species 0..S-1,   *
- *   any finite values after).  phi_fix_dev: ld doubles (phi_fix in the first   *
- *   Nv, zeros when there are no fixed ions).  E = q^T J_vv q + 2 q . phi_fix +  *
- *   E_const into E_dev (B doubles).  Runs on the current device, on `stream`. */
+ *   species_dev: B x Nv int8, every value in 0 .. 63 (it indexes z_dev; a     *
+ *   value outside is not checked and gives undefined energies).  z_dev: 64    *
+ *   doubles (charges of species 0..S-1, any finite values after).             *
+ *   phi_fix_dev: ld doubles (phi_fix in the first Nv, zeros when there are    *
+ *   no fixed ions).  E = q^T J_vv q + 2 q . phi_fix + E_const into E_dev      *
+ *   (B doubles).  Runs on the current device, on `stream`.                    */
 goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld, int32_t Nv, const int8_t* species_dev,
                                    int32_t B, const double* z_dev, const double* phi_fix_dev, double E_const,
                                    void* stream, double* E_dev);

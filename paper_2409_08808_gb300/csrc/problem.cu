@@ -1196,17 +1196,24 @@ extern "C" goac_status goac_score_f64_noalloc(const double* Jvv_dev, int32_t ld,
     int dev = 0;
     GOAC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_f64_noalloc: device ordinal >= 64");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GOAC_CUDA(cudaStreamIsCapturing(st, &cap));
     double* part = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
+            // outside a stream capture the address is looked up on every call, so a device whose
+            // context was reset (and the library's module loaded again) gets the array's new address
             void* p = nullptr;
             GOAC_CUDA(cudaGetSymbolAddress(&p, g_static_partial));
             g_static_ptr[dev] = (double*)p;
+        } else if (!g_static_ptr[dev]) {
+            return goac::fail(GOAC_ERR_INVALID_ARG,
+                              "goac_score_f64_noalloc: the first call on a device must come before any stream capture");
         }
         part = g_static_ptr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
     dim3 grid((B + PB_N - 1) / PB_N, (unsigned)mt);
     goac::launch(k_phi<double, true, false>, grid, 256, 0, st, Jvv_dev, ld, Nv, species_dev, B, z_dev, phi_fix_dev,
                  part, (double*)nullptr);

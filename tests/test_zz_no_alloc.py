@@ -54,6 +54,23 @@ def test_noalloc_matches_score_twice():
         rel = ((E - ref).abs() / ref.abs()).max().item()
         assert rel <= 1e-10, (call, rel)
 
+    # the largest accepted call: ceil(Nv/64) * B equal to the array's 524,288 entries, so the last
+    # configuration tile writes the array's last entry; a sample including that tile against the oracle
+    import oracle
+    mt = (Nv + 63) // 64
+    B_max = 524288 // mt
+    assert mt * B_max == 524288
+    sp = torch.tensor(synth.random_population(prob, B_max, 7), device="cuda")
+    E = torch.full((B_max,), float("nan"), dtype=torch.float64, device="cuda")
+    rc = _lib.lib.goac_score_f64_noalloc(_ptr(Jvv), ld, Nv, _ptr(sp), B_max, _ptr(z), _ptr(pf), gp.E_const, stream,
+                                         _ptr(E))
+    assert rc == 0, _lib.lib.goac_last_error()
+    torch.cuda.synchronize()
+    rows = np.array([0, 1, B_max // 2, B_max - 65, B_max - 2, B_max - 1])
+    Eo = oracle.score(J.cpu().numpy(), prob.site_class, prob.fixed_q, prob.z, sp.cpu().numpy()[rows])
+    assert np.max(np.abs(E.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
+    assert not torch.isnan(E).any()
+
     # sizes beyond the fixed scratch are rejected, nothing is launched
     big = torch.zeros((1, Nv), dtype=torch.int8, device="cuda")
     too_many = (524288 // ((Nv + 63) // 64)) + 1
