@@ -465,7 +465,7 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const int Nv = p->Nv, S = p->S, ncls = p->ncls, ld = p->Nv_pad;
     const bool tc = precision == GOAC_PREC_TF32X2;
-    const int Bpad = ((B + 127) / 128) * 128;
+    const int Bpad = ((B + 255) / 256) * 256;      // whole 256-configuration tiles of the contraction
     const long BN = (long)B * Nv;
     cudaStream_t st = p->ctx->stream;
     if (tc) {

@@ -49,6 +49,13 @@ constexpr int A_TILE = TC_M * ROW_BYTES;
 constexpr int B_TILE = TC_N * ROW_BYTES;
 constexpr long long WAIT_LIMIT = 4000000000LL;   // ~2 s of SM clock
 
+// 2^e as a double for e in the normal range (exact; multiplying by it equals
+// ldexp(x, e) whenever the product is normal).
+__device__ __forceinline__ double pow2(int e)
+{
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 template <int T, int TN = TC_N>
 struct TcCfg {
     static constexpr int STAGE = T * A_TILE + TN * ROW_BYTES;
@@ -277,19 +284,24 @@ __device__ __forceinline__ float to_tf32_rna(float x)
 // Phi = J_hi Q_hi + J_hi Q_lo + J_lo Q_hi (the lo*lo product is dropped).
 // Used by the relaxed-occupation gradient, where q = p . z is not integer.
 // Persistent grid (one CTA per SM, 192 threads): warp 0 lane 0 TMA producer,
-// warp 1 lane 0 MMA issuer (kind::tf32, M = 128 sites, N = 128
+// warp 1 lane 0 MMA issuer (kind::tf32, M = 128 sites, N = 256
 // configurations, K = 8), warps 2-5 epilogue (warp 2 owns TMEM).  Tiles of
-// 128 sites x 128 configurations over the whole k-range, dealt round robin
-// with the configuration block fastest (CTAs running together share J's rows
-// in L2); each stage holds J hi / lo and Q hi / lo (128 x 32 FP32 each).  Two
-// FP32 accumulators in TMEM (2 x 128 columns) let the epilogue of one tile,
-// which writes its 32 TMEM lanes (sites) to Phi[b][v] coalesced over sites,
-// overlap the MMAs of the next.
-constexpr int PT_N = 128;
+// 128 sites x 256 configurations over the whole k-range, dealt round robin
+// with the configuration block fastest, so the CTAs of one wave cover every
+// configuration block of 19 row panels: each panel's J rows come from DRAM
+// once and are shared in L2, and the Q tiles are re-read once per wave.  Each
+// stage holds J hi / lo (128 x 32 FP32 each) and Q hi / lo (256 x 32 FP32
+// each): 96 KB for twelve MMAs, which keeps the shared-memory traffic per MMA
+// (12 KB in by TMA, 12 KB out to the tensor core) at the level of the
+// two-term BF16 scoring kernel; two stages fit.  Two FP32 accumulators in
+// TMEM (2 x 256 columns) let the epilogue of one tile, which writes its 32
+// TMEM lanes (sites) to Phi[b][v] coalesced over sites, overlap the MMAs of
+// the next.  The padded batch is a multiple of 256.
+constexpr int PT_N = 256;
 constexpr int PT_A = TC_M * ROW_BYTES;        // 16 KB
-constexpr int PT_B = PT_N * ROW_BYTES;        // 16 KB
-constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 64 KB
-constexpr int PT_STAGES = 3;
+constexpr int PT_B = PT_N * ROW_BYTES;        // 32 KB
+constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 96 KB
+constexpr int PT_STAGES = 2;
 constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
 
 __global__ void __launch_bounds__(192, 1)
@@ -863,9 +875,9 @@ __global__ void __launch_bounds__(256)
     double e = 0.0;
     for (int v = threadIdx.x; v < Nv; v += blockDim.x) {
         double d = 0.0;
-        for (int t = T - 1; t >= 0; --t) d += ldexp((double)Phi[((long)t * Bpad + b) * ld + v], -r * t);
+        for (int t = T - 1; t >= 0; --t) d += (double)Phi[((long)t * Bpad + b) * ld + v] * pow2(-r * t);
         const double pf = phifix[v];
-        const double ph = ldexp(d, pexp[v / TC_M] - (r - 1) - kq) + pf;
+        const double ph = d * pow2(pexp[v / TC_M] - (r - 1) - kq) + pf;
         if (phi_out) phi_out[(long)b * Nv + v] = (PT)ph;      // FP32 chains: phi rounded once
         e += z[species[(long)b * Nv + v]] * (ph + pf);
     }
@@ -991,13 +1003,16 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
     if (threadIdx.x == 0) lin[b] = red[0];
 }
 
+constexpr int EX_TMAX = 6;                     // most digits of the exact form
+
 // E_b = 2^-2kq sum_I 2^(e_I - (r-1)) sum_t 2^-rt P_t,I,b + lin_b + E_const,
 // P_t,I,b the sum of panel I's k-chunk partials (slots pslot[I] ..
 // pslot[I+1]) of digit t: exact integers below 2^53, so the result does not
 // depend on how the panel's k-range was split.  One block of 8 warps per 32
 // configurations: lane = configuration (coalesced loads of the partials), warp
-// w takes panels w, w + 8, ...; digits are added smallest first and the 8
-// warp sums in a fixed order (deterministic).
+// w takes panels w, w + 8, ...; a panel's T partials are loaded together, the
+// digits added smallest first and the 8 warp sums in a fixed order
+// (deterministic); the scalings are exact powers of two.
 __global__ void __launch_bounds__(256)
     k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pslot,
                    const int* __restrict__ pexp, int Bpad, int B, int r, int T, int kq2, double E_const,
@@ -1011,13 +1026,20 @@ __global__ void __launch_bounds__(256)
     if (b < B)
         for (int m = warp; m < npanels; m += 8) {
             const int s0 = pslot[m], s1 = pslot[m + 1];
-            double d = 0.0;
-            for (int t = T - 1; t >= 0; --t) {
-                double P = 0.0;
-                for (int sl = s0; sl < s1; ++sl) P += partial[((long)sl * T + t) * Bpad + b];
-                d += ldexp(P, -r * t);
+            double P[EX_TMAX];
+#pragma unroll
+            for (int t = 0; t < EX_TMAX; ++t) P[t] = 0.0;
+            for (int sl = s0; sl < s1; ++sl) {
+                const double* ps = partial + (long)sl * T * Bpad + b;
+#pragma unroll
+                for (int t = 0; t < EX_TMAX; ++t)
+                    if (t < T) P[t] += ps[(long)t * Bpad];
             }
-            s += ldexp(d, pexp[m] - (r - 1));
+            double d = 0.0;
+#pragma unroll
+            for (int t = EX_TMAX - 1; t >= 0; --t)
+                if (t < T) d += P[t] * pow2(-r * t);
+            s += d * pow2(pexp[m] - (r - 1));
         }
     red[warp][lane] = s;
     __syncthreads();
@@ -1025,7 +1047,7 @@ __global__ void __launch_bounds__(256)
         double tot = 0.0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) tot += red[w][lane];
-        E[b] = ldexp(tot, -kq2) + (lin ? lin[b] : 0.0) + E_const;
+        E[b] = tot * pow2(-kq2) + (lin ? lin[b] : 0.0) + E_const;
     }
 }
 
@@ -1286,7 +1308,7 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     static std::atomic<uint64_t> attr_done{0};
     rc = smem_attr_once((const void*)k_phi_tc, PT_SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
-    if (Bpad % PT_N != 0) return fail(GOAC_ERR_INTERNAL, "phi_tc: padded batch must be a multiple of 128");
+    if (Bpad % PT_N != 0) return fail(GOAC_ERR_INTERNAL, "phi_tc: padded batch must be a multiple of 256");
     const int nbn = Bpad / PT_N;
     const int ntiles = (ld / TC_M) * nbn;
     const int grid = std::min(ntiles, p->ctx->num_sms);
