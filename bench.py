@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", default=FORM, choices=sorted(TERMS))
     ap.add_argument("--mc-steps", type=int, default=4096)
+    ap.add_argument("--mc-shapes", default="",
+                    help="'W,c:W,c' fixed Monte Carlo launch shapes (FP64:FP32) instead of the autotuner")
     ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
     ap.add_argument("--suite", action="store_true", help="measure the other workloads, one JSON line each")
     ap.add_argument("--only", default="mc,ga,batch,forms,relaxed,gd",
@@ -487,7 +489,11 @@ def run_ours(args, world, rank, local):
     for prec in ("f64", "f32"):
         Cn = 152 * (6 if prec == "f64" else 8)
         chains = gp.random_configs(Cn, 77 + rank)
-        W_t, cpc_t, _ = gp.mc_autotune(chains, 0.05, 128, prec)      # launch shape for this cell
+        if args.mc_shapes:                                        # fixed shapes (profiling runs)
+            W_t, cpc_t = (int(x) for x in args.mc_shapes.split(":")[0 if prec == "f64" else 1].split(","))
+            gp.mc_set_shape(W_t, cpc_t, prec)
+        else:
+            W_t, cpc_t, _ = gp.mc_autotune(chains, 0.05, 128, prec)  # launch shape for this cell
         gp.mc_run(chains, 0.05, args.mc_steps, 5, step0=0, precision=prec)
         torch.cuda.synchronize()
         ctx.set_timing(True)
