@@ -296,7 +296,10 @@ __device__ __forceinline__ float to_tf32_rna(float x)
 // two-term BF16 scoring kernel; two stages fit.  Two FP32 accumulators in
 // TMEM (2 x 256 columns) let the epilogue of one tile, which writes its 32
 // TMEM lanes (sites) to Phi[b][v] coalesced over sites, overlap the MMAs of
-// the next.  The padded batch is a multiple of 256.
+// the next.  The padded batch is a multiple of 256.  The tiles that would
+// leave the last wave partly idle are split into two k-halves whose epilogues
+// add into a zeroed Phi (two FP32 addends onto zero: the same sum in either
+// order), so the wave count matches the work.
 constexpr int PT_N = 256;
 constexpr int PT_A = TC_M * ROW_BYTES;        // 16 KB
 constexpr int PT_B = PT_N * ROW_BYTES;        // 32 KB
@@ -304,9 +307,32 @@ constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 96 KB
 constexpr int PT_STAGES = 2;
 constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
 
+// Work item `it` of k_phi_tc: the first nfull items are whole tiles (m-block,
+// configuration block fastest); each later tile is two items, its k-halves.
+struct PhiItem {
+    int m0, n0, kb0, kb1;
+    bool add;
+};
+
+__device__ __forceinline__ PhiItem phi_item(int it, int nfull, int nbn, int nkb)
+{
+    PhiItem w;
+    int tile = it, half = -1;
+    if (it >= nfull) {
+        tile = nfull + (it - nfull) / 2;
+        half = (it - nfull) % 2;
+    }
+    w.m0 = (tile / nbn) * TC_M;
+    w.n0 = (tile % nbn) * PT_N;
+    w.kb0 = half <= 0 ? 0 : nkb / 2;
+    w.kb1 = half == 0 ? nkb / 2 : nkb;
+    w.add = half >= 0;
+    return w;
+}
+
 __global__ void __launch_bounds__(192, 1)
-    k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ntiles, int nbn,
-             int nkb, int ld, int Bpad, float* __restrict__ Phi, int* __restrict__ err)
+    k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nitems, int nfull,
+             int nbn, int nkb, int ld, int Bpad, float* __restrict__ Phi, int* __restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -345,9 +371,10 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- TMA producer ----------------
         if (lane == 0) {
             int it = 0;
-            for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x) {
-                const int m0 = (id / nbn) * TC_M, n0 = (id % nbn) * PT_N;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+            for (int id = blockIdx.x; id < nitems && !*abort_flag; id += gridDim.x) {
+                const PhiItem w = phi_item(id, nfull, nbn, nkb);
+                const int m0 = w.m0, n0 = w.n0;
+                for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
                     const int s = it % PT_STAGES;
                     const uint32_t use = (uint32_t)(it / PT_STAGES);
                     if (it >= PT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
@@ -375,7 +402,8 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = goacd::idesc_f32acc(2u, TC_M, PT_N);
             int it = 0, tl = 0;
-            for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
+            for (int id = blockIdx.x; id < nitems; id += gridDim.x, ++tl) {
+                const PhiItem w = phi_item(id, nfull, nbn, nkb);
                 const int acc_i = tl & 1;
                 const uint32_t ause = (uint32_t)(tl >> 1);
                 if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
@@ -384,7 +412,7 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 goacd::tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc_i * PT_N);
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
                     if (*abort_flag) break;
                     const int s = it % PT_STAGES;
                     const uint32_t use = (uint32_t)(it / PT_STAGES);
@@ -402,7 +430,7 @@ __global__ void __launch_bounds__(192, 1)
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint32_t off = kk * 32;
                         goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_hi + off), idesc,
-                                        (kb | kk) != 0);
+                                        (kb != w.kb0 || kk != 0) ? 1u : 0u);
                         goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_lo + off), idesc,
                                         1u);
                         goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_lo + off), goacd::sdesc_k128(b_hi + off), idesc,
@@ -418,8 +446,9 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- epilogue: warps 2..5 ----------------
         const int lg = warp & 3;                   // TMEM lane group this warp may access
         int tl = 0;
-        for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++tl) {
-            const int m0 = (id / nbn) * TC_M, n0 = (id % nbn) * PT_N;
+        for (int id = blockIdx.x; id < nitems; id += gridDim.x, ++tl) {
+            const PhiItem w = phi_item(id, nfull, nbn, nkb);
+            const int m0 = w.m0, n0 = w.n0;
             const int acc_i = tl & 1;
             const uint32_t ause = (uint32_t)(tl >> 1);
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
@@ -433,9 +462,13 @@ __global__ void __launch_bounds__(192, 1)
                                               (uint32_t)(c * 32),
                                           r);
                 goacd::tmem_ld_wait();
-                if (ok)
+                if (ok && !w.add) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]);
+                } else if (ok) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) atomicAdd(&Phi[(long)(n0 + c * 32 + j) * ld + v], __uint_as_float(r[j]));
+                }
             }
             goacd::tc_fence_before();
             __syncwarp();
@@ -1312,8 +1345,14 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     const int nbn = Bpad / PT_N;
     const int ntiles = (ld / TC_M) * nbn;
     const int grid = std::min(ntiles, p->ctx->num_sms);
+    // whole waves of whole tiles; the rest split in k-halves when that keeps them within one wave
+    const int rest = ntiles % grid;
+    const int nfull = (rest > 0 && 2 * rest <= grid && ld / 32 >= 2) ? ntiles - rest : ntiles;
+    const int nitems = nfull + 2 * (ntiles - nfull);
+    if (nitems > nfull) GOAC_CUDA(cudaMemsetAsync(Phi, 0, sizeof(float) * (size_t)Bpad * ld, st));
     KTimer kt(p->ctx, KID_SCORE_TC, st);
-    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, ntiles, nbn, ld / 32, ld, Bpad, Phi, p->ctx->d_err);
+    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, ld / 32, ld, Bpad, Phi,
+                 p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_phi_tc");
     return GOAC_OK;
 }
