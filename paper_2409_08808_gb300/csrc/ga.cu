@@ -244,35 +244,6 @@ __host__ __device__ inline size_t ga_slot_bytes(int Nv, int S)
 // Children of generation `gen` (which reads pop[parity] of every population
 // and writes pop[parity ^ 1]); the warps of a block all serve the population
 // whose block range holds the block.
-// Species masks held in registers (REG): lane w keeps word w of every
-// species' mask, for populations with at most 32 words (Nv <= 1,024) and at
-// most GA_REG_S species; a runtime species index selects among the
-// registers by predication.
-constexpr int GA_REG_S = 8;
-
-__device__ __forceinline__ uint32_t reg_get(const uint32_t (&mk)[GA_REG_S], int s)
-{
-    uint32_t v = 0u;
-#pragma unroll
-    for (int t = 0; t < GA_REG_S; ++t) v = t == s ? mk[t] : v;
-    return v;
-}
-
-__device__ __forceinline__ void reg_and(uint32_t (&mk)[GA_REG_S], int s, uint32_t m)
-{
-#pragma unroll
-    for (int t = 0; t < GA_REG_S; ++t)
-        if (t == s) mk[t] &= m;
-}
-
-__device__ __forceinline__ void reg_or(uint32_t (&mk)[GA_REG_S], int s, uint32_t m)
-{
-#pragma unroll
-    for (int t = 0; t < GA_REG_S; ++t)
-        if (t == s) mk[t] |= m;
-}
-
-template <bool REG>
 __global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int wpb, uint32_t gen, int parity,
                               uint32_t p_mut, int* err)
 {
@@ -333,11 +304,6 @@ __global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int 
         if ((unsigned)s < (unsigned)a.S && s != pb[w]) atomicOr(&mis[s * W + (q >> 5)], 1u << (q & 31));
     }
     __syncwarp();
-    uint32_t mk[GA_REG_S];
-    if (REG) {
-#pragma unroll
-        for (int t = 0; t < GA_REG_S; ++t) mk[t] = (t < a.S && lane < W) ? mis[t * W + lane] : 0u;
-    }
 
     // Crossover: for each site i (ascending) where the child differs from B,
     // the candidate swap pairs i with the lowest class position holding B_i
@@ -352,7 +318,6 @@ __global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int 
     uint4 blk = make_uint4(0, 0, 0, 0);
     uint32_t cache_lo = 0u, cache_hi = 0u;
     for (int i0 = 0; i0 < Nv; i0 += 32) {
-        if (REG) __syncwarp();                      // lane 0's stores of the child's earlier swaps
         const int il = i0 + lane;
         // per lane: B's species, the child's species and the class position (8 + 8 + 16 bits),
         // and the class's position range (16 + 16 bits), so a candidate takes two shuffles
@@ -398,24 +363,9 @@ __global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int 
             const int want = (int8_t)(bcr & 0xffu), old = (int8_t)((bcr >> 8) & 0xffu), pi = (int)(bcr >> 16);
             const int cs = (int)(rng & 0xffffu), ce = (int)(rng >> 16);
             const int wlo = cs >> 5, whi = (ce - 1) >> 5;
-            int pp = -1;
-            if (REG) {
-                // the lowest set bit of want's mask in the class range: one ballot over the lanes' words
-                uint32_t bits = 0u;
-                if (lane >= wlo && lane <= whi) {
-                    bits = reg_get(mk, want);
-                    if (lane == wlo) bits &= ~0u << (cs & 31);
-                    if (lane == whi && (ce & 31)) bits &= (1u << (ce & 31)) - 1u;
-                }
-                const uint32_t mm = __ballot_sync(0xffffffffu, bits != 0u);
-                if (mm) {
-                    const int ll = __ffs(mm) - 1;
-                    const uint32_t bw = __shfl_sync(0xffffffffu, bits, ll);
-                    pp = ll * 32 + __ffs(bw) - 1;
-                }
-            }
             const uint32_t* mw = mis + want * W;
-            for (int w0 = wlo; !REG && w0 <= whi; w0 += 32) {
+            int pp = -1;
+            for (int w0 = wlo; w0 <= whi; w0 += 32) {
                 const int wi = w0 + lane;
                 uint32_t bits = 0u;
                 if (wi <= whi) {
@@ -441,28 +391,15 @@ __global__ void k_ga_children(const GaEntry* __restrict__ ents, int n_ents, int 
             if (lane == l) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)want << 8);
             if (lane == jl) my_bcr = (my_bcr & 0xffff00ffu) | ((uint32_t)(uint8_t)old << 8);
             if (jl > l && jl < 32) m = old != pbj ? (m | (1u << jl)) : (m & ~(1u << jl));
-            if (REG) {
-                // the owning lanes update their mask words; lane 0 records the child in shared memory
-                if (lane == (pi >> 5)) reg_and(mk, old, ~(1u << (pi & 31)));     // i now equals B_i
-                if (lane == (pp >> 5)) {
-                    reg_and(mk, want, ~(1u << (pp & 31)));                        // j no longer holds B_i
-                    if (pbj != old) reg_or(mk, old, 1u << (pp & 31));
-                }
-                if (lane == 0) {
-                    ch[j] = (int8_t)old;
-                    ch[ii] = (int8_t)want;
-                }
-            } else {
-                __syncwarp();                           // every lane has read mis for this candidate
-                if (lane == 0) {                        // three updates of different bits
-                    ch[j] = (int8_t)old;
-                    ch[ii] = (int8_t)want;
-                    atomicAnd(&mis[old * W + (pi >> 5)], ~(1u << (pi & 31)));     // i now equals B_i
-                    atomicAnd(&mis[want * W + (pp >> 5)], ~(1u << (pp & 31)));    // j no longer holds B_i
-                    if (pbj != old) atomicOr(&mis[old * W + (pp >> 5)], 1u << (pp & 31));
-                }
-                __syncwarp();
+            __syncwarp();                               // every lane has read mis for this candidate
+            if (lane == 0) {                            // three updates of different bits
+                ch[j] = (int8_t)old;
+                ch[ii] = (int8_t)want;
+                atomicAnd(&mis[old * W + (pi >> 5)], ~(1u << (pi & 31)));     // i now equals B_i
+                atomicAnd(&mis[want * W + (pp >> 5)], ~(1u << (pp & 31)));    // j no longer holds B_i
+                if (pbj != old) atomicOr(&mis[old * W + (pp >> 5)], 1u << (pp & 31));
             }
+            __syncwarp();
             ++nsw;
         }
     }
@@ -786,14 +723,10 @@ static goac_status ga_gen_launch(goac_ctx* ctx, const GaLaunch& L, uint32_t gen,
     goac::launch(k_ga_select, n, 1024, 0, st, (const GaEntry*)L.dev, 1, g, patience);
     if (L.any_elite) goac::launch(k_ga_rank, (int)((L.total + 7) / 8), 256, 0, st, (const GaEntry*)L.dev, n, L.total);
     GOAC_LAUNCH_CHECK("ga prep");
-    // masks in registers when every population has at most 1,024 variable sites and GA_REG_S species
-    bool reg = true;
-    for (const GaEntry& e : L.e) reg = reg && e.Nv <= 1024 && e.S <= GA_REG_S;
-    auto kern = reg ? k_ga_children<true> : k_ga_children<false>;
-    GOAC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    GOAC_CUDA(cudaFuncSetAttribute(k_ga_children, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     KTimer kt(ctx, KID_GA, st);
-    goac::launch(kern, L.blocks, 32 * L.wpb, L.smem_children, st, (const GaEntry*)L.dev, n, L.wpb, gen, parity,
-                 p_mut, ctx->d_err);
+    goac::launch(k_ga_children, L.blocks, 32 * L.wpb, L.smem_children, st, (const GaEntry*)L.dev, n, L.wpb, gen,
+                 parity, p_mut, ctx->d_err);
     GOAC_LAUNCH_CHECK("k_ga_children");
     return GOAC_OK;
 }
