@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--form", default=FORM, choices=sorted(TERMS))
     ap.add_argument("--mc-steps", type=int, default=4096)
+    ap.add_argument("--tile", action="append", default=[],
+                    help="FORM=M,N,K: fixed scoring tile shape for a form instead of the autotuner (profiling runs)")
     ap.add_argument("--mc-shapes", default="",
                     help="'W,c:W,c' fixed Monte Carlo launch shapes (FP64:FP32) instead of the autotuner")
     ap.add_argument("--cpu-sample", type=int, default=512, help="configurations the CPU oracle scores")
@@ -254,9 +256,12 @@ def _kernel_hash(form="bf16x2") -> str:
     while it is unchanged."""
     csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
     src = open(os.path.join(csrc, "score_tc.cu")).read()
-    if form == "exact":
-        a = src.index("__global__ void __launch_bounds__(192, 1)\n    k_score_exact(")
+    if form == "exact_pair":
+        a = src.index("__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
         b = src.index("// Per 128-row panel I of the symmetric operand")
+    elif form == "exact":
+        a = src.index("__global__ void __launch_bounds__(192, 1)\n    k_score_exact(")
+        b = src.index("// Exact form on CTA pairs (tcgen05 cta_group::2)")
     else:
         a = src.index("template <int T, bool TF32, int TN>\n__global__ void __launch_bounds__(192, 1)")
         b = src.index("__device__ __forceinline__ float to_tf32_rna(")
@@ -313,20 +318,25 @@ def _kernel_ms(ctx, gp, pop, form, steps, flush, E):
     return kern_ms / max(kern_n, 1), kern_n
 
 
-def _roofline(form, terms, kern_ms, kern_n, N, B):
+def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128):
     ld = ((N + 127) // 128) * 128
     bpad = ((B + 255) // 256) * 256
     nbm = ld // 128
-    # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld
-    flops_exec = terms * 2.0 * 128 * 128 * (nbm * (nbm + 1) // 2) * bpad
+    pair = form == "exact" and tile_m == 256
+    # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld; on CTA pairs
+    # both panels of pair-panel P run from column 256 P (one block of zeros for the odd panel)
+    blocks = (sum(min(2, nbm - 2 * P) * (nbm - 2 * P) for P in range((nbm + 1) // 2)) if pair
+              else nbm * (nbm + 1) // 2)
+    flops_exec = terms * 2.0 * 128 * 128 * blocks * bpad
     flops_useful = 2.0 * N * N * B
     bf16_peak, _, peak_kind = _peaks()
     tf32 = "tf32" in form
     peak = bf16_peak / 2.0 if tf32 else bf16_peak     # TF32 runs at half the BF16 rate; FP16 = BF16
     achieved = flops_exec / (kern_ms / 1e3) / 1e12
-    kernel = "k_score_exact" if form == "exact" else f"k_score_tc<{terms},{'true' if tf32 else 'false'}>"
+    kernel = ("k_score_exact_pair" if pair else "k_score_exact<256>") if form == "exact" else \
+        f"k_score_tc<{terms},{'true' if tf32 else 'false'},256>"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": _traffic(form), "kernel": kernel, "kernel_ms": kern_ms,
+            "traffic": _traffic("exact_pair" if pair else form), "kernel": kernel, "kernel_ms": kern_ms,
             "kernel_timing": f"CUDA events around each launch, a second loop of {kern_n} steps (L2 flushed "
                              f"between steps)",
             "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
@@ -372,7 +382,16 @@ def run_ours(args, world, rank, local):
     info = gp.exact_info()
     terms = {f: (info[1] if f == "exact" else TERMS[f]) for f in (form, other)}
 
-    # warm-up (also builds the split operand copies of both forms)
+    # tile shapes of both forms from the library's autotuner (also builds the split operand copies),
+    # or fixed by --tile
+    fixed = {t.split("=")[0]: tuple(int(x) for x in t.split("=")[1].split(",")) for t in args.tile}
+    shapes = {}
+    for f in (form, other):
+        if f in fixed:
+            shapes[f] = fixed[f]
+            gp.score_set_shape(B_POP, f, shapes[f][1], shapes[f][2], tile_m=shapes[f][0])
+        else:
+            shapes[f] = gp.score_autotune(pop, f)[:3]
     for _ in range(max(3, args.warmup)):
         gp.score(pop, form)
         gp.score(pop, other)
@@ -394,7 +413,7 @@ def run_ours(args, world, rank, local):
     # the dominant kernel's own duration: the same steps again with the library's
     # per-kernel CUDA events around the scoring kernel
     kern_ms, kern_n = _kernel_ms(ctx, gp, pop, form, min(args.steps, 400), flush, E)
-    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP)
+    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP, shapes[form][0])
 
     # the other form (BF16x2 beside the FP64-grade headline): same timing, own roofline
     o_ms, _ = _time_form(gp, pop, other, min(args.steps, 400), flush, E)
@@ -561,13 +580,19 @@ def run_ours(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": WORKLOAD, "N": prob.N, "B": B_POP, "form": form, "form_detail": detail,
+                           "tile_shape": {"sites": shapes[form][0], "configurations": shapes[form][1],
+                                          "k_chunk_blocks": shapes[form][2],
+                                          "chosen_by": "fixed (--tile)" if form in fixed else
+                                          "goac_score_autotune (CUDA events over 15 shapes)"},
                            "l2": "256 MB buffer written between steps (outside the step events)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk,
                 "energy_error_vs_fp64": err_vs_fp64(E_form),
                 other: {"value": world * B_POP / (o_ms / 1e3), "unit": "evals/s", "ms_per_step": o_ms,
-                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP),
+                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP, shapes[other][0]),
+                        "tile_shape": {"sites": shapes[other][0], "configurations": shapes[other][1],
+                                       "k_chunk_blocks": shapes[other][2]},
                         "energy_error_vs_fp64": err_vs_fp64(E_other), "speedup_over_fp64_path": f64_ms / o_ms},
                 "fp64_gpu_path": {"evals_per_s": world * B_POP / (f64_ms / 1e3), "ms_per_step": f64_ms,
                                   "speedup_of_form": f64_ms / ms},

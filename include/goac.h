@@ -160,20 +160,24 @@ goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B,
 
 /* Tile shape of the tensor-core scoring kernels (no counterpart in the       *
  * paper; the results of EXACT do not depend on it, those of the split forms  *
- * change only by FP32 rounding).  A tile covers 128 sites x tile_n (128 or   *
- * 256) configurations; ksplit > 0 cuts each 128-row panel's column range     *
- * into chunks of ksplit 128-column blocks scored as separate tiles (the       *
- * row-dot is linear, so each chunk adds a partial sum; this spreads small    *
- * populations over all SMs).  goac_score_set_shape stores a shape for         *
- * (precision, B rounded up to 256) (tile_n = ksplit = 0: the default, 256     *
- * and whole ranges); goac_score_autotune times every shape in {256, 128} x   *
- * {0, 16, 8, 4, 2} on species_dev (B x Nv), CUDA events on the context       *
- * stream, stores the fastest for later goac_score calls with that precision  *
- * and padded B, and returns it (tile_n_out, ksplit_out, ms_out: nullable;    *
- * ms per scoring call).  Host-side store; autotune synchronises.              */
-goac_status goac_score_set_shape(goac_problem* prob, int32_t precision, int32_t B, int32_t tile_n, int32_t ksplit);
+ * change only by FP32 rounding).  A tile covers tile_m sites x tile_n        *
+ * configurations: tile_m 128 (one CTA) or 256 (EXACT only: a pair of CTAs on *
+ * one TPC issuing M = 256 tcgen05 MMAs, each CTA loading its own 128 digit   *
+ * rows and half of the configurations; needs tile_n 256), tile_n 128 or 256; *
+ * ksplit > 0 cuts each row panel's column range into chunks of ksplit         *
+ * 128-column blocks scored as separate tiles (the row-dot is linear, so each  *
+ * chunk adds a partial sum; this spreads small populations over all SMs).    *
+ * goac_score_set_shape stores a shape for (precision, B rounded up to 256)    *
+ * (all 0: the default, 128 x 256 and whole ranges); goac_score_autotune times *
+ * every shape in {128 x 256, 128 x 128, 256 x 256 (EXACT)} x {0, 16, 8, 4, 2}*
+ * on species_dev (B x Nv), CUDA events on the context stream, stores the      *
+ * fastest for later goac_score calls with that precision and padded B, and    *
+ * returns it (outputs nullable; ms per scoring call).  Host-side store;       *
+ * autotune synchronises.                                                      */
+goac_status goac_score_set_shape(goac_problem* prob, int32_t precision, int32_t B, int32_t tile_m, int32_t tile_n,
+                                 int32_t ksplit);
 goac_status goac_score_autotune(goac_problem* prob, const int8_t* species_dev, int32_t B, int32_t precision,
-                                int32_t* tile_n_out, int32_t* ksplit_out, double* ms_out);
+                                int32_t* tile_m_out, int32_t* tile_n_out, int32_t* ksplit_out, double* ms_out);
 
 /* Digit layout the EXACT form uses on this problem (host outputs, nullable):  *
  * digit_bits r, digits T and the charge scaling kq of the rule above; the     *

@@ -240,18 +240,19 @@ class Problem:
         _check(lib.goac_score(self.handle, _ptr(species), B, _prec(precision), _ptr(E)), "goac_score")
         return E
 
-    def score_set_shape(self, B: int, precision="bf16x2", tile_n: int = 0, ksplit: int = 0):
-        """Tile shape for scoring B configurations in a tensor-core form (0, 0 = default)."""
-        _check(lib.goac_score_set_shape(self.handle, _prec(precision), int(B), int(tile_n), int(ksplit)),
+    def score_set_shape(self, B: int, precision="bf16x2", tile_n: int = 0, ksplit: int = 0, tile_m: int = 0):
+        """Tile shape for scoring B configurations in a tensor-core form (all 0 = default;
+        tile_m 256 = CTA pairs, exact form only)."""
+        _check(lib.goac_score_set_shape(self.handle, _prec(precision), int(B), int(tile_m), int(tile_n), int(ksplit)),
                "goac_score_set_shape")
 
     def score_autotune(self, species: torch.Tensor, precision="bf16x2"):
         """Time the scoring tile shapes on `species` and keep the fastest for this
-        (precision, padded B).  Returns (tile_n, ksplit, ms per call)."""
-        tn, kc, ms = C.c_int32(), C.c_int32(), C.c_double()
-        _check(lib.goac_score_autotune(self.handle, _ptr(species), species.shape[0], _prec(precision), C.byref(tn),
-                                       C.byref(kc), C.byref(ms)), "goac_score_autotune")
-        return int(tn.value), int(kc.value), float(ms.value)
+        (precision, padded B).  Returns (tile_m, tile_n, ksplit, ms per call)."""
+        tm, tn, kc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib.goac_score_autotune(self.handle, _ptr(species), species.shape[0], _prec(precision), C.byref(tm),
+                                       C.byref(tn), C.byref(kc), C.byref(ms)), "goac_score_autotune")
+        return int(tm.value), int(tn.value), int(kc.value), float(ms.value)
 
     def score_host(self, species: np.ndarray | torch.Tensor, precision="f64", out=None):
         """End-to-end scoring from host memory (pinned torch tensors are fastest)."""

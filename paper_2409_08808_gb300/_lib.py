@@ -62,8 +62,8 @@ SIGNATURES = {
     "goac_problem_phi_fix": (_st, [_p, _p]),
     "goac_score": (_st, [_p, _p, _i32, _i32, _p]),
     "goac_problem_exact_info": (_st, [_p, _p, _p, _p]),
-    "goac_score_set_shape": (_st, [_p, _i32, _i32, _i32, _i32]),
-    "goac_score_autotune": (_st, [_p, _p, _i32, _i32, _p, _p, _p]),
+    "goac_score_set_shape": (_st, [_p, _i32, _i32, _i32, _i32, _i32]),
+    "goac_score_autotune": (_st, [_p, _p, _i32, _i32, _p, _p, _p, _p]),
     "goac_score_host": (_st, [_p, _p, _i32, _i32, _p]),
     "goac_score_host_async": (_st, [_p, _p, _i32, _i32, _p]),
     "goac_score_f64_noalloc": (_st, [_p, _i32, _i32, _p, _i32, _p, _p, _d, _p, _p]),

@@ -33,6 +33,7 @@
 #include <functional>
 #include <mutex>
 #include <queue>
+#include <tuple>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -704,6 +705,216 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+// Exact form on CTA pairs (tcgen05 cta_group::2): a cluster of two CTAs on
+// one TPC computes a tile of 256 sites (panels 2P in the even CTA, 2P + 1 in
+// the odd one) x 256 configurations with M = 256 MMAs issued by the even CTA.
+// Each CTA loads its own panel's digit rows and half of the configuration
+// tile's Q rows (128 each), so per MMA a CTA's shared memory takes in 8 KB
+// and serves 12 KB (its A rows, and its Q rows to both tensor cores) instead of
+// 12 + 12 KB: the same traffic per tensor-core cycle as the two-term BF16
+// kernel.  Pair-panel P covers columns from 256 P, so panel 2P + 1 multiplies
+// one 128 x 128 block of zeros (below the diagonal of the symmetric operand).
+// Barriers: the even CTA's full[s] counts both CTAs' TMA bytes (the odd CTA's
+// loads signal it through its cluster address), the MMA commits arrive on
+// empty[s] and tfull[a] of both CTAs, and the eight epilogue warps of the pair
+// arrive on the even CTA's tempty[a].  Every wait is clock-bounded as in the
+// one-CTA kernels; both CTAs meet at a cluster barrier before freeing their
+// tensor memory and exiting.
+struct PairTile {
+    int P, n, kb0, kb1, slot0, slot1, t;    // slot1 < 0: panel 2P + 1 does not exist
+};
+
+constexpr int PX_HN = 128;                              // configurations per CTA's half of the tile
+constexpr int PX_STAGE = A_TILE + PX_HN * ROW_BYTES;    // 32 KB
+constexpr int PX_STAGES = 6;
+constexpr int PX_SMEM = PX_STAGES * PX_STAGE + 1024 + 256;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    k_score_exact_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const PairTile* __restrict__ work, const int* __restrict__ work_start, int ld, int T,
+                       const __half* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
+{
+    constexpr int TN = 256;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + PX_STAGES * PX_STAGE);
+    uint64_t* empty = full + PX_STAGES;
+    uint64_t* tfull = empty + PX_STAGES;        // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;               // [2] accumulator drained (the even CTA's counts both)
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    __shared__ int red_hi[4][TN], red_lo[4][TN];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = goacd::cluster_ctarank();
+    const int pair = blockIdx.x >> 1;
+    const int w0 = work_start[pair], w1 = work_start[pair + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PX_STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 8);
+        }
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmA);
+        goacd::prefetch_tmap(&tmB);
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc_pair(tmem_slot, 2 * TN);
+        goacd::tmem_relinquish_pair();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::cluster_sync();                      // the even CTA's barriers exist before the odd one signals them
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    goacd::pdl_wait();
+    goacd::pdl_trigger();
+
+    if (warp == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        if (lane == 0) {
+            int it = 0;
+            for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
+                const PairTile tile = work[wi];
+                const int m0 = (2 * tile.P + (int)rank) * TC_M, n0 = tile.n * TN + (int)rank * PX_HN;
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
+                    const int s = it % PX_STAGES;
+                    const uint32_t use = (uint32_t)(it / PX_STAGES);
+                    if (it >= PX_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * PX_STAGE;
+                    const uint32_t fbar = goacd::mapa_shared(goacd::smem_u32(&full[s]), 0);
+                    if (rank == 0) goacd::mbar_arrive_expect_tx(&full[s], 2 * PX_STAGE);
+                    goacd::tma_load_2d_pair(st, &tmA, fbar, kb * 64, tile.t * ld + m0);
+                    goacd::tma_load_2d_pair(st + A_TILE, &tmB, fbar, kb * 64, n0);
+                }
+            }
+            if (*abort_flag && rank == 0)
+                // every copy of the pair counted on these barriers must land before the CTAs exit
+                for (int k = it - PX_STAGES < 0 ? 0 : it - PX_STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % PX_STAGES], (uint32_t)(k / PX_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (the even CTA) ----------------
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, 2 * TC_M, TN);   // FP16, M = 256
+            int it = 0, tl = 0;
+            for (int wi = w0; wi < w1; ++wi, ++tl) {
+                const PairTile tile = work[wi];
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
+                }
+                goacd::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TN);
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % PX_STAGES;
+                    const uint32_t use = (uint32_t)(it / PX_STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t a0 = goacd::smem_u32(smem + s * PX_STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        goacd::mma_f16_pair(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
+                                            goacd::sdesc_k128(a0 + A_TILE + kk * 32), idesc,
+                                            (kb != tile.kb0 || kk != 0) ? 1u : 0u);
+                    goacd::mma_commit_pair(&empty[s], 0x3);
+                }
+                goacd::mma_commit_pair(&tfull[acc_i], 0x3);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5 of both CTAs ----------------
+        const int lg = warp & 3;
+        const int etid = threadIdx.x - 64;
+        int tl = 0;
+        for (int wi = w0; wi < w1; ++wi, ++tl) {
+            const PairTile tile = work[wi];
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            const int slot = rank == 0 ? tile.slot0 : tile.slot1;
+            const int v = (2 * tile.P + (int)rank) * TC_M + lg * 32 + lane;
+            const long n0 = (long)tile.n * TN;
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                int hi[32], lo[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const long b = n0 + c * 32 + j;
+                    const int q = slot >= 0 ? __float2int_rn(__half2float(qt[b * ld + v])) : 0;
+                    const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
+                    hi[j] = (a >> 12) * q;
+                    lo[j] = (a & 4095) * q;
+                }
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const bool up = (lane & sft) != 0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < sft) {
+                            const int sh = up ? hi[k] : hi[k + sft], kh = up ? hi[k + sft] : hi[k];
+                            const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
+                            hi[k] = kh + __shfl_xor_sync(0xffffffffu, sh, sft);
+                            lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                        }
+                }
+                red_hi[lg][c * 32 + lane] = hi[0];
+                red_lo[lg][c * 32 + lane] = lo[0];
+            }
+            goacd::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) goacd::mbar_arrive(&tempty[acc_i]);
+                else goacd::mbar_arrive_cluster(goacd::mapa_shared(goacd::smem_u32(&tempty[acc_i]), 0));
+            }
+            goacd::named_bar_sync(1, 128);
+            if (ok && slot >= 0)
+                for (int col = etid; col < TN; col += 128) {
+                    const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
+                    const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
+                    partial[((long)slot * T + tile.t) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                }
+            goacd::named_bar_sync(1, 128);
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::cluster_sync();                      // no CTA leaves while its peer may still reach its memory
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc_pair(tmem, 2 * TN);
+    }
+}
+
 // Per 128-row panel I of the symmetric operand (sym != 0) or of J itself:
 // e_I with max |J'| (max |J|) < 2^e_I.
 __global__ void k_panel_exp(const double* __restrict__ J, int ld, int sym, int* __restrict__ pexp)
@@ -1284,6 +1495,147 @@ goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorM
     return GOAC_OK;
 }
 
+// Schedule of the CTA-pair kernel: pair tiles (pair-panel P, configuration
+// tile n, k-chunk, digit t) longest first over the pairs; panel I's k-chunk
+// slots are numbered panel by panel (pslot[I] .. pslot[I+1]) as for the
+// one-CTA kernel, with panel 2P + 1 chunked like its pair-panel.
+goac_status pair_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int npairs, const PairTile** work,
+                          const int** starts, const int** pslot)
+{
+    if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || npairs <= 0 || npairs >= (1 << 19) ||
+        T < 1 || T > 15 || kc < 0 || kc >= (1 << 16))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "pair schedule: shape out of range");
+    const uint64_t k0 = ((uint64_t)nbm << 46) | ((uint64_t)nbn << 20) | (uint64_t)npairs;
+    const uint64_t k1 = (1ull << 40) | ((uint64_t)T << 24) | ((uint64_t)kc << 8) | 2ull;
+    if (sc.key[0] != k0 || sc.key[1] != k1) {
+        const int kbm = 2, nkb = nbm * kbm, npp = (nbm + 1) / 2;
+        std::vector<int> ps(nbm + 1, 0), nch(npp, 0);
+        for (int P = 0; P < npp; ++P) {
+            const int span = nkb - 2 * P * kbm;
+            const int step = kc > 0 ? kc * kbm : span;
+            nch[P] = (span + step - 1) / step;
+        }
+        int slot = 0;
+        for (int I = 0; I < nbm; ++I) {
+            ps[I] = slot;
+            slot += nch[I / 2];
+        }
+        ps[nbm] = slot;
+        std::vector<PairTile> tiles;
+        for (int P = 0; P < npp; ++P) {
+            const int step = kc > 0 ? kc * kbm : nkb - 2 * P * kbm;
+            int c = 0;
+            for (int kb0 = 2 * P * kbm; kb0 < nkb; kb0 += step, ++c) {
+                const int kb1 = std::min(nkb, kb0 + step);
+                const int s0 = ps[2 * P] + c, s1 = 2 * P + 1 < nbm ? ps[2 * P + 1] + c : -1;
+                for (int n = 0; n < nbn; ++n)
+                    for (int t = 0; t < T; ++t) tiles.push_back(PairTile{P, n, kb0, kb1, s0, s1, t});
+            }
+        }
+        std::stable_sort(tiles.begin(), tiles.end(),
+                         [](const PairTile& a, const PairTile& b) { return a.kb1 - a.kb0 > b.kb1 - b.kb0; });
+        std::vector<std::vector<PairTile>> per(npairs);
+        std::priority_queue<std::pair<long, int>, std::vector<std::pair<long, int>>,
+                            std::greater<std::pair<long, int>>>
+            heap;
+        for (int c = 0; c < npairs; ++c) heap.push({0L, c});
+        for (const PairTile& t : tiles) {
+            const auto [ld0, best] = heap.top();
+            heap.pop();
+            per[best].push_back(t);
+            heap.push({ld0 + (t.kb1 - t.kb0) / kbm + 1, best});
+        }
+        std::vector<PairTile> flat;
+        std::vector<int> st(npairs + 1, 0);
+        for (int c = 0; c < npairs; ++c) {
+            st[c] = (int)flat.size();
+            flat.insert(flat.end(), per[c].begin(), per[c].end());
+        }
+        st[npairs] = (int)flat.size();
+        const size_t bytes = sizeof(PairTile) * flat.size() + sizeof(int) * (npairs + 1 + nbm + 1) + 64;
+        goac_status rc = goac::ensure(sc.buf, bytes);
+        if (rc) return rc;
+        PairTile* dw = (PairTile*)sc.buf.ptr;
+        int* ds = (int*)(dw + flat.size());
+        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(PairTile) * flat.size(), cudaMemcpyHostToDevice));
+        GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (npairs + 1), cudaMemcpyHostToDevice));
+        GOAC_CUDA(cudaMemcpy(ds + npairs + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice));
+        sc.key[0] = k0;
+        sc.key[1] = k1;
+        sc.ntiles = (int)flat.size();
+        sc.nslots = slot;
+        sc.grid = npairs;
+    }
+    *work = (const PairTile*)sc.buf.ptr;
+    *starts = (const int*)((const PairTile*)sc.buf.ptr + sc.ntiles);
+    *pslot = *starts + sc.grid + 1;
+    return GOAC_OK;
+}
+
+// Partial-sum slots of the pair kernel's shape (see pair_schedule).
+int pair_slot_count(int nbm, int kc)
+{
+    int slot = 0;
+    for (int I = 0; I < nbm; ++I) {
+        const int span = 2 * nbm - 2 * 2 * (I / 2);
+        const int step = kc > 0 ? kc * 2 : span;
+        slot += (span + step - 1) / step;
+    }
+    return slot;
+}
+
+// CTA pairs that can be resident at once (clusters of two with the pair kernel's shared memory).
+static int max_pairs(goac_problem* p)
+{
+    static std::atomic<int> cached[64] = {};
+    const int dev = p->ctx->device & 63;
+    int v = cached[dev].load();
+    if (v > 0) return v;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (p->ctx->num_sms / 2));
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = PX_SMEM;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_score_exact_pair, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = p->ctx->num_sms / 2;
+    }
+    n = std::min(n, p->ctx->num_sms / 2);
+    cached[dev].store(n);
+    return n;
+}
+
+goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, int B, int kc,
+                              double* part, const double* lin, double* E_out)
+{
+    static std::atomic<uint64_t> attr_done{0};
+    goac_status rc = smem_attr_once((const void*)k_score_exact_pair, PX_SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
+    const int ld = p->Nv_pad, T = p->dig_T;
+    const int nbm = ld / TC_M, nbn = (B + 255) / 256, npp = (nbm + 1) / 2;
+    long ntiles = 0;
+    for (int P = 0; P < npp; ++P) {
+        const int span = 2 * nbm - 4 * P;
+        ntiles += (long)(kc > 0 ? (span + 2 * kc - 1) / (2 * kc) : 1) * nbn * T;
+    }
+    const int npairs = (int)std::min<long>(ntiles, max_pairs(p));
+    const PairTile* work = nullptr;
+    const int* starts = nullptr;
+    const int* pslot = nullptr;
+    rc = pair_schedule(p->sched_ex, nbm, nbn, T, kc, npairs, &work, &starts, &pslot);
+    if (rc) return rc;
+    {
+        goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
+        goac::launch_pdl(k_score_exact_pair, 2 * npairs, 192, PX_SMEM, p->ctx->stream, ma, mb, work, starts, ld, T,
+                         (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+        GOAC_LAUNCH_CHECK("k_score_exact_pair");
+    }
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, p->ctx->stream, (const double*)part, nbm, pslot,
+                     (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
+    GOAC_LAUNCH_CHECK("k_finish_exact");
+    return GOAC_OK;
+}
+
 }  // namespace
 
 namespace goac {
@@ -1489,13 +1841,15 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
 }
 
 // Tile shape of the scoring kernels for (precision, padded batch): the one
-// goac_score_autotune or goac_score_set_shape stored, else 256 configurations
-// per tile and whole panel ranges.
-static void pick_shape(const goac_problem* p, int precision, int Bpad, int* TN, int* kc)
+// goac_score_autotune or goac_score_set_shape stored, else 128 sites x 256
+// configurations per tile and whole panel ranges.
+static void pick_shape(const goac_problem* p, int precision, int Bpad, int* TM, int* TN, int* kc)
 {
     const auto it = p->tile_shape.find(std::make_pair(precision, Bpad));
-    *TN = it != p->tile_shape.end() ? it->second.first : TC_N;
-    *kc = it != p->tile_shape.end() ? it->second.second : 0;
+    const bool has = it != p->tile_shape.end();
+    *TM = has ? std::get<0>(it->second) : TC_M;
+    *TN = has ? std::get<1>(it->second) : TC_N;
+    *kc = has ? std::get<2>(it->second) : 0;
 }
 
 static goac_status score_exact(goac_problem* p, const int8_t* species, int B, double* E_out)
@@ -1506,9 +1860,10 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     const int T = p->dig_T;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int nbm = ld / TC_M;
-    int TN = 0, kc = 0;
-    pick_shape(p, GOAC_PREC_EXACT, Bpad, &TN, &kc);
-    const int nslots = tc_tile_count(nbm, (B + TN - 1) / TN, T, kc).y;
+    int TM = 0, TN = 0, kc = 0;
+    pick_shape(p, GOAC_PREC_EXACT, Bpad, &TM, &TN, &kc);
+    const bool pair = TM == 2 * TC_M;
+    const int nslots = pair ? pair_slot_count(nbm, kc) : tc_tile_count(nbm, (B + TN - 1) / TN, T, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * 2);
     if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * T * Bpad + Bpad));
     if (rc) return rc;
@@ -1521,8 +1876,9 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
     CUtensorMap ma, mb;
     rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TN);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, pair ? PX_HN : TN);
     if (rc) return rc;
+    if (pair) return launch_exact_pair(p, ma, mb, Bpad, B, kc, part, lin, E_out);
     if (TN == TC_NS) return launch_exact<TC_NS>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
     return launch_exact<TC_N>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
 }
@@ -1549,8 +1905,8 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     const int ld = p->Nv_pad;
     const int Bpad = ((B + TC_N - 1) / TC_N) * TC_N;
     const int eb = tf32 ? 4 : 2;
-    int TN = 0, kc = 0;
-    pick_shape(p, precision, Bpad, &TN, &kc);
+    int TM = 0, TN = 0, kc = 0;
+    pick_shape(p, precision, Bpad, &TM, &TN, &kc);
     const int nslots = tc_tile_count(ld / TC_M, (B + TN - 1) / TN, 1, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * eb);
     if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * Bpad + Bpad));
@@ -1592,24 +1948,28 @@ static bool shaped_form(int precision)
 
 }  // namespace goac
 
-extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, int32_t B, int32_t tile_n,
-                                            int32_t ksplit)
+extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, int32_t B, int32_t tile_m,
+                                            int32_t tile_n, int32_t ksplit)
 {
     if (!p) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: NULL problem");
     if (!goac::shaped_form(precision))
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: not a tensor-core form");
-    if (B < 1 || B > GOAC_MAX_BATCH || !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 ||
-        ksplit > 65535)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: B >= 1, tile_n 0, 128 or 256, ksplit 0..65535");
+    if (B < 1 || B > GOAC_MAX_BATCH || !(tile_m == 0 || tile_m == 128 || tile_m == 256) ||
+        !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 || ksplit > 65535)
+        return goac::fail(GOAC_ERR_INVALID_ARG,
+                          "goac_score_set_shape: B >= 1, tile_m 0, 128 or 256, tile_n 0, 128 or 256, ksplit 0..65535");
+    if (tile_m == 256 && (precision != GOAC_PREC_EXACT || tile_n == 128))
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: 256-site tiles (CTA pairs) need EXACT and tile_n 256");
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
-    if (tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
-    else p->tile_shape[key] = std::make_pair(tile_n == 0 ? 256 : (int)tile_n, (int)ksplit);
+    if (tile_m == 0 && tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
+    else p->tile_shape[key] = std::make_tuple(tile_m == 0 ? 128 : (int)tile_m, tile_n == 0 ? 256 : (int)tile_n, (int)ksplit);
     return GOAC_OK;
 }
 
 extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* species_dev, int32_t B, int32_t precision,
-                                           int32_t* tile_n_out, int32_t* ksplit_out, double* ms_out)
+                                           int32_t* tile_m_out, int32_t* tile_n_out, int32_t* ksplit_out,
+                                           double* ms_out)
 {
     if (!p || !species_dev || B < 1 || B > GOAC_MAX_BATCH)
         return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_autotune: bad argument");
@@ -1625,14 +1985,17 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
     const int nbm = p->Nv_pad / 128;
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
-    const int tns[2] = {256, 128}, kcs[5] = {0, 16, 8, 4, 2};
-    int best_tn = 0, best_kc = 0;
+    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles (CTA pairs) for the exact form
+    const int shapes[3][2] = {{128, 256}, {128, 128}, {256, 256}};
+    const int nshapes = precision == GOAC_PREC_EXACT ? 3 : 2;
+    const int kcs[5] = {0, 16, 8, 4, 2};
+    int best_tm = 0, best_tn = 0, best_kc = 0;
     float best = 0.0f;
     goac_status rc = GOAC_OK;
-    for (int i = 0; i < 2 && !rc; ++i)
+    for (int i = 0; i < nshapes && !rc; ++i)
         for (int j = 0; j < 5 && !rc; ++j) {
             if (kcs[j] >= nbm) continue;                 // the same as whole panel ranges
-            p->tile_shape[key] = std::make_pair(tns[i], kcs[j]);
+            p->tile_shape[key] = std::make_tuple(shapes[i][0], shapes[i][1], kcs[j]);
             rc = goac_score(p, species_dev, B, precision, E);     // schedule, operands, warm-up
             if (rc) break;
             cudaEventRecord(a, st);
@@ -1643,7 +2006,8 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, a, b);
             if (best_tn == 0 || ms < best) {
-                best_tn = tns[i];
+                best_tm = shapes[i][0];
+                best_tn = shapes[i][1];
                 best_kc = kcs[j];
                 best = ms;
             }
@@ -1656,7 +2020,8 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
         p->tile_shape.erase(key);
         return rc;
     }
-    p->tile_shape[key] = std::make_pair(best_tn, best_kc);
+    p->tile_shape[key] = std::make_tuple(best_tm, best_tn, best_kc);
+    if (tile_m_out) *tile_m_out = best_tm;
     if (tile_n_out) *tile_n_out = best_tn;
     if (ksplit_out) *ksplit_out = best_kc;
     if (ms_out) *ms_out = best / 3.0;

@@ -17,6 +17,8 @@ from gpu_common import build_pair, form_tolerance, gpu_problem
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(256, 0), (128, 0), (256, 16), (128, 8), (256, 4), (128, 2), (256, 1)]
+# (tile_m, tile_n, ksplit) of the CTA-pair kernel (exact form only)
+PAIR_SHAPES = [(256, 256, 0), (256, 256, 8), (256, 256, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -44,6 +46,10 @@ def test_exact_form_identical_in_every_shape(cubic, B):
         gp.score_set_shape(B, "exact", tn, kc)
         E = gp.score(pop, "exact")
         assert torch.equal(E, ref), (tn, kc)
+    for tm, tn, kc in PAIR_SHAPES:
+        gp.score_set_shape(B, "exact", tn, kc, tile_m=tm)
+        E = gp.score(pop, "exact")
+        assert torch.equal(E, ref), (tm, tn, kc)
     gp.score_set_shape(B, "exact", 0, 0)
     rows = np.array([0, 1, B // 2, B - 1])
     Eo = oracle.score(Jc, prob.site_class, prob.fixed_q, prob.z, pop.cpu().numpy()[rows])
@@ -91,8 +97,9 @@ def test_autotuner_choice(cubic, form, B):
     pop = torch.tensor(pop_np, device="cuda")
     gp.score_set_shape(B, form, 0, 0)
     ref = gp.score(pop, form).clone()
-    tn, kc, ms = gp.score_autotune(pop, form)
+    tm, tn, kc, ms = gp.score_autotune(pop, form)
     assert tn in (128, 256) and kc in (0, 16, 8, 4, 2) and ms > 0
+    assert tm == 128 or (tm == 256 and form == "exact" and tn == 256)
     E = gp.score(pop, form)
     if form == "exact":
         assert torch.equal(E, ref)
@@ -114,3 +121,31 @@ def test_set_shape_rejects_bad_shapes(cubic):
                  (16, "f32", 0, 4)]:
         with pytest.raises(g.GoacError):
             gp.score_set_shape(*args)
+    for kw in [dict(tile_m=64), dict(tile_m=256, precision="bf16x2"), dict(tile_m=256, tile_n=128)]:
+        args = dict(B=16, precision="exact", tile_n=256, ksplit=0)
+        args.update(kw)
+        with pytest.raises(g.GoacError):
+            gp.score_set_shape(**args)
+
+
+def test_pair_kernel_odd_panel_count(ctx):
+    """Layered 12x12x1 cell: Nv = 864 sites make seven 128-row panels, so the
+    last CTA pair has no second panel; with fixed ions (a linear term).  Every
+    shape, the CTA pairs included, gives the default shape's exact energies."""
+    import paper_2409_08808_gb300 as g
+    prob = synth.layered_problem()
+    frac = torch.tensor(prob.frac, device="cuda")
+    Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, Jg)
+    B = 777
+    pop_np = synth.random_population(prob, B, 12)
+    pop = torch.tensor(pop_np, device="cuda")
+    gp.score_set_shape(B, "exact", 0, 0)
+    ref = gp.score(pop, "exact").clone()
+    for tm, tn, kc in PAIR_SHAPES + [(128, 256, 2)]:
+        gp.score_set_shape(B, "exact", tn, kc, tile_m=tm)
+        assert torch.equal(gp.score(pop, "exact"), ref), (tm, tn, kc)
+    gp.score_set_shape(B, "exact", 0, 0)
+    rows = np.array([0, 255, 256, B - 1])
+    Eo = oracle.score(Jg.cpu().numpy(), prob.site_class, prob.fixed_q, prob.z, pop_np[rows])
+    assert np.max(np.abs(ref.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
