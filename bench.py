@@ -257,10 +257,10 @@ def _kernel_hash(form="bf16x2") -> str:
     csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
     src = open(os.path.join(csrc, "score_tc.cu")).read()
     if form == "exact_pair":
-        a = src.index("__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
+        a = src.index("template <bool SPLIT>\n__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
         b = src.index("// Per 128-row panel I of the symmetric operand")
     elif form == "exact":
-        a = src.index("__global__ void __launch_bounds__(192, 1)\n    k_score_exact(")
+        a = src.index("template <int TN, bool SPLIT>\n__global__ void __launch_bounds__(192, SPLIT ? 1 : 2)\n    k_score_exact(")
         b = src.index("// Exact form on CTA pairs (tcgen05 cta_group::2)")
     else:
         a = src.index("template <int T, bool TF32, int TN>\n__global__ void __launch_bounds__(192, 1)")
@@ -318,7 +318,16 @@ def _kernel_ms(ctx, gp, pop, form, steps, flush, E):
     return kern_ms / max(kern_n, 1), kern_n
 
 
-def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128):
+def _exact_split(info, z, N):
+    """Whether the exact kernel's epilogue splits its integer sums in 12-bit
+    halves: the library does unless 32 max|q|^2 2^(r-1) Nv_pad < 2^31 (q the
+    charges scaled to integers, r the digit width)."""
+    r, _, kq = info
+    qmax = max(abs(float(x)) for x in z) * 2.0 ** kq
+    return not (32.0 * qmax * qmax * 2.0 ** (r - 1) * (((N + 127) // 128) * 128) < 2.0 ** 31)
+
+
+def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128, split=True):
     ld = ((N + 127) // 128) * 128
     bpad = ((B + 255) // 256) * 256
     nbm = ld // 128
@@ -333,7 +342,8 @@ def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128):
     tf32 = "tf32" in form
     peak = bf16_peak / 2.0 if tf32 else bf16_peak     # TF32 runs at half the BF16 rate; FP16 = BF16
     achieved = flops_exec / (kern_ms / 1e3) / 1e12
-    kernel = ("k_score_exact_pair" if pair else "k_score_exact<256>") if form == "exact" else \
+    kernel = (f"k_score_exact_pair<{str(split).lower()}>" if pair else
+              f"k_score_exact<256, {str(split).lower()}>") if form == "exact" else \
         f"k_score_tc<{terms},{'true' if tf32 else 'false'},256>"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": _traffic("exact_pair" if pair else form), "kernel": kernel, "kernel_ms": kern_ms,
@@ -413,7 +423,8 @@ def run_ours(args, world, rank, local):
     # the dominant kernel's own duration: the same steps again with the library's
     # per-kernel CUDA events around the scoring kernel
     kern_ms, kern_n = _kernel_ms(ctx, gp, pop, form, min(args.steps, 400), flush, E)
-    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP, shapes[form][0])
+    split = _exact_split(info, prob.z, prob.N)
+    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP, shapes[form][0], split)
 
     # the other form (BF16x2 beside the FP64-grade headline): same timing, own roofline
     o_ms, _ = _time_form(gp, pop, other, min(args.steps, 400), flush, E)
@@ -590,7 +601,7 @@ def run_ours(args, world, rank, local):
                 "clocks": clk,
                 "energy_error_vs_fp64": err_vs_fp64(E_form),
                 other: {"value": world * B_POP / (o_ms / 1e3), "unit": "evals/s", "ms_per_step": o_ms,
-                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP, shapes[other][0]),
+                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP, shapes[other][0], split),
                         "tile_shape": {"sites": shapes[other][0], "configurations": shapes[other][1],
                                        "k_chunk_blocks": shapes[other][2]},
                         "energy_error_vs_fp64": err_vs_fp64(E_other), "speedup_over_fp64_path": f64_ms / o_ms},

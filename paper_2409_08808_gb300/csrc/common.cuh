@@ -142,6 +142,7 @@ struct goac_problem {
     double* zq_dev = nullptr;          // 64, charges times 2^dig_kq
     int dig_kq = -1;
     int dig_r = 0, dig_T = 0;          // digit width (bits) and number of digits
+    bool dig_split = true;             // epilogue splits each digit sum in 12-bit halves (else one int32 sum)
     // exact-form potentials: digits of J_vv itself, its panel exponents, digit sums
     __half* J_dig_full = nullptr;      // [dig_T][Nv_pad][Nv_pad]
     int* dig_exp_full = nullptr;       // Nv_pad / 128

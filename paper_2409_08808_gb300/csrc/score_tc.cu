@@ -291,22 +291,40 @@ __device__ __forceinline__ float to_tf32_rna(float x)
 // with the configuration block fastest, so the CTAs of one wave cover every
 // configuration block of 19 row panels: each panel's J rows come from DRAM
 // once and are shared in L2, and the Q tiles are re-read once per wave.  Each
-// stage holds J hi / lo (128 x 32 FP32 each) and Q hi / lo (256 x 32 FP32
-// each): 96 KB for twelve MMAs, which keeps the shared-memory traffic per MMA
-// (12 KB in by TMA, 12 KB out to the tensor core) at the level of the
-// two-term BF16 scoring kernel; two stages fit.  Two FP32 accumulators in
+// stage holds J hi / lo (128 x 16 FP32 each) and Q hi / lo (256 x 16 FP32
+// each) in 64-byte-swizzled rows: 48 KB for six MMAs (8 KB in by TMA and
+// 12 KB out to the tensor core per MMA, as in the two-term BF16 scoring
+// kernel); four stages fit, three of them in flight while the tensor core
+// works on the fourth.  Two FP32 accumulators in
 // TMEM (2 x 256 columns) let the epilogue of one tile, which writes its 32
 // TMEM lanes (sites) to Phi[b][v] coalesced over sites, overlap the MMAs of
 // the next.  The padded batch is a multiple of 256.  The tiles that would
 // leave the last wave partly idle are split into two k-halves whose epilogues
 // add into a zeroed Phi (two FP32 addends onto zero: the same sum in either
-// order), so the wave count matches the work.
+// order), so the wave count matches the work.  Odd waves walk the k-range
+// backwards: the Q slices the previous wave read last are still in L2 when
+// the next wave starts, which saves part of the once-per-wave Q re-read.
 constexpr int PT_N = 256;
-constexpr int PT_A = TC_M * ROW_BYTES;        // 16 KB
-constexpr int PT_B = PT_N * ROW_BYTES;        // 32 KB
-constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 96 KB
-constexpr int PT_STAGES = 2;
+constexpr int PT_ROW = 64;                    // bytes of one operand row in a stage (16 FP32)
+constexpr int PT_KB = PT_ROW / 4;             // k elements per stage
+constexpr int PT_A = TC_M * PT_ROW;           // 8 KB
+constexpr int PT_B = PT_N * PT_ROW;           // 16 KB
+constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 48 KB
+constexpr int PT_STAGES = 4;
 constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
+
+// Shared-memory descriptor of a K-major operand tile with 64-byte rows and the
+// 64-byte swizzle (8-row groups 512 bytes apart).
+__device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;                // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
+    d |= (uint64_t)4 << 61;                         // 64-byte swizzle
+    return d;
+}
 
 // Work item `it` of k_phi_tc: the first nfull items are whole tiles (m-block,
 // configuration block fastest); each later tile is two items, its k-halves.
@@ -375,7 +393,9 @@ __global__ void __launch_bounds__(192, 1)
             for (int id = blockIdx.x; id < nitems && !*abort_flag; id += gridDim.x) {
                 const PhiItem w = phi_item(id, nfull, nbn, nkb);
                 const int m0 = w.m0, n0 = w.n0;
-                for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
+                const bool rev = ((id / gridDim.x) & 1) != 0;
+                for (int j = 0; j < w.kb1 - w.kb0; ++j, ++it) {
+                    const int kb = rev ? w.kb1 - 1 - j : w.kb0 + j;
                     const int s = it % PT_STAGES;
                     const uint32_t use = (uint32_t)(it / PT_STAGES);
                     if (it >= PT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
@@ -386,10 +406,10 @@ __global__ void __launch_bounds__(192, 1)
                     if (*abort_flag) break;
                     uint8_t* st = smem + s * PT_STAGE;
                     goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
-                    goacd::tma_load_2d(st, &tmA, &full[s], kb * 32, m0);
-                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * 32, ld + m0);
-                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * 32, n0);
-                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * 32, Bpad + n0);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * PT_KB, m0);
+                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * PT_KB, ld + m0);
+                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * PT_KB, n0);
+                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * PT_KB, Bpad + n0);
                 }
             }
             if (*abort_flag)
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(192, 1)
                 }
                 goacd::tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc_i * PT_N);
-                for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
+                for (int j = 0; j < w.kb1 - w.kb0; ++j, ++it) {
                     if (*abort_flag) break;
                     const int s = it % PT_STAGES;
                     const uint32_t use = (uint32_t)(it / PT_STAGES);
@@ -428,14 +448,12 @@ __global__ void __launch_bounds__(192, 1)
                     const uint32_t b_hi = a_hi + 2 * PT_A;
                     const uint32_t b_lo = b_hi + PT_B;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
+                    for (int kk = 0; kk < PT_KB / 8; ++kk) {          // K = 8 per TF32 MMA: 32 bytes of each row
                         const uint32_t off = kk * 32;
-                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_hi + off), idesc,
-                                        (kb != w.kb0 || kk != 0) ? 1u : 0u);
-                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_hi + off), goacd::sdesc_k128(b_lo + off), idesc,
-                                        1u);
-                        goacd::mma_tf32(d_tmem, goacd::sdesc_k128(a_lo + off), goacd::sdesc_k128(b_hi + off), idesc,
-                                        1u);
+                        goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_hi + off), idesc,
+                                        (j != 0 || kk != 0) ? 1u : 0u);
+                        goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_lo + off), idesc, 1u);
+                        goacd::mma_tf32(d_tmem, sdesc_k64(a_lo + off), sdesc_k64(b_hi + off), idesc, 1u);
                     }
                     goacd::mma_commit(&empty[s]);
                 }
@@ -509,9 +527,12 @@ __global__ void k_split_tf32_full(const double* __restrict__ J, long n, float* _
 // digit t): the same M = 128 sites x N = 256 configurations MMA shape, stage
 // layout and double-buffered TMEM accumulators as k_score_tc with one term,
 // with kind::f16 on FP16 operands.  The epilogue forms P_t,b = sum_i q_bi
-// Phi_t,ib exactly in 32-bit integers (each accumulator split into 12-bit
-// halves so that no sum over the 128 sites can overflow) and stores it as an
-// FP64 integer; k_finish_exact scales by 2^(e_I - (r-1) - rt).
+// Phi_t,ib exactly in 32-bit integers and stores it as an FP64 integer
+// (k_finish_exact scales by 2^(e_I - (r-1) - rt)): when the host's bound
+// 32 max|q| max|Phi| < 2^31 holds, each warp sums q Phi over its 32 sites in
+// one int32 butterfly and the four warp sums are added in 64 bits; else
+// (SPLIT) each accumulator is split into 12-bit halves so that no sum over the
+// 128 sites can overflow, at twice the shuffles.
 constexpr int EX_STAGE = A_TILE + B_TILE;      // 48 KB (k_phi_exact)
 constexpr int EX_STAGES = 4;
 constexpr int EX_SMEM = EX_STAGES * EX_STAGE + 1024 + 256;
@@ -524,8 +545,10 @@ struct ExCfg {
     static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-template <int TN>
-__global__ void __launch_bounds__(192, 1)
+// Non-split instances are compiled for at most 168 registers (two blocks' worth; the shared memory
+// still admits one) so that k_make_qt's blocks can share the SM while the kernel's prologue runs.
+template <int TN, bool SPLIT>
+__global__ void __launch_bounds__(192, SPLIT ? 1 : 2)
     k_score_exact(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const TcTile* __restrict__ work, const int* __restrict__ work_start, int ld, int T,
                   const __half* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
@@ -642,6 +665,27 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- epilogue: warps 2..5 ----------------
         const int lg = warp & 3;
         const int etid = threadIdx.x - 64;
+        // the charges of this thread's site for the tile's TN configurations, loaded before the
+        // tile's accumulator is ready so that the epilogue itself is pure ALU work: int16 pairs when
+        // SPLIT (|q| < 1024: the digit width rule keeps 2^7 max|q| Nv_pad < 2^24, Nv_pad >= 128),
+        // else int8 quadruples (32 max|q|^2 2^(r-1) Nv_pad < 2^31 with r >= 8 gives |q| < 64), which
+        // keeps the register count low enough for k_make_qt's blocks to share the SM
+        constexpr int QPW = SPLIT ? 2 : 4;           // charges per 32-bit word
+        uint32_t qp[TN / QPW];
+        auto load_q = [&](const TcTile& tq) {
+            const __half* src = qt + (long)tq.n * TN * ld + tq.I * TC_M + lg * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < TN / QPW; ++j) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < QPW; ++e) {
+                    const int q = __float2int_rn(__half2float(src[(long)(QPW * j + e) * ld]));
+                    w |= ((uint32_t)q & (SPLIT ? 0xffffu : 0xffu)) << ((32 / QPW) * e);
+                }
+                qp[j] = w;
+            }
+        };
+        if (w0 < w1) load_q(work[w0]);
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
             const TcTile tile = work[wi];
@@ -650,9 +694,8 @@ __global__ void __launch_bounds__(192, 1)
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
-            const int v = tile.I * TC_M + lg * 32 + lane;
             const long n0 = (long)tile.n * TN;
-#pragma unroll 1
+#pragma unroll
             for (int c = 0; c < TN / 32; ++c) {
                 uint32_t r[32];
                 goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
@@ -662,11 +705,17 @@ __global__ void __launch_bounds__(192, 1)
                 int hi[32], lo[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const long b = n0 + c * 32 + j;
-                    const int q = __float2int_rn(__half2float(qt[b * ld + v]));
+                    const uint32_t w2 = qp[(c * 32 + j) / QPW];
+                    constexpr int QB = 32 / QPW;             // bits per charge
+                    const int e = j % QPW;
+                    const int q = (int)(w2 << (32 - QB * (e + 1))) >> (32 - QB);   // sign-extended field e
                     const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
-                    hi[j] = (a >> 12) * q;
-                    lo[j] = (a & 4095) * q;
+                    if (SPLIT) {
+                        hi[j] = (a >> 12) * q;
+                        lo[j] = (a & 4095) * q;
+                    } else {
+                        hi[j] = a * q;          // the host checked 32 max|q a| < 2^31
+                    }
                 }
                 // butterfly transpose-reduce: afterwards lane l holds column l summed over the warp
 #pragma unroll
@@ -676,23 +725,32 @@ __global__ void __launch_bounds__(192, 1)
                     for (int k = 0; k < 16; ++k)
                         if (k < sft) {
                             const int sh = up ? hi[k] : hi[k + sft], kh = up ? hi[k + sft] : hi[k];
-                            const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
                             hi[k] = kh + __shfl_xor_sync(0xffffffffu, sh, sft);
-                            lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                            if (SPLIT) {
+                                const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
+                                lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                            }
                         }
                 }
                 red_hi[lg][c * 32 + lane] = hi[0];
-                red_lo[lg][c * 32 + lane] = lo[0];
+                if (SPLIT) red_lo[lg][c * 32 + lane] = lo[0];
             }
             goacd::tc_fence_before();
             __syncwarp();
             if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
+            if (wi + 1 < w1) load_q(work[wi + 1]);
             goacd::named_bar_sync(1, 128);
             if (ok)
                 for (int col = etid; col < TN; col += 128) {
-                    const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
-                    const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
-                    partial[((long)tile.slot * T + tile.t) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                    double pt;
+                    if (SPLIT) {
+                        const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
+                        const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
+                        pt = (double)sh * 4096.0 + (double)sl;
+                    } else {
+                        pt = (double)((long long)red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col]);
+                    }
+                    partial[((long)tile.slot * T + tile.t) * Bpad + n0 + col] = pt;
                 }
             goacd::named_bar_sync(1, 128);
         }
@@ -729,6 +787,7 @@ constexpr int PX_STAGE = A_TILE + PX_HN * ROW_BYTES;    // 32 KB
 constexpr int PX_STAGES = 6;
 constexpr int PX_SMEM = PX_STAGES * PX_STAGE + 1024 + 256;
 
+template <bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     k_score_exact_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const PairTile* __restrict__ work, const int* __restrict__ work_start, int ld, int T,
@@ -872,8 +931,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     const long b = n0 + c * 32 + j;
                     const int q = slot >= 0 ? __float2int_rn(__half2float(qt[b * ld + v])) : 0;
                     const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
-                    hi[j] = (a >> 12) * q;
-                    lo[j] = (a & 4095) * q;
+                    if (SPLIT) {
+                        hi[j] = (a >> 12) * q;
+                        lo[j] = (a & 4095) * q;
+                    } else {
+                        hi[j] = a * q;          // the host checked 32 max|q a| < 2^31
+                    }
                 }
 #pragma unroll
                 for (int sft = 16; sft >= 1; sft >>= 1) {
@@ -882,13 +945,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     for (int k = 0; k < 16; ++k)
                         if (k < sft) {
                             const int sh = up ? hi[k] : hi[k + sft], kh = up ? hi[k + sft] : hi[k];
-                            const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
                             hi[k] = kh + __shfl_xor_sync(0xffffffffu, sh, sft);
-                            lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                            if (SPLIT) {
+                                const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
+                                lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
+                            }
                         }
                 }
                 red_hi[lg][c * 32 + lane] = hi[0];
-                red_lo[lg][c * 32 + lane] = lo[0];
+                if (SPLIT) red_lo[lg][c * 32 + lane] = lo[0];
             }
             goacd::tc_fence_before();
             __syncwarp();
@@ -899,9 +964,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             goacd::named_bar_sync(1, 128);
             if (ok && slot >= 0)
                 for (int col = etid; col < TN; col += 128) {
-                    const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
-                    const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
-                    partial[((long)slot * T + tile.t) * Bpad + n0 + col] = (double)sh * 4096.0 + (double)sl;
+                    double pt;
+                    if (SPLIT) {
+                        const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
+                        const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
+                        pt = (double)sh * 4096.0 + (double)sl;
+                    } else {
+                        pt = (double)((long long)red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col]);
+                    }
+                    partial[((long)slot * T + tile.t) * Bpad + n0 + col] = pt;
                 }
             goacd::named_bar_sync(1, 128);
         }
@@ -1337,7 +1408,7 @@ goac_status smem_attr_once(const void* kern, int smem, std::atomic<uint64_t>& do
 // 2D K-major tensor map: inner dim = `inner` elements (row pitch `pitch_elems`),
 // outer dim = `rows`; box = 128 bytes x box_rows, 128-byte swizzle.
 goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int elem_bytes, long inner, long rows,
-                     long pitch_elems, int box_rows)
+                     long pitch_elems, int box_rows, int row_bytes = ROW_BYTES)
 {
     auto enc = get_encode();
     if (!enc) return goac::fail(GOAC_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
@@ -1345,11 +1416,12 @@ goac_status make_map(CUtensorMap* map, void* base, CUtensorMapDataType dt, int e
         return goac::fail(GOAC_ERR_INTERNAL, "tensor map base / pitch not 16-byte aligned");
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(pitch_elems * elem_bytes)};
-    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / elem_bytes), (cuuint32_t)box_rows};
+    if (row_bytes != 128 && row_bytes != 64) return goac::fail(GOAC_ERR_INTERNAL, "tensor map row bytes");
+    cuuint32_t box[2] = {(cuuint32_t)(row_bytes / elem_bytes), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return goac::fail(GOAC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return GOAC_OK;
 }
@@ -1374,7 +1446,10 @@ int2 tc_tile_count(int nbm, int nbn, int T, int kc)
 // k-blocks per 128 columns) is cut into chunks of kc 128-column blocks (kc = 0:
 // one chunk); each (I, chunk) is one partial-sum slot, slots numbered panel by
 // panel, so the slots of panel I are pslot[I] .. pslot[I+1].  Tiles go
-// longest first to the least-loaded CTA (ties: the lowest index).
+// longest first to the least-loaded CTA (ties: the lowest index); each CTA
+// then runs its tiles longest, shortest, second longest, ... so that the
+// epilogue of a short tile (which can take longer than its MMAs) overlaps the
+// MMAs of a long one through the two TMEM accumulators.
 goac_status tc_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int kbm, int grid, const TcTile** work,
                         const int** starts, const int** pslot)
 {
@@ -1416,7 +1491,11 @@ goac_status tc_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int kbm, i
         std::vector<int> st(grid + 1, 0);
         for (int c = 0; c < grid; ++c) {
             st[c] = (int)flat.size();
-            flat.insert(flat.end(), per[c].begin(), per[c].end());
+            // longest, shortest, second longest, ...: a short tile's epilogue overlaps a long tile's MMAs
+            for (int lo = 0, hi = (int)per[c].size() - 1; lo <= hi; ++lo, --hi) {
+                flat.push_back(per[c][lo]);
+                if (hi > lo) flat.push_back(per[c][hi]);
+            }
         }
         st[grid] = (int)flat.size();
         const size_t bytes = sizeof(TcTile) * flat.size() + sizeof(int) * (grid + 1 + nbm + 1) + 64;
@@ -1465,12 +1544,12 @@ goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap&
     return GOAC_OK;
 }
 
-template <int TN>
+template <int TN, bool SPLIT>
 goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, int B, int kc,
                          double* part, const double* lin, double* E_out)
 {
     using Cfg = ExCfg<TN>;
-    auto kern = k_score_exact<TN>;
+    auto kern = k_score_exact<TN, SPLIT>;
     static std::atomic<uint64_t> attr_done{0};
     goac_status rc = smem_attr_once((const void*)kern, Cfg::SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
@@ -1549,7 +1628,10 @@ goac_status pair_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int npai
         std::vector<int> st(npairs + 1, 0);
         for (int c = 0; c < npairs; ++c) {
             st[c] = (int)flat.size();
-            flat.insert(flat.end(), per[c].begin(), per[c].end());
+            for (int lo = 0, hi = (int)per[c].size() - 1; lo <= hi; ++lo, --hi) {
+                flat.push_back(per[c][lo]);
+                if (hi > lo) flat.push_back(per[c][hi]);
+            }
         }
         st[npairs] = (int)flat.size();
         const size_t bytes = sizeof(PairTile) * flat.size() + sizeof(int) * (npairs + 1 + nbm + 1) + 64;
@@ -1596,7 +1678,7 @@ static int max_pairs(goac_problem* p)
     cfg.blockDim = dim3(192);
     cfg.dynamicSmemBytes = PX_SMEM;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_score_exact_pair, &cfg) != cudaSuccess || n <= 0) {
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_score_exact_pair<true>, &cfg) != cudaSuccess || n <= 0) {
         cudaGetLastError();
         n = p->ctx->num_sms / 2;
     }
@@ -1605,11 +1687,12 @@ static int max_pairs(goac_problem* p)
     return n;
 }
 
+template <bool SPLIT>
 goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUtensorMap& mb, int Bpad, int B, int kc,
                               double* part, const double* lin, double* E_out)
 {
     static std::atomic<uint64_t> attr_done{0};
-    goac_status rc = smem_attr_once((const void*)k_score_exact_pair, PX_SMEM, attr_done, p->ctx->device);
+    goac_status rc = smem_attr_once((const void*)k_score_exact_pair<SPLIT>, PX_SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
     const int ld = p->Nv_pad, T = p->dig_T;
     const int nbm = ld / TC_M, nbn = (B + 255) / 256, npp = (nbm + 1) / 2;
@@ -1626,7 +1709,7 @@ goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUte
     if (rc) return rc;
     {
         goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
-        goac::launch_pdl(k_score_exact_pair, 2 * npairs, 192, PX_SMEM, p->ctx->stream, ma, mb, work, starts, ld, T,
+        goac::launch_pdl(k_score_exact_pair<SPLIT>, 2 * npairs, 192, PX_SMEM, p->ctx->stream, ma, mb, work, starts, ld, T,
                          (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact_pair");
     }
@@ -1687,8 +1770,8 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
         GOAC_LAUNCH_CHECK("k_split_tf32_full");
     }
     CUtensorMap ma, mb;
-    goac_status rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N);
+    goac_status rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M, PT_ROW);
+    if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N, PT_ROW);
     if (rc) return rc;
     static std::atomic<uint64_t> attr_done{0};
     rc = smem_attr_once((const void*)k_phi_tc, PT_SMEM, attr_done, p->ctx->device);
@@ -1699,11 +1782,12 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     const int grid = std::min(ntiles, p->ctx->num_sms);
     // whole waves of whole tiles; the rest split in k-halves when that keeps them within one wave
     const int rest = ntiles % grid;
-    const int nfull = (rest > 0 && 2 * rest <= grid && ld / 32 >= 2) ? ntiles - rest : ntiles;
+    const int nkb = ld / PT_KB;
+    const int nfull = (rest > 0 && 2 * rest <= grid && nkb >= 2) ? ntiles - rest : ntiles;
     const int nitems = nfull + 2 * (ntiles - nfull);
     if (nitems > nfull) GOAC_CUDA(cudaMemsetAsync(Phi, 0, sizeof(float) * (size_t)Bpad * ld, st));
     KTimer kt(p->ctx, KID_SCORE_TC, st);
-    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, ld / 32, ld, Bpad, Phi,
+    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, nkb, ld, Bpad, Phi,
                  p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_phi_tc");
     return GOAC_OK;
@@ -1769,6 +1853,11 @@ static goac_status exact_charges(goac_problem* p)
     p->dig_kq = kq;
     p->dig_r = r;
     p->dig_T = T;
+    // |Phi| <= 2^(r-1) max|q| Nv_pad (a digit times at most Nv_pad charges), so a warp's sum of
+    // 32 products q Phi stays inside int32 when 32 max|q|^2 2^(r-1) Nv_pad < 2^31
+    double qmax = 0.0;
+    for (int s2 = 0; s2 < p->S; ++s2) qmax = std::max(qmax, fabs(zq[s2]));
+    p->dig_split = !(32.0 * qmax * qmax * ldexp(1.0, r - 1) * (double)p->Nv_pad < 2147483648.0);
     return GOAC_OK;
 }
 
@@ -1878,9 +1967,15 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
     if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, pair ? PX_HN : TN);
     if (rc) return rc;
-    if (pair) return launch_exact_pair(p, ma, mb, Bpad, B, kc, part, lin, E_out);
-    if (TN == TC_NS) return launch_exact<TC_NS>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
-    return launch_exact<TC_N>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
+    const bool split = p->dig_split;
+    if (pair)
+        return split ? launch_exact_pair<true>(p, ma, mb, Bpad, B, kc, part, lin, E_out)
+                     : launch_exact_pair<false>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
+    if (TN == TC_NS)
+        return split ? launch_exact<TC_NS, true>(p, ma, mb, Bpad, B, kc, part, lin, E_out)
+                     : launch_exact<TC_NS, false>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
+    return split ? launch_exact<TC_N, true>(p, ma, mb, Bpad, B, kc, part, lin, E_out)
+                 : launch_exact<TC_N, false>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
 }
 
 template <int TN>

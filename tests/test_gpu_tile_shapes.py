@@ -149,3 +149,33 @@ def test_pair_kernel_odd_panel_count(ctx):
     rows = np.array([0, 255, 256, B - 1])
     Eo = oracle.score(Jg.cpu().numpy(), prob.site_class, prob.fixed_q, prob.z, pop_np[rows])
     assert np.max(np.abs(ref.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
+
+
+def test_exact_form_split_epilogue(ctx):
+    """Charges +49/16, +1, -1, -49/16 in counts 64, 192, 192, 64 on 512 sites
+    (neutral): scaled to integers (x16) the largest is 49, so
+    32 max|q|^2 2^9 Nv_pad >= 2^31 and the epilogue splits each integer sum in
+    12-bit halves; the energies must still be identical in every shape and
+    match the oracle to FP64 rounding."""
+    import dataclasses
+    prob = dataclasses.replace(synth.random_cubic_problem(n_side=8), z=np.array([49.0 / 16, 1.0, -1.0, -49.0 / 16]),
+                               counts=np.array([[64, 192, 192, 64]], dtype=np.int32))
+    import paper_2409_08808_gb300 as g
+    frac = torch.tensor(prob.frac, device="cuda")
+    Jg = g.build_ewald(ctx, prob.lattice, frac, prob.alpha, prob.nimg, prob.kcut)
+    gp = gpu_problem(ctx, prob, Jg)
+    assert gp.exact_info() == (10, 5, 4)
+    B = 777
+    pop = torch.tensor(synth.random_population(prob, B, 23), device="cuda")
+    gp.score_set_shape(B, "exact", 0, 0)
+    ref = gp.score(pop, "exact").clone()
+    for tn, kc in SHAPES:
+        gp.score_set_shape(B, "exact", tn, kc)
+        assert torch.equal(gp.score(pop, "exact"), ref), (tn, kc)
+    for tm, tn, kc in PAIR_SHAPES:
+        gp.score_set_shape(B, "exact", tn, kc, tile_m=tm)
+        assert torch.equal(gp.score(pop, "exact"), ref), (tm, tn, kc)
+    gp.score_set_shape(B, "exact", 0, 0)
+    rows = np.array([0, 255, 256, 511, 512, B - 1])
+    Eo = oracle.score(Jg.cpu().numpy(), prob.site_class, prob.fixed_q, prob.z, pop.cpu().numpy()[rows])
+    assert np.max(np.abs(ref.cpu().numpy()[rows] - Eo) / np.abs(Eo)) <= 1e-10
