@@ -341,6 +341,306 @@ __global__ void __launch_bounds__(256) k_grad_finish_f32(const float* __restrict
     }
 }
 
+// ---- vectorised fast path (S <= 8, ncls S <= 64, Nv % 4 == 0) ------------------
+// The logits and p are B x Nv x S floats, so a thread that owns one site reads
+// S floats 4 S bytes from its neighbour's and fetches every sector S times.
+// Here a thread owns four consecutive sites of one configuration: their 4 S
+// floats are S aligned float4 (the flattened site index b Nv + v is a multiple
+// of 4), S is a template parameter so that all of them stay in registers, and
+// Phi, phi_fix and the site classes of the four sites are one vector load each.
+constexpr int RV_T = 256;                     // threads per block
+constexpr int RV_G = 4;                       // sites per thread
+constexpr int RV_C = RV_T * RV_G;             // sites per block (a chunk of one configuration's row)
+constexpr int RV_SMAX = 8;
+constexpr int RV_KS = 64;                     // ncls * S limit of the chunk partials
+
+// One block per (configuration b < B, chunk c of 1,024 sites): p = softmax over
+// the species allowed in the site's class, q = sum_s p_s z_s and q's TF32 hi /
+// lo planes (zero for Nv <= v < ld; rows B .. Bpad are zeroed by the host), and
+// the chunk's occupation sums cpart[(b nch + c) ncls S + k S + s] = sum over
+// the chunk's sites v of class k of p_vs (FP32 within a thread and a warp in a
+// fixed order, FP64 over the eight warps in order).
+template <int S>
+__global__ void __launch_bounds__(RV_T) k_relax_prep_v4(const float* __restrict__ logits, int Nv, int ld, int nch,
+                                                      const int32_t* __restrict__ vclass,
+                                                      const int32_t* __restrict__ counts,
+                                                      const double* __restrict__ z, int ncls, float* __restrict__ p,
+                                                      float* __restrict__ qt2, long plane, double* __restrict__ cpart)
+{
+    __shared__ int cnt[RV_KS];
+    __shared__ double wsum[RV_T / 32][RV_KS];
+    const int nks = ncls * S;
+    if (threadIdx.x < nks) cnt[threadIdx.x] = counts[threadIdx.x];
+    __syncthreads();
+    float zf[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) zf[t] = (float)z[t];
+    const int c = blockIdx.x % nch, b = blockIdx.x / nch;
+    const int v0 = c * RV_C + threadIdx.x * RV_G;
+    const int nv = max(0, min(RV_G, Nv - v0));
+    const long t0 = (long)b * Nv + v0;
+    float P[RV_G * S];
+    if (nv == RV_G) {
+        const float4* src = reinterpret_cast<const float4*>(logits + t0 * S);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float4 f = src[j];
+            P[4 * j] = f.x;
+            P[4 * j + 1] = f.y;
+            P[4 * j + 2] = f.z;
+            P[4 * j + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < RV_G * S; ++j) P[j] = j < nv * S ? logits[t0 * S + j] : 0.0f;
+    }
+    int kc[RV_G];
+    float qv[RV_G];
+    if (nv == RV_G) {
+        const int4 k4 = *reinterpret_cast<const int4*>(vclass + v0);
+        kc[0] = k4.x;
+        kc[1] = k4.y;
+        kc[2] = k4.z;
+        kc[3] = k4.w;
+    } else {
+#pragma unroll
+        for (int g = 0; g < RV_G; ++g) kc[g] = g < nv ? vclass[v0 + g] : -1;
+    }
+#pragma unroll
+    for (int g = 0; g < RV_G; ++g) {
+        qv[g] = 0.0f;
+        if (kc[g] >= 0) {
+            const int k = kc[g];
+            float m = -INFINITY;
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                if (cnt[k * S + t] > 0) m = fmaxf(m, P[g * S + t]);
+            float den = 0.0f;
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                const float e = cnt[k * S + t] > 0 ? expf(P[g * S + t] - m) : 0.0f;
+                P[g * S + t] = e;
+                den += e;
+            }
+            const float inv = 1.0f / den;
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                P[g * S + t] *= inv;
+                qv[g] = fmaf(P[g * S + t], zf[t], qv[g]);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < S; ++t) P[g * S + t] = 0.0f;
+        }
+    }
+    if (nv == RV_G) {
+        float4* dst = reinterpret_cast<float4*>(p + t0 * S);
+#pragma unroll
+        for (int j = 0; j < S; ++j) dst[j] = make_float4(P[4 * j], P[4 * j + 1], P[4 * j + 2], P[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < RV_G * S; ++j)
+            if (j < nv * S) p[t0 * S + j] = P[j];
+    }
+    if (v0 + RV_G <= ld) {
+        float hi[RV_G], lo[RV_G];
+#pragma unroll
+        for (int g = 0; g < RV_G; ++g) {
+            hi[g] = tf32_rna(qv[g]);
+            lo[g] = tf32_rna(qv[g] - hi[g]);
+        }
+        *reinterpret_cast<float4*>(qt2 + (long)b * ld + v0) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4*>(qt2 + plane + (long)b * ld + v0) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int kk = 0; kk < ncls; ++kk)
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            float x = 0.0f;
+#pragma unroll
+            for (int g = 0; g < RV_G; ++g) x += kc[g] == kk ? P[g * S + t] : 0.0f;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) wsum[warp][kk * S + t] = (double)x;
+        }
+    __syncthreads();
+    if (threadIdx.x < nks) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < RV_T / 32; ++w) acc += wsum[w][threadIdx.x];
+        cpart[((long)b * nch + c) * nks + threadIdx.x] = acc;
+    }
+}
+
+// The FP32 chain rule of k_grad_finish_f32 for four sites per thread, one block
+// per (configuration b, chunk c); colsum of b is the sum of its chunk partials
+// in chunk order, and the block's share of the energy sum_v q_v (Phi_v +
+// 2 phi_fix_v) goes to epart[b nch + c] (FP64, fixed order).
+template <int S>
+__global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict__ p, const float* __restrict__ Phi,
+                                                       long phi_ld, const double* __restrict__ phifix,
+                                                       const double* __restrict__ cpart, int nch,
+                                                       const int32_t* __restrict__ vclass,
+                                                       const int32_t* __restrict__ counts,
+                                                       const double* __restrict__ z, int Nv, int ncls, double lambda,
+                                                       double* __restrict__ epart, float* __restrict__ dlogits,
+                                                       float* logits_upd, float eta)
+{
+    __shared__ float pen[RV_KS];
+    __shared__ int cnt[RV_KS];
+    __shared__ double red[RV_T / 32];
+    const int c = blockIdx.x % nch, b = blockIdx.x / nch;
+    const int nks = ncls * S;
+    if (threadIdx.x < nks) {
+        double a = 0.0;
+        for (int cc = 0; cc < nch; ++cc) a += cpart[((long)b * nch + cc) * nks + threadIdx.x];
+        cnt[threadIdx.x] = counts[threadIdx.x];
+        pen[threadIdx.x] = (float)(2.0 * lambda * (a - counts[threadIdx.x]));
+    }
+    __syncthreads();
+    float zf[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) zf[t] = (float)z[t];
+    const int v0 = c * RV_C + threadIdx.x * RV_G;
+    const int nv = max(0, min(RV_G, Nv - v0));
+    const long t0 = (long)b * Nv + v0;
+    float P[RV_G * S];
+    float phi[RV_G], pf[RV_G];
+    int kc[RV_G];
+    if (nv == RV_G) {
+        const float4* src = reinterpret_cast<const float4*>(p + t0 * S);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float4 f = src[j];
+            P[4 * j] = f.x;
+            P[4 * j + 1] = f.y;
+            P[4 * j + 2] = f.z;
+            P[4 * j + 3] = f.w;
+        }
+        const float4 f = *reinterpret_cast<const float4*>(Phi + (long)b * phi_ld + v0);
+        phi[0] = f.x;
+        phi[1] = f.y;
+        phi[2] = f.z;
+        phi[3] = f.w;
+        const double2 d0 = *reinterpret_cast<const double2*>(phifix + v0);
+        const double2 d1 = *reinterpret_cast<const double2*>(phifix + v0 + 2);
+        pf[0] = (float)d0.x;
+        pf[1] = (float)d0.y;
+        pf[2] = (float)d1.x;
+        pf[3] = (float)d1.y;
+        const int4 k4 = *reinterpret_cast<const int4*>(vclass + v0);
+        kc[0] = k4.x;
+        kc[1] = k4.y;
+        kc[2] = k4.z;
+        kc[3] = k4.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < RV_G * S; ++j) P[j] = j < nv * S ? p[t0 * S + j] : 0.0f;
+#pragma unroll
+        for (int g = 0; g < RV_G; ++g) {
+            phi[g] = g < nv ? Phi[(long)b * phi_ld + v0 + g] : 0.0f;
+            pf[g] = g < nv ? (float)phifix[v0 + g] : 0.0f;
+            kc[g] = g < nv ? vclass[v0 + g] : -1;
+        }
+    }
+    double acc = 0.0;
+    const bool grad = dlogits || logits_upd;
+    float G[RV_G * S];
+#pragma unroll
+    for (int g = 0; g < RV_G; ++g) {
+        float q = 0.0f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) q = fmaf(P[g * S + t], zf[t], q);
+        acc += (double)(q * (phi[g] + 2.0f * pf[g]));
+        const int k = kc[g] < 0 ? 0 : kc[g];
+        const float jq = phi[g] + pf[g];           // (J q)_v over all sites
+        float pg = 0.0f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) pg = fmaf(P[g * S + t], fmaf(2.0f * zf[t], jq, pen[k * S + t]), pg);
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            G[g * S + t] = cnt[k * S + t] > 0 ? P[g * S + t] * (fmaf(2.0f * zf[t], jq, pen[k * S + t]) - pg) : 0.0f;
+    }
+    if (grad && nv == RV_G) {
+        if (dlogits) {
+            float4* dst = reinterpret_cast<float4*>(dlogits + t0 * S);
+#pragma unroll
+            for (int j = 0; j < S; ++j) dst[j] = make_float4(G[4 * j], G[4 * j + 1], G[4 * j + 2], G[4 * j + 3]);
+        }
+        if (logits_upd) {
+            // descent step in place (this step's p was formed from the old logits)
+            float4* dst = reinterpret_cast<float4*>(logits_upd + t0 * S);
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                float4 f = dst[j];
+                f.x -= eta * G[4 * j];
+                f.y -= eta * G[4 * j + 1];
+                f.z -= eta * G[4 * j + 2];
+                f.w -= eta * G[4 * j + 3];
+                dst[j] = f;
+            }
+        }
+    } else if (grad) {
+#pragma unroll
+        for (int j = 0; j < RV_G * S; ++j)
+            if (j < nv * S) {
+                if (dlogits) dlogits[t0 * S + j] = G[j];
+                if (logits_upd) logits_upd[t0 * S + j] = logits_upd[t0 * S + j] - eta * G[j];
+            }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+#pragma unroll
+        for (int w = 0; w < RV_T / 32; ++w) e += red[w];
+        epart[(long)b * nch + blockIdx.x % nch] = e;
+    }
+}
+
+// E_b = sum_c epart[b nch + c] + E_const + lambda sum_{k,s allowed} (colsum - n)^2,
+// colsum summed from the chunk partials in chunk order; one thread per configuration.
+__global__ void k_energy_v4(const double* __restrict__ epart, const double* __restrict__ cpart, int nch, int B,
+                            int ncls, int S, const int32_t* __restrict__ counts, double lambda, double E_const,
+                            double* __restrict__ E)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int nks = ncls * S;
+    double e = 0.0;
+    for (int c = 0; c < nch; ++c) e += epart[(long)b * nch + c];
+    double pn = 0.0;
+    for (int i = 0; i < nks; ++i) {
+        if (counts[i] <= 0) continue;
+        double a = 0.0;
+        for (int c = 0; c < nch; ++c) a += cpart[((long)b * nch + c) * nks + i];
+        const double r = a - counts[i];
+        pn += r * r;
+    }
+    E[b] = e + E_const + lambda * pn;
+}
+
+template <int S>
+void launch_relax_v4(int B, int Nv, int ld, int nch, const goac_problem* p, const float* logits, float* P32,
+                     float* qt2, long plane, double* cpart, cudaStream_t st)
+{
+    goac::launch(k_relax_prep_v4<S>, B * nch, RV_T, 0, st, logits, Nv, ld, nch, (const int32_t*)p->vclass_dev,
+                 (const int32_t*)p->counts_dev, (const double*)p->z_dev, p->ncls, P32, qt2, plane, cpart);
+}
+
+template <int S>
+void launch_finish_v4(int B, int Nv, int nch, int ld, const goac_problem* p, const float* P32, const float* Phi,
+                      const double* cpart, double* epart, double lambda, float* dlogits, float* logits_upd, float eta,
+                      cudaStream_t st)
+{
+    goac::launch(k_grad_finish_v4<S>, B * nch, RV_T, 0, st, P32, Phi, (long)ld, (const double*)p->phifix, cpart, nch,
+                 (const int32_t*)p->vclass_dev, (const int32_t*)p->counts_dev, (const double*)p->z_dev, Nv, p->ncls,
+                 lambda, epart, dlogits, logits_upd, eta);
+}
+
 // L -= eta * dL (FP32, in place).
 __global__ void k_descent_step(float* __restrict__ L, const float* __restrict__ dL, long n, float eta)
 {
@@ -470,25 +770,68 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
     cudaStream_t st = p->ctx->stream;
     if (tc) {
         // FP32 elementwise chain around the TF32x2 contraction
-        size_t need = sizeof(float) * (size_t)BN * S + sizeof(double) * (size_t)B * ncls * S +
-                      sizeof(float) * 3 * (size_t)Bpad * ld + 1024;
+        // four sites per thread for up to 8 species, 64 (class, species) pairs and Nv % 4 == 0 with
+        // 16-byte aligned logits / gradient arrays; else one site per thread
+        const bool a16 = ((uintptr_t)logits_dev & 15) == 0 && ((uintptr_t)dlogits_dev & 15) == 0 &&
+                         ((uintptr_t)logits_upd & 15) == 0;
+        const bool vec = S <= RV_SMAX && ncls * S <= RV_KS && Nv % 4 == 0 && a16;
+        const int nch = (Nv + RV_C - 1) / RV_C;
+        const size_t ncol = vec ? (size_t)B * nch * ncls * S + (size_t)B * nch : (size_t)B * ncls * S;
+        size_t need = sizeof(float) * (size_t)BN * S + sizeof(double) * ncol + sizeof(float) * 3 * (size_t)Bpad * ld +
+                      1024;
         goac_status rc = goac::ensure(p->grad_tmp, need);
         if (rc) return rc;
         float* P32 = (float*)p->grad_tmp.ptr;
         double* colsum = (double*)(((uintptr_t)(P32 + BN * S) + 255) & ~(uintptr_t)255);
-        float* qt2 = (float*)(((uintptr_t)(colsum + (long)B * ncls * S) + 255) & ~(uintptr_t)255);   // TMA: aligned
+        double* epart = colsum + (size_t)B * nch * ncls * S;        // vec only
+        float* qt2 = (float*)(((uintptr_t)(colsum + ncol) + 255) & ~(uintptr_t)255);   // TMA: aligned
         float* Phi = qt2 + 2 * (size_t)Bpad * ld;
         const long plane = (long)Bpad * ld;
-        goac::launch(k_relax_prep, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, logits_dev, B,
-                     Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2);
-        goac::launch(k_colsum_f32, B * ncls, 256, 0, st, (const float*)P32, Nv, S, ncls, p->cls_start_dev,
-                     p->cls_pos_dev, colsum);
+        if (vec) {
+            if (Bpad > B) {
+                GOAC_CUDA(cudaMemsetAsync(qt2 + (size_t)B * ld, 0, sizeof(float) * (size_t)(Bpad - B) * ld, st));
+                GOAC_CUDA(cudaMemsetAsync(qt2 + plane + (size_t)B * ld, 0, sizeof(float) * (size_t)(Bpad - B) * ld, st));
+            }
+            switch (S) {
+            case 1: launch_relax_v4<1>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 2: launch_relax_v4<2>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 3: launch_relax_v4<3>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 4: launch_relax_v4<4>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 5: launch_relax_v4<5>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 6: launch_relax_v4<6>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 7: launch_relax_v4<7>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            default: launch_relax_v4<8>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            }
+        } else {
+            goac::launch(k_relax_prep, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, logits_dev,
+                         B, Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2);
+            goac::launch(k_colsum_f32, B * ncls, 256, 0, st, (const float*)P32, Nv, S, ncls, p->cls_start_dev,
+                         p->cls_pos_dev, colsum);
+        }
         GOAC_LAUNCH_CHECK("k_relax_prep");
         rc = goac::phi_tc(p, qt2, Bpad, Phi);
         if (rc) return rc;
-        goac::launch(k_grad_finish_f32, B, 256, 0, st, (const float*)P32, (const float*)Phi, (long)ld,
-                     (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv, S,
-                     ncls, lambda, p->E_const, E_dev, dlogits_dev, logits_upd, eta);
+        if (vec) {
+#define GOAC_FINISH_V4(SS)                                                                                         \
+    launch_finish_v4<SS>(B, Nv, nch, ld, p, P32, Phi, colsum, epart, lambda, dlogits_dev, logits_upd, eta, st)
+            switch (S) {
+            case 1: GOAC_FINISH_V4(1); break;
+            case 2: GOAC_FINISH_V4(2); break;
+            case 3: GOAC_FINISH_V4(3); break;
+            case 4: GOAC_FINISH_V4(4); break;
+            case 5: GOAC_FINISH_V4(5); break;
+            case 6: GOAC_FINISH_V4(6); break;
+            case 7: GOAC_FINISH_V4(7); break;
+            default: GOAC_FINISH_V4(8); break;
+            }
+#undef GOAC_FINISH_V4
+            goac::launch(k_energy_v4, (B + 255) / 256, 256, 0, st, (const double*)epart, (const double*)colsum, nch, B,
+                         ncls, S, p->counts_dev, lambda, p->E_const, E_dev);
+        } else {
+            goac::launch(k_grad_finish_f32, B, 256, 0, st, (const float*)P32, (const float*)Phi, (long)ld,
+                         (const double*)p->phifix, (const double*)colsum, p->vclass_dev, p->counts_dev, p->z_dev, Nv,
+                         S, ncls, lambda, p->E_const, E_dev, dlogits_dev, logits_upd, eta);
+        }
     } else {
         size_t need = sizeof(double) * ((size_t)BN * S + (size_t)BN + (size_t)B * ncls * S + (size_t)BN) + 2048;
         goac_status rc = goac::ensure(p->grad_tmp, need);

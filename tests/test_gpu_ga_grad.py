@@ -212,17 +212,22 @@ def _many_species_problem():
     return prob
 
 
-@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5), ("s10", 4)])
+@pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5), ("s10", 4), ("layered864", 3)])
 def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
     """J.Q on tcgen05 with J and the real Q split in TF32 hi/lo: within the
     deterministic bound of the form.  Per site, |dPhi_v| <= (gamma_K + 2^-20)
     sum_w |J_vw q_w| (K = 3 Nv products accumulated in FP32; the three kept
     products miss at most 2^-20 relative), so |dE| <= sum_v |q_v| that bound
-    and |d(dE/dL_vs)| <= 4 max|z| p_vs that bound (+ FP32 output rounding)."""
+    and |d(dE/dL_vs)| <= 4 max|z| p_vs that bound (+ FP32 output rounding).
+    Cases: one 256-site chunk of the elementwise kernels (layered 2x1x1, bcc
+    4^3), more than 8 species (the general kernels), and several classes over
+    Nv = 864 = 3 x 256 + 96 sites (chunk partials of every class, a ragged
+    last chunk)."""
     import paper_2409_08808_gb300 as g
     prob = {"layered": lambda: synth.layered_problem(reps=(2, 1, 1)),
             "bcc": lambda: synth.bcc_relaxed_problem(n_side=4),
-            "s10": _many_species_problem}[which]()
+            "s10": _many_species_problem,
+            "layered864": lambda: synth.layered_problem()}[which]()
     Jg, Jo = build_pair(ctx, prob)
     gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
     L = synth.random_logits(prob, B, 13)
