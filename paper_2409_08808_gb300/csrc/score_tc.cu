@@ -1258,17 +1258,60 @@ __global__ void k_copy_f32(const double* __restrict__ J, long n, float* __restri
 }
 
 // Q^T[b][v] = z[species[b][v]] in BF16, FP16 or FP32, zero padded to Bpad x ld, one
-// block per configuration row; 16 species per thread and step (one 16-byte load
-// when the row is 16-byte aligned), 16-byte stores.  With fixed ions also
-// lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
+// block of 128 threads per configuration row; a thread converts two chunks of
+// 16 species per step (one 16-byte load each when the row is 16-byte aligned,
+// both issued before either is converted), 16-byte stores.  With fixed ions
+// also lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
+constexpr int MQ_T = 128;
+
 template <typename QT>
-__global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ species, int B, int Nv,
-                                                 const double* __restrict__ zq, const double* __restrict__ z, int ld,
-                                                 QT* __restrict__ qt, const double* __restrict__ phifix,
-                                                 double* __restrict__ lin)
+__device__ __forceinline__ void make_qt_chunk(const int8_t (&s16)[16], const float* zs, const double* __restrict__ z,
+                                              const double* __restrict__ phifix, int v0, QT* __restrict__ row,
+                                              double& acc)
+{
+    float q[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        q[u] = s16[u] >= 0 ? zs[s16[u]] : 0.0f;
+        if (phifix && s16[u] >= 0) acc += z[s16[u]] * (2.0 * phifix[v0 + u]);
+    }
+    if constexpr (std::is_same<QT, __half>::value) {
+        __align__(16) __half o[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) o[u] = __float2half_rn(q[u]);
+        ((int4*)(row + v0))[0] = ((const int4*)o)[0];
+        ((int4*)(row + v0))[1] = ((const int4*)o)[1];
+    } else if constexpr (sizeof(QT) == 2) {
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16(q[u]);
+        ((int4*)(row + v0))[0] = ((const int4*)o)[0];
+        ((int4*)(row + v0))[1] = ((const int4*)o)[1];
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ((float4*)(row + v0))[u] = make_float4(q[4 * u], q[4 * u + 1], q[4 * u + 2], q[4 * u + 3]);
+    }
+}
+
+__device__ __forceinline__ void make_qt_load(const int8_t* __restrict__ src, int b, int B, int Nv, bool aligned, int v0,
+                                             int8_t (&s16)[16])
+{
+    if (b < B && aligned && v0 + 16 <= Nv) {
+        *(int4*)s16 = *(const int4*)(src + v0);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s16[u] = (b < B && v0 + u < Nv) ? src[v0 + u] : (int8_t)-1;
+    }
+}
+
+template <typename QT>
+__global__ void __launch_bounds__(MQ_T) k_make_qt(const int8_t* __restrict__ species, int B, int Nv,
+                                                  const double* __restrict__ zq, const double* __restrict__ z, int ld,
+                                                  QT* __restrict__ qt, const double* __restrict__ phifix,
+                                                  double* __restrict__ lin)
 {
     __shared__ float zs[64];
-    __shared__ double red[256];
+    __shared__ double red[MQ_T];
     goacd::pdl_trigger();       // the scoring kernel may set itself up meanwhile
     if (threadIdx.x < 64) zs[threadIdx.x] = (float)zq[threadIdx.x];
     __syncthreads();
@@ -1277,41 +1320,18 @@ __global__ void __launch_bounds__(256) k_make_qt(const int8_t* __restrict__ spec
     const int8_t* src = species + (long)b * Nv;
     const bool aligned = ((Nv & 15) == 0) && (((uintptr_t)species & 15) == 0);
     double acc = 0.0;
-    for (int v0 = threadIdx.x * 16; v0 < ld; v0 += blockDim.x * 16) {   // ld is a multiple of 128
-        int8_t s16[16];
-        if (b < B && aligned && v0 + 16 <= Nv) {
-            *(int4*)s16 = *(const int4*)(src + v0);
-        } else {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) s16[u] = (b < B && v0 + u < Nv) ? src[v0 + u] : (int8_t)-1;
-        }
-        float q[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            q[u] = s16[u] >= 0 ? zs[s16[u]] : 0.0f;
-            if (phifix && s16[u] >= 0) acc += z[s16[u]] * (2.0 * phifix[v0 + u]);
-        }
-        if constexpr (std::is_same<QT, __half>::value) {
-            __align__(16) __half o[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) o[u] = __float2half_rn(q[u]);
-            ((int4*)(row + v0))[0] = ((const int4*)o)[0];
-            ((int4*)(row + v0))[1] = ((const int4*)o)[1];
-        } else if constexpr (sizeof(QT) == 2) {
-            __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16(q[u]);
-            ((int4*)(row + v0))[0] = ((const int4*)o)[0];
-            ((int4*)(row + v0))[1] = ((const int4*)o)[1];
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) ((float4*)(row + v0))[u] = make_float4(q[4 * u], q[4 * u + 1], q[4 * u + 2], q[4 * u + 3]);
-        }
+    for (int v0 = threadIdx.x * 16; v0 < ld; v0 += 2 * MQ_T * 16) {   // ld is a multiple of 128
+        const int v1 = v0 + MQ_T * 16;
+        int8_t sa[16], sb[16];
+        make_qt_load(src, b, B, Nv, aligned, v0, sa);
+        if (v1 < ld) make_qt_load(src, b, B, Nv, aligned, v1, sb);
+        make_qt_chunk<QT>(sa, zs, z, phifix, v0, row, acc);
+        if (v1 < ld) make_qt_chunk<QT>(sb, zs, z, phifix, v1, row, acc);
     }
     if (phifix == nullptr || b >= B) return;
     red[threadIdx.x] = acc;
     __syncthreads();
-    for (int w = 128; w; w >>= 1) {
+    for (int w = MQ_T / 2; w; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
@@ -1323,23 +1343,26 @@ constexpr int EX_TMAX = 6;                     // most digits of the exact form
 // E_b = 2^-2kq sum_I 2^(e_I - (r-1)) sum_t 2^-rt P_t,I,b + lin_b + E_const,
 // P_t,I,b the sum of panel I's k-chunk partials (slots pslot[I] ..
 // pslot[I+1]) of digit t: exact integers below 2^53, so the result does not
-// depend on how the panel's k-range was split.  One block of 8 warps per 32
+// depend on how the panel's k-range was split.  One block of 32 warps per 32
 // configurations: lane = configuration (coalesced loads of the partials), warp
-// w takes panels w, w + 8, ...; a panel's T partials are loaded together, the
-// digits added smallest first and the 8 warp sums in a fixed order
-// (deterministic); the scalings are exact powers of two.
-__global__ void __launch_bounds__(256)
+// w takes panels w, w + 32, ... (up to Nv = 4,096 one panel per warp: one round
+// trip for the panel's slot bounds and one for its partials); a panel's T
+// partials are loaded together, the digits added smallest first and the 32
+// warp sums in a fixed order (deterministic); the scalings are exact powers of
+// two.
+constexpr int FX_WARPS = 32;
+__global__ void __launch_bounds__(FX_WARPS * 32)
     k_finish_exact(const double* __restrict__ partial, int npanels, const int* __restrict__ pslot,
                    const int* __restrict__ pexp, int Bpad, int B, int r, int T, int kq2, double E_const,
                    const double* __restrict__ lin, double* __restrict__ E)
 {
-    __shared__ double red[8][33];
+    __shared__ double red[FX_WARPS][33];
     goacd::pdl_wait();          // the digit sums of the scoring kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 32 + lane;
     double s = 0.0;
     if (b < B)
-        for (int m = warp; m < npanels; m += 8) {
+        for (int m = warp; m < npanels; m += FX_WARPS) {
             const int s0 = pslot[m], s1 = pslot[m + 1];
             double P[EX_TMAX];
 #pragma unroll
@@ -1361,7 +1384,7 @@ __global__ void __launch_bounds__(256)
     if (warp == 0 && b < B) {
         double tot = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) tot += red[w][lane];
+        for (int w = 0; w < FX_WARPS; ++w) tot += red[w][lane];
         E[b] = tot * pow2(-kq2) + (lin ? lin[b] : 0.0) + E_const;
     }
 }
@@ -1568,7 +1591,7 @@ goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorM
                          (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact");
     }
-    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, p->ctx->stream, (const double*)part, nbm, pslot,
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, FX_WARPS * 32, 0, p->ctx->stream, (const double*)part, nbm, pslot,
                      (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_exact");
     return GOAC_OK;
@@ -1713,7 +1736,7 @@ goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUte
                          (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact_pair");
     }
-    goac::launch_pdl(k_finish_exact, (B + 31) / 32, 256, 0, p->ctx->stream, (const double*)part, nbm, pslot,
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, FX_WARPS * 32, 0, p->ctx->stream, (const double*)part, nbm, pslot,
                      (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_exact");
     return GOAC_OK;
@@ -1899,7 +1922,7 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
     if (!rc) rc = ensure(p->phi_dig, sizeof(int) * (size_t)T * Bpad * ld);
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
-    goac::launch(k_make_qt<__half>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+    goac::launch(k_make_qt<__half>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
                  (const double*)p->z_dev, ld, (__half*)p->qt.ptr, (const double*)nullptr, (double*)nullptr);
     GOAC_LAUNCH_CHECK("k_make_qt (exact potentials)");
     CUtensorMap ma, mb;
@@ -1959,7 +1982,7 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     cudaStream_t st = p->ctx->stream;
     double* part = (double*)p->partial.ptr;
     double* lin = p->has_fixed ? part + (size_t)nslots * T * Bpad : nullptr;
-    goac::launch(k_make_qt<__half>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
+    goac::launch(k_make_qt<__half>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
                  (const double*)p->z_dev, ld, (__half*)p->qt.ptr,
                  (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
@@ -2011,10 +2034,10 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     {
         const double* pf = p->has_fixed ? p->phifix : nullptr;
         if (tf32)
-            goac::launch(k_make_qt<float>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->z_dev,
+            goac::launch(k_make_qt<float>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->z_dev,
                          (const double*)p->z_dev, ld, (float*)p->qt.ptr, pf, lin);
         else
-            goac::launch(k_make_qt<__nv_bfloat16>, Bpad, 256, 0, st, species, B, p->Nv, (const double*)p->z_dev,
+            goac::launch(k_make_qt<__nv_bfloat16>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->z_dev,
                          (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, pf, lin);
         GOAC_LAUNCH_CHECK("k_make_qt");
     }
