@@ -88,6 +88,17 @@ __device__ __forceinline__ double rd_fma<double>(double a, double b, double c) {
 template <>
 __device__ __forceinline__ float rd_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+};
+
 // Barrier over the W warps of one chain group (named barrier `id`, 1..15).
 template <int W>
 __device__ __forceinline__ void chain_sync(int id)
@@ -159,17 +170,22 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
 
     const double kT = P.kT[chain];
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-    for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
-        const int64_t tb = (int64_t)sc.step0 + s0;      // first step of this batch
-        if (tb >= t_stop) break;
+    // ---- this lane's proposal of the batch starting at step offset s0 (state independent) ----
+    // The gathers diag[va], diag[vb], J[va][vb] are kept raw, so that the next batch's proposals
+    // can be drawn and their loads issued before the current batch is evaluated.
+    struct Prop {
+        int va, vb;
+        R da, db, jab;
+        R thr;                     // accept iff dE <= 1e-9 eV or dE < thr = -kT ln u
+    };
+    auto draw = [&](int64_t s0, Prop& pr) {
         const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
         const uint64_t t = sc.step0 + (uint64_t)s0 + (uint64_t)lane;
-        // ---- draw this lane's proposal (state independent) ----
-        int va = 0, vb = 0;
-        double u = 0.0, kTl = kT;
-        R jsum = (R)0;
-        R thr = (R)-INFINITY;      // accept iff dE <= 1e-9 eV or dE < thr = -kT ln u
+        pr.va = pr.vb = 0;
+        pr.da = pr.db = pr.jab = (R)0;
+        pr.thr = (R)-INFINITY;
         if (lane < nb) {
+            double kTl = kT;
             if (P.kT1 && P.total > 1)     // simulated annealing: kT0 (kT1/kT0)^(t/(total-1))
                 kTl = kT * exp(log(P.kT1[chain] / kT) * ((double)t / (double)(P.total - 1)));
             const uint4 x = goacd::philox(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)chain, 0u), k0, k1);
@@ -177,10 +193,10 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             if (P.nmovable != 1) {
                 const uint4 y =
                     goacd::philox(make_uint4((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)chain, 1u), k0, k1);
-                const uint32_t thr = goacd::draw_below(y.x, P.wtotal);
+                const uint32_t th = goacd::draw_below(y.x, P.wtotal);
                 k = P.ncls - 1;
                 for (int c = 0; c < P.ncls; ++c)
-                    if (P.wprefix[c] > thr) {
+                    if (P.wprefix[c] > th) {
                         k = c;
                         break;
                     }
@@ -190,18 +206,36 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
             const uint32_t a = goacd::draw_below(x.x, n);
             const uint32_t bb = goacd::draw_below(x.y, n - 1);
             const uint32_t b = bb + (bb >= a);
-            va = P.cls_pos[start + a];
-            vb = P.cls_pos[start + b];
-            u = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6)) * (1.0 / 9007199254740992.0);
-            jsum = rd_sub<R>(rd_add<R>(diag[va], diag[vb]), rd_mul<R>((R)2, J[(long)va * ld + vb]));
+            pr.va = P.cls_pos[start + a];
+            pr.vb = P.cls_pos[start + b];
+            const double u = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6)) * (1.0 / 9007199254740992.0);
+            pr.da = diag[pr.va];
+            pr.db = diag[pr.vb];
+            pr.jab = J[(long)pr.va * ld + pr.vb];
             // Metropolis: u < exp(-dE/kT) is the event dE < -kT ln u, so the
             // threshold is formed once per proposal, not per evaluation
             if (kTl > 0.0) {
-                if (u == 0.0) thr = (R)INFINITY;
-                else if (sizeof(R) == 8) thr = (R)(-kTl * log(u));
-                else thr = (R)(-(float)kTl * logf((float)u));
+                if (u == 0.0) pr.thr = (R)INFINITY;
+                else if (sizeof(R) == 8) pr.thr = (R)(-kTl * log(u));
+                else pr.thr = (R)(-(float)kTl * logf((float)u));
             }
         }
+    };
+    Prop cur, nxt;
+    if (W > 1 && sc.n_steps > 0) draw(0, nxt);
+    for (int64_t s0 = 0; s0 < sc.n_steps; s0 += 32) {
+        const int64_t tb = (int64_t)sc.step0 + s0;      // first step of this batch
+        if (tb >= t_stop) break;
+        const int nb = (int)((sc.n_steps - s0) < 32 ? (sc.n_steps - s0) : 32);
+        if (W > 1) {                                     // the next batch's loads fly meanwhile
+            cur = nxt;
+            if (s0 + 32 < sc.n_steps) draw(s0 + 32, nxt);
+        } else {
+            draw(s0, cur);
+        }
+        const int va = cur.va, vb = cur.vb;
+        const R thr = cur.thr;
+        const R jsum = rd_sub<R>(rd_add<R>(cur.da, cur.db), rd_mul<R>((R)2, cur.jab));
         const uint32_t valid = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
         // lanes whose step lies before t_stop
         auto live = [&](int64_t ts) -> uint32_t {
@@ -240,22 +274,56 @@ __device__ void run_chain(const McProb& P, int chain, const McScalars& sc, int8_
                 sp[ca] = sp[cb];
                 sp[cb] = ta;
             }
-            if (cd != (R)0) {
+            if (cd != (R)0 && W == 1) {
                 const R* __restrict__ ra = J + (long)ca * ld;
                 const R* __restrict__ rb = J + (long)cb * ld;
-                // this warp's slice, 8 loads of each row in flight per lane
-                for (int w0 = cw * 32 + lane; w0 < Nv; w0 += 32 * W * 8) {
+                // one warp: 8 loads of each row in flight per lane
+                for (int w0 = lane; w0 < Nv; w0 += 32 * 8) {
                     R xa[8], xb[8];
 #pragma unroll
                     for (int uu = 0; uu < 8; ++uu) {
-                        const int w = w0 + 32 * W * uu;
+                        const int w = w0 + 32 * uu;
                         xa[uu] = w < Nv ? ra[w] : (R)0;
                         xb[uu] = w < Nv ? rb[w] : (R)0;
                     }
 #pragma unroll
                     for (int uu = 0; uu < 8; ++uu) {
-                        const int w = w0 + 32 * W * uu;
+                        const int w = w0 + 32 * uu;
                         if (w < Nv) phi[w] = rd_fma<R>(cd, rd_sub<R>(xa[uu], xb[uu]), phi[w]);
+                    }
+                }
+            } else if (cd != (R)0) {
+                const R* __restrict__ ra = J + (long)ca * ld;
+                const R* __restrict__ rb = J + (long)cb * ld;
+                // W warps: 16-byte vectors of both rows (rows are ld >= Nv long, ld a multiple of 128), U
+                // of each in flight per thread; phi (its slot rounded up to 16 bytes) read and written as
+                // vectors, each element updated as phi + d (J_a - J_b) exactly as one element at a time
+                constexpr int V = 16 / (int)sizeof(R);
+                constexpr int U = 4;
+                using VT = typename Vec16<R>::T;
+                for (int w0 = ct * V; w0 < Nv; w0 += 32 * W * V * U) {
+                    VT xa[U], xb[U];
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int w = w0 + 32 * W * V * uu;
+                        if (w < Nv) {
+                            xa[uu] = *reinterpret_cast<const VT*>(ra + w);
+                            xb[uu] = *reinterpret_cast<const VT*>(rb + w);
+                        }
+                    }
+#pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                        const int w = w0 + 32 * W * V * uu;
+                        if (w < Nv) {
+                            VT pv = *reinterpret_cast<const VT*>(phi + w);
+                            R* pe = reinterpret_cast<R*>(&pv);
+                            const R* ae = reinterpret_cast<const R*>(&xa[uu]);
+                            const R* be = reinterpret_cast<const R*>(&xb[uu]);
+#pragma unroll
+                            for (int e = 0; e < V; ++e)
+                                if (w + e < Nv) pe[e] = rd_fma<R>(cd, rd_sub<R>(ae[e], be[e]), pe[e]);
+                            *reinterpret_cast<VT*>(phi + w) = pv;
+                        }
                     }
                 }
             }
@@ -397,6 +465,26 @@ McProb make_desc(goac_problem* p, bool f32, int8_t* species, int C, const double
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
+// Most chains per CTA that k_mc<R, W> can launch with (its register count
+// limits the threads of a block below 1,024 when it is above 64 per thread).
+template <typename R, int W>
+int mc_cpc_limit()
+{
+    static int lim = 0;
+    if (!lim) {
+        cudaFuncAttributes fa;
+        const int mt = cudaFuncGetAttributes(&fa, k_mc<R, W>) == cudaSuccess ? fa.maxThreadsPerBlock : 1024;
+        lim = std::max(1, mt / (32 * W));
+    }
+    return lim;
+}
+
+int mc_cpc_limit(bool f32, int W)
+{
+    if (f32) return W == 4 ? mc_cpc_limit<float, 4>() : W == 2 ? mc_cpc_limit<float, 2>() : mc_cpc_limit<float, 1>();
+    return W == 4 ? mc_cpc_limit<double, 4>() : W == 2 ? mc_cpc_limit<double, 2>() : mc_cpc_limit<double, 1>();
+}
+
 }  // namespace
 
 // W_force / cpc_force (> 0) override the launch shape (the autotuner's probes).
@@ -442,7 +530,7 @@ static goac_status mc_run_impl(goac_problem* p, int8_t* species_dev, int32_t C, 
     const int* tuned = p->mc_tuned[f32 ? 1 : 0];
     int W = W_force ? W_force : (tuned[0] ? tuned[0] : (p->Nv >= 3072 ? 4 : (p->Nv >= 1536 ? 2 : 1)));
     int cpc = (int)(kSmemBudget / slot);
-    cpc = std::min(cpc, 1024 / (32 * W));
+    cpc = std::min(cpc, mc_cpc_limit(f32, W));
     cpc = std::min(cpc, cpc_force ? cpc_force : (tuned[1] ? tuned[1] : 15));
     cpc = std::min(cpc, C);
     if (cpc < 1) cpc = 1;
@@ -542,7 +630,9 @@ extern "C" goac_status goac_mc_autotune(goac_problem* p, const int8_t* species_d
     for (int wi = 0; wi < 3 && !rc; ++wi) {
         for (int ci = 0; ci < 5 && !rc; ++ci) {
             const int W = Ws[wi], cpc = cpcs[ci];
-            if (slot * cpc > kSmemBudget || 32 * W * cpc > 1024 || (cpc > C && cpc != 1)) continue;
+            if (slot * cpc > kSmemBudget || cpc > mc_cpc_limit(precision == GOAC_PREC_F32, W) ||
+                (cpc > C && cpc != 1))
+                continue;
             for (int rep = 0; rep < 2 && !rc; ++rep) {
                 const cudaError_t e = cudaMemcpyAsync(sp, species_dev, (size_t)C * p->Nv, cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) {
