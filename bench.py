@@ -890,19 +890,22 @@ def run_suite(args, ctx=None, out=None):
         L = torch.tensor(synth.random_logits(prob, B, 5), device=dev)
         lam, eta = 1.0, 0.01
         res = {}
-        for prec in ("f64", "tf32x2"):
+        for prec in ("f64", "tf32x2", "f16x2"):
             gp.energy_grad(L[:2].contiguous(), lam, prec)
             box = {}
             ms = timed(lambda: box.setdefault("r", gp.energy_grad(L, lam, prec)))
             res[prec] = {"energy_grad_ms": ms, "grad_steps_per_s": 1e3 / ms}
         E64, g64 = gp.energy_grad(L, lam, "f64")
-        Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
-        res["tf32x2"]["max_rel_E_err"] = float(((Etc - E64).abs() / E64.abs()).max())
-        res["tf32x2"]["max_abs_grad_err_rel_to_max"] = float((gtc - g64).abs().max() / g64.abs().max())
-        Ld = L.clone()
-        E0 = gp.energy_grad(Ld, lam, "tf32x2")[0]
+        for prec in ("tf32x2", "f16x2"):
+            Etc, gtc = gp.energy_grad(L, lam, prec)
+            res[prec]["max_rel_E_err"] = float(((Etc - E64).abs() / E64.abs()).max())
+            res[prec]["max_abs_grad_err_rel_to_max"] = float((gtc - g64).abs().max() / g64.abs().max())
         steps = args.grad_steps
         box = {}
+        Lf = L.clone()
+        dms16 = timed(lambda: box.setdefault("E16", gp.relaxed_descent(Lf, lam, eta, steps, "f16x2")))
+        Ld = L.clone()
+        E0 = gp.energy_grad(Ld, lam, "tf32x2")[0]
         dms = timed(lambda: box.setdefault("E", gp.relaxed_descent(Ld, lam, eta, steps, "tf32x2")))
         p_occ = gp.occupations(Ld)
         rms = timed(lambda: box.setdefault("sp", gp.round_to_counts(p_occ)))
@@ -913,8 +916,10 @@ def run_suite(args, ctx=None, out=None):
         gms = timed(lambda: box.setdefault("Eg", gp.ga_run(seeded, 5, 40, oracle.p_mut_to_u32(0.1), 3, 0, "bf16x3")))
         emit({"workload": f"bcc 16^3 (N=8192, 5 species +1/+2/+3/+4/0), relaxed occupations, B={B} logits sets, "
                           f"counts penalty lambda={lam}", "forms": res,
-              "descent": {"steps": steps, "eta": eta, "ms": dms, "steps_per_s": steps / (dms / 1e3),
+              "descent": {"form": "tf32x2", "steps": steps, "eta": eta, "ms": dms, "steps_per_s": steps / (dms / 1e3),
                           "mean_E_before_eV": float(E0.mean()), "mean_E_after_eV": float(box["E"].mean())},
+              "descent_f16x2": {"steps": steps, "ms": dms16, "steps_per_s": steps / (dms16 / 1e3),
+                                "mean_E_after_eV": float(box["E16"].mean())},
               "round_to_counts_ms": rms,
               "seeded_population": {"mean_E_eV": float(E_seed.mean()), "min_E_eV": float(E_seed.min()),
                                     "random_population_mean_E_eV": float(E_rand.mean()),

@@ -65,6 +65,7 @@ typedef int32_t goac_status;
 #define GOAC_PREC_F32 5     /* FP32 CUDA cores (Monte Carlo / GA variant only)   */
 #define GOAC_PREC_EXACT 6   /* tcgen05 integer-digit split (FP64-grade, see below) */
 #define GOAC_PREC_F64_INCR 7 /* GA runs only: incremental FP64 rescoring (goac_ga_run) */
+#define GOAC_PREC_F16X2 8   /* relaxed gradient only: tcgen05 kind::f16 (FP16), J = hi + lo */
 
 typedef struct goac_ctx goac_ctx;
 typedef struct goac_problem goac_problem;
@@ -502,9 +503,12 @@ goac_status goac_batch_ga_run(goac_ctx* ctx, goac_problem* const* probs, int32_t
  *   g_vs = z_s (2 J q)_v + 2 lambda (sum_{w in k} p_ws - n_ks),             *
  *   dE/dL_vs = p_vs (g_vs - sum_t p_vt g_vt)  (0 for masked species).       *
  * E_dev: B doubles; dlogits_dev: B x Nv x S floats (nullable).  precision: *
- * GOAC_PREC_F64 (FP64 CUDA-core GEMM) or GOAC_PREC_TF32X2 (J.Q on tcgen05, *
+ * GOAC_PREC_F64 (FP64 CUDA-core GEMM), GOAC_PREC_TF32X2 (J.Q on tcgen05,  *
  * J and the real-valued Q each split in TF32 hi / lo, the products hi.hi,   *
- * hi.lo and lo.hi accumulated in FP32; Phi kept in FP32).                   *
+ * hi.lo and lo.hi accumulated in FP32; Phi kept in FP32) or                 *
+ * GOAC_PREC_F16X2 (the same three products with FP16 hi / lo parts, J      *
+ * scaled per 128-row panel by a power of two into FP16's range: the same   *
+ * 11-bit parts as TF32, at the FP16 tensor rate, twice TF32's).            *
  * ------------------------------------------------------------------------ */
 goac_status goac_energy_grad(goac_problem* prob, const float* logits_dev, int32_t B, double lambda,
                              int32_t precision, double* E_dev, float* dlogits_dev);

@@ -22,7 +22,7 @@ from ._lib import lib, LIB_PATH, SIGNATURES, GaParams, GaStats, McStats  # noqa:
 #: Coulomb constant e^2 / (4 pi eps0) in eV * Angstrom (CODATA 2018).
 KE = 14.3996454784
 
-PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5, "exact": 6, "f64_incr": 7}
+PREC = {"f64": 0, "tf32": 1, "tf32x2": 2, "bf16x2": 3, "bf16x3": 4, "f32": 5, "exact": 6, "f64_incr": 7, "f16x2": 8}
 
 
 class GoacError(RuntimeError):

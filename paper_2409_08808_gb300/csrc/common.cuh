@@ -123,6 +123,8 @@ struct goac_problem {
     __nv_bfloat16* J_bf16 = nullptr;   // [3][Nv_pad][Nv_pad]
     float* J_tf32 = nullptr;           // [2][Nv_pad][Nv_pad] (hi, lo) of the symmetric operand
     float* J_tf32_full = nullptr;      // [2][Nv_pad][Nv_pad] (hi, lo) of J_vv itself
+    __half* J_f16_full = nullptr;      // [2][Nv_pad][Nv_pad] (hi, lo) of J_vv 2^(15 - e_I), FP16
+    int* f16_exp = nullptr;            // e_I per 128-row panel of J_vv (max |J| < 2^e_I)
     float* J_f32 = nullptr;            // Nv_pad x Nv_pad (MC / GA FP32 variant)
     float* diag_f32 = nullptr;
     // scoring scratch
@@ -530,7 +532,7 @@ goac_status score_f64(goac_problem* p, const int8_t* species, int B, double* E_o
 goac_status score_f32(goac_problem* p, const int8_t* species, int B, double* E_out, float* phi_out);
 goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precision, double* E_out);
 goac_status prepare_f32(goac_problem* p);
-goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi);
+goac_status phi_tc(goac_problem* p, const void* qt2, int Bpad, float* Phi, bool f16 = false, int qshift = 0);
 // Exact-form potentials and energies (phi = J_vv q + phi_fix, B x Nv FP64, and
 // E as score_f64) on the tensor cores; false from exact_supported() means the
 // charges do not admit the exact form and score_f64 must be used.

@@ -170,6 +170,25 @@ __device__ __forceinline__ float tf32_rna(float x)
     return __uint_as_float(r);
 }
 
+// q's hi / lo parts at element e of the two planes [2][plane]: TF32 in FP32
+// storage, or FP16 of q qscale (F16), lo the rounding of what hi leaves.
+template <bool F16>
+__device__ __forceinline__ void store_q_planes(void* qt2, long plane, long e, float q, float qscale)
+{
+    if constexpr (F16) {
+        q *= qscale;                           // a power of two: |q qscale| < 2^14
+        __half* h = (__half*)qt2;
+        const __half hi = __float2half_rn(q);
+        h[e] = hi;
+        h[plane + e] = __float2half_rn(q - __half2float(hi));
+    } else {
+        float* f = (float*)qt2;
+        const float hi = tf32_rna(q);
+        f[e] = hi;
+        f[plane + e] = tf32_rna(q - hi);
+    }
+}
+
 // p = softmax of the logits over the species allowed in the site's class, FP32 out.
 __global__ void k_softmax_f32(const float* __restrict__ logits, long BN, int Nv, int S,
                               const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
@@ -191,9 +210,11 @@ __global__ void k_softmax_f32(const float* __restrict__ logits, long BN, int Nv,
 // One pass over the padded operand: p = softmax of the logits over the
 // species allowed in the site's class (FP32, B x Nv x S), q = sum_s p_s z_s,
 // and q's TF32 hi / lo planes [2][Bpad][ld] for the contraction (zero padded).
+template <bool F16>
 __global__ void k_relax_prep(const float* __restrict__ logits, int B, int Nv, int S, int Bpad, int ld,
                              const int32_t* __restrict__ vclass, const int32_t* __restrict__ counts,
-                             const double* __restrict__ z, float* __restrict__ p, float* __restrict__ qt2)
+                             const double* __restrict__ z, float* __restrict__ p, void* __restrict__ qt2,
+                             float qscale)
 {
     const long plane = (long)Bpad * ld;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (long)gridDim.x * blockDim.x) {
@@ -215,9 +236,7 @@ __global__ void k_relax_prep(const float* __restrict__ logits, int B, int Nv, in
                 q = fmaf(ps, (float)z[s], q);
             }
         }
-        const float hi = tf32_rna(q);
-        qt2[e] = hi;
-        qt2[plane + e] = tf32_rna(q - hi);
+        store_q_planes<F16>(qt2, plane, e, q, qscale);
     }
 }
 
@@ -360,12 +379,13 @@ constexpr int RV_KS = 64;                     // ncls * S limit of the chunk par
 // the chunk's occupation sums cpart[(b nch + c) ncls S + k S + s] = sum over
 // the chunk's sites v of class k of p_vs (FP32 within a thread and a warp in a
 // fixed order, FP64 over the eight warps in order).
-template <int S>
+template <int S, bool F16>
 __global__ void __launch_bounds__(RV_T) k_relax_prep_v4(const float* __restrict__ logits, int Nv, int ld, int nch,
                                                       const int32_t* __restrict__ vclass,
                                                       const int32_t* __restrict__ counts,
                                                       const double* __restrict__ z, int ncls, float* __restrict__ p,
-                                                      float* __restrict__ qt2, long plane, double* __restrict__ cpart)
+                                                      void* __restrict__ qt2, long plane, double* __restrict__ cpart,
+                                                      float qscale)
 {
     __shared__ int cnt[RV_KS];
     __shared__ double wsum[RV_T / 32][RV_KS];
@@ -443,14 +463,29 @@ __global__ void __launch_bounds__(RV_T) k_relax_prep_v4(const float* __restrict_
             if (j < nv * S) p[t0 * S + j] = P[j];
     }
     if (v0 + RV_G <= ld) {
-        float hi[RV_G], lo[RV_G];
+        if constexpr (F16) {
+            __half2 hi[2], lo[2];
 #pragma unroll
-        for (int g = 0; g < RV_G; ++g) {
-            hi[g] = tf32_rna(qv[g]);
-            lo[g] = tf32_rna(qv[g] - hi[g]);
+            for (int g = 0; g < RV_G; g += 2) {
+                const float a0 = qv[g] * qscale, a1 = qv[g + 1] * qscale;   // a power of two: |a| < 2^14
+                const __half h0 = __float2half_rn(a0), h1 = __float2half_rn(a1);
+                hi[g / 2] = __halves2half2(h0, h1);
+                lo[g / 2] = __halves2half2(__float2half_rn(a0 - __half2float(h0)), __float2half_rn(a1 - __half2float(h1)));
+            }
+            __half* h = (__half*)qt2;
+            *reinterpret_cast<uint2*>(h + (long)b * ld + v0) = *reinterpret_cast<const uint2*>(hi);
+            *reinterpret_cast<uint2*>(h + plane + (long)b * ld + v0) = *reinterpret_cast<const uint2*>(lo);
+        } else {
+            float hi[RV_G], lo[RV_G];
+#pragma unroll
+            for (int g = 0; g < RV_G; ++g) {
+                hi[g] = tf32_rna(qv[g]);
+                lo[g] = tf32_rna(qv[g] - hi[g]);
+            }
+            float* f = (float*)qt2;
+            *reinterpret_cast<float4*>(f + (long)b * ld + v0) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<float4*>(f + plane + (long)b * ld + v0) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
-        *reinterpret_cast<float4*>(qt2 + (long)b * ld + v0) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<float4*>(qt2 + plane + (long)b * ld + v0) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int kk = 0; kk < ncls; ++kk)
@@ -625,10 +660,15 @@ __global__ void k_energy_v4(const double* __restrict__ epart, const double* __re
 
 template <int S>
 void launch_relax_v4(int B, int Nv, int ld, int nch, const goac_problem* p, const float* logits, float* P32,
-                     float* qt2, long plane, double* cpart, cudaStream_t st)
+                     void* qt2, long plane, double* cpart, bool f16, float qscale, cudaStream_t st)
 {
-    goac::launch(k_relax_prep_v4<S>, B * nch, RV_T, 0, st, logits, Nv, ld, nch, (const int32_t*)p->vclass_dev,
-                 (const int32_t*)p->counts_dev, (const double*)p->z_dev, p->ncls, P32, qt2, plane, cpart);
+    if (f16)
+        goac::launch(k_relax_prep_v4<S, true>, B * nch, RV_T, 0, st, logits, Nv, ld, nch, (const int32_t*)p->vclass_dev,
+                     (const int32_t*)p->counts_dev, (const double*)p->z_dev, p->ncls, P32, qt2, plane, cpart, qscale);
+    else
+        goac::launch(k_relax_prep_v4<S, false>, B * nch, RV_T, 0, st, logits, Nv, ld, nch,
+                     (const int32_t*)p->vclass_dev, (const int32_t*)p->counts_dev, (const double*)p->z_dev, p->ncls,
+                     P32, qt2, plane, cpart, 1.0f);
 }
 
 template <int S>
@@ -760,11 +800,24 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
     if (B <= 0 || B > GOAC_MAX_BATCH)
         return B == 0 ? GOAC_OK : goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: B < 0 or B > GOAC_MAX_BATCH");
     if (!logits_dev || !E_dev) return goac::fail(GOAC_ERR_INVALID_ARG, "goac_energy_grad: NULL");
-    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_TF32X2)
-        return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: precision must be F64 or TF32X2");
+    if (precision != GOAC_PREC_F64 && precision != GOAC_PREC_TF32X2 && precision != GOAC_PREC_F16X2)
+        return goac::fail(GOAC_ERR_UNSUPPORTED, "goac_energy_grad: precision must be F64, TF32X2 or F16X2");
     GOAC_CUDA(cudaSetDevice(p->ctx->device));
     const int Nv = p->Nv, S = p->S, ncls = p->ncls, ld = p->Nv_pad;
-    const bool tc = precision == GOAC_PREC_TF32X2;
+    const bool tc = precision == GOAC_PREC_TF32X2 || precision == GOAC_PREC_F16X2;
+    const bool f16 = precision == GOAC_PREC_F16X2;
+    const size_t qbytes = f16 ? sizeof(__half) : sizeof(float);   // one element of q's hi / lo planes
+    // FP16: q is scaled by 2^qshift so that |q| 2^qshift < 2^14 (|q| <= max |z|), and so that the lo
+    // parts of all but the smallest charges stay in FP16's normal range; the contraction undoes it
+    int qshift = 0;
+    if (f16) {
+        double zmax = 0.0;
+        for (int s2 = 0; s2 < S; ++s2) zmax = std::max(zmax, fabs(p->z[s2]));
+        int ez = 0;
+        if (zmax > 0.0) frexp(zmax, &ez);         // zmax < 2^ez
+        qshift = 14 - ez;
+    }
+    const float qscale = (float)ldexp(1.0, qshift);
     const int Bpad = ((B + 255) / 256) * 256;      // whole 256-configuration tiles of the contraction
     const long BN = (long)B * Nv;
     cudaStream_t st = p->ctx->stream;
@@ -784,32 +837,40 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
         float* P32 = (float*)p->grad_tmp.ptr;
         double* colsum = (double*)(((uintptr_t)(P32 + BN * S) + 255) & ~(uintptr_t)255);
         double* epart = colsum + (size_t)B * nch * ncls * S;        // vec only
-        float* qt2 = (float*)(((uintptr_t)(colsum + ncol) + 255) & ~(uintptr_t)255);   // TMA: aligned
-        float* Phi = qt2 + 2 * (size_t)Bpad * ld;
+        float* qt2f = (float*)(((uintptr_t)(colsum + ncol) + 255) & ~(uintptr_t)255);   // TMA: aligned
+        void* qt2 = qt2f;                                       // FP32 planes, or FP16 planes in their front half
+        float* Phi = qt2f + 2 * (size_t)Bpad * ld;
         const long plane = (long)Bpad * ld;
         if (vec) {
             if (Bpad > B) {
-                GOAC_CUDA(cudaMemsetAsync(qt2 + (size_t)B * ld, 0, sizeof(float) * (size_t)(Bpad - B) * ld, st));
-                GOAC_CUDA(cudaMemsetAsync(qt2 + plane + (size_t)B * ld, 0, sizeof(float) * (size_t)(Bpad - B) * ld, st));
+                uint8_t* q8 = (uint8_t*)qt2;
+                GOAC_CUDA(cudaMemsetAsync(q8 + qbytes * (size_t)B * ld, 0, qbytes * (size_t)(Bpad - B) * ld, st));
+                GOAC_CUDA(cudaMemsetAsync(q8 + qbytes * ((size_t)plane + (size_t)B * ld), 0,
+                                          qbytes * (size_t)(Bpad - B) * ld, st));
             }
             switch (S) {
-            case 1: launch_relax_v4<1>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 2: launch_relax_v4<2>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 3: launch_relax_v4<3>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 4: launch_relax_v4<4>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 5: launch_relax_v4<5>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 6: launch_relax_v4<6>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            case 7: launch_relax_v4<7>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
-            default: launch_relax_v4<8>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, st); break;
+            case 1: launch_relax_v4<1>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 2: launch_relax_v4<2>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 3: launch_relax_v4<3>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 4: launch_relax_v4<4>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 5: launch_relax_v4<5>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 6: launch_relax_v4<6>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            case 7: launch_relax_v4<7>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
+            default: launch_relax_v4<8>(B, Nv, ld, nch, p, logits_dev, P32, qt2, plane, colsum, f16, qscale, st); break;
             }
         } else {
-            goac::launch(k_relax_prep, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st, logits_dev,
-                         B, Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2);
+            if (f16)
+                goac::launch(k_relax_prep<true>, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st,
+                             logits_dev, B, Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2,
+                             qscale);
+            else
+                goac::launch(k_relax_prep<false>, (int)std::min<long>((plane + 255) / 256, 65535L * 4), 256, 0, st,
+                             logits_dev, B, Nv, S, Bpad, ld, p->vclass_dev, p->counts_dev, p->z_dev, P32, qt2, 1.0f);
             goac::launch(k_colsum_f32, B * ncls, 256, 0, st, (const float*)P32, Nv, S, ncls, p->cls_start_dev,
                          p->cls_pos_dev, colsum);
         }
         GOAC_LAUNCH_CHECK("k_relax_prep");
-        rc = goac::phi_tc(p, qt2, Bpad, Phi);
+        rc = goac::phi_tc(p, qt2, Bpad, Phi, f16, qshift);
         if (rc) return rc;
         if (vec) {
 #define GOAC_FINISH_V4(SS)                                                                                         \
@@ -908,7 +969,7 @@ extern "C" goac_status goac_relaxed_descent(goac_problem* p, float* logits_dev, 
     const long n = (long)B * p->Nv * p->S;
     const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
     for (int it = 0; it < n_steps; ++it) {
-        if (precision == GOAC_PREC_TF32X2) {
+        if (precision == GOAC_PREC_TF32X2 || precision == GOAC_PREC_F16X2) {
             // gradient and step fused: the chain-rule kernel updates the logits in place
             goac_status rc = energy_grad_impl(p, logits_dev, B, lambda, precision, E_dev, nullptr, logits_dev, (float)eta);
             if (rc) return rc;

@@ -958,6 +958,8 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->J_bf16);
     cudaFree(p->J_tf32);
     cudaFree(p->J_tf32_full);
+    cudaFree(p->J_f16_full);
+    cudaFree(p->f16_exp);
     cudaFree(p->J_f32);
     cudaFree(p->diag_f32);
     free_buf(p->qt);

@@ -349,10 +349,17 @@ __device__ __forceinline__ PhiItem phi_item(int it, int nfull, int nbn, int nkb)
     return w;
 }
 
+// F16: the same kernel on kind::f16 with FP16 operands (J scaled per 128-row
+// panel I by 2^(15 - e_I) and q by 2^qshift, so that the hi / lo parts stay in
+// FP16's range; 32 k-columns per 64-byte row), twice the TF32 rate; the
+// epilogue multiplies the tile by 2^(e_I - 15 - qshift) (exact).
+template <bool F16>
 __global__ void __launch_bounds__(192, 1)
     k_phi_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nitems, int nfull,
-             int nbn, int nkb, int ld, int Bpad, float* __restrict__ Phi, int* __restrict__ err)
+             int nbn, int nkb, int ld, int Bpad, const int* __restrict__ pexp, int qshift, float* __restrict__ Phi,
+             int* __restrict__ err)
 {
+    constexpr int KB = F16 ? 32 : PT_KB;         // k elements per stage (64-byte rows)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + PT_STAGES * PT_STAGE);
@@ -406,10 +413,10 @@ __global__ void __launch_bounds__(192, 1)
                     if (*abort_flag) break;
                     uint8_t* st = smem + s * PT_STAGE;
                     goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
-                    goacd::tma_load_2d(st, &tmA, &full[s], kb * PT_KB, m0);
-                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * PT_KB, ld + m0);
-                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * PT_KB, n0);
-                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * PT_KB, Bpad + n0);
+                    goacd::tma_load_2d(st, &tmA, &full[s], kb * KB, m0);
+                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * KB, ld + m0);
+                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * KB, n0);
+                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * KB, Bpad + n0);
                 }
             }
             if (*abort_flag)
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(2u, TC_M, PT_N);
+            constexpr uint32_t idesc = goacd::idesc_f32acc(F16 ? 0u : 2u, TC_M, PT_N);   // FP16 or TF32
             int it = 0, tl = 0;
             for (int id = blockIdx.x; id < nitems; id += gridDim.x, ++tl) {
                 const PhiItem w = phi_item(id, nfull, nbn, nkb);
@@ -448,12 +455,19 @@ __global__ void __launch_bounds__(192, 1)
                     const uint32_t b_hi = a_hi + 2 * PT_A;
                     const uint32_t b_lo = b_hi + PT_B;
 #pragma unroll
-                    for (int kk = 0; kk < PT_KB / 8; ++kk) {          // K = 8 per TF32 MMA: 32 bytes of each row
+                    for (int kk = 0; kk < 2; ++kk) {    // K = 8 (TF32) or 16 (FP16) per MMA: 32 bytes of each row
                         const uint32_t off = kk * 32;
-                        goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_hi + off), idesc,
-                                        (j != 0 || kk != 0) ? 1u : 0u);
-                        goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_lo + off), idesc, 1u);
-                        goacd::mma_tf32(d_tmem, sdesc_k64(a_lo + off), sdesc_k64(b_hi + off), idesc, 1u);
+                        if constexpr (F16) {
+                            goacd::mma_bf16(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_hi + off), idesc,
+                                            (j != 0 || kk != 0) ? 1u : 0u);
+                            goacd::mma_bf16(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_lo + off), idesc, 1u);
+                            goacd::mma_bf16(d_tmem, sdesc_k64(a_lo + off), sdesc_k64(b_hi + off), idesc, 1u);
+                        } else {
+                            goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_hi + off), idesc,
+                                            (j != 0 || kk != 0) ? 1u : 0u);
+                            goacd::mma_tf32(d_tmem, sdesc_k64(a_hi + off), sdesc_k64(b_lo + off), idesc, 1u);
+                            goacd::mma_tf32(d_tmem, sdesc_k64(a_lo + off), sdesc_k64(b_hi + off), idesc, 1u);
+                        }
                     }
                     goacd::mma_commit(&empty[s]);
                 }
@@ -474,6 +488,7 @@ __global__ void __launch_bounds__(192, 1)
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
             const int v = m0 + lg * 32 + lane;
+            const float sc = F16 ? __int_as_float((pexp[m0 / TC_M] - 15 - qshift + 127) << 23) : 1.0f;
 #pragma unroll 1
             for (int c = 0; c < PT_N / 32; ++c) {
                 uint32_t r[32];
@@ -483,10 +498,11 @@ __global__ void __launch_bounds__(192, 1)
                 goacd::tmem_ld_wait();
                 if (ok && !w.add) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; ++j) Phi[(long)(n0 + c * 32 + j) * ld + v] = __uint_as_float(r[j]) * sc;
                 } else if (ok) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) atomicAdd(&Phi[(long)(n0 + c * 32 + j) * ld + v], __uint_as_float(r[j]));
+                    for (int j = 0; j < 32; ++j)
+                        atomicAdd(&Phi[(long)(n0 + c * 32 + j) * ld + v], __uint_as_float(r[j]) * sc);
                 }
             }
             goacd::tc_fence_before();
@@ -1010,6 +1026,22 @@ __global__ void k_panel_exp(const double* __restrict__ J, int ld, int sym, int* 
         int e = 0;
         if (red[0] > 0.0) frexp(red[0], &e);     // red < 2^e
         pexp[I] = e;
+    }
+}
+
+// FP16 hi / lo of J_vv 2^(15 - e_I) (e_I of row i's panel, max |J| < 2^e_I, so
+// every scaled entry is below 2^15): out[0][i][j] = hi, out[1][i][j] = lo, each
+// the FP16 rounding of what the parts before it leave.
+__global__ void k_split_f16_full(const double* __restrict__ J, int ld, const int* __restrict__ pexp,
+                                 __half* __restrict__ out)
+{
+    const long n = (long)ld * ld;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld);
+        const double x = ldexp(J[e], 15 - pexp[i / TC_M]);
+        const __half hi = __double2half(x);
+        out[e] = hi;
+        out[n + e] = __double2half(x - (double)__half2float(hi));
     }
 }
 
@@ -1780,24 +1812,39 @@ goac_status prepare_f32(goac_problem* p)
 }
 
 // Phi[b][v] (FP32, Bpad x Nv_pad) = sum_w J_vv[v][w] q[b][w] for real q given as
-// TF32 hi / lo planes qt2 = [2][Bpad][Nv_pad] (FP32 storage), on tcgen05.
-goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
+// hi / lo planes qt2 = [2][Bpad][Nv_pad], TF32 in FP32 storage (f16: FP16), on tcgen05.
+goac_status phi_tc(goac_problem* p, const void* qt2, int Bpad, float* Phi, bool f16, int qshift)
 {
     const int ld = p->Nv_pad;
     const long n = (long)ld * ld;
     cudaStream_t st = p->ctx->stream;
-    if (!p->J_tf32_full) {
-        GOAC_CUDA(cudaMalloc(&p->J_tf32_full, sizeof(float) * 2 * (size_t)n));
-        const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
-        goac::launch(k_split_tf32_full, blocks, 256, 0, st, (const double*)p->J_vv, n, p->J_tf32_full);
-        GOAC_LAUNCH_CHECK("k_split_tf32_full");
-    }
+    const int blocks = (int)std::min<long>((n + 255) / 256, 65535L * 4);
     CUtensorMap ma, mb;
-    goac_status rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M, PT_ROW);
-    if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N, PT_ROW);
+    goac_status rc = GOAC_OK;
+    if (f16) {
+        if (!p->J_f16_full) {
+            GOAC_CUDA(cudaMalloc(&p->f16_exp, sizeof(int) * (ld / TC_M)));
+            GOAC_CUDA(cudaMalloc(&p->J_f16_full, sizeof(__half) * 2 * (size_t)n));
+            goac::launch(k_panel_exp, ld / TC_M, 256, 0, st, (const double*)p->J_vv, ld, 0, p->f16_exp);
+            goac::launch(k_split_f16_full, blocks, 256, 0, st, (const double*)p->J_vv, ld, (const int*)p->f16_exp,
+                         p->J_f16_full);
+            GOAC_LAUNCH_CHECK("k_split_f16_full");
+        }
+        rc = make_map(&ma, p->J_f16_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, 2L * ld, ld, TC_M, PT_ROW);
+        if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, 2L * Bpad, ld, PT_N, PT_ROW);
+    } else {
+        if (!p->J_tf32_full) {
+            GOAC_CUDA(cudaMalloc(&p->J_tf32_full, sizeof(float) * 2 * (size_t)n));
+            goac::launch(k_split_tf32_full, blocks, 256, 0, st, (const double*)p->J_vv, n, p->J_tf32_full);
+            GOAC_LAUNCH_CHECK("k_split_tf32_full");
+        }
+        rc = make_map(&ma, p->J_tf32_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * ld, ld, TC_M, PT_ROW);
+        if (!rc) rc = make_map(&mb, (void*)qt2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, 2L * Bpad, ld, PT_N, PT_ROW);
+    }
     if (rc) return rc;
-    static std::atomic<uint64_t> attr_done{0};
-    rc = smem_attr_once((const void*)k_phi_tc, PT_SMEM, attr_done, p->ctx->device);
+    static std::atomic<uint64_t> attr_tf32{0}, attr_f16{0};
+    rc = f16 ? smem_attr_once((const void*)k_phi_tc<true>, PT_SMEM, attr_f16, p->ctx->device)
+             : smem_attr_once((const void*)k_phi_tc<false>, PT_SMEM, attr_tf32, p->ctx->device);
     if (rc) return rc;
     if (Bpad % PT_N != 0) return fail(GOAC_ERR_INTERNAL, "phi_tc: padded batch must be a multiple of 256");
     const int nbn = Bpad / PT_N;
@@ -1805,13 +1852,17 @@ goac_status phi_tc(goac_problem* p, const float* qt2, int Bpad, float* Phi)
     const int grid = std::min(ntiles, p->ctx->num_sms);
     // whole waves of whole tiles; the rest split in k-halves when that keeps them within one wave
     const int rest = ntiles % grid;
-    const int nkb = ld / PT_KB;
+    const int nkb = ld / (f16 ? 32 : PT_KB);
     const int nfull = (rest > 0 && 2 * rest <= grid && nkb >= 2) ? ntiles - rest : ntiles;
     const int nitems = nfull + 2 * (ntiles - nfull);
     if (nitems > nfull) GOAC_CUDA(cudaMemsetAsync(Phi, 0, sizeof(float) * (size_t)Bpad * ld, st));
     KTimer kt(p->ctx, KID_SCORE_TC, st);
-    goac::launch(k_phi_tc, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, nkb, ld, Bpad, Phi,
-                 p->ctx->d_err);
+    if (f16)
+        goac::launch(k_phi_tc<true>, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, nkb, ld, Bpad,
+                     (const int*)p->f16_exp, qshift, Phi, p->ctx->d_err);
+    else
+        goac::launch(k_phi_tc<false>, grid, 192, PT_SMEM, st, ma, mb, nitems, nfull, nbn, nkb, ld, Bpad,
+                     (const int*)nullptr, 0, Phi, p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_phi_tc");
     return GOAC_OK;
 }

@@ -212,13 +212,18 @@ def _many_species_problem():
     return prob
 
 
+@pytest.mark.parametrize("form", ["tf32x2", "f16x2"])
 @pytest.mark.parametrize("which,B", [("layered", 3), ("bcc", 5), ("s10", 4), ("layered864", 3)])
-def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
-    """J.Q on tcgen05 with J and the real Q split in TF32 hi/lo: within the
-    deterministic bound of the form.  Per site, |dPhi_v| <= (gamma_K + 2^-20)
-    sum_w |J_vw q_w| (K = 3 Nv products accumulated in FP32; the three kept
-    products miss at most 2^-20 relative), so |dE| <= sum_v |q_v| that bound
-    and |d(dE/dL_vs)| <= 4 max|z| p_vs that bound (+ FP32 output rounding).
+def test_energy_grad_tensor_core_tf32x2(ctx, which, B, form):
+    """J.Q on tcgen05 with J and the real Q split in hi/lo parts of 11-bit
+    significands (TF32, or FP16 with J scaled per 128-row panel and q scaled
+    by powers of two into FP16's range): within the deterministic bound of
+    the form.  Per site, |dPhi_v| <= (gamma_K + 2^-20) sum_w |J_vw q_w|
+    (K = 3 Nv products accumulated in FP32; the three kept products miss at
+    most 2^-20 relative; an FP16 lo part below the normal range is off by at
+    most 2^-39 of its panel's largest |J| or of max|z|, far inside that
+    margin), so |dE| <= sum_v |q_v| that bound and |d(dE/dL_vs)| <=
+    4 max|z| p_vs that bound (+ FP32 output rounding).
     Cases: one 256-site chunk of the elementwise kernels (layered 2x1x1, bcc
     4^3), more than 8 species (the general kernels), and several classes over
     Nv = 864 = 3 x 256 + 96 sites (chunk partials of every class, a ragged
@@ -232,7 +237,7 @@ def test_energy_grad_tensor_core_tf32x2(ctx, which, B):
     gp = g.Problem(ctx, Jg, prob.site_class, prob.fixed_q, prob.z, prob.counts, allow_charged=True)
     L = synth.random_logits(prob, B, 13)
     lam = 0.05
-    E, dL = gp.energy_grad(torch.tensor(L, device="cuda"), lam, "tf32x2")
+    E, dL = gp.energy_grad(torch.tensor(L, device="cuda"), lam, form)
     E, dL = E.cpu().numpy(), dL.cpu().numpy()
     K = 3 * gp.Nv
     eps = K * 2.0 ** -24 + 2.0 ** -20
@@ -291,16 +296,17 @@ def test_energy_grad_full_size(ctx):
     B, lam = 4, 1.0
     L = torch.tensor(synth.random_logits(prob, B, 21), device="cuda")
     E64, g64 = gp.energy_grad(L, lam, "f64")
-    Etc, gtc = gp.energy_grad(L, lam, "tf32x2")
     z = torch.tensor(prob.z, device="cuda")
     p = torch.softmax(L.double(), dim=2)
     q = p @ z
     mass = J.abs() @ q.abs().T                       # (N, B): sum_w |J_vw q_w|
     eps = 3 * gp.Nv * 2.0 ** -24 + 2.0 ** -20
     boundE = eps * (q.abs() * mass.T).sum(dim=1) + 1e-9
-    assert torch.all((Etc - E64).abs() <= boundE)
     boundG = 4 * z.abs().max() * p * (eps * mass.T)[:, :, None] + 2.0 ** -23 * g64.abs()
-    assert torch.all((gtc - g64).abs() <= boundG + 1e-30)
+    for form in ("tf32x2", "f16x2"):
+        Etc, gtc = gp.energy_grad(L, lam, form)
+        assert torch.all((Etc - E64).abs() <= boundE), form
+        assert torch.all((gtc - g64).abs() <= boundG + 1e-30), form
     rng = np.random.default_rng(5)
     for _ in range(8):
         b, v, s = int(rng.integers(B)), int(rng.integers(gp.Nv)), int(rng.integers(prob.S))
@@ -314,10 +320,10 @@ def test_energy_grad_full_size(ctx):
         assert abs(fd - g64[b, v, s].item()) <= 1e-5 * g64[b].abs().max().item() + 1e-6
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x2"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x2", "f16x2"])
 def test_relaxed_descent_equals_gradient_steps(ctx, prec):
-    """goac_relaxed_descent (for TF32x2 the step is fused into the chain-rule
-    kernel) gives the logits of the same number of explicit steps
+    """goac_relaxed_descent (for TF32x2 and FP16x2 the step is fused into the
+    chain-rule kernel) gives the logits of the same number of explicit steps
     L <- L - eta dE/dL taken with goac_energy_grad, up to the FP32 rounding of
     the update, and the energy decreases."""
     import paper_2409_08808_gb300 as g
