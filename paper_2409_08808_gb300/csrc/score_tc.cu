@@ -313,6 +313,31 @@ constexpr int PT_STAGE = 2 * PT_A + 2 * PT_B; // 48 KB
 constexpr int PT_STAGES = 4;
 constexpr int PT_SMEM = PT_STAGES * PT_STAGE + 1024 + 256;
 
+// TMA tile load with an L2 eviction-priority hint (a policy made by createpolicy).
+__device__ __forceinline__ void tma_load_2d_hint(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(goacd::smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(goacd::smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Shared-memory descriptor of a K-major operand tile with 64-byte rows and the
 // 64-byte swizzle (8-row groups 512 bytes apart).
 __device__ __forceinline__ uint64_t sdesc_k64(uint32_t saddr)
@@ -396,6 +421,7 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            const uint64_t pol_j = l2_policy_evict_first(), pol_q = l2_policy_evict_last();
             int it = 0;
             for (int id = blockIdx.x; id < nitems && !*abort_flag; id += gridDim.x) {
                 const PhiItem w = phi_item(id, nfull, nbn, nkb);
@@ -413,10 +439,12 @@ __global__ void __launch_bounds__(192, 1)
                     if (*abort_flag) break;
                     uint8_t* st = smem + s * PT_STAGE;
                     goacd::mbar_arrive_expect_tx(&full[s], PT_STAGE);
-                    goacd::tma_load_2d(st, &tmA, &full[s], kb * KB, m0);
-                    goacd::tma_load_2d(st + PT_A, &tmA, &full[s], kb * KB, ld + m0);
-                    goacd::tma_load_2d(st + 2 * PT_A, &tmB, &full[s], kb * KB, n0);
-                    goacd::tma_load_2d(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * KB, Bpad + n0);
+                    // J's panels stream past (each is read by one wave), Q is read again by every wave:
+                    // J's lines go first from L2, Q's last
+                    tma_load_2d_hint(st, &tmA, &full[s], kb * KB, m0, pol_j);
+                    tma_load_2d_hint(st + PT_A, &tmA, &full[s], kb * KB, ld + m0, pol_j);
+                    tma_load_2d_hint(st + 2 * PT_A, &tmB, &full[s], kb * KB, n0, pol_q);
+                    tma_load_2d_hint(st + 2 * PT_A + PT_B, &tmB, &full[s], kb * KB, Bpad + n0, pol_q);
                 }
             }
             if (*abort_flag)
