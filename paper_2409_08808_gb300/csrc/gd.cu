@@ -10,10 +10,16 @@
 // then swapped: phi += d (J_:a - J_:b), E += dE.
 //
 // The pair scan is a tile computation over the upper triangle of 64 x 64
-// blocks of J_vv: each CTA stages its J tile in shared memory once and
-// evaluates it for GD_CFG configurations; per-tile candidates are reduced per
-// configuration in a fixed order.  FP64 with explicitly rounded operations in
-// the order of the definition.
+// blocks of J_vv: each CTA stages its J tile (doubled: 2 J_ab, exact) in
+// shared memory once and evaluates it for GD_CFG configurations, with 2d and
+// d^2 taken from a per-species-pair table, so that each pair costs six FP64
+// operations with the roundings of the definition.  Pass 0 also keeps each
+// tile's tie set (its pairs within 1e-9 eV of the tile's minimum, up to GK of
+// them): the pairs eligible in pass 1 all lie in the tie sets of the tiles
+// whose minimum is within 1e-9 eV of dmin, so pass 1 runs (for that
+// configuration) only when one of those tie sets overflowed.  Per-tile
+// candidates are reduced per configuration in a fixed order.  FP64 with
+// explicitly rounded operations in the order of the definition.
 #include <math.h>
 
 #include <algorithm>
@@ -24,6 +30,8 @@ namespace {
 
 constexpr int GT = 64;        // tile edge (sites)
 constexpr int GD_CFG = 4;     // configurations per CTA
+constexpr int GK = 4;         // tie-set entries kept per tile and configuration
+constexpr int GS = 16;        // species of the (2d, d^2) table (more: formed per pair)
 constexpr double kTie = 1e-9; // energy tie tolerance (eV)
 
 struct GdArgs {
@@ -35,15 +43,27 @@ struct GdArgs {
     const double* z;          // 64
     const int* active;        // B
     const double* dmin;       // B (pass 1)
-    double* cand_val;         // ntiles x B
-    unsigned long long* cand_key;   // ntiles x B
-    int ld, Nv, B, ntiles;
+    const int* need1;         // B: pass 1 needed (a tie set overflowed)
+    double* cand_val;         // ntiles x B: tile minimum (pass 0)
+    unsigned long long* cand_key;   // ntiles x B (pass 1)
+    double* tie_val;          // ntiles x B x GK: tie-set energies (pass 0)
+    unsigned long long* tie_key;    // ntiles x B x GK: tie-set pair keys a Nv + b
+    int* tie_n;               // ntiles x B: tie-set size (> GK: overflow)
+    int ld, Nv, B, ntiles, S;
 };
 
 __device__ __forceinline__ double pair_dE(double d, double pa, double pb, double jaa, double jbb, double jab)
 {
     return __dadd_rn(__dmul_rn(__dmul_rn(2.0, d), __dsub_rn(pa, pb)),
                      __dmul_rn(__dmul_rn(d, d), __dsub_rn(__dadd_rn(jaa, jbb), __dmul_rn(2.0, jab))));
+}
+
+// dE with c1 = 2 d and c2 = d d (both as the definition rounds them) and
+// jab2 = 2 J_ab: the same value as pair_dE, bit for bit.
+__device__ __forceinline__ double pair_dE_c(double c1, double c2, double pa, double pb, double jaa, double jbb,
+                                            double jab2)
+{
+    return __dadd_rn(__dmul_rn(c1, __dsub_rn(pa, pb)), __dmul_rn(c2, __dsub_rn(__dadd_rn(jaa, jbb), jab2)));
 }
 
 template <int PASS>
@@ -54,19 +74,35 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
     __shared__ int8_t spI[GD_CFG][GT], spJ[GD_CFG][GT];
     __shared__ int clI[GT], clJ[GT];
     __shared__ double dgI[GT], dgJ[GT];
+    __shared__ double c1t[GS * GS], c2t[GS * GS];
     __shared__ double redv[256];
     __shared__ unsigned long long redk[256];
+    __shared__ double tv[GK];
+    __shared__ unsigned long long tk[GK];
+    __shared__ int tn;
+    const int c0 = blockIdx.y * GD_CFG;
+    if (PASS == 1) {            // only the configurations whose tie sets overflowed
+        bool any = false;
+        for (int c = 0; c < GD_CFG; ++c) any |= c0 + c < g.B && g.active[c0 + c] && g.need1[c0 + c];
+        if (!any) return;       // uniform over the block
+    }
     int t = blockIdx.x;
     int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
     while (bj * (bj + 1) / 2 > t) --bj;
     const int bi = t - bj * (bj + 1) / 2;
     const int i0 = bi * GT, j0 = bj * GT;
-    const int c0 = blockIdx.y * GD_CFG;
     for (int e = threadIdx.x; e < GT * GT; e += 256) {
         const int r = e / GT, c = e % GT;
-        Jt[r][c] = g.J[(long)(i0 + r) * g.ld + j0 + c];
+        Jt[r][c] = 2.0 * g.J[(long)(i0 + r) * g.ld + j0 + c];    // exact
     }
+    const bool table = g.S <= GS;
+    if (table)
+        for (int e = threadIdx.x; e < g.S * g.S; e += 256) {
+            const double d = __dsub_rn(g.z[e % g.S], g.z[e / g.S]);     // [sa][sb]: z_sb - z_sa
+            c1t[e] = __dmul_rn(2.0, d);
+            c2t[e] = __dmul_rn(d, d);
+        }
     for (int e = threadIdx.x; e < GT; e += 256) {
         const bool vi = i0 + e < g.Nv, vj = j0 + e < g.Nv;
         clI[e] = vi ? g.vclass[i0 + e] : -1;
@@ -87,20 +123,32 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
     const int jq = (threadIdx.x / GT) * 16;
     for (int c = 0; c < GD_CFG; ++c) {
         const int b = c0 + c;
-        const bool live = b < g.B && g.active[b];   // uniform over the block
+        const bool live = b < g.B && g.active[b] && (PASS == 0 || g.need1[b]);   // uniform over the block
         if (!live) continue;
         const double lim = PASS == 1 ? g.dmin[b] + kTie : 0.0;
         double best = INFINITY;
         unsigned long long key = ~0ull;
+        double dEv[16];
         const int a = i0 + ii;
         const int sa = spI[c][ii];
-        for (int jj = jq; jj < jq + 16; ++jj) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int jj = jq + u;
             const int bb = j0 + jj;
+            dEv[u] = INFINITY;
             if (!(a < bb) || clI[ii] != clJ[jj]) continue;
             const int sb = spJ[c][jj];
             if (sa == sb || sa < 0 || sb < 0) continue;
-            const double d = __dsub_rn(g.z[sb], g.z[sa]);
-            const double dE = pair_dE(d, phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj], Jt[ii][jj]);
+            double dE;
+            if (table) {
+                dE = pair_dE_c(c1t[sa * g.S + sb], c2t[sa * g.S + sb], phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj],
+                               Jt[ii][jj]);
+            } else {
+                const double d = __dsub_rn(g.z[sb], g.z[sa]);
+                dE = pair_dE_c(__dmul_rn(2.0, d), __dmul_rn(d, d), phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj],
+                               Jt[ii][jj]);
+            }
+            dEv[u] = dE;
             if (PASS == 0) {
                 if (dE < best) best = dE;
             } else if (dE <= lim) {
@@ -110,6 +158,7 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
         }
         redv[threadIdx.x] = best;
         redk[threadIdx.x] = key;
+        if (PASS == 0 && threadIdx.x == 0) tn = 0;
         __syncthreads();
         for (int w = 128; w; w >>= 1) {
             if (threadIdx.x < w) {
@@ -118,9 +167,32 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
             }
             __syncthreads();
         }
+        if (PASS == 0) {
+            // the tile's tie set: its pairs within kTie of the tile minimum (order of the list does not matter)
+            const double tlim = redv[0] + kTie;
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (dEv[u] <= tlim) {
+                    const int slot = atomicAdd(&tn, 1);
+                    if (slot < GK) {
+                        tv[slot] = dEv[u];
+                        tk[slot] = (unsigned long long)a * (unsigned long long)g.Nv + (unsigned long long)(j0 + jq + u);
+                    }
+                }
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
-            if (PASS == 0) g.cand_val[(long)blockIdx.x * g.B + b] = redv[0];
-            else g.cand_key[(long)blockIdx.x * g.B + b] = redk[0];
+            const long o = (long)blockIdx.x * g.B + b;
+            if (PASS == 0) {
+                g.cand_val[o] = redv[0];
+                g.tie_n[o] = tn;
+                for (int k = 0; k < GK && k < tn; ++k) {
+                    g.tie_val[o * GK + k] = tv[k];
+                    g.tie_key[o * GK + k] = tk[k];
+                }
+            } else {
+                g.cand_key[o] = redk[0];
+            }
         }
         __syncthreads();
     }
@@ -131,7 +203,8 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
 template <int PASS>
 __global__ void k_gd_apply(GdArgs g, const double* __restrict__ Jfull, int8_t* __restrict__ species,
                            double* __restrict__ phi, int* __restrict__ active, double* __restrict__ dmin,
-                           double* __restrict__ E, long long* __restrict__ steps, int* __restrict__ n_active)
+                           double* __restrict__ E, long long* __restrict__ steps, int* __restrict__ n_active,
+                           int* __restrict__ need1, unsigned long long* __restrict__ chosen)
 {
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -140,16 +213,37 @@ __global__ void k_gd_apply(GdArgs g, const double* __restrict__ Jfull, int8_t* _
         double m = INFINITY;
         for (int t = lane; t < g.ntiles; t += 32) m = fmin(m, g.cand_val[(long)t * g.B + b]);
         for (int o = 16; o; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // the lowest eligible pair from the tie sets of the tiles whose minimum is within kTie of m
+        const double lim = m + kTie;
+        unsigned long long k = ~0ull;
+        int over = 0;
+        for (int t = lane; t < g.ntiles; t += 32) {
+            const long o = (long)t * g.B + b;
+            if (!(g.cand_val[o] <= lim)) continue;
+            const int n = g.tie_n[o];
+            if (n > GK) over = 1;
+            for (int e = 0; e < GK && e < n; ++e)
+                if (g.tie_val[o * GK + e] <= lim) k = min(k, g.tie_key[o * GK + e]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+            over |= __shfl_xor_sync(0xffffffffu, over, o);
+        }
         if (lane == 0) {
             dmin[b] = m;
+            need1[b] = over;
+            chosen[b] = k;
             if (!(m < -kTie)) active[b] = 0;
             else atomicAdd(n_active, 1);
         }
         return;
     }
-    unsigned long long k = ~0ull;
-    for (int t = lane; t < g.ntiles; t += 32) k = min(k, g.cand_key[(long)t * g.B + b]);
-    for (int o = 16; o; o >>= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+    unsigned long long k = chosen[b];
+    if (need1[b]) {
+        k = ~0ull;
+        for (int t = lane; t < g.ntiles; t += 32) k = min(k, g.cand_key[(long)t * g.B + b]);
+        for (int o = 16; o; o >>= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+    }
     const int a = (int)(k / (unsigned long long)g.Nv), c = (int)(k % (unsigned long long)g.Nv);
     int8_t* sp = species + (long)b * g.Nv;
     double* ph = phi + (long)b * g.Nv;
@@ -191,17 +285,24 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     cudaStream_t st = ctx->stream;
     const int nb = (p->Nv + GT - 1) / GT;
     const int ntiles = nb * (nb + 1) / 2;
-    const size_t need = sizeof(double) * (size_t)B * p->Nv + sizeof(double) * (size_t)ntiles * B +
-                        sizeof(unsigned long long) * (size_t)ntiles * B + sizeof(double) * B + sizeof(int) * (B + 4) +
-                        1024;
+    const size_t tiles_b = (size_t)ntiles * B;
+    const size_t need = sizeof(double) * (size_t)B * p->Nv + sizeof(double) * tiles_b +
+                        sizeof(unsigned long long) * tiles_b + sizeof(double) * tiles_b * GK +
+                        sizeof(unsigned long long) * tiles_b * GK + sizeof(unsigned long long) * B +
+                        sizeof(double) * B + sizeof(int) * (tiles_b + 2 * (size_t)B + 4) + 1024;
     goac_status rc = goac::ensure(p->grad_tmp, need);
     if (rc) return rc;
     double* phi = (double*)p->grad_tmp.ptr;
     double* cval = phi + (size_t)B * p->Nv;
-    unsigned long long* ckey = (unsigned long long*)(cval + (size_t)ntiles * B);
-    double* dmin = (double*)(ckey + (size_t)ntiles * B);
+    unsigned long long* ckey = (unsigned long long*)(cval + tiles_b);
+    double* tval = (double*)(ckey + tiles_b);
+    unsigned long long* tkey = (unsigned long long*)(tval + tiles_b * GK);
+    unsigned long long* chosen = tkey + tiles_b * GK;
+    double* dmin = (double*)(chosen + B);
     int* active = (int*)(dmin + B);
     int* n_active = active + B;
+    int* need1 = n_active + 4;
+    int* tn = need1 + B;
     // starting potentials: exact integer-digit contraction on the tensor cores
     // when the charges admit it, else the FP64 GEMM
     rc = goac::exact_supported(p) ? goac::phi_exact(p, species_dev, B, E_dev, phi)
@@ -217,22 +318,27 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     g.z = p->z_dev;
     g.active = active;
     g.dmin = dmin;
+    g.need1 = need1;
     g.cand_val = cval;
     g.cand_key = ckey;
+    g.tie_val = tval;
+    g.tie_key = tkey;
+    g.tie_n = tn;
     g.ld = p->Nv_pad;
     g.Nv = p->Nv;
     g.B = B;
     g.ntiles = ntiles;
+    g.S = p->S;
     dim3 grid(ntiles, (B + GD_CFG - 1) / GD_CFG);
     const int ablocks = (B + 7) / 8;
     for (int s = 0; s < max_steps; ++s) {
         GOAC_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
         goac::launch(k_gd_pairs<0>, grid, 256, 0, st, g);
         goac::launch(k_gd_apply<0>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
-                     E_dev, (long long*)steps_dev, n_active);
-        goac::launch(k_gd_pairs<1>, grid, 256, 0, st, g);
+                     E_dev, (long long*)steps_dev, n_active, need1, chosen);
+        goac::launch(k_gd_pairs<1>, grid, 256, 0, st, g);      // blocks without an overflowed tie set return
         goac::launch(k_gd_apply<1>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
-                     E_dev, (long long*)steps_dev, n_active);
+                     E_dev, (long long*)steps_dev, n_active, need1, chosen);
         GOAC_LAUNCH_CHECK("gd step");
         if ((s & 7) == 7 || s + 1 == max_steps) {
             int h = 0;
