@@ -517,8 +517,10 @@ goac_status goac_energy_grad(goac_problem* prob, const float* logits_dev, int32_
  * paper's own gradient descent is discrete, SI Gradient Descent; used to     *
  * seed MC / GA populations): n_steps of L -= eta dE/dL with the gradient of  *
  * goac_energy_grad (softmax keeps p on the simplex), in place on logits_dev. *
- * dlogits_scratch_dev: caller buffer of B x Nv x S floats.  E_dev: energies   *
- * after the last step.                                                        */
+ * precision: as goac_energy_grad; with TF32X2 and F16X2 the chain-rule       *
+ * kernel applies each step itself.  dlogits_scratch_dev: caller buffer of    *
+ * B x Nv x S floats, not NULL (the F64 path's gradient).  E_dev: energies    *
+ * after the last step.                                                       */
 goac_status goac_relaxed_descent(goac_problem* prob, float* logits_dev, int32_t B, double lambda, double eta,
                                  int32_t n_steps, int32_t precision, float* dlogits_scratch_dev, double* E_dev);
 
