@@ -724,7 +724,7 @@ def run_suite(args, ctx=None, out=None):
                 res[prec]["incremental_kernel_ms"] = ik_ms / ik_n
         # R independent populations in one run: the children of all come from one launch and
         # are rescored by one call over R P configurations
-        for prec in ("f64_incr", "bf16x3"):
+        for prec in ("f64_incr", "exact", "bf16x3"):
             R_pop = 8
             popR = gp.random_configs(R_pop * 1024, 17)
             gp.ga_run_populations(popR.clone(), R_pop, 2, 20, oracle.p_mut_to_u32(0.1), 9, 0, prec)
