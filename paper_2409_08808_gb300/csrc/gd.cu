@@ -12,14 +12,18 @@
 // The pair scan is a tile computation over the upper triangle of 64 x 64
 // blocks of J_vv: each CTA stages its J tile (doubled: 2 J_ab, exact) in
 // shared memory once and evaluates it for GD_CFG configurations, with 2d and
-// d^2 taken from a per-species-pair table, so that each pair costs six FP64
-// operations with the roundings of the definition.  Pass 0 also keeps each
-// tile's tie set (its pairs within 1e-9 eV of the tile's minimum, up to GK of
-// them): the pairs eligible in pass 1 all lie in the tie sets of the tiles
-// whose minimum is within 1e-9 eV of dmin, so pass 1 runs (for that
-// configuration) only when one of those tie sets overflowed.  Per-tile
-// candidates are reduced per configuration in a fixed order.  FP64 with
-// explicitly rounded operations in the order of the definition.
+// d^2 taken from a per-species-pair table.  Pass 0 filters in FP32 and decides
+// in FP64: every pair's dE is formed in FP32 with a bound e on its distance
+// from the FP64 value (a multiple of 2^-24 of the magnitudes that enter it);
+// with U the least dE32 + e of the tile, only the pairs with dE32 - e <=
+// U + 1e-9 eV can be the tile's minimum or lie within 1e-9 eV of it, and
+// those few are evaluated again in FP64 with the definition's roundings, so
+// the tile minimum and its tie set (its pairs within 1e-9 eV of the minimum,
+// up to GK of them) are exactly those of an FP64 scan.  The pairs eligible in
+// pass 1 all lie in the tie sets of the tiles whose minimum is within 1e-9 eV
+// of dmin, so pass 1 (an FP64 scan of every pair) runs for a configuration
+// only when one of those tie sets overflowed.  Per-tile candidates are reduced
+// per configuration in a fixed order.
 #include <math.h>
 
 #include <algorithm>
@@ -66,8 +70,195 @@ __device__ __forceinline__ double pair_dE_c(double c1, double c2, double pa, dou
     return __dadd_rn(__dmul_rn(c1, __dsub_rn(pa, pb)), __dmul_rn(c2, __dsub_rn(__dadd_rn(jaa, jbb), jab2)));
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
+// Upper triangle tile t -> (row block bi, column block bj), bi <= bj.
+__device__ __forceinline__ void gd_tile(int t, int& bi, int& bj)
+{
+    bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    while (bj * (bj + 1) / 2 > t) --bj;
+    bi = t - bj * (bj + 1) / 2;
+}
+
+// Pass 0: FP32 filter, FP64 decision (see the top of the file).  Per pair the
+// FP32 value is c1 (p_a - p_b) + c2 ((j_aa + j_bb) - 2 j_ab) from FP32 copies;
+// each of its five roundings and each rounding of an input to FP32 moves it by
+// at most 2^-24 of the magnitudes involved, and the bound e = 2^-19 (|c1|
+// (|p_a| + |p_b|) + |c2| (|j_aa| + |j_bb| + |2 j_ab|)) + 2^-20 |dE32| also
+// covers the FP32 roundings of the comparisons below (the threshold carries
+// 2^-20 |U| for the same reason).
+__global__ void __launch_bounds__(256, 4) k_gd_pass0(GdArgs g)
+{
+    __shared__ float Jf[GT][GT + 1];
+    __shared__ double phI[GD_CFG][GT], phJ[GD_CFG][GT];
+    __shared__ float pfI[GD_CFG][GT], pfJ[GD_CFG][GT];
+    __shared__ int8_t spI[GD_CFG][GT], spJ[GD_CFG][GT];
+    __shared__ int clI[GT], clJ[GT];
+    __shared__ double dgI[GT], dgJ[GT];
+    __shared__ float dfI[GT], dfJ[GT];
+    __shared__ double c1t[GS * GS], c2t[GS * GS];
+    __shared__ float c1f[GS * GS], c2f[GS * GS];
+    __shared__ float redf[8];
+    __shared__ double redv[8];
+    __shared__ double tv[GK];
+    __shared__ unsigned long long tk[GK];
+    __shared__ int tn, tover;
+    const int c0 = blockIdx.y * GD_CFG;
+    int bi, bj;
+    gd_tile(blockIdx.x, bi, bj);
+    const int i0 = bi * GT, j0 = bj * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += 256) {
+        const int r = e / GT, c = e % GT;
+        Jf[r][c] = (float)(2.0 * g.J[(long)(i0 + r) * g.ld + j0 + c]);
+    }
+    const bool table = g.S <= GS;
+    if (table)
+        for (int e = threadIdx.x; e < g.S * g.S; e += 256) {
+            const double d = __dsub_rn(g.z[e % g.S], g.z[e / g.S]);     // [sa][sb]: z_sb - z_sa
+            c1t[e] = __dmul_rn(2.0, d);
+            c2t[e] = __dmul_rn(d, d);
+            c1f[e] = (float)c1t[e];
+            c2f[e] = (float)c2t[e];
+        }
+    for (int e = threadIdx.x; e < GT; e += 256) {
+        const bool vi = i0 + e < g.Nv, vj = j0 + e < g.Nv;
+        clI[e] = vi ? g.vclass[i0 + e] : -1;
+        clJ[e] = vj ? g.vclass[j0 + e] : -2;
+        dgI[e] = vi ? g.diag[i0 + e] : 0.0;
+        dgJ[e] = vj ? g.diag[j0 + e] : 0.0;
+        dfI[e] = (float)dgI[e];
+        dfJ[e] = (float)dgJ[e];
+    }
+    for (int e = threadIdx.x; e < GD_CFG * GT; e += 256) {
+        const int c = e / GT, x = e % GT, b = c0 + c;
+        const bool okb = b < g.B;
+        phI[c][x] = okb && i0 + x < g.Nv ? g.phi[(long)b * g.Nv + i0 + x] : 0.0;
+        phJ[c][x] = okb && j0 + x < g.Nv ? g.phi[(long)b * g.Nv + j0 + x] : 0.0;
+        pfI[c][x] = (float)phI[c][x];
+        pfJ[c][x] = (float)phJ[c][x];
+        spI[c][x] = okb && i0 + x < g.Nv ? g.species[(long)b * g.Nv + i0 + x] : (int8_t)-1;
+        spJ[c][x] = okb && j0 + x < g.Nv ? g.species[(long)b * g.Nv + j0 + x] : (int8_t)-1;
+    }
+    __syncthreads();
+    const int ii = threadIdx.x % GT;
+    const int jq = (threadIdx.x / GT) * 16;
+    const int a = i0 + ii;
+    for (int c = 0; c < GD_CFG; ++c) {
+        const int b = c0 + c;
+        const bool live = b < g.B && g.active[b];   // uniform over the block
+        if (!live) continue;
+        const int sa = spI[c][ii];
+        float lo[16];                              // dE32 - e (INFINITY: no pair)
+        float ub = INFINITY;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int jj = jq + u;
+            lo[u] = INFINITY;
+            if (!(a < j0 + jj) || clI[ii] != clJ[jj]) continue;
+            const int sb = spJ[c][jj];
+            if (sa == sb || sa < 0 || sb < 0) continue;
+            float x1, x2;
+            if (table) {
+                x1 = c1f[sa * g.S + sb];
+                x2 = c2f[sa * g.S + sb];
+            } else {
+                const double d = __dsub_rn(g.z[sb], g.z[sa]);
+                x1 = (float)__dmul_rn(2.0, d);
+                x2 = (float)__dmul_rn(d, d);
+            }
+            const float pa = pfI[c][ii], pb = pfJ[c][jj], ja = dfI[ii], jb = dfJ[jj], j2 = Jf[ii][jj];
+            const float v = __fadd_rn(__fmul_rn(x1, __fsub_rn(pa, pb)), __fmul_rn(x2, __fsub_rn(__fadd_rn(ja, jb), j2)));
+            const float mag = fabsf(x1) * (fabsf(pa) + fabsf(pb)) + fabsf(x2) * (fabsf(ja) + fabsf(jb) + fabsf(j2));
+            const float e = 1.9073486e-6f * mag + 9.5367432e-7f * fabsf(v) + 1e-30f;   // 2^-19, 2^-20
+            lo[u] = v - e;
+            ub = fminf(ub, v + e);
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+        if (lane == 0) redf[wid] = ub;
+        if (threadIdx.x == 0) {
+            tn = 0;
+            tover = 0;
+        }
+        __syncthreads();
+        float U = redf[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) U = fminf(U, redf[w]);
+        const float thr = U + (float)kTie + 9.5367432e-7f * fabsf(U);
+        // the candidates, in FP64 as the definition rounds them; a thread keeps its lowest two
+        double cmin = INFINITY, v1 = INFINITY, v2 = INFINITY;
+        unsigned long long k1 = ~0ull, k2 = ~0ull;
+        int ncand = 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            if (!(lo[u] <= thr)) continue;         // no pair: INFINITY (U is finite when a pair exists)
+            const int jj = jq + u;
+            const int sb = spJ[c][jj];
+            double x1, x2;
+            if (table) {
+                x1 = c1t[sa * g.S + sb];
+                x2 = c2t[sa * g.S + sb];
+            } else {
+                const double d = __dsub_rn(g.z[sb], g.z[sa]);
+                x1 = __dmul_rn(2.0, d);
+                x2 = __dmul_rn(d, d);
+            }
+            const double jab2 = 2.0 * g.J[(long)a * g.ld + j0 + jj];
+            const double v = pair_dE_c(x1, x2, phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj], jab2);
+            const unsigned long long k = (unsigned long long)a * (unsigned long long)g.Nv + (unsigned long long)(j0 + jj);
+            ++ncand;
+            cmin = fmin(cmin, v);
+            if (v < v1) {
+                v2 = v1;
+                k2 = k1;
+                v1 = v;
+                k1 = k;
+            } else if (v < v2) {
+                v2 = v;
+                k2 = k;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cmin = fmin(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+        if (lane == 0) redv[wid] = cmin;
+        __syncthreads();
+        double tmin = redv[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) tmin = fmin(tmin, redv[w]);
+        const double tlim = tmin + kTie;             // the tile's exact minimum + the tie
+        if (ncand > 2 && v2 <= tlim) atomicOr(&tover, 1);   // a third could be in the tie set too
+        if (v1 <= tlim) {
+            const int slot = atomicAdd(&tn, 1);
+            if (slot < GK) {
+                tv[slot] = v1;
+                tk[slot] = k1;
+            }
+        }
+        if (v2 <= tlim) {
+            const int slot = atomicAdd(&tn, 1);
+            if (slot < GK) {
+                tv[slot] = v2;
+                tk[slot] = k2;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long o = (long)blockIdx.x * g.B + b;
+            g.cand_val[o] = tmin;
+            g.tie_n[o] = tover ? GK + 1 : tn;
+            for (int k = 0; k < GK && k < tn; ++k) {
+                g.tie_val[o * GK + k] = tv[k];
+                g.tie_key[o * GK + k] = tk[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 1, for the configurations whose relevant tie set overflowed: every
+// pair in FP64 with the definition's roundings; per tile the lowest pair key
+// (a Nv + b) with dE <= dmin + 1e-9 eV.
+__global__ void __launch_bounds__(256) k_gd_pass1(GdArgs g)
 {
     __shared__ double Jt[GT][GT + 1];
     __shared__ double phI[GD_CFG][GT], phJ[GD_CFG][GT];
@@ -75,22 +266,13 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
     __shared__ int clI[GT], clJ[GT];
     __shared__ double dgI[GT], dgJ[GT];
     __shared__ double c1t[GS * GS], c2t[GS * GS];
-    __shared__ double redv[256];
     __shared__ unsigned long long redk[256];
-    __shared__ double tv[GK];
-    __shared__ unsigned long long tk[GK];
-    __shared__ int tn;
     const int c0 = blockIdx.y * GD_CFG;
-    if (PASS == 1) {            // only the configurations whose tie sets overflowed
-        bool any = false;
-        for (int c = 0; c < GD_CFG; ++c) any |= c0 + c < g.B && g.active[c0 + c] && g.need1[c0 + c];
-        if (!any) return;       // uniform over the block
-    }
-    int t = blockIdx.x;
-    int bj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-    while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
-    while (bj * (bj + 1) / 2 > t) --bj;
-    const int bi = t - bj * (bj + 1) / 2;
+    bool any = false;
+    for (int c = 0; c < GD_CFG; ++c) any |= c0 + c < g.B && g.active[c0 + c] && g.need1[c0 + c];
+    if (!any) return;           // uniform over the block
+    int bi, bj;
+    gd_tile(blockIdx.x, bi, bj);
     const int i0 = bi * GT, j0 = bj * GT;
     for (int e = threadIdx.x; e < GT * GT; e += 256) {
         const int r = e / GT, c = e % GT;
@@ -123,77 +305,39 @@ __global__ void __launch_bounds__(256) k_gd_pairs(GdArgs g)
     const int jq = (threadIdx.x / GT) * 16;
     for (int c = 0; c < GD_CFG; ++c) {
         const int b = c0 + c;
-        const bool live = b < g.B && g.active[b] && (PASS == 0 || g.need1[b]);   // uniform over the block
+        const bool live = b < g.B && g.active[b] && g.need1[b];   // uniform over the block
         if (!live) continue;
-        const double lim = PASS == 1 ? g.dmin[b] + kTie : 0.0;
-        double best = INFINITY;
+        const double lim = g.dmin[b] + kTie;
         unsigned long long key = ~0ull;
-        double dEv[16];
         const int a = i0 + ii;
         const int sa = spI[c][ii];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int jj = jq + u;
+        for (int jj = jq; jj < jq + 16; ++jj) {
             const int bb = j0 + jj;
-            dEv[u] = INFINITY;
             if (!(a < bb) || clI[ii] != clJ[jj]) continue;
             const int sb = spJ[c][jj];
             if (sa == sb || sa < 0 || sb < 0) continue;
-            double dE;
+            double x1, x2;
             if (table) {
-                dE = pair_dE_c(c1t[sa * g.S + sb], c2t[sa * g.S + sb], phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj],
-                               Jt[ii][jj]);
+                x1 = c1t[sa * g.S + sb];
+                x2 = c2t[sa * g.S + sb];
             } else {
                 const double d = __dsub_rn(g.z[sb], g.z[sa]);
-                dE = pair_dE_c(__dmul_rn(2.0, d), __dmul_rn(d, d), phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj],
-                               Jt[ii][jj]);
+                x1 = __dmul_rn(2.0, d);
+                x2 = __dmul_rn(d, d);
             }
-            dEv[u] = dE;
-            if (PASS == 0) {
-                if (dE < best) best = dE;
-            } else if (dE <= lim) {
+            const double dE = pair_dE_c(x1, x2, phI[c][ii], phJ[c][jj], dgI[ii], dgJ[jj], Jt[ii][jj]);
+            if (dE <= lim) {
                 const unsigned long long k = (unsigned long long)a * (unsigned long long)g.Nv + (unsigned long long)bb;
                 if (k < key) key = k;
             }
         }
-        redv[threadIdx.x] = best;
         redk[threadIdx.x] = key;
-        if (PASS == 0 && threadIdx.x == 0) tn = 0;
         __syncthreads();
         for (int w = 128; w; w >>= 1) {
-            if (threadIdx.x < w) {
-                redv[threadIdx.x] = fmin(redv[threadIdx.x], redv[threadIdx.x + w]);
-                redk[threadIdx.x] = min(redk[threadIdx.x], redk[threadIdx.x + w]);
-            }
+            if (threadIdx.x < w) redk[threadIdx.x] = min(redk[threadIdx.x], redk[threadIdx.x + w]);
             __syncthreads();
         }
-        if (PASS == 0) {
-            // the tile's tie set: its pairs within kTie of the tile minimum (order of the list does not matter)
-            const double tlim = redv[0] + kTie;
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                if (dEv[u] <= tlim) {
-                    const int slot = atomicAdd(&tn, 1);
-                    if (slot < GK) {
-                        tv[slot] = dEv[u];
-                        tk[slot] = (unsigned long long)a * (unsigned long long)g.Nv + (unsigned long long)(j0 + jq + u);
-                    }
-                }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const long o = (long)blockIdx.x * g.B + b;
-            if (PASS == 0) {
-                g.cand_val[o] = redv[0];
-                g.tie_n[o] = tn;
-                for (int k = 0; k < GK && k < tn; ++k) {
-                    g.tie_val[o * GK + k] = tv[k];
-                    g.tie_key[o * GK + k] = tk[k];
-                }
-            } else {
-                g.cand_key[o] = redk[0];
-            }
-        }
+        if (threadIdx.x == 0) g.cand_key[(long)blockIdx.x * g.B + b] = redk[0];
         __syncthreads();
     }
 }
@@ -333,10 +477,10 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     const int ablocks = (B + 7) / 8;
     for (int s = 0; s < max_steps; ++s) {
         GOAC_CUDA(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-        goac::launch(k_gd_pairs<0>, grid, 256, 0, st, g);
+        goac::launch(k_gd_pass0, grid, 256, 0, st, g);
         goac::launch(k_gd_apply<0>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
                      E_dev, (long long*)steps_dev, n_active, need1, chosen);
-        goac::launch(k_gd_pairs<1>, grid, 256, 0, st, g);      // blocks without an overflowed tie set return
+        goac::launch(k_gd_pass1, grid, 256, 0, st, g);         // blocks without an overflowed tie set return
         goac::launch(k_gd_apply<1>, ablocks, 256, 0, st, g, (const double*)p->J_vv, species_dev, phi, active, dmin,
                      E_dev, (long long*)steps_dev, n_active, need1, chosen);
         GOAC_LAUNCH_CHECK("gd step");
