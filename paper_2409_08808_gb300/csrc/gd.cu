@@ -53,8 +53,27 @@ struct GdArgs {
     double* tie_val;          // ntiles x B x GK: tie-set energies (pass 0)
     unsigned long long* tie_key;    // ntiles x B x GK: tie-set pair keys a Nv + b
     int* tie_n;               // ntiles x B: tie-set size (> GK: overflow)
+    const float* J2f;         // Nv_pad x ld: 2 J_vv rounded to FP32 (pass 0's filter)
+    const float* diagf;       // Nv: diag rounded to FP32
+    float* phif;              // B x Nv: phi rounded to FP32, kept beside phi
     int ld, Nv, B, ntiles, S;
 };
+
+// FP32 copies for the filter of pass 0: 2 J (once per run) and the diagonal.
+__global__ void k_gd_f32_consts(const double* __restrict__ J, long n, const double* __restrict__ diag, int Nv,
+                                float* __restrict__ J2f, float* __restrict__ diagf)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        J2f[e] = (float)(2.0 * J[e]);
+        if (e < Nv) diagf[e] = (float)diag[e];
+    }
+}
+
+__global__ void k_gd_f32_phi(const double* __restrict__ phi, long n, float* __restrict__ phif)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        phif[e] = (float)phi[e];
+}
 
 __device__ __forceinline__ double pair_dE(double d, double pa, double pb, double jaa, double jbb, double jab)
 {
@@ -106,9 +125,11 @@ __global__ void __launch_bounds__(256, 4) k_gd_pass0(GdArgs g)
     int bi, bj;
     gd_tile(blockIdx.x, bi, bj);
     const int i0 = bi * GT, j0 = bj * GT;
+    // FP32 copies staged as they are (FP64 to FP32 conversions run on GB300's FP64 pipe);
+    // the FP64 values only for the candidates
     for (int e = threadIdx.x; e < GT * GT; e += 256) {
         const int r = e / GT, c = e % GT;
-        Jf[r][c] = (float)(2.0 * g.J[(long)(i0 + r) * g.ld + j0 + c]);
+        Jf[r][c] = g.J2f[(long)(i0 + r) * g.ld + j0 + c];
     }
     const bool table = g.S <= GS;
     if (table)
@@ -125,18 +146,19 @@ __global__ void __launch_bounds__(256, 4) k_gd_pass0(GdArgs g)
         clJ[e] = vj ? g.vclass[j0 + e] : -2;
         dgI[e] = vi ? g.diag[i0 + e] : 0.0;
         dgJ[e] = vj ? g.diag[j0 + e] : 0.0;
-        dfI[e] = (float)dgI[e];
-        dfJ[e] = (float)dgJ[e];
+        dfI[e] = vi ? g.diagf[i0 + e] : 0.0f;
+        dfJ[e] = vj ? g.diagf[j0 + e] : 0.0f;
     }
     for (int e = threadIdx.x; e < GD_CFG * GT; e += 256) {
         const int c = e / GT, x = e % GT, b = c0 + c;
         const bool okb = b < g.B;
-        phI[c][x] = okb && i0 + x < g.Nv ? g.phi[(long)b * g.Nv + i0 + x] : 0.0;
-        phJ[c][x] = okb && j0 + x < g.Nv ? g.phi[(long)b * g.Nv + j0 + x] : 0.0;
-        pfI[c][x] = (float)phI[c][x];
-        pfJ[c][x] = (float)phJ[c][x];
-        spI[c][x] = okb && i0 + x < g.Nv ? g.species[(long)b * g.Nv + i0 + x] : (int8_t)-1;
-        spJ[c][x] = okb && j0 + x < g.Nv ? g.species[(long)b * g.Nv + j0 + x] : (int8_t)-1;
+        const bool vi = okb && i0 + x < g.Nv, vj = okb && j0 + x < g.Nv;
+        phI[c][x] = vi ? g.phi[(long)b * g.Nv + i0 + x] : 0.0;
+        phJ[c][x] = vj ? g.phi[(long)b * g.Nv + j0 + x] : 0.0;
+        pfI[c][x] = vi ? g.phif[(long)b * g.Nv + i0 + x] : 0.0f;
+        pfJ[c][x] = vj ? g.phif[(long)b * g.Nv + j0 + x] : 0.0f;
+        spI[c][x] = vi ? g.species[(long)b * g.Nv + i0 + x] : (int8_t)-1;
+        spJ[c][x] = vj ? g.species[(long)b * g.Nv + j0 + x] : (int8_t)-1;
     }
     __syncthreads();
     const int ii = threadIdx.x % GT;
@@ -397,7 +419,12 @@ __global__ void k_gd_apply(GdArgs g, const double* __restrict__ Jfull, int8_t* _
     __syncwarp();
     const double* ra = Jfull + (long)a * g.ld;
     const double* rc = Jfull + (long)c * g.ld;
-    for (int w = lane; w < g.Nv; w += 32) ph[w] = __dadd_rn(ph[w], __dmul_rn(d, __dsub_rn(ra[w], rc[w])));
+    float* pf = g.phif + (long)b * g.Nv;
+    for (int w = lane; w < g.Nv; w += 32) {
+        const double v = __dadd_rn(ph[w], __dmul_rn(d, __dsub_rn(ra[w], rc[w])));
+        ph[w] = v;
+        pf[w] = (float)v;
+    }
     __syncwarp();
     if (lane == 0) {
         sp[a] = (int8_t)sc;
@@ -430,10 +457,12 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     const int nb = (p->Nv + GT - 1) / GT;
     const int ntiles = nb * (nb + 1) / 2;
     const size_t tiles_b = (size_t)ntiles * B;
+    const size_t nJ = (size_t)p->Nv_pad * p->Nv_pad;
     const size_t need = sizeof(double) * (size_t)B * p->Nv + sizeof(double) * tiles_b +
                         sizeof(unsigned long long) * tiles_b + sizeof(double) * tiles_b * GK +
                         sizeof(unsigned long long) * tiles_b * GK + sizeof(unsigned long long) * B +
-                        sizeof(double) * B + sizeof(int) * (tiles_b + 2 * (size_t)B + 4) + 1024;
+                        sizeof(double) * B + sizeof(int) * (tiles_b + 2 * (size_t)B + 4) +
+                        sizeof(float) * (nJ + (size_t)p->Nv + (size_t)B * p->Nv) + 4096;
     goac_status rc = goac::ensure(p->grad_tmp, need);
     if (rc) return rc;
     double* phi = (double*)p->grad_tmp.ptr;
@@ -447,12 +476,19 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     int* n_active = active + B;
     int* need1 = n_active + 4;
     int* tn = need1 + B;
+    float* J2f = (float*)(((uintptr_t)(tn + tiles_b) + 255) & ~(uintptr_t)255);
+    float* diagf = J2f + nJ;
+    float* phif = diagf + p->Nv;
     // starting potentials: exact integer-digit contraction on the tensor cores
     // when the charges admit it, else the FP64 GEMM
     rc = goac::exact_supported(p) ? goac::phi_exact(p, species_dev, B, E_dev, phi)
                                   : goac::score_f64(p, species_dev, B, E_dev, phi);
     if (rc) return rc;
     goac::launch(k_gd_init, (B + 255) / 256, 256, 0, st, B, active, (long long*)steps_dev);
+    goac::launch(k_gd_f32_consts, (int)std::min<size_t>((nJ + 255) / 256, 65535 * 4), 256, 0, st,
+                 (const double*)p->J_vv, (long)nJ, (const double*)p->diag, p->Nv, J2f, diagf);
+    goac::launch(k_gd_f32_phi, (int)std::min<size_t>(((size_t)B * p->Nv + 255) / 256, 65535 * 4), 256, 0, st,
+                 (const double*)phi, (long)B * p->Nv, phif);
     GdArgs g;
     g.J = p->J_vv;
     g.diag = p->diag;
@@ -468,6 +504,9 @@ extern "C" goac_status goac_gd_run(goac_problem* p, int8_t* species_dev, int32_t
     g.tie_val = tval;
     g.tie_key = tkey;
     g.tie_n = tn;
+    g.J2f = J2f;
+    g.diagf = diagf;
+    g.phif = phif;
     g.ld = p->Nv_pad;
     g.Nv = p->Nv;
     g.B = B;
