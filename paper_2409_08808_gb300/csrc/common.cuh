@@ -112,6 +112,7 @@ struct goac_problem {
     double* J_vv = nullptr;    // Nv_pad x Nv_pad FP64, zero padded
     double* diag = nullptr;    // Nv   (J_vv diagonal)
     double* phifix = nullptr;  // Nv_pad (zero padded)
+    float* phifix_f32 = nullptr;  // Nv_pad, phifix rounded to FP32 (relaxed-gradient chain rule)
     double* z_dev = nullptr;   // S
     int32_t* vclass_dev = nullptr;
     int32_t* cls_start_dev = nullptr;

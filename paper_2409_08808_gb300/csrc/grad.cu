@@ -388,13 +388,15 @@ __global__ void __launch_bounds__(RV_T) k_relax_prep_v4(const float* __restrict_
                                                       float qscale)
 {
     __shared__ int cnt[RV_KS];
+    __shared__ float zs[S];
     __shared__ double wsum[RV_T / 32][RV_KS];
     const int nks = ncls * S;
     if (threadIdx.x < nks) cnt[threadIdx.x] = counts[threadIdx.x];
+    if (threadIdx.x < S) zs[threadIdx.x] = (float)z[threadIdx.x];   // once per block: conversions use the FP64 pipe
     __syncthreads();
     float zf[S];
 #pragma unroll
-    for (int t = 0; t < S; ++t) zf[t] = (float)z[t];
+    for (int t = 0; t < S; ++t) zf[t] = zs[t];
     const int c = blockIdx.x % nch, b = blockIdx.x / nch;
     const int v0 = c * RV_C + threadIdx.x * RV_G;
     const int nv = max(0, min(RV_G, Nv - v0));
@@ -513,7 +515,7 @@ __global__ void __launch_bounds__(RV_T) k_relax_prep_v4(const float* __restrict_
 // 2 phi_fix_v) goes to epart[b nch + c] (FP64, fixed order).
 template <int S>
 __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict__ p, const float* __restrict__ Phi,
-                                                       long phi_ld, const double* __restrict__ phifix,
+                                                       long phi_ld, const float* __restrict__ phifixf,
                                                        const double* __restrict__ cpart, int nch,
                                                        const int32_t* __restrict__ vclass,
                                                        const int32_t* __restrict__ counts,
@@ -523,6 +525,7 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
 {
     __shared__ float pen[RV_KS];
     __shared__ int cnt[RV_KS];
+    __shared__ float zs[S];
     __shared__ double red[RV_T / 32];
     const int c = blockIdx.x % nch, b = blockIdx.x / nch;
     const int nks = ncls * S;
@@ -532,10 +535,11 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
         cnt[threadIdx.x] = counts[threadIdx.x];
         pen[threadIdx.x] = (float)(2.0 * lambda * (a - counts[threadIdx.x]));
     }
+    if (threadIdx.x < S) zs[threadIdx.x] = (float)z[threadIdx.x];   // once per block: conversions use the FP64 pipe
     __syncthreads();
     float zf[S];
 #pragma unroll
-    for (int t = 0; t < S; ++t) zf[t] = (float)z[t];
+    for (int t = 0; t < S; ++t) zf[t] = zs[t];
     const int v0 = c * RV_C + threadIdx.x * RV_G;
     const int nv = max(0, min(RV_G, Nv - v0));
     const long t0 = (long)b * Nv + v0;
@@ -557,12 +561,11 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
         phi[1] = f.y;
         phi[2] = f.z;
         phi[3] = f.w;
-        const double2 d0 = *reinterpret_cast<const double2*>(phifix + v0);
-        const double2 d1 = *reinterpret_cast<const double2*>(phifix + v0 + 2);
-        pf[0] = (float)d0.x;
-        pf[1] = (float)d0.y;
-        pf[2] = (float)d1.x;
-        pf[3] = (float)d1.y;
+        const float4 f4 = *reinterpret_cast<const float4*>(phifixf + v0);
+        pf[0] = f4.x;
+        pf[1] = f4.y;
+        pf[2] = f4.z;
+        pf[3] = f4.w;
         const int4 k4 = *reinterpret_cast<const int4*>(vclass + v0);
         kc[0] = k4.x;
         kc[1] = k4.y;
@@ -574,11 +577,13 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
 #pragma unroll
         for (int g = 0; g < RV_G; ++g) {
             phi[g] = g < nv ? Phi[(long)b * phi_ld + v0 + g] : 0.0f;
-            pf[g] = g < nv ? (float)phifix[v0 + g] : 0.0f;
+            pf[g] = g < nv ? phifixf[v0 + g] : 0.0f;
             kc[g] = g < nv ? vclass[v0 + g] : -1;
         }
     }
-    double acc = 0.0;
+    // the four sites' energy terms summed in FP32, the threads' sums in FP64 (conversions and FP64
+    // additions run on GB300's narrow FP64 pipe: one per thread, not one per site)
+    float accf = 0.0f;
     const bool grad = dlogits || logits_upd;
     float G[RV_G * S];
 #pragma unroll
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
         float q = 0.0f;
 #pragma unroll
         for (int t = 0; t < S; ++t) q = fmaf(P[g * S + t], zf[t], q);
-        acc += (double)(q * (phi[g] + 2.0f * pf[g]));
+        accf += q * (phi[g] + 2.0f * pf[g]);
         const int k = kc[g] < 0 ? 0 : kc[g];
         const float jq = phi[g] + pf[g];           // (J q)_v over all sites
         float pg = 0.0f;
@@ -624,6 +629,7 @@ __global__ void __launch_bounds__(RV_T) k_grad_finish_v4(const float* __restrict
             }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = (double)accf;
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
@@ -676,9 +682,16 @@ void launch_finish_v4(int B, int Nv, int nch, int ld, const goac_problem* p, con
                       const double* cpart, double* epart, double lambda, float* dlogits, float* logits_upd, float eta,
                       cudaStream_t st)
 {
-    goac::launch(k_grad_finish_v4<S>, B * nch, RV_T, 0, st, P32, Phi, (long)ld, (const double*)p->phifix, cpart, nch,
+    goac::launch(k_grad_finish_v4<S>, B * nch, RV_T, 0, st, P32, Phi, (long)ld, (const float*)p->phifix_f32, cpart, nch,
                  (const int32_t*)p->vclass_dev, (const int32_t*)p->counts_dev, (const double*)p->z_dev, Nv, p->ncls,
                  lambda, epart, dlogits, logits_upd, eta);
+}
+
+// out = (float) in.
+__global__ void k_to_f32(const double* __restrict__ in, long n, float* __restrict__ out)
+{
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        out[e] = (float)in[e];
 }
 
 // L -= eta * dL (FP32, in place).
@@ -841,6 +854,10 @@ static goac_status energy_grad_impl(goac_problem* p, const float* logits_dev, in
         void* qt2 = qt2f;                                       // FP32 planes, or FP16 planes in their front half
         float* Phi = qt2f + 2 * (size_t)Bpad * ld;
         const long plane = (long)Bpad * ld;
+        if (vec && !p->phifix_f32) {
+            GOAC_CUDA(cudaMalloc(&p->phifix_f32, sizeof(float) * (size_t)ld));
+            goac::launch(k_to_f32, (ld + 255) / 256, 256, 0, st, (const double*)p->phifix, (long)ld, p->phifix_f32);
+        }
         if (vec) {
             if (Bpad > B) {
                 uint8_t* q8 = (uint8_t*)qt2;

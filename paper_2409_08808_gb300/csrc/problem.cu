@@ -959,6 +959,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->J_tf32);
     cudaFree(p->J_tf32_full);
     cudaFree(p->J_f16_full);
+    cudaFree(p->phifix_f32);
     cudaFree(p->f16_exp);
     cudaFree(p->J_f32);
     cudaFree(p->diag_f32);
