@@ -599,8 +599,9 @@ __global__ void __launch_bounds__(192, SPLIT ? 1 : 2)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int STAGE = A_TILE + TN * ROW_BYTES;
+    constexpr int STAGE = ExCfg<TN>::STAGE;
     constexpr int STAGES = ExCfg<TN>::STAGES;
+    static_assert(STAGES * STAGE + 1024 + 256 <= ExCfg<TN>::SMEM, "stages exceed the dynamic shared memory");
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;           // [2] accumulator ready
