@@ -258,6 +258,9 @@ def _kernel_hash(form="bf16x2") -> str:
     src = open(os.path.join(csrc, "score_tc.cu")).read()
     if form == "exact_pair":
         a = src.index("template <bool SPLIT>\n__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
+        b = src.index("// Exact form with the configurations on the tensor-memory lanes")
+    elif form == "exact_ct":
+        a = src.index("// Exact form with the configurations on the tensor-memory lanes")
         b = src.index("// Per 128-row panel I of the symmetric operand")
     elif form == "exact":
         a = src.index("template <int TN, bool SPLIT>\n__global__ void __launch_bounds__(192, SPLIT ? 1 : 2)\n    k_score_exact(")
@@ -327,26 +330,31 @@ def _exact_split(info, z, N):
     return not (32.0 * qmax * qmax * 2.0 ** (r - 1) * (((N + 127) // 128) * 128) < 2.0 ** 31)
 
 
-def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128, split=True):
+def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128, split=True, tile_n=256):
     ld = ((N + 127) // 128) * 128
     bpad = ((B + 255) // 256) * 256
     nbm = ld // 128
-    pair = form == "exact" and tile_m == 256
+    pair = form == "exact" and tile_m == 256 and tile_n == 256
+    ct = form == "exact" and tile_m == 256 and tile_n == 128
     # upper block triangle of the symmetric operand: m-block I runs over columns 128 I .. ld; on CTA pairs
-    # both panels of pair-panel P run from column 256 P (one block of zeros for the odd panel)
+    # both panels of pair-panel P run from column 256 P (one block of zeros for the odd panel); the
+    # configuration-lane kernel skips that block and covers the configurations in blocks of 128
     blocks = (sum(min(2, nbm - 2 * P) * (nbm - 2 * P) for P in range((nbm + 1) // 2)) if pair
               else nbm * (nbm + 1) // 2)
-    flops_exec = terms * 2.0 * 128 * 128 * blocks * bpad
+    ncfg = ((B + 127) // 128) * 128 if ct else bpad
+    flops_exec = terms * 2.0 * 128 * 128 * blocks * ncfg
     flops_useful = 2.0 * N * N * B
     bf16_peak, _, peak_kind = _peaks()
     tf32 = "tf32" in form
     peak = bf16_peak / 2.0 if tf32 else bf16_peak     # TF32 runs at half the BF16 rate; FP16 = BF16
     achieved = flops_exec / (kern_ms / 1e3) / 1e12
     kernel = (f"k_score_exact_pair<{str(split).lower()}>" if pair else
+              f"k_score_exact_ct<{str(split).lower()}>" if ct else
               f"k_score_exact<256, {str(split).lower()}>") if form == "exact" else \
         f"k_score_tc<{terms},{'true' if tf32 else 'false'},256>"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": _traffic("exact_pair" if pair else form), "kernel": kernel, "kernel_ms": kern_ms,
+            "traffic": _traffic("exact_pair" if pair else "exact_ct" if ct else form), "kernel": kernel,
+            "kernel_ms": kern_ms,
             "kernel_timing": f"CUDA events around each launch, a second loop of {kern_n} steps (L2 flushed "
                              f"between steps)",
             "flops_per_launch": flops_exec, "useful_flops_per_launch": flops_useful,
@@ -424,7 +432,7 @@ def run_ours(args, world, rank, local):
     # per-kernel CUDA events around the scoring kernel
     kern_ms, kern_n = _kernel_ms(ctx, gp, pop, form, min(args.steps, 400), flush, E)
     split = _exact_split(info, prob.z, prob.N)
-    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP, shapes[form][0], split)
+    roofline = _roofline(form, terms[form], kern_ms, kern_n, prob.N, B_POP, shapes[form][0], split, shapes[form][1])
 
     # the other form (BF16x2 beside the FP64-grade headline): same timing, own roofline
     o_ms, _ = _time_form(gp, pop, other, min(args.steps, 400), flush, E)
@@ -594,14 +602,16 @@ def run_ours(args, world, rank, local):
                            "tile_shape": {"sites": shapes[form][0], "configurations": shapes[form][1],
                                           "k_chunk_blocks": shapes[form][2],
                                           "chosen_by": "fixed (--tile)" if form in fixed else
-                                          "goac_score_autotune (CUDA events over 15 shapes)"},
+                                          f"goac_score_autotune (CUDA events over "
+                                          f"{(4 if form == 'exact' else 2) * sum(k < (prob.N + 127) // 128 for k in (0, 16, 8, 4, 2))} shapes)"},
                            "l2": "256 MB buffer written between steps (outside the step events)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk,
                 "energy_error_vs_fp64": err_vs_fp64(E_form),
                 other: {"value": world * B_POP / (o_ms / 1e3), "unit": "evals/s", "ms_per_step": o_ms,
-                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP, shapes[other][0], split),
+                        "roofline": _roofline(other, terms[other], o_kms, o_kn, prob.N, B_POP, shapes[other][0], split,
+                                              shapes[other][1]),
                         "tile_shape": {"sites": shapes[other][0], "configurations": shapes[other][1],
                                        "k_chunk_blocks": shapes[other][2]},
                         "energy_error_vs_fp64": err_vs_fp64(E_other), "speedup_over_fp64_path": f64_ms / o_ms},

@@ -130,6 +130,7 @@ struct goac_problem {
     float* diag_f32 = nullptr;
     // scoring scratch
     DevBuf qt, partial, phi, score_tmp, topk_tmp, grad_tmp;
+    DevBuf qi;                 // exact form: integer charges beside Q^T (int8, or int16 when the digit sums split)
     DevBuf ga_incr;            // incremental GA rescoring: 2 x P x Nv potentials, P x 2 parents
     DevBuf ga_buf;             // GA: second population buffer, fitness sums, elite, stop states, parents
     DevBuf ga_dev;             // GA: device copy of the population entries

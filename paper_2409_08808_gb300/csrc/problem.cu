@@ -964,6 +964,7 @@ extern "C" goac_status goac_problem_destroy(goac_problem* p)
     cudaFree(p->J_f32);
     cudaFree(p->diag_f32);
     free_buf(p->qt);
+    free_buf(p->qi);
     free_buf(p->partial);
     free_buf(p->phi);
     free_buf(p->score_tmp);

@@ -809,23 +809,43 @@ __global__ void __launch_bounds__(192, SPLIT ? 1 : 2)
 }
 
 // Exact form on CTA pairs (tcgen05 cta_group::2): a cluster of two CTAs on
-// one TPC computes a tile of 256 sites (panels 2P in the even CTA, 2P + 1 in
-// the odd one) x 256 configurations with M = 256 MMAs issued by the even CTA.
-// Each CTA loads its own panel's digit rows and half of the configuration
-// tile's Q rows (128 each), so per MMA a CTA's shared memory takes in 8 KB
-// and serves 12 KB (its A rows, and its Q rows to both tensor cores) instead of
-// 12 + 12 KB: the same traffic per tensor-core cycle as the two-term BF16
-// kernel.  Pair-panel P covers columns from 256 P, so panel 2P + 1 multiplies
-// one 128 x 128 block of zeros (below the diagonal of the symmetric operand).
+// one TPC computes a tile of 256 configurations (128 on each CTA's tensor-
+// memory lanes) x one pair-panel of 256 sites (the rows 256 P .. 256 P + 255
+// of digit t of J': panels 2P and 2P + 1) with M = 256 MMAs issued by the even
+// CTA.  Each CTA loads its own 128 configurations' rows of Q^T (the M half)
+// and its panel's 128 digit rows (the N half), 16 KB each per k-block, so a
+// CTA's shared memory takes in 32 KB per k-block where the one-CTA kernels
+// take 48 KB, and six stages fit where those fit four.  The accumulator row of
+// configuration b holds Phi_t,ib for the pair-panel's 256 sites, and the
+// epilogue thread that owns it forms P_t,I,b = sum_i q_bi Phi_t,ib over each
+// panel's 128 sites by itself, from an int8 copy of Q^T (int16 when the digit
+// sums split) that k_make_qt writes beside the FP16 operand: no cross-lane
+// reduction and no shared memory.  Each 32-site chunk of products is summed in
+// int32 under the same host bound as the one-CTA kernel (32 max|q a| < 2^31),
+// the chunks in 64 bits; the split case sums the products in 64 bits directly.
+// Pair-panel P covers columns from 256 P, so panel 2P + 1 multiplies one
+// 128 x 128 block of zeros (below the diagonal of the symmetric operand).
 // Barriers: the even CTA's full[s] counts both CTAs' TMA bytes (the odd CTA's
 // loads signal it through its cluster address), the MMA commits arrive on
 // empty[s] and tfull[a] of both CTAs, and the eight epilogue warps of the pair
-// arrive on the even CTA's tempty[a].  Every wait is clock-bounded as in the
-// one-CTA kernels; both CTAs meet at a cluster barrier before freeing their
-// tensor memory and exiting.
+// arrive on the even CTA's tempty[a] as soon as their accumulator rows are
+// read.  Every wait is clock-bounded as in the one-CTA kernels; both CTAs
+// meet at a cluster barrier before freeing their tensor memory and exiting.
 struct PairTile {
     int P, n, kb0, kb1, slot0, slot1, t;    // slot1 < 0: panel 2P + 1 does not exist
 };
+
+// Byte e (SPLIT: half-word e) of w, sign-extended: prmt's selector nibbles with
+// the top bit set replicate the sign of the selected byte.
+template <bool WIDE, int E>
+__device__ __forceinline__ int ct_charge(uint32_t w)
+{
+    constexpr uint32_t lo = WIDE ? 2 * E : E, hi = WIDE ? 2 * E + 1 : E;
+    constexpr uint32_t sel = lo | (WIDE ? hi << 4 : (8 | hi) << 4) | ((8 | hi) << 8) | ((8 | hi) << 12);
+    int r;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "r"(sel));
+    return r;
+}
 
 constexpr int PX_HN = 128;                              // configurations per CTA's half of the tile
 constexpr int PX_STAGE = A_TILE + PX_HN * ROW_BYTES;    // 32 KB
@@ -836,9 +856,9 @@ template <bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     k_score_exact_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const PairTile* __restrict__ work, const int* __restrict__ work_start, int ld, int T,
-                       const __half* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
+                       const void* __restrict__ qi, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
-    constexpr int TN = 256;
+    constexpr int TN = 256;                     // sites per tile: TMEM columns
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + PX_STAGES * PX_STAGE);
@@ -847,7 +867,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     uint64_t* tempty = tfull + 2;               // [2] accumulator drained (the even CTA's counts both)
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    __shared__ int red_hi[4][TN], red_lo[4][TN];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = goacd::cluster_ctarank();
@@ -887,7 +906,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             int it = 0;
             for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
                 const PairTile tile = work[wi];
-                const int m0 = (2 * tile.P + (int)rank) * TC_M, n0 = tile.n * TN + (int)rank * PX_HN;
+                // this CTA's 128 configurations (the M half) and its panel's digit rows (the N half)
+                const int q0 = tile.n * 256 + (int)rank * PX_HN, j0 = tile.t * ld + (2 * tile.P + (int)rank) * TC_M;
                 for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
                     const int s = it % PX_STAGES;
                     const uint32_t use = (uint32_t)(it / PX_STAGES);
@@ -900,8 +920,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     uint8_t* st = smem + s * PX_STAGE;
                     const uint32_t fbar = goacd::mapa_shared(goacd::smem_u32(&full[s]), 0);
                     if (rank == 0) goacd::mbar_arrive_expect_tx(&full[s], 2 * PX_STAGE);
-                    goacd::tma_load_2d_pair(st, &tmA, fbar, kb * 64, tile.t * ld + m0);
-                    goacd::tma_load_2d_pair(st + A_TILE, &tmB, fbar, kb * 64, n0);
+                    goacd::tma_load_2d_pair(st, &tmA, fbar, kb * 64, q0);
+                    goacd::tma_load_2d_pair(st + A_TILE, &tmB, fbar, kb * 64, j0);
                 }
             }
             if (*abort_flag && rank == 0)
@@ -914,7 +934,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer (the even CTA) ----------------
         if (lane == 0 && rank == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, 2 * TC_M, TN);   // FP16, M = 256
+            constexpr uint32_t idesc = goacd::idesc_f32acc(0u, 2 * PX_HN, TN);   // FP16, M = 256
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
                 const PairTile tile = work[wi];
@@ -949,9 +969,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..5 of both CTAs ----------------
+        // ---------------- epilogue: warps 2..5 of both CTAs, one configuration per thread ----------------
         const int lg = warp & 3;
-        const int etid = threadIdx.x - 64;
+        constexpr int QPW = SPLIT ? 2 : 4;          // charges per 32-bit word
+        uint32_t qp[TN / QPW];
+        auto load_q = [&](const PairTile& tq) {
+            const long b = (long)tq.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
+            const uint4* src = (const uint4*)((const uint8_t*)qi + (b * ld + 2 * tq.P * TC_M) * (SPLIT ? 2 : 1));
+            const bool two = tq.slot1 >= 0;     // else the sites past panel 2P lie outside the row
+#pragma unroll
+            for (int u = 0; u < TN / QPW / 4; ++u) {
+                const uint4 v = (u < TN / QPW / 8 || two) ? __ldg(src + u) : make_uint4(0u, 0u, 0u, 0u);
+                qp[4 * u] = v.x;
+                qp[4 * u + 1] = v.y;
+                qp[4 * u + 2] = v.z;
+                qp[4 * u + 3] = v.w;
+            }
+        };
+        if (w0 < w1) load_q(work[w0]);
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
             const PairTile tile = work[wi];
@@ -960,66 +995,53 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
             if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
             goacd::tc_fence_after();
-            const int slot = rank == 0 ? tile.slot0 : tile.slot1;
-            const int v = (2 * tile.P + (int)rank) * TC_M + lg * 32 + lane;
-            const long n0 = (long)tile.n * TN;
-#pragma unroll 1
+            long long s0 = 0, s1 = 0;               // panels 2P and 2P + 1
+#pragma unroll
             for (int c = 0; c < TN / 32; ++c) {
                 uint32_t r[32];
                 goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
                                               (uint32_t)(c * 32),
                                           r);
                 goacd::tmem_ld_wait();
-                int hi[32], lo[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long b = n0 + c * 32 + j;
-                    const int q = slot >= 0 ? __float2int_rn(__half2float(qt[b * ld + v])) : 0;
-                    const int a = __float2int_rn(__uint_as_float(r[j]));   // |a| < 2^24, exact
-                    if (SPLIT) {
-                        hi[j] = (a >> 12) * q;
-                        lo[j] = (a & 4095) * q;
-                    } else {
-                        hi[j] = a * q;          // the host checked 32 max|q a| < 2^31
+                if (c == TN / 32 - 1) {
+                    // the accumulator rows have been read: the MMA may start the tile after next in them
+                    goacd::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0) goacd::mbar_arrive(&tempty[acc_i]);
+                        else goacd::mbar_arrive_cluster(goacd::mapa_shared(goacd::smem_u32(&tempty[acc_i]), 0));
                     }
                 }
+                long long cs;
+                if constexpr (SPLIT) {
+                    cs = 0;
 #pragma unroll
-                for (int sft = 16; sft >= 1; sft >>= 1) {
-                    const bool up = (lane & sft) != 0;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (k < sft) {
-                            const int sh = up ? hi[k] : hi[k + sft], kh = up ? hi[k + sft] : hi[k];
-                            hi[k] = kh + __shfl_xor_sync(0xffffffffu, sh, sft);
-                            if (SPLIT) {
-                                const int sl = up ? lo[k] : lo[k + sft], kl = up ? lo[k + sft] : lo[k];
-                                lo[k] = kl + __shfl_xor_sync(0xffffffffu, sl, sft);
-                            }
-                        }
-                }
-                red_hi[lg][c * 32 + lane] = hi[0];
-                if (SPLIT) red_lo[lg][c * 32 + lane] = lo[0];
-            }
-            goacd::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                if (rank == 0) goacd::mbar_arrive(&tempty[acc_i]);
-                else goacd::mbar_arrive_cluster(goacd::mapa_shared(goacd::smem_u32(&tempty[acc_i]), 0));
-            }
-            goacd::named_bar_sync(1, 128);
-            if (ok && slot >= 0)
-                for (int col = etid; col < TN; col += 128) {
-                    double pt;
-                    if (SPLIT) {
-                        const int sh = red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col];
-                        const int sl = red_lo[0][col] + red_lo[1][col] + red_lo[2][col] + red_lo[3][col];
-                        pt = (double)sh * 4096.0 + (double)sl;
-                    } else {
-                        pt = (double)((long long)red_hi[0][col] + red_hi[1][col] + red_hi[2][col] + red_hi[3][col]);
+                    for (int j = 0; j < 32; j += 2) {
+                        const uint32_t w = qp[(c * 32 + j) / 2];
+                        cs += (long long)__float2int_rn(__uint_as_float(r[j])) * ct_charge<true, 0>(w);
+                        cs += (long long)__float2int_rn(__uint_as_float(r[j + 1])) * ct_charge<true, 1>(w);
                     }
-                    partial[((long)slot * T + tile.t) * Bpad + n0 + col] = pt;
+                } else {
+                    int sum = 0;                    // |a| < 2^24 exact in FP32; 32 max|q a| < 2^31
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const uint32_t w = qp[(c * 32 + j) / 4];
+                        sum += __float2int_rn(__uint_as_float(r[j])) * ct_charge<false, 0>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 1])) * ct_charge<false, 1>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 2])) * ct_charge<false, 2>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 3])) * ct_charge<false, 3>(w);
+                    }
+                    cs = sum;
                 }
-            goacd::named_bar_sync(1, 128);
+                if (c < TN / 64) s0 += cs;
+                else s1 += cs;
+            }
+            if (wi + 1 < w1) load_q(work[wi + 1]);
+            if (ok) {
+                const long b = (long)tile.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
+                partial[((long)tile.slot0 * T + tile.t) * Bpad + b] = (double)s0;
+                if (tile.slot1 >= 0) partial[((long)tile.slot1 * T + tile.t) * Bpad + b] = (double)s1;
+            }
         }
     }
     goacd::tc_fence_before();
@@ -1028,6 +1050,246 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     if (warp == 2) {
         goacd::tc_fence_after();
         goacd::tmem_dealloc_pair(tmem, 2 * TN);
+    }
+}
+
+// Exact form with the configurations on the tensor-memory lanes: a tile is
+// 128 configurations (M, rows of Q^T) x one pair-panel of 256 sites (N, the
+// rows 256 P .. 256 P + 255 of digit t of J', i.e. panels 2P and 2P + 1) over
+// the pair-panel's k-range (from 256 P; the host may cut it into chunks).  The
+// accumulator row of configuration b then holds Phi_t,ib for the tile's 256
+// sites, and the epilogue thread that owns the row forms
+// P_t,I,b = sum_i q_bi Phi_t,ib over each panel's 128 sites by itself: no
+// cross-lane reduction, no shared memory, no barrier between the epilogue
+// warps.  The pair-panel's first two k-blocks meet panel 2P + 1 below its
+// diagonal, where J' is zero: unless they are the whole tile they go last, as
+// N = 128 MMAs over panel 2P's rows (a 128-row copy of J'); a pair-panel
+// without panel 2P + 1 (odd panel count) runs N = 128 MMAs throughout.  The
+// charges come from the int8 copy of Q^T (int16 when SPLIT) that k_make_qt
+// writes beside the FP16 operand: 256 contiguous bytes per configuration and
+// tile, loaded before the tile's accumulator is ready.  Each 32-site chunk of
+// products is summed in int32 under the same host bound as the one-CTA kernel
+// (32 max|q a| < 2^31), the chunks in 64 bits; SPLIT sums the products in 64
+// bits directly.  Work units and slots are pair_schedule's.
+constexpr int CT_M = 128;                       // configurations per tile (TMEM lanes)
+constexpr int CT_N = 256;                       // sites per tile (TMEM columns): one pair-panel
+constexpr int CT_STAGE = A_TILE + B_TILE;       // 48 KB: 128 rows of Q^T, 256 rows of J'
+constexpr int CT_STAGES = 4;
+constexpr int CT_SMEM = CT_STAGES * CT_STAGE + 1024 + 256;
+
+// The i-th k-block of a tile in processing order and whether its MMAs are
+// N = 128: the range after the pair-panel's first two k-blocks first, those two
+// (the head) last.
+struct CtStep {
+    int kb;
+    bool narrow;
+};
+__device__ __forceinline__ CtStep ct_step(const PairTile& tile, int i)
+{
+    const int kp = 4 * tile.P;
+    const bool single = tile.slot1 < 0;
+    const int h1 = (tile.kb0 == kp && tile.kb1 > kp + 2) ? kp + 2 : tile.kb0;
+    const int nrest = tile.kb1 - h1;
+    const int kb = i < nrest ? h1 + i : tile.kb0 + (i - nrest);
+    return CtStep{kb, single || kb < h1};
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(192, SPLIT ? 1 : 2)
+    k_score_exact_ct(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmJ,
+                     const __grid_constant__ CUtensorMap tmJn, const PairTile* __restrict__ work,
+                     const int* __restrict__ work_start, int ld, int T, const void* __restrict__ qi,
+                     double* __restrict__ partial, int Bpad, int* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    static_assert(CT_STAGES * CT_STAGE + 1024 + 256 <= CT_SMEM, "stages exceed the dynamic shared memory");
+    uint64_t* full = (uint64_t*)(smem + CT_STAGES * CT_STAGE);
+    uint64_t* empty = full + CT_STAGES;
+    uint64_t* tfull = empty + CT_STAGES;        // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;               // [2] accumulator drained
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w0 = work_start[blockIdx.x], w1 = work_start[blockIdx.x + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CT_STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 4);
+        }
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmQ);
+        goacd::prefetch_tmap(&tmJ);
+        goacd::prefetch_tmap(&tmJn);
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc(tmem_slot, 2 * CT_N);
+        goacd::tmem_relinquish();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // launched as a dependent of k_make_qt: the set-up above overlaps its tail
+    goacd::pdl_wait();
+    goacd::pdl_trigger();
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int it = 0;
+            for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
+                const PairTile tile = work[wi];
+                const int nsteps = tile.kb1 - tile.kb0;
+                const int jrow = tile.t * ld + 2 * tile.P * TC_M;
+                for (int i = 0; i < nsteps; ++i, ++it) {
+                    const int s = it % CT_STAGES;
+                    const uint32_t use = (uint32_t)(it / CT_STAGES);
+                    if (it >= CT_STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    const CtStep k = ct_step(tile, i);
+                    uint8_t* st = smem + s * CT_STAGE;
+                    goacd::mbar_arrive_expect_tx(&full[s], A_TILE + (k.narrow ? A_TILE : B_TILE));
+                    goacd::tma_load_2d(st, &tmQ, &full[s], k.kb * 64, tile.n * CT_M);
+                    goacd::tma_load_2d(st + A_TILE, k.narrow ? &tmJn : &tmJ, &full[s], k.kb * 64, jrow);
+                }
+            }
+            if (*abort_flag)
+                for (int k = it - CT_STAGES < 0 ? 0 : it - CT_STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % CT_STAGES], (uint32_t)(k / CT_STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idw = goacd::idesc_f32acc(0u, CT_M, CT_N);    // FP16 charges and digits
+            constexpr uint32_t idn = goacd::idesc_f32acc(0u, CT_M, CT_N / 2);
+            int it = 0, tl = 0;
+            for (int wi = w0; wi < w1; ++wi, ++tl) {
+                const PairTile tile = work[wi];
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
+                }
+                goacd::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * CT_N);
+                const int nsteps = tile.kb1 - tile.kb0;
+                for (int i = 0; i < nsteps; ++i, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % CT_STAGES;
+                    const uint32_t use = (uint32_t)(it / CT_STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t idesc = ct_step(tile, i).narrow ? idn : idw;
+                    const uint32_t a0 = goacd::smem_u32(smem + s * CT_STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        goacd::mma_bf16(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
+                                        goacd::sdesc_k128(a0 + A_TILE + kk * 32), idesc,
+                                        (i != 0 || kk != 0) ? 1u : 0u);
+                    goacd::mma_commit(&empty[s]);
+                }
+                goacd::mma_commit(&tfull[acc_i]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5, one configuration per thread ----------------
+        const int lg = warp & 3;
+        constexpr int QPW = SPLIT ? 2 : 4;          // charges per 32-bit word
+        uint32_t qp[CT_N / QPW];
+        auto load_q = [&](const PairTile& tq) {
+            const long b = (long)tq.n * CT_M + lg * 32 + lane;
+            const uint4* src = (const uint4*)((const uint8_t*)qi + (b * ld + 2 * tq.P * TC_M) * (SPLIT ? 2 : 1));
+            const bool two = tq.slot1 >= 0;     // else the sites past panel 2P lie outside the row
+#pragma unroll
+            for (int u = 0; u < CT_N / QPW / 4; ++u) {
+                const uint4 v = (u < CT_N / QPW / 8 || two) ? __ldg(src + u) : make_uint4(0u, 0u, 0u, 0u);
+                qp[4 * u] = v.x;
+                qp[4 * u + 1] = v.y;
+                qp[4 * u + 2] = v.z;
+                qp[4 * u + 3] = v.w;
+            }
+        };
+        if (w0 < w1) load_q(work[w0]);
+        int tl = 0;
+        for (int wi = w0; wi < w1; ++wi, ++tl) {
+            const PairTile tile = work[wi];
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            long long s0 = 0, s1 = 0;               // panels 2P and 2P + 1
+#pragma unroll
+            for (int c = 0; c < CT_N / 32; ++c) {
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * CT_N) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                if (c == CT_N / 32 - 1) {
+                    // the accumulator has been read: the MMA warp may start the tile after next in it
+                    goacd::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) goacd::mbar_arrive(&tempty[acc_i]);
+                }
+                long long cs;
+                if constexpr (SPLIT) {
+                    cs = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        const uint32_t w = qp[(c * 32 + j) / 2];
+                        cs += (long long)__float2int_rn(__uint_as_float(r[j])) * ct_charge<true, 0>(w);
+                        cs += (long long)__float2int_rn(__uint_as_float(r[j + 1])) * ct_charge<true, 1>(w);
+                    }
+                } else {
+                    int sum = 0;                    // |a| < 2^24 exact in FP32; 32 max|q a| < 2^31
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const uint32_t w = qp[(c * 32 + j) / 4];
+                        sum += __float2int_rn(__uint_as_float(r[j])) * ct_charge<false, 0>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 1])) * ct_charge<false, 1>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 2])) * ct_charge<false, 2>(w);
+                        sum += __float2int_rn(__uint_as_float(r[j + 3])) * ct_charge<false, 3>(w);
+                    }
+                    cs = sum;
+                }
+                if (c < CT_N / 64) s0 += cs;
+                else s1 += cs;
+            }
+            if (wi + 1 < w1) load_q(work[wi + 1]);
+            if (ok) {
+                const long b = (long)tile.n * CT_M + lg * 32 + lane;
+                partial[((long)tile.slot0 * T + tile.t) * Bpad + b] = (double)s0;
+                if (tile.slot1 >= 0) partial[((long)tile.slot1 * T + tile.t) * Bpad + b] = (double)s1;
+            }
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc(tmem, 2 * CT_N);
     }
 }
 
@@ -1322,13 +1584,15 @@ __global__ void k_copy_f32(const double* __restrict__ J, long n, float* __restri
 // block of 128 threads per configuration row; a thread converts two chunks of
 // 16 species per step (one 16-byte load each when the row is 16-byte aligned,
 // both issued before either is converted), 16-byte stores.  With fixed ions
-// also lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).
+// also lin[b] = sum_v q_bv 2 phi_fix_v in FP64 (fixed reduction order).  FP16
+// with qbytes 1 or 2: the same integer charges also as int8 or int16 at
+// qi[b][v] (the exact form's epilogue operand).
 constexpr int MQ_T = 128;
 
 template <typename QT>
 __device__ __forceinline__ void make_qt_chunk(const int8_t (&s16)[16], const float* zs, const double* __restrict__ z,
                                               const double* __restrict__ phifix, int v0, QT* __restrict__ row,
-                                              double& acc)
+                                              double& acc, uint8_t* __restrict__ qrow, int qbytes)
 {
     float q[16];
 #pragma unroll
@@ -1342,6 +1606,19 @@ __device__ __forceinline__ void make_qt_chunk(const int8_t (&s16)[16], const flo
         for (int u = 0; u < 16; ++u) o[u] = __float2half_rn(q[u]);
         ((int4*)(row + v0))[0] = ((const int4*)o)[0];
         ((int4*)(row + v0))[1] = ((const int4*)o)[1];
+        if (qbytes == 1) {
+            // integer charges (the exact form's q are integers below 2^6 here)
+            __align__(16) int8_t c[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) c[u] = (int8_t)__float2int_rn(q[u]);
+            *(int4*)(qrow + v0) = *(const int4*)c;
+        } else if (qbytes == 2) {
+            __align__(16) int16_t c[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) c[u] = (int16_t)__float2int_rn(q[u]);
+            ((int4*)(qrow + 2 * v0))[0] = ((const int4*)c)[0];
+            ((int4*)(qrow + 2 * v0))[1] = ((const int4*)c)[1];
+        }
     } else if constexpr (sizeof(QT) == 2) {
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
@@ -1369,7 +1646,7 @@ template <typename QT>
 __global__ void __launch_bounds__(MQ_T) k_make_qt(const int8_t* __restrict__ species, int B, int Nv,
                                                   const double* __restrict__ zq, const double* __restrict__ z, int ld,
                                                   QT* __restrict__ qt, const double* __restrict__ phifix,
-                                                  double* __restrict__ lin)
+                                                  double* __restrict__ lin, void* __restrict__ qi, int qbytes)
 {
     __shared__ float zs[64];
     __shared__ double red[MQ_T];
@@ -1380,14 +1657,16 @@ __global__ void __launch_bounds__(MQ_T) k_make_qt(const int8_t* __restrict__ spe
     QT* row = qt + (long)b * ld;
     const int8_t* src = species + (long)b * Nv;
     const bool aligned = ((Nv & 15) == 0) && (((uintptr_t)species & 15) == 0);
+    uint8_t* qrow = qi ? (uint8_t*)qi + (long)b * ld * qbytes : nullptr;
+    if (!qi) qbytes = 0;
     double acc = 0.0;
     for (int v0 = threadIdx.x * 16; v0 < ld; v0 += 2 * MQ_T * 16) {   // ld is a multiple of 128
         const int v1 = v0 + MQ_T * 16;
         int8_t sa[16], sb[16];
         make_qt_load(src, b, B, Nv, aligned, v0, sa);
         if (v1 < ld) make_qt_load(src, b, B, Nv, aligned, v1, sb);
-        make_qt_chunk<QT>(sa, zs, z, phifix, v0, row, acc);
-        if (v1 < ld) make_qt_chunk<QT>(sb, zs, z, phifix, v1, row, acc);
+        make_qt_chunk<QT>(sa, zs, z, phifix, v0, row, acc, qrow, qbytes);
+        if (v1 < ld) make_qt_chunk<QT>(sb, zs, z, phifix, v1, row, acc, qrow, qbytes);
     }
     if (phifix == nullptr || b >= B) return;
     red[threadIdx.x] = acc;
@@ -1534,7 +1813,8 @@ int2 tc_tile_count(int nbm, int nbn, int T, int kc)
 // then runs its tiles longest, shortest, second longest, ... so that the
 // epilogue of a short tile (which can take longer than its MMAs) overlaps the
 // MMAs of a long one through the two TMEM accumulators.
-goac_status tc_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int kbm, int grid, const TcTile** work,
+goac_status tc_schedule(TcSched& sc, cudaStream_t stream, int nbm, int nbn, int T, int kc, int kbm, int grid,
+                        const TcTile** work,
                         const int** starts, const int** pslot)
 {
     if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || grid <= 0 || grid >= (1 << 20) || T < 1 ||
@@ -1587,9 +1867,11 @@ goac_status tc_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int kbm, i
         if (rc) return rc;
         TcTile* dw = (TcTile*)sc.buf.ptr;
         int* ds = (int*)(dw + flat.size());
-        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(TcTile) * flat.size(), cudaMemcpyHostToDevice));
-        GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice));
-        GOAC_CUDA(cudaMemcpy(ds + grid + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice));
+        // stream-ordered: a launch still reading the previous schedule finishes first
+        GOAC_CUDA(cudaMemcpyAsync(dw, flat.data(), sizeof(TcTile) * flat.size(), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaMemcpyAsync(ds, st.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaMemcpyAsync(ds + grid + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaStreamSynchronize(stream));   // the host vectors go out of scope
         sc.key[0] = k0;
         sc.key[1] = k1;
         sc.ntiles = (int)flat.size();
@@ -1619,7 +1901,7 @@ goac_status launch_tc(goac_problem* p, const CUtensorMap& ma, const CUtensorMap&
     const int grid = std::min(cnt.x, p->ctx->num_sms);
     const TcTile* work = nullptr;
     const int* starts = nullptr;
-    goac_status rc = tc_schedule(p->sched, nbm, nbn, 1, kc, TF32 ? 4 : 2, grid, &work, &starts, nullptr);
+    goac_status rc = tc_schedule(p->sched, p->ctx->stream, nbm, nbn, 1, kc, TF32 ? 4 : 2, grid, &work, &starts, nullptr);
     if (rc) return rc;
     goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
     goac::launch_pdl(kern, grid, 192, Cfg::SMEM, p->ctx->stream, ma, mb, work, starts, ld, qt, ld, part, Bpad,
@@ -1644,7 +1926,7 @@ goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorM
     const TcTile* work = nullptr;
     const int* starts = nullptr;
     const int* pslot = nullptr;
-    rc = tc_schedule(p->sched_ex, nbm, nbn, T, kc, 2, grid, &work, &starts, &pslot);
+    rc = tc_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, 2, grid, &work, &starts, &pslot);
     if (rc) return rc;
     {
         goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
@@ -1662,7 +1944,8 @@ goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorM
 // tile n, k-chunk, digit t) longest first over the pairs; panel I's k-chunk
 // slots are numbered panel by panel (pslot[I] .. pslot[I+1]) as for the
 // one-CTA kernel, with panel 2P + 1 chunked like its pair-panel.
-goac_status pair_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int npairs, const PairTile** work,
+goac_status pair_schedule(TcSched& sc, cudaStream_t stream, int nbm, int nbn, int T, int kc, int npairs,
+                          const PairTile** work,
                           const int** starts, const int** pslot)
 {
     if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || npairs <= 0 || npairs >= (1 << 19) ||
@@ -1723,9 +2006,11 @@ goac_status pair_schedule(TcSched& sc, int nbm, int nbn, int T, int kc, int npai
         if (rc) return rc;
         PairTile* dw = (PairTile*)sc.buf.ptr;
         int* ds = (int*)(dw + flat.size());
-        GOAC_CUDA(cudaMemcpy(dw, flat.data(), sizeof(PairTile) * flat.size(), cudaMemcpyHostToDevice));
-        GOAC_CUDA(cudaMemcpy(ds, st.data(), sizeof(int) * (npairs + 1), cudaMemcpyHostToDevice));
-        GOAC_CUDA(cudaMemcpy(ds + npairs + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice));
+        // stream-ordered: a launch still reading the previous schedule finishes first
+        GOAC_CUDA(cudaMemcpyAsync(dw, flat.data(), sizeof(PairTile) * flat.size(), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaMemcpyAsync(ds, st.data(), sizeof(int) * (npairs + 1), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaMemcpyAsync(ds + npairs + 1, ps.data(), sizeof(int) * (nbm + 1), cudaMemcpyHostToDevice, stream));
+        GOAC_CUDA(cudaStreamSynchronize(stream));   // the host vectors go out of scope
         sc.key[0] = k0;
         sc.key[1] = k1;
         sc.ntiles = (int)flat.size();
@@ -1789,13 +2074,47 @@ goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUte
     const PairTile* work = nullptr;
     const int* starts = nullptr;
     const int* pslot = nullptr;
-    rc = pair_schedule(p->sched_ex, nbm, nbn, T, kc, npairs, &work, &starts, &pslot);
+    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, npairs, &work, &starts, &pslot);
     if (rc) return rc;
     {
         goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
         goac::launch_pdl(k_score_exact_pair<SPLIT>, 2 * npairs, 192, PX_SMEM, p->ctx->stream, ma, mb, work, starts, ld, T,
-                         (const __half*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+                         (const void*)p->qi.ptr, part, Bpad, p->ctx->d_err);
         GOAC_LAUNCH_CHECK("k_score_exact_pair");
+    }
+    goac::launch_pdl(k_finish_exact, (B + 31) / 32, FX_WARPS * 32, 0, p->ctx->stream, (const double*)part, nbm, pslot,
+                     (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
+    GOAC_LAUNCH_CHECK("k_finish_exact");
+    return GOAC_OK;
+}
+
+// The configuration-lane kernel: pair_schedule's work units over a persistent
+// grid of one CTA per SM (128-configuration blocks), then k_finish_exact.
+template <bool SPLIT>
+goac_status launch_exact_ct(goac_problem* p, const CUtensorMap& mq, const CUtensorMap& mj, const CUtensorMap& mjn,
+                            int Bpad, int B, int kc, double* part, const double* lin, double* E_out)
+{
+    static std::atomic<uint64_t> attr_done{0};
+    goac_status rc = smem_attr_once((const void*)k_score_exact_ct<SPLIT>, CT_SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
+    const int ld = p->Nv_pad, T = p->dig_T;
+    const int nbm = ld / TC_M, nbn = (B + CT_M - 1) / CT_M, npp = (nbm + 1) / 2;
+    long ntiles = 0;
+    for (int P = 0; P < npp; ++P) {
+        const int span = 2 * nbm - 4 * P;
+        ntiles += (long)(kc > 0 ? (span + 2 * kc - 1) / (2 * kc) : 1) * nbn * T;
+    }
+    const int grid = (int)std::min<long>(ntiles, p->ctx->num_sms);
+    const PairTile* work = nullptr;
+    const int* starts = nullptr;
+    const int* pslot = nullptr;
+    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, grid, &work, &starts, &pslot);
+    if (rc) return rc;
+    {
+        goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
+        goac::launch_pdl(k_score_exact_ct<SPLIT>, grid, 192, CT_SMEM, p->ctx->stream, mq, mj, mjn, work, starts, ld,
+                         T, (const void*)p->qi.ptr, part, Bpad, p->ctx->d_err);
+        GOAC_LAUNCH_CHECK("k_score_exact_ct");
     }
     goac::launch_pdl(k_finish_exact, (B + 31) / 32, FX_WARPS * 32, 0, p->ctx->stream, (const double*)part, nbm, pslot,
                      (const int*)p->dig_exp, Bpad, B, p->dig_r, T, 2 * p->dig_kq, p->E_const, lin, E_out);
@@ -2003,7 +2322,7 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
     goac::launch(k_make_qt<__half>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
-                 (const double*)p->z_dev, ld, (__half*)p->qt.ptr, (const double*)nullptr, (double*)nullptr);
+                 (const double*)p->z_dev, ld, (__half*)p->qt.ptr, (const double*)nullptr, (double*)nullptr, (void*)nullptr, 0);
     GOAC_LAUNCH_CHECK("k_make_qt (exact potentials)");
     CUtensorMap ma, mb;
     rc = make_map(&ma, p->J_dig_full, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
@@ -2033,13 +2352,14 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
 }
 
 // Tile shape of the scoring kernels for (precision, padded batch): the one
-// goac_score_autotune or goac_score_set_shape stored, else 128 sites x 256
-// configurations per tile and whole panel ranges.
+// goac_score_autotune or goac_score_set_shape stored, else whole panel ranges
+// in tiles of 256 sites x 256 configurations on CTA pairs for the exact form
+// and of 128 sites x 256 configurations for the split forms.
 static void pick_shape(const goac_problem* p, int precision, int Bpad, int* TM, int* TN, int* kc)
 {
     const auto it = p->tile_shape.find(std::make_pair(precision, Bpad));
     const bool has = it != p->tile_shape.end();
-    *TM = has ? std::get<0>(it->second) : TC_M;
+    *TM = has ? std::get<0>(it->second) : (precision == GOAC_PREC_EXACT ? 2 * TC_M : TC_M);
     *TN = has ? std::get<1>(it->second) : TC_N;
     *kc = has ? std::get<2>(it->second) : 0;
 }
@@ -2054,9 +2374,13 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     const int nbm = ld / TC_M;
     int TM = 0, TN = 0, kc = 0;
     pick_shape(p, GOAC_PREC_EXACT, Bpad, &TM, &TN, &kc);
-    const bool pair = TM == 2 * TC_M;
-    const int nslots = pair ? pair_slot_count(nbm, kc) : tc_tile_count(nbm, (B + TN - 1) / TN, T, kc).y;
+    const bool pair = TM == 2 * TC_M && TN == TC_N;
+    const bool ct = TM == 2 * TC_M && TN == TC_NS;      // configurations on the TMEM lanes
+    const bool split = p->dig_split;
+    const int qbytes = ct || pair ? (split ? 2 : 1) : 0;    // the configuration-lane epilogues' charges
+    const int nslots = pair || ct ? pair_slot_count(nbm, kc) : tc_tile_count(nbm, (B + TN - 1) / TN, T, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * 2);
+    if (!rc && qbytes) rc = ensure(p->qi, (size_t)Bpad * ld * qbytes);
     if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * T * Bpad + Bpad));
     if (rc) return rc;
     cudaStream_t st = p->ctx->stream;
@@ -2064,13 +2388,27 @@ static goac_status score_exact(goac_problem* p, const int8_t* species, int B, do
     double* lin = p->has_fixed ? part + (size_t)nslots * T * Bpad : nullptr;
     goac::launch(k_make_qt<__half>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->zq_dev,
                  (const double*)p->z_dev, ld, (__half*)p->qt.ptr,
-                 (const double*)(p->has_fixed ? p->phifix : nullptr), lin);
+                 (const double*)(p->has_fixed ? p->phifix : nullptr), lin, qbytes ? p->qi.ptr : nullptr, qbytes);
     GOAC_LAUNCH_CHECK("k_make_qt (exact)");
     CUtensorMap ma, mb;
-    rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, pair ? PX_HN : TN);
+    if (ct) {
+        CUtensorMap mj, mjn;
+        rc = make_map(&ma, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, CT_M);
+        if (!rc) rc = make_map(&mj, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, CT_N);
+        if (!rc) rc = make_map(&mjn, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, CT_N / 2);
+        if (rc) return rc;
+        return split ? launch_exact_ct<true>(p, ma, mj, mjn, Bpad, B, kc, part, lin, E_out)
+                     : launch_exact_ct<false>(p, ma, mj, mjn, Bpad, B, kc, part, lin, E_out);
+    }
+    if (pair) {
+        // M: each CTA's 128 configurations of Q^T; N: each CTA's 128 digit rows of J'
+        rc = make_map(&ma, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, PX_HN);
+        if (!rc) rc = make_map(&mb, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
+    } else {
+        rc = make_map(&ma, p->J_dig, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, (long)T * ld, ld, TC_M);
+        if (!rc) rc = make_map(&mb, p->qt.ptr, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, ld, Bpad, ld, TN);
+    }
     if (rc) return rc;
-    const bool split = p->dig_split;
     if (pair)
         return split ? launch_exact_pair<true>(p, ma, mb, Bpad, B, kc, part, lin, E_out)
                      : launch_exact_pair<false>(p, ma, mb, Bpad, B, kc, part, lin, E_out);
@@ -2115,10 +2453,10 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
         const double* pf = p->has_fixed ? p->phifix : nullptr;
         if (tf32)
             goac::launch(k_make_qt<float>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->z_dev,
-                         (const double*)p->z_dev, ld, (float*)p->qt.ptr, pf, lin);
+                         (const double*)p->z_dev, ld, (float*)p->qt.ptr, pf, lin, (void*)nullptr, 0);
         else
             goac::launch(k_make_qt<__nv_bfloat16>, Bpad, MQ_T, 0, st, species, B, p->Nv, (const double*)p->z_dev,
-                         (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, pf, lin);
+                         (const double*)p->z_dev, ld, (__nv_bfloat16*)p->qt.ptr, pf, lin, (void*)nullptr, 0);
         GOAC_LAUNCH_CHECK("k_make_qt");
     }
     CUtensorMap ma, mb;
@@ -2156,8 +2494,8 @@ extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, 
         !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 || ksplit > 65535)
         return goac::fail(GOAC_ERR_INVALID_ARG,
                           "goac_score_set_shape: B >= 1, tile_m 0, 128 or 256, tile_n 0, 128 or 256, ksplit 0..65535");
-    if (tile_m == 256 && (precision != GOAC_PREC_EXACT || tile_n == 128))
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: 256-site tiles (CTA pairs) need EXACT and tile_n 256");
+    if (tile_m == 256 && precision != GOAC_PREC_EXACT)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: 256-site tiles need EXACT");
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
     if (tile_m == 0 && tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
@@ -2183,9 +2521,10 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
     const int nbm = p->Nv_pad / 128;
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
-    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles (CTA pairs) for the exact form
-    const int shapes[3][2] = {{128, 256}, {128, 128}, {256, 256}};
-    const int nshapes = precision == GOAC_PREC_EXACT ? 3 : 2;
+    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles (CTA pairs, configurations on the TMEM
+    // lanes) for the exact form
+    const int shapes[4][2] = {{128, 256}, {128, 128}, {256, 256}, {256, 128}};
+    const int nshapes = precision == GOAC_PREC_EXACT ? 4 : 2;
     const int kcs[5] = {0, 16, 8, 4, 2};
     int best_tm = 0, best_tn = 0, best_kc = 0;
     float best = 0.0f;

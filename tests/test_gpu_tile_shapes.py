@@ -2,7 +2,9 @@
 
 A tile covers 128 sites x 128 or 256 configurations, over the whole column
 range of its row panel or over chunks of it (each chunk adds a partial row-dot
-sum).  The exact integer-digit form must give the same energies bit for bit in
+sum); the exact form also has 256-site tiles: CTA pairs with 256
+configurations, and one CTA with 128 configurations on the tensor-memory lanes
+(its pair-panel's first two k-blocks run as 128-site MMAs, last).  The exact integer-digit form must give the same energies bit for bit in
 every shape (its chunk partials are exact integers added exactly); the split
 forms must stay within their derived bound of the oracle in every shape; the
 autotuner's choice must be one of the shapes and be used afterwards."""
@@ -17,8 +19,10 @@ from gpu_common import build_pair, form_tolerance, gpu_problem
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(256, 0), (128, 0), (256, 16), (128, 8), (256, 4), (128, 2), (256, 1)]
-# (tile_m, tile_n, ksplit) of the CTA-pair kernel (exact form only)
-PAIR_SHAPES = [(256, 256, 0), (256, 256, 8), (256, 256, 1)]
+# (tile_m, tile_n, ksplit) of the 256-site tiles (exact form only): the CTA-pair kernel (tile_n 256) and
+# the configuration-lane kernel (tile_n 128; ksplit 1 makes each pair-panel's first chunk its two
+# head k-blocks alone)
+PAIR_SHAPES = [(256, 256, 0), (256, 256, 8), (256, 256, 1), (256, 128, 0), (256, 128, 8), (256, 128, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +103,7 @@ def test_autotuner_choice(cubic, form, B):
     ref = gp.score(pop, form).clone()
     tm, tn, kc, ms = gp.score_autotune(pop, form)
     assert tn in (128, 256) and kc in (0, 16, 8, 4, 2) and ms > 0
-    assert tm == 128 or (tm == 256 and form == "exact" and tn == 256)
+    assert tm == 128 or (tm == 256 and form == "exact")
     E = gp.score(pop, form)
     if form == "exact":
         assert torch.equal(E, ref)
@@ -121,7 +125,7 @@ def test_set_shape_rejects_bad_shapes(cubic):
                  (16, "f32", 0, 4)]:
         with pytest.raises(g.GoacError):
             gp.score_set_shape(*args)
-    for kw in [dict(tile_m=64), dict(tile_m=256, precision="bf16x2"), dict(tile_m=256, tile_n=128)]:
+    for kw in [dict(tile_m=64), dict(tile_m=256, precision="bf16x2"), dict(tile_m=256, tile_n=128, precision="tf32x2")]:
         args = dict(B=16, precision="exact", tile_n=256, ksplit=0)
         args.update(kw)
         with pytest.raises(g.GoacError):
@@ -130,8 +134,10 @@ def test_set_shape_rejects_bad_shapes(cubic):
 
 def test_pair_kernel_odd_panel_count(ctx):
     """Layered 12x12x1 cell: Nv = 864 sites make seven 128-row panels, so the
-    last CTA pair has no second panel; with fixed ions (a linear term).  Every
-    shape, the CTA pairs included, gives the default shape's exact energies."""
+    last pair-panel has no second panel (the CTA pair's odd CTA idles, the
+    configuration-lane kernel runs 128-site MMAs); with fixed ions (a linear
+    term) and a population whose last 128-configuration block is empty.  Every
+    shape gives the default shape's exact energies."""
     import paper_2409_08808_gb300 as g
     prob = synth.layered_problem()
     frac = torch.tensor(prob.frac, device="cuda")
