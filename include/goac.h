@@ -162,20 +162,21 @@ goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B,
 /* Tile shape of the tensor-core scoring kernels (no counterpart in the       *
  * paper; the results of EXACT do not depend on it, those of the split forms  *
  * change only by FP32 rounding).  A tile covers tile_m sites x tile_n        *
- * configurations: tile_m 128 (one CTA) or 256 (EXACT only: with tile_n 256  *
- * a pair of CTAs on one TPC issuing M = 256 tcgen05 MMAs, each CTA loading   *
- * its own 128 digit rows and half of the configurations; with tile_n 128 one *
- * CTA with the configurations on the tensor-memory lanes, each epilogue      *
- * thread weighting one configuration's 256 site sums by its charges), tile_n *
- * 128 or 256;                                                                 *
+ * configurations: tile_m 128 (one CTA) or 256 (EXACT, BF16X2, BF16X3: with  *
+ * tile_n 256 a pair of CTAs on one TPC issuing M = 256 tcgen05 MMAs over the *
+ * configurations, each CTA loading its own 128 configurations and its own    *
+ * panel's rows of J', each epilogue thread weighting one configuration's 256 *
+ * site sums by its charges; EXACT only, with tile_n 128: one CTA with the    *
+ * configurations on the tensor-memory lanes), tile_n 128 or 256;             *
  * ksplit > 0 cuts each row panel's column range into chunks of ksplit         *
  * 128-column blocks scored as separate tiles (the row-dot is linear, so each  *
  * chunk adds a partial sum; this spreads small populations over all SMs).    *
  * goac_score_set_shape stores a shape for (precision, B rounded up to 256)    *
  * (all 0: the default, whole ranges in 256 x 256 tiles on CTA pairs for EXACT *
- * and 128 x 256 tiles for the split forms); goac_score_autotune times         *
- * every shape in {128 x 256, 128 x 128, 256 x 256 and 256 x 128 (EXACT)} x   *
- * {0, 16, 8, 4, 2}                                                            *
+ * and the BF16 forms, 128 x 256 tiles for the TF32 forms);                    *
+ * goac_score_autotune times                                                   *
+ * every shape in {128 x 256, 128 x 128, 256 x 256 (EXACT, BF16X2, BF16X3),   *
+ * 256 x 128 (EXACT)} x {0, 16, 8, 4, 2}                                       *
  * on species_dev (B x Nv), CUDA events on the context stream, stores the      *
  * fastest for later goac_score calls with that precision and padded B, and    *
  * returns it (outputs nullable; ms per scoring call).  Host-side store;       *

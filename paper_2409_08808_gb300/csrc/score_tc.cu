@@ -1053,6 +1053,223 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     }
 }
 
+// Split forms (BF16 terms) on CTA pairs, laid out as k_score_exact_pair: a
+// tile is 256 configurations (128 on each CTA's tensor-memory lanes) x one
+// pair-panel of 256 sites, M = 256 MMAs issued by the even CTA; each CTA loads
+// its own 128 configurations' rows of Q^T and, for each of the T terms of J',
+// its panel's 128 rows, and the T terms accumulate into the same FP32 tile.
+// The epilogue thread that owns configuration b forms q_b . Phi over each
+// panel's 128 sites by itself: per 32-site chunk an FP32 sum of q Phi (the
+// charges read from the BF16 row of Q^T two chunks ahead), the chunks added in
+// FP64.  Slots are pair_schedule's (one per panel and k-chunk, no digit index).
+template <int T>
+struct TpCfg {
+    static constexpr int STAGE = (1 + T) * A_TILE;                  // Q^T rows, then T x J' rows
+    static constexpr int STAGES = (196 * 1024) / STAGE > 6 ? 6 : (196 * 1024) / STAGE;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int T>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    k_score_tc_pair(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmJ,
+                    const PairTile* __restrict__ work, const int* __restrict__ work_start, int ld,
+                    const __nv_bfloat16* __restrict__ qt, double* __restrict__ partial, int Bpad,
+                    int* __restrict__ err)
+{
+    using Cfg = TpCfg<T>;
+    constexpr int STAGES = Cfg::STAGES, STAGE = Cfg::STAGE;
+    constexpr int TN = 256;                     // sites per tile: TMEM columns
+    static_assert(STAGES * STAGE + 1024 + 256 <= Cfg::SMEM, "stages exceed the dynamic shared memory");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;           // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;               // [2] accumulator drained (the even CTA's counts both)
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = goacd::cluster_ctarank();
+    const int pair = blockIdx.x >> 1;
+    const int w0 = work_start[pair], w1 = work_start[pair + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            goacd::mbar_init(&full[s], 1);
+            goacd::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            goacd::mbar_init(&tfull[a], 1);
+            goacd::mbar_init(&tempty[a], 8);
+        }
+        *abort_flag = 0;
+        goacd::fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        goacd::prefetch_tmap(&tmQ);
+        goacd::prefetch_tmap(&tmJ);
+    }
+    if (warp == 2) {
+        goacd::tmem_alloc_pair(tmem_slot, 2 * TN);
+        goacd::tmem_relinquish_pair();
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::cluster_sync();                      // the even CTA's barriers exist before the odd one signals them
+    goacd::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    goacd::pdl_wait();
+    goacd::pdl_trigger();
+
+    if (warp == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        if (lane == 0) {
+            int it = 0;
+            for (int wi = w0; wi < w1 && !*abort_flag; ++wi) {
+                const PairTile tile = work[wi];
+                const int q0 = tile.n * 256 + (int)rank * PX_HN, j0 = (2 * tile.P + (int)rank) * TC_M;
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
+                    if (it >= STAGES && !goacd::mbar_wait_bounded(&empty[s], (use - 1) & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_PRODUCER, it);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    uint8_t* st = smem + s * STAGE;
+                    const uint32_t fbar = goacd::mapa_shared(goacd::smem_u32(&full[s]), 0);
+                    if (rank == 0) goacd::mbar_arrive_expect_tx(&full[s], 2 * STAGE);
+                    goacd::tma_load_2d_pair(st, &tmQ, fbar, kb * 64, q0);
+#pragma unroll
+                    for (int t = 0; t < T; ++t)
+                        goacd::tma_load_2d_pair(st + (1 + t) * A_TILE, &tmJ, fbar, kb * 64, t * ld + j0);
+                }
+            }
+            if (*abort_flag && rank == 0)
+                // every copy of the pair counted on these barriers must land before the CTAs exit
+                for (int k = it - STAGES < 0 ? 0 : it - STAGES; k < it; ++k)
+                    if (!goacd::mbar_wait_bounded(&full[k % STAGES], (uint32_t)(k / STAGES) & 1, WAIT_LIMIT))
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_DRAIN, k);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (the even CTA) ----------------
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, 2 * PX_HN, TN);   // BF16, M = 256
+            int it = 0, tl = 0;
+            for (int wi = w0; wi < w1; ++wi, ++tl) {
+                const PairTile tile = work[wi];
+                const int acc_i = tl & 1;
+                const uint32_t ause = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !goacd::mbar_wait_bounded(&tempty[acc_i], (ause - 1) & 1, WAIT_LIMIT)) {
+                    *abort_flag = 1;
+                    goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, -1 - tl);
+                }
+                goacd::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * TN);
+                for (int kb = tile.kb0; kb < tile.kb1; ++kb, ++it) {
+                    if (*abort_flag) break;
+                    const int s = it % STAGES;
+                    const uint32_t use = (uint32_t)(it / STAGES);
+                    if (!goacd::mbar_wait_bounded(&full[s], use & 1, WAIT_LIMIT)) {
+                        *abort_flag = 1;
+                        goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_MMA, it);
+                        break;
+                    }
+                    goacd::tc_fence_after();
+                    const uint32_t a0 = goacd::smem_u32(smem + s * STAGE);
+#pragma unroll
+                    for (int t = 0; t < T; ++t)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            goacd::mma_f16_pair(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
+                                                goacd::sdesc_k128(a0 + (1 + t) * A_TILE + kk * 32), idesc,
+                                                (kb != tile.kb0 || t != 0 || kk != 0) ? 1u : 0u);
+                    goacd::mma_commit_pair(&empty[s], 0x3);
+                }
+                goacd::mma_commit_pair(&tfull[acc_i], 0x3);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5 of both CTAs, one configuration per thread ----------------
+        const int lg = warp & 3;
+        uint32_t qw[TN / 32][16];               // BF16 charge pairs per 32-site chunk (a few live at a time)
+        auto load_chunk = [&](const PairTile& tq, int c, uint32_t (&dst)[16]) {
+            const long b = (long)tq.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
+            const uint4* src = (const uint4*)(qt + b * ld + 2 * tq.P * TC_M + c * 32);
+            const bool in_row = c < TN / 64 || tq.slot1 >= 0;   // else past the end of the row
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint4 v = in_row ? __ldg(src + u) : make_uint4(0u, 0u, 0u, 0u);
+                dst[4 * u] = v.x;
+                dst[4 * u + 1] = v.y;
+                dst[4 * u + 2] = v.z;
+                dst[4 * u + 3] = v.w;
+            }
+        };
+        if (w0 < w1) {
+            load_chunk(work[w0], 0, qw[0]);
+            load_chunk(work[w0], 1, qw[1]);
+        }
+        int tl = 0;
+        for (int wi = w0; wi < w1; ++wi, ++tl) {
+            const PairTile tile = work[wi];
+            const int acc_i = tl & 1;
+            const uint32_t ause = (uint32_t)(tl >> 1);
+            const bool ok = goacd::mbar_wait_bounded(&tfull[acc_i], ause & 1, WAIT_LIMIT) && !*abort_flag;
+            if (!ok && lane == 0) goacd::report(err, GOAC_ERR_TIMEOUT, goac::SITE_TC_EPILOGUE, tl);
+            goacd::tc_fence_after();
+            double s0 = 0.0, s1 = 0.0;              // panels 2P and 2P + 1
+#pragma unroll
+            for (int c = 0; c < TN / 32; ++c) {
+                if (c + 2 < TN / 32) load_chunk(tile, c + 2, qw[c + 2]);
+                uint32_t r[32];
+                goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
+                                              (uint32_t)(c * 32),
+                                          r);
+                goacd::tmem_ld_wait();
+                if (c == TN / 32 - 1) {
+                    // the accumulator rows have been read: the MMA may start the tile after next in them
+                    goacd::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0) goacd::mbar_arrive(&tempty[acc_i]);
+                        else goacd::mbar_arrive_cluster(goacd::mapa_shared(goacd::smem_u32(&tempty[acc_i]), 0));
+                    }
+                }
+                float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    const uint32_t w = qw[c][j / 2];
+                    a4[(j / 2) & 3] = fmaf(__uint_as_float(w << 16), __uint_as_float(r[j]), a4[(j / 2) & 3]);
+                    a4[(j / 2) & 3] = fmaf(__uint_as_float(w & 0xffff0000u), __uint_as_float(r[j + 1]), a4[(j / 2) & 3]);
+                }
+                const double cs = (double)((a4[0] + a4[1]) + (a4[2] + a4[3]));
+                if (c < TN / 64) s0 += cs;
+                else s1 += cs;
+            }
+            if (wi + 1 < w1) {
+                load_chunk(work[wi + 1], 0, qw[0]);
+                load_chunk(work[wi + 1], 1, qw[1]);
+            }
+            if (ok) {
+                const long b = (long)tile.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
+                partial[(long)tile.slot0 * Bpad + b] = s0;
+                if (tile.slot1 >= 0) partial[(long)tile.slot1 * Bpad + b] = s1;
+            }
+        }
+    }
+    goacd::tc_fence_before();
+    __syncthreads();
+    goacd::cluster_sync();                      // no CTA leaves while its peer may still reach its memory
+    if (warp == 2) {
+        goacd::tc_fence_after();
+        goacd::tmem_dealloc_pair(tmem, 2 * TN);
+    }
+}
+
 // Exact form with the configurations on the tensor-memory lanes: a tile is
 // 128 configurations (M, rows of Q^T) x one pair-panel of 256 sites (N, the
 // rows 256 P .. 256 P + 255 of digit t of J', i.e. panels 2P and 2P + 1) over
@@ -2122,6 +2339,37 @@ goac_status launch_exact_ct(goac_problem* p, const CUtensorMap& mq, const CUtens
     return GOAC_OK;
 }
 
+// The split forms' CTA-pair kernel (BF16 terms): pair_schedule's work units
+// (one digit index) over the resident clusters, then k_finish_tc.
+template <int T>
+goac_status launch_tc_pair(goac_problem* p, const CUtensorMap& mq, const CUtensorMap& mj, int Bpad, int B, int kc,
+                           double* part)
+{
+    using Cfg = TpCfg<T>;
+    static_assert(Cfg::SMEM <= PX_SMEM, "the resident-pair count is taken with the exact pair kernel's memory");
+    static std::atomic<uint64_t> attr_done{0};
+    goac_status rc = smem_attr_once((const void*)k_score_tc_pair<T>, Cfg::SMEM, attr_done, p->ctx->device);
+    if (rc) return rc;
+    const int ld = p->Nv_pad;
+    const int nbm = ld / TC_M, nbn = (B + 255) / 256, npp = (nbm + 1) / 2;
+    long ntiles = 0;
+    for (int P = 0; P < npp; ++P) {
+        const int span = 2 * nbm - 4 * P;
+        ntiles += (long)(kc > 0 ? (span + 2 * kc - 1) / (2 * kc) : 1) * nbn;
+    }
+    const int npairs = (int)std::min<long>(ntiles, max_pairs(p));
+    const PairTile* work = nullptr;
+    const int* starts = nullptr;
+    const int* pslot = nullptr;
+    rc = pair_schedule(p->sched, p->ctx->stream, nbm, nbn, 1, kc, npairs, &work, &starts, &pslot);
+    if (rc) return rc;
+    goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
+    goac::launch_pdl(k_score_tc_pair<T>, 2 * npairs, 192, Cfg::SMEM, p->ctx->stream, mq, mj, work, starts, ld,
+                     (const __nv_bfloat16*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+    GOAC_LAUNCH_CHECK("k_score_tc_pair");
+    return GOAC_OK;
+}
+
 }  // namespace
 
 namespace goac {
@@ -2353,13 +2601,14 @@ goac_status phi_exact(goac_problem* p, const int8_t* species, int B, double* E_o
 
 // Tile shape of the scoring kernels for (precision, padded batch): the one
 // goac_score_autotune or goac_score_set_shape stored, else whole panel ranges
-// in tiles of 256 sites x 256 configurations on CTA pairs for the exact form
-// and of 128 sites x 256 configurations for the split forms.
+// in tiles of 256 sites x 256 configurations on CTA pairs for the exact and
+// BF16 forms and of 128 sites x 256 configurations for the TF32 forms.
 static void pick_shape(const goac_problem* p, int precision, int Bpad, int* TM, int* TN, int* kc)
 {
     const auto it = p->tile_shape.find(std::make_pair(precision, Bpad));
     const bool has = it != p->tile_shape.end();
-    *TM = has ? std::get<0>(it->second) : (precision == GOAC_PREC_EXACT ? 2 * TC_M : TC_M);
+    const bool pairs = precision == GOAC_PREC_EXACT || precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3;
+    *TM = has ? std::get<0>(it->second) : (pairs ? 2 * TC_M : TC_M);
     *TN = has ? std::get<1>(it->second) : TC_N;
     *kc = has ? std::get<2>(it->second) : 0;
 }
@@ -2443,7 +2692,8 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     const int eb = tf32 ? 4 : 2;
     int TM = 0, TN = 0, kc = 0;
     pick_shape(p, precision, Bpad, &TM, &TN, &kc);
-    const int nslots = tc_tile_count(ld / TC_M, (B + TN - 1) / TN, 1, kc).y;
+    const bool pair = TM == 2 * TC_M;       // BF16 terms on CTA pairs
+    const int nslots = pair ? pair_slot_count(ld / TC_M, kc) : tc_tile_count(ld / TC_M, (B + TN - 1) / TN, 1, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * eb);
     if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * Bpad + Bpad));
     if (rc) return rc;
@@ -2464,11 +2714,15 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     void* abase = tf32 ? (void*)p->J_tf32 : (void*)p->J_bf16;
     const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     rc = make_map(&ma, abase, dt, eb, ld, (long)terms_alloc * ld, ld, TC_M);
-    if (!rc) rc = make_map(&mb, p->qt.ptr, dt, eb, ld, Bpad, ld, TN);
+    if (!rc) rc = make_map(&mb, p->qt.ptr, dt, eb, ld, Bpad, ld, pair ? PX_HN : TN);
     if (rc) return rc;
     double* part = (double*)p->partial.ptr;
-    rc = TN == TC_NS ? launch_split<TC_NS>(p, precision, ma, mb, Bpad, B, kc, part)
-                     : launch_split<TC_N>(p, precision, ma, mb, Bpad, B, kc, part);
+    if (pair)   // M: each CTA's 128 configurations of Q^T; N: each CTA's 128 rows of every term of J'
+        rc = precision == GOAC_PREC_BF16X3 ? launch_tc_pair<3>(p, mb, ma, Bpad, B, kc, part)
+                                           : launch_tc_pair<2>(p, mb, ma, Bpad, B, kc, part);
+    else
+        rc = TN == TC_NS ? launch_split<TC_NS>(p, precision, ma, mb, Bpad, B, kc, part)
+                         : launch_split<TC_N>(p, precision, ma, mb, Bpad, B, kc, part);
     if (rc) return rc;
     goac::launch_pdl(k_finish_tc, (B + 255) / 256, 256, 0, st, part, nslots, Bpad, B, p->E_const, lin, E_out);
     GOAC_LAUNCH_CHECK("k_finish_tc");
@@ -2494,8 +2748,10 @@ extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, 
         !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 || ksplit > 65535)
         return goac::fail(GOAC_ERR_INVALID_ARG,
                           "goac_score_set_shape: B >= 1, tile_m 0, 128 or 256, tile_n 0, 128 or 256, ksplit 0..65535");
-    if (tile_m == 256 && precision != GOAC_PREC_EXACT)
-        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: 256-site tiles need EXACT");
+    if (tile_m == 256 && !(precision == GOAC_PREC_EXACT ||
+                           ((precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3) && tile_n != 128)))
+        return goac::fail(GOAC_ERR_INVALID_ARG,
+                          "goac_score_set_shape: 256-site tiles need EXACT, or BF16X2 / BF16X3 with tile_n 256");
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
     if (tile_m == 0 && tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
@@ -2521,10 +2777,12 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
     const int nbm = p->Nv_pad / 128;
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
-    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles (CTA pairs, configurations on the TMEM
-    // lanes) for the exact form
+    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles on CTA pairs for the exact and BF16 forms, and
+    // the one-CTA configuration-lane tiles for the exact form
     const int shapes[4][2] = {{128, 256}, {128, 128}, {256, 256}, {256, 128}};
-    const int nshapes = precision == GOAC_PREC_EXACT ? 4 : 2;
+    const int nshapes = precision == GOAC_PREC_EXACT                                       ? 4
+                        : precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3 ? 3
+                                                                                          : 2;
     const int kcs[5] = {0, 16, 8, 4, 2};
     int best_tm = 0, best_tn = 0, best_kc = 0;
     float best = 0.0f;
