@@ -258,9 +258,9 @@ def _kernel_hash(form="bf16x2") -> str:
     src = open(os.path.join(csrc, "score_tc.cu")).read()
     if form == "exact_pair":
         a = src.index("template <bool SPLIT>\n__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
-        b = src.index("// Split forms (BF16 terms) on CTA pairs")
-    elif form in ("bf16x2_pair", "bf16x3_pair"):
-        a = src.index("// Split forms (BF16 terms) on CTA pairs")
+        b = src.index("// Split forms (BF16 or TF32 terms) on CTA pairs")
+    elif form.endswith("_pair"):
+        a = src.index("// Split forms (BF16 or TF32 terms) on CTA pairs")
         b = src.index("// Exact form with the configurations on the tensor-memory lanes")
     elif form == "exact_ct":
         a = src.index("// Exact form with the configurations on the tensor-memory lanes")
@@ -354,7 +354,8 @@ def _roofline(form, terms, kern_ms, kern_n, N, B, tile_m=128, split=True, tile_n
     kernel = (f"k_score_exact_pair<{str(split).lower()}>" if pair else
               f"k_score_exact_ct<{str(split).lower()}>" if ct else
               f"k_score_exact<256, {str(split).lower()}>") if form == "exact" else \
-        f"k_score_tc_pair<{terms}>" if pair else f"k_score_tc<{terms},{'true' if tf32 else 'false'},256>"
+        f"k_score_tc_pair<{terms},{'true' if tf32 else 'false'}>" if pair else \
+        f"k_score_tc<{terms},{'true' if tf32 else 'false'},256>"
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": _traffic(f"{form}_pair" if pair else "exact_ct" if ct else form), "kernel": kernel,
             "kernel_ms": kern_ms,
@@ -606,7 +607,7 @@ def run_ours(args, world, rank, local):
                                           "k_chunk_blocks": shapes[form][2],
                                           "chosen_by": "fixed (--tile)" if form in fixed else
                                           f"goac_score_autotune (CUDA events over "
-                                          f"{(4 if form == 'exact' else 3 if form.startswith('bf16') else 2) * sum(k < (prob.N + 127) // 128 for k in (0, 16, 8, 4, 2))} shapes)"},
+                                          f"{(4 if form == 'exact' else 3) * sum(k < (prob.N + 127) // 128 for k in (0, 16, 8, 4, 2))} shapes)"},
                            "l2": "256 MB buffer written between steps (outside the step events)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

@@ -162,8 +162,8 @@ goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B,
 /* Tile shape of the tensor-core scoring kernels (no counterpart in the       *
  * paper; the results of EXACT do not depend on it, those of the split forms  *
  * change only by FP32 rounding).  A tile covers tile_m sites x tile_n        *
- * configurations: tile_m 128 (one CTA) or 256 (EXACT, BF16X2, BF16X3: with  *
- * tile_n 256 a pair of CTAs on one TPC issuing M = 256 tcgen05 MMAs over the *
+ * configurations: tile_m 128 (one CTA) or 256 (every form with tile_n 256:   *
+ * a pair of CTAs on one TPC issuing M = 256 tcgen05 MMAs over the            *
  * configurations, each CTA loading its own 128 configurations and its own    *
  * panel's rows of J', each epilogue thread weighting one configuration's 256 *
  * site sums by its charges; EXACT only, with tile_n 128: one CTA with the    *
@@ -175,8 +175,8 @@ goac_status goac_score(goac_problem* prob, const int8_t* species_dev, int32_t B,
  * (all 0: the default, whole ranges in 256 x 256 tiles on CTA pairs for EXACT *
  * and the BF16 forms, 128 x 256 tiles for the TF32 forms);                    *
  * goac_score_autotune times                                                   *
- * every shape in {128 x 256, 128 x 128, 256 x 256 (EXACT, BF16X2, BF16X3),   *
- * 256 x 128 (EXACT)} x {0, 16, 8, 4, 2}                                       *
+ * every shape in {128 x 256, 128 x 128, 256 x 256, 256 x 128 (EXACT)} x     *
+ * {0, 16, 8, 4, 2}                                                            *
  * on species_dev (B x Nv), CUDA events on the context stream, stores the      *
  * fastest for later goac_score calls with that precision and padded B, and    *
  * returns it (outputs nullable; ms per scoring call).  Host-side store;       *

@@ -242,9 +242,9 @@ class Problem:
 
     def score_set_shape(self, B: int, precision="bf16x2", tile_n: int = 0, ksplit: int = 0, tile_m: int = 0):
         """Tile shape for scoring B configurations in a tensor-core form (all 0 = default;
-        tile_m 256: CTA pairs with tile_n 256 for the exact and BF16 forms, one CTA
-        with the configurations on the tensor-memory lanes with tile_n 128 for the
-        exact form)."""
+        tile_m 256: CTA pairs with tile_n 256 for every form, one CTA with the
+        configurations on the tensor-memory lanes with tile_n 128 for the exact
+        form)."""
         _check(lib.goac_score_set_shape(self.handle, _prec(precision), int(B), int(tile_m), int(tile_n), int(ksplit)),
                "goac_score_set_shape")
 

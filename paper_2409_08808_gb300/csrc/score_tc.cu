@@ -1053,15 +1053,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     }
 }
 
-// Split forms (BF16 terms) on CTA pairs, laid out as k_score_exact_pair: a
-// tile is 256 configurations (128 on each CTA's tensor-memory lanes) x one
-// pair-panel of 256 sites, M = 256 MMAs issued by the even CTA; each CTA loads
-// its own 128 configurations' rows of Q^T and, for each of the T terms of J',
-// its panel's 128 rows, and the T terms accumulate into the same FP32 tile.
-// The epilogue thread that owns configuration b forms q_b . Phi over each
-// panel's 128 sites by itself: per 32-site chunk an FP32 sum of q Phi (the
-// charges read from the BF16 row of Q^T two chunks ahead), the chunks added in
-// FP64.  Slots are pair_schedule's (one per panel and k-chunk, no digit index).
+// Split forms (BF16 or TF32 terms) on CTA pairs, laid out as
+// k_score_exact_pair: a tile is 256 configurations (128 on each CTA's
+// tensor-memory lanes) x one pair-panel of 256 sites, M = 256 MMAs issued by
+// the even CTA; each CTA loads its own 128 configurations' rows of Q^T and,
+// for each of the T terms of J', its panel's 128 rows (128-byte rows: 64 BF16
+// or 32 TF32 k-elements per stage), and the T terms accumulate into the same
+// FP32 tile.  The epilogue thread that owns configuration b forms q_b . Phi
+// over each panel's 128 sites by itself: per 32-site chunk an FP32 sum of
+// q Phi (the charges read from the BF16 or FP32 row of Q^T two chunks ahead,
+// one for FP32),
+// the chunks added in FP64.  Slots are pair_schedule's (one per panel and
+// k-chunk, no digit index).
 template <int T>
 struct TpCfg {
     static constexpr int STAGE = (1 + T) * A_TILE;                  // Q^T rows, then T x J' rows
@@ -1069,16 +1072,29 @@ struct TpCfg {
     static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-template <int T>
+// D (+)= A * B^T over the CTA pair, kind::tf32 (operand layout as mma_f16_pair).
+__device__ __forceinline__ void mma_tf32_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+template <int T, bool TF32>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     k_score_tc_pair(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmJ,
                     const PairTile* __restrict__ work, const int* __restrict__ work_start, int ld,
-                    const __nv_bfloat16* __restrict__ qt, double* __restrict__ partial, int Bpad,
-                    int* __restrict__ err)
+                    const void* __restrict__ qt, double* __restrict__ partial, int Bpad, int* __restrict__ err)
 {
     using Cfg = TpCfg<T>;
     constexpr int STAGES = Cfg::STAGES, STAGE = Cfg::STAGE;
     constexpr int TN = 256;                     // sites per tile: TMEM columns
+    constexpr int KE = TF32 ? 32 : 64;          // k elements per 128-byte row
+    constexpr int QB = TF32 ? 4 : 2;            // bytes of one charge in Q^T
     static_assert(STAGES * STAGE + 1024 + 256 <= Cfg::SMEM, "stages exceed the dynamic shared memory");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1140,10 +1156,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     uint8_t* st = smem + s * STAGE;
                     const uint32_t fbar = goacd::mapa_shared(goacd::smem_u32(&full[s]), 0);
                     if (rank == 0) goacd::mbar_arrive_expect_tx(&full[s], 2 * STAGE);
-                    goacd::tma_load_2d_pair(st, &tmQ, fbar, kb * 64, q0);
+                    goacd::tma_load_2d_pair(st, &tmQ, fbar, kb * KE, q0);
 #pragma unroll
                     for (int t = 0; t < T; ++t)
-                        goacd::tma_load_2d_pair(st + (1 + t) * A_TILE, &tmJ, fbar, kb * 64, t * ld + j0);
+                        goacd::tma_load_2d_pair(st + (1 + t) * A_TILE, &tmJ, fbar, kb * KE, t * ld + j0);
                 }
             }
             if (*abort_flag && rank == 0)
@@ -1156,7 +1172,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer (the even CTA) ----------------
         if (lane == 0 && rank == 0) {
-            constexpr uint32_t idesc = goacd::idesc_f32acc(1u, 2 * PX_HN, TN);   // BF16, M = 256
+            constexpr uint32_t idesc = goacd::idesc_f32acc(TF32 ? 2u : 1u, 2 * PX_HN, TN);   // M = 256
             int it = 0, tl = 0;
             for (int wi = w0; wi < w1; ++wi, ++tl) {
                 const PairTile tile = work[wi];
@@ -1182,10 +1198,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 #pragma unroll
                     for (int t = 0; t < T; ++t)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            goacd::mma_f16_pair(d_tmem, goacd::sdesc_k128(a0 + kk * 32),
-                                                goacd::sdesc_k128(a0 + (1 + t) * A_TILE + kk * 32), idesc,
-                                                (kb != tile.kb0 || t != 0 || kk != 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = goacd::sdesc_k128(a0 + kk * 32);
+                            const uint64_t bd = goacd::sdesc_k128(a0 + (1 + t) * A_TILE + kk * 32);
+                            const uint32_t acc = (kb != tile.kb0 || t != 0 || kk != 0) ? 1u : 0u;
+                            if (TF32) mma_tf32_pair(d_tmem, ad, bd, idesc, acc);
+                            else goacd::mma_f16_pair(d_tmem, ad, bd, idesc, acc);
+                        }
                     goacd::mma_commit_pair(&empty[s], 0x3);
                 }
                 goacd::mma_commit_pair(&tfull[acc_i], 0x3);
@@ -1195,13 +1214,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     } else {
         // ---------------- epilogue: warps 2..5 of both CTAs, one configuration per thread ----------------
         const int lg = warp & 3;
-        uint32_t qw[TN / 32][16];               // BF16 charge pairs per 32-site chunk (a few live at a time)
-        auto load_chunk = [&](const PairTile& tq, int c, uint32_t (&dst)[16]) {
+        constexpr int QW = 32 * QB / 4;             // words of one 32-site chunk's charges
+        constexpr int PF = TF32 ? 1 : 2;            // chunks loaded ahead (FP32 charges take twice the registers)
+        uint32_t qw[TN / 32][QW];               // per 32-site chunk (a few live at a time)
+        auto load_chunk = [&](const PairTile& tq, int c, uint32_t (&dst)[QW]) {
             const long b = (long)tq.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
-            const uint4* src = (const uint4*)(qt + b * ld + 2 * tq.P * TC_M + c * 32);
+            const uint4* src =
+                (const uint4*)((const uint8_t*)qt + (b * ld + 2 * tq.P * TC_M + c * 32) * QB);
             const bool in_row = c < TN / 64 || tq.slot1 >= 0;   // else past the end of the row
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < QW / 4; ++u) {
                 const uint4 v = in_row ? __ldg(src + u) : make_uint4(0u, 0u, 0u, 0u);
                 dst[4 * u] = v.x;
                 dst[4 * u + 1] = v.y;
@@ -1209,10 +1231,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 dst[4 * u + 3] = v.w;
             }
         };
-        if (w0 < w1) {
-            load_chunk(work[w0], 0, qw[0]);
-            load_chunk(work[w0], 1, qw[1]);
-        }
+        if (w0 < w1)
+#pragma unroll
+            for (int c = 0; c < PF; ++c) load_chunk(work[w0], c, qw[c]);
         int tl = 0;
         for (int wi = w0; wi < w1; ++wi, ++tl) {
             const PairTile tile = work[wi];
@@ -1224,7 +1245,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             double s0 = 0.0, s1 = 0.0;              // panels 2P and 2P + 1
 #pragma unroll
             for (int c = 0; c < TN / 32; ++c) {
-                if (c + 2 < TN / 32) load_chunk(tile, c + 2, qw[c + 2]);
+                if (c + PF < TN / 32) load_chunk(tile, c + PF, qw[c + PF]);
                 uint32_t r[32];
                 goacd::tmem_ld_32x32b_x32(tmem + (uint32_t)(acc_i * TN) + ((uint32_t)(lg * 32) << 16) +
                                               (uint32_t)(c * 32),
@@ -1242,18 +1263,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
-                    const uint32_t w = qw[c][j / 2];
-                    a4[(j / 2) & 3] = fmaf(__uint_as_float(w << 16), __uint_as_float(r[j]), a4[(j / 2) & 3]);
-                    a4[(j / 2) & 3] = fmaf(__uint_as_float(w & 0xffff0000u), __uint_as_float(r[j + 1]), a4[(j / 2) & 3]);
+                    // BF16 pairs widen to FP32 by position; FP32 charges are taken as they are
+                    const float q0 = TF32 ? __uint_as_float(qw[c][j]) : __uint_as_float(qw[c][j / 2] << 16);
+                    const float q1 = TF32 ? __uint_as_float(qw[c][j + 1]) : __uint_as_float(qw[c][j / 2] & 0xffff0000u);
+                    a4[(j / 2) & 3] = fmaf(q0, __uint_as_float(r[j]), a4[(j / 2) & 3]);
+                    a4[(j / 2) & 3] = fmaf(q1, __uint_as_float(r[j + 1]), a4[(j / 2) & 3]);
                 }
                 const double cs = (double)((a4[0] + a4[1]) + (a4[2] + a4[3]));
                 if (c < TN / 64) s0 += cs;
                 else s1 += cs;
             }
-            if (wi + 1 < w1) {
-                load_chunk(work[wi + 1], 0, qw[0]);
-                load_chunk(work[wi + 1], 1, qw[1]);
-            }
+            if (wi + 1 < w1)
+#pragma unroll
+                for (int c = 0; c < PF; ++c) load_chunk(work[wi + 1], c, qw[c]);
             if (ok) {
                 const long b = (long)tile.n * 256 + (int)rank * PX_HN + lg * 32 + lane;
                 partial[(long)tile.slot0 * Bpad + b] = s0;
@@ -2161,17 +2183,16 @@ goac_status launch_exact(goac_problem* p, const CUtensorMap& ma, const CUtensorM
 // tile n, k-chunk, digit t) longest first over the pairs; panel I's k-chunk
 // slots are numbered panel by panel (pslot[I] .. pslot[I+1]) as for the
 // one-CTA kernel, with panel 2P + 1 chunked like its pair-panel.
-goac_status pair_schedule(TcSched& sc, cudaStream_t stream, int nbm, int nbn, int T, int kc, int npairs,
-                          const PairTile** work,
-                          const int** starts, const int** pslot)
+goac_status pair_schedule(TcSched& sc, cudaStream_t stream, int nbm, int nbn, int T, int kc, int kbm, int npairs,
+                          const PairTile** work, const int** starts, const int** pslot)
 {
     if (nbm <= 0 || nbm >= (1 << 18) || nbn <= 0 || nbn >= (1 << 26) || npairs <= 0 || npairs >= (1 << 19) ||
-        T < 1 || T > 15 || kc < 0 || kc >= (1 << 16))
+        T < 1 || T > 15 || kc < 0 || kc >= (1 << 16) || kbm < 1 || kbm > 15)
         return goac::fail(GOAC_ERR_INVALID_ARG, "pair schedule: shape out of range");
     const uint64_t k0 = ((uint64_t)nbm << 46) | ((uint64_t)nbn << 20) | (uint64_t)npairs;
-    const uint64_t k1 = (1ull << 40) | ((uint64_t)T << 24) | ((uint64_t)kc << 8) | 2ull;
+    const uint64_t k1 = (1ull << 40) | ((uint64_t)T << 24) | ((uint64_t)kc << 8) | (uint64_t)kbm;
     if (sc.key[0] != k0 || sc.key[1] != k1) {
-        const int kbm = 2, nkb = nbm * kbm, npp = (nbm + 1) / 2;
+        const int nkb = nbm * kbm, npp = (nbm + 1) / 2;
         std::vector<int> ps(nbm + 1, 0), nch(npp, 0);
         for (int P = 0; P < npp; ++P) {
             const int span = nkb - 2 * P * kbm;
@@ -2291,7 +2312,7 @@ goac_status launch_exact_pair(goac_problem* p, const CUtensorMap& ma, const CUte
     const PairTile* work = nullptr;
     const int* starts = nullptr;
     const int* pslot = nullptr;
-    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, npairs, &work, &starts, &pslot);
+    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, 2, npairs, &work, &starts, &pslot);
     if (rc) return rc;
     {
         goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
@@ -2325,7 +2346,7 @@ goac_status launch_exact_ct(goac_problem* p, const CUtensorMap& mq, const CUtens
     const PairTile* work = nullptr;
     const int* starts = nullptr;
     const int* pslot = nullptr;
-    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, grid, &work, &starts, &pslot);
+    rc = pair_schedule(p->sched_ex, p->ctx->stream, nbm, nbn, T, kc, 2, grid, &work, &starts, &pslot);
     if (rc) return rc;
     {
         goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
@@ -2339,16 +2360,17 @@ goac_status launch_exact_ct(goac_problem* p, const CUtensorMap& mq, const CUtens
     return GOAC_OK;
 }
 
-// The split forms' CTA-pair kernel (BF16 terms): pair_schedule's work units
-// (one digit index) over the resident clusters, then k_finish_tc.
-template <int T>
+// The split forms' CTA-pair kernel: pair_schedule's work units (one digit
+// index; 2 k-blocks per 128 columns in BF16, 4 in TF32) over the resident
+// clusters, then k_finish_tc.
+template <int T, bool TF32>
 goac_status launch_tc_pair(goac_problem* p, const CUtensorMap& mq, const CUtensorMap& mj, int Bpad, int B, int kc,
                            double* part)
 {
     using Cfg = TpCfg<T>;
     static_assert(Cfg::SMEM <= PX_SMEM, "the resident-pair count is taken with the exact pair kernel's memory");
     static std::atomic<uint64_t> attr_done{0};
-    goac_status rc = smem_attr_once((const void*)k_score_tc_pair<T>, Cfg::SMEM, attr_done, p->ctx->device);
+    goac_status rc = smem_attr_once((const void*)k_score_tc_pair<T, TF32>, Cfg::SMEM, attr_done, p->ctx->device);
     if (rc) return rc;
     const int ld = p->Nv_pad;
     const int nbm = ld / TC_M, nbn = (B + 255) / 256, npp = (nbm + 1) / 2;
@@ -2361,11 +2383,11 @@ goac_status launch_tc_pair(goac_problem* p, const CUtensorMap& mq, const CUtenso
     const PairTile* work = nullptr;
     const int* starts = nullptr;
     const int* pslot = nullptr;
-    rc = pair_schedule(p->sched, p->ctx->stream, nbm, nbn, 1, kc, npairs, &work, &starts, &pslot);
+    rc = pair_schedule(p->sched, p->ctx->stream, nbm, nbn, 1, kc, TF32 ? 4 : 2, npairs, &work, &starts, &pslot);
     if (rc) return rc;
     goac::KTimer kt(p->ctx, goac::KID_SCORE_TC, p->ctx->stream);
-    goac::launch_pdl(k_score_tc_pair<T>, 2 * npairs, 192, Cfg::SMEM, p->ctx->stream, mq, mj, work, starts, ld,
-                     (const __nv_bfloat16*)p->qt.ptr, part, Bpad, p->ctx->d_err);
+    goac::launch_pdl(k_score_tc_pair<T, TF32>, 2 * npairs, 192, Cfg::SMEM, p->ctx->stream, mq, mj, work, starts, ld,
+                     (const void*)p->qt.ptr, part, Bpad, p->ctx->d_err);
     GOAC_LAUNCH_CHECK("k_score_tc_pair");
     return GOAC_OK;
 }
@@ -2692,7 +2714,7 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     const int eb = tf32 ? 4 : 2;
     int TM = 0, TN = 0, kc = 0;
     pick_shape(p, precision, Bpad, &TM, &TN, &kc);
-    const bool pair = TM == 2 * TC_M;       // BF16 terms on CTA pairs
+    const bool pair = TM == 2 * TC_M;       // on CTA pairs
     const int nslots = pair ? pair_slot_count(ld / TC_M, kc) : tc_tile_count(ld / TC_M, (B + TN - 1) / TN, 1, kc).y;
     rc = ensure(p->qt, (size_t)Bpad * ld * eb);
     if (!rc) rc = ensure(p->partial, sizeof(double) * ((size_t)nslots * Bpad + Bpad));
@@ -2717,10 +2739,14 @@ goac_status score_tc(goac_problem* p, const int8_t* species, int B, int precisio
     if (!rc) rc = make_map(&mb, p->qt.ptr, dt, eb, ld, Bpad, ld, pair ? PX_HN : TN);
     if (rc) return rc;
     double* part = (double*)p->partial.ptr;
-    if (pair)   // M: each CTA's 128 configurations of Q^T; N: each CTA's 128 rows of every term of J'
-        rc = precision == GOAC_PREC_BF16X3 ? launch_tc_pair<3>(p, mb, ma, Bpad, B, kc, part)
-                                           : launch_tc_pair<2>(p, mb, ma, Bpad, B, kc, part);
-    else
+    if (pair) {  // M: each CTA's 128 configurations of Q^T; N: each CTA's 128 rows of every term of J'
+        switch (precision) {
+            case GOAC_PREC_TF32: rc = launch_tc_pair<1, true>(p, mb, ma, Bpad, B, kc, part); break;
+            case GOAC_PREC_TF32X2: rc = launch_tc_pair<2, true>(p, mb, ma, Bpad, B, kc, part); break;
+            case GOAC_PREC_BF16X3: rc = launch_tc_pair<3, false>(p, mb, ma, Bpad, B, kc, part); break;
+            default: rc = launch_tc_pair<2, false>(p, mb, ma, Bpad, B, kc, part); break;
+        }
+    } else
         rc = TN == TC_NS ? launch_split<TC_NS>(p, precision, ma, mb, Bpad, B, kc, part)
                          : launch_split<TC_N>(p, precision, ma, mb, Bpad, B, kc, part);
     if (rc) return rc;
@@ -2748,10 +2774,8 @@ extern "C" goac_status goac_score_set_shape(goac_problem* p, int32_t precision, 
         !(tile_n == 0 || tile_n == 128 || tile_n == 256) || ksplit < 0 || ksplit > 65535)
         return goac::fail(GOAC_ERR_INVALID_ARG,
                           "goac_score_set_shape: B >= 1, tile_m 0, 128 or 256, tile_n 0, 128 or 256, ksplit 0..65535");
-    if (tile_m == 256 && !(precision == GOAC_PREC_EXACT ||
-                           ((precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3) && tile_n != 128)))
-        return goac::fail(GOAC_ERR_INVALID_ARG,
-                          "goac_score_set_shape: 256-site tiles need EXACT, or BF16X2 / BF16X3 with tile_n 256");
+    if (tile_m == 256 && precision != GOAC_PREC_EXACT && tile_n == 128)
+        return goac::fail(GOAC_ERR_INVALID_ARG, "goac_score_set_shape: 256 x 128 tiles need EXACT");
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
     if (tile_m == 0 && tile_n == 0 && ksplit == 0) p->tile_shape.erase(key);
@@ -2777,12 +2801,10 @@ extern "C" goac_status goac_score_autotune(goac_problem* p, const int8_t* specie
     const int nbm = p->Nv_pad / 128;
     const int Bpad = ((B + 255) / 256) * 256;
     const auto key = std::make_pair((int)precision, Bpad);
-    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles on CTA pairs for the exact and BF16 forms, and
-    // the one-CTA configuration-lane tiles for the exact form
+    // candidates: {tile_m, tile_n} x k-chunks; 256-site tiles on CTA pairs for every form, and the one-CTA
+    // configuration-lane tiles for the exact form
     const int shapes[4][2] = {{128, 256}, {128, 128}, {256, 256}, {256, 128}};
-    const int nshapes = precision == GOAC_PREC_EXACT                                       ? 4
-                        : precision == GOAC_PREC_BF16X2 || precision == GOAC_PREC_BF16X3 ? 3
-                                                                                          : 2;
+    const int nshapes = precision == GOAC_PREC_EXACT ? 4 : 3;
     const int kcs[5] = {0, 16, 8, 4, 2};
     int best_tm = 0, best_tn = 0, best_kc = 0;
     float best = 0.0f;

@@ -2,7 +2,7 @@
 
 A tile covers 128 sites x 128 or 256 configurations, over the whole column
 range of its row panel or over chunks of it (each chunk adds a partial row-dot
-sum); the exact and BF16 forms also have 256-site tiles on CTA pairs with 256
+sum); every form also has 256-site tiles on CTA pairs with 256
 configurations, and the exact form one CTA with 128 configurations on the
 tensor-memory lanes (its pair-panel's first two k-blocks run as 128-site MMAs,
 last).  The exact integer-digit form must give the same energies bit for bit in
@@ -88,12 +88,11 @@ def test_split_forms_within_bound_in_every_shape(ctx, form):
         elif kc == 0:
             # the same k-order per tile: only the configuration tiling differs
             assert np.array_equal(E, base), (tn, kc)
-    if form.startswith("bf16"):
-        # CTA pairs (256 sites x 256 configurations; the last pair-panel of this cell has one panel)
-        for kc in (0, 8, 1):
-            gp.score_set_shape(B, form, 256, kc, tile_m=256)
-            E = gp.score(pop, form).cpu().numpy()
-            assert np.all(np.abs(E[rows] - Eo) <= tol), (256, kc)
+    # CTA pairs (256 sites x 256 configurations; the last pair-panel of this cell has one panel)
+    for kc in (0, 8, 1):
+        gp.score_set_shape(B, form, 256, kc, tile_m=256)
+        E = gp.score(pop, form).cpu().numpy()
+        assert np.all(np.abs(E[rows] - Eo) <= tol), (256, kc)
     gp.score_set_shape(B, form, 0, 0)
 
 
@@ -110,7 +109,7 @@ def test_autotuner_choice(cubic, form, B):
     ref = gp.score(pop, form).clone()
     tm, tn, kc, ms = gp.score_autotune(pop, form)
     assert tn in (128, 256) and kc in (0, 16, 8, 4, 2) and ms > 0
-    assert tm == 128 or (tm == 256 and (form == "exact" or (form.startswith("bf16") and tn == 256)))
+    assert tm == 128 or (tm == 256 and (form == "exact" or tn == 256))
     E = gp.score(pop, form)
     if form == "exact":
         assert torch.equal(E, ref)
@@ -132,7 +131,8 @@ def test_set_shape_rejects_bad_shapes(cubic):
                  (16, "f32", 0, 4)]:
         with pytest.raises(g.GoacError):
             gp.score_set_shape(*args)
-    for kw in [dict(tile_m=64), dict(tile_m=256, precision="tf32x2"), dict(tile_m=256, tile_n=128, precision="bf16x2")]:
+    for kw in [dict(tile_m=64), dict(tile_m=256, tile_n=128, precision="tf32x2"),
+               dict(tile_m=256, tile_n=128, precision="bf16x2")]:
         args = dict(B=16, precision="exact", tile_n=256, ksplit=0)
         args.update(kw)
         with pytest.raises(g.GoacError):

@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("form", ["bf16x2", "exact", "exact_pair"])
+@pytest.mark.parametrize("form", ["bf16x2", "exact", "exact_pair", "bf16x2_pair"])
 def test_scoring_profile_matches_kernel_source(form):
     sys.path.insert(0, ROOT)
     import bench
