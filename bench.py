@@ -256,8 +256,12 @@ def _kernel_hash(form="bf16x2") -> str:
     while it is unchanged."""
     csrc = os.path.join(ROOT, "paper_2409_08808_gb300", "csrc")
     src = open(os.path.join(csrc, "score_tc.cu")).read()
+    def template_of(name):
+        # the template line that opens the kernel's definition (its launch bounds may change)
+        return src.rindex("template <", 0, src.index(f"\n    {name}("))
+
     if form == "exact_pair":
-        a = src.index("template <bool SPLIT>\n__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)\n    k_score_exact_pair(")
+        a = template_of("k_score_exact_pair")
         b = src.index("// Split forms (BF16 or TF32 terms) on CTA pairs")
     elif form.endswith("_pair"):
         a = src.index("// Split forms (BF16 or TF32 terms) on CTA pairs")
@@ -266,7 +270,7 @@ def _kernel_hash(form="bf16x2") -> str:
         a = src.index("// Exact form with the configurations on the tensor-memory lanes")
         b = src.index("// Per 128-row panel I of the symmetric operand")
     elif form == "exact":
-        a = src.index("template <int TN, bool SPLIT>\n__global__ void __launch_bounds__(192, SPLIT ? 1 : 2)\n    k_score_exact(")
+        a = template_of("k_score_exact")
         b = src.index("// Exact form on CTA pairs (tcgen05 cta_group::2)")
     else:
         a = src.index("template <int T, bool TF32, int TN>\n__global__ void __launch_bounds__(192, 1)")
