@@ -1302,11 +1302,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 // cross-lane reduction, no shared memory, no barrier between the epilogue
 // warps.  The pair-panel's first two k-blocks meet panel 2P + 1 below its
 // diagonal, where J' is zero: unless they are the whole tile they go last, as
-// N = 128 MMAs over panel 2P's rows (a 128-row copy of J'); a pair-panel
-// without panel 2P + 1 (odd panel count) runs N = 128 MMAs throughout.  The
-// charges come from the int8 copy of Q^T (int16 when SPLIT) that k_make_qt
-// writes beside the FP16 operand: 256 contiguous bytes per configuration and
-// tile, loaded before the tile's accumulator is ready.  Each 32-site chunk of
+// N = 128 MMAs over panel 2P's rows (loaded through a 128-row tensor map of
+// J'); a pair-panel without panel 2P + 1 (odd panel count) runs N = 128 MMAs
+// throughout.  The charges come from the int8 copy of Q^T (int16 when SPLIT)
+// that k_make_qt writes beside the FP16 operand: 256 contiguous bytes (512)
+// per configuration and tile, loaded before the tile's accumulator is ready.  Each 32-site chunk of
 // products is summed in int32 under the same host bound as the one-CTA kernel
 // (32 max|q a| < 2^31), the chunks in 64 bits; SPLIT sums the products in 64
 // bits directly.  Work units and slots are pair_schedule's.
